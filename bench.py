@@ -1,0 +1,294 @@
+"""Benchmark of the offload-pattern hot path on GB300.
+
+Workload: the 19-point Jacobi program on a 257 x 257 x 513 float grid,
+200 iterations, all six loop nests offloaded (gene 0b111111) with hoisted
+transfers -- the configuration the GA search at scale runs on.  One step is
+one whole pattern run (setup nests + 200 x [stencil, copy-back, two boundary
+nests]).  Metric: effective HBM GB/s of the pattern = algorithmic bytes of
+all nests / step time (stencil 56 B, copy-back 8 B per interior point and
+iteration; setup 56 B per point; faces 4 B per face point and iteration).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the FP64 C oracle (test infrastructure) on the host
+cores on a bounded sample of the same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+I, J, K, ITERS = 257, 257, 513, 200
+GENE, HOIST = 0b111111, 1
+METRIC = "stencil GB/s; GEMM/FFT solves/s; p50/p99 served vs plain offload at stated tol"
+WORKLOAD = "jacobi19_257x257x513_it200_gene63_hoist"
+
+
+def nint(i=None, j=None, k=None):
+    i, j, k = i or I, j or J, k or K
+    return (i - 2) * (j - 2) * (k - 2)
+
+
+def pattern_bytes(i=None, j=None, k=None, iters=None):
+    """Algorithmic bytes of one whole pattern run."""
+    i, j, k = i or I, j or J, k or K
+    iters = ITERS if iters is None else iters
+    n = i * j * k
+    faces = n - nint(i, j, k)
+    setup = 48 * n + 8 * n
+    per_iter = 56 * nint(i, j, k) + 8 * nint(i, j, k) + 4 * faces + 4 * 2 * i * j
+    return setup + iters * per_iter
+
+
+STENCIL_BYTES = 56 * nint()   # per stencil launch
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % index)
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[4:]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        loaded = [r for r in rows if r[2] > 250.0] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in loaded for i, v in enumerate(r[3][1:5]) if v == "Active"})
+        return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows), "samples": len(loaded), "reasons": reasons}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def oracle_sample(iters):
+    """The oracle as it stands on a bounded sample: the whole program at full
+    grid size for `iters` iterations, single-threaded FP64 C."""
+    import oracle
+    t0 = time.perf_counter()
+    oracle.jacobi_run(I, J, K, iters, mode=1, want_p=False)
+    dt = time.perf_counter() - t0
+    return pattern_bytes(iters=iters) / dt / 1e9, dt
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    iters = 2
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        oracle_sample(iters)
+    vals, times = [], []
+    for _ in range(args.steps):
+        v, dt = oracle_sample(iters)
+        vals.append(v)
+        times.append(dt)
+    value = len(vals) * pattern_bytes(iters=iters) / sum(times) / 1e9
+    sample = "%dx%dx%d grid, %d of %d iterations per step (whole program), FP64 C oracle" % (
+        I, J, K, iters, ITERS)
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GB/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1e3 * sum(times) / len(times), 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": [I, J, K], "iters": ITERS, "gene": GENE,
+                       "hoist": HOIST, "l2": "inputs larger than L2 (2 GB working set)"},
+            "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    from paper_2011_03602_gb300 import oo
+
+    ws, rank, local = dist_env()
+    dev = local if ws > 1 else 0
+    torch.cuda.set_device(dev)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", dev))
+        pg = dist
+    stream = torch.cuda.Stream()
+    ctx = oo.oo_create(dev, stream)
+    prob = oo.jacobi(I, J, K, ITERS)
+    p_dev = torch.empty(I * J * K, dtype=torch.float32, device="cuda")
+    r_dev = torch.empty(ITERS, dtype=torch.float64, device="cuda")
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up (also allocates the workspace)
+    for _ in range(max(args.warmup, 3)):
+        oo.oo_run_pattern_dev(ctx, GENE, HOIST, prob, p_dev, r_dev)
+
+    # ---- timed region: device-resident outputs
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(dev)
+    with sampler:
+        barrier()
+        e0.record(stream)
+        for _ in range(args.steps):
+            oo.oo_run_pattern_dev(ctx, GENE, HOIST, prob, p_dev, r_dev)
+        e1.record(stream)
+        barrier()
+    ms = e0.elapsed_time(e1)
+    if pg is not None:
+        t = torch.tensor([ms], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = ws * pattern_bytes() / (ms_step * 1e-3) / 1e9
+    res_check = r_dev.cpu().numpy()
+
+    # ---- per-kernel durations with CUDA events on the launching stream
+    st = oo.oo_run_pattern_dev(ctx, GENE, HOIST, oo.jacobi(I, J, K, ITERS, timing=True), p_dev, r_dev)
+    stencil_ms = st["nest_ms"][2] / ITERS
+    copy_ms = st["nest_ms"][3] / ITERS
+    peak, peak_src = load_peaks()
+    achieved = STENCIL_BYTES / (stencil_ms * 1e-3) / 1e9
+
+    # ---- end to end through the C ABI with host buffers
+    p_host = np.empty(I * J * K, np.float32)
+    r_host = np.empty(ITERS, np.float64)
+    oo.oo_run_pattern(ctx, GENE, HOIST, prob, p_host, r_host)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oo.oo_run_pattern(ctx, GENE, HOIST, prob, p_host, r_host)
+    e2e_s = time.perf_counter() - t0
+    if pg is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = ws * pattern_bytes() * args.steps / e2e_s / 1e9
+    oo.oo_destroy(ctx)
+
+    if rank == 0:
+        cpu = None
+        if ws == 1 and not args.no_cpu_baseline:
+            v, dt = oracle_sample(2)
+            cpu = {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                   "sample": "%dx%dx%d grid, 2 of %d iterations, whole program, FP64 C oracle, %.1f s"
+                             % (I, J, K, ITERS, dt)}
+        traffic = None
+        tpath = os.path.join(ROOT, "profiles", "stencil_traffic.json")
+        if os.path.exists(tpath):
+            try:
+                traffic = json.load(open(tpath)).get("bytes_per_full_launch")
+            except Exception:
+                traffic = None
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": [I, J, K], "iters": ITERS, "gene": GENE,
+                       "hoist": HOIST, "parallelism": "replicas" if ws > 1 else "single",
+                       "l2": "inputs larger than L2 (2 GB working set), no flush"},
+            "roofline": {"bound": "hbm", "kernel": "stencil (nest N2)",
+                         "achieved": round(achieved, 1), "peak": peak, "peak_source": peak_src,
+                         "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": traffic,
+                         "stencil_ms": round(stencil_ms, 5), "copyback_ms": round(copy_ms, 5)},
+            "cpu_baseline": cpu,
+            "e2e": {"value": round(e2e, 2), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 4 * I * J * K + 8 * ITERS},
+            "gpu_launches": (2 + 4 * ITERS) * args.steps,
+            "clocks": sampler.summary(),
+            "residual_last": float(res_check[-1]),
+        }
+        print(json.dumps(line))
+    if pg is not None:
+        pg.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid", type=int, nargs=3, default=None,
+                    help="profiling only: a smaller I J K than the benchmark workload")
+    ap.add_argument("--iters", type=int, default=None, help="profiling only")
+    args = ap.parse_args()
+    global I, J, K, ITERS, STENCIL_BYTES, WORKLOAD
+    if args.grid or args.iters:
+        I, J, K = args.grid or (I, J, K)
+        ITERS = args.iters or ITERS
+        STENCIL_BYTES = 56 * nint(I, J, K)
+        WORKLOAD = "jacobi19_%dx%dx%d_it%d_gene63_hoist" % (I, J, K, ITERS)
+        args.no_cpu_baseline = True
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,229 @@
+/*
+ * oo.h -- C ABI of the GB300 offload-pattern library (liboo.so).
+ *
+ * The library executes "offload patterns" in the sense of Yamato, "Study of
+ * Automatic GPU Offloading Method from Various Language Applications"
+ * (arXiv:2011.03602):
+ *   - loop offload (Sec. 3.2.1, Sec. 4.2.2): a gene holds one bit per
+ *     parallelisable loop nest (1 = run on the GPU, 0 = on the CPU); the
+ *     CPU<->GPU copies the placement implies are derived from which side sets
+ *     and which side references each variable, and are hoisted to the
+ *     outermost level the variable allows; a GA searches genes by measured
+ *     time, a result outside tolerance counting as infinitely slow;
+ *   - function-block offload (Sec. 3.2.2, Sec. 4.2.1): a callee found by name
+ *     in a code-pattern table (a matrix product, a Fourier transform) is
+ *     replaced by a GPU implementation behind a CPU-side interface;
+ *   - the language-independent common part (Sec. 4.3): loop/variable tables,
+ *     gene handling and name matching live here, behind one C ABI that C,
+ *     Python (ctypes) and Java (JNI) front-ends call.
+ *
+ * Conventions for every entry point:
+ *   - Every call returns an oo_status; OO_OK (0) on success, a negative code
+ *     otherwise.  No C++ exception crosses this boundary.  On error the
+ *     context's oo_last_error() holds a one-line description.
+ *   - Host pointers are caller-owned and only read/written during the call.
+ *     "_dev" variants take device pointers the caller owns (for example
+ *     torch tensors' data_ptr()); work is queued on the context's stream and
+ *     the call returns without synchronising unless stated otherwise.
+ *   - The library owns the device memory and pinned host memory it allocates
+ *     for its own workspaces and frees them in oo_destroy().
+ *   - A context is used by one host thread at a time.
+ *   - There is no CPU fallback: if the CUDA path fails, the call returns
+ *     OO_ECUDA.  CPU execution of gene bits set to 0 is the method itself.
+ */
+#ifndef OO_H
+#define OO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status */
+typedef int oo_status;
+enum {
+    OO_OK = 0,
+    OO_EINVAL = -1,      /* bad argument (size, pointer, gene, mode)          */
+    OO_ENOMEM = -2,      /* device or pinned host allocation failed           */
+    OO_ECUDA = -3,       /* a CUDA call or kernel failed                      */
+    OO_ETIMEOUT = -4,    /* a bounded device or host wait ran out             */
+    OO_ETOLERANCE = -5,  /* result outside the correctness tolerance          */
+    OO_EBUSY = -6,       /* no slot / memory free right now (back-pressure)   */
+    OO_ENOTFOUND = -7,   /* name not in the code-pattern table                */
+    OO_ESTATE = -8       /* call not valid in the context's current state     */
+};
+
+typedef struct oo_ctx oo_ctx;
+
+/* Create a context on CUDA device `device`.  `cuda_stream` is a
+ * cudaStream_t to queue work on, or NULL for a stream the context creates
+ * and owns.  *out receives the context.  OO_ECUDA if the device cannot be
+ * used (no GPU, driver missing), OO_EINVAL for a NULL `out`.
+ * device == -1 makes a host-only context: loop tables, transfer plans and
+ * lookups work, any call that needs the GPU returns OO_ESTATE.             */
+oo_status oo_create(int device, void *cuda_stream, oo_ctx **out);
+/* Free every resource of the context (NULL is ignored). */
+void oo_destroy(oo_ctx *ctx);
+/* Static text for a status code. */
+const char *oo_status_str(oo_status s);
+/* Detail of the last error on this context; valid until the next call. */
+const char *oo_last_error(const oo_ctx *ctx);
+/* Block until all work queued on the context's stream is done. */
+oo_status oo_sync(oo_ctx *ctx);
+
+/* ----------------------------------------------- loop / variable table */
+/* Sec. 4.3: loops and the variables each one reads and sets are kept in a
+ * language-independent table.  A nest's variable sets are bit masks over
+ * the variable list (at most 64 variables, 64 nests).
+ *   level          0 = runs once before the loop, 1 = runs every iteration
+ *   parallelisable 1 if the nest can run on the GPU at all (Sec. 4.2.2:
+ *                  loops that fail to compile with a GPU directive get no
+ *                  gene bit); the gene length is the count of these
+ *   reads          variables the nest references
+ *   writes         variables the nest sets
+ *   partial        subset of writes that the nest only partly overwrites
+ *                  (the rest of the variable must be current on the side
+ *                  that runs the nest)                                      */
+typedef struct {
+    const char *name;
+    uint64_t bytes;
+} oo_var;
+
+typedef struct {
+    const char *name;
+    int32_t level;
+    int32_t parallelisable;
+    uint64_t reads;
+    uint64_t writes;
+    uint64_t partial;
+} oo_nest;
+
+/* Replace the context's table.  `outputs` = variables the program's caller
+ * reads on the host at the end.  *gene_len_out (may be NULL) receives the
+ * gene length.  Copies the table; the caller keeps ownership of its arrays. */
+oo_status oo_load_nests(oo_ctx *ctx, const oo_nest *nests, int n_nests,
+                        const oo_var *vars, int n_vars, uint64_t outputs,
+                        int *gene_len_out);
+
+/* Load the table of the built-in Jacobi program (six nests: coef, pinit,
+ * stencil, copyback, bc_ij, bc_k; fifteen variables a0..a3, b0..b2,
+ * c0..c2, bnd, wrk1, p, wrk2, res) for an I x J x K grid and `iters`
+ * iterations. */
+oo_status oo_load_jacobi_nests(oo_ctx *ctx, int I, int J, int K, int iters,
+                               int *gene_len_out);
+
+/* One planned copy: before program point `point` (the point-th nest
+ * invocation: setup nests once, then the loop nests `iters` times; point ==
+ * number of invocations is the program end), copy variable `var` in
+ * direction `dir` (+1 host->device, -1 device->host), `bytes` bytes.      */
+typedef struct {
+    int32_t point;
+    int32_t var;
+    int32_t dir;
+    int32_t pad;
+    uint64_t bytes;
+} oo_xfer;
+
+/* Sec. 4.2.2 transfer rules with Sec. 3.2.1 hoisting.  hoist = 1: a copy is
+ * made only when the side about to run a nest lacks a current copy of a
+ * variable the nest reads or partly writes (so loop-invariant data moves
+ * once, outside the loop); hoist = 0: each GPU nest invocation copies its
+ * reads and partial writes in and all its writes out.  Writes up to `cap`
+ * records to `out` (may be NULL with cap 0 to count); *n_out receives the
+ * full count, *h2d / *d2h (may be NULL) the byte totals.                  */
+oo_status oo_transfer_plan(oo_ctx *ctx, uint64_t gene, int hoist, int iters,
+                           oo_xfer *out, int cap, int *n_out, uint64_t *h2d,
+                           uint64_t *d2h);
+
+/* ------------------------------------------------ Jacobi offload patterns */
+/* The loop program: a 19-point 3D Jacobi pressure solver on an I x J x K
+ * float grid (k fastest).  Setup: a0=a1=a2=1, a3=1/6, b*=0, c*=1, bnd=1,
+ * wrk1=0, p = wrk2 = (k/(K-1))^2.  Each iteration: stencil on the interior
+ *   s0 = a0 p[i+1,j,k] + a1 p[i,j+1,k] + a2 p[i,j,k+1]
+ *      + b0 Xij + b1 Xjk + b2 Xik + c0 p[i-1,j,k] + c1 p[i,j-1,k]
+ *      + c2 p[i,j,k-1] + wrk1,
+ *   Xuv = p(+u,+v) - p(+u,-v) - p(-u,+v) + p(-u,-v),
+ *   ss = (s0 a3 - p) bnd,  res[it] += ss^2 (FP64),  wrk2 = p + omega ss;
+ * copy-back p = wrk2 on the interior; faces reset to (k/(K-1))^2.
+ * Per-point arithmetic is carried in float-float (about 44 significant
+ * bits) and rounded once at each float store.                             */
+typedef struct {
+    int32_t I, J, K, iters;
+    float omega;
+    int32_t timing;       /* 1: record per-nest device times (adds events) */
+} oo_jacobi;
+
+typedef struct {
+    double wall_ms;       /* whole pattern, host wall clock, synchronised   */
+    double nest_ms[6];    /* per nest: summed event time (GPU) or host time */
+    double xfer_ms;       /* host wall time spent waiting on copies          */
+    uint64_t h2d_bytes;
+    uint64_t d2h_bytes;
+    int32_t n_xfers;
+    int32_t n_launches;   /* kernels launched by the pattern                */
+} oo_run_stats;
+
+/* Run the Jacobi program with nest placement `gene` (bit b = nest b on the
+ * GPU) and the transfer plan for `hoist`, synchronously.  p_out (host,
+ * I*J*K floats) and res_out (host, iters doubles) receive the final
+ * pressure and the per-iteration residuals; either may be NULL.  stats may
+ * be NULL.  Grids need I, J, K >= 3; K <= 4096; iters >= 0.               */
+oo_status oo_run_pattern(oo_ctx *ctx, uint64_t gene, int hoist,
+                         const oo_jacobi *prob, float *p_out, double *res_out,
+                         oo_run_stats *stats);
+
+/* Same, but the results go to caller-owned DEVICE buffers (p_dev: I*J*K
+ * floats, unpadded, k fastest; res_dev: iters doubles), so no final copy to
+ * the host is made for GPU-resident results.  Synchronous.                */
+oo_status oo_run_pattern_dev(oo_ctx *ctx, uint64_t gene, int hoist,
+                             const oo_jacobi *prob, float *p_dev,
+                             double *res_dev, oo_run_stats *stats);
+
+/* One stencil sweep (nest N2) on caller-owned device arrays.  Every array is
+ * I x J x pitch floats (pitch >= K, pitch % 4 == 0, k fastest, base 16-byte
+ * aligned); coef points to 12 device pointers in the order a0 a1 a2 a3 b0
+ * b1 b2 c0 c1 c2 bnd wrk1.  Writes wrk2 on the interior only and stores the
+ * FP64 sum of ss^2 into *res_dev (device).  Asynchronous on the context's
+ * stream.                                                                 */
+oo_status oo_stencil_dev(oo_ctx *ctx, int I, int J, int K, int pitch,
+                         const float *const *coef, const float *p, float omega,
+                         float *wrk2, double *res_dev);
+
+/* Device row pitch (floats) the library uses for a row of K floats. */
+int oo_jacobi_pitch(int K);
+
+/* ------------------------------------------------------------------- GA */
+/* Sec. 4.2.2 GA over genes, with fitness from measured time.  Readings the
+ * paper leaves open: fitness t^-1/2 (0 when the result failed the
+ * tolerance check against the all-CPU run or the run exceeded
+ * eval_timeout_ms); elitism 1; roulette selection; one-point crossover
+ * (probability pc); per-bit mutation (probability pm); random numbers from
+ * xoshiro256** seeded by splitmix64(seed).  Each distinct gene is measured
+ * once.  history (gens*pop genes) and gene_ms (2^L entries, INFINITY for
+ * genes never measured or failed) may be NULL.                            */
+oo_status oo_ga_search(oo_ctx *ctx, const oo_jacobi *prob, int hoist, int pop,
+                       int gens, double pc, double pm, uint64_t seed,
+                       double eval_timeout_ms, uint64_t *best_gene,
+                       double *best_ms, uint64_t *history, double *gene_ms);
+
+/* The same GA driven by a given time table time_of_gene[2^L] instead of
+ * measurements (L <= 20).  No context needed.                             */
+oo_status oo_ga_table(int L, int pop, int gens, double pc, double pm,
+                      uint64_t seed, const double *time_of_gene,
+                      uint64_t *history, uint64_t *best_gene,
+                      double *best_time);
+
+/* ------------------------------------------------------- function blocks */
+enum { OO_BLOCK_GEMM = 1, OO_BLOCK_FFT = 2 };
+enum { OO_LANG_C = 0, OO_LANG_PYTHON = 1, OO_LANG_JAVA = 2 };
+
+/* Sec. 3.2.2 / Sec. 4.2.1 name match: look a callee name up in the
+ * code-pattern table for language `lang`.  OO_ENOTFOUND if absent.       */
+oo_status oo_lookup_block(const char *callee, int lang, int *block_id);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OO_H */

@@ -1,0 +1,301 @@
+// C ABI of liboo: argument checks, error translation, context lifetime.
+#include <cmath>
+#include <cstring>
+#include <limits>
+#include <map>
+
+#include "oo_internal.h"
+
+using namespace oo;
+
+struct oo_ctx {
+    Ctx c;
+    // cached stencil launch state for oo_stencil_dev (keyed by its arguments)
+    StencilPlan *user_plan = nullptr;
+    std::vector<const void *> user_key;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+template <class F>
+oo_status guarded(oo_ctx *ctx, F &&f) {
+    try {
+        f();
+        if (ctx) ctx->c.last_error.clear();
+        return OO_OK;
+    } catch (const Error &e) {
+        if (ctx) ctx->c.last_error = e.msg;
+        g_last_error = e.msg;
+        return e.code;
+    } catch (const std::bad_alloc &) {
+        if (ctx) ctx->c.last_error = "host allocation failed";
+        return OO_ENOMEM;
+    } catch (const std::exception &e) {
+        if (ctx) ctx->c.last_error = e.what();
+        return OO_EINVAL;
+    } catch (...) {
+        if (ctx) ctx->c.last_error = "unknown failure";
+        return OO_ECUDA;
+    }
+}
+
+void use_device(Ctx &c) {
+    OO_REQUIRE(c.device >= 0, OO_ESTATE, "host-only context (device -1) cannot run GPU work");
+    OO_CUDA_TRY(cudaSetDevice(c.device));
+}
+
+const Ctx::Ref &cpu_reference(Ctx &c, const oo_jacobi &prob) {
+    for (const auto &r : c.refs)
+        if (r.I == prob.I && r.J == prob.J && r.K == prob.K && r.iters == prob.iters &&
+            r.omega == prob.omega)
+            return r;
+    Ctx::Ref r{prob.I, prob.J, prob.K, prob.iters, prob.omega, {}, {}};
+    r.res.resize((size_t)prob.iters);
+    r.p.resize((size_t)prob.I * prob.J * prob.K);
+    oo_jacobi q = prob;
+    q.timing = 0;
+    run_pattern(c, 0, 1, q, r.p.data(), r.res.data(), false, nullptr);
+    c.refs.push_back(std::move(r));
+    return c.refs.back();
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *oo_status_str(oo_status s) {
+    switch (s) {
+        case OO_OK: return "ok";
+        case OO_EINVAL: return "invalid argument";
+        case OO_ENOMEM: return "out of memory";
+        case OO_ECUDA: return "CUDA failure";
+        case OO_ETIMEOUT: return "timed out";
+        case OO_ETOLERANCE: return "result outside tolerance";
+        case OO_EBUSY: return "busy";
+        case OO_ENOTFOUND: return "not found";
+        case OO_ESTATE: return "invalid state";
+        default: return "unknown status";
+    }
+}
+
+const char *oo_last_error(const oo_ctx *ctx) {
+    return ctx ? ctx->c.last_error.c_str() : g_last_error.c_str();
+}
+
+oo_status oo_create(int device, void *cuda_stream, oo_ctx **out) {
+    if (!out) return OO_EINVAL;
+    *out = nullptr;
+    oo_ctx *ctx = new (std::nothrow) oo_ctx();
+    if (!ctx) return OO_ENOMEM;
+    if (device == -1) {  // host-only context: tables, plans, table-driven GA
+        ctx->c.device = -1;
+        *out = ctx;
+        return OO_OK;
+    }
+    const oo_status st = guarded(nullptr, [&] {
+        int n = 0;
+        OO_CUDA_TRY(cudaGetDeviceCount(&n));
+        OO_REQUIRE(device >= 0 && device < n, OO_EINVAL, "no such CUDA device");
+        ctx->c.device = device;
+        OO_CUDA_TRY(cudaSetDevice(device));
+        OO_CUDA_TRY(cudaDeviceGetAttribute(&ctx->c.num_sms, cudaDevAttrMultiProcessorCount, device));
+        if (cuda_stream) {
+            ctx->c.stream = static_cast<cudaStream_t>(cuda_stream);
+        } else {
+            OO_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->c.stream, cudaStreamNonBlocking));
+            ctx->c.own_stream = true;
+        }
+    });
+    if (st != OO_OK) {
+        delete ctx;
+        return st;
+    }
+    *out = ctx;
+    return OO_OK;
+}
+
+void oo_destroy(oo_ctx *ctx) {
+    if (!ctx) return;
+    if (ctx->c.device < 0) {
+        delete ctx;
+        return;
+    }
+    cudaSetDevice(ctx->c.device);
+    if (ctx->c.stream) cudaStreamSynchronize(ctx->c.stream);
+    stencil_plan_destroy(ctx->user_plan);
+    jacobi_work_free(ctx->c.jw);
+    if (ctx->c.own_stream && ctx->c.stream) cudaStreamDestroy(ctx->c.stream);
+    delete ctx;
+}
+
+oo_status oo_sync(oo_ctx *ctx) {
+    if (!ctx) return OO_EINVAL;
+    return guarded(ctx, [&] {
+        use_device(ctx->c);
+        OO_CUDA_TRY(cudaStreamSynchronize(ctx->c.stream));
+    });
+}
+
+oo_status oo_load_nests(oo_ctx *ctx, const oo_nest *nests, int n_nests, const oo_var *vars,
+                        int n_vars, uint64_t outputs, int *gene_len_out) {
+    if (!ctx) return OO_EINVAL;
+    return guarded(ctx, [&] {
+        OO_REQUIRE(nests && vars && n_nests > 0 && n_vars > 0, OO_EINVAL, "empty table");
+        NestTable t;
+        for (int v = 0; v < n_vars; ++v) t.vars.push_back({vars[v].name ? vars[v].name : "", vars[v].bytes});
+        for (int n = 0; n < n_nests; ++n)
+            t.nests.push_back({nests[n].name ? nests[n].name : "", nests[n].level,
+                               nests[n].parallelisable ? 1 : 0, nests[n].reads, nests[n].writes,
+                               nests[n].partial});
+        t.outputs = outputs;
+        validate_table(t);
+        ctx->c.table = std::move(t);
+        ctx->c.have_table = true;
+        if (gene_len_out) *gene_len_out = ctx->c.table.gene_len();
+    });
+}
+
+oo_status oo_load_jacobi_nests(oo_ctx *ctx, int I, int J, int K, int iters, int *gene_len_out) {
+    if (!ctx) return OO_EINVAL;
+    return guarded(ctx, [&] {
+        OO_REQUIRE(I >= 3 && J >= 3 && K >= 3 && iters >= 0, OO_EINVAL, "bad Jacobi problem");
+        ctx->c.table = jacobi_table(I, J, K, iters);
+        ctx->c.have_table = true;
+        if (gene_len_out) *gene_len_out = ctx->c.table.gene_len();
+    });
+}
+
+oo_status oo_transfer_plan(oo_ctx *ctx, uint64_t gene, int hoist, int iters, oo_xfer *out, int cap,
+                           int *n_out, uint64_t *h2d, uint64_t *d2h) {
+    if (!ctx) return OO_EINVAL;
+    return guarded(ctx, [&] {
+        OO_REQUIRE(ctx->c.have_table, OO_ESTATE, "no loop-nest table loaded");
+        OO_REQUIRE(hoist == 0 || hoist == 1, OO_EINVAL, "hoist must be 0 or 1");
+        OO_REQUIRE(cap >= 0 && (cap == 0 || out), OO_EINVAL, "bad output buffer");
+        const auto plan = make_plan(ctx->c.table, gene, hoist, iters, h2d, d2h);
+        const size_t n = std::min(plan.size(), (size_t)cap);
+        if (n) std::memcpy(out, plan.data(), n * sizeof(oo_xfer));
+        if (n_out) *n_out = (int)plan.size();
+    });
+}
+
+int oo_jacobi_pitch(int K) { return jacobi_pitch(K); }
+
+oo_status oo_run_pattern(oo_ctx *ctx, uint64_t gene, int hoist, const oo_jacobi *prob, float *p_out,
+                         double *res_out, oo_run_stats *stats) {
+    if (!ctx || !prob) return OO_EINVAL;
+    return guarded(ctx, [&] {
+        use_device(ctx->c);
+        run_pattern(ctx->c, gene, hoist, *prob, p_out, res_out, false, stats);
+    });
+}
+
+oo_status oo_run_pattern_dev(oo_ctx *ctx, uint64_t gene, int hoist, const oo_jacobi *prob, float *p_dev,
+                             double *res_dev, oo_run_stats *stats) {
+    if (!ctx || !prob) return OO_EINVAL;
+    return guarded(ctx, [&] {
+        use_device(ctx->c);
+        run_pattern(ctx->c, gene, hoist, *prob, p_dev, res_dev, true, stats);
+    });
+}
+
+oo_status oo_stencil_dev(oo_ctx *ctx, int I, int J, int K, int pitch, const float *const *coef,
+                         const float *p, float omega, float *wrk2, double *res_dev) {
+    if (!ctx) return OO_EINVAL;
+    return guarded(ctx, [&] {
+        OO_REQUIRE(coef && p && wrk2 && res_dev, OO_EINVAL, "null pointer");
+        for (int a = 0; a < NCOEF; ++a) OO_REQUIRE(coef[a] != nullptr, OO_EINVAL, "null coefficient array");
+        OO_REQUIRE(I >= 3 && J >= 3 && K >= 3 && K <= 4096, OO_EINVAL, "bad grid");
+        OO_REQUIRE(pitch >= K && pitch % 4 == 0, OO_EINVAL, "pitch must be >= K and a multiple of 4");
+        OO_REQUIRE(std::isfinite(omega), OO_EINVAL, "omega must be finite");
+        use_device(ctx->c);
+        std::vector<const void *> key(coef, coef + NCOEF);
+        key.push_back(p);
+        key.push_back(wrk2);
+        key.push_back(reinterpret_cast<const void *>((uintptr_t)I));
+        key.push_back(reinterpret_cast<const void *>((uintptr_t)J));
+        key.push_back(reinterpret_cast<const void *>((uintptr_t)K));
+        key.push_back(reinterpret_cast<const void *>((uintptr_t)pitch));
+        if (!ctx->user_plan || ctx->user_key != key) {
+            if (ctx->user_plan) {
+                OO_CUDA_TRY(cudaStreamSynchronize(ctx->c.stream));
+                stencil_plan_destroy(ctx->user_plan);
+                ctx->user_plan = nullptr;
+            }
+            ctx->user_plan = stencil_plan_create(JacobiDims{I, J, K, pitch}, coef, p, wrk2, ctx->c.num_sms);
+            ctx->user_key = key;
+        }
+        launch_stencil(ctx->user_plan, omega, res_dev, ctx->c.stream);
+    });
+}
+
+oo_status oo_ga_table(int L, int pop, int gens, double pc, double pm, uint64_t seed,
+                      const double *time_of_gene, uint64_t *history, uint64_t *best_gene,
+                      double *best_time) {
+    return guarded(nullptr, [&] {
+        OO_REQUIRE(L >= 1 && L <= 20, OO_EINVAL, "table GA needs 1 <= L <= 20");
+        OO_REQUIRE(time_of_gene && best_gene && best_time, OO_EINVAL, "null pointer");
+        const GaResult r = ga_run(L, pop, gens, pc, pm, seed,
+                                  [&](uint64_t g) { return time_of_gene[g]; });
+        if (history) std::memcpy(history, r.history.data(), r.history.size() * 8);
+        *best_gene = r.best_gene;
+        *best_time = r.best_time;
+    });
+}
+
+oo_status oo_ga_search(oo_ctx *ctx, const oo_jacobi *prob, int hoist, int pop, int gens, double pc,
+                       double pm, uint64_t seed, double eval_timeout_ms, uint64_t *best_gene,
+                       double *best_ms, uint64_t *history, double *gene_ms) {
+    if (!ctx || !prob) return OO_EINVAL;
+    return guarded(ctx, [&] {
+        OO_REQUIRE(best_gene && best_ms, OO_EINVAL, "null pointer");
+        use_device(ctx->c);
+        const Ctx::Ref &ref = cpu_reference(ctx->c, *prob);
+        const int L = 6;
+        std::map<uint64_t, double> memo;
+        std::vector<float> p((size_t)prob->I * prob->J * prob->K);
+        std::vector<double> res((size_t)prob->iters);
+        auto measure = [&](uint64_t g) -> double {
+            auto it = memo.find(g);
+            if (it != memo.end()) return it->second;
+            oo_run_stats st{};
+            bool aborted = false;
+            oo_jacobi q = *prob;
+            q.timing = 0;
+            run_pattern(ctx->c, g, hoist, q, p.data(), res.data(), false, &st, eval_timeout_ms, &aborted);
+            double t = aborted ? INFINITY : st.wall_ms;
+            if (!aborted) {
+                // Sec. 4.2.2: a result that differs from the original beyond
+                // tolerance counts as infinitely slow
+                for (size_t x = 0; x < res.size(); ++x)
+                    if (!(std::fabs(res[x] - ref.res[x]) <= 1e-5 * std::fabs(ref.res[x]))) t = INFINITY;
+                for (size_t x = 0; x < p.size() && std::isfinite(t); ++x)
+                    if (!(std::fabs(p[x] - ref.p[x]) <= 1e-5f)) t = INFINITY;
+            }
+            memo[g] = t;
+            return t;
+        };
+        const GaResult r = ga_run(L, pop, gens, pc, pm, seed, measure);
+        if (history) std::memcpy(history, r.history.data(), r.history.size() * 8);
+        if (gene_ms) {
+            for (int g = 0; g < (1 << L); ++g) gene_ms[g] = INFINITY;
+            for (const auto &kv : memo) gene_ms[kv.first] = kv.second;
+        }
+        *best_gene = r.best_gene;
+        *best_ms = r.best_time;
+    });
+}
+
+oo_status oo_lookup_block(const char *callee, int lang, int *block_id) {
+    return guarded(nullptr, [&] {
+        OO_REQUIRE(callee && block_id, OO_EINVAL, "null pointer");
+        OO_REQUIRE(lang >= OO_LANG_C && lang <= OO_LANG_JAVA, OO_EINVAL, "unknown language");
+        const int b = lookup_block(callee, lang);
+        OO_REQUIRE(b != 0, OO_ENOTFOUND, std::string("no code pattern for ") + callee);
+        *block_id = b;
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,738 @@
+// GPU nests of the Jacobi program (sm_103a).
+//
+// The six loop nests a gene can place on the GPU (Sec. 3.2.1, Sec. 4.2.2):
+//   N0 coef      fill the twelve coefficient arrays           (write stream)
+//   N1 pinit     p = wrk2 = (k/(K-1))^2                        (write stream)
+//   N2 stencil   19-point update + FP64 residual               (HBM bound)
+//   N3 copyback  p = wrk2 on the interior                      (copy)
+//   N4 bc_ij     Dirichlet faces i, j                          (tiny)
+//   N5 bc_k      Dirichlet faces k                             (tiny)
+//
+// Device layout: each array is I x J x pitch floats, k fastest, pitch a
+// multiple of 32 floats (128-byte rows) so every row starts on a TMA- and
+// float4-aligned address.
+//
+// N2 is a persistent, warp-specialised kernel.  One producer thread streams
+// tiles with TMA (cp.async.bulk.tensor) into shared memory: for every plane i
+// of a work unit, the twelve coefficient tiles (TK x TJ) and one p tile with
+// a one-point halo in j and a 4-float-aligned halo in k.  Consumer warps
+// march i through the unit with the three p planes i-1, i, i+1 resident in a
+// ring, compute the update in float-float arithmetic (error-free sums and
+// FMA products, about 44 significant bits, rounded once at the store), and
+// accumulate ss^2 in FP64.  Every unit's partial residual goes to scratch;
+// the last CTA to finish sums the partials in unit order, so the residual
+// is deterministic.  Every mbarrier wait is bounded; a wait that runs out
+// sets an error word the host reads, drains the copies in flight and exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "oo_internal.h"
+
+namespace oo {
+
+// ===================================================================== helpers
+namespace {
+
+constexpr long long kWaitLimitCycles = 2000000000ll;  // ~1 s at 2 GHz
+
+__device__ __forceinline__ float dirichlet_dev(int k, int K) {
+    return __fdiv_rn((float)(k * k), (float)((K - 1) * (K - 1)));
+}
+
+// -------- float-float building blocks (Knuth two-sum, FMA two-product)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+// (H, L) += (th, tl)
+__device__ __forceinline__ void ff_acc(float &H, float &L, float th, float tl) {
+    float e;
+    two_sum(H, th, H, e);
+    L = __fadd_rn(L, __fadd_rn(e, tl));
+}
+// b * (q1 - q2 - q3 + q4) as a float-float product term
+__device__ __forceinline__ void ff_cross(float b, float q1, float q2, float q3, float q4,
+                                         float &th, float &tl) {
+    float d1, e1, d2, e2, xh, e3;
+    two_sum(q1, -q2, d1, e1);
+    two_sum(q4, -q3, d2, e2);
+    two_sum(d1, d2, xh, e3);
+    const float xl = __fadd_rn(__fadd_rn(e1, e2), e3);
+    float t1;
+    two_prod(b, xh, th, t1);
+    tl = __fmaf_rn(b, xl, t1);
+}
+
+// -------- mbarrier / TMA (inline PTX)
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile(
+        "{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
+            bar),
+        "r"(bytes)
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred P;\n\tmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, P;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait.  Returns false when the CTA aborted or the limit ran out.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag,
+                                          unsigned *err, unsigned code) {
+    if (mbar_try(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (true) {
+        if (mbar_try(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (clock64() - t0 > kWaitLimitCycles) {
+            *abort_flag = 1;
+            atomicOr(err, code);
+            return false;
+        }
+    }
+}
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, int c0, int c1,
+                                            int c2, uint32_t bar, uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        ".L2::cache_hint [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(bar), "l"(policy)
+        : "memory");
+}
+
+}  // namespace
+
+// ============================================================ simple nests
+namespace {
+
+__global__ void coef_kernel(float *base, size_t stride, size_t n4) {
+    const float val[NCOEF] = {1.0f, 1.0f, 1.0f, 1.0f / 6.0f, 0.0f, 0.0f,
+                              0.0f, 1.0f, 1.0f, 1.0f,        1.0f, 0.0f};
+    const size_t step = (size_t)gridDim.x * blockDim.x;
+    for (size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x; x < n4; x += step) {
+#pragma unroll
+        for (int a = 0; a < NCOEF; ++a) {
+            const float v = val[a];
+            reinterpret_cast<float4 *>(base + a * stride)[x] = make_float4(v, v, v, v);
+        }
+    }
+}
+
+// rows = I*J, each `pitch` floats; thread handles float4 chunk c of row r.
+__global__ void pinit_kernel(float *p, float *wrk2, int rows, int pitch, int K) {
+    const unsigned chunks = (unsigned)pitch / 4u;
+    const size_t total = (size_t)rows * chunks;
+    const size_t step = (size_t)gridDim.x * blockDim.x;
+    for (size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += step) {
+        const int k = (int)(x % chunks) * 4;
+        float v[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) v[e] = (k + e < K) ? dirichlet_dev(k + e, K) : 0.0f;
+        const float4 q = make_float4(v[0], v[1], v[2], v[3]);
+        reinterpret_cast<float4 *>(p)[x] = q;
+        reinterpret_cast<float4 *>(wrk2)[x] = q;
+    }
+}
+
+// interior rows (I-2)*(J-2); chunks cover k in [0, 4*ceil((K-1)/4))
+__global__ void copyback_kernel(float *p, const float *wrk2, int I, int J, int K, int pitch) {
+    const unsigned chunks = (unsigned)(K - 1 + 3) / 4u;
+    const unsigned jr = (unsigned)(J - 2);
+    const size_t total = (size_t)(I - 2) * jr * chunks;
+    const size_t step = (size_t)gridDim.x * blockDim.x;
+    for (size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += step) {
+        const unsigned c = (unsigned)(x % chunks);
+        const size_t row = x / chunks;
+        const int i = 1 + (int)(row / jr), j = 1 + (int)(row % jr);
+        const size_t off = ((size_t)i * J + j) * pitch + 4u * c;
+        const int k = 4 * (int)c;
+        if (k >= 1 && k + 3 <= K - 2) {
+            reinterpret_cast<float4 *>(p + off)[0] = reinterpret_cast<const float4 *>(wrk2 + off)[0];
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (k + e >= 1 && k + e <= K - 2) p[off + e] = wrk2[off + e];
+        }
+    }
+}
+
+__global__ void bc_ij_kernel(float *p, int I, int J, int K, int pitch) {
+    const unsigned chunks = (unsigned)(K + 3) / 4u;
+    const unsigned face_rows = 2u * J + 2u * (I - 2);
+    const size_t total = (size_t)face_rows * chunks;
+    const size_t step = (size_t)gridDim.x * blockDim.x;
+    for (size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += step) {
+        const unsigned c = (unsigned)(x % chunks);
+        const unsigned r = (unsigned)(x / chunks);
+        int i, j;
+        if (r < 2u * J) {
+            i = (r < (unsigned)J) ? 0 : I - 1;
+            j = (int)(r % (unsigned)J);
+        } else {
+            const unsigned q = r - 2u * J;
+            i = 1 + (int)(q / 2u);
+            j = (q % 2u) ? J - 1 : 0;
+        }
+        const size_t off = ((size_t)i * J + j) * pitch + 4u * c;
+        const int k = 4 * (int)c;
+        if (k + 3 < K) {
+            reinterpret_cast<float4 *>(p + off)[0] =
+                make_float4(dirichlet_dev(k, K), dirichlet_dev(k + 1, K), dirichlet_dev(k + 2, K),
+                            dirichlet_dev(k + 3, K));
+        } else {
+            for (int e = 0; e < 4 && k + e < K; ++e) p[off + e] = dirichlet_dev(k + e, K);
+        }
+    }
+}
+
+__global__ void bc_k_kernel(float *p, int rows, int K, int pitch) {
+    const float g0 = dirichlet_dev(0, K), g1 = dirichlet_dev(K - 1, K);
+    const int step = gridDim.x * blockDim.x;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += step) {
+        p[(size_t)r * pitch] = g0;
+        p[(size_t)r * pitch + K - 1] = g1;
+    }
+}
+
+int grid_for(size_t work, int threads, int max_blocks) {
+    const size_t b = (work + threads - 1) / threads;
+    return (int)std::max<size_t>(1, std::min<size_t>(b, (size_t)max_blocks));
+}
+
+int sm_count() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 148;
+    return n;
+}
+
+}  // namespace
+
+void launch_coef(const JacobiDims &d, float *const coef[NCOEF], cudaStream_t s) {
+    const size_t stride = (size_t)(coef[1] - coef[0]);
+    for (int a = 1; a < NCOEF; ++a)
+        OO_REQUIRE((size_t)(coef[a] - coef[a - 1]) == stride, OO_EINVAL,
+                   "coefficient arrays must be equally spaced");
+    const size_t n4 = d.n_dev() / 4;
+    coef_kernel<<<grid_for(n4, 256, sm_count() * 8), 256, 0, s>>>(coef[0], stride, n4);
+    OO_CUDA_TRY(cudaGetLastError());
+}
+
+void launch_pinit(const JacobiDims &d, float *p, float *wrk2, cudaStream_t s) {
+    const size_t n4 = d.n_dev() / 4;
+    pinit_kernel<<<grid_for(n4, 256, sm_count() * 8), 256, 0, s>>>(p, wrk2, d.I * d.J, d.pitch, d.K);
+    OO_CUDA_TRY(cudaGetLastError());
+}
+
+void launch_copyback(const JacobiDims &d, float *p, const float *wrk2, cudaStream_t s) {
+    const size_t work = (size_t)(d.I - 2) * (d.J - 2) * ((d.K + 2) / 4);
+    copyback_kernel<<<grid_for(work, 256, sm_count() * 8), 256, 0, s>>>(p, wrk2, d.I, d.J, d.K,
+                                                                          d.pitch);
+    OO_CUDA_TRY(cudaGetLastError());
+}
+
+void launch_bc_ij(const JacobiDims &d, float *p, cudaStream_t s) {
+    const size_t work = (size_t)(2 * d.J + 2 * (d.I - 2)) * ((d.K + 3) / 4);
+    bc_ij_kernel<<<grid_for(work, 256, sm_count() * 4), 256, 0, s>>>(p, d.I, d.J, d.K, d.pitch);
+    OO_CUDA_TRY(cudaGetLastError());
+}
+
+void launch_bc_k(const JacobiDims &d, float *p, cudaStream_t s) {
+    const int rows = d.I * d.J;
+    bc_k_kernel<<<grid_for(rows, 256, sm_count() * 4), 256, 0, s>>>(p, rows, d.K, d.pitch);
+    OO_CUDA_TRY(cudaGetLastError());
+}
+
+// ================================================================== stencil
+struct StencilMaps {
+    CUtensorMap coef[NCOEF];
+    CUtensorMap p;
+};
+
+struct StencilArgs {
+    int I, J, K, pitch;
+    int n_kt, n_jt, n_seg, n_units;
+    float omega;
+    float *wrk2;
+    double *partials;   // n_units
+    unsigned *counter;  // CTAs finished (reset by the last one)
+    unsigned *err;      // error bits
+    double *res;        // FP64 residual of this sweep
+};
+
+namespace {
+
+template <int TK, int TJ>
+struct Tile {
+    static constexpr int PW = TK + 8;                   // p tile row: k0-4 .. k0+TK+3
+    static constexpr int PH = TJ + 2;                   // p tile rows: j0-1 .. j0+TJ
+    static constexpr int PSLOT = (PW * PH + 31) / 32 * 32;  // floats, 128-byte multiple
+    static constexpr int CTILE = TK * TJ;               // floats per coefficient tile
+    static constexpr uint32_t PBYTES = PW * PH * 4;
+    static constexpr uint32_t CBYTES = NCOEF * CTILE * 4;
+};
+
+__device__ __forceinline__ void decode_unit(const StencilArgs &a, int u, int I, int TK, int TJ,
+                                            int &k0, int &j0, int &ib, int &ie) {
+    const int kt = u % a.n_kt;
+    const int jt = (u / a.n_kt) % a.n_jt;
+    const int sg = u / (a.n_kt * a.n_jt);
+    k0 = kt * TK;
+    j0 = 1 + jt * TJ;
+    const long long span = I - 2;
+    ib = 1 + (int)(span * sg / a.n_seg);
+    ie = 1 + (int)(span * (sg + 1) / a.n_seg);
+}
+
+template <int TK, int TJ, int NCW, int DC, int DP>
+__global__ void __launch_bounds__((NCW + 1) * 32, 1)
+    stencil_kernel(const __grid_constant__ StencilMaps maps, const StencilArgs a) {
+    using T = Tile<TK, TJ>;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // TMA destinations need 128-byte alignment; the launch adds 128 bytes of slack
+    unsigned char *smem_base = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~static_cast<uintptr_t>(127));
+    float *coef_s = reinterpret_cast<float *>(smem_base);
+    float *p_s = coef_s + (size_t)DC * NCOEF * T::CTILE;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(p_s + (size_t)DP * T::PSLOT);
+    uint64_t *full_c = bars, *empty_c = bars + DC, *full_p = bars + 2 * DC,
+             *empty_p = bars + 2 * DC + DP;
+    double *red = reinterpret_cast<double *>(bars + 2 * (DC + DP));  // 32 doubles
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(red + 32);
+    int *last_flag = const_cast<int *>(reinterpret_cast<volatile int *>(abort_flag + 1));
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int c = 0; c < DC; ++c) {
+            mbar_init(smem_u32(&full_c[c]), 1);
+            mbar_init(smem_u32(&empty_c[c]), NCW);
+        }
+        for (int q = 0; q < DP; ++q) {
+            mbar_init(smem_u32(&full_p[q]), 1);
+            mbar_init(smem_u32(&empty_p[q]), NCW);
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+
+    const int I = a.I, J = a.J, K = a.K;
+
+    if (warp == NCW) {
+        // ------------------------------------------------------ producer
+        if (lane == 0) {
+            const uint64_t pol_stream = policy_evict_first();
+            const uint64_t pol_p = policy_evict_last();
+            uint32_t cfill = 0, pfill = 0;
+            bool ok = true;
+            for (int u = blockIdx.x; ok && u < a.n_units; u += gridDim.x) {
+                int k0, j0, ib, ie;
+                decode_unit(a, u, I, TK, TJ, k0, j0, ib, ie);
+                for (int q = ib - 1; q <= ie; ++q) {
+                    {
+                        const uint32_t slot = pfill % DP, use = pfill / DP;
+                        if (use > 0 &&
+                            !mbar_wait(smem_u32(&empty_p[slot]), (use - 1) & 1, abort_flag, a.err, 1u)) {
+                            ok = false;
+                            break;
+                        }
+                        const uint32_t bar = smem_u32(&full_p[slot]);
+                        mbar_expect_tx(bar, T::PBYTES);
+                        tma_load_3d(smem_u32(p_s + (size_t)slot * T::PSLOT), &maps.p, k0 - 4, j0 - 1, q,
+                                    bar, pol_p);
+                        ++pfill;
+                    }
+                    if (q >= ib + 1) {
+                        const uint32_t slot = cfill % DC, use = cfill / DC;
+                        if (use > 0 &&
+                            !mbar_wait(smem_u32(&empty_c[slot]), (use - 1) & 1, abort_flag, a.err, 2u)) {
+                            ok = false;
+                            break;
+                        }
+                        const uint32_t bar = smem_u32(&full_c[slot]);
+                        mbar_expect_tx(bar, T::CBYTES);
+                        float *dst = coef_s + (size_t)slot * NCOEF * T::CTILE;
+#pragma unroll
+                        for (int c = 0; c < NCOEF; ++c)
+                            tma_load_3d(smem_u32(dst + c * T::CTILE), &maps.coef[c], k0, j0, q - 1, bar,
+                                        pol_stream);
+                        ++cfill;
+                    }
+                }
+            }
+            if (!ok) {
+                // drain: wait (bounded) for the last fill of every slot to land
+                for (int s = 0; s < DP; ++s) {
+                    const uint32_t n = pfill > (uint32_t)s ? (pfill - 1 - s) / DP : 0;
+                    if (pfill > (uint32_t)s) {
+                        const long long t0 = clock64();
+                        while (!mbar_try(smem_u32(&full_p[s]), n & 1) && clock64() - t0 < kWaitLimitCycles) {
+                        }
+                    }
+                }
+                for (int s = 0; s < DC; ++s) {
+                    const uint32_t n = cfill > (uint32_t)s ? (cfill - 1 - s) / DC : 0;
+                    if (cfill > (uint32_t)s) {
+                        const long long t0 = clock64();
+                        while (!mbar_try(smem_u32(&full_c[s]), n & 1) && clock64() - t0 < kWaitLimitCycles) {
+                        }
+                    }
+                }
+            }
+        }
+    } else {
+        // ------------------------------------------------------ consumers
+        constexpr int QR = TK / 4;                       // quads per tile row
+        constexpr int QPT = TJ * QR / (NCW * 32);        // quads per thread per plane
+        static_assert(QPT >= 1 && QPT * NCW * 32 == TJ * QR, "tile / warp mismatch");
+        const float omega = a.omega;
+        uint32_t cuse = 0, pseq = 0;
+        bool ok = true;
+        for (int u = blockIdx.x; ok && u < a.n_units; u += gridDim.x) {
+            int k0, j0, ib, ie;
+            decode_unit(a, u, I, TK, TJ, k0, j0, ib, ie);
+            double racc = 0.0;
+            const uint32_t pbase = pseq;
+            // planes ib-1 and ib must be present before the first compute
+            for (uint32_t s = pbase; s < pbase + 2; ++s)
+                if (!mbar_wait(smem_u32(&full_p[s % DP]), (s / DP) & 1, abort_flag, a.err, 4u)) {
+                    ok = false;
+                    break;
+                }
+            for (int i = ib; ok && i < ie; ++i) {
+                const uint32_t sprev = pbase + (uint32_t)(i - ib);
+                const uint32_t snext = sprev + 2;
+                if (!mbar_wait(smem_u32(&full_p[snext % DP]), (snext / DP) & 1, abort_flag, a.err, 4u) ||
+                    !mbar_wait(smem_u32(&full_c[cuse % DC]), (cuse / DC) & 1, abort_flag, a.err, 8u)) {
+                    ok = false;
+                    break;
+                }
+                const float *P0 = p_s + (size_t)(sprev % DP) * T::PSLOT;
+                const float *P1 = p_s + (size_t)((sprev + 1) % DP) * T::PSLOT;
+                const float *P2 = p_s + (size_t)(snext % DP) * T::PSLOT;
+                const float *CS = coef_s + (size_t)(cuse % DC) * NCOEF * T::CTILE;
+#pragma unroll
+                for (int m = 0; m < QPT; ++m) {
+                    const int qd = (warp * 32 + lane) + m * NCW * 32;
+                    const int r = qd / QR, c4 = qd % QR;
+                    const int cc = 4 * c4 + 4;  // column of k in the p tile
+                    auto win6 = [&](const float *P, int row, float w[6]) {
+                        const float *base = P + row * T::PW + cc;
+                        const float4 v = *reinterpret_cast<const float4 *>(base);
+                        w[0] = base[-1];
+                        w[1] = v.x;
+                        w[2] = v.y;
+                        w[3] = v.z;
+                        w[4] = v.w;
+                        w[5] = base[4];
+                    };
+                    auto win4 = [&](const float *P, int row) {
+                        return *reinterpret_cast<const float4 *>(P + row * T::PW + cc);
+                    };
+                    float C6[6], N6[6], S6[6], E6[6], W6[6];
+                    win6(P1, r + 1, C6);
+                    win6(P1, r + 2, N6);
+                    win6(P1, r, S6);
+                    win6(P2, r + 1, E6);
+                    win6(P0, r + 1, W6);
+                    const float4 en = win4(P2, r + 2), es = win4(P2, r), wn = win4(P0, r + 2),
+                                 ws = win4(P0, r);
+                    const float EN[4] = {en.x, en.y, en.z, en.w}, ES[4] = {es.x, es.y, es.z, es.w};
+                    const float WN[4] = {wn.x, wn.y, wn.z, wn.w}, WS[4] = {ws.x, ws.y, ws.z, ws.w};
+                    float cf[NCOEF][4];
+#pragma unroll
+                    for (int c = 0; c < NCOEF; ++c) {
+                        const float4 v = *reinterpret_cast<const float4 *>(CS + c * T::CTILE + r * TK + 4 * c4);
+                        cf[c][0] = v.x;
+                        cf[c][1] = v.y;
+                        cf[c][2] = v.z;
+                        cf[c][3] = v.w;
+                    }
+                    const int j = j0 + r, kb = k0 + 4 * c4;
+                    const bool row_in = (j <= J - 2);
+                    float out[4];
+                    bool inside[4];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int k = kb + e;
+                        inside[e] = row_in && k >= 1 && k <= K - 2;
+                        float H, L, th, tl;
+                        two_prod(cf[0][e], E6[e + 1], H, L);                      // a0 p[i+1]
+                        two_prod(cf[1][e], N6[e + 1], th, tl); ff_acc(H, L, th, tl);  // a1 p[j+1]
+                        two_prod(cf[2][e], C6[e + 2], th, tl); ff_acc(H, L, th, tl);  // a2 p[k+1]
+                        ff_cross(cf[4][e], EN[e], ES[e], WN[e], WS[e], th, tl);       // b0 Xij
+                        ff_acc(H, L, th, tl);
+                        ff_cross(cf[5][e], N6[e + 2], S6[e + 2], N6[e], S6[e], th, tl);  // b1 Xjk
+                        ff_acc(H, L, th, tl);
+                        ff_cross(cf[6][e], E6[e + 2], W6[e + 2], E6[e], W6[e], th, tl);  // b2 Xik
+                        ff_acc(H, L, th, tl);
+                        two_prod(cf[7][e], W6[e + 1], th, tl); ff_acc(H, L, th, tl);  // c0 p[i-1]
+                        two_prod(cf[8][e], S6[e + 1], th, tl); ff_acc(H, L, th, tl);  // c1 p[j-1]
+                        two_prod(cf[9][e], C6[e], th, tl); ff_acc(H, L, th, tl);      // c2 p[k-1]
+                        ff_acc(H, L, cf[11][e], 0.0f);                                // wrk1
+                        // ss = (s0 * a3 - p) * bnd
+                        const float pc = C6[e + 1];
+                        float t1, dh, dl, e1, sh, s1;
+                        two_prod(H, cf[3][e], th, t1);
+                        tl = __fmaf_rn(L, cf[3][e], t1);
+                        two_sum(th, -pc, dh, e1);
+                        dl = __fadd_rn(e1, tl);
+                        two_prod(dh, cf[10][e], sh, s1);
+                        const float sl = __fmaf_rn(dl, cf[10][e], s1);
+                        // wrk2 = p + omega * ss, rounded once
+                        float wh, w1, yh, e2;
+                        two_prod(omega, sh, wh, w1);
+                        const float wl = __fmaf_rn(omega, sl, w1);
+                        two_sum(pc, wh, yh, e2);
+                        out[e] = __fadd_rn(yh, __fadd_rn(e2, wl));
+                        if (inside[e]) {
+                            const double sd = (double)sh + (double)sl;
+                            racc = fma(sd, sd, racc);
+                        }
+                    }
+                    if (row_in) {
+                        float *dst = a.wrk2 + ((size_t)i * J + j) * a.pitch + kb;
+                        if (inside[0] && inside[1] && inside[2] && inside[3]) {
+                            *reinterpret_cast<float4 *>(dst) = make_float4(out[0], out[1], out[2], out[3]);
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < 4; ++e)
+                                if (inside[e]) dst[e] = out[e];
+                        }
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(smem_u32(&empty_c[cuse % DC]));
+                    mbar_arrive(smem_u32(&empty_p[sprev % DP]));
+                }
+                ++cuse;
+            }
+            if (!ok) break;
+            // release the unit's last two planes
+            __syncwarp();
+            if (lane == 0) {
+                const uint32_t s1 = pbase + (uint32_t)(ie - ib);
+                mbar_arrive(smem_u32(&empty_p[s1 % DP]));
+                mbar_arrive(smem_u32(&empty_p[(s1 + 1) % DP]));
+            }
+            pseq = pbase + (uint32_t)(ie - ib + 2);
+            // unit partial residual of this warp (no cross-warp barrier, so an
+            // aborting warp can never leave another one waiting)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) racc += __shfl_xor_sync(0xffffffffu, racc, o);
+            if (lane == 0) {
+                a.partials[(size_t)u * NCW + warp] = racc;
+                __threadfence();
+            }
+        }
+    }
+    __syncthreads();
+
+    // ------------------------------------------ last CTA sums the partials
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned t = atomicAdd(a.counter, 1u);
+        *last_flag = (t == gridDim.x - 1) ? 1 : 0;
+    }
+    __syncthreads();
+    if (*last_flag) {
+        __threadfence();
+        const int np = a.n_units * NCW;
+        double s = 0.0;
+        for (int u = threadIdx.x; u < np; u += blockDim.x) s += __ldcg(&a.partials[u]);
+        // fixed-shape tree: within warps, then warp sums in warp order
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) red[warp] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double tot = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+            *a.res = tot;
+            *a.counter = 0u;
+        }
+    }
+}
+
+// variants: (TK, TJ, NCW, DC, DP)
+template <int TK, int TJ, int NCW, int DC, int DP>
+struct Variant {
+    using T = Tile<TK, TJ>;
+    static constexpr int kThreads = (NCW + 1) * 32;
+    static size_t smem_bytes() {
+        return 128 + (size_t)DC * NCOEF * T::CTILE * 4 + (size_t)DP * T::PSLOT * 4 +
+               2 * (DC + DP) * 8 + 32 * 8 + 16;
+    }
+    static void prepare() {
+        static bool done = false;
+        if (!done) {
+            OO_CUDA_TRY(cudaFuncSetAttribute(stencil_kernel<TK, TJ, NCW, DC, DP>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem_bytes()));
+            done = true;
+        }
+    }
+    static void launch(int grid, const StencilMaps &m, const StencilArgs &a, cudaStream_t s) {
+        prepare();
+        stencil_kernel<TK, TJ, NCW, DC, DP><<<grid, kThreads, smem_bytes(), s>>>(m, a);
+        OO_CUDA_TRY(cudaGetLastError());
+    }
+};
+
+using BigVariant = Variant<128, 8, 8, 3, 5>;
+using SmallVariant = Variant<64, 8, 4, 3, 5>;
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        OO_CUDA_TRY(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                                     cudaEnableDefault, &q));
+        OO_REQUIRE(q == cudaDriverEntryPointSuccess && p != nullptr, OO_ECUDA,
+                   "driver has no cuTensorMapEncodeTiled");
+        fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+void make_map(CUtensorMap *m, const float *base, const JacobiDims &d, uint32_t bx, uint32_t by) {
+    OO_REQUIRE(((uintptr_t)base & 15u) == 0, OO_EINVAL, "array base must be 16-byte aligned");
+    const cuuint64_t dims[3] = {(cuuint64_t)d.pitch, (cuuint64_t)d.J, (cuuint64_t)d.I};
+    const cuuint64_t strides[2] = {(cuuint64_t)d.pitch * 4, (cuuint64_t)d.pitch * d.J * 4};
+    const cuuint32_t box[3] = {bx, by, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float *>(base), dims,
+                                   strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                                   CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    OO_REQUIRE(r == CUDA_SUCCESS, OO_ECUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+}
+
+}  // namespace
+
+struct StencilPlan {
+    JacobiDims d{};
+    bool big = true;
+    int TK = 128, TJ = 8;
+    StencilMaps maps;
+    StencilArgs args{};
+    int grid = 0;
+    void *scratch = nullptr;
+};
+
+StencilPlan *stencil_plan_create(const JacobiDims &d, const float *const coef[NCOEF], const float *p,
+                                 float *wrk2, int num_sms) {
+    OO_REQUIRE(d.I >= 3 && d.J >= 3 && d.K >= 3, OO_EINVAL, "grid must be at least 3 x 3 x 3");
+    OO_REQUIRE(d.pitch >= d.K && d.pitch % 4 == 0, OO_EINVAL, "pitch must be >= K and a multiple of 4");
+    OO_REQUIRE(((uintptr_t)wrk2 & 15u) == 0, OO_EINVAL, "wrk2 must be 16-byte aligned");
+    auto sp = new StencilPlan();
+    sp->d = d;
+    sp->big = d.K - 1 > 64;
+    sp->TK = sp->big ? 128 : 64;
+    sp->TJ = 8;
+    try {
+        for (int c = 0; c < NCOEF; ++c) make_map(&sp->maps.coef[c], coef[c], d, sp->TK, sp->TJ);
+        make_map(&sp->maps.p, p, d, sp->TK + 8, sp->TJ + 2);
+        StencilArgs &a = sp->args;
+        a.I = d.I;
+        a.J = d.J;
+        a.K = d.K;
+        a.pitch = d.pitch;
+        a.n_kt = (d.K - 1 + sp->TK - 1) / sp->TK;
+        a.n_jt = (d.J - 2 + sp->TJ - 1) / sp->TJ;
+        const int cols = a.n_kt * a.n_jt;
+        const int span = d.I - 2;
+        // segments of the i range: balance units over one CTA per SM, with
+        // a small charge for the two halo planes every unit reloads
+        const int G = std::max(1, num_sms);
+        double best = 1e300;
+        int best_seg = 1;
+        for (int ns = 1; ns <= span; ++ns) {
+            const int smax = (span + ns - 1) / ns;
+            const long long units = (long long)cols * ns;
+            const long long rounds = (units + G - 1) / G;
+            const double cost = (double)rounds * (smax + 0.15);
+            if (cost < best - 1e-9) {
+                best = cost;
+                best_seg = ns;
+            }
+        }
+        a.n_seg = best_seg;
+        a.n_units = cols * best_seg;
+        sp->grid = std::min(a.n_units, G);
+        a.wrk2 = wrk2;
+        const size_t bytes = (size_t)a.n_units * 8 * 8 + 256;  // up to 8 consumer warps
+        OO_CUDA_TRY(cudaMalloc(&sp->scratch, bytes));
+        OO_CUDA_TRY(cudaMemset(sp->scratch, 0, bytes));
+        a.partials = reinterpret_cast<double *>(sp->scratch);
+        a.counter = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(sp->scratch) +
+                                                 (size_t)a.n_units * 8 * 8);
+        a.err = a.counter + 1;
+    } catch (...) {
+        if (sp->scratch) cudaFree(sp->scratch);
+        delete sp;
+        throw;
+    }
+    return sp;
+}
+
+void stencil_plan_destroy(StencilPlan *sp) {
+    if (!sp) return;
+    if (sp->scratch) cudaFree(sp->scratch);
+    delete sp;
+}
+
+void launch_stencil(StencilPlan *sp, float omega, double *res_dev, cudaStream_t s) {
+    sp->args.omega = omega;
+    sp->args.res = res_dev;
+    if (sp->big)
+        BigVariant::launch(sp->grid, sp->maps, sp->args, s);
+    else
+        SmallVariant::launch(sp->grid, sp->maps, sp->args, s);
+}
+
+unsigned stencil_plan_check(StencilPlan *sp, cudaStream_t s) {
+    unsigned e = 0;
+    OO_CUDA_TRY(cudaMemcpyAsync(&e, sp->args.err, 4, cudaMemcpyDeviceToHost, s));
+    OO_CUDA_TRY(cudaStreamSynchronize(s));
+    if (e) OO_CUDA_TRY(cudaMemsetAsync(sp->args.err, 0, 4, s));
+    return e;
+}
+
+}  // namespace oo

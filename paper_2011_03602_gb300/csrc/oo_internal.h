@@ -1,0 +1,160 @@
+// Internal declarations of liboo: context, workspaces, kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <functional>
+#include <string>
+#include <vector>
+
+#include "../../include/oo.h"
+
+namespace oo {
+
+// ------------------------------------------------------------ error helpers
+struct Error {
+    oo_status code;
+    std::string msg;
+};
+
+#define OO_CUDA_TRY(expr)                                                        \
+    do {                                                                         \
+        cudaError_t e_ = (expr);                                                 \
+        if (e_ != cudaSuccess)                                                   \
+            throw ::oo::Error{OO_ECUDA, std::string(#expr) + ": " +              \
+                                            cudaGetErrorString(e_)};             \
+    } while (0)
+
+#define OO_REQUIRE(cond, code, text)                                             \
+    do {                                                                         \
+        if (!(cond)) throw ::oo::Error{(code), (text)};                          \
+    } while (0)
+
+// ------------------------------------------------------------- nest tables
+struct NestTable {
+    struct Var {
+        std::string name;
+        uint64_t bytes;
+    };
+    struct Nest {
+        std::string name;
+        int level;
+        int parallelisable;
+        uint64_t reads, writes, partial;
+    };
+    std::vector<Var> vars;
+    std::vector<Nest> nests;
+    uint64_t outputs = 0;
+    int gene_len() const;
+    // placement[n] = 1 when nest n runs on the GPU under `gene`
+    std::vector<int> placement(uint64_t gene) const;
+};
+
+void validate_table(const NestTable &t);
+NestTable jacobi_table(int I, int J, int K, int iters);
+
+// The coherence walk of the transfer rules; returns the ordered copy list.
+std::vector<oo_xfer> make_plan(const NestTable &t, uint64_t gene, int hoist, int iters,
+                               uint64_t *h2d, uint64_t *d2h);
+
+// ------------------------------------------------------------------ Jacobi
+enum { NCOEF = 12, NARR = 14, VAR_P = 12, VAR_WRK2 = 13, VAR_RES = 14 };
+
+struct JacobiDims {
+    int I, J, K, pitch;
+    size_t n_host() const { return (size_t)I * J * K; }
+    size_t n_dev() const { return (size_t)I * J * pitch; }
+};
+
+int jacobi_pitch(int K);
+
+// Opaque per-(I,J,K) stencil launch state (tensor maps, work split, scratch).
+struct StencilPlan;
+
+// Device + pinned host workspace of the Jacobi program for one grid size.
+struct JacobiWork {
+    JacobiDims d{};
+    int iters_cap = 0;
+    float *dev = nullptr;             // NARR arrays, each n_dev() floats
+    size_t dev_stride = 0;            // floats between arrays
+    double *res_dev = nullptr;        // iters_cap doubles
+    float *host = nullptr;            // NARR arrays, each n_host() floats (pinned)
+    double *res_host = nullptr;       // iters_cap doubles (pinned)
+    StencilPlan *splan = nullptr;
+    float *dptr(int v) const { return dev + (size_t)v * dev_stride; }
+    float *hptr(int v) const { return host + (size_t)v * d.n_host(); }
+};
+
+// --------------------------------------------------------------- context
+struct Ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int num_sms = 0;
+    std::string last_error;
+    NestTable table;
+    bool have_table = false;
+    JacobiWork *jw = nullptr;
+    // correctness references for the GA gate: all-CPU residuals per problem
+    struct Ref {
+        int I, J, K, iters;
+        float omega;
+        std::vector<double> res;
+        std::vector<float> p;
+    };
+    std::vector<Ref> refs;
+};
+
+// Kernel launchers (jacobi.cu).  All asynchronous on `s`.
+void launch_coef(const JacobiDims &d, float *const coef[NCOEF], cudaStream_t s);
+void launch_pinit(const JacobiDims &d, float *p, float *wrk2, cudaStream_t s);
+void launch_copyback(const JacobiDims &d, float *p, const float *wrk2, cudaStream_t s);
+void launch_bc_ij(const JacobiDims &d, float *p, cudaStream_t s);
+void launch_bc_k(const JacobiDims &d, float *p, cudaStream_t s);
+
+StencilPlan *stencil_plan_create(const JacobiDims &d, const float *const coef[NCOEF],
+                                 const float *p, float *wrk2, int num_sms);
+void stencil_plan_destroy(StencilPlan *sp);
+// One stencil sweep; the residual (FP64) lands in *res_dev.
+void launch_stencil(StencilPlan *sp, float omega, double *res_dev, cudaStream_t s);
+// Reads and clears the device-side error word of the plan (0 = fine).
+unsigned stencil_plan_check(StencilPlan *sp, cudaStream_t s);
+
+// Host nests (host_nests.cpp), on unpadded I x J x K arrays.
+void host_coef(const JacobiDims &d, float *const coef[NCOEF]);
+void host_pinit(const JacobiDims &d, float *p, float *wrk2);
+double host_stencil(const JacobiDims &d, const float *const coef[NCOEF], const float *p,
+                    float omega, float *wrk2);
+void host_copyback(const JacobiDims &d, float *p, const float *wrk2);
+void host_bc_ij(const JacobiDims &d, float *p);
+void host_bc_k(const JacobiDims &d, float *p);
+
+// Pattern execution (pattern.cpp).
+void run_pattern(Ctx &c, uint64_t gene, int hoist, const oo_jacobi &prob, float *p_out,
+                 double *res_out, bool out_on_device, oo_run_stats *stats,
+                 double abort_after_ms = 0.0, bool *aborted = nullptr);
+void jacobi_work_free(JacobiWork *w);
+
+// GA (ga.cpp).
+struct Rng {
+    uint64_t s[4];
+    void seed(uint64_t seed);
+    uint64_t next();
+    double uniform();
+    int randint(int n);
+};
+uint64_t splitmix64(uint64_t &state);
+
+struct GaResult {
+    uint64_t best_gene = 0;
+    double best_time = 0;
+    std::vector<uint64_t> history;
+};
+// time_of(gene) returns the gene's time (infinity = failed the gate)
+GaResult ga_run(int L, int pop, int gens, double pc, double pm, uint64_t seed,
+                const std::function<double(uint64_t)> &time_of);
+
+// Function-block lookup (blocks.cpp).
+int lookup_block(const char *callee, int lang);
+
+}  // namespace oo

@@ -1,0 +1,285 @@
+// Execution of an offload pattern of the Jacobi program.
+//
+// Sec. 3.2.1 / Sec. 4.2.2: the gene places each parallelisable nest on the
+// GPU (1) or CPU (0); the transfer plan for the placement (hoisted or not)
+// says which variables cross between host and device before which nest.
+// This file walks the program order, issues the planned copies on the
+// context's stream, launches GPU nests there and runs CPU nests on the host
+// after synchronising, then delivers the outputs p and res.  Host arrays are
+// the library's pinned buffers (unpadded, k fastest); device arrays use the
+// padded row pitch the kernels want; copies between the two are 2D.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+
+#include "oo_internal.h"
+
+namespace oo {
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double ms_since(Clock::time_point t0) {
+    return std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
+}
+
+void free_work(JacobiWork *w) {
+    if (!w) return;
+    stencil_plan_destroy(w->splan);
+    if (w->dev) cudaFree(w->dev);
+    if (w->res_dev) cudaFree(w->res_dev);
+    if (w->host) cudaFreeHost(w->host);
+    if (w->res_host) cudaFreeHost(w->res_host);
+    delete w;
+}
+
+JacobiWork *ensure_work(Ctx &c, int I, int J, int K, int iters) {
+    JacobiWork *w = c.jw;
+    if (w && w->d.I == I && w->d.J == J && w->d.K == K && w->iters_cap >= std::max(iters, 1)) return w;
+    if (w && w->d.I == I && w->d.J == J && w->d.K == K) {
+        // only the residual buffers are too small
+        const int cap = std::max(iters, 1);
+        double *rd = nullptr, *rh = nullptr;
+        OO_CUDA_TRY(cudaMalloc(&rd, (size_t)cap * 8));
+        if (cudaHostAlloc(&rh, (size_t)cap * 8, cudaHostAllocDefault) != cudaSuccess) {
+            cudaFree(rd);
+            throw Error{OO_ENOMEM, "pinned residual buffer"};
+        }
+        cudaFree(w->res_dev);
+        cudaFreeHost(w->res_host);
+        w->res_dev = rd;
+        w->res_host = rh;
+        w->iters_cap = cap;
+        return w;
+    }
+    free_work(w);
+    c.jw = nullptr;
+    w = new JacobiWork();
+    try {
+        w->d = JacobiDims{I, J, K, jacobi_pitch(K)};
+        w->iters_cap = std::max(iters, 1);
+        w->dev_stride = (w->d.n_dev() + 63) / 64 * 64;
+        if (cudaMalloc(&w->dev, (size_t)NARR * w->dev_stride * 4) != cudaSuccess) {
+            cudaGetLastError();
+            throw Error{OO_ENOMEM, "device arrays of the Jacobi program"};
+        }
+        OO_CUDA_TRY(cudaMalloc(&w->res_dev, (size_t)w->iters_cap * 8));
+        if (cudaHostAlloc(&w->host, (size_t)NARR * w->d.n_host() * 4, cudaHostAllocDefault) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            throw Error{OO_ENOMEM, "pinned host arrays of the Jacobi program"};
+        }
+        OO_CUDA_TRY(cudaHostAlloc(&w->res_host, (size_t)w->iters_cap * 8, cudaHostAllocDefault));
+        const float *coef[NCOEF];
+        for (int a = 0; a < NCOEF; ++a) coef[a] = w->dptr(a);
+        w->splan = stencil_plan_create(w->d, coef, w->dptr(VAR_P), w->dptr(VAR_WRK2), c.num_sms);
+    } catch (...) {
+        free_work(w);
+        throw;
+    }
+    c.jw = w;
+    return w;
+}
+
+// Copy variable v between the host workspace and the device workspace.
+void copy_var(JacobiWork &w, int v, int dir, int iters, cudaStream_t s) {
+    if (v == VAR_RES) {
+        const size_t bytes = (size_t)iters * 8;
+        if (bytes == 0) return;
+        if (dir > 0)
+            OO_CUDA_TRY(cudaMemcpyAsync(w.res_dev, w.res_host, bytes, cudaMemcpyHostToDevice, s));
+        else
+            OO_CUDA_TRY(cudaMemcpyAsync(w.res_host, w.res_dev, bytes, cudaMemcpyDeviceToHost, s));
+        return;
+    }
+    const size_t wb = (size_t)w.d.K * 4, rows = (size_t)w.d.I * w.d.J;
+    if (dir > 0)
+        OO_CUDA_TRY(cudaMemcpy2DAsync(w.dptr(v), (size_t)w.d.pitch * 4, w.hptr(v), wb, wb, rows,
+                                      cudaMemcpyHostToDevice, s));
+    else
+        OO_CUDA_TRY(cudaMemcpy2DAsync(w.hptr(v), wb, w.dptr(v), (size_t)w.d.pitch * 4, wb, rows,
+                                      cudaMemcpyDeviceToHost, s));
+}
+
+}  // namespace
+
+void jacobi_work_free(JacobiWork *w) { free_work(w); }
+
+void run_pattern(Ctx &c, uint64_t gene, int hoist, const oo_jacobi &prob, float *p_out,
+                 double *res_out, bool out_on_device, oo_run_stats *stats, double abort_after_ms,
+                 bool *aborted) {
+    OO_REQUIRE(prob.I >= 3 && prob.J >= 3 && prob.K >= 3, OO_EINVAL, "grid must be at least 3 x 3 x 3");
+    OO_REQUIRE(prob.K <= 4096 && prob.iters >= 0, OO_EINVAL, "K must be <= 4096 and iters >= 0");
+    OO_REQUIRE((size_t)prob.I * prob.J * prob.K < (1ull << 34), OO_EINVAL, "grid too large");
+    OO_REQUIRE(hoist == 0 || hoist == 1, OO_EINVAL, "hoist must be 0 or 1");
+    OO_REQUIRE(std::isfinite(prob.omega), OO_EINVAL, "omega must be finite");
+    const int iters = prob.iters;
+    const NestTable t = jacobi_table(prob.I, prob.J, prob.K, iters);
+    OO_REQUIRE((gene >> 6) == 0, OO_EINVAL, "the Jacobi program has a 6-bit gene");
+    uint64_t h2d = 0, d2h = 0;
+    const std::vector<oo_xfer> plan = make_plan(t, gene, hoist, iters, &h2d, &d2h);
+    const std::vector<int> gpu = t.placement(gene);
+    JacobiWork &w = *ensure_work(c, prob.I, prob.J, prob.K, iters);
+    const JacobiDims &d = w.d;
+    cudaStream_t s = c.stream;
+    if (aborted) *aborted = false;
+
+    float *hc[NCOEF];
+    float *dc[NCOEF];
+    for (int a = 0; a < NCOEF; ++a) {
+        hc[a] = w.hptr(a);
+        dc[a] = w.dptr(a);
+    }
+    const bool timing = prob.timing != 0;
+    std::vector<cudaEvent_t> evs;
+    std::vector<int> ev_nest;
+    double nest_ms[6] = {0, 0, 0, 0, 0, 0};
+    double xfer_ms = 0.0;
+    int launches = 0;
+    bool stencil_on_gpu = false;
+
+    OO_CUDA_TRY(cudaStreamSynchronize(s));
+    const Clock::time_point t0 = Clock::now();
+
+    const int n_points = 2 + 4 * iters;
+    size_t xi = 0;
+    auto run_transfers = [&](int point) {
+        while (xi < plan.size() && plan[xi].point == point) {
+            if (point == n_points) break;  // outputs are delivered below
+            copy_var(w, plan[xi].var, plan[xi].dir, iters, s);
+            ++xi;
+        }
+    };
+    auto run_nest = [&](int n, int it) {
+        if (gpu[n]) {
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            if (timing) {
+                OO_CUDA_TRY(cudaEventCreate(&e0));
+                OO_CUDA_TRY(cudaEventCreate(&e1));
+                OO_CUDA_TRY(cudaEventRecord(e0, s));
+            }
+            switch (n) {
+                case 0: launch_coef(d, dc, s); break;
+                case 1: launch_pinit(d, w.dptr(VAR_P), w.dptr(VAR_WRK2), s); break;
+                case 2:
+                    launch_stencil(w.splan, prob.omega, w.res_dev + it, s);
+                    if (!stencil_on_gpu) {
+                        // a pipeline wait that ran out would repeat in every
+                        // sweep: check the first one before queueing the rest
+                        const unsigned e = stencil_plan_check(w.splan, s);
+                        OO_REQUIRE(e == 0, OO_ETIMEOUT,
+                                   "stencil kernel pipeline wait ran out (error bits " +
+                                       std::to_string(e) + ")");
+                    }
+                    stencil_on_gpu = true;
+                    break;
+                case 3: launch_copyback(d, w.dptr(VAR_P), w.dptr(VAR_WRK2), s); break;
+                case 4: launch_bc_ij(d, w.dptr(VAR_P), s); break;
+                case 5: launch_bc_k(d, w.dptr(VAR_P), s); break;
+            }
+            ++launches;
+            if (timing) {
+                OO_CUDA_TRY(cudaEventRecord(e1, s));
+                evs.push_back(e0);
+                evs.push_back(e1);
+                ev_nest.push_back(n);
+            }
+        } else {
+            const Clock::time_point ts = Clock::now();
+            OO_CUDA_TRY(cudaStreamSynchronize(s));
+            const Clock::time_point th = Clock::now();
+            xfer_ms += std::chrono::duration<double, std::milli>(th - ts).count();
+            switch (n) {
+                case 0: host_coef(d, hc); break;
+                case 1: host_pinit(d, w.hptr(VAR_P), w.hptr(VAR_WRK2)); break;
+                case 2: w.res_host[it] = host_stencil(d, hc, w.hptr(VAR_P), prob.omega, w.hptr(VAR_WRK2)); break;
+                case 3: host_copyback(d, w.hptr(VAR_P), w.hptr(VAR_WRK2)); break;
+                case 4: host_bc_ij(d, w.hptr(VAR_P)); break;
+                case 5: host_bc_k(d, w.hptr(VAR_P)); break;
+            }
+            nest_ms[n] += ms_since(th);
+        }
+    };
+
+    int point = 0;
+    bool stop = false;
+    for (int n = 0; n < 2; ++n) {
+        run_transfers(point++);
+        run_nest(n, 0);
+    }
+    for (int it = 0; it < iters && !stop; ++it) {
+        for (int n = 2; n < 6; ++n) {
+            run_transfers(point++);
+            run_nest(n, it);
+        }
+        if (abort_after_ms > 0.0 && ms_since(t0) > abort_after_ms) stop = true;
+    }
+    if (stop) {
+        OO_CUDA_TRY(cudaStreamSynchronize(s));
+        for (auto e : evs) cudaEventDestroy(e);
+        if (aborted) *aborted = true;
+        if (stats) {
+            std::memset(stats, 0, sizeof(*stats));
+            stats->wall_ms = INFINITY;
+        }
+        return;
+    }
+
+    // deliver the outputs: the end-of-program copies land directly in the
+    // caller's buffers; outputs already current on the host are copied there
+    const size_t wb = (size_t)d.K * 4, rows = (size_t)d.I * d.J;
+    bool p_dev_valid = false, res_dev_valid = false;
+    for (size_t x = xi; x < plan.size(); ++x) {
+        if (plan[x].point != n_points) continue;
+        if (plan[x].var == VAR_P) p_dev_valid = true;
+        if (plan[x].var == VAR_RES) res_dev_valid = true;
+    }
+    const cudaMemcpyKind from_dev = out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const cudaMemcpyKind from_host = out_on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
+    if ((p_out && !p_dev_valid) || (res_out && !res_dev_valid))
+        OO_CUDA_TRY(cudaStreamSynchronize(s));  // host copies must be complete
+    if (p_out) {
+        if (p_dev_valid)
+            OO_CUDA_TRY(cudaMemcpy2DAsync(p_out, wb, w.dptr(VAR_P), (size_t)d.pitch * 4, wb, rows, from_dev, s));
+        else if (out_on_device)
+            OO_CUDA_TRY(cudaMemcpyAsync(p_out, w.hptr(VAR_P), wb * rows, from_host, s));
+        else
+            std::memcpy(p_out, w.hptr(VAR_P), wb * rows);
+    }
+    if (res_out && iters > 0) {
+        if (res_dev_valid)
+            OO_CUDA_TRY(cudaMemcpyAsync(res_out, w.res_dev, (size_t)iters * 8, from_dev, s));
+        else if (out_on_device)
+            OO_CUDA_TRY(cudaMemcpyAsync(res_out, w.res_host, (size_t)iters * 8, from_host, s));
+        else
+            std::memcpy(res_out, w.res_host, (size_t)iters * 8);
+    }
+    OO_CUDA_TRY(cudaStreamSynchronize(s));
+    const double wall = ms_since(t0);
+    if (stencil_on_gpu) {
+        const unsigned e = stencil_plan_check(w.splan, s);
+        OO_REQUIRE(e == 0, OO_ETIMEOUT,
+                   "stencil kernel pipeline wait ran out (error bits " + std::to_string(e) + ")");
+    }
+    OO_CUDA_TRY(cudaGetLastError());
+    if (timing) {
+        for (size_t x = 0; x < ev_nest.size(); ++x) {
+            float ms = 0.f;
+            OO_CUDA_TRY(cudaEventElapsedTime(&ms, evs[2 * x], evs[2 * x + 1]));
+            nest_ms[ev_nest[x]] += ms;
+        }
+    }
+    for (auto e : evs) cudaEventDestroy(e);
+    if (stats) {
+        stats->wall_ms = wall;
+        for (int n = 0; n < 6; ++n) stats->nest_ms[n] = nest_ms[n];
+        stats->xfer_ms = xfer_ms;
+        stats->h2d_bytes = h2d;
+        stats->d2h_bytes = d2h;
+        stats->n_xfers = (int32_t)plan.size();
+        stats->n_launches = launches;
+    }
+}
+
+}  // namespace oo

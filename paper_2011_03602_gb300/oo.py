@@ -1,0 +1,268 @@
+"""ctypes binding of liboo (include/oo.h), same names as the C entry points.
+
+Argument marshalling only: every step of the computation runs inside the
+library.  Host arrays are numpy arrays; device arrays are anything with a
+``data_ptr()`` (torch CUDA tensors) or a raw integer address.  A non-zero
+status raises OOError carrying the status and the library's error text.
+If liboo.so has not been built the first call raises; there is no fallback.
+"""
+import ctypes
+import math
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liboo.so")
+
+OO_OK, OO_EINVAL, OO_ENOMEM, OO_ECUDA, OO_ETIMEOUT = 0, -1, -2, -3, -4
+OO_ETOLERANCE, OO_EBUSY, OO_ENOTFOUND, OO_ESTATE = -5, -6, -7, -8
+OO_BLOCK_GEMM, OO_BLOCK_FFT = 1, 2
+OO_LANG_C, OO_LANG_PYTHON, OO_LANG_JAVA = 0, 1, 2
+
+_c = ctypes
+_u64, _i32, _dbl, _vp = _c.c_uint64, _c.c_int32, _c.c_double, _c.c_void_p
+
+
+class OOError(RuntimeError):
+    def __init__(self, status, text):
+        super().__init__("%s (%d): %s" % (oo_status_str(status), status, text))
+        self.status = status
+
+
+class oo_var(_c.Structure):
+    _fields_ = [("name", _c.c_char_p), ("bytes", _u64)]
+
+
+class oo_nest(_c.Structure):
+    _fields_ = [("name", _c.c_char_p), ("level", _i32), ("parallelisable", _i32),
+                ("reads", _u64), ("writes", _u64), ("partial", _u64)]
+
+
+class oo_xfer(_c.Structure):
+    _fields_ = [("point", _i32), ("var", _i32), ("dir", _i32), ("pad", _i32), ("bytes", _u64)]
+
+
+class oo_jacobi(_c.Structure):
+    _fields_ = [("I", _i32), ("J", _i32), ("K", _i32), ("iters", _i32),
+                ("omega", _c.c_float), ("timing", _i32)]
+
+
+class oo_run_stats(_c.Structure):
+    _fields_ = [("wall_ms", _dbl), ("nest_ms", _dbl * 6), ("xfer_ms", _dbl),
+                ("h2d_bytes", _u64), ("d2h_bytes", _u64), ("n_xfers", _i32),
+                ("n_launches", _i32)]
+
+    def as_dict(self):
+        return {"wall_ms": self.wall_ms, "nest_ms": list(self.nest_ms), "xfer_ms": self.xfer_ms,
+                "h2d_bytes": self.h2d_bytes, "d2h_bytes": self.d2h_bytes,
+                "n_xfers": self.n_xfers, "n_launches": self.n_launches}
+
+
+_lib = None
+
+
+def lib():
+    """Load liboo.so once; raise if it is missing (no fallback path exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise OSError("liboo.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+    L = _c.CDLL(LIB_PATH)
+    P = _c.POINTER
+    sig = {
+        "oo_create": (_c.c_int, [_c.c_int, _vp, P(_vp)]),
+        "oo_destroy": (None, [_vp]),
+        "oo_status_str": (_c.c_char_p, [_c.c_int]),
+        "oo_last_error": (_c.c_char_p, [_vp]),
+        "oo_sync": (_c.c_int, [_vp]),
+        "oo_load_nests": (_c.c_int, [_vp, P(oo_nest), _c.c_int, P(oo_var), _c.c_int, _u64, P(_c.c_int)]),
+        "oo_load_jacobi_nests": (_c.c_int, [_vp, _c.c_int, _c.c_int, _c.c_int, _c.c_int, P(_c.c_int)]),
+        "oo_transfer_plan": (_c.c_int, [_vp, _u64, _c.c_int, _c.c_int, P(oo_xfer), _c.c_int,
+                                        P(_c.c_int), P(_u64), P(_u64)]),
+        "oo_run_pattern": (_c.c_int, [_vp, _u64, _c.c_int, P(oo_jacobi), _vp, _vp, P(oo_run_stats)]),
+        "oo_run_pattern_dev": (_c.c_int, [_vp, _u64, _c.c_int, P(oo_jacobi), _vp, _vp, P(oo_run_stats)]),
+        "oo_stencil_dev": (_c.c_int, [_vp, _c.c_int, _c.c_int, _c.c_int, _c.c_int, P(_vp), _vp,
+                                      _c.c_float, _vp, _vp]),
+        "oo_jacobi_pitch": (_c.c_int, [_c.c_int]),
+        "oo_ga_search": (_c.c_int, [_vp, P(oo_jacobi), _c.c_int, _c.c_int, _c.c_int, _dbl, _dbl, _u64,
+                                    _dbl, P(_u64), P(_dbl), _vp, _vp]),
+        "oo_ga_table": (_c.c_int, [_c.c_int, _c.c_int, _c.c_int, _dbl, _dbl, _u64, _vp, _vp,
+                                   P(_u64), P(_dbl)]),
+        "oo_lookup_block": (_c.c_int, [_c.c_char_p, _c.c_int, P(_c.c_int)]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(ctx, st):
+    if st != OO_OK:
+        txt = lib().oo_last_error(ctx)
+        raise OOError(st, (txt or b"").decode(errors="replace"))
+
+
+def _host_ptr(a, dtype, n=None):
+    if a is None:
+        return None
+    if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags.c_contiguous:
+        raise TypeError("expected a C-contiguous numpy %s array" % np.dtype(dtype).name)
+    if n is not None and a.size != n:
+        raise ValueError("expected %d elements, got %d" % (n, a.size))
+    return a.ctypes.data_as(_vp)
+
+
+def _dev_ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return _vp(t)
+    if hasattr(t, "is_cuda") and not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if hasattr(t, "is_contiguous") and not t.is_contiguous():
+        raise TypeError("expected a contiguous tensor")
+    return _vp(t.data_ptr())
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return _vp(stream)
+    return _vp(stream.cuda_stream)
+
+
+# ------------------------------------------------------------------ context
+def oo_status_str(status):
+    return lib().oo_status_str(status).decode()
+
+
+def oo_create(device=0, stream=None):
+    """Returns an opaque context handle (c_void_p)."""
+    h = _vp()
+    st = lib().oo_create(device, _stream_handle(stream), _c.byref(h))
+    if st != OO_OK:
+        raise OOError(st, (lib().oo_last_error(None) or b"").decode(errors="replace"))
+    return h
+
+
+def oo_destroy(ctx):
+    lib().oo_destroy(ctx)
+
+
+def oo_last_error(ctx):
+    return (lib().oo_last_error(ctx) or b"").decode(errors="replace")
+
+
+def oo_sync(ctx):
+    _check(ctx, lib().oo_sync(ctx))
+
+
+# -------------------------------------------------------------- nest table
+def oo_load_nests(ctx, nests, var_bytes, outputs, var_names=None):
+    """nests: sequence of dicts(name, level, parallelisable, reads, writes, partial)."""
+    n = len(nests)
+    arr = (oo_nest * n)()
+    keep = []
+    for i, d in enumerate(nests):
+        nm = d.get("name", "n%d" % i).encode()
+        keep.append(nm)
+        arr[i] = oo_nest(nm, d["level"], d["parallelisable"], d["reads"], d["writes"], d["partial"])
+    v = (oo_var * len(var_bytes))()
+    for i, b in enumerate(var_bytes):
+        nm = (var_names[i] if var_names else "v%d" % i).encode()
+        keep.append(nm)
+        v[i] = oo_var(nm, b)
+    gl = _c.c_int()
+    _check(ctx, lib().oo_load_nests(ctx, arr, n, v, len(var_bytes), outputs, _c.byref(gl)))
+    return gl.value
+
+
+def oo_load_jacobi_nests(ctx, I, J, K, iters):
+    gl = _c.c_int()
+    _check(ctx, lib().oo_load_jacobi_nests(ctx, I, J, K, iters, _c.byref(gl)))
+    return gl.value
+
+
+def oo_transfer_plan(ctx, gene, hoist, iters):
+    """-> (list of (point, var, dir, bytes), h2d_bytes, d2h_bytes)."""
+    n = _c.c_int()
+    h2d, d2h = _u64(), _u64()
+    _check(ctx, lib().oo_transfer_plan(ctx, gene, hoist, iters, None, 0, _c.byref(n), None, None))
+    buf = (oo_xfer * max(n.value, 1))()
+    _check(ctx, lib().oo_transfer_plan(ctx, gene, hoist, iters, buf, n.value, _c.byref(n),
+                                       _c.byref(h2d), _c.byref(d2h)))
+    return [(x.point, x.var, x.dir, x.bytes) for x in buf[:n.value]], h2d.value, d2h.value
+
+
+# ------------------------------------------------------------------ Jacobi
+def jacobi(I, J, K, iters, omega=0.8, timing=False):
+    return oo_jacobi(I, J, K, iters, omega, 1 if timing else 0)
+
+
+def oo_jacobi_pitch(K):
+    return lib().oo_jacobi_pitch(K)
+
+
+def oo_run_pattern(ctx, gene, hoist, prob, p_out=None, res_out=None):
+    """Host outputs (numpy float32 [I*J*K] / float64 [iters]); returns stats dict."""
+    st = oo_run_stats()
+    n = prob.I * prob.J * prob.K
+    _check(ctx, lib().oo_run_pattern(ctx, gene, hoist, _c.byref(prob), _host_ptr(p_out, np.float32, n),
+                                     _host_ptr(res_out, np.float64, prob.iters), _c.byref(st)))
+    return st.as_dict()
+
+
+def oo_run_pattern_dev(ctx, gene, hoist, prob, p_dev=None, res_dev=None):
+    """Device outputs (torch tensors or raw addresses); returns stats dict."""
+    st = oo_run_stats()
+    _check(ctx, lib().oo_run_pattern_dev(ctx, gene, hoist, _c.byref(prob), _dev_ptr(p_dev),
+                                         _dev_ptr(res_dev), _c.byref(st)))
+    return st.as_dict()
+
+
+def oo_stencil_dev(ctx, I, J, K, pitch, coef, p, omega, wrk2, res_dev):
+    """coef: 12 device arrays (a0 a1 a2 a3 b0 b1 b2 c0 c1 c2 bnd wrk1)."""
+    if len(coef) != 12:
+        raise ValueError("need 12 coefficient arrays")
+    ptrs = (_vp * 12)(*[_dev_ptr(c).value for c in coef])
+    _check(ctx, lib().oo_stencil_dev(ctx, I, J, K, pitch, ptrs, _dev_ptr(p), _c.c_float(omega),
+                                     _dev_ptr(wrk2), _dev_ptr(res_dev)))
+
+
+# ---------------------------------------------------------------------- GA
+def oo_ga_table(L, pop, gens, pc, pm, seed, times):
+    times = np.ascontiguousarray(times, np.float64)
+    if times.size != (1 << L):
+        raise ValueError("need 2^L times")
+    hist = np.empty(gens * pop, np.uint64)
+    bg, bt = _u64(), _dbl()
+    _check(None, lib().oo_ga_table(L, pop, gens, pc, pm, seed, times.ctypes.data_as(_vp),
+                                   hist.ctypes.data_as(_vp), _c.byref(bg), _c.byref(bt)))
+    return hist.reshape(gens, pop), bg.value, bt.value
+
+
+def oo_ga_search(ctx, prob, hoist, pop, gens, pc, pm, seed, eval_timeout_ms=0.0):
+    hist = np.empty(gens * pop, np.uint64)
+    gene_ms = np.empty(64, np.float64)
+    bg, bt = _u64(), _dbl()
+    _check(ctx, lib().oo_ga_search(ctx, _c.byref(prob), hoist, pop, gens, pc, pm, seed,
+                                   eval_timeout_ms, _c.byref(bg), _c.byref(bt),
+                                   hist.ctypes.data_as(_vp), gene_ms.ctypes.data_as(_vp)))
+    return {"best_gene": bg.value, "best_ms": bt.value, "history": hist.reshape(gens, pop),
+            "gene_ms": gene_ms}
+
+
+# --------------------------------------------------------- function blocks
+def oo_lookup_block(callee, lang):
+    b = _c.c_int()
+    _check(None, lib().oo_lookup_block(callee.encode(), lang, _c.byref(b)))
+    return b.value
+
+
+__all__ = [n for n in dir() if n.startswith("oo_") or n in ("OOError", "jacobi", "lib")]
+del math

@@ -1,0 +1,88 @@
+"""The C-ABI library loads, exports every entry point include/*.h declares,
+and its host-only logic matches the oracle (no GPU calls here)."""
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2011_03602_gb300 import build as pkg_build
+from paper_2011_03602_gb300 import oo
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    pkg_build.build()
+
+
+def declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\b(oo_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported():
+    names = declared_symbols()
+    assert "oo_run_pattern" in names and "oo_create" in names
+    L = oo.lib()
+    missing = [n for n in names if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_status_strings():
+    assert oo.oo_status_str(0) == "ok"
+    assert oo.oo_status_str(oo.OO_ETIMEOUT) == "timed out"
+
+
+def test_lookup_block_by_language():
+    assert oo.oo_lookup_block("cblas_dgemm", oo.OO_LANG_C) == oo.OO_BLOCK_GEMM
+    assert oo.oo_lookup_block("numpy.fft.fft", oo.OO_LANG_PYTHON) == oo.OO_BLOCK_FFT
+    assert oo.oo_lookup_block("org.jtransforms.fft.DoubleFFT_1D.complexForward",
+                              oo.OO_LANG_JAVA) == oo.OO_BLOCK_FFT
+    with pytest.raises(oo.OOError) as e:
+        oo.oo_lookup_block("cblas_dgemm", oo.OO_LANG_JAVA)
+    assert e.value.status == oo.OO_ENOTFOUND
+
+
+def test_host_only_context_rejects_gpu_work():
+    ctx = oo.oo_create(-1)
+    try:
+        assert oo.oo_load_jacobi_nests(ctx, 5, 5, 5, 2) == 6
+        with pytest.raises(oo.OOError) as e:
+            oo.oo_run_pattern(ctx, 63, 1, oo.jacobi(5, 5, 5, 2))
+        assert e.value.status == oo.OO_ESTATE
+    finally:
+        oo.oo_destroy(ctx)
+
+
+def test_bad_tables_are_rejected():
+    ctx = oo.oo_create(-1)
+    try:
+        with pytest.raises(oo.OOError) as e:
+            oo.oo_load_nests(ctx, [dict(level=2, parallelisable=1, reads=0, writes=1, partial=0)],
+                             [8], 1)
+        assert e.value.status == oo.OO_EINVAL
+        with pytest.raises(oo.OOError):
+            oo.oo_load_nests(ctx, [dict(level=0, parallelisable=1, reads=0, writes=1, partial=2)],
+                             [8, 8], 1)
+        with pytest.raises(oo.OOError) as e:
+            oo.oo_transfer_plan(ctx, 1, 1, 1)   # no table loaded yet
+        assert e.value.status == oo.OO_ESTATE
+    finally:
+        oo.oo_destroy(ctx)
+
+
+def test_missing_gpu_fails_loudly_or_creates():
+    # on a machine without a GPU the context cannot be created on device 0
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(oo.OOError) as e:
+        oo.oo_create(0)
+    assert e.value.status in (oo.OO_ECUDA, oo.OO_EINVAL)

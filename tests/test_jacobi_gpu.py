@@ -1,0 +1,191 @@
+"""GPU parity of the Jacobi offload patterns against the FP64 oracle.
+
+Tolerance (stated for the float residual): every res[it] within 1e-5
+relative of the float-store oracle; p compared point by point.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from jacobi_table import NESTS, OUTPUTS, var_bytes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RES_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def oo_mod():
+    from paper_2011_03602_gb300 import build as pkg_build
+    from paper_2011_03602_gb300 import oo
+    pkg_build.build()
+    return oo
+
+
+@pytest.fixture(scope="module")
+def ctx(oo_mod):
+    c = oo_mod.oo_create(0)
+    yield c
+    oo_mod.oo_destroy(c)
+
+
+def run(oo, ctx, shape, iters, gene=63, hoist=1):
+    I, J, K = shape
+    p = np.empty(I * J * K, np.float32)
+    res = np.empty(iters, np.float64)
+    st = oo.oo_run_pattern(ctx, gene, hoist, oo.jacobi(I, J, K, iters), p, res)
+    return p.reshape(I, J, K), res, st
+
+
+def test_setup_nests_bit_exact(oo_mod, ctx):
+    I, J, K = 9, 11, 70
+    p, _, _ = run(oo_mod, ctx, (I, J, K), 0, gene=0b000011)
+    _, p_ref = oracle.jacobi_setup(I, J, K)
+    assert np.array_equal(p, p_ref)
+    # N0 on the GPU, the rest on the CPU: coefficients copied back must give
+    # bit-identical results to the all-CPU run
+    pa, ra, _ = run(oo_mod, ctx, (I, J, K), 3, gene=0b000001)
+    pb, rb, _ = run(oo_mod, ctx, (I, J, K), 3, gene=0)
+    assert np.array_equal(pa, pb) and np.array_equal(ra, rb)
+
+
+def _pad(a, pitch):
+    I, J, K = a.shape
+    out = torch.zeros((I, J, pitch), dtype=torch.float32, device="cuda")
+    out[:, :, :K] = torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    return out
+
+
+@pytest.mark.parametrize("shape", [(3, 3, 3), (5, 7, 9), (12, 19, 70), (33, 33, 65), (20, 21, 300),
+                                   (11, 10, 130), (6, 40, 517)])
+def test_stencil_random_fields(oo_mod, ctx, shape):
+    from paper_2011_03602_gb300 import synth
+    I, J, K = shape
+    coef = np.stack([synth.field(100 + a, shape, -1.0, 1.0) for a in range(12)])
+    coef[3] = synth.field(50, shape, 0.1, 0.3)       # a3
+    coef[10] = synth.field(51, shape, 0.5, 1.5)      # bnd
+    p = synth.field(52, shape, 0.0, 1.0)
+    omega = np.float32(0.8)
+    w_ref, r_ref = oracle.stencil(coef, p.astype(np.float64), omega)
+    pitch = oo_mod.oo_jacobi_pitch(K)
+    dcoef = [_pad(coef[a], pitch) for a in range(12)]
+    dp = _pad(p, pitch)
+    sentinel = -7.0
+    dw = torch.full((I, J, pitch), sentinel, dtype=torch.float32, device="cuda")
+    dres = torch.zeros(1, dtype=torch.float64, device="cuda")
+    oo_mod.oo_stencil_dev(ctx, I, J, K, pitch, dcoef, dp, float(omega), dw, dres)
+    oo_mod.oo_sync(ctx)
+    w = dw[:, :, :K].cpu().numpy()
+    inner = (slice(1, -1),) * 3
+    ref32 = w_ref.astype(np.float32)
+    diff = w[inner] != ref32[inner]
+    assert diff.mean() <= 1e-3, diff.mean()
+    if diff.any():
+        ulp = np.spacing(np.abs(ref32[inner][diff]))
+        assert np.all(np.abs(w[inner][diff] - ref32[inner][diff]) <= ulp)
+    # points outside the interior are never written
+    mask = np.ones(shape, bool)
+    mask[inner] = False
+    assert np.all(w[mask] == sentinel)
+    r = float(dres.item())
+    assert abs(r - r_ref) <= 1e-11 * abs(r_ref)
+
+
+def test_stencil_repeatable(oo_mod, ctx):
+    from paper_2011_03602_gb300 import synth
+    shape = (40, 37, 200)
+    I, J, K = shape
+    pitch = oo_mod.oo_jacobi_pitch(K)
+    dcoef = [_pad(synth.field(a, shape, 0.5, 1.0), pitch) for a in range(12)]
+    dp = _pad(synth.field(99, shape), pitch)
+    dw = torch.zeros((I, J, pitch), dtype=torch.float32, device="cuda")
+    r = []
+    for _ in range(3):
+        dres = torch.zeros(1, dtype=torch.float64, device="cuda")
+        oo_mod.oo_stencil_dev(ctx, I, J, K, pitch, dcoef, dp, 0.8, dw, dres)
+        oo_mod.oo_sync(ctx)
+        r.append(dres.item())
+    assert r[0] == r[1] == r[2]
+
+
+@pytest.fixture(scope="module")
+def small_ref():
+    res, p = oracle.jacobi_run(33, 33, 65, 50, mode=1)
+    res64, _ = oracle.jacobi_run(33, 33, 65, 50, mode=0, want_p=False)
+    return res, p, res64
+
+
+@pytest.mark.parametrize("hoist", [1, 0])
+def test_all_64_genes_small_config(oo_mod, ctx, small_ref, hoist):
+    ref_res, ref_p, res64 = small_ref
+    I, J, K, iters = 33, 33, 65, 50
+    vb = var_bytes(I, J, K, iters)
+    for gene in range(64):
+        p, res, st = run(oo_mod, ctx, (I, J, K), iters, gene, hoist)
+        rel = np.max(np.abs(res - ref_res) / np.abs(ref_res))
+        assert rel <= RES_TOL, (gene, rel)
+        assert np.max(np.abs(p - ref_p)) <= 1e-6, gene
+        assert np.mean(p != ref_p.astype(np.float32)) <= 1e-3, gene
+        assert np.max(np.abs(res - res64) / res64) <= RES_TOL, gene
+        _, h2d, d2h = oracle.plan(NESTS, vb, OUTPUTS, gene, hoist, iters)
+        assert (st["h2d_bytes"], st["d2h_bytes"]) == (h2d, d2h), gene
+        launches = sum(((gene >> n) & 1) * (1 if n < 2 else iters) for n in range(6))
+        assert st["n_launches"] == launches, gene
+
+
+@pytest.mark.parametrize("shape,iters", [((3, 3, 3), 4), ((4, 4, 4), 2), ((5, 7, 9), 7),
+                                         ((9, 10, 131), 5), ((40, 13, 129), 6), ((18, 66, 34), 3)])
+def test_ragged_grids(oo_mod, ctx, shape, iters):
+    ref_res, ref_p = oracle.jacobi_run(*shape, iters, mode=1)
+    for gene in (63, 0b000100, 0b111100):
+        p, res, _ = run(oo_mod, ctx, shape, iters, gene, 1)
+        assert np.max(np.abs(res - ref_res) / np.maximum(np.abs(ref_res), 1e-300)) <= RES_TOL
+        assert np.max(np.abs(p - ref_p)) <= 1e-6
+
+
+def test_device_outputs_match_host_outputs(oo_mod, ctx):
+    I, J, K, iters = 21, 23, 97, 6
+    p, res, _ = run(oo_mod, ctx, (I, J, K), iters)
+    dp = torch.empty(I * J * K, dtype=torch.float32, device="cuda")
+    dr = torch.empty(iters, dtype=torch.float64, device="cuda")
+    for gene in (63, 0):
+        oo_mod.oo_run_pattern_dev(ctx, gene, 1, oo_mod.jacobi(I, J, K, iters), dp, dr)
+        hp, hr, _ = run(oo_mod, ctx, (I, J, K), iters, gene, 1)
+        assert np.array_equal(dp.cpu().numpy(), hp.reshape(-1))
+        assert np.array_equal(dr.cpu().numpy(), hr)
+
+
+def test_timing_and_stats(oo_mod, ctx):
+    I, J, K, iters = 33, 33, 65, 4
+    p = np.empty(I * J * K, np.float32)
+    st = oo_mod.oo_run_pattern(ctx, 63, 1, oo_mod.jacobi(I, J, K, iters, timing=True), p, None)
+    assert all(t > 0 for t in st["nest_ms"])
+    assert st["n_launches"] == 2 + 4 * iters and st["n_xfers"] == 2
+
+
+def test_full_size_grid_sampled():
+    """257 x 257 x 513, the launch configuration the benchmark times, a few
+    iterations: residuals against the oracle, p on a sample of points."""
+    from paper_2011_03602_gb300 import oo
+    I, J, K, iters = 257, 257, 513, 2
+    ctx = oo.oo_create(0)
+    try:
+        p = np.empty(I * J * K, np.float32)
+        res = np.empty(iters)
+        oo.oo_run_pattern(ctx, 63, 1, oo.jacobi(I, J, K, iters), p, res)
+    finally:
+        oo.oo_destroy(ctx)
+    ref_res, ref_p = oracle.jacobi_run(I, J, K, iters, mode=1)
+    assert np.max(np.abs(res - ref_res) / ref_res) <= RES_TOL
+    idx = np.random.default_rng(0).integers(0, I * J * K, 200000)
+    assert np.max(np.abs(p[idx] - ref_p.reshape(-1)[idx])) <= 1e-6
+
+
+def test_bad_arguments(oo_mod, ctx):
+    with pytest.raises(oo_mod.OOError):
+        oo_mod.oo_run_pattern(ctx, 64, 1, oo_mod.jacobi(5, 5, 5, 1))
+    with pytest.raises(oo_mod.OOError):
+        oo_mod.oo_run_pattern(ctx, 1, 1, oo_mod.jacobi(2, 5, 5, 1))
+    with pytest.raises(oo_mod.OOError):
+        oo_mod.oo_run_pattern(ctx, 1, 2, oo_mod.jacobi(5, 5, 5, 1))
