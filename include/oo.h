@@ -223,6 +223,22 @@ enum { OO_LANG_C = 0, OO_LANG_PYTHON = 1, OO_LANG_JAVA = 2 };
  * code-pattern table for language `lang`.  OO_ENOTFOUND if absent.       */
 oo_status oo_lookup_block(const char *callee, int lang, int *block_id);
 
+/* Sec. 3.2.2 Fourier-transform block: complex128 FFT of length n = 2^k,
+ * 0 <= k <= 24, interleaved (re, im) doubles.  dir -1: forward,
+ * X_k = sum_j x_j exp(-2 pi i jk/n); dir +1: inverse with exp(+...) and 1/n.
+ * Butterflies run in float-float arithmetic (relative L2 error ~1e-14 for
+ * normal inputs); each transform is scaled by a power of two internally, so
+ * any finite input is accepted (components more than ~2^126 below the
+ * transform's largest one are flushed).  Non-finite inputs give unspecified
+ * output.
+ * oo_fft_c128: host buffers, synchronous; in may equal out.               */
+oo_status oo_fft_c128(oo_ctx *ctx, int64_t n, int dir, const double *in, double *out);
+/* batch contiguous transforms on caller device buffers (16-byte aligned,
+ * batch * n complex values each; din may equal dout), asynchronous on the
+ * context's stream.  batch <= 65535.                                      */
+oo_status oo_fft_c128_dev(oo_ctx *ctx, int64_t n, int batch, int dir, const double *din,
+                          double *dout);
+
 #ifdef __cplusplus
 }
 #endif

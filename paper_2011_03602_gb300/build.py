@@ -25,6 +25,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # error-free transforms contracted into FMAs
 CU_FLAGS = {
     "jacobi.cu": ["-fmad=false"],
+    "fft.cu": ["-fmad=false"],
 }
 CXX_FLAGS = ["-O3", "-std=c++17", "-fPIC", "-fopenmp", "-ffp-contract=off", "-Wall",
              "-I" + os.path.join(CUDA_HOME, "include"), "-I" + os.path.join(ROOT, "include")]

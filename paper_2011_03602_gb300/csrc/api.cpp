@@ -126,6 +126,11 @@ void oo_destroy(oo_ctx *ctx) {
     if (ctx->c.stream) cudaStreamSynchronize(ctx->c.stream);
     stencil_plan_destroy(ctx->user_plan);
     jacobi_work_free(ctx->c.jw);
+    for (auto &kv : ctx->c.fft_plans) fft_plan_destroy(kv.second);
+    ctx->c.fft_scratch.release();
+    ctx->c.stage_a.release();
+    ctx->c.stage_b.release();
+    ctx->c.stage_c.release();
     if (ctx->c.own_stream && ctx->c.stream) cudaStreamDestroy(ctx->c.stream);
     delete ctx;
 }
@@ -285,6 +290,35 @@ oo_status oo_ga_search(oo_ctx *ctx, const oo_jacobi *prob, int hoist, int pop, i
         }
         *best_gene = r.best_gene;
         *best_ms = r.best_time;
+    });
+}
+
+oo_status oo_fft_c128_dev(oo_ctx *ctx, int64_t n, int batch, int dir, const double *din, double *dout) {
+    if (!ctx) return OO_EINVAL;
+    return guarded(ctx, [&] {
+        OO_REQUIRE(din && dout, OO_EINVAL, "null pointer");
+        OO_REQUIRE((((uintptr_t)din) & 15u) == 0 && (((uintptr_t)dout) & 15u) == 0, OO_EINVAL,
+                   "FFT buffers must be 16-byte aligned");
+        use_device(ctx->c);
+        FftPlan *p = ctx->c.fft_plan(n);
+        void *scratch = ctx->c.fft_scratch.get(fft_scratch_bytes(p, batch));
+        launch_fft(p, batch, dir, din, dout, scratch, ctx->c.stream);
+    });
+}
+
+oo_status oo_fft_c128(oo_ctx *ctx, int64_t n, int dir, const double *in, double *out) {
+    if (!ctx) return OO_EINVAL;
+    return guarded(ctx, [&] {
+        OO_REQUIRE(in && out, OO_EINVAL, "null pointer");
+        use_device(ctx->c);
+        FftPlan *p = ctx->c.fft_plan(n);
+        const size_t bytes = (size_t)n * 16;
+        double *d = static_cast<double *>(ctx->c.stage_a.get(bytes));
+        void *scratch = ctx->c.fft_scratch.get(fft_scratch_bytes(p, 1));
+        OO_CUDA_TRY(cudaMemcpyAsync(d, in, bytes, cudaMemcpyHostToDevice, ctx->c.stream));
+        launch_fft(p, 1, dir, d, d, scratch, ctx->c.stream);
+        OO_CUDA_TRY(cudaMemcpyAsync(out, d, bytes, cudaMemcpyDeviceToHost, ctx->c.stream));
+        OO_CUDA_TRY(cudaStreamSynchronize(ctx->c.stream));
     });
 }
 

@@ -1,0 +1,431 @@
+// Fourier-transform function block (Sec. 3.2.2, Sec. 4.2.1): complex128 1D
+// FFT, forward X_k = sum_n x_n e^{-2 pi i nk/N} and inverse with e^{+} and 1/N.
+//
+// GB300 design.  FP64 units run at 1/59 of FP32 on this part, so butterflies
+// use float-float arithmetic (ff.cuh; ~47 significant bits, error ~ log2(N)
+// * 2^-47 relative) and FP64 is used only to generate twiddle tables
+// (sincospi) and to widen results back to double.  Each input transform is
+// scaled by a power of two (exact) so its largest component lies in [1/2, 1)
+// before the split into float pairs, which keeps float-float's exponent range
+// out of the way for any finite double input.
+//
+// Structure: a CTA holds 4096 complex float-float values (64 KB) in shared
+// memory and runs Stockham auto-sort radix-4 stages (one radix-2 stage first
+// for odd log2 L), 512 threads x 2 butterflies per stage, twiddles W_L^t from
+// a per-length table staged into shared memory.  N <= 4096 runs in one pass
+// (several transforms per CTA when N is small).  Larger N uses the four-step
+// split N = N1 x N2: pass 1 does N2 column FFTs of length N1 and multiplies
+// by W_N^{k1 n2} (two-level twiddle table), writing float-float
+// intermediates; pass 2 does N1 row FFTs of length N2 and writes X[k1 + N1 k2]
+// as doubles.
+#include <cmath>
+
+#include "ff.cuh"
+#include "oo_internal.h"
+
+namespace oo {
+
+namespace {
+
+constexpr int kFftThreads = 512;
+constexpr int kFftBpt = 2;                               // radix-4 butterflies per thread
+constexpr int kFftElems = 4 * kFftThreads * kFftBpt;     // 4096 values per CTA
+constexpr int kTwSplit = 11;                             // four-step twiddle split: 2^11
+
+using ff::cplx;
+
+__device__ __forceinline__ cplx ld_cplx(const float4 *p) {
+    const float4 v = *p;
+    return cplx{v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ void st_cplx(float4 *p, const cplx &c) { *p = make_float4(c.rh, c.rl, c.ih, c.il); }
+
+// x * 2^-S split into a float pair (hi: top 24 mantissa bits; lo: the rest
+// rounded to 24 bits), integer-only; values below 2^-126 after scaling flush.
+__device__ __forceinline__ void split_scaled(double x, int S, float &h, float &l) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi32 = (unsigned)(b >> 32), lo32 = (unsigned)b;
+    const unsigned sign = hi32 & 0x80000000u;
+    const int e = (int)((hi32 >> 20) & 0x7ffu);
+    const int fe = e - 1023 - S + 127;  // biased float exponent of the scaled value
+    if (e == 0 || e == 0x7ff || fe <= 0) {
+        h = 0.0f;
+        l = 0.0f;
+        return;
+    }
+    const unsigned mtop = ((hi32 & 0xfffffu) << 3) | (lo32 >> 29);
+    h = __uint_as_float(sign | ((unsigned)fe << 23) | mtop);
+    const unsigned r = lo32 & 0x1fffffffu;
+    const int le = fe - 52;  // biased exponent of 2^(unbiased(fe) - 52)
+    float lf = 0.0f;
+    if (le > 0 && r != 0) lf = __fmul_rn(__uint2float_rn(r), __uint_as_float((unsigned)le << 23));
+    l = sign ? -lf : lf;
+}
+
+// (h + l) * 2^S as a double
+__device__ __forceinline__ double widen_scaled(float h, float l, int S) {
+    const double d = (double)h + (double)l;
+    return ldexp(d, S);
+}
+
+struct FftArgs {
+    int log2n, log2n1, log2n2;
+    long long n;
+    int batch;
+    int inverse;
+    const double *in_d;   // mode 0 / 1
+    double *out_d;        // mode 0 / 2
+    const float4 *in_ff;  // mode 2
+    float4 *out_ff;       // mode 1
+    const float4 *tw;     // W_L^t for the pass length L (table of L entries)
+    const float4 *tw_hi;  // W_N^{m_hi * 2^kTwSplit}
+    const float4 *tw_lo;  // W_N^{m_lo}
+    const int *expo;      // per transform: biased double exponent of its largest component
+};
+
+__device__ __forceinline__ int scale_of(const FftArgs &a, int b) {
+    const int e = a.expo[b];
+    return e == 0 ? 0 : e - 1023 + 1;
+}
+
+__device__ __forceinline__ cplx twiddle(const float4 *stw, int idx, bool inv) {
+    cplx w = ld_cplx(stw + idx);
+    return inv ? ff::conj(w) : w;
+}
+
+// Stockham radix-2 stage with sub-length Ls on C columns of length L.
+__device__ __forceinline__ void stage_r2(float4 *sd, const float4 *stw, int log2L, int Ls, bool inv) {
+    const int L = 1 << log2L, half = L >> 1;
+    cplx y0[2 * kFftBpt], y1[2 * kFftBpt];
+    int base_c[2 * kFftBpt], jj[2 * kFftBpt];
+#pragma unroll
+    for (int r = 0; r < 2 * kFftBpt; ++r) {
+        const int bidx = threadIdx.x + r * kFftThreads;
+        const int c = bidx >> (log2L - 1), j = bidx & (half - 1);
+        base_c[r] = c << log2L;
+        jj[r] = j;
+        y0[r] = ld_cplx(sd + base_c[r] + j);
+        cplx x1 = ld_cplx(sd + base_c[r] + j + half);
+        if (Ls > 1) x1 = ff::cmul(x1, twiddle(stw, (j & (Ls - 1)) * (L / (2 * Ls)), inv));
+        y1[r] = x1;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 2 * kFftBpt; ++r) {
+        const int j = jj[r], k = j & (Ls - 1);
+        const int o = base_c[r] + (j - k) * 2 + k;
+        st_cplx(sd + o, ff::cadd(y0[r], y1[r]));
+        st_cplx(sd + o + Ls, ff::csub(y0[r], y1[r]));
+    }
+    __syncthreads();
+}
+
+// Stockham radix-4 stage with sub-length Ls.
+__device__ __forceinline__ void stage_r4(float4 *sd, const float4 *stw, int log2L, int Ls, bool inv) {
+    const int L = 1 << log2L, q4 = L >> 2;
+    cplx Y[kFftBpt][4];
+    int base_c[kFftBpt], jj[kFftBpt];
+#pragma unroll
+    for (int r = 0; r < kFftBpt; ++r) {
+        const int bidx = threadIdx.x + r * kFftThreads;
+        const int c = bidx >> (log2L - 2), j = bidx & (q4 - 1);
+        base_c[r] = c << log2L;
+        jj[r] = j;
+        cplx x[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) x[q] = ld_cplx(sd + base_c[r] + j + q * q4);
+        if (Ls > 1) {
+            const int k = j & (Ls - 1), step = L / (4 * Ls);
+#pragma unroll
+            for (int q = 1; q < 4; ++q) x[q] = ff::cmul(x[q], twiddle(stw, k * q * step, inv));
+        }
+        const cplx a0 = ff::cadd(x[0], x[2]), a1 = ff::csub(x[0], x[2]);
+        const cplx b0 = ff::cadd(x[1], x[3]), b1 = ff::csub(x[1], x[3]);
+        const cplx rb1 = inv ? ff::mul_pos_i(b1) : ff::mul_neg_i(b1);
+        Y[r][0] = ff::cadd(a0, b0);
+        Y[r][2] = ff::csub(a0, b0);
+        Y[r][1] = ff::cadd(a1, rb1);
+        Y[r][3] = ff::csub(a1, rb1);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kFftBpt; ++r) {
+        const int j = jj[r], k = j & (Ls - 1);
+        const int o = base_c[r] + (j - k) * 4 + k;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) st_cplx(sd + o + p * Ls, Y[r][p]);
+    }
+    __syncthreads();
+}
+
+__device__ void fft_in_smem(float4 *sd, const float4 *stw, int log2L, bool inv) {
+    int Ls = 1;
+    if (log2L & 1) {
+        stage_r2(sd, stw, log2L, 1, inv);
+        Ls = 2;
+    }
+    for (; Ls < (1 << log2L); Ls *= 4) stage_r4(sd, stw, log2L, Ls, inv);
+}
+
+// MODE 0: whole transforms of length L = n, several per CTA (double in/out)
+// MODE 1: four-step pass 1: columns of length N1 (double in, ff out x twiddle)
+// MODE 2: four-step pass 2: rows of length N2 (ff in, double out at k1 + N1 k2)
+template <int MODE>
+__global__ void __launch_bounds__(kFftThreads, 1) fft_pass_kernel(FftArgs a) {
+    extern __shared__ __align__(16) float4 fsmem[];
+    float4 *sd = fsmem;
+    float4 *stw = fsmem + kFftElems;
+    const int log2L = MODE == 0 ? a.log2n : (MODE == 1 ? a.log2n1 : a.log2n2);
+    const int L = 1 << log2L;
+    const int C = kFftElems >> log2L;  // columns (transforms / rows) in this CTA
+    const bool inv = a.inverse != 0;
+    for (int t = threadIdx.x; t < L; t += kFftThreads) stw[t] = a.tw[t];
+
+    const long long n = a.n;
+    const int N1 = 1 << a.log2n1, N2 = 1 << a.log2n2;
+    int b = 0, c0 = 0;  // transform index, first column / row of this CTA
+    if (MODE == 0) {
+        c0 = blockIdx.x * C;
+    } else {
+        const int per = (MODE == 1 ? N2 : N1) / C;
+        b = blockIdx.x / per;
+        c0 = (blockIdx.x % per) * C;
+    }
+
+    // ---- load
+    for (int q = threadIdx.x; q < kFftElems; q += kFftThreads) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        int c, t;
+        if (MODE == 1) {  // column-fastest for coalescing
+            c = q & (C - 1);
+            t = q >> (31 - __clz(C));
+        } else {
+            c = q >> log2L;
+            t = q & (L - 1);
+        }
+        if (MODE == 0) {
+            const int tb = c0 + c;
+            if (tb < a.batch) {
+                const int S = scale_of(a, tb);
+                const double2 x = reinterpret_cast<const double2 *>(a.in_d)[(long long)tb * n + t];
+                split_scaled(x.x, S, v.x, v.y);
+                split_scaled(x.y, S, v.z, v.w);
+            }
+        } else if (MODE == 1) {
+            const int S = scale_of(a, b);
+            const double2 x = reinterpret_cast<const double2 *>(a.in_d)[(long long)b * n + (long long)t * N2 + c0 + c];
+            split_scaled(x.x, S, v.x, v.y);
+            split_scaled(x.y, S, v.z, v.w);
+        } else {
+            v = a.in_ff[(long long)b * n + (long long)(c0 + c) * N2 + t];
+        }
+        sd[(c << log2L) + t] = v;
+    }
+    __syncthreads();
+
+    fft_in_smem(sd, stw, log2L, inv);
+
+    // ---- store
+    for (int q = threadIdx.x; q < kFftElems; q += kFftThreads) {
+        int c, t;
+        if (MODE == 0) {
+            c = q >> log2L;
+            t = q & (L - 1);
+        } else {  // column / row index fastest
+            c = q & (C - 1);
+            t = q >> (31 - __clz(C));
+        }
+        cplx v = ld_cplx(sd + (c << log2L) + t);
+        if (MODE == 1) {
+            // W_N^{k1 n2}, k1 = t, n2 = c0 + c; m < N so no reduction needed
+            const long long m = (long long)t * (c0 + c);
+            const int mh = (int)(m >> kTwSplit), ml = (int)(m & ((1 << kTwSplit) - 1));
+            cplx w = ff::cmul(ld_cplx(a.tw_hi + mh), ld_cplx(a.tw_lo + ml));
+            if (inv) w = ff::conj(w);
+            v = ff::cmul(v, w);
+            st_cplx(a.out_ff + (long long)b * n + (long long)t * N2 + c0 + c, v);
+        } else {
+            const int tb = MODE == 0 ? c0 + c : b;
+            if (MODE == 0 && tb >= a.batch) continue;
+            const int S = scale_of(a, tb) - (inv ? a.log2n : 0);
+            const double re = widen_scaled(v.rh, v.rl, S), im = widen_scaled(v.ih, v.il, S);
+            const long long idx = MODE == 0 ? (long long)tb * n + t
+                                            : (long long)b * n + (c0 + c) + (long long)N1 * t;
+            reinterpret_cast<double2 *>(a.out_d)[idx] = make_double2(re, im);
+        }
+    }
+}
+
+// biased exponent of the largest |re|, |im| of every transform
+__global__ void fft_maxexp_kernel(const double *in, long long n, int *expo) {
+    const int b = blockIdx.y;
+    const unsigned long long *p = reinterpret_cast<const unsigned long long *>(in) + (long long)b * 2 * n;
+    int m = 0;
+    for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < 2 * n;
+         x += (long long)gridDim.x * blockDim.x) {
+        const int e = (int)((p[x] >> 52) & 0x7ffu);
+        m = max(m, e == 0x7ff ? 0x7fe : e);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(expo + b, m);
+}
+
+// table[t] = W_M^{t * stride} = exp(-2 pi i t stride / M), t < count, in FP64, split to float pairs
+__global__ void fft_twiddle_kernel(float4 *table, int count, long long stride, int log2M) {
+    const long long M = 1ll << log2M;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x) {
+        const long long m = ((long long)t * stride) & (M - 1);
+        double s, c;
+        sincospi(ldexp((double)(2 * m), -log2M), &s, &c);  // angle 2 pi m / M
+        const double re = c, im = -s;
+        const float rh = (float)re, ih = (float)im;
+        table[t] = make_float4(rh, (float)(re - (double)rh), ih, (float)(im - (double)ih));
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ plans
+struct FftPlan {
+    int log2n = -1, log2n1 = 0, log2n2 = 0;
+    float4 *tables = nullptr;   // tw for each pass length, tw_hi, tw_lo
+    const float4 *tw_single = nullptr, *tw_n1 = nullptr, *tw_n2 = nullptr, *tw_hi = nullptr,
+                 *tw_lo = nullptr;
+};
+
+static int ilog2_exact(long long n) {
+    int k = 0;
+    while ((1ll << k) < n) ++k;
+    return (1ll << k) == n ? k : -1;
+}
+
+FftPlan *fft_plan_create(long long n) {
+    const int k = ilog2_exact(n);
+    OO_REQUIRE(k >= 0 && k <= 24, OO_EINVAL, "FFT length must be a power of two, 1 .. 2^24");
+    auto p = new FftPlan();
+    p->log2n = k;
+    const int four_step = k > 12;
+    p->log2n1 = four_step ? k / 2 : k;
+    p->log2n2 = four_step ? k - k / 2 : 0;
+    OO_REQUIRE(p->log2n2 <= 12, OO_EINVAL, "FFT length above 2^24 not supported");
+    size_t count = 0;
+    if (!four_step) {
+        count = (size_t)1 << k;
+    } else {
+        count = ((size_t)1 << p->log2n1) + ((size_t)1 << p->log2n2) + ((size_t)1 << (k - kTwSplit > 0 ? k - kTwSplit : 0)) +
+                ((size_t)1 << kTwSplit);
+    }
+    try {
+        OO_CUDA_TRY(cudaMalloc(&p->tables, std::max<size_t>(count, 1) * sizeof(float4)));
+        float4 *t = p->tables;
+        auto gen = [&](int cnt, long long stride, int log2M) {
+            fft_twiddle_kernel<<<std::max(1, std::min(1024, (cnt + 255) / 256)), 256>>>(t, cnt, stride, log2M);
+            OO_CUDA_TRY(cudaGetLastError());
+            const float4 *r = t;
+            t += cnt;
+            return r;
+        };
+        if (!four_step) {
+            p->tw_single = gen(1 << k, 1, k);
+        } else {
+            p->tw_n1 = gen(1 << p->log2n1, 1, p->log2n1);
+            p->tw_n2 = gen(1 << p->log2n2, 1, p->log2n2);
+            p->tw_hi = gen(1 << std::max(0, k - kTwSplit), 1ll << kTwSplit, k);
+            p->tw_lo = gen(1 << kTwSplit, 1, k);
+        }
+        OO_CUDA_TRY(cudaDeviceSynchronize());
+    } catch (...) {
+        if (p->tables) cudaFree(p->tables);
+        delete p;
+        throw;
+    }
+    return p;
+}
+
+void fft_plan_destroy(FftPlan *p) {
+    if (!p) return;
+    if (p->tables) cudaFree(p->tables);
+    delete p;
+}
+
+size_t fft_scratch_bytes(const FftPlan *p, int batch) {
+    const size_t n = (size_t)1 << p->log2n;
+    return (p->log2n > 12 ? n * (size_t)batch * sizeof(float4) : 0) + (size_t)batch * sizeof(int) + 256;
+}
+
+void launch_fft(const FftPlan *p, int batch, int dir, const double *in, double *out, void *scratch,
+                cudaStream_t s) {
+    OO_REQUIRE(batch >= 1, OO_EINVAL, "batch must be >= 1");
+    OO_REQUIRE(dir == -1 || dir == 1, OO_EINVAL, "dir must be -1 (forward) or +1 (inverse)");
+    const long long n = 1ll << p->log2n;
+    const bool four_step = p->log2n > 12;
+    float4 *mid = reinterpret_cast<float4 *>(scratch);
+    int *expo = reinterpret_cast<int *>(reinterpret_cast<char *>(scratch) +
+                                        (four_step ? (size_t)n * batch * sizeof(float4) : 0));
+    OO_CUDA_TRY(cudaMemsetAsync(expo, 0, (size_t)batch * sizeof(int), s));
+    {
+        const long long per = 2 * n;
+        const int bx = (int)std::min<long long>(64, (per + 255) / 256);
+        OO_REQUIRE(batch <= 65535, OO_EINVAL, "batch above 65535");
+        fft_maxexp_kernel<<<dim3(bx, batch), 256, 0, s>>>(in, n, expo);
+        OO_CUDA_TRY(cudaGetLastError());
+    }
+    FftArgs a{};
+    a.log2n = p->log2n;
+    a.log2n1 = p->log2n1;
+    a.log2n2 = p->log2n2;
+    a.n = n;
+    a.batch = batch;
+    a.inverse = dir > 0 ? 1 : 0;
+    a.expo = expo;
+    static bool attr_done[3] = {false, false, false};
+    auto smem_for = [&](int log2L) { return (size_t)(kFftElems + (1 << log2L)) * sizeof(float4); };
+    auto prep = [&](int mode, const void *fn, size_t smem) {
+        if (!attr_done[mode]) {
+            OO_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem_for(12)));
+            attr_done[mode] = true;
+        }
+        (void)smem;
+    };
+    if (!four_step) {
+        const int C = kFftElems >> p->log2n;
+        const int grid = (int)((batch + C - 1) / C);
+        a.in_d = in;
+        a.out_d = out;
+        a.tw = p->tw_single;
+        const size_t smem = smem_for(p->log2n);
+        prep(0, (const void *)fft_pass_kernel<0>, smem);
+        fft_pass_kernel<0><<<grid, kFftThreads, smem, s>>>(a);
+        OO_CUDA_TRY(cudaGetLastError());
+        return;
+    }
+    const int N1 = 1 << p->log2n1, N2 = 1 << p->log2n2;
+    a.tw_hi = p->tw_hi;
+    a.tw_lo = p->tw_lo;
+    {
+        a.in_d = in;
+        a.out_ff = mid;
+        a.tw = p->tw_n1;
+        const int C = kFftElems / N1;
+        const long long grid = (long long)batch * (N2 / C);
+        const size_t smem = smem_for(p->log2n1);
+        prep(1, (const void *)fft_pass_kernel<1>, smem);
+        fft_pass_kernel<1><<<(unsigned)grid, kFftThreads, smem, s>>>(a);
+        OO_CUDA_TRY(cudaGetLastError());
+    }
+    {
+        a.in_ff = mid;
+        a.out_d = out;
+        a.tw = p->tw_n2;
+        const int R = kFftElems / N2;
+        const long long grid = (long long)batch * (N1 / R);
+        const size_t smem = smem_for(p->log2n2);
+        prep(2, (const void *)fft_pass_kernel<2>, smem);
+        fft_pass_kernel<2><<<(unsigned)grid, kFftThreads, smem, s>>>(a);
+        OO_CUDA_TRY(cudaGetLastError());
+    }
+}
+
+}  // namespace oo

@@ -28,7 +28,10 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
+#include <type_traits>
 
+#include "ff.cuh"
 #include "oo_internal.h"
 
 namespace oo {
@@ -42,22 +45,10 @@ __device__ __forceinline__ float dirichlet_dev(int k, int K) {
     return __fdiv_rn((float)(k * k), (float)((K - 1) * (K - 1)));
 }
 
-// -------- float-float building blocks (Knuth two-sum, FMA two-product)
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-    s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
-    p = __fmul_rn(a, b);
-    e = __fmaf_rn(a, b, -p);
-}
+using ff::two_prod;
+using ff::two_sum;
 // (H, L) += (th, tl)
-__device__ __forceinline__ void ff_acc(float &H, float &L, float th, float tl) {
-    float e;
-    two_sum(H, th, H, e);
-    L = __fadd_rn(L, __fadd_rn(e, tl));
-}
+__device__ __forceinline__ void ff_acc(float &H, float &L, float th, float tl) { ff::acc(H, L, th, tl); }
 // b * (q1 - q2 - q3 + q4) as a float-float product term
 __device__ __forceinline__ void ff_cross(float b, float q1, float q2, float q3, float q4,
                                          float &th, float &tl) {
@@ -317,8 +308,8 @@ __device__ __forceinline__ void decode_unit(const StencilArgs &a, int u, int I, 
     ie = 1 + (int)(span * (sg + 1) / a.n_seg);
 }
 
-template <int TK, int TJ, int NCW, int DC, int DP>
-__global__ void __launch_bounds__((NCW + 1) * 32, 1)
+template <int TK, int TJ, int NCW, int DC, int DP, int PPT, int MINB>
+__global__ void __launch_bounds__((NCW + 1) * 32, MINB)
     stencil_kernel(const __grid_constant__ StencilMaps maps, const StencilArgs a) {
     using T = Tile<TK, TJ>;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -416,16 +407,19 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1)
         }
     } else {
         // ------------------------------------------------------ consumers
-        constexpr int QR = TK / 4;                       // quads per tile row
-        constexpr int QPT = TJ * QR / (NCW * 32);        // quads per thread per plane
+        // each thread owns PPT consecutive k points of one tile row
+        constexpr int QR = TK / PPT;                     // point groups per tile row
+        constexpr int QPT = TJ * QR / (NCW * 32);        // groups per thread per plane
         static_assert(QPT >= 1 && QPT * NCW * 32 == TJ * QR, "tile / warp mismatch");
+        static_assert(PPT == 2 || PPT == 4, "2 or 4 points per group");
+        using VecT = typename std::conditional<PPT == 4, float4, float2>::type;
         const float omega = a.omega;
         uint32_t cuse = 0, pseq = 0;
         bool ok = true;
         for (int u = blockIdx.x; ok && u < a.n_units; u += gridDim.x) {
             int k0, j0, ib, ie;
             decode_unit(a, u, I, TK, TJ, k0, j0, ib, ie);
-            double racc = 0.0;
+            float RH = 0.0f, RL = 0.0f;  // this thread's ss^2 sum over the unit (float-float)
             const uint32_t pbase = pseq;
             // planes ib-1 and ib must be present before the first compute
             for (uint32_t s = pbase; s < pbase + 2; ++s)
@@ -448,64 +442,69 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1)
 #pragma unroll
                 for (int m = 0; m < QPT; ++m) {
                     const int qd = (warp * 32 + lane) + m * NCW * 32;
-                    const int r = qd / QR, c4 = qd % QR;
-                    const int cc = 4 * c4 + 4;  // column of k in the p tile
-                    auto win6 = [&](const float *P, int row, float w[6]) {
+                    const int r = qd / QR, cg = qd % QR;
+                    const int cc = PPT * cg + 4;  // p-tile column of the group's first k
+                    // window of PPT+2 values: k-1 .. k+PPT
+                    auto winw = [&](const float *P, int row, float w[PPT + 2]) {
                         const float *base = P + row * T::PW + cc;
-                        const float4 v = *reinterpret_cast<const float4 *>(base);
+                        const VecT v = *reinterpret_cast<const VecT *>(base);
+                        const float *vf = reinterpret_cast<const float *>(&v);
                         w[0] = base[-1];
-                        w[1] = v.x;
-                        w[2] = v.y;
-                        w[3] = v.z;
-                        w[4] = v.w;
-                        w[5] = base[4];
+#pragma unroll
+                        for (int e = 0; e < PPT; ++e) w[e + 1] = vf[e];
+                        w[PPT + 1] = base[PPT];
                     };
-                    auto win4 = [&](const float *P, int row) {
-                        return *reinterpret_cast<const float4 *>(P + row * T::PW + cc);
+                    auto winv = [&](const float *P, int row, float w[PPT]) {
+                        const VecT v = *reinterpret_cast<const VecT *>(P + row * T::PW + cc);
+                        const float *vf = reinterpret_cast<const float *>(&v);
+#pragma unroll
+                        for (int e = 0; e < PPT; ++e) w[e] = vf[e];
                     };
-                    float C6[6], N6[6], S6[6], E6[6], W6[6];
-                    win6(P1, r + 1, C6);
-                    win6(P1, r + 2, N6);
-                    win6(P1, r, S6);
-                    win6(P2, r + 1, E6);
-                    win6(P0, r + 1, W6);
-                    const float4 en = win4(P2, r + 2), es = win4(P2, r), wn = win4(P0, r + 2),
-                                 ws = win4(P0, r);
-                    const float EN[4] = {en.x, en.y, en.z, en.w}, ES[4] = {es.x, es.y, es.z, es.w};
-                    const float WN[4] = {wn.x, wn.y, wn.z, wn.w}, WS[4] = {ws.x, ws.y, ws.z, ws.w};
-                    float cf[NCOEF][4];
+                    float Cw[PPT + 2], Nw[PPT + 2], Sw[PPT + 2], Ew[PPT + 2], Ww[PPT + 2];
+                    float EN[PPT], ES[PPT], WN[PPT], WS[PPT];
+                    winw(P1, r + 1, Cw);
+                    winw(P1, r + 2, Nw);
+                    winw(P1, r, Sw);
+                    winw(P2, r + 1, Ew);
+                    winw(P0, r + 1, Ww);
+                    winv(P2, r + 2, EN);
+                    winv(P2, r, ES);
+                    winv(P0, r + 2, WN);
+                    winv(P0, r, WS);
+                    float cf[NCOEF][PPT];
 #pragma unroll
                     for (int c = 0; c < NCOEF; ++c) {
-                        const float4 v = *reinterpret_cast<const float4 *>(CS + c * T::CTILE + r * TK + 4 * c4);
-                        cf[c][0] = v.x;
-                        cf[c][1] = v.y;
-                        cf[c][2] = v.z;
-                        cf[c][3] = v.w;
-                    }
-                    const int j = j0 + r, kb = k0 + 4 * c4;
-                    const bool row_in = (j <= J - 2);
-                    float out[4];
-                    bool inside[4];
+                        const VecT v = *reinterpret_cast<const VecT *>(CS + c * T::CTILE + r * TK + PPT * cg);
+                        const float *vf = reinterpret_cast<const float *>(&v);
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
+                        for (int e = 0; e < PPT; ++e) cf[c][e] = vf[e];
+                    }
+                    const int j = j0 + r, kb = k0 + PPT * cg;
+                    const bool row_in = (j <= J - 2);
+                    float out[PPT];
+                    bool inside[PPT];
+                    bool all_in = row_in;
+#pragma unroll
+                    for (int e = 0; e < PPT; ++e) {
                         const int k = kb + e;
                         inside[e] = row_in && k >= 1 && k <= K - 2;
+                        all_in = all_in && inside[e];
                         float H, L, th, tl;
-                        two_prod(cf[0][e], E6[e + 1], H, L);                      // a0 p[i+1]
-                        two_prod(cf[1][e], N6[e + 1], th, tl); ff_acc(H, L, th, tl);  // a1 p[j+1]
-                        two_prod(cf[2][e], C6[e + 2], th, tl); ff_acc(H, L, th, tl);  // a2 p[k+1]
+                        two_prod(cf[0][e], Ew[e + 1], H, L);                          // a0 p[i+1]
+                        two_prod(cf[1][e], Nw[e + 1], th, tl); ff_acc(H, L, th, tl);  // a1 p[j+1]
+                        two_prod(cf[2][e], Cw[e + 2], th, tl); ff_acc(H, L, th, tl);  // a2 p[k+1]
                         ff_cross(cf[4][e], EN[e], ES[e], WN[e], WS[e], th, tl);       // b0 Xij
                         ff_acc(H, L, th, tl);
-                        ff_cross(cf[5][e], N6[e + 2], S6[e + 2], N6[e], S6[e], th, tl);  // b1 Xjk
+                        ff_cross(cf[5][e], Nw[e + 2], Sw[e + 2], Nw[e], Sw[e], th, tl);  // b1 Xjk
                         ff_acc(H, L, th, tl);
-                        ff_cross(cf[6][e], E6[e + 2], W6[e + 2], E6[e], W6[e], th, tl);  // b2 Xik
+                        ff_cross(cf[6][e], Ew[e + 2], Ww[e + 2], Ew[e], Ww[e], th, tl);  // b2 Xik
                         ff_acc(H, L, th, tl);
-                        two_prod(cf[7][e], W6[e + 1], th, tl); ff_acc(H, L, th, tl);  // c0 p[i-1]
-                        two_prod(cf[8][e], S6[e + 1], th, tl); ff_acc(H, L, th, tl);  // c1 p[j-1]
-                        two_prod(cf[9][e], C6[e], th, tl); ff_acc(H, L, th, tl);      // c2 p[k-1]
+                        two_prod(cf[7][e], Ww[e + 1], th, tl); ff_acc(H, L, th, tl);  // c0 p[i-1]
+                        two_prod(cf[8][e], Sw[e + 1], th, tl); ff_acc(H, L, th, tl);  // c1 p[j-1]
+                        two_prod(cf[9][e], Cw[e], th, tl); ff_acc(H, L, th, tl);      // c2 p[k-1]
                         ff_acc(H, L, cf[11][e], 0.0f);                                // wrk1
                         // ss = (s0 * a3 - p) * bnd
-                        const float pc = C6[e + 1];
+                        const float pc = Cw[e + 1];
                         float t1, dh, dl, e1, sh, s1;
                         two_prod(H, cf[3][e], th, t1);
                         tl = __fmaf_rn(L, cf[3][e], t1);
@@ -519,18 +518,25 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1)
                         const float wl = __fmaf_rn(omega, sl, w1);
                         two_sum(pc, wh, yh, e2);
                         out[e] = __fadd_rn(yh, __fadd_rn(e2, wl));
-                        if (inside[e]) {
-                            const double sd = (double)sh + (double)sl;
-                            racc = fma(sd, sd, racc);
-                        }
+                        // ss^2 from the renormalised pair (sl can be ~1% of sh when ss
+                        // cancels deeply, so it must be folded in before squaring)
+                        float nh, nl, qh, q1;
+                        two_sum(sh, sl, nh, nl);
+                        two_prod(nh, nh, qh, q1);
+                        const float ql = __fmaf_rn(__fadd_rn(nh, nh), nl, q1);
+                        ff_acc(RH, RL, inside[e] ? qh : 0.0f, inside[e] ? ql : 0.0f);
                     }
                     if (row_in) {
                         float *dst = a.wrk2 + ((size_t)i * J + j) * a.pitch + kb;
-                        if (inside[0] && inside[1] && inside[2] && inside[3]) {
-                            *reinterpret_cast<float4 *>(dst) = make_float4(out[0], out[1], out[2], out[3]);
+                        if (all_in) {
+                            VecT v;
+                            float *vf = reinterpret_cast<float *>(&v);
+#pragma unroll
+                            for (int e = 0; e < PPT; ++e) vf[e] = out[e];
+                            *reinterpret_cast<VecT *>(dst) = v;
                         } else {
 #pragma unroll
-                            for (int e = 0; e < 4; ++e)
+                            for (int e = 0; e < PPT; ++e)
                                 if (inside[e]) dst[e] = out[e];
                         }
                     }
@@ -551,15 +557,14 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1)
                 mbar_arrive(smem_u32(&empty_p[(s1 + 1) % DP]));
             }
             pseq = pbase + (uint32_t)(ie - ib + 2);
-            // unit partial residual of this warp (no cross-warp barrier, so an
-            // aborting warp can never leave another one waiting)
+            // unit partial residual of this warp in FP64 (no cross-warp
+            // barrier, so an aborting warp can never leave another waiting)
+            double racc = (double)RH + (double)RL;
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) racc += __shfl_xor_sync(0xffffffffu, racc, o);
-            if (lane == 0) {
-                a.partials[(size_t)u * NCW + warp] = racc;
-                __threadfence();
-            }
+            if (lane == 0) a.partials[(size_t)u * NCW + warp] = racc;
         }
+        if (lane == 0) __threadfence();  // partials visible before the CTA is counted
     }
     __syncthreads();
 
@@ -589,8 +594,13 @@ __global__ void __launch_bounds__((NCW + 1) * 32, 1)
     }
 }
 
-// variants: (TK, TJ, NCW, DC, DP)
-template <int TK, int TJ, int NCW, int DC, int DP>
+// variants: (TK, TJ, NCW, DC, DP, PPT, MINB)
+struct VariantInfo {
+    int TK, TJ, ctas_per_sm;
+    void (*launch)(int grid, const StencilMaps &m, const StencilArgs &a, cudaStream_t s);
+};
+
+template <int TK, int TJ, int NCW, int DC, int DP, int PPT, int MINB>
 struct Variant {
     using T = Tile<TK, TJ>;
     static constexpr int kThreads = (NCW + 1) * 32;
@@ -598,24 +608,37 @@ struct Variant {
         return 128 + (size_t)DC * NCOEF * T::CTILE * 4 + (size_t)DP * T::PSLOT * 4 +
                2 * (DC + DP) * 8 + 32 * 8 + 16;
     }
-    static void prepare() {
+    static void launch(int grid, const StencilMaps &m, const StencilArgs &a, cudaStream_t s) {
         static bool done = false;
         if (!done) {
-            OO_CUDA_TRY(cudaFuncSetAttribute(stencil_kernel<TK, TJ, NCW, DC, DP>,
+            OO_CUDA_TRY(cudaFuncSetAttribute(stencil_kernel<TK, TJ, NCW, DC, DP, PPT, MINB>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem_bytes()));
             done = true;
         }
-    }
-    static void launch(int grid, const StencilMaps &m, const StencilArgs &a, cudaStream_t s) {
-        prepare();
-        stencil_kernel<TK, TJ, NCW, DC, DP><<<grid, kThreads, smem_bytes(), s>>>(m, a);
+        stencil_kernel<TK, TJ, NCW, DC, DP, PPT, MINB><<<grid, kThreads, smem_bytes(), s>>>(m, a);
         OO_CUDA_TRY(cudaGetLastError());
     }
+    static VariantInfo info() { return VariantInfo{TK, TJ, MINB, &launch}; }
 };
 
-using BigVariant = Variant<128, 8, 8, 3, 5>;
-using SmallVariant = Variant<64, 8, 4, 3, 5>;
+// 0: 128x8 tile, 8 consumer warps x 4 points, 1 CTA/SM
+// 1: 128x8 tile, 16 consumer warps x 2 points, 1 CTA/SM
+// 2: 128x4 tile, 8 consumer warps x 2 points, 2 CTAs/SM
+// 3: 64x8 tile, 4 consumer warps x 4 points (short rows, K <= 65)
+// 4: 64x8 tile, 8 consumer warps x 2 points, 2 CTAs/SM (short rows)
+const VariantInfo &variant(int v) {
+    static const VariantInfo table[] = {
+        Variant<128, 8, 8, 3, 5, 4, 1>::info(),
+        Variant<128, 8, 16, 3, 5, 2, 1>::info(),
+        Variant<128, 4, 8, 3, 5, 2, 2>::info(),
+        Variant<64, 8, 4, 3, 5, 4, 1>::info(),
+        Variant<64, 8, 8, 3, 5, 2, 2>::info(),
+    };
+    constexpr int n = sizeof(table) / sizeof(table[0]);
+    return table[(v >= 0 && v < n) ? v : 0];
+}
+constexpr int kNumVariants = 5;
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -648,7 +671,7 @@ void make_map(CUtensorMap *m, const float *base, const JacobiDims &d, uint32_t b
 
 struct StencilPlan {
     JacobiDims d{};
-    bool big = true;
+    int variant = 0;
     int TK = 128, TJ = 8;
     StencilMaps maps;
     StencilArgs args{};
@@ -663,9 +686,14 @@ StencilPlan *stencil_plan_create(const JacobiDims &d, const float *const coef[NC
     OO_REQUIRE(((uintptr_t)wrk2 & 15u) == 0, OO_EINVAL, "wrk2 must be 16-byte aligned");
     auto sp = new StencilPlan();
     sp->d = d;
-    sp->big = d.K - 1 > 64;
-    sp->TK = sp->big ? 128 : 64;
-    sp->TJ = 8;
+    // default tile shape by row length; OO_STENCIL_VARIANT overrides (tuning sweeps)
+    sp->variant = d.K - 1 > 64 ? 0 : 4;
+    if (const char *ev = std::getenv("OO_STENCIL_VARIANT")) {
+        const int v = std::atoi(ev);
+        if (v >= 0 && v < kNumVariants) sp->variant = v;
+    }
+    sp->TK = variant(sp->variant).TK;
+    sp->TJ = variant(sp->variant).TJ;
     try {
         for (int c = 0; c < NCOEF; ++c) make_map(&sp->maps.coef[c], coef[c], d, sp->TK, sp->TJ);
         make_map(&sp->maps.p, p, d, sp->TK + 8, sp->TJ + 2);
@@ -680,7 +708,7 @@ StencilPlan *stencil_plan_create(const JacobiDims &d, const float *const coef[NC
         const int span = d.I - 2;
         // segments of the i range: balance units over one CTA per SM, with
         // a small charge for the two halo planes every unit reloads
-        const int G = std::max(1, num_sms);
+        const int G = std::max(1, num_sms * variant(sp->variant).ctas_per_sm);
         double best = 1e300;
         int best_seg = 1;
         for (int ns = 1; ns <= span; ++ns) {
@@ -697,12 +725,12 @@ StencilPlan *stencil_plan_create(const JacobiDims &d, const float *const coef[NC
         a.n_units = cols * best_seg;
         sp->grid = std::min(a.n_units, G);
         a.wrk2 = wrk2;
-        const size_t bytes = (size_t)a.n_units * 8 * 8 + 256;  // up to 8 consumer warps
+        const size_t bytes = (size_t)a.n_units * 16 * 8 + 256;  // up to 16 consumer warps
         OO_CUDA_TRY(cudaMalloc(&sp->scratch, bytes));
         OO_CUDA_TRY(cudaMemset(sp->scratch, 0, bytes));
         a.partials = reinterpret_cast<double *>(sp->scratch);
         a.counter = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(sp->scratch) +
-                                                 (size_t)a.n_units * 8 * 8);
+                                                 (size_t)a.n_units * 16 * 8);
         a.err = a.counter + 1;
     } catch (...) {
         if (sp->scratch) cudaFree(sp->scratch);
@@ -721,10 +749,7 @@ void stencil_plan_destroy(StencilPlan *sp) {
 void launch_stencil(StencilPlan *sp, float omega, double *res_dev, cudaStream_t s) {
     sp->args.omega = omega;
     sp->args.res = res_dev;
-    if (sp->big)
-        BigVariant::launch(sp->grid, sp->maps, sp->args, s);
-    else
-        SmallVariant::launch(sp->grid, sp->maps, sp->args, s);
+    variant(sp->variant).launch(sp->grid, sp->maps, sp->args, s);
 }
 
 unsigned stencil_plan_check(StencilPlan *sp, cudaStream_t s) {

@@ -85,6 +85,39 @@ struct JacobiWork {
     float *hptr(int v) const { return host + (size_t)v * d.n_host(); }
 };
 
+// -------------------------------------------------------------------- FFT
+struct FftPlan;
+FftPlan *fft_plan_create(long long n);
+void fft_plan_destroy(FftPlan *p);
+size_t fft_scratch_bytes(const FftPlan *p, int batch);
+// batch transforms of length n (contiguous, interleaved complex128); dir -1
+// forward, +1 inverse (1/n scaled); in may equal out; async on s
+void launch_fft(const FftPlan *p, int batch, int dir, const double *in, double *out, void *scratch,
+                cudaStream_t s);
+
+// Grow-only device buffer owned by a context.
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    void *get(size_t want) {
+        if (want <= bytes) return ptr;
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        bytes = 0;
+        if (cudaMalloc(&ptr, want) != cudaSuccess) {
+            cudaGetLastError();
+            throw Error{OO_ENOMEM, "device scratch of " + std::to_string(want) + " bytes"};
+        }
+        bytes = want;
+        return ptr;
+    }
+    void release() {
+        if (ptr) cudaFree(ptr);
+        ptr = nullptr;
+        bytes = 0;
+    }
+};
+
 // --------------------------------------------------------------- context
 struct Ctx {
     int device = 0;
@@ -103,6 +136,16 @@ struct Ctx {
         std::vector<float> p;
     };
     std::vector<Ref> refs;
+    // function blocks
+    std::vector<std::pair<long long, FftPlan *>> fft_plans;
+    DevBuf fft_scratch, stage_a, stage_b, stage_c;
+    FftPlan *fft_plan(long long n) {
+        for (auto &kv : fft_plans)
+            if (kv.first == n) return kv.second;
+        FftPlan *p = fft_plan_create(n);
+        fft_plans.push_back({n, p});
+        return p;
+    }
 };
 
 // Kernel launchers (jacobi.cu).  All asynchronous on `s`.

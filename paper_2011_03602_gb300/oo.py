@@ -91,6 +91,8 @@ def lib():
         "oo_ga_table": (_c.c_int, [_c.c_int, _c.c_int, _c.c_int, _dbl, _dbl, _u64, _vp, _vp,
                                    P(_u64), P(_dbl)]),
         "oo_lookup_block": (_c.c_int, [_c.c_char_p, _c.c_int, P(_c.c_int)]),
+        "oo_fft_c128": (_c.c_int, [_vp, _c.c_int64, _c.c_int, _vp, _vp]),
+        "oo_fft_c128_dev": (_c.c_int, [_vp, _c.c_int64, _c.c_int, _c.c_int, _vp, _vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -258,6 +260,20 @@ def oo_ga_search(ctx, prob, hoist, pop, gens, pc, pm, seed, eval_timeout_ms=0.0)
 
 
 # --------------------------------------------------------- function blocks
+def oo_fft_c128(ctx, x, direction=-1, out=None):
+    """Host complex128 array -> its FFT (new array unless out is given)."""
+    x = np.ascontiguousarray(x, np.complex128)
+    if out is None:
+        out = np.empty_like(x)
+    _check(ctx, lib().oo_fft_c128(ctx, x.size, direction, x.ctypes.data_as(_vp), _host_ptr(out, np.complex128)))
+    return out
+
+
+def oo_fft_c128_dev(ctx, n, batch, direction, din, dout):
+    """Device buffers of batch * n complex128 (torch tensors or addresses)."""
+    _check(ctx, lib().oo_fft_c128_dev(ctx, n, batch, direction, _dev_ptr(din), _dev_ptr(dout)))
+
+
 def oo_lookup_block(callee, lang):
     b = _c.c_int()
     _check(None, lib().oo_lookup_block(callee.encode(), lang, _c.byref(b)))
