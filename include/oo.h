@@ -223,6 +223,28 @@ enum { OO_LANG_C = 0, OO_LANG_PYTHON = 1, OO_LANG_JAVA = 2 };
  * code-pattern table for language `lang`.  OO_ENOTFOUND if absent.       */
 oo_status oo_lookup_block(const char *callee, int lang, int *block_id);
 
+/* Sec. 3.2.2 matrix-product block: C = A B for FP64 row-major A (m x k,
+ * leading dimension lda >= k), B (k x n, ldb >= n), C (m x n, ldc >= n).
+ * prec selects the precision pattern:
+ *   OO_PREC_SPLIT3_BF16  A and B are scaled per row / column by powers of
+ *                        two and split into BF16 hi + lo; C = A1 B1 +
+ *                        (A1 B2 + A2 B1) on the tensor cores (FP32
+ *                        accumulators in tensor memory), the two partial
+ *                        products summed in FP64.  Error about 5e-5 of
+ *                        sum_l |a_il b_lj| per element; callers needing
+ *                        FP64 accuracy must not use this mode.
+ * oo_gemm_f64: host buffers, synchronous.                                 */
+enum { OO_PREC_SPLIT3_BF16 = 0 };
+oo_status oo_gemm_f64(oo_ctx *ctx, int prec, int m, int n, int k, const double *A, int lda,
+                      const double *B, int ldb, double *C, int ldc);
+/* Device buffers (caller-owned), asynchronous on the context's stream; the
+ * library's scratch for the split operands is reused across calls.        */
+oo_status oo_gemm_f64_dev(oo_ctx *ctx, int prec, int m, int n, int k, const double *dA, int lda,
+                          const double *dB, int ldb, double *dC, int ldc);
+/* After oo_gemm_f64_dev calls of shape (m, n, k): synchronise and report
+ * OO_ETIMEOUT if a bounded pipeline wait inside the kernel ran out.       */
+oo_status oo_gemm_check(oo_ctx *ctx, int m, int n, int k);
+
 /* Sec. 3.2.2 Fourier-transform block: complex128 FFT of length n = 2^k,
  * 0 <= k <= 24, interleaved (re, im) doubles.  dir -1: forward,
  * X_k = sum_j x_j exp(-2 pi i jk/n); dir +1: inverse with exp(+...) and 1/n.

@@ -131,6 +131,7 @@ void oo_destroy(oo_ctx *ctx) {
     ctx->c.stage_a.release();
     ctx->c.stage_b.release();
     ctx->c.stage_c.release();
+    ctx->c.gemm_scratch.release();
     if (ctx->c.own_stream && ctx->c.stream) cudaStreamDestroy(ctx->c.stream);
     delete ctx;
 }
@@ -319,6 +320,59 @@ oo_status oo_fft_c128(oo_ctx *ctx, int64_t n, int dir, const double *in, double 
         launch_fft(p, 1, dir, d, d, scratch, ctx->c.stream);
         OO_CUDA_TRY(cudaMemcpyAsync(out, d, bytes, cudaMemcpyDeviceToHost, ctx->c.stream));
         OO_CUDA_TRY(cudaStreamSynchronize(ctx->c.stream));
+    });
+}
+
+namespace {
+void gemm_checks(int prec, int m, int n, int k, int lda, int ldb, int ldc) {
+    OO_REQUIRE(prec == OO_PREC_SPLIT3_BF16, OO_EINVAL, "unsupported precision pattern");
+    OO_REQUIRE(m >= 1 && n >= 1 && k >= 1, OO_EINVAL, "m, n, k must be >= 1");
+    OO_REQUIRE(m <= (1 << 20) && n <= (1 << 20) && k <= (1 << 21), OO_EINVAL, "matrix too large");
+    OO_REQUIRE(lda >= k && ldb >= n && ldc >= n, OO_EINVAL, "leading dimension too small");
+}
+}  // namespace
+
+oo_status oo_gemm_f64_dev(oo_ctx *ctx, int prec, int m, int n, int k, const double *dA, int lda,
+                          const double *dB, int ldb, double *dC, int ldc) {
+    if (!ctx) return OO_EINVAL;
+    return guarded(ctx, [&] {
+        OO_REQUIRE(dA && dB && dC, OO_EINVAL, "null pointer");
+        gemm_checks(prec, m, n, k, lda, ldb, ldc);
+        use_device(ctx->c);
+        void *scratch = ctx->c.gemm_scratch.get(gemm_scratch_bytes(m, n, k));
+        launch_gemm_split3(m, n, k, dA, lda, dB, ldb, dC, ldc, scratch, ctx->c.stream);
+    });
+}
+
+oo_status oo_gemm_f64(oo_ctx *ctx, int prec, int m, int n, int k, const double *A, int lda, const double *B,
+                      int ldb, double *C, int ldc) {
+    if (!ctx) return OO_EINVAL;
+    return guarded(ctx, [&] {
+        OO_REQUIRE(A && B && C, OO_EINVAL, "null pointer");
+        gemm_checks(prec, m, n, k, lda, ldb, ldc);
+        use_device(ctx->c);
+        cudaStream_t s = ctx->c.stream;
+        double *dA = static_cast<double *>(ctx->c.stage_a.get((size_t)m * k * 8));
+        double *dB = static_cast<double *>(ctx->c.stage_b.get((size_t)k * n * 8));
+        double *dC = static_cast<double *>(ctx->c.stage_c.get((size_t)m * n * 8));
+        OO_CUDA_TRY(cudaMemcpy2DAsync(dA, (size_t)k * 8, A, (size_t)lda * 8, (size_t)k * 8, m, cudaMemcpyHostToDevice, s));
+        OO_CUDA_TRY(cudaMemcpy2DAsync(dB, (size_t)n * 8, B, (size_t)ldb * 8, (size_t)n * 8, k, cudaMemcpyHostToDevice, s));
+        void *scratch = ctx->c.gemm_scratch.get(gemm_scratch_bytes(m, n, k));
+        launch_gemm_split3(m, n, k, dA, k, dB, n, dC, n, scratch, s);
+        OO_CUDA_TRY(cudaMemcpy2DAsync(C, (size_t)ldc * 8, dC, (size_t)n * 8, (size_t)n * 8, m, cudaMemcpyDeviceToHost, s));
+        const unsigned e = gemm_check_error(scratch, m, n, k, s);
+        OO_REQUIRE(e == 0, OO_ETIMEOUT, "GEMM pipeline wait ran out (error bits " + std::to_string(e) + ")");
+    });
+}
+
+oo_status oo_gemm_check(oo_ctx *ctx, int m, int n, int k) {
+    if (!ctx) return OO_EINVAL;
+    return guarded(ctx, [&] {
+        use_device(ctx->c);
+        OO_REQUIRE(ctx->c.gemm_scratch.ptr && ctx->c.gemm_scratch.bytes >= gemm_scratch_bytes(m, n, k), OO_ESTATE,
+                   "no GEMM of that shape has run on this context");
+        const unsigned e = gemm_check_error(ctx->c.gemm_scratch.ptr, m, n, k, ctx->c.stream);
+        OO_REQUIRE(e == 0, OO_ETIMEOUT, "GEMM pipeline wait ran out (error bits " + std::to_string(e) + ")");
     });
 }
 

@@ -62,10 +62,9 @@ __device__ __forceinline__ void split_scaled(double x, int S, float &h, float &l
     l = sign ? -lf : lf;
 }
 
-// (h + l) * 2^S as a double
+// (h + l) * 2^S as a double, integer-only conversion
 __device__ __forceinline__ double widen_scaled(float h, float l, int S) {
-    const double d = (double)h + (double)l;
-    return ldexp(d, S);
+    return ff::scale_pow2(ff::to_double(h, l), S);
 }
 
 struct FftArgs {

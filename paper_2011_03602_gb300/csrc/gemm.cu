@@ -1,0 +1,478 @@
+// Matrix-product function block (Sec. 3.2.2, Sec. 4.2.1): C = A B for FP64
+// A (m x k), B (k x n), row-major, computed on the 5th-generation tensor
+// cores with the split-precision ("precision pattern") scheme:
+//
+//   A = 2^sA (A1 + A2 + dA),  B = (B1 + B2 + dB) 2^sB,  A1, A2, B1, B2 in BF16
+//   C ~= 2^(sA + sB) ( A1 B1 + [A1 B2 + A2 B1] )
+//
+// sA is a per-row power of two (per-column sB for B) that brings the row's
+// largest entry into [1/2, 1), so the split keeps 16 significant bits of
+// every entry regardless of the input's range.  The two accumulators live
+// in tensor memory (TMEM) in FP32: D_hh = A1 B1 and D_x = A1 B2 + A2 B1; the
+// epilogue sums them in FP64 ("split-term correction sum") and applies the
+// power-of-two scales.  Error: about 3 * 2^-16 of sum|a||b| per element
+// plus FP32 accumulation rounding; the result is reported against an FP64
+// oracle, not claimed to be FP64.
+//
+// Kernel: one CTA per 128 x 256 output tile; warp 0 issues TMA loads of the
+// four BF16 operand tiles (128B-swizzled, K-major) into a 2-stage ring,
+// warp 1 allocates 512 TMEM columns and one of its threads issues
+// tcgen05.mma (M=128, N=256, K=16, kind::f16, BF16 x BF16 -> FP32) and
+// tcgen05.commit to release stages; warps 4-7 read the accumulators with
+// tcgen05.ld and write FP64 C.  Every mbarrier wait is bounded.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+
+#include "ff.cuh"
+#include "oo_internal.h"
+
+namespace oo {
+
+namespace {
+
+constexpr int kBM = 128, kBN = 256, kBK = 64, kStages = 2;
+constexpr int kGemmThreads = 256;
+constexpr uint32_t kTileA = kBM * kBK * 2;   // 16 KB
+constexpr uint32_t kTileB = kBN * kBK * 2;   // 32 KB
+constexpr uint32_t kStageBytes = 2 * kTileA + 2 * kTileB;  // 96 KB
+constexpr long long kGemmWaitLimit = 2000000000ll;
+
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void bar_init(uint32_t b, uint32_t c) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b), "r"(c) : "memory");
+}
+__device__ __forceinline__ void bar_expect_tx(uint32_t b, uint32_t bytes) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(b),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool bar_try(uint32_t b, uint32_t par) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred P;\n\tmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\tselp.u32 %0, 1, 0, P;\n\t}"
+        : "=r"(ok)
+        : "r"(b), "r"(par)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool bar_wait(uint32_t b, uint32_t par, volatile int *abort_flag, unsigned *err,
+                                         unsigned code) {
+    if (bar_try(b, par)) return true;
+    const long long t0 = clock64();
+    while (true) {
+        if (bar_try(b, par)) return true;
+        if (*abort_flag) return false;
+        if (clock64() - t0 > kGemmWaitLimit) {
+            *abort_flag = 1;
+            atomicOr(err, code);
+            return false;
+        }
+    }
+}
+__device__ __forceinline__ void tma_2d(uint32_t dst, const CUtensorMap *map, int c0, int c1, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
+        : "memory");
+}
+
+// ---- tcgen05 helpers
+// Shared-memory matrix descriptor: K-major operand tile stored as rows of
+// 128 bytes (64 BF16) with the 128-byte swizzle that TMA SWIZZLE_128B writes;
+// 8-row core groups 1024 bytes apart (SBO); LBO unused for this layout.
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr) {
+    uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;                 // LBO (encoded 16 B; ignored)
+    d |= (uint64_t)(1024u >> 4) << 32;      // SBO = 1024 B
+    d |= (uint64_t)1 << 46;                 // descriptor version
+    d |= (uint64_t)2 << 61;                 // 128-byte swizzle
+    return d;
+}
+// Instruction descriptor, kind::f16: D=F32, A=B=BF16, both K-major, M=128, N=256
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBN >> 3) << 17) |
+                            ((uint32_t)(kBM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+#define OO_TMEM_LD32(taddr, r)                                                                              \
+    asm volatile(                                                                                           \
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"   \
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"                           \
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),   \
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),          \
+          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),        \
+          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),        \
+          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])                                                             \
+        : "r"(taddr))
+
+struct GemmMaps {
+    CUtensorMap a1, a2, b1, b2;
+};
+
+struct GemmArgs {
+    int m, n, k, kp;        // kp: padded K of the split operands (multiple of 64)
+    int m_tiles, n_tiles;
+    double *C;
+    long long ldc;
+    const int *ea;          // per-row scale exponents of A (power of two)
+    const int *eb;          // per-column scale exponents of B
+    unsigned *err;
+};
+
+__global__ void __launch_bounds__(kGemmThreads, 1) gemm_split3_kernel(const __grid_constant__ GemmMaps maps,
+                                                                     const GemmArgs a) {
+    extern __shared__ __align__(1024) unsigned char gsm_raw[];
+    unsigned char *gsm = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(gsm_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(gsm + kStages * kStageBytes);
+    uint64_t *full = bars, *empty = bars + kStages, *accum = bars + 2 * kStages;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * kStages + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tm = blockIdx.x / a.n_tiles, tn = blockIdx.x % a.n_tiles;
+    const int m0 = tm * kBM, n0 = tn * kBN;
+    const int ksteps = a.kp / kBK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            bar_init(su32(&full[s]), 1);
+            bar_init(su32(&empty[s]), 1);
+        }
+        bar_init(su32(accum), 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        tc_fence_before();
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const uint32_t d_hh = tmem, d_x = tmem + 256;
+
+    bool issued_any = false;
+    int loaded = 0;
+    if (warp == 0 && lane == 0) {
+        // ---------------------------------------------------- TMA producer
+        for (int ks = 0; ks < ksteps; ++ks) {
+            const int s = ks % kStages;
+            const uint32_t use = ks / kStages;
+            if (use > 0 && !bar_wait(su32(&empty[s]), (use - 1) & 1, abort_flag, a.err, 1u)) break;
+            ++loaded;
+            unsigned char *st = gsm + (size_t)s * kStageBytes;
+            const uint32_t fb = su32(&full[s]);
+            bar_expect_tx(fb, kStageBytes);
+            const int k0 = ks * kBK;
+            tma_2d(su32(st), &maps.a1, k0, m0, fb);
+            tma_2d(su32(st + kTileA), &maps.a2, k0, m0, fb);
+            tma_2d(su32(st + 2 * kTileA), &maps.b1, k0, n0, fb);
+            tma_2d(su32(st + 2 * kTileA + kTileB), &maps.b2, k0, n0, fb);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------------------------------------------- MMA issuer
+        for (int ks = 0; ks < ksteps; ++ks) {
+            const int s = ks % kStages;
+            const uint32_t use = ks / kStages;
+            if (!bar_wait(su32(&full[s]), use & 1, abort_flag, a.err, 2u)) break;
+            tc_fence_after();
+            const uint32_t base = su32(gsm + (size_t)s * kStageBytes);
+            const uint32_t a1 = base, a2 = base + kTileA, b1 = base + 2 * kTileA, b2 = b1 + kTileB;
+#pragma unroll
+            for (int kk = 0; kk < kBK / 16; ++kk) {
+                const uint32_t off = kk * 32;  // 16 BF16 along K inside the 128-byte row
+                const uint32_t first = (ks == 0 && kk == 0) ? 0u : 1u;
+                mma_bf16(d_hh, sdesc_sw128(a1 + off), sdesc_sw128(b1 + off), first);
+                mma_bf16(d_x, sdesc_sw128(a1 + off), sdesc_sw128(b2 + off), first);
+                mma_bf16(d_x, sdesc_sw128(a2 + off), sdesc_sw128(b1 + off), 1u);
+            }
+            mma_commit(su32(&empty[s]));
+            issued_any = true;
+        }
+        if (issued_any) mma_commit(su32(accum));
+    } else if (warp >= 4) {
+        // ---------------------------------------------------- epilogue
+        const int q = warp - 4;  // TMEM lane quarter
+        if (bar_wait(su32(accum), 0, abort_flag, a.err, 4u)) {
+            tc_fence_after();
+            const int row = m0 + q * 32 + lane;
+            const bool row_ok = row < a.m;
+            const int sa = row_ok ? a.ea[row] : 0;
+            double *crow = a.C + (long long)row * a.ldc;
+            for (int c = 0; c < kBN; c += 32) {
+                uint32_t h[32], x[32];
+                const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+                OO_TMEM_LD32(d_hh + lane_off + c, h);
+                OO_TMEM_LD32(d_x + lane_off + c, x);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (!row_ok) continue;
+#pragma unroll
+                for (int t = 0; t < 32; ++t) {
+                    const int col = n0 + c + t;
+                    if (col < a.n) {
+                        // exact two-sum of the partial products, widened and scaled
+                        // without the (slow) FP64 pipe
+                        const double v = ff::to_double(__uint_as_float(h[t]), __uint_as_float(x[t]));
+                        crow[col] = ff::scale_pow2(v, sa + a.eb[col]);
+                    }
+                }
+            }
+        }
+    }
+    // drain on abort: the accumulator barrier completes only after every
+    // issued MMA; a stage's full barrier only after its copies landed
+    if (warp == 1 && lane == 0 && issued_any && *abort_flag) {
+        const long long t0 = clock64();
+        while (!bar_try(su32(accum), 0) && clock64() - t0 < kGemmWaitLimit) {
+        }
+    }
+    if (warp == 0 && lane == 0 && *abort_flag) {
+        for (int ks = (loaded > kStages ? loaded - kStages : 0); ks < loaded; ++ks) {
+            const long long t0 = clock64();
+            while (!bar_try(su32(&full[ks % kStages]), (ks / kStages) & 1) && clock64() - t0 < kGemmWaitLimit) {
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+    }
+}
+
+// ---------------------------------------------------------------- splitting
+// biased exponent of the largest |A[i][:]| per row (0 for an all-zero row)
+__global__ void row_maxexp_kernel(const double *A, long long lda, int m, int k, int *e) {
+    const int row = blockIdx.x;
+    if (row >= m) return;
+    const unsigned long long *p = reinterpret_cast<const unsigned long long *>(A + (long long)row * lda);
+    int mx = 0;
+    for (int l = threadIdx.x; l < k; l += blockDim.x) {
+        const int ex = (int)((p[l] >> 52) & 0x7ffu);
+        mx = max(mx, ex == 0x7ff ? 0x7fe : ex);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    __shared__ int ws[32];
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = max(mx, ws[w]);
+        e[row] = mx == 0 ? 0 : mx - 1023 + 1;
+    }
+}
+// per-column maxima of B (k x n): grid.x over column blocks of 32, grid.y over k chunks
+__global__ void col_maxexp_kernel(const double *B, long long ldb, int k, int n, int rows_per, int *e) {
+    const int col = blockIdx.x * 32 + threadIdx.x;
+    const int r0 = blockIdx.y * rows_per, r1 = min(k, r0 + rows_per);
+    if (col >= n) return;
+    int mx = 0;
+    for (int l = r0 + threadIdx.y; l < r1; l += blockDim.y) {
+        const int ex = (int)((__double_as_longlong(B[(long long)l * ldb + col]) >> 52) & 0x7ff);
+        mx = max(mx, ex == 0x7ff ? 0x7fe : ex);
+    }
+    if (mx > 0) atomicMax(e + col, mx);
+}
+__global__ void exp_to_scale_kernel(int *e, int count) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) e[i] = e[i] == 0 ? 0 : e[i] - 1023 + 1;
+}
+
+// x * 2^-S -> (hi, lo) BF16 pair with hi + lo = x * 2^-S to ~16 bits
+__device__ __forceinline__ void split_bf16(double x, int S, __nv_bfloat16 &hi, __nv_bfloat16 &lo) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi32 = (unsigned)(b >> 32), lo32 = (unsigned)b;
+    const unsigned sign = hi32 & 0x80000000u;
+    const int e = (int)((hi32 >> 20) & 0x7ffu);
+    const int fe = e - 1023 - S + 127;
+    float h = 0.0f, l = 0.0f;
+    if (e != 0 && e != 0x7ff && fe > 0) {
+        h = __uint_as_float(sign | ((unsigned)fe << 23) | ((hi32 & 0xfffffu) << 3) | (lo32 >> 29));
+        const unsigned r = lo32 & 0x1fffffffu;
+        const int le = fe - 52;
+        if (le > 0 && r != 0) {
+            const float lf = __fmul_rn(__uint2float_rn(r), __uint_as_float((unsigned)le << 23));
+            l = sign ? -lf : lf;
+        }
+    }
+    hi = __float2bfloat16_rn(h);
+    const float rem = __fadd_rn(__fsub_rn(h, __bfloat162float(hi)), l);
+    lo = __float2bfloat16_rn(rem);
+}
+
+// A (m x k, lda) -> A1, A2 (m x kp), zero padding in [k, kp)
+__global__ void split_rows_kernel(const double *A, long long lda, int m, int k, int kp, const int *ea,
+                                  __nv_bfloat16 *A1, __nv_bfloat16 *A2) {
+    const long long total = (long long)m * kp;
+    for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < total;
+         x += (long long)gridDim.x * blockDim.x) {
+        const int row = (int)(x / kp), l = (int)(x % kp);
+        __nv_bfloat16 h = __float2bfloat16_rn(0.0f), lo = h;
+        if (l < k) split_bf16(A[(long long)row * lda + l], ea[row], h, lo);
+        A1[x] = h;
+        A2[x] = lo;
+    }
+}
+
+// B (k x n, ldb) -> B1t, B2t (n x kp, transposed), zero padding in [k, kp)
+__global__ void split_cols_t_kernel(const double *B, long long ldb, int k, int n, int kp, const int *eb,
+                                    __nv_bfloat16 *B1t, __nv_bfloat16 *B2t) {
+    __shared__ __nv_bfloat16 th[32][33], tl[32][33];
+    const int l0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
+        const int l = l0 + yy, col = c0 + threadIdx.x;
+        __nv_bfloat16 h = __float2bfloat16_rn(0.0f), lo = h;
+        if (l < k && col < n) split_bf16(B[(long long)l * ldb + col], eb[col], h, lo);
+        th[yy][threadIdx.x] = h;
+        tl[yy][threadIdx.x] = lo;
+    }
+    __syncthreads();
+    for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
+        const int col = c0 + yy, l = l0 + threadIdx.x;
+        if (col < n && l < kp) {
+            B1t[(long long)col * kp + l] = th[threadIdx.x][yy];
+            B2t[(long long)col * kp + l] = tl[threadIdx.x][yy];
+        }
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        OO_CUDA_TRY(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+        OO_REQUIRE(q == cudaDriverEntryPointSuccess && p != nullptr, OO_ECUDA, "driver has no cuTensorMapEncodeTiled");
+        fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+void map_bf16(CUtensorMap *m, const void *base, int rows, int kp, int box_rows) {
+    OO_REQUIRE(((uintptr_t)base & 15u) == 0, OO_EINVAL, "split operand must be 16-byte aligned");
+    const cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)kp * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
+    const cuuint32_t es[2] = {1, 1};
+    const CUresult r = encode_tiled()(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims,
+                                      strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    OO_REQUIRE(r == CUDA_SUCCESS, OO_ECUDA, "cuTensorMapEncodeTiled (GEMM) failed: " + std::to_string((int)r));
+}
+
+size_t smem_gemm() { return 1024 + (size_t)kStages * kStageBytes + 256; }
+
+}  // namespace
+
+size_t gemm_scratch_bytes(int m, int n, int k) {
+    const size_t kp = (size_t)(k + kBK - 1) / kBK * kBK;
+    const size_t a = (size_t)m * kp * 2, b = (size_t)n * kp * 2;
+    return 2 * ((a + 255) / 256 * 256) + 2 * ((b + 255) / 256 * 256) + ((size_t)m + n) * 4 + 1024;
+}
+
+void launch_gemm_split3(int m, int n, int k, const double *A, long long lda, const double *B, long long ldb,
+                        double *C, long long ldc, void *scratch, cudaStream_t s) {
+    OO_REQUIRE(m >= 1 && n >= 1 && k >= 1, OO_EINVAL, "m, n, k must be >= 1");
+    OO_REQUIRE(lda >= k && ldb >= n && ldc >= n, OO_EINVAL, "leading dimensions too small");
+    const int kp = (k + kBK - 1) / kBK * kBK;
+    const size_t a_bytes = ((size_t)m * kp * 2 + 255) / 256 * 256, b_bytes = ((size_t)n * kp * 2 + 255) / 256 * 256;
+    char *p = static_cast<char *>(scratch);
+    auto *A1 = reinterpret_cast<__nv_bfloat16 *>(p);
+    auto *A2 = reinterpret_cast<__nv_bfloat16 *>(p + a_bytes);
+    auto *B1 = reinterpret_cast<__nv_bfloat16 *>(p + 2 * a_bytes);
+    auto *B2 = reinterpret_cast<__nv_bfloat16 *>(p + 2 * a_bytes + b_bytes);
+    int *ea = reinterpret_cast<int *>(p + 2 * a_bytes + 2 * b_bytes);
+    int *eb = ea + m;
+    unsigned *err = reinterpret_cast<unsigned *>(eb + n);
+    OO_CUDA_TRY(cudaMemsetAsync(err, 0, 4, s));
+
+    row_maxexp_kernel<<<m, 256, 0, s>>>(A, lda, m, k, ea);
+    OO_CUDA_TRY(cudaGetLastError());
+    OO_CUDA_TRY(cudaMemsetAsync(eb, 0, (size_t)n * 4, s));
+    {
+        const int rows_per = 256;
+        dim3 grid((n + 31) / 32, (k + rows_per - 1) / rows_per), block(32, 8);
+        OO_REQUIRE(grid.y <= 65535, OO_EINVAL, "k too large");
+        col_maxexp_kernel<<<grid, block, 0, s>>>(B, ldb, k, n, rows_per, eb);
+        OO_CUDA_TRY(cudaGetLastError());
+        exp_to_scale_kernel<<<(n + 255) / 256, 256, 0, s>>>(eb, n);
+        OO_CUDA_TRY(cudaGetLastError());
+    }
+    {
+        int dev = 0, sms = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const long long tot = (long long)m * kp;
+        split_rows_kernel<<<(int)std::min<long long>((tot + 255) / 256, (long long)sms * 16), 256, 0, s>>>(
+            A, lda, m, k, kp, ea, A1, A2);
+        OO_CUDA_TRY(cudaGetLastError());
+        dim3 grid((n + 31) / 32, (kp + 31) / 32), block(32, 8);
+        OO_REQUIRE(grid.y <= 65535, OO_EINVAL, "k too large");
+        split_cols_t_kernel<<<grid, block, 0, s>>>(B, ldb, k, n, kp, eb, B1, B2);
+        OO_CUDA_TRY(cudaGetLastError());
+    }
+    GemmMaps maps;
+    map_bf16(&maps.a1, A1, m, kp, kBM);
+    map_bf16(&maps.a2, A2, m, kp, kBM);
+    map_bf16(&maps.b1, B1, n, kp, kBN);
+    map_bf16(&maps.b2, B2, n, kp, kBN);
+    GemmArgs ga{};
+    ga.m = m;
+    ga.n = n;
+    ga.k = k;
+    ga.kp = kp;
+    ga.m_tiles = (m + kBM - 1) / kBM;
+    ga.n_tiles = (n + kBN - 1) / kBN;
+    ga.C = C;
+    ga.ldc = ldc;
+    ga.ea = ea;
+    ga.eb = eb;
+    ga.err = err;
+    static bool attr = false;
+    if (!attr) {
+        OO_CUDA_TRY(cudaFuncSetAttribute(gemm_split3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_gemm()));
+        attr = true;
+    }
+    const long long tiles = (long long)ga.m_tiles * ga.n_tiles;
+    OO_REQUIRE(tiles < (1ll << 31), OO_EINVAL, "too many tiles");
+    gemm_split3_kernel<<<(unsigned)tiles, kGemmThreads, smem_gemm(), s>>>(maps, ga);
+    OO_CUDA_TRY(cudaGetLastError());
+}
+
+unsigned gemm_check_error(void *scratch, int m, int n, int k, cudaStream_t s) {
+    const int kp = (k + kBK - 1) / kBK * kBK;
+    const size_t a_bytes = ((size_t)m * kp * 2 + 255) / 256 * 256, b_bytes = ((size_t)n * kp * 2 + 255) / 256 * 256;
+    unsigned *err = reinterpret_cast<unsigned *>(static_cast<char *>(scratch) + 2 * a_bytes + 2 * b_bytes +
+                                                 ((size_t)m + n) * 4);
+    unsigned e = 0;
+    OO_CUDA_TRY(cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, s));
+    OO_CUDA_TRY(cudaStreamSynchronize(s));
+    if (e) OO_CUDA_TRY(cudaMemsetAsync(err, 0, 4, s));
+    return e;
+}
+
+}  // namespace oo

@@ -407,26 +407,82 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB)
         }
     } else {
         // ------------------------------------------------------ consumers
-        // each thread owns PPT consecutive k points of one tile row
+        // Each thread owns PPT consecutive k points of one tile row and marches
+        // them through the unit's planes.  Carried in registers from plane to
+        // plane: the row-(j) window of planes i-1 and i, the j+-1 centres of
+        // plane i, D = p(j+1) - p(j-1) on plane i (exact two-sum pairs, all
+        // window positions) and its centres on plane i-1.  Per plane only the
+        // three rows of plane i+1 are read from shared memory, and every cross
+        // difference is one float-float subtraction of carried exact pairs:
+        //   Xij = D(i+1) - D(i-1),  Xjk = D(i)(k+1) - D(i)(k-1),
+        //   Xik = F(k+1) - F(k-1)  with  F = p(i+1) - p(i-1)  on row j.
         constexpr int QR = TK / PPT;                     // point groups per tile row
-        constexpr int QPT = TJ * QR / (NCW * 32);        // groups per thread per plane
-        static_assert(QPT >= 1 && QPT * NCW * 32 == TJ * QR, "tile / warp mismatch");
+        static_assert(TJ * QR == NCW * 32, "one point group per consumer thread");
         static_assert(PPT == 2 || PPT == 4, "2 or 4 points per group");
+        constexpr int W = PPT + 2;                       // window: k-1 .. k+PPT
         using VecT = typename std::conditional<PPT == 4, float4, float2>::type;
         const float omega = a.omega;
+        const int r = (warp * 32 + lane) / QR, cg = (warp * 32 + lane) % QR;
+        const int cc = PPT * cg + 4;                     // p-tile column of the group's first k
+        auto winw = [&](const float *P, int row, float w[W]) {
+            const float *base = P + row * T::PW + cc;
+            const VecT v = *reinterpret_cast<const VecT *>(base);
+            const float *vf = reinterpret_cast<const float *>(&v);
+            w[0] = base[-1];
+#pragma unroll
+            for (int e = 0; e < PPT; ++e) w[e + 1] = vf[e];
+            w[PPT + 1] = base[PPT];
+        };
+        auto winc = [&](const float *P, int row, float w[PPT]) {
+            const VecT v = *reinterpret_cast<const VecT *>(P + row * T::PW + cc);
+            const float *vf = reinterpret_cast<const float *>(&v);
+#pragma unroll
+            for (int e = 0; e < PPT; ++e) w[e] = vf[e];
+        };
+        // float-float difference (ah + al) - (bh + bl), unnormalised
+        auto ffsub = [](float ah, float al, float bh, float bl, float &h, float &l) {
+            float e;
+            two_sum(ah, -bh, h, e);
+            l = __fadd_rn(e, __fsub_rn(al, bl));
+        };
         uint32_t cuse = 0, pseq = 0;
         bool ok = true;
         for (int u = blockIdx.x; ok && u < a.n_units; u += gridDim.x) {
             int k0, j0, ib, ie;
             decode_unit(a, u, I, TK, TJ, k0, j0, ib, ie);
+            const int j = j0 + r, kb = k0 + PPT * cg;
+            const bool row_in = (j <= J - 2);
             float RH = 0.0f, RL = 0.0f;  // this thread's ss^2 sum over the unit (float-float)
             const uint32_t pbase = pseq;
-            // planes ib-1 and ib must be present before the first compute
             for (uint32_t s = pbase; s < pbase + 2; ++s)
                 if (!mbar_wait(smem_u32(&full_p[s % DP]), (s / DP) & 1, abort_flag, a.err, 4u)) {
                     ok = false;
                     break;
                 }
+            if (!ok) break;
+            // prologue: planes ib-1 and ib
+            float Ww[W], Cw[W], Nc[PPT], Sc[PPT];
+            float Dh[W], Dl[W], Gh[PPT], Gl[PPT];
+            {
+                const float *P0 = p_s + (size_t)(pbase % DP) * T::PSLOT;
+                const float *P1 = p_s + (size_t)((pbase + 1) % DP) * T::PSLOT;
+                float t0[PPT], t1[PPT], n6[W], s6[W];
+                winw(P0, r + 1, Ww);
+                winc(P0, r + 2, t0);
+                winc(P0, r, t1);
+#pragma unroll
+                for (int e = 0; e < PPT; ++e) two_sum(t0[e], -t1[e], Gh[e], Gl[e]);
+                winw(P1, r + 1, Cw);
+                winw(P1, r + 2, n6);
+                winw(P1, r, s6);
+#pragma unroll
+                for (int x = 0; x < W; ++x) two_sum(n6[x], -s6[x], Dh[x], Dl[x]);
+#pragma unroll
+                for (int e = 0; e < PPT; ++e) {
+                    Nc[e] = n6[e + 1];
+                    Sc[e] = s6[e + 1];
+                }
+            }
             for (int i = ib; ok && i < ie; ++i) {
                 const uint32_t sprev = pbase + (uint32_t)(i - ib);
                 const uint32_t snext = sprev + 2;
@@ -435,118 +491,114 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB)
                     ok = false;
                     break;
                 }
-                const float *P0 = p_s + (size_t)(sprev % DP) * T::PSLOT;
-                const float *P1 = p_s + (size_t)((sprev + 1) % DP) * T::PSLOT;
                 const float *P2 = p_s + (size_t)(snext % DP) * T::PSLOT;
                 const float *CS = coef_s + (size_t)(cuse % DC) * NCOEF * T::CTILE;
+                float Ew[W], ENw[W], ESw[W];
+                winw(P2, r + 1, Ew);
+                winw(P2, r + 2, ENw);
+                winw(P2, r, ESw);
+                float cf[NCOEF][PPT];
 #pragma unroll
-                for (int m = 0; m < QPT; ++m) {
-                    const int qd = (warp * 32 + lane) + m * NCW * 32;
-                    const int r = qd / QR, cg = qd % QR;
-                    const int cc = PPT * cg + 4;  // p-tile column of the group's first k
-                    // window of PPT+2 values: k-1 .. k+PPT
-                    auto winw = [&](const float *P, int row, float w[PPT + 2]) {
-                        const float *base = P + row * T::PW + cc;
-                        const VecT v = *reinterpret_cast<const VecT *>(base);
-                        const float *vf = reinterpret_cast<const float *>(&v);
-                        w[0] = base[-1];
+                for (int c = 0; c < NCOEF; ++c) {
+                    const VecT v = *reinterpret_cast<const VecT *>(CS + c * T::CTILE + r * TK + PPT * cg);
+                    const float *vf = reinterpret_cast<const float *>(&v);
 #pragma unroll
-                        for (int e = 0; e < PPT; ++e) w[e + 1] = vf[e];
-                        w[PPT + 1] = base[PPT];
-                    };
-                    auto winv = [&](const float *P, int row, float w[PPT]) {
-                        const VecT v = *reinterpret_cast<const VecT *>(P + row * T::PW + cc);
-                        const float *vf = reinterpret_cast<const float *>(&v);
-#pragma unroll
-                        for (int e = 0; e < PPT; ++e) w[e] = vf[e];
-                    };
-                    float Cw[PPT + 2], Nw[PPT + 2], Sw[PPT + 2], Ew[PPT + 2], Ww[PPT + 2];
-                    float EN[PPT], ES[PPT], WN[PPT], WS[PPT];
-                    winw(P1, r + 1, Cw);
-                    winw(P1, r + 2, Nw);
-                    winw(P1, r, Sw);
-                    winw(P2, r + 1, Ew);
-                    winw(P0, r + 1, Ww);
-                    winv(P2, r + 2, EN);
-                    winv(P2, r, ES);
-                    winv(P0, r + 2, WN);
-                    winv(P0, r, WS);
-                    float cf[NCOEF][PPT];
-#pragma unroll
-                    for (int c = 0; c < NCOEF; ++c) {
-                        const VecT v = *reinterpret_cast<const VecT *>(CS + c * T::CTILE + r * TK + PPT * cg);
-                        const float *vf = reinterpret_cast<const float *>(&v);
-#pragma unroll
-                        for (int e = 0; e < PPT; ++e) cf[c][e] = vf[e];
-                    }
-                    const int j = j0 + r, kb = k0 + PPT * cg;
-                    const bool row_in = (j <= J - 2);
-                    float out[PPT];
-                    bool inside[PPT];
-                    bool all_in = row_in;
-#pragma unroll
-                    for (int e = 0; e < PPT; ++e) {
-                        const int k = kb + e;
-                        inside[e] = row_in && k >= 1 && k <= K - 2;
-                        all_in = all_in && inside[e];
-                        float H, L, th, tl;
-                        two_prod(cf[0][e], Ew[e + 1], H, L);                          // a0 p[i+1]
-                        two_prod(cf[1][e], Nw[e + 1], th, tl); ff_acc(H, L, th, tl);  // a1 p[j+1]
-                        two_prod(cf[2][e], Cw[e + 2], th, tl); ff_acc(H, L, th, tl);  // a2 p[k+1]
-                        ff_cross(cf[4][e], EN[e], ES[e], WN[e], WS[e], th, tl);       // b0 Xij
-                        ff_acc(H, L, th, tl);
-                        ff_cross(cf[5][e], Nw[e + 2], Sw[e + 2], Nw[e], Sw[e], th, tl);  // b1 Xjk
-                        ff_acc(H, L, th, tl);
-                        ff_cross(cf[6][e], Ew[e + 2], Ww[e + 2], Ew[e], Ww[e], th, tl);  // b2 Xik
-                        ff_acc(H, L, th, tl);
-                        two_prod(cf[7][e], Ww[e + 1], th, tl); ff_acc(H, L, th, tl);  // c0 p[i-1]
-                        two_prod(cf[8][e], Sw[e + 1], th, tl); ff_acc(H, L, th, tl);  // c1 p[j-1]
-                        two_prod(cf[9][e], Cw[e], th, tl); ff_acc(H, L, th, tl);      // c2 p[k-1]
-                        ff_acc(H, L, cf[11][e], 0.0f);                                // wrk1
-                        // ss = (s0 * a3 - p) * bnd
-                        const float pc = Cw[e + 1];
-                        float t1, dh, dl, e1, sh, s1;
-                        two_prod(H, cf[3][e], th, t1);
-                        tl = __fmaf_rn(L, cf[3][e], t1);
-                        two_sum(th, -pc, dh, e1);
-                        dl = __fadd_rn(e1, tl);
-                        two_prod(dh, cf[10][e], sh, s1);
-                        const float sl = __fmaf_rn(dl, cf[10][e], s1);
-                        // wrk2 = p + omega * ss, rounded once
-                        float wh, w1, yh, e2;
-                        two_prod(omega, sh, wh, w1);
-                        const float wl = __fmaf_rn(omega, sl, w1);
-                        two_sum(pc, wh, yh, e2);
-                        out[e] = __fadd_rn(yh, __fadd_rn(e2, wl));
-                        // ss^2 from the renormalised pair (sl can be ~1% of sh when ss
-                        // cancels deeply, so it must be folded in before squaring)
-                        float nh, nl, qh, q1;
-                        two_sum(sh, sl, nh, nl);
-                        two_prod(nh, nh, qh, q1);
-                        const float ql = __fmaf_rn(__fadd_rn(nh, nh), nl, q1);
-                        ff_acc(RH, RL, inside[e] ? qh : 0.0f, inside[e] ? ql : 0.0f);
-                    }
-                    if (row_in) {
-                        float *dst = a.wrk2 + ((size_t)i * J + j) * a.pitch + kb;
-                        if (all_in) {
-                            VecT v;
-                            float *vf = reinterpret_cast<float *>(&v);
-#pragma unroll
-                            for (int e = 0; e < PPT; ++e) vf[e] = out[e];
-                            *reinterpret_cast<VecT *>(dst) = v;
-                        } else {
-#pragma unroll
-                            for (int e = 0; e < PPT; ++e)
-                                if (inside[e]) dst[e] = out[e];
-                        }
-                    }
+                    for (int e = 0; e < PPT; ++e) cf[c][e] = vf[e];
                 }
                 __syncwarp();
                 if (lane == 0) {
+                    // all shared-memory reads of this plane are in registers
                     mbar_arrive(smem_u32(&empty_c[cuse % DC]));
                     mbar_arrive(smem_u32(&empty_p[sprev % DP]));
                 }
                 ++cuse;
+                float DNh[W], DNl[W], Fh[W], Fl[W];
+#pragma unroll
+                for (int x = 0; x < W; ++x) {
+                    two_sum(ENw[x], -ESw[x], DNh[x], DNl[x]);  // D on plane i+1
+                    two_sum(Ew[x], -Ww[x], Fh[x], Fl[x]);      // F on row j
+                }
+                float out[PPT];
+                bool inside[PPT];
+                bool all_in = row_in;
+#pragma unroll
+                for (int e = 0; e < PPT; ++e) {
+                    const int k = kb + e;
+                    inside[e] = row_in && k >= 1 && k <= K - 2;
+                    all_in = all_in && inside[e];
+                    float H, L, th, tl, xh, xl, t1;
+                    two_prod(cf[0][e], Ew[e + 1], H, L);                         // a0 p[i+1]
+                    two_prod(cf[1][e], Nc[e], th, tl); ff_acc(H, L, th, tl);     // a1 p[j+1]
+                    two_prod(cf[2][e], Cw[e + 2], th, tl); ff_acc(H, L, th, tl); // a2 p[k+1]
+                    ffsub(DNh[e + 1], DNl[e + 1], Gh[e], Gl[e], xh, xl);        // b0 Xij
+                    two_prod(cf[4][e], xh, th, t1);
+                    tl = __fmaf_rn(cf[4][e], xl, t1);
+                    ff_acc(H, L, th, tl);
+                    ffsub(Dh[e + 2], Dl[e + 2], Dh[e], Dl[e], xh, xl);          // b1 Xjk
+                    two_prod(cf[5][e], xh, th, t1);
+                    tl = __fmaf_rn(cf[5][e], xl, t1);
+                    ff_acc(H, L, th, tl);
+                    ffsub(Fh[e + 2], Fl[e + 2], Fh[e], Fl[e], xh, xl);          // b2 Xik
+                    two_prod(cf[6][e], xh, th, t1);
+                    tl = __fmaf_rn(cf[6][e], xl, t1);
+                    ff_acc(H, L, th, tl);
+                    two_prod(cf[7][e], Ww[e + 1], th, tl); ff_acc(H, L, th, tl); // c0 p[i-1]
+                    two_prod(cf[8][e], Sc[e], th, tl); ff_acc(H, L, th, tl);     // c1 p[j-1]
+                    two_prod(cf[9][e], Cw[e], th, tl); ff_acc(H, L, th, tl);     // c2 p[k-1]
+                    ff_acc(H, L, cf[11][e], 0.0f);                               // wrk1
+                    // ss = (s0 * a3 - p) * bnd
+                    const float pc = Cw[e + 1];
+                    float dh, dl, e1, sh, s1;
+                    two_prod(H, cf[3][e], th, t1);
+                    tl = __fmaf_rn(L, cf[3][e], t1);
+                    two_sum(th, -pc, dh, e1);
+                    dl = __fadd_rn(e1, tl);
+                    two_prod(dh, cf[10][e], sh, s1);
+                    const float sl = __fmaf_rn(dl, cf[10][e], s1);
+                    // wrk2 = p + omega * ss, rounded once
+                    float wh, w1, yh, e2;
+                    two_prod(omega, sh, wh, w1);
+                    const float wl = __fmaf_rn(omega, sl, w1);
+                    two_sum(pc, wh, yh, e2);
+                    out[e] = __fadd_rn(yh, __fadd_rn(e2, wl));
+                    // ss^2 from the renormalised pair: on smooth fields ss is nearly the
+                    // same at every point, so rounding it to float first would bias the
+                    // residual by up to 2^-24; sl can be ~1% of sh when ss cancels deeply
+                    float nh, nl, qh, q1;
+                    two_sum(sh, sl, nh, nl);
+                    two_prod(nh, nh, qh, q1);
+                    const float ql = __fmaf_rn(__fadd_rn(nh, nh), nl, q1);
+                    ff_acc(RH, RL, inside[e] ? qh : 0.0f, inside[e] ? ql : 0.0f);
+                }
+                if (row_in) {
+                    float *dst = a.wrk2 + ((size_t)i * J + j) * a.pitch + kb;
+                    if (all_in) {
+                        VecT v;
+                        float *vf = reinterpret_cast<float *>(&v);
+#pragma unroll
+                        for (int e = 0; e < PPT; ++e) vf[e] = out[e];
+                        *reinterpret_cast<VecT *>(dst) = v;
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < PPT; ++e)
+                            if (inside[e]) dst[e] = out[e];
+                    }
+                }
+                // march: plane i+1 becomes the centre plane
+#pragma unroll
+                for (int e = 0; e < PPT; ++e) {
+                    Gh[e] = Dh[e + 1];
+                    Gl[e] = Dl[e + 1];
+                    Nc[e] = ENw[e + 1];
+                    Sc[e] = ESw[e + 1];
+                }
+#pragma unroll
+                for (int x = 0; x < W; ++x) {
+                    Ww[x] = Cw[x];
+                    Cw[x] = Ew[x];
+                    Dh[x] = DNh[x];
+                    Dl[x] = DNl[x];
+                }
             }
             if (!ok) break;
             // release the unit's last two planes
@@ -715,7 +767,7 @@ StencilPlan *stencil_plan_create(const JacobiDims &d, const float *const coef[NC
             const int smax = (span + ns - 1) / ns;
             const long long units = (long long)cols * ns;
             const long long rounds = (units + G - 1) / G;
-            const double cost = (double)rounds * (smax + 0.15);
+            const double cost = (double)rounds * (smax + 0.6);
             if (cost < best - 1e-9) {
                 best = cost;
                 best_seg = ns;

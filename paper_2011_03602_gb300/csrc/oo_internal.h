@@ -95,6 +95,14 @@ size_t fft_scratch_bytes(const FftPlan *p, int batch);
 void launch_fft(const FftPlan *p, int batch, int dir, const double *in, double *out, void *scratch,
                 cudaStream_t s);
 
+// ------------------------------------------------------------------- GEMM
+size_t gemm_scratch_bytes(int m, int n, int k);
+// C = A B (FP64, row-major) via split BF16 tensor-core products; async on s
+void launch_gemm_split3(int m, int n, int k, const double *A, long long lda, const double *B, long long ldb,
+                        double *C, long long ldc, void *scratch, cudaStream_t s);
+// reads and clears the kernel's error word (0 = fine); synchronises s
+unsigned gemm_check_error(void *scratch, int m, int n, int k, cudaStream_t s);
+
 // Grow-only device buffer owned by a context.
 struct DevBuf {
     void *ptr = nullptr;
@@ -138,7 +146,7 @@ struct Ctx {
     std::vector<Ref> refs;
     // function blocks
     std::vector<std::pair<long long, FftPlan *>> fft_plans;
-    DevBuf fft_scratch, stage_a, stage_b, stage_c;
+    DevBuf fft_scratch, stage_a, stage_b, stage_c, gemm_scratch;
     FftPlan *fft_plan(long long n) {
         for (auto &kv : fft_plans)
             if (kv.first == n) return kv.second;

@@ -92,6 +92,11 @@ def lib():
                                    P(_u64), P(_dbl)]),
         "oo_lookup_block": (_c.c_int, [_c.c_char_p, _c.c_int, P(_c.c_int)]),
         "oo_fft_c128": (_c.c_int, [_vp, _c.c_int64, _c.c_int, _vp, _vp]),
+        "oo_gemm_f64": (_c.c_int, [_vp, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _vp, _c.c_int, _vp, _c.c_int,
+                                   _vp, _c.c_int]),
+        "oo_gemm_f64_dev": (_c.c_int, [_vp, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _vp, _c.c_int, _vp,
+                                       _c.c_int, _vp, _c.c_int]),
+        "oo_gemm_check": (_c.c_int, [_vp, _c.c_int, _c.c_int, _c.c_int]),
         "oo_fft_c128_dev": (_c.c_int, [_vp, _c.c_int64, _c.c_int, _c.c_int, _vp, _vp]),
     }
     for name, (res, args) in sig.items():
@@ -267,6 +272,32 @@ def oo_fft_c128(ctx, x, direction=-1, out=None):
         out = np.empty_like(x)
     _check(ctx, lib().oo_fft_c128(ctx, x.size, direction, x.ctypes.data_as(_vp), _host_ptr(out, np.complex128)))
     return out
+
+
+OO_PREC_SPLIT3_BF16 = 0
+
+
+def oo_gemm_f64(ctx, A, B, prec=OO_PREC_SPLIT3_BF16, out=None):
+    """Host float64 A (m x k) @ B (k x n) -> C (m x n) float64."""
+    A = np.ascontiguousarray(A, np.float64)
+    B = np.ascontiguousarray(B, np.float64)
+    m, k = A.shape
+    k2, n = B.shape
+    if k != k2:
+        raise ValueError("inner dimensions differ")
+    C = np.empty((m, n), np.float64) if out is None else out
+    _check(ctx, lib().oo_gemm_f64(ctx, prec, m, n, k, A.ctypes.data_as(_vp), k, B.ctypes.data_as(_vp), n,
+                                  _host_ptr(C, np.float64, m * n), n))
+    return C
+
+
+def oo_gemm_f64_dev(ctx, m, n, k, dA, lda, dB, ldb, dC, ldc, prec=OO_PREC_SPLIT3_BF16):
+    _check(ctx, lib().oo_gemm_f64_dev(ctx, prec, m, n, k, _dev_ptr(dA), lda, _dev_ptr(dB), ldb,
+                                      _dev_ptr(dC), ldc))
+
+
+def oo_gemm_check(ctx, m, n, k):
+    _check(ctx, lib().oo_gemm_check(ctx, m, n, k))
 
 
 def oo_fft_c128_dev(ctx, n, batch, direction, din, dout):

@@ -53,7 +53,7 @@ def test_closed_forms(oo_mod, ctx):
     X = oo_mod.oo_fft_c128(ctx, tone)
     expect = np.zeros(n, complex)
     expect[m] = n
-    assert np.max(np.abs(X - expect)) <= 1e-9
+    assert np.max(np.abs(X - expect)) <= 1e-12 * n
 
 
 @pytest.mark.parametrize("scale", [1e-200, 1e-30, 1e30, 1e200])
@@ -62,7 +62,9 @@ def test_any_finite_magnitude(oo_mod, ctx, scale):
     x = synth.complex_normal(7, n) * scale
     got = oo_mod.oo_fft_c128(ctx, x)
     ref = oracle.fft(x)
-    assert rel(got, ref) <= TOL
+    # compare in units of the scale: squares of 1e+-200 values over/underflow
+    assert np.all(np.isfinite(got))
+    assert rel(got / scale, ref / scale) <= TOL
 
 
 def test_round_trip_and_parseval(oo_mod, ctx):
