@@ -191,6 +191,28 @@ oo_status oo_stencil_dev(oo_ctx *ctx, int I, int J, int K, int pitch,
                          const float *const *coef, const float *p, float omega,
                          float *wrk2, double *res_dev);
 
+/* The same stencil sweep as oo_stencil_dev, for callers that cannot
+ * allocate device memory at the time they call: for example code being
+ * captured into a CUDA graph (cudaMalloc is not a capturable stream
+ * operation), serving loops that draw on a fixed, pre-reserved memory pool,
+ * or language runtimes that own every device allocation.  The paper has no
+ * counterpart; this is a deployment variant of the same nest.
+ * It calls no cudaMalloc, cudaFree or allocating library routine: its
+ * scratch (per-warp partial residuals, a completion counter, an error word)
+ * lives in one static device array of 512 KB + 256 B that every device
+ * loading the library holds until the process exits.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress) with
+ * the device current; make that first call before any stream capture.
+ * Every call shares the array and clears its counter and error word first,
+ * so calls that overlap on the GPU (other streams, other contexts on the
+ * same device) race and must not be issued.  Grids needing more than 65536
+ * partial slots (ceil((K-1)/128) * ceil((J-2)/8) > 8192 for K > 65) are
+ * rejected with OO_EINVAL.  Arguments, layout and results as for
+ * oo_stencil_dev; asynchronous on the context's stream.                  */
+oo_status oo_stencil_noalloc_dev(oo_ctx *ctx, int I, int J, int K, int pitch,
+                                 const float *const *coef, const float *p, float omega,
+                                 float *wrk2, double *res_dev);
+
 /* Device row pitch (floats) the library uses for a row of K floats. */
 int oo_jacobi_pitch(int K);
 

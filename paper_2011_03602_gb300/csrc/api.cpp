@@ -15,6 +15,10 @@ struct oo_ctx {
     std::vector<const void *> user_key;
 };
 
+namespace oo {
+Ctx &ctx_state(oo_ctx *ctx) { return ctx->c; }
+}  // namespace oo
+
 namespace {
 
 thread_local std::string g_last_error;

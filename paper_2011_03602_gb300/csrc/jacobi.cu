@@ -812,4 +812,107 @@ unsigned stencil_plan_check(StencilPlan *sp, cudaStream_t s) {
     return e;
 }
 
+// ======================================= allocation-free stencil entry point
+// Some callers cannot allocate device memory when they call in: a host that
+// is capturing its work into a CUDA graph (cudaMalloc is not a stream
+// operation and is not allowed inside a capture), a serving loop with a
+// fixed device-memory budget handed out by its own pool, or a language
+// runtime that owns every allocation on the device.  For them the stencil
+// sweep below keeps its scratch (per-warp partial residuals, the CTA-done
+// counter and the error word) in one static device array instead of
+// cudaMalloc'd memory.  The caller still passes every input and output.
+namespace {
+
+constexpr int kStaticPartials = 65536;  // doubles: 512 KB of partial residuals
+constexpr size_t kStaticScratchBytes = (size_t)kStaticPartials * 8 + 256;
+constexpr int kMaxDevices = 64;
+
+// Held by every device that loads the library until the process exits.  In
+// host code this name is only a stand-in for the device symbol: its device
+// address is looked up with cudaGetSymbolAddress per device below.
+static __device__ __align__(256) unsigned char g_stencil_scratch[kStaticScratchBytes];
+
+void *static_scratch_ptr(int device) {
+    static void *addr[kMaxDevices] = {nullptr};
+    OO_REQUIRE(device >= 0 && device < kMaxDevices, OO_EINVAL, "device index beyond the static table");
+    if (!addr[device]) {
+        void *p = nullptr;
+        OO_CUDA_TRY(cudaGetSymbolAddress(&p, g_stencil_scratch));
+        addr[device] = p;
+    }
+    return addr[device];
+}
+
+}  // namespace
+
 }  // namespace oo
+
+extern "C" oo_status oo_stencil_noalloc_dev(oo_ctx *ctx, int I, int J, int K, int pitch,
+                                            const float *const *coef, const float *p, float omega,
+                                            float *wrk2, double *res_dev) {
+    using namespace oo;
+    if (!ctx) return OO_EINVAL;
+    Ctx &c = ctx_state(ctx);
+    try {
+        OO_REQUIRE(c.device >= 0, OO_ESTATE, "host-only context (device -1) cannot run GPU work");
+        OO_REQUIRE(coef && p && wrk2 && res_dev, OO_EINVAL, "null pointer");
+        for (int a = 0; a < NCOEF; ++a) OO_REQUIRE(coef[a] != nullptr, OO_EINVAL, "null coefficient array");
+        OO_REQUIRE(I >= 3 && J >= 3 && K >= 3 && K <= 4096, OO_EINVAL, "bad grid");
+        OO_REQUIRE(pitch >= K && pitch % 4 == 0, OO_EINVAL, "pitch must be >= K and a multiple of 4");
+        OO_REQUIRE(((uintptr_t)wrk2 & 15u) == 0, OO_EINVAL, "wrk2 must be 16-byte aligned");
+        OO_REQUIRE(std::isfinite(omega), OO_EINVAL, "omega must be finite");
+        OO_CUDA_TRY(cudaSetDevice(c.device));
+        const JacobiDims d{I, J, K, pitch};
+        const int v = d.K - 1 > 64 ? 0 : 4;
+        const VariantInfo &vi = variant(v);
+        const int ncw = 8;  // consumer warps per CTA in variants 0 and 4
+        StencilMaps maps;
+        for (int a = 0; a < NCOEF; ++a) make_map(&maps.coef[a], coef[a], d, vi.TK, vi.TJ);
+        make_map(&maps.p, p, d, vi.TK + 8, vi.TJ + 2);
+        StencilArgs sa{};
+        sa.I = I;
+        sa.J = J;
+        sa.K = K;
+        sa.pitch = pitch;
+        sa.n_kt = (K - 1 + vi.TK - 1) / vi.TK;
+        sa.n_jt = (J - 2 + vi.TJ - 1) / vi.TJ;
+        const long long cols = (long long)sa.n_kt * sa.n_jt;
+        OO_REQUIRE(cols * ncw <= kStaticPartials, OO_EINVAL,
+                   "grid too large for the static scratch: ceil((K-1)/tile_k) * ceil((J-2)/8) * 8 must be <= 65536");
+        const int span = I - 2;
+        const int G = std::max(1, c.num_sms * vi.ctas_per_sm);
+        double best = 1e300;
+        int best_seg = 1;
+        for (int ns = 1; ns <= span; ++ns) {
+            if (cols * ns * ncw > kStaticPartials) break;
+            const int smax = (span + ns - 1) / ns;
+            const long long rounds = (cols * ns + G - 1) / G;
+            const double cost = (double)rounds * (smax + 0.6);
+            if (cost < best - 1e-9) {
+                best = cost;
+                best_seg = ns;
+            }
+        }
+        sa.n_seg = best_seg;
+        sa.n_units = (int)(cols * best_seg);
+        sa.omega = omega;
+        sa.wrk2 = wrk2;
+        sa.res = res_dev;
+        char *scratch = static_cast<char *>(static_scratch_ptr(c.device));
+        sa.partials = reinterpret_cast<double *>(scratch);
+        sa.counter = reinterpret_cast<unsigned *>(scratch + (size_t)kStaticPartials * 8);
+        sa.err = sa.counter + 1;
+        // the array keeps the previous call's contents: the CTA counter and
+        // the error word must start at zero
+        OO_CUDA_TRY(cudaMemsetAsync(sa.counter, 0, 8, c.stream));
+        vi.launch(std::min(sa.n_units, G), maps, sa, c.stream);
+        c.last_error.clear();
+        return OO_OK;
+    } catch (const Error &e) {
+        c.last_error = e.msg;
+        return e.code;
+    } catch (...) {
+        c.last_error = "unknown failure";
+        return OO_ECUDA;
+    }
+}

@@ -156,6 +156,9 @@ struct Ctx {
     }
 };
 
+// The library state behind a C-ABI context handle (api.cpp).
+Ctx &ctx_state(oo_ctx *ctx);
+
 // Kernel launchers (jacobi.cu).  All asynchronous on `s`.
 void launch_coef(const JacobiDims &d, float *const coef[NCOEF], cudaStream_t s);
 void launch_pinit(const JacobiDims &d, float *p, float *wrk2, cudaStream_t s);

@@ -85,6 +85,8 @@ def lib():
         "oo_run_pattern_dev": (_c.c_int, [_vp, _u64, _c.c_int, P(oo_jacobi), _vp, _vp, P(oo_run_stats)]),
         "oo_stencil_dev": (_c.c_int, [_vp, _c.c_int, _c.c_int, _c.c_int, _c.c_int, P(_vp), _vp,
                                       _c.c_float, _vp, _vp]),
+        "oo_stencil_noalloc_dev": (_c.c_int, [_vp, _c.c_int, _c.c_int, _c.c_int, _c.c_int, P(_vp), _vp,
+                                              _c.c_float, _vp, _vp]),
         "oo_jacobi_pitch": (_c.c_int, [_c.c_int]),
         "oo_ga_search": (_c.c_int, [_vp, P(oo_jacobi), _c.c_int, _c.c_int, _c.c_int, _dbl, _dbl, _u64,
                                     _dbl, P(_u64), P(_dbl), _vp, _vp]),
@@ -239,6 +241,15 @@ def oo_stencil_dev(ctx, I, J, K, pitch, coef, p, omega, wrk2, res_dev):
     ptrs = (_vp * 12)(*[_dev_ptr(c).value for c in coef])
     _check(ctx, lib().oo_stencil_dev(ctx, I, J, K, pitch, ptrs, _dev_ptr(p), _c.c_float(omega),
                                      _dev_ptr(wrk2), _dev_ptr(res_dev)))
+
+
+def oo_stencil_noalloc_dev(ctx, I, J, K, pitch, coef, p, omega, wrk2, res_dev):
+    """oo_stencil_dev without any device allocation (static scratch); see oo.h."""
+    if len(coef) != 12:
+        raise ValueError("need 12 coefficient arrays")
+    ptrs = (_vp * 12)(*[_dev_ptr(c).value for c in coef])
+    _check(ctx, lib().oo_stencil_noalloc_dev(ctx, I, J, K, pitch, ptrs, _dev_ptr(p), _c.c_float(omega),
+                                             _dev_ptr(wrk2), _dev_ptr(res_dev)))
 
 
 # ---------------------------------------------------------------------- GA
