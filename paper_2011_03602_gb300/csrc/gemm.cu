@@ -33,11 +33,12 @@ namespace oo {
 
 namespace {
 
-constexpr int kBM = 128, kBN = 256, kBK = 64, kStages = 2;
+constexpr int kBM = 128, kBN = 128, kBK = 64, kStages = 3;
 constexpr int kGemmThreads = 256;
 constexpr uint32_t kTileA = kBM * kBK * 2;   // 16 KB
-constexpr uint32_t kTileB = kBN * kBK * 2;   // 32 KB
-constexpr uint32_t kStageBytes = 2 * kTileA + 2 * kTileB;  // 96 KB
+constexpr uint32_t kTileB = kBN * kBK * 2;   // 16 KB
+constexpr uint32_t kStageBytes = 2 * kTileA + 2 * kTileB;  // 64 KB
+constexpr int kGroupM = 8;                   // tile raster: groups of 8 m-tiles share B panels in L2
 constexpr long long kGemmWaitLimit = 2000000000ll;
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -49,6 +50,9 @@ __device__ __forceinline__ void bar_expect_tx(uint32_t b, uint32_t bytes) {
     asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(b),
                  "r"(bytes)
                  : "memory");
+}
+__device__ __forceinline__ void bar_arrive(uint32_t b) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(b) : "memory");
 }
 __device__ __forceinline__ bool bar_try(uint32_t b, uint32_t par) {
     uint32_t ok;
@@ -93,7 +97,7 @@ __device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr) {
     d |= (uint64_t)2 << 61;                 // 128-byte swizzle
     return d;
 }
-// Instruction descriptor, kind::f16: D=F32, A=B=BF16, both K-major, M=128, N=256
+// Instruction descriptor, kind::f16: D=F32, A=B=BF16, both K-major, M=128, N=128
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBN >> 3) << 17) |
                             ((uint32_t)(kBM >> 4) << 24);
 
@@ -136,19 +140,31 @@ struct GemmArgs {
     unsigned *err;
 };
 
+// Persistent, warp-specialised: CTA c processes tiles c, c + G, c + 2G, ...
+// (grouped raster order).  TMEM holds two accumulator buffers, each with
+// D_hh (128 columns) and D_x (128 columns), so the epilogue of one tile
+// overlaps the main loop of the next.
+__device__ __forceinline__ void tile_coords(const GemmArgs &a, int t, int &m0, int &n0) {
+    const int per_group = kGroupM * a.n_tiles;
+    const int g = t / per_group, r = t % per_group;
+    const int rows = min(kGroupM, a.m_tiles - g * kGroupM);
+    m0 = (g * kGroupM + r % rows) * kBM;
+    n0 = (r / rows) * kBN;
+}
+
 __global__ void __launch_bounds__(kGemmThreads, 1) gemm_split3_kernel(const __grid_constant__ GemmMaps maps,
                                                                      const GemmArgs a) {
     extern __shared__ __align__(1024) unsigned char gsm_raw[];
     unsigned char *gsm = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(gsm_raw) + 1023) & ~static_cast<uintptr_t>(1023));
     uint64_t *bars = reinterpret_cast<uint64_t *>(gsm + kStages * kStageBytes);
-    uint64_t *full = bars, *empty = bars + kStages, *accum = bars + 2 * kStages;
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * kStages + 1);
+    uint64_t *full = bars, *empty = bars + kStages;
+    uint64_t *tfull = bars + 2 * kStages, *tempty = bars + 2 * kStages + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * kStages + 4);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tm = blockIdx.x / a.n_tiles, tn = blockIdx.x % a.n_tiles;
-    const int m0 = tm * kBM, n0 = tn * kBN;
+    const int tiles = a.m_tiles * a.n_tiles;
     const int ksteps = a.kp / kBK;
 
     if (threadIdx.x == 0) {
@@ -156,7 +172,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_split3_kernel(const __gr
             bar_init(su32(&full[s]), 1);
             bar_init(su32(&empty[s]), 1);
         }
-        bar_init(su32(accum), 1);
+        for (int b = 0; b < 2; ++b) {
+            bar_init(su32(&tfull[b]), 1);
+            bar_init(su32(&tempty[b]), 4);  // one arrival per epilogue warp
+        }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -171,87 +190,119 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_split3_kernel(const __gr
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    const uint32_t d_hh = tmem, d_x = tmem + 256;
 
-    bool issued_any = false;
-    int loaded = 0;
+    int loaded = 0;          // producer: stages issued
+    int tiles_mma = 0;       // MMA issuer: tiles whose accumulation was issued
     if (warp == 0 && lane == 0) {
         // ---------------------------------------------------- TMA producer
-        for (int ks = 0; ks < ksteps; ++ks) {
-            const int s = ks % kStages;
-            const uint32_t use = ks / kStages;
-            if (use > 0 && !bar_wait(su32(&empty[s]), (use - 1) & 1, abort_flag, a.err, 1u)) break;
-            ++loaded;
-            unsigned char *st = gsm + (size_t)s * kStageBytes;
-            const uint32_t fb = su32(&full[s]);
-            bar_expect_tx(fb, kStageBytes);
-            const int k0 = ks * kBK;
-            tma_2d(su32(st), &maps.a1, k0, m0, fb);
-            tma_2d(su32(st + kTileA), &maps.a2, k0, m0, fb);
-            tma_2d(su32(st + 2 * kTileA), &maps.b1, k0, n0, fb);
-            tma_2d(su32(st + 2 * kTileA + kTileB), &maps.b2, k0, n0, fb);
+        int it = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; ok && t < tiles; t += gridDim.x) {
+            int m0, n0;
+            tile_coords(a, t, m0, n0);
+            for (int ks = 0; ks < ksteps; ++ks, ++it) {
+                const int s = it % kStages;
+                const uint32_t use = it / kStages;
+                if (use > 0 && !bar_wait(su32(&empty[s]), (use - 1) & 1, abort_flag, a.err, 1u)) {
+                    ok = false;
+                    break;
+                }
+                unsigned char *st = gsm + (size_t)s * kStageBytes;
+                const uint32_t fb = su32(&full[s]);
+                bar_expect_tx(fb, kStageBytes);
+                const int k0 = ks * kBK;
+                tma_2d(su32(st), &maps.a1, k0, m0, fb);
+                tma_2d(su32(st + kTileA), &maps.a2, k0, m0, fb);
+                tma_2d(su32(st + 2 * kTileA), &maps.b1, k0, n0, fb);
+                tma_2d(su32(st + 2 * kTileA + kTileB), &maps.b2, k0, n0, fb);
+                ++loaded;
+            }
         }
     } else if (warp == 1 && lane == 0) {
         // ---------------------------------------------------- MMA issuer
-        for (int ks = 0; ks < ksteps; ++ks) {
-            const int s = ks % kStages;
-            const uint32_t use = ks / kStages;
-            if (!bar_wait(su32(&full[s]), use & 1, abort_flag, a.err, 2u)) break;
+        int it = 0, lt = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; ok && t < tiles; t += gridDim.x, ++lt) {
+            const int b = lt & 1;
+            const uint32_t buse = lt >> 1;
+            if (buse > 0 && !bar_wait(su32(&tempty[b]), (buse - 1) & 1, abort_flag, a.err, 2u)) break;
             tc_fence_after();
-            const uint32_t base = su32(gsm + (size_t)s * kStageBytes);
-            const uint32_t a1 = base, a2 = base + kTileA, b1 = base + 2 * kTileA, b2 = b1 + kTileB;
+            const uint32_t d_hh = tmem + (uint32_t)(b * 256), d_x = d_hh + 128;
+            for (int ks = 0; ks < ksteps; ++ks, ++it) {
+                const int s = it % kStages;
+                const uint32_t use = it / kStages;
+                if (!bar_wait(su32(&full[s]), use & 1, abort_flag, a.err, 2u)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t base = su32(gsm + (size_t)s * kStageBytes);
+                const uint32_t a1 = base, a2 = base + kTileA, b1 = base + 2 * kTileA, b2 = b1 + kTileB;
 #pragma unroll
-            for (int kk = 0; kk < kBK / 16; ++kk) {
-                const uint32_t off = kk * 32;  // 16 BF16 along K inside the 128-byte row
-                const uint32_t first = (ks == 0 && kk == 0) ? 0u : 1u;
-                mma_bf16(d_hh, sdesc_sw128(a1 + off), sdesc_sw128(b1 + off), first);
-                mma_bf16(d_x, sdesc_sw128(a1 + off), sdesc_sw128(b2 + off), first);
-                mma_bf16(d_x, sdesc_sw128(a2 + off), sdesc_sw128(b1 + off), 1u);
+                for (int kk = 0; kk < kBK / 16; ++kk) {
+                    const uint32_t off = kk * 32;  // 16 BF16 along K inside the 128-byte row
+                    const uint32_t acc = (ks == 0 && kk == 0) ? 0u : 1u;
+                    mma_bf16(d_hh, sdesc_sw128(a1 + off), sdesc_sw128(b1 + off), acc);
+                    mma_bf16(d_x, sdesc_sw128(a1 + off), sdesc_sw128(b2 + off), acc);
+                    mma_bf16(d_x, sdesc_sw128(a2 + off), sdesc_sw128(b1 + off), 1u);
+                }
+                mma_commit(su32(&empty[s]));
             }
-            mma_commit(su32(&empty[s]));
-            issued_any = true;
+            mma_commit(su32(&tfull[b]));  // accumulators of this tile complete
+            ++tiles_mma;
         }
-        if (issued_any) mma_commit(su32(accum));
     } else if (warp >= 4) {
         // ---------------------------------------------------- epilogue
         const int q = warp - 4;  // TMEM lane quarter
-        if (bar_wait(su32(accum), 0, abort_flag, a.err, 4u)) {
+        int lt = 0;
+        for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++lt) {
+            const int b = lt & 1;
+            if (!bar_wait(su32(&tfull[b]), (lt >> 1) & 1, abort_flag, a.err, 4u)) break;
             tc_fence_after();
+            int m0, n0;
+            tile_coords(a, t, m0, n0);
             const int row = m0 + q * 32 + lane;
             const bool row_ok = row < a.m;
             const int sa = row_ok ? a.ea[row] : 0;
             double *crow = a.C + (long long)row * a.ldc;
+            const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+            const uint32_t d_hh = tmem + (uint32_t)(b * 256), d_x = d_hh + 128;
             for (int c = 0; c < kBN; c += 32) {
                 uint32_t h[32], x[32];
-                const uint32_t lane_off = (uint32_t)(q * 32) << 16;
                 OO_TMEM_LD32(d_hh + lane_off + c, h);
                 OO_TMEM_LD32(d_x + lane_off + c, x);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
                 if (!row_ok) continue;
 #pragma unroll
-                for (int t = 0; t < 32; ++t) {
-                    const int col = n0 + c + t;
+                for (int t2 = 0; t2 < 32; ++t2) {
+                    const int col = n0 + c + t2;
                     if (col < a.n) {
                         // exact two-sum of the partial products, widened and scaled
                         // without the (slow) FP64 pipe
-                        const double v = ff::to_double(__uint_as_float(h[t]), __uint_as_float(x[t]));
+                        const double v = ff::to_double(__uint_as_float(h[t2]), __uint_as_float(x[t2]));
                         crow[col] = ff::scale_pow2(v, sa + a.eb[col]);
                     }
                 }
             }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) bar_arrive(su32(&tempty[b]));
         }
     }
-    // drain on abort: the accumulator barrier completes only after every
-    // issued MMA; a stage's full barrier only after its copies landed
-    if (warp == 1 && lane == 0 && issued_any && *abort_flag) {
-        const long long t0 = clock64();
-        while (!bar_try(su32(accum), 0) && clock64() - t0 < kGemmWaitLimit) {
-        }
-    }
-    if (warp == 0 && lane == 0 && *abort_flag) {
-        for (int ks = (loaded > kStages ? loaded - kStages : 0); ks < loaded; ++ks) {
+    // drain on abort: wait (bounded) for issued MMAs and copies before TMEM
+    // is released and the CTA exits
+    if (*abort_flag) {
+        if (warp == 1 && lane == 0 && tiles_mma > 0) {
+            const int lb = (tiles_mma - 1) & 1;
             const long long t0 = clock64();
-            while (!bar_try(su32(&full[ks % kStages]), (ks / kStages) & 1) && clock64() - t0 < kGemmWaitLimit) {
+            while (!bar_try(su32(&tfull[lb]), ((tiles_mma - 1) >> 1) & 1) && clock64() - t0 < kGemmWaitLimit) {
+            }
+        }
+        if (warp == 0 && lane == 0) {
+            for (int it = (loaded > kStages ? loaded - kStages : 0); it < loaded; ++it) {
+                const long long t0 = clock64();
+                while (!bar_try(su32(&full[it % kStages]), (it / kStages) & 1) && clock64() - t0 < kGemmWaitLimit) {
+                }
             }
         }
     }
@@ -264,26 +315,6 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_split3_kernel(const __gr
 }
 
 // ---------------------------------------------------------------- splitting
-// biased exponent of the largest |A[i][:]| per row (0 for an all-zero row)
-__global__ void row_maxexp_kernel(const double *A, long long lda, int m, int k, int *e) {
-    const int row = blockIdx.x;
-    if (row >= m) return;
-    const unsigned long long *p = reinterpret_cast<const unsigned long long *>(A + (long long)row * lda);
-    int mx = 0;
-    for (int l = threadIdx.x; l < k; l += blockDim.x) {
-        const int ex = (int)((p[l] >> 52) & 0x7ffu);
-        mx = max(mx, ex == 0x7ff ? 0x7fe : ex);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    __shared__ int ws[32];
-    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = mx;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = max(mx, ws[w]);
-        e[row] = mx == 0 ? 0 : mx - 1023 + 1;
-    }
-}
 // per-column maxima of B (k x n): grid.x over column blocks of 32, grid.y over k chunks
 __global__ void col_maxexp_kernel(const double *B, long long ldb, int k, int n, int rows_per, int *e) {
     const int col = blockIdx.x * 32 + threadIdx.x;
@@ -323,19 +354,40 @@ __device__ __forceinline__ void split_bf16(double x, int S, __nv_bfloat16 &hi, _
     lo = __float2bfloat16_rn(rem);
 }
 
-// A (m x k, lda) -> A1, A2 (m x kp), zero padding in [k, kp)
-__global__ void split_rows_kernel(const double *A, long long lda, int m, int k, int kp, const int *ea,
-                                  __nv_bfloat16 *A1, __nv_bfloat16 *A2) {
-    const long long total = (long long)m * kp;
-    for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < total;
-         x += (long long)gridDim.x * blockDim.x) {
-        const int row = (int)(x / kp), l = (int)(x % kp);
+// A (m x k, lda) -> per-row scale ea and A1, A2 (m x kp), zero padding in
+// [k, kp); one block per row: the second pass re-reads the row from cache
+__global__ void split_rows_fused_kernel(const double *A, long long lda, int m, int k, int kp, int *ea,
+                                        __nv_bfloat16 *A1, __nv_bfloat16 *A2) {
+    const int row = blockIdx.x;
+    if (row >= m) return;
+    const double *src = A + (long long)row * lda;
+    int mx = 0;
+    for (int l = threadIdx.x; l < k; l += blockDim.x) {
+        const int ex = (int)((__double_as_longlong(src[l]) >> 52) & 0x7ff);
+        mx = max(mx, ex == 0x7ff ? 0x7fe : ex);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    __shared__ int ws[32];
+    __shared__ int scale;
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = max(mx, ws[w]);
+        scale = mx == 0 ? 0 : mx - 1023 + 1;
+        ea[row] = scale;
+    }
+    __syncthreads();
+    const int S = scale;
+    __nv_bfloat16 *d1 = A1 + (long long)row * kp, *d2 = A2 + (long long)row * kp;
+    for (int l = threadIdx.x; l < kp; l += blockDim.x) {
         __nv_bfloat16 h = __float2bfloat16_rn(0.0f), lo = h;
-        if (l < k) split_bf16(A[(long long)row * lda + l], ea[row], h, lo);
-        A1[x] = h;
-        A2[x] = lo;
+        if (l < k) split_bf16(src[l], S, h, lo);
+        d1[l] = h;
+        d2[l] = lo;
     }
 }
+
 
 // B (k x n, ldb) -> B1t, B2t (n x kp, transposed), zero padding in [k, kp)
 __global__ void split_cols_t_kernel(const double *B, long long ldb, int k, int n, int kp, const int *eb,
@@ -409,8 +461,6 @@ void launch_gemm_split3(int m, int n, int k, const double *A, long long lda, con
     unsigned *err = reinterpret_cast<unsigned *>(eb + n);
     OO_CUDA_TRY(cudaMemsetAsync(err, 0, 4, s));
 
-    row_maxexp_kernel<<<m, 256, 0, s>>>(A, lda, m, k, ea);
-    OO_CUDA_TRY(cudaGetLastError());
     OO_CUDA_TRY(cudaMemsetAsync(eb, 0, (size_t)n * 4, s));
     {
         const int rows_per = 256;
@@ -425,9 +475,8 @@ void launch_gemm_split3(int m, int n, int k, const double *A, long long lda, con
         int dev = 0, sms = 148;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        const long long tot = (long long)m * kp;
-        split_rows_kernel<<<(int)std::min<long long>((tot + 255) / 256, (long long)sms * 16), 256, 0, s>>>(
-            A, lda, m, k, kp, ea, A1, A2);
+        (void)sms;
+        split_rows_fused_kernel<<<m, 256, 0, s>>>(A, lda, m, k, kp, ea, A1, A2);
         OO_CUDA_TRY(cudaGetLastError());
         dim3 grid((n + 31) / 32, (kp + 31) / 32), block(32, 8);
         OO_REQUIRE(grid.y <= 65535, OO_EINVAL, "k too large");
@@ -459,7 +508,11 @@ void launch_gemm_split3(int m, int n, int k, const double *A, long long lda, con
     }
     const long long tiles = (long long)ga.m_tiles * ga.n_tiles;
     OO_REQUIRE(tiles < (1ll << 31), OO_EINVAL, "too many tiles");
-    gemm_split3_kernel<<<(unsigned)tiles, kGemmThreads, smem_gemm(), s>>>(maps, ga);
+    int dev2 = 0, sms2 = 148;
+    cudaGetDevice(&dev2);
+    cudaDeviceGetAttribute(&sms2, cudaDevAttrMultiProcessorCount, dev2);
+    const int grid = (int)std::min<long long>(tiles, sms2);
+    gemm_split3_kernel<<<grid, kGemmThreads, smem_gemm(), s>>>(maps, ga);
     OO_CUDA_TRY(cudaGetLastError());
 }
 
