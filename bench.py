@@ -411,6 +411,64 @@ def run_block(args):
     return 0
 
 
+def run_batched(args):
+    """Batched uneven function blocks: 4096 split-BF16 GEMMs with m, n, k
+    log-uniform in [16, 512] and 2048 complex FFTs with lengths 2^8..2^16
+    (directions alternating), device-resident; grouped persistent kernels,
+    the same as one CUDA-graph replay, and one library call per request."""
+    import torch
+    from paper_2011_03602_gb300 import oo, synth
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    ctx = oo.oo_create(0, stream)
+    n_gemm, n_fft = args.batch_gemms, args.batch_ffts
+    dims = synth.log_uniform_int(4, 3 * n_gemm, 16, 512).reshape(n_gemm, 3)
+    expo = 8 + np.floor(synth.uniform(5, n_fft) * 9).astype(int)
+    reqs = []
+    with torch.cuda.stream(stream):
+        for i, (m, n, k) in enumerate(dims.tolist()):
+            A = torch.from_numpy(synth.gemm_matrix(100 + i, m, k)).to("cuda", non_blocking=False)
+            B = torch.from_numpy(synth.gemm_matrix(200000 + i, k, n)).to("cuda", non_blocking=False)
+            reqs.append(dict(kind="gemm", m=m, n=n, k=k, A=A, B=B,
+                             C=torch.empty((m, n), dtype=torch.float64, device="cuda")))
+        for i, e in enumerate(expo.tolist()):
+            x = synth.complex_normal(400000 + i, 1 << e)
+            reqs.append(dict(kind="fft", n=1 << e, dir=-1 if i % 2 == 0 else 1,
+                             x=torch.from_numpy(x.view(np.float64).copy()).cuda(),
+                             X=torch.empty(2 << e, dtype=torch.float64, device="cuda")))
+    torch.cuda.synchronize()
+    b = oo.oo_batch_create(ctx, reqs)
+    info = oo.oo_batch_info(b)
+    res = {}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    names = {2: "one_call_per_request", 0: "grouped_persistent", 1: "grouped_cuda_graph"}
+    for mode in (2, 0, 1):
+        for _ in range(max(args.warmup, 2)):
+            oo.oo_batch_run(ctx, b, mode)
+        oo.oo_batch_check(ctx, b)
+        e0.record(stream)
+        for _ in range(args.steps):
+            oo.oo_batch_run(ctx, b, mode)
+        e1.record(stream)
+        e1.synchronize()
+        oo.oo_batch_check(ctx, b)
+        ms = e0.elapsed_time(e1) / args.steps
+        res[names[mode]] = {"ms": round(ms, 3), "solves_per_s": round((n_gemm + n_fft) / (ms * 1e-3), 1),
+                            "gemm_fp64_equiv_tflops": round(info["gemm_flops"] / (ms * 1e-3) / 1e12, 2)}
+    oo.oo_batch_destroy(b)
+    oo.oo_destroy(ctx)
+    out = {"metric": "batched GEMM/FFT solves/s", "unit": "solves/s",
+           "value": res["grouped_cuda_graph"]["solves_per_s"], "higher_is_better": True,
+           "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
+           "config": {"workload": "batched_%dgemm_logu16-512_%dfft_2e8-2e16" % (n_gemm, n_fft),
+                      "gemm_flops_per_batch": info["gemm_flops"], "fft_points_per_batch": info["fft_points"],
+                      "precision": "split3_bf16 GEMM, float-float FFT"},
+           "modes": res,
+           "speedup_graph_vs_per_call": round(res["one_call_per_request"]["ms"] / res["grouped_cuda_graph"]["ms"], 2)}
+    print(json.dumps(out))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -421,6 +479,9 @@ def main():
     ap.add_argument("--no-blocks", action="store_true", help="skip the GEMM / FFT component timings")
     ap.add_argument("--ga", action="store_true", help="run the GA search at scale instead of the step benchmark")
     ap.add_argument("--block", choices=["gemm", "fft"], default=None, help="profiling: run one function block")
+    ap.add_argument("--batched", action="store_true", help="batched uneven GEMM/FFT configuration")
+    ap.add_argument("--batch-gemms", type=int, default=4096)
+    ap.add_argument("--batch-ffts", type=int, default=2048)
     ap.add_argument("--n", type=int, default=4096, help="profiling: GEMM size or FFT length")
     ap.add_argument("--batch", type=int, default=1, help="profiling: FFT batch")
     ap.add_argument("--ga-seed", type=int, default=2011)
@@ -443,6 +504,8 @@ def main():
         return run_ga(args)
     if args.block:
         return run_block(args)
+    if args.batched:
+        return run_batched(args)
     return run_gpu(args)
 
 

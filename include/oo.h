@@ -283,6 +283,41 @@ oo_status oo_fft_c128(oo_ctx *ctx, int64_t n, int dir, const double *in, double 
 oo_status oo_fft_c128_dev(oo_ctx *ctx, int64_t n, int batch, int dir, const double *din,
                           double *dout);
 
+/* --------------------------------------------------- batched function blocks */
+/* Many GEMM and FFT requests of uneven sizes, on caller-owned device buffers.
+ *   GEMM (kind OO_BLOCK_GEMM): C (m x n) = A (m x k) B (k x n), row-major,
+ *        contiguous (leading dimensions k, n, n); in0 = A, in1 = B, out = C;
+ *        prec as for oo_gemm_f64.
+ *   FFT  (kind OO_BLOCK_FFT): length n = 2^e (e <= 24), in0 = x, out = X
+ *        (interleaved complex128, 16-byte aligned), dir -1 / +1; m, k unused.
+ * oo_batch_create builds the grouped plan once (tensor maps, split-operand
+ * arena, tile and item lists; it allocates device memory).                */
+typedef struct {
+    int32_t kind;
+    int32_t prec;
+    int64_t m, n, k;
+    const void *in0;
+    const void *in1;
+    void *out;
+    int32_t dir;
+    int32_t pad;
+} oo_req;
+typedef struct oo_batch oo_batch;
+oo_status oo_batch_create(oo_ctx *ctx, const oo_req *reqs, int n_req, oo_batch **out);
+/* mode 0: grouped persistent kernels (GEMM split pass + one tensor-core
+ *         kernel over every tile; FFT maxima pass + two item passes), the
+ *         GEMM and FFT groups on forked streams;
+ * mode 1: the same, captured into a CUDA graph on first use and replayed;
+ * mode 2: one library call per request (oo_gemm_f64_dev / oo_fft_c128_dev).
+ * Asynchronous on the context's stream.                                  */
+oo_status oo_batch_run(oo_batch *b, int mode);
+/* Synchronise; OO_ETIMEOUT if a bounded wait in a grouped kernel ran out. */
+oo_status oo_batch_check(oo_batch *b);
+/* Totals of the batch: 2 m n k summed over GEMMs, points summed over FFTs. */
+oo_status oo_batch_info(const oo_batch *b, double *gemm_flops, double *fft_points, int *n_gemm,
+                        int *n_fft);
+void oo_batch_destroy(oo_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,0 +1,203 @@
+// Batched function blocks (Sec. 3.2.2 replacements at scale): many GEMM and
+// FFT requests of uneven sizes executed as grouped persistent kernels -- one
+// split pass and one tensor-core kernel over the tiles of every GEMM, two
+// launches over the items of every FFT -- optionally captured once into a
+// CUDA graph with the GEMM and FFT groups on forked streams, or, for
+// comparison, as one library call per request.
+#include <cstring>
+
+#include "oo_internal.h"
+
+struct oo_batch {
+    oo_ctx *ctx = nullptr;
+    oo::Ctx *c = nullptr;
+    std::vector<oo_req> reqs;
+    oo::GemmGroup *gg = nullptr;
+    oo::FftGroup *fg = nullptr;
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    bool warmed = false;
+};
+
+namespace {
+
+using namespace oo;
+
+void free_batch(oo_batch *b) {
+    if (!b) return;
+    if (b->c && b->c->stream) cudaStreamSynchronize(b->c->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->join) cudaEventDestroy(b->join);
+    if (b->side) cudaStreamDestroy(b->side);
+    gemm_group_destroy(b->gg);
+    fft_group_destroy(b->fg);
+    delete b;
+}
+
+// the grouped launches; GEMMs on the context stream, FFTs on a forked stream
+void launch_grouped(oo_batch *b) {
+    cudaStream_t s = b->c->stream;
+    if (b->gg && b->fg) {
+        OO_CUDA_TRY(cudaEventRecord(b->fork, s));
+        OO_CUDA_TRY(cudaStreamWaitEvent(b->side, b->fork, 0));
+        gemm_group_launch(b->gg, s);
+        fft_group_launch(b->fg, b->side);
+        OO_CUDA_TRY(cudaEventRecord(b->join, b->side));
+        OO_CUDA_TRY(cudaStreamWaitEvent(s, b->join, 0));
+    } else if (b->gg) {
+        gemm_group_launch(b->gg, s);
+    } else if (b->fg) {
+        fft_group_launch(b->fg, s);
+    }
+}
+
+template <class F>
+oo_status guard(oo_batch *b, F &&f) {
+    try {
+        f();
+        if (b && b->c) b->c->last_error.clear();
+        return OO_OK;
+    } catch (const Error &e) {
+        if (b && b->c) b->c->last_error = e.msg;
+        return e.code;
+    } catch (const std::bad_alloc &) {
+        return OO_ENOMEM;
+    } catch (...) {
+        return OO_ECUDA;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+oo_status oo_batch_create(oo_ctx *ctx, const oo_req *reqs, int n_req, oo_batch **out) {
+    if (!ctx || !out || !reqs || n_req < 1) return OO_EINVAL;
+    *out = nullptr;
+    auto *b = new (std::nothrow) oo_batch();
+    if (!b) return OO_ENOMEM;
+    b->ctx = ctx;
+    b->c = &ctx_state(ctx);
+    const oo_status st = guard(b, [&] {
+        Ctx &c = *b->c;
+        OO_REQUIRE(c.device >= 0, OO_ESTATE, "host-only context (device -1) cannot run GPU work");
+        OO_CUDA_TRY(cudaSetDevice(c.device));
+        b->reqs.assign(reqs, reqs + n_req);
+        std::vector<GemmDesc> gd;
+        std::vector<FftDesc> fd;
+        std::vector<const FftPlan *> fp;
+        for (int i = 0; i < n_req; ++i) {
+            const oo_req &r = reqs[i];
+            if (r.kind == OO_BLOCK_GEMM) {
+                OO_REQUIRE(r.prec == OO_PREC_SPLIT3_BF16, OO_EINVAL, "unsupported precision pattern");
+                OO_REQUIRE(r.m >= 1 && r.n >= 1 && r.k >= 1 && r.m <= (1 << 20) && r.n <= (1 << 20) &&
+                               r.k <= (1 << 21),
+                           OO_EINVAL, "bad GEMM dimensions in request " + std::to_string(i));
+                OO_REQUIRE(r.in0 && r.in1 && r.out, OO_EINVAL, "null pointer in request " + std::to_string(i));
+                gd.push_back(GemmDesc{(int)r.m, (int)r.n, (int)r.k, static_cast<const double *>(r.in0), r.k,
+                                      static_cast<const double *>(r.in1), r.n, static_cast<double *>(r.out), r.n});
+            } else if (r.kind == OO_BLOCK_FFT) {
+                OO_REQUIRE(r.in0 && r.out, OO_EINVAL, "null pointer in request " + std::to_string(i));
+                fp.push_back(c.fft_plan(r.n));
+                fd.push_back(FftDesc{r.n, r.dir, static_cast<const double *>(r.in0), static_cast<double *>(r.out)});
+            } else {
+                throw Error{OO_EINVAL, "unknown request kind in request " + std::to_string(i)};
+            }
+        }
+        if (!gd.empty()) b->gg = gemm_group_create(gd, c.num_sms);
+        if (!fd.empty()) b->fg = fft_group_create(fd, fp, c.num_sms);
+        OO_CUDA_TRY(cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking));
+        OO_CUDA_TRY(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
+        OO_CUDA_TRY(cudaEventCreateWithFlags(&b->join, cudaEventDisableTiming));
+    });
+    if (st != OO_OK) {
+        free_batch(b);
+        return st;
+    }
+    *out = b;
+    return OO_OK;
+}
+
+oo_status oo_batch_run(oo_batch *b, int mode) {
+    if (!b) return OO_EINVAL;
+    return guard(b, [&] {
+        Ctx &c = *b->c;
+        OO_CUDA_TRY(cudaSetDevice(c.device));
+        cudaStream_t s = c.stream;
+        if (mode == 0) {
+            launch_grouped(b);
+            b->warmed = true;
+        } else if (mode == 1) {
+            if (!b->exec) {
+                if (!b->warmed) {  // first launches set kernel attributes outside any capture
+                    launch_grouped(b);
+                    b->warmed = true;
+                }
+                OO_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+                try {
+                    launch_grouped(b);
+                } catch (...) {
+                    cudaGraph_t g = nullptr;
+                    cudaStreamEndCapture(s, &g);
+                    if (g) cudaGraphDestroy(g);
+                    throw;
+                }
+                OO_CUDA_TRY(cudaStreamEndCapture(s, &b->graph));
+                OO_CUDA_TRY(cudaGraphInstantiate(&b->exec, b->graph, 0));
+            }
+            OO_CUDA_TRY(cudaGraphLaunch(b->exec, s));
+        } else if (mode == 2) {
+            for (const oo_req &r : b->reqs) {
+                if (r.kind == OO_BLOCK_GEMM) {
+                    const oo_status st = oo_gemm_f64_dev(b->ctx, r.prec, (int)r.m, (int)r.n, (int)r.k,
+                                                         static_cast<const double *>(r.in0), (int)r.k,
+                                                         static_cast<const double *>(r.in1), (int)r.n,
+                                                         static_cast<double *>(r.out), (int)r.n);
+                    OO_REQUIRE(st == OO_OK, st, "per-call GEMM failed: " + c.last_error);
+                } else {
+                    const oo_status st = oo_fft_c128_dev(b->ctx, r.n, 1, r.dir, static_cast<const double *>(r.in0),
+                                                         static_cast<double *>(r.out));
+                    OO_REQUIRE(st == OO_OK, st, "per-call FFT failed: " + c.last_error);
+                }
+            }
+        } else {
+            throw Error{OO_EINVAL, "mode must be 0 (grouped), 1 (grouped, CUDA graph) or 2 (one call per request)"};
+        }
+    });
+}
+
+oo_status oo_batch_check(oo_batch *b) {
+    if (!b) return OO_EINVAL;
+    return guard(b, [&] {
+        OO_CUDA_TRY(cudaSetDevice(b->c->device));
+        OO_CUDA_TRY(cudaStreamSynchronize(b->c->stream));
+        if (b->gg) {
+            const unsigned e = gemm_group_check(b->gg, b->c->stream);
+            OO_REQUIRE(e == 0, OO_ETIMEOUT, "grouped GEMM pipeline wait ran out (error bits " + std::to_string(e) + ")");
+        }
+        OO_CUDA_TRY(cudaGetLastError());
+    });
+}
+
+oo_status oo_batch_info(const oo_batch *b, double *gemm_flops, double *fft_points, int *n_gemm, int *n_fft) {
+    if (!b) return OO_EINVAL;
+    int ng = 0, nf = 0;
+    for (const oo_req &r : b->reqs) (r.kind == OO_BLOCK_GEMM ? ng : nf)++;
+    if (gemm_flops) *gemm_flops = b->gg ? gemm_group_flops(b->gg) : 0.0;
+    if (fft_points) *fft_points = b->fg ? fft_group_elements(b->fg) : 0.0;
+    if (n_gemm) *n_gemm = ng;
+    if (n_fft) *n_fft = nf;
+    return OO_OK;
+}
+
+void oo_batch_destroy(oo_batch *b) {
+    if (!b) return;
+    if (b->c && b->c->device >= 0) cudaSetDevice(b->c->device);
+    free_batch(b);
+}
+
+}  // extern "C"

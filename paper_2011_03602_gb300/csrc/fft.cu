@@ -18,7 +18,9 @@
 // by W_N^{k1 n2} (two-level twiddle table), writing float-float
 // intermediates; pass 2 does N1 row FFTs of length N2 and writes X[k1 + N1 k2]
 // as doubles.
+#include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "ff.cuh"
 #include "oo_internal.h"
@@ -283,6 +285,116 @@ __global__ void fft_twiddle_kernel(float4 *table, int count, long long stride, i
     }
 }
 
+// ------------------------------------------------- grouped transforms
+// A CTA's worth of work in a batch of transforms of different lengths:
+// mode 0: `count` whole transforms of length 2^log2L (request ids at
+// tlist[first ..]); mode 1 / 2: the four-step column / row pass of request
+// `first` starting at column / row c0.
+struct FftItem {
+    int mode, log2L, first, count, c0, pad0, pad1, pad2;
+};
+struct FftGroupReq {
+    const double *in;
+    double *out;
+    float4 *mid;
+    const float4 *tw, *tw_n1, *tw_n2, *tw_hi, *tw_lo;
+    int log2n, log2n1, log2n2, inverse;
+};
+
+__global__ void fft_maxexp_group_kernel(const FftGroupReq *reqs, int *expo) {
+    const int r = blockIdx.y;
+    const long long cnt = 2ll << reqs[r].log2n;
+    const unsigned long long *p = reinterpret_cast<const unsigned long long *>(reqs[r].in);
+    int m = 0;
+    for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < cnt; x += (long long)gridDim.x * blockDim.x) {
+        const int e = (int)((p[x] >> 52) & 0x7ffu);
+        m = max(m, e == 0x7ff ? 0x7fe : e);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(expo + r, m);
+}
+
+__device__ __forceinline__ int scale_from(int e) { return e == 0 ? 0 : e - 1023 + 1; }
+
+__global__ void __launch_bounds__(kFftThreads, 1)
+    fft_group_kernel(const FftItem *items, int nitems, const FftGroupReq *reqs, const int *tlist, const int *expo) {
+    extern __shared__ __align__(16) float4 fsmem[];
+    float4 *sd = fsmem;
+    float4 *stw = fsmem + kFftElems;
+    for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        const FftItem item = items[it];
+        const int log2L = item.log2L, L = 1 << log2L;
+        const int C = kFftElems >> log2L;
+        const FftGroupReq &R0 = reqs[item.mode == 0 ? tlist[item.first] : item.first];
+        const float4 *tw = item.mode == 0 ? R0.tw : (item.mode == 1 ? R0.tw_n1 : R0.tw_n2);
+        const bool inv = R0.inverse != 0;
+        __syncthreads();  // previous item's shared-memory reads are done
+        for (int t = threadIdx.x; t < L; t += kFftThreads) stw[t] = tw[t];
+        const int N1 = 1 << R0.log2n1, N2 = 1 << R0.log2n2;
+        // ---- load
+        for (int q = threadIdx.x; q < kFftElems; q += kFftThreads) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            int c, t;
+            if (item.mode == 1) {
+                c = q & (C - 1);
+                t = q >> (31 - __clz(C));
+            } else {
+                c = q >> log2L;
+                t = q & (L - 1);
+            }
+            if (item.mode == 0) {
+                if (c < item.count) {
+                    const int r = tlist[item.first + c];
+                    const double2 x = reinterpret_cast<const double2 *>(reqs[r].in)[t];
+                    const int S = scale_from(expo[r]);
+                    split_scaled(x.x, S, v.x, v.y);
+                    split_scaled(x.y, S, v.z, v.w);
+                }
+            } else if (item.mode == 1) {
+                const int S = scale_from(expo[item.first]);
+                const double2 x = reinterpret_cast<const double2 *>(R0.in)[(long long)t * N2 + item.c0 + c];
+                split_scaled(x.x, S, v.x, v.y);
+                split_scaled(x.y, S, v.z, v.w);
+            } else {
+                v = R0.mid[(long long)(item.c0 + c) * N2 + t];
+            }
+            sd[(c << log2L) + t] = v;
+        }
+        __syncthreads();
+        fft_in_smem(sd, stw, log2L, inv);
+        // ---- store
+        for (int q = threadIdx.x; q < kFftElems; q += kFftThreads) {
+            int c, t;
+            if (item.mode == 0) {
+                c = q >> log2L;
+                t = q & (L - 1);
+            } else {
+                c = q & (C - 1);
+                t = q >> (31 - __clz(C));
+            }
+            cplx v = ld_cplx(sd + (c << log2L) + t);
+            if (item.mode == 1) {
+                const long long m = (long long)t * (item.c0 + c);
+                const int mh = (int)(m >> kTwSplit), ml = (int)(m & ((1 << kTwSplit) - 1));
+                cplx w = ff::cmul(ld_cplx(R0.tw_hi + mh), ld_cplx(R0.tw_lo + ml));
+                if (inv) w = ff::conj(w);
+                st_cplx(R0.mid + (long long)t * N2 + item.c0 + c, ff::cmul(v, w));
+            } else if (item.mode == 0) {
+                if (c >= item.count) continue;
+                const int r = tlist[item.first + c];
+                const int S = scale_from(expo[r]) - (inv ? log2L : 0);
+                reinterpret_cast<double2 *>(reqs[r].out)[t] =
+                    make_double2(widen_scaled(v.rh, v.rl, S), widen_scaled(v.ih, v.il, S));
+            } else {
+                const int S = scale_from(expo[item.first]) - (inv ? R0.log2n : 0);
+                reinterpret_cast<double2 *>(R0.out)[(item.c0 + c) + (long long)N1 * t] =
+                    make_double2(widen_scaled(v.rh, v.rl, S), widen_scaled(v.ih, v.il, S));
+            }
+        }
+    }
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ plans
@@ -364,8 +476,10 @@ void launch_fft(const FftPlan *p, int batch, int dir, const double *in, double *
                                         (four_step ? (size_t)n * batch * sizeof(float4) : 0));
     OO_CUDA_TRY(cudaMemsetAsync(expo, 0, (size_t)batch * sizeof(int), s));
     {
+        // enough blocks to stream the input at full bandwidth: ~8 doubles per thread
         const long long per = 2 * n;
-        const int bx = (int)std::min<long long>(64, (per + 255) / 256);
+        const int bx = (int)std::max<long long>(1, std::min<long long>(4096 / std::max(1, batch) + 1,
+                                                                         (per + 2047) / 2048));
         OO_REQUIRE(batch <= 65535, OO_EINVAL, "batch above 65535");
         fft_maxexp_kernel<<<dim3(bx, batch), 256, 0, s>>>(in, n, expo);
         OO_CUDA_TRY(cudaGetLastError());
@@ -425,6 +539,139 @@ void launch_fft(const FftPlan *p, int batch, int dir, const double *in, double *
         fft_pass_kernel<2><<<(unsigned)grid, kFftThreads, smem, s>>>(a);
         OO_CUDA_TRY(cudaGetLastError());
     }
+}
+
+// ------------------------------------------------------------ group plans
+struct FftGroup {
+    void *arena = nullptr;
+    FftItem *d_items = nullptr;
+    FftGroupReq *d_reqs = nullptr;
+    int *d_tlist = nullptr, *d_expo = nullptr;
+    int n_items_a = 0, n_items_b = 0, nreq = 0, grid_a = 1, grid_b = 1, maxexp_x = 1;
+    double elems = 0;
+};
+
+FftGroup *fft_group_create(const std::vector<FftDesc> &v, const std::vector<const FftPlan *> &plans, int num_sms) {
+    OO_REQUIRE(!v.empty() && v.size() == plans.size(), OO_EINVAL, "empty FFT group");
+    OO_REQUIRE(v.size() <= 65535, OO_EINVAL, "at most 65535 transforms in a group");
+    auto up = [](size_t x, size_t a) { return (x + a - 1) / a * a; };
+    size_t at = 0;
+    std::vector<size_t> off_mid(v.size(), 0);
+    long long maxn = 1;
+    for (size_t i = 0; i < v.size(); ++i) {
+        OO_REQUIRE(v[i].dir == -1 || v[i].dir == 1, OO_EINVAL, "dir must be -1 or +1");
+        OO_REQUIRE((((uintptr_t)v[i].in) & 15u) == 0 && (((uintptr_t)v[i].out) & 15u) == 0, OO_EINVAL,
+                   "FFT buffers must be 16-byte aligned");
+        maxn = std::max(maxn, 1ll << plans[i]->log2n);
+        if (plans[i]->log2n > 12) {
+            off_mid[i] = at;
+            at += up(((size_t)1 << plans[i]->log2n) * sizeof(float4), 256);
+        }
+    }
+    // items: whole transforms grouped by (length, direction); then the passes
+    std::vector<FftItem> items_a, items_b;
+    std::vector<int> tlist;
+    std::vector<std::pair<std::pair<int, int>, int>> small;
+    for (size_t i = 0; i < v.size(); ++i)
+        if (plans[i]->log2n <= 12) small.push_back({{plans[i]->log2n, v[i].dir}, (int)i});
+    std::stable_sort(small.begin(), small.end(),
+                     [](const std::pair<std::pair<int, int>, int> &x, const std::pair<std::pair<int, int>, int> &y) {
+                         return x.first < y.first;
+                     });
+    for (size_t a = 0; a < small.size();) {
+        size_t b = a;
+        while (b < small.size() && small[b].first == small[a].first) ++b;
+        const int log2L = small[a].first.first, C = kFftElems >> log2L;
+        for (size_t c = a; c < b; c += C) {
+            const int cnt = (int)std::min<size_t>(C, b - c);
+            items_a.push_back(FftItem{0, log2L, (int)tlist.size(), cnt, 0, 0, 0, 0});
+            for (int x = 0; x < cnt; ++x) tlist.push_back(small[c + x].second);
+        }
+        a = b;
+    }
+    for (size_t i = 0; i < v.size(); ++i) {
+        const FftPlan *p = plans[i];
+        if (p->log2n <= 12) continue;
+        const int N1 = 1 << p->log2n1, N2 = 1 << p->log2n2;
+        const int C1 = kFftElems / N1, C2 = kFftElems / N2;
+        for (int c0 = 0; c0 < N2; c0 += C1) items_a.push_back(FftItem{1, p->log2n1, (int)i, 0, c0, 0, 0, 0});
+        for (int r0 = 0; r0 < N1; r0 += C2) items_b.push_back(FftItem{2, p->log2n2, (int)i, 0, r0, 0, 0, 0});
+    }
+    at = up(at, 256);
+    const size_t off_items = at; at += up((items_a.size() + items_b.size()) * sizeof(FftItem), 256);
+    const size_t off_reqs = at; at += up(v.size() * sizeof(FftGroupReq), 256);
+    const size_t off_tlist = at; at += up(std::max<size_t>(tlist.size(), 1) * 4, 256);
+    const size_t off_expo = at; at += up(v.size() * 4, 256);
+    auto *g = new FftGroup();
+    try {
+        if (cudaMalloc(&g->arena, at) != cudaSuccess) {
+            cudaGetLastError();
+            throw Error{OO_ENOMEM, "FFT group arena of " + std::to_string(at) + " bytes"};
+        }
+        char *base = static_cast<char *>(g->arena);
+        std::vector<FftGroupReq> reqs(v.size());
+        double elems = 0;
+        for (size_t i = 0; i < v.size(); ++i) {
+            const FftPlan *p = plans[i];
+            reqs[i] = FftGroupReq{v[i].in, v[i].out,
+                                  p->log2n > 12 ? reinterpret_cast<float4 *>(base + off_mid[i]) : nullptr,
+                                  p->tw_single, p->tw_n1, p->tw_n2, p->tw_hi, p->tw_lo,
+                                  p->log2n, p->log2n1, p->log2n2, v[i].dir > 0 ? 1 : 0};
+            elems += (double)(1ll << p->log2n);
+        }
+        std::vector<FftItem> all(items_a);
+        all.insert(all.end(), items_b.begin(), items_b.end());
+        OO_CUDA_TRY(cudaMemcpy(base + off_items, all.data(), all.size() * sizeof(FftItem), cudaMemcpyHostToDevice));
+        OO_CUDA_TRY(cudaMemcpy(base + off_reqs, reqs.data(), reqs.size() * sizeof(FftGroupReq), cudaMemcpyHostToDevice));
+        if (!tlist.empty())
+            OO_CUDA_TRY(cudaMemcpy(base + off_tlist, tlist.data(), tlist.size() * 4, cudaMemcpyHostToDevice));
+        g->d_items = reinterpret_cast<FftItem *>(base + off_items);
+        g->d_reqs = reinterpret_cast<FftGroupReq *>(base + off_reqs);
+        g->d_tlist = reinterpret_cast<int *>(base + off_tlist);
+        g->d_expo = reinterpret_cast<int *>(base + off_expo);
+        g->n_items_a = (int)items_a.size();
+        g->n_items_b = (int)items_b.size();
+        g->nreq = (int)v.size();
+        g->grid_a = std::max(1, std::min(g->n_items_a, num_sms));
+        g->grid_b = std::max(1, std::min(g->n_items_b, num_sms));
+        g->maxexp_x = (int)std::max<long long>(1, std::min<long long>(16, (2 * maxn + 8191) / 8192));
+        g->elems = elems;
+    } catch (...) {
+        if (g->arena) cudaFree(g->arena);
+        delete g;
+        throw;
+    }
+    return g;
+}
+
+void fft_group_launch(FftGroup *g, cudaStream_t s) {
+    OO_CUDA_TRY(cudaMemsetAsync(g->d_expo, 0, (size_t)g->nreq * 4, s));
+    fft_maxexp_group_kernel<<<dim3(g->maxexp_x, g->nreq), 256, 0, s>>>(g->d_reqs, g->d_expo);
+    OO_CUDA_TRY(cudaGetLastError());
+    const size_t smem = (size_t)(kFftElems + 4096) * sizeof(float4);
+    static bool attr = false;
+    if (!attr) {
+        OO_CUDA_TRY(cudaFuncSetAttribute(fft_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr = true;
+    }
+    if (g->n_items_a > 0) {
+        fft_group_kernel<<<g->grid_a, kFftThreads, smem, s>>>(g->d_items, g->n_items_a, g->d_reqs, g->d_tlist,
+                                                               g->d_expo);
+        OO_CUDA_TRY(cudaGetLastError());
+    }
+    if (g->n_items_b > 0) {
+        fft_group_kernel<<<g->grid_b, kFftThreads, smem, s>>>(g->d_items + g->n_items_a, g->n_items_b, g->d_reqs,
+                                                               g->d_tlist, g->d_expo);
+        OO_CUDA_TRY(cudaGetLastError());
+    }
+}
+
+double fft_group_elements(const FftGroup *g) { return g->elems; }
+
+void fft_group_destroy(FftGroup *g) {
+    if (!g) return;
+    if (g->arena) cudaFree(g->arena);
+    delete g;
 }
 
 }  // namespace oo

@@ -25,6 +25,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstring>
 
 #include "ff.cuh"
 #include "oo_internal.h"
@@ -152,8 +153,52 @@ __device__ __forceinline__ void tile_coords(const GemmArgs &a, int t, int &m0, i
     n0 = (r / rows) * kBN;
 }
 
-__global__ void __launch_bounds__(kGemmThreads, 1) gemm_split3_kernel(const __grid_constant__ GemmMaps maps,
-                                                                     const GemmArgs a) {
+// One output tile: where its operands and outputs are.
+struct TileJob {
+    const CUtensorMap *a1, *a2, *b1, *b2;
+    double *C;
+    long long ldc;
+    const int *ea, *eb;
+    int m, n, m0, n0, ksteps;
+};
+
+// Single problem: tensor maps are kernel parameters, tiles in grouped raster order.
+struct SingleSrc {
+    const GemmMaps *maps;
+    const GemmArgs *a;
+    __device__ __forceinline__ int count() const { return a->m_tiles * a->n_tiles; }
+    __device__ __forceinline__ TileJob job(int t) const {
+        int m0, n0;
+        tile_coords(*a, t, m0, n0);
+        return TileJob{&maps->a1, &maps->a2, &maps->b1, &maps->b2, a->C, a->ldc, a->ea, a->eb,
+                       a->m, a->n, m0, n0, a->kp / kBK};
+    }
+};
+
+// Many problems: each has its own tensor maps in global memory; the tile
+// list (problem, m0, n0, k steps) is sorted by work so the round-robin
+// assignment to persistent CTAs stays balanced.
+struct alignas(128) GroupProblem {
+    CUtensorMap a1, a2, b1, b2;
+    double *C;
+    long long ldc;
+    const int *ea, *eb;
+    int m, n, k, kp;
+};
+struct GroupSrc {
+    const GroupProblem *probs;
+    const int4 *tiles;
+    int ntiles;
+    __device__ __forceinline__ int count() const { return ntiles; }
+    __device__ __forceinline__ TileJob job(int t) const {
+        const int4 td = tiles[t];
+        const GroupProblem &P = probs[td.x];
+        return TileJob{&P.a1, &P.a2, &P.b1, &P.b2, P.C, P.ldc, P.ea, P.eb, P.m, P.n, td.y, td.z, td.w};
+    }
+};
+
+template <class Src>
+__device__ __forceinline__ void gemm_body(const Src &src, unsigned *err) {
     extern __shared__ __align__(1024) unsigned char gsm_raw[];
     unsigned char *gsm = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(gsm_raw) + 1023) & ~static_cast<uintptr_t>(1023));
@@ -164,8 +209,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_split3_kernel(const __gr
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tiles = a.m_tiles * a.n_tiles;
-    const int ksteps = a.kp / kBK;
+    const int tiles = src.count();
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -198,12 +242,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_split3_kernel(const __gr
         int it = 0;
         bool ok = true;
         for (int t = blockIdx.x; ok && t < tiles; t += gridDim.x) {
-            int m0, n0;
-            tile_coords(a, t, m0, n0);
-            for (int ks = 0; ks < ksteps; ++ks, ++it) {
+            const TileJob jb = src.job(t);
+            for (int ks = 0; ks < jb.ksteps; ++ks, ++it) {
                 const int s = it % kStages;
                 const uint32_t use = it / kStages;
-                if (use > 0 && !bar_wait(su32(&empty[s]), (use - 1) & 1, abort_flag, a.err, 1u)) {
+                if (use > 0 && !bar_wait(su32(&empty[s]), (use - 1) & 1, abort_flag, err, 1u)) {
                     ok = false;
                     break;
                 }
@@ -211,10 +254,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_split3_kernel(const __gr
                 const uint32_t fb = su32(&full[s]);
                 bar_expect_tx(fb, kStageBytes);
                 const int k0 = ks * kBK;
-                tma_2d(su32(st), &maps.a1, k0, m0, fb);
-                tma_2d(su32(st + kTileA), &maps.a2, k0, m0, fb);
-                tma_2d(su32(st + 2 * kTileA), &maps.b1, k0, n0, fb);
-                tma_2d(su32(st + 2 * kTileA + kTileB), &maps.b2, k0, n0, fb);
+                tma_2d(su32(st), jb.a1, k0, jb.m0, fb);
+                tma_2d(su32(st + kTileA), jb.a2, k0, jb.m0, fb);
+                tma_2d(su32(st + 2 * kTileA), jb.b1, k0, jb.n0, fb);
+                tma_2d(su32(st + 2 * kTileA + kTileB), jb.b2, k0, jb.n0, fb);
                 ++loaded;
             }
         }
@@ -225,13 +268,14 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_split3_kernel(const __gr
         for (int t = blockIdx.x; ok && t < tiles; t += gridDim.x, ++lt) {
             const int b = lt & 1;
             const uint32_t buse = lt >> 1;
-            if (buse > 0 && !bar_wait(su32(&tempty[b]), (buse - 1) & 1, abort_flag, a.err, 2u)) break;
+            if (buse > 0 && !bar_wait(su32(&tempty[b]), (buse - 1) & 1, abort_flag, err, 2u)) break;
             tc_fence_after();
             const uint32_t d_hh = tmem + (uint32_t)(b * 256), d_x = d_hh + 128;
+            const int ksteps = src.job(t).ksteps;
             for (int ks = 0; ks < ksteps; ++ks, ++it) {
                 const int s = it % kStages;
                 const uint32_t use = it / kStages;
-                if (!bar_wait(su32(&full[s]), use & 1, abort_flag, a.err, 2u)) {
+                if (!bar_wait(su32(&full[s]), use & 1, abort_flag, err, 2u)) {
                     ok = false;
                     break;
                 }
@@ -257,14 +301,14 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_split3_kernel(const __gr
         int lt = 0;
         for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++lt) {
             const int b = lt & 1;
-            if (!bar_wait(su32(&tfull[b]), (lt >> 1) & 1, abort_flag, a.err, 4u)) break;
+            if (!bar_wait(su32(&tfull[b]), (lt >> 1) & 1, abort_flag, err, 4u)) break;
             tc_fence_after();
-            int m0, n0;
-            tile_coords(a, t, m0, n0);
-            const int row = m0 + q * 32 + lane;
-            const bool row_ok = row < a.m;
-            const int sa = row_ok ? a.ea[row] : 0;
-            double *crow = a.C + (long long)row * a.ldc;
+            const TileJob jb = src.job(t);
+            const int n0 = jb.n0;
+            const int row = jb.m0 + q * 32 + lane;
+            const bool row_ok = row < jb.m;
+            const int sa = row_ok ? jb.ea[row] : 0;
+            double *crow = jb.C + (long long)row * jb.ldc;
             const uint32_t lane_off = (uint32_t)(q * 32) << 16;
             const uint32_t d_hh = tmem + (uint32_t)(b * 256), d_x = d_hh + 128;
             for (int c = 0; c < kBN; c += 32) {
@@ -276,11 +320,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_split3_kernel(const __gr
 #pragma unroll
                 for (int t2 = 0; t2 < 32; ++t2) {
                     const int col = n0 + c + t2;
-                    if (col < a.n) {
+                    if (col < jb.n) {
                         // exact two-sum of the partial products, widened and scaled
                         // without the (slow) FP64 pipe
                         const double v = ff::to_double(__uint_as_float(h[t2]), __uint_as_float(x[t2]));
-                        crow[col] = ff::scale_pow2(v, sa + a.eb[col]);
+                        crow[col] = ff::scale_pow2(v, sa + jb.eb[col]);
                     }
                 }
             }
@@ -314,6 +358,18 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_split3_kernel(const __gr
     }
 }
 
+__global__ void __launch_bounds__(kGemmThreads, 1) gemm_split3_kernel(const __grid_constant__ GemmMaps maps,
+                                                                     const __grid_constant__ GemmArgs a) {
+    const SingleSrc src{&maps, &a};
+    gemm_body(src, a.err);
+}
+
+__global__ void __launch_bounds__(kGemmThreads, 1) gemm_group_kernel(const GroupProblem *probs, const int4 *tiles,
+                                                                    int ntiles, unsigned *err) {
+    const GroupSrc src{probs, tiles, ntiles};
+    gemm_body(src, err);
+}
+
 // ---------------------------------------------------------------- splitting
 // per-column maxima of B (k x n): grid.x over column blocks of 32, grid.y over k chunks
 __global__ void col_maxexp_kernel(const double *B, long long ldb, int k, int n, int rows_per, int *e) {
@@ -321,6 +377,7 @@ __global__ void col_maxexp_kernel(const double *B, long long ldb, int k, int n, 
     const int r0 = blockIdx.y * rows_per, r1 = min(k, r0 + rows_per);
     if (col >= n) return;
     int mx = 0;
+#pragma unroll 8
     for (int l = r0 + threadIdx.y; l < r1; l += blockDim.y) {
         const int ex = (int)((__double_as_longlong(B[(long long)l * ldb + col]) >> 52) & 0x7ff);
         mx = max(mx, ex == 0x7ff ? 0x7fe : ex);
@@ -354,61 +411,127 @@ __device__ __forceinline__ void split_bf16(double x, int S, __nv_bfloat16 &hi, _
     lo = __float2bfloat16_rn(rem);
 }
 
-// A (m x k, lda) -> per-row scale ea and A1, A2 (m x kp), zero padding in
-// [k, kp); one block per row: the second pass re-reads the row from cache
-__global__ void split_rows_fused_kernel(const double *A, long long lda, int m, int k, int kp, int *ea,
-                                        __nv_bfloat16 *A1, __nv_bfloat16 *A2) {
-    const int row = blockIdx.x;
-    if (row >= m) return;
-    const double *src = A + (long long)row * lda;
+// One row of A -> its scale exponent and BF16 hi / lo rows (kp entries,
+// zero padding in [k, kp)); executed by one warp; the second pass re-reads
+// the row from cache.
+__device__ __forceinline__ void split_row_warp(const double *src, int k, int kp, int *ea_out,
+                                               __nv_bfloat16 *A1row, __nv_bfloat16 *A2row) {
+    const int lane = threadIdx.x & 31;
     int mx = 0;
-    for (int l = threadIdx.x; l < k; l += blockDim.x) {
+#pragma unroll 4
+    for (int l = lane; l < k; l += 32) {
         const int ex = (int)((__double_as_longlong(src[l]) >> 52) & 0x7ff);
         mx = max(mx, ex == 0x7ff ? 0x7fe : ex);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    __shared__ int ws[32];
-    __shared__ int scale;
-    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = mx;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = max(mx, ws[w]);
-        scale = mx == 0 ? 0 : mx - 1023 + 1;
-        ea[row] = scale;
-    }
-    __syncthreads();
-    const int S = scale;
-    __nv_bfloat16 *d1 = A1 + (long long)row * kp, *d2 = A2 + (long long)row * kp;
-    for (int l = threadIdx.x; l < kp; l += blockDim.x) {
-        __nv_bfloat16 h = __float2bfloat16_rn(0.0f), lo = h;
-        if (l < k) split_bf16(src[l], S, h, lo);
-        d1[l] = h;
-        d2[l] = lo;
+    const int S = mx == 0 ? 0 : mx - 1023 + 1;
+    if (lane == 0) *ea_out = S;
+    __nv_bfloat162 *d1 = reinterpret_cast<__nv_bfloat162 *>(A1row);
+    __nv_bfloat162 *d2 = reinterpret_cast<__nv_bfloat162 *>(A2row);
+#pragma unroll 2
+    for (int l2 = lane; l2 < kp / 2; l2 += 32) {
+        const int l = 2 * l2;
+        __nv_bfloat16 h0 = __float2bfloat16_rn(0.0f), o0 = h0, h1 = h0, o1 = h0;
+        if (l < k) split_bf16(src[l], S, h0, o0);
+        if (l + 1 < k) split_bf16(src[l + 1], S, h1, o1);
+        d1[l2] = __halves2bfloat162(h0, h1);
+        d2[l2] = __halves2bfloat162(o0, o1);
     }
 }
 
+// A (m x k, lda) -> per-row scale ea and A1, A2 (m x kp); one warp per row
+__global__ void split_rows_fused_kernel(const double *A, long long lda, int m, int k, int kp, int *ea,
+                                        __nv_bfloat16 *A1, __nv_bfloat16 *A2) {
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= m) return;
+    split_row_warp(A + (long long)row * lda, k, kp, ea + row, A1 + (long long)row * kp, A2 + (long long)row * kp);
+}
+
+// One 64 (k) x 64 (column) tile of B -> transposed BF16 hi / lo tiles of
+// B1t, B2t (n x kp); 256 threads, through shared memory.
+__device__ __forceinline__ void split_b_tile(const double *B, long long ldb, int k, int n, int kp, const int *eb,
+                                             __nv_bfloat16 *B1t, __nv_bfloat16 *B2t, int l0, int c0) {
+    __shared__ __nv_bfloat16 th[64][66], tl[64][66];
+    const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;  // 64 x 4
+    const int col = c0 + tx;
+    const int S = col < n ? eb[col] : 0;
+#pragma unroll 4
+    for (int yy = ty; yy < 64; yy += 4) {
+        const int l = l0 + yy;
+        __nv_bfloat16 h = __float2bfloat16_rn(0.0f), lo = h;
+        if (l < k && col < n) split_bf16(B[(long long)l * ldb + col], S, h, lo);
+        th[yy][tx] = h;
+        tl[yy][tx] = lo;
+    }
+    __syncthreads();
+    // write: each warp covers 8 columns x 64 k values (128 bytes per column)
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int cc = w * 8; cc < w * 8 + 8; ++cc) {
+        const int c = c0 + cc;
+        const int l = l0 + 2 * lane;
+        if (c < n && l < kp) {
+            __nv_bfloat162 *o1 = reinterpret_cast<__nv_bfloat162 *>(B1t + (long long)c * kp + l);
+            __nv_bfloat162 *o2 = reinterpret_cast<__nv_bfloat162 *>(B2t + (long long)c * kp + l);
+            *o1 = __halves2bfloat162(th[2 * lane][cc], th[2 * lane + 1][cc]);
+            *o2 = __halves2bfloat162(tl[2 * lane][cc], tl[2 * lane + 1][cc]);
+        }
+    }
+}
 
 // B (k x n, ldb) -> B1t, B2t (n x kp, transposed), zero padding in [k, kp)
 __global__ void split_cols_t_kernel(const double *B, long long ldb, int k, int n, int kp, const int *eb,
                                     __nv_bfloat16 *B1t, __nv_bfloat16 *B2t) {
-    __shared__ __nv_bfloat16 th[32][33], tl[32][33];
-    const int l0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
-    for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
-        const int l = l0 + yy, col = c0 + threadIdx.x;
-        __nv_bfloat16 h = __float2bfloat16_rn(0.0f), lo = h;
-        if (l < k && col < n) split_bf16(B[(long long)l * ldb + col], eb[col], h, lo);
-        th[yy][threadIdx.x] = h;
-        tl[yy][threadIdx.x] = lo;
-    }
-    __syncthreads();
-    for (int yy = threadIdx.y; yy < 32; yy += blockDim.y) {
-        const int col = c0 + yy, l = l0 + threadIdx.x;
-        if (col < n && l < kp) {
-            B1t[(long long)col * kp + l] = th[threadIdx.x][yy];
-            B2t[(long long)col * kp + l] = tl[threadIdx.x][yy];
+    split_b_tile(B, ldb, k, n, kp, eb, B1t, B2t, blockIdx.y * 64, blockIdx.x * 64);
+}
+
+// ------------------------------------------------------- grouped splitting
+struct GroupSplit {
+    const double *A, *B;
+    long long lda, ldb;
+    int m, n, k, kp;
+    __nv_bfloat16 *A1, *A2, *B1, *B2;
+    int *ea, *eb;
+};
+
+// job (problem, first row): 8 warps, one row each
+__global__ void split_a_group_kernel(const GroupSplit *gs, const int2 *jobs) {
+    const int2 jb = jobs[blockIdx.x];
+    const GroupSplit &G = gs[jb.x];
+    const int row = jb.y + (threadIdx.x >> 5);
+    if (row >= G.m) return;
+    split_row_warp(G.A + (long long)row * G.lda, G.k, G.kp, G.ea + row, G.A1 + (long long)row * G.kp,
+                   G.A2 + (long long)row * G.kp);
+}
+
+// job (problem, first column): 32 x 8 threads, the whole k range of 32 columns
+__global__ void colmax_b_group_kernel(const GroupSplit *gs, const int2 *jobs) {
+    const int2 jb = jobs[blockIdx.x];
+    const GroupSplit &G = gs[jb.x];
+    const int col = jb.y + threadIdx.x;
+    int mx = 0;
+    if (col < G.n) {
+#pragma unroll 8
+        for (int l = threadIdx.y; l < G.k; l += blockDim.y) {
+            const int ex = (int)((__double_as_longlong(G.B[(long long)l * G.ldb + col]) >> 52) & 0x7ff);
+            mx = max(mx, ex == 0x7ff ? 0x7fe : ex);
         }
     }
+    __shared__ int red[8][33];
+    red[threadIdx.y][threadIdx.x] = mx;
+    __syncthreads();
+    if (threadIdx.y == 0 && col < G.n) {
+        for (int y = 1; y < (int)blockDim.y; ++y) mx = max(mx, red[y][threadIdx.x]);
+        G.eb[col] = mx == 0 ? 0 : mx - 1023 + 1;
+    }
+}
+
+// job (problem, first column, first k): one 64 x 64 tile
+__global__ void split_b_group_kernel(const GroupSplit *gs, const int3 *jobs) {
+    const int3 jb = jobs[blockIdx.x];
+    const GroupSplit &G = gs[jb.x];
+    split_b_tile(G.B, G.ldb, G.k, G.n, G.kp, G.eb, G.B1, G.B2, jb.z, jb.y);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
@@ -476,11 +599,11 @@ void launch_gemm_split3(int m, int n, int k, const double *A, long long lda, con
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         (void)sms;
-        split_rows_fused_kernel<<<m, 256, 0, s>>>(A, lda, m, k, kp, ea, A1, A2);
+        split_rows_fused_kernel<<<(m + 7) / 8, 256, 0, s>>>(A, lda, m, k, kp, ea, A1, A2);
         OO_CUDA_TRY(cudaGetLastError());
-        dim3 grid((n + 31) / 32, (kp + 31) / 32), block(32, 8);
+        dim3 grid((n + 63) / 64, kp / 64);
         OO_REQUIRE(grid.y <= 65535, OO_EINVAL, "k too large");
-        split_cols_t_kernel<<<grid, block, 0, s>>>(B, ldb, k, n, kp, eb, B1, B2);
+        split_cols_t_kernel<<<grid, 256, 0, s>>>(B, ldb, k, n, kp, eb, B1, B2);
         OO_CUDA_TRY(cudaGetLastError());
     }
     GemmMaps maps;
@@ -514,6 +637,161 @@ void launch_gemm_split3(int m, int n, int k, const double *A, long long lda, con
     const int grid = (int)std::min<long long>(tiles, sms2);
     gemm_split3_kernel<<<grid, kGemmThreads, smem_gemm(), s>>>(maps, ga);
     OO_CUDA_TRY(cudaGetLastError());
+}
+
+// ------------------------------------------------------------ group plans
+struct GemmGroup {
+    void *arena = nullptr;
+    GroupProblem *d_probs = nullptr;
+    GroupSplit *d_split = nullptr;
+    int4 *d_tiles = nullptr;
+    int2 *d_ajobs = nullptr, *d_cjobs = nullptr;
+    int3 *d_bjobs = nullptr;
+    unsigned *d_err = nullptr;
+    int ntiles = 0, na = 0, nc = 0, nb = 0, grid = 1;
+    double flops = 0;
+};
+
+GemmGroup *gemm_group_create(const std::vector<GemmDesc> &v, int num_sms) {
+    OO_REQUIRE(!v.empty(), OO_EINVAL, "empty GEMM group");
+    auto up = [](size_t x, size_t a) { return (x + a - 1) / a * a; };
+    // arena layout: split operands | scale exponents | descriptors | job lists | error word
+    std::vector<size_t> off_a1(v.size()), off_a2(v.size()), off_b1(v.size()), off_b2(v.size()), off_ea(v.size()),
+        off_eb(v.size());
+    size_t at = 0;
+    std::vector<int> kp(v.size());
+    for (size_t i = 0; i < v.size(); ++i) {
+        const GemmDesc &d = v[i];
+        OO_REQUIRE(d.m >= 1 && d.n >= 1 && d.k >= 1 && d.lda >= d.k && d.ldb >= d.n && d.ldc >= d.n, OO_EINVAL,
+                   "bad GEMM in group");
+        kp[i] = (d.k + kBK - 1) / kBK * kBK;
+        const size_t ab = up((size_t)d.m * kp[i] * 2, 256), bb = up((size_t)d.n * kp[i] * 2, 256);
+        off_a1[i] = at; at += ab;
+        off_a2[i] = at; at += ab;
+        off_b1[i] = at; at += bb;
+        off_b2[i] = at; at += bb;
+    }
+    for (size_t i = 0; i < v.size(); ++i) {
+        off_ea[i] = at; at += up((size_t)v[i].m * 4, 16);
+        off_eb[i] = at; at += up((size_t)v[i].n * 4, 16);
+    }
+    at = up(at, 128);
+    const size_t off_probs = at; at += v.size() * sizeof(GroupProblem);
+    const size_t off_split = at; at += up(v.size() * sizeof(GroupSplit), 16);
+    std::vector<int4> tiles;
+    std::vector<int2> ajobs, cjobs;
+    std::vector<int3> bjobs;
+    double flops = 0;
+    for (size_t i = 0; i < v.size(); ++i) {
+        const GemmDesc &d = v[i];
+        flops += 2.0 * d.m * d.n * d.k;
+        for (int m0 = 0; m0 < d.m; m0 += kBM)
+            for (int n0 = 0; n0 < d.n; n0 += kBN) tiles.push_back(make_int4((int)i, m0, n0, kp[i] / kBK));
+        for (int r0 = 0; r0 < d.m; r0 += 8) ajobs.push_back(make_int2((int)i, r0));
+        for (int c0 = 0; c0 < d.n; c0 += 32) cjobs.push_back(make_int2((int)i, c0));
+        for (int c0 = 0; c0 < d.n; c0 += 64)
+            for (int l0 = 0; l0 < kp[i]; l0 += 64) bjobs.push_back(make_int3((int)i, c0, l0));
+    }
+    std::stable_sort(tiles.begin(), tiles.end(), [](const int4 &x, const int4 &y) { return x.w > y.w; });
+    const size_t off_tiles = at; at += up(tiles.size() * sizeof(int4), 16);
+    const size_t off_aj = at; at += up(ajobs.size() * sizeof(int2), 16);
+    const size_t off_cj = at; at += up(cjobs.size() * sizeof(int2), 16);
+    const size_t off_bj = at; at += up(bjobs.size() * sizeof(int3), 16);
+    const size_t off_err = at; at += 16;
+    auto *g = new GemmGroup();
+    try {
+        if (cudaMalloc(&g->arena, at) != cudaSuccess) {
+            cudaGetLastError();
+            throw Error{OO_ENOMEM, "GEMM group arena of " + std::to_string(at) + " bytes"};
+        }
+        char *base = static_cast<char *>(g->arena);
+        std::vector<GroupProblem> probs(v.size());
+        std::vector<GroupSplit> splits(v.size());
+        for (size_t i = 0; i < v.size(); ++i) {
+            const GemmDesc &d = v[i];
+            auto *A1 = reinterpret_cast<__nv_bfloat16 *>(base + off_a1[i]);
+            auto *A2 = reinterpret_cast<__nv_bfloat16 *>(base + off_a2[i]);
+            auto *B1 = reinterpret_cast<__nv_bfloat16 *>(base + off_b1[i]);
+            auto *B2 = reinterpret_cast<__nv_bfloat16 *>(base + off_b2[i]);
+            int *ea = reinterpret_cast<int *>(base + off_ea[i]);
+            int *eb = reinterpret_cast<int *>(base + off_eb[i]);
+            GroupProblem &P = probs[i];
+            std::memset(&P, 0, sizeof(P));
+            map_bf16(&P.a1, A1, d.m, kp[i], kBM);
+            map_bf16(&P.a2, A2, d.m, kp[i], kBM);
+            map_bf16(&P.b1, B1, d.n, kp[i], kBN);
+            map_bf16(&P.b2, B2, d.n, kp[i], kBN);
+            P.C = d.C;
+            P.ldc = d.ldc;
+            P.ea = ea;
+            P.eb = eb;
+            P.m = d.m;
+            P.n = d.n;
+            P.k = d.k;
+            P.kp = kp[i];
+            splits[i] = GroupSplit{d.A, d.B, d.lda, d.ldb, d.m, d.n, d.k, kp[i], A1, A2, B1, B2, ea, eb};
+        }
+        OO_CUDA_TRY(cudaMemcpy(base + off_probs, probs.data(), probs.size() * sizeof(GroupProblem),
+                               cudaMemcpyHostToDevice));
+        OO_CUDA_TRY(cudaMemcpy(base + off_split, splits.data(), splits.size() * sizeof(GroupSplit),
+                               cudaMemcpyHostToDevice));
+        OO_CUDA_TRY(cudaMemcpy(base + off_tiles, tiles.data(), tiles.size() * sizeof(int4), cudaMemcpyHostToDevice));
+        OO_CUDA_TRY(cudaMemcpy(base + off_aj, ajobs.data(), ajobs.size() * sizeof(int2), cudaMemcpyHostToDevice));
+        OO_CUDA_TRY(cudaMemcpy(base + off_cj, cjobs.data(), cjobs.size() * sizeof(int2), cudaMemcpyHostToDevice));
+        OO_CUDA_TRY(cudaMemcpy(base + off_bj, bjobs.data(), bjobs.size() * sizeof(int3), cudaMemcpyHostToDevice));
+        OO_CUDA_TRY(cudaMemset(base + off_err, 0, 16));
+        g->d_probs = reinterpret_cast<GroupProblem *>(base + off_probs);
+        g->d_split = reinterpret_cast<GroupSplit *>(base + off_split);
+        g->d_tiles = reinterpret_cast<int4 *>(base + off_tiles);
+        g->d_ajobs = reinterpret_cast<int2 *>(base + off_aj);
+        g->d_cjobs = reinterpret_cast<int2 *>(base + off_cj);
+        g->d_bjobs = reinterpret_cast<int3 *>(base + off_bj);
+        g->d_err = reinterpret_cast<unsigned *>(base + off_err);
+        g->ntiles = (int)tiles.size();
+        g->na = (int)ajobs.size();
+        g->nc = (int)cjobs.size();
+        g->nb = (int)bjobs.size();
+        g->grid = std::max(1, std::min(g->ntiles, num_sms));
+        g->flops = flops;
+    } catch (...) {
+        if (g->arena) cudaFree(g->arena);
+        delete g;
+        throw;
+    }
+    return g;
+}
+
+void gemm_group_launch(GemmGroup *g, cudaStream_t s) {
+    split_a_group_kernel<<<g->na, 256, 0, s>>>(g->d_split, g->d_ajobs);
+    OO_CUDA_TRY(cudaGetLastError());
+    colmax_b_group_kernel<<<g->nc, dim3(32, 8), 0, s>>>(g->d_split, g->d_cjobs);
+    OO_CUDA_TRY(cudaGetLastError());
+    split_b_group_kernel<<<g->nb, 256, 0, s>>>(g->d_split, g->d_bjobs);
+    OO_CUDA_TRY(cudaGetLastError());
+    static bool attr = false;
+    if (!attr) {
+        OO_CUDA_TRY(cudaFuncSetAttribute(gemm_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_gemm()));
+        attr = true;
+    }
+    gemm_group_kernel<<<g->grid, kGemmThreads, smem_gemm(), s>>>(g->d_probs, g->d_tiles, g->ntiles, g->d_err);
+    OO_CUDA_TRY(cudaGetLastError());
+}
+
+unsigned gemm_group_check(GemmGroup *g, cudaStream_t s) {
+    unsigned e = 0;
+    OO_CUDA_TRY(cudaMemcpyAsync(&e, g->d_err, 4, cudaMemcpyDeviceToHost, s));
+    OO_CUDA_TRY(cudaStreamSynchronize(s));
+    if (e) OO_CUDA_TRY(cudaMemsetAsync(g->d_err, 0, 4, s));
+    return e;
+}
+
+double gemm_group_flops(const GemmGroup *g) { return g->flops; }
+
+void gemm_group_destroy(GemmGroup *g) {
+    if (!g) return;
+    if (g->arena) cudaFree(g->arena);
+    delete g;
 }
 
 unsigned gemm_check_error(void *scratch, int m, int n, int k, cudaStream_t s) {

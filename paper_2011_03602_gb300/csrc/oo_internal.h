@@ -103,6 +103,38 @@ void launch_gemm_split3(int m, int n, int k, const double *A, long long lda, con
 // reads and clears the kernel's error word (0 = fine); synchronises s
 unsigned gemm_check_error(void *scratch, int m, int n, int k, cudaStream_t s);
 
+// Grouped FFTs (batched function blocks): transforms of different lengths
+// and directions in two persistent launches.
+struct FftDesc {
+    long long n;
+    int dir;
+    const double *in;
+    double *out;
+};
+struct FftGroup;
+FftGroup *fft_group_create(const std::vector<FftDesc> &v, const std::vector<const FftPlan *> &plans, int num_sms);
+void fft_group_launch(FftGroup *g, cudaStream_t s);
+double fft_group_elements(const FftGroup *g);
+void fft_group_destroy(FftGroup *g);
+
+// Grouped GEMMs (batched function blocks): one split pass and one persistent
+// tensor-core kernel over the tiles of every problem.
+struct GemmDesc {
+    int m, n, k;
+    const double *A;
+    long long lda;
+    const double *B;
+    long long ldb;
+    double *C;
+    long long ldc;
+};
+struct GemmGroup;
+GemmGroup *gemm_group_create(const std::vector<GemmDesc> &v, int num_sms);
+void gemm_group_launch(GemmGroup *g, cudaStream_t s);
+unsigned gemm_group_check(GemmGroup *g, cudaStream_t s);
+double gemm_group_flops(const GemmGroup *g);
+void gemm_group_destroy(GemmGroup *g);
+
 // Grow-only device buffer owned by a context.
 struct DevBuf {
     void *ptr = nullptr;

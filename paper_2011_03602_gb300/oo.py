@@ -48,6 +48,11 @@ class oo_jacobi(_c.Structure):
                 ("omega", _c.c_float), ("timing", _i32)]
 
 
+class oo_req(_c.Structure):
+    _fields_ = [("kind", _i32), ("prec", _i32), ("m", _c.c_int64), ("n", _c.c_int64), ("k", _c.c_int64),
+                ("in0", _vp), ("in1", _vp), ("out", _vp), ("dir", _i32), ("pad", _i32)]
+
+
 class oo_run_stats(_c.Structure):
     _fields_ = [("wall_ms", _dbl), ("nest_ms", _dbl * 6), ("xfer_ms", _dbl),
                 ("h2d_bytes", _u64), ("d2h_bytes", _u64), ("n_xfers", _i32),
@@ -99,6 +104,11 @@ def lib():
         "oo_gemm_f64_dev": (_c.c_int, [_vp, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _vp, _c.c_int, _vp,
                                        _c.c_int, _vp, _c.c_int]),
         "oo_gemm_check": (_c.c_int, [_vp, _c.c_int, _c.c_int, _c.c_int]),
+        "oo_batch_create": (_c.c_int, [_vp, P(oo_req), _c.c_int, P(_vp)]),
+        "oo_batch_run": (_c.c_int, [_vp, _c.c_int]),
+        "oo_batch_check": (_c.c_int, [_vp]),
+        "oo_batch_info": (_c.c_int, [_vp, P(_dbl), P(_dbl), P(_c.c_int), P(_c.c_int)]),
+        "oo_batch_destroy": (None, [_vp]),
         "oo_fft_c128_dev": (_c.c_int, [_vp, _c.c_int64, _c.c_int, _c.c_int, _vp, _vp]),
     }
     for name, (res, args) in sig.items():
@@ -314,6 +324,42 @@ def oo_gemm_check(ctx, m, n, k):
 def oo_fft_c128_dev(ctx, n, batch, direction, din, dout):
     """Device buffers of batch * n complex128 (torch tensors or addresses)."""
     _check(ctx, lib().oo_fft_c128_dev(ctx, n, batch, direction, _dev_ptr(din), _dev_ptr(dout)))
+
+
+# ------------------------------------------------------ batched function blocks
+def oo_batch_create(ctx, reqs):
+    """reqs: dicts kind ('gemm' | 'fft'), sizes and device buffers:
+    gemm: m, n, k, A, B, C (contiguous row-major); fft: n, x, X, dir."""
+    arr = (oo_req * len(reqs))()
+    for i, r in enumerate(reqs):
+        if r["kind"] == "gemm":
+            arr[i] = oo_req(OO_BLOCK_GEMM, r.get("prec", 0), r["m"], r["n"], r["k"], _dev_ptr(r["A"]),
+                            _dev_ptr(r["B"]), _dev_ptr(r["C"]), 0, 0)
+        else:
+            arr[i] = oo_req(OO_BLOCK_FFT, 0, 0, r["n"], 0, _dev_ptr(r["x"]), None, _dev_ptr(r["X"]),
+                            r.get("dir", -1), 0)
+    h = _vp()
+    _check(ctx, lib().oo_batch_create(ctx, arr, len(reqs), _c.byref(h)))
+    return h
+
+
+def oo_batch_run(ctx, b, mode):
+    """mode 0 grouped, 1 grouped in a CUDA graph, 2 one call per request."""
+    _check(ctx, lib().oo_batch_run(b, mode))
+
+
+def oo_batch_check(ctx, b):
+    _check(ctx, lib().oo_batch_check(b))
+
+
+def oo_batch_info(b):
+    fl, pts, ng, nf = _dbl(), _dbl(), _c.c_int(), _c.c_int()
+    lib().oo_batch_info(b, _c.byref(fl), _c.byref(pts), _c.byref(ng), _c.byref(nf))
+    return {"gemm_flops": fl.value, "fft_points": pts.value, "n_gemm": ng.value, "n_fft": nf.value}
+
+
+def oo_batch_destroy(b):
+    lib().oo_batch_destroy(b)
 
 
 def oo_lookup_block(callee, lang):

@@ -1,0 +1,109 @@
+"""Batched uneven function blocks: grouped persistent kernels (and their
+CUDA-graph replay) must give exactly what one call per request gives, and
+both must match the FP64 oracle at the blocks' tolerances."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2011_03602_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def oo_mod():
+    from paper_2011_03602_gb300 import build as pkg_build
+    from paper_2011_03602_gb300 import oo
+    pkg_build.build()
+    return oo
+
+
+def make_requests(seed, n_gemm, n_fft, gemm_range=(1, 300), fft_logn=(0, 15)):
+    rng = np.random.default_rng(seed)
+    reqs, host = [], []
+    for i in range(n_gemm):
+        m, n, k = (int(x) for x in rng.integers(gemm_range[0], gemm_range[1] + 1, 3))
+        A = synth.gemm_matrix(10 * i + 1, m, k)
+        B = synth.gemm_matrix(10 * i + 2, k, n)
+        reqs.append(dict(kind="gemm", m=m, n=n, k=k, A=torch.from_numpy(A).cuda(), B=torch.from_numpy(B).cuda(),
+                         C=torch.full((m, n), np.nan, dtype=torch.float64, device="cuda")))
+        host.append((A, B))
+    for i in range(n_fft):
+        e = int(rng.integers(fft_logn[0], fft_logn[1] + 1))
+        d = int(rng.choice([-1, 1]))
+        x = synth.complex_normal(1000 + i, 1 << e) * 10.0 ** int(rng.integers(-3, 4))
+        reqs.append(dict(kind="fft", n=1 << e, dir=d, x=torch.from_numpy(x.view(np.float64).copy()).cuda(),
+                         X=torch.full((2 << e,), np.nan, dtype=torch.float64, device="cuda")))
+        host.append((x, d))
+    return reqs, host
+
+
+def outputs(reqs):
+    return [(r["C"] if r["kind"] == "gemm" else r["X"]).cpu().numpy().copy() for r in reqs]
+
+
+def test_grouped_equals_per_call_and_oracle(oo_mod):
+    ctx = oo_mod.oo_create(0)
+    try:
+        reqs, host = make_requests(5, 24, 18)
+        b = oo_mod.oo_batch_create(ctx, reqs)
+        try:
+            got = {}
+            for mode in (2, 0, 1, 1):
+                for r in reqs:
+                    (r["C"] if r["kind"] == "gemm" else r["X"]).fill_(np.nan)
+                oo_mod.oo_batch_run(ctx, b, mode)
+                oo_mod.oo_batch_check(ctx, b)
+                got[mode] = outputs(reqs)
+            info = oo_mod.oo_batch_info(b)
+            assert info["n_gemm"] == 24 and info["n_fft"] == 18
+        finally:
+            oo_mod.oo_batch_destroy(b)
+        for i in range(len(reqs)):
+            assert np.array_equal(got[0][i], got[2][i]), i      # grouped == one call per request
+            assert np.array_equal(got[1][i], got[2][i]), i      # graph replay == one call per request
+        for r, h, out in zip(reqs, host, got[0]):
+            if r["kind"] == "gemm":
+                A, B = h
+                ref = oracle.gemm(A, B)
+                assert np.max(np.abs(out - ref) / (np.abs(A) @ np.abs(B))) <= 1e-4
+            else:
+                x, d = h
+                X = out.view(np.complex128)
+                ref = oracle.fft(x, d)
+                assert np.linalg.norm(X - ref) / np.linalg.norm(ref) <= 1e-12
+    finally:
+        oo_mod.oo_destroy(ctx)
+
+
+def test_only_ffts_and_only_gemms(oo_mod):
+    ctx = oo_mod.oo_create(0)
+    try:
+        for ng, nf in ((0, 9), (7, 0)):
+            reqs, host = make_requests(11 + ng, ng, nf, gemm_range=(16, 200), fft_logn=(8, 14))
+            b = oo_mod.oo_batch_create(ctx, reqs)
+            try:
+                oo_mod.oo_batch_run(ctx, b, 1)
+                oo_mod.oo_batch_check(ctx, b)
+                a = outputs(reqs)
+                oo_mod.oo_batch_run(ctx, b, 2)
+                oo_mod.oo_batch_check(ctx, b)
+                c = outputs(reqs)
+                assert all(np.array_equal(x, y) for x, y in zip(a, c))
+            finally:
+                oo_mod.oo_batch_destroy(b)
+    finally:
+        oo_mod.oo_destroy(ctx)
+
+
+def test_bad_requests(oo_mod):
+    ctx = oo_mod.oo_create(0)
+    try:
+        x = torch.zeros(24, dtype=torch.float64, device="cuda")
+        with pytest.raises(oo_mod.OOError):
+            oo_mod.oo_batch_create(ctx, [dict(kind="fft", n=12, x=x, X=x)])
+        with pytest.raises(oo_mod.OOError):
+            oo_mod.oo_batch_create(ctx, [dict(kind="gemm", m=0, n=2, k=2, A=x, B=x, C=x)])
+    finally:
+        oo_mod.oo_destroy(ctx)
