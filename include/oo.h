@@ -283,6 +283,58 @@ oo_status oo_fft_c128(oo_ctx *ctx, int64_t n, int dir, const double *in, double 
 oo_status oo_fft_c128_dev(oo_ctx *ctx, int64_t n, int batch, int dir, const double *din,
                           double *dout);
 
+/* ----------------------------------------------------------------- serving */
+/* Mixed requests from any number of client threads (C, Python ctypes, Java
+ * JNI front-ends alike), admitted continuously onto the GPU: whenever one of
+ * `slots` CUDA streams is free, the oldest waiting requests whose device
+ * footprint fits the free part of a `hbm_budget_bytes` device arena start
+ * (a request that has waited 50 ms at the head of the queue is not
+ * overtaken); their copies and kernels overlap on the device.  Inputs are
+ * copied into a pinned staging pool (as large as the budget) by oo_submit;
+ * results are copied into the caller's buffer by oo_wait.
+ *   kind OO_BLOCK_GEMM   : C (m x n) = A (m x k) B (k x n), host row-major
+ *                          contiguous; in0 = A, in1 = B, out = C; prec.
+ *   kind OO_BLOCK_FFT    : length n, dir; in0 = x, out = X (complex128).
+ *   kind OO_BLOCK_JACOBI : the Jacobi program on an m x n x k grid (I, J, K)
+ *                          for `iters` iterations with `omega`, every nest
+ *                          on the GPU; out = final p (I*J*K floats), res =
+ *                          residuals (iters doubles, may be NULL).
+ * Host buffers must stay valid until oo_wait returns for the ticket, and
+ * every ticket must be waited for (that releases its staging).           */
+enum { OO_BLOCK_JACOBI = 3 };
+typedef struct {
+    int32_t kind;
+    int32_t prec;
+    int64_t m, n, k;
+    int32_t dir;
+    int32_t iters;
+    float omega;
+    int32_t client;  /* front-end tag for the caller's statistics */
+    const void *in0;
+    const void *in1;
+    void *out;
+    double *res;
+} oo_serve_req;
+typedef struct {
+    uint64_t submitted, completed, rejected_busy, failed, queued, running;
+    uint64_t device_free_bytes, device_budget_bytes;
+} oo_serve_stats_t;
+/* Start the scheduler thread; allocates the device arena and pinned pool. */
+oo_status oo_serve_start(oo_ctx *ctx, int slots, uint64_t hbm_budget_bytes, int queue_cap);
+/* Thread-safe.  OO_EBUSY: queue or staging pool full (back-pressure, retry
+ * later); OO_EINVAL: malformed, or larger than the device budget.        */
+oo_status oo_submit(oo_ctx *ctx, const oo_serve_req *req, uint64_t *ticket);
+/* Thread-safe.  Waits up to timeout_ms; *latency_ms (may be NULL) is the
+ * time from submission to completion.  OO_ETIMEOUT if not done in time (the
+ * ticket stays valid); other errors are the request's own status.  Only one
+ * thread may wait for a given ticket, and oo_serve_stop must not be called
+ * while waits are in progress.                                           */
+oo_status oo_wait(oo_ctx *ctx, uint64_t ticket, int timeout_ms, double *latency_ms);
+oo_status oo_serve_stats(oo_ctx *ctx, oo_serve_stats_t *out);
+/* Finish admitted and queued work, stop the scheduler, free the arena.
+ * Tickets not yet waited for are discarded.                              */
+oo_status oo_serve_stop(oo_ctx *ctx);
+
 /* --------------------------------------------------- batched function blocks */
 /* Many GEMM and FFT requests of uneven sizes, on caller-owned device buffers.
  *   GEMM (kind OO_BLOCK_GEMM): C (m x n) = A (m x k) B (k x n), row-major,

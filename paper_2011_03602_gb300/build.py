@@ -91,6 +91,24 @@ def build(force: bool = False, verbose: bool = False) -> str:
     return LIB
 
 
+CLIENT_SRC = os.path.join(PKG, "frontends", "c", "oo_client.c")
+CLIENT_BIN = os.path.join(PKG, "frontends", "c", "oo_client")
+
+
+def build_c_client(force: bool = False) -> str:
+    """The C front-end example, linked against the in-tree liboo.so."""
+    lib = build()
+    if not force and os.path.exists(CLIENT_BIN) and \
+            os.path.getmtime(CLIENT_BIN) >= max(os.path.getmtime(CLIENT_SRC), os.path.getmtime(lib)):
+        return CLIENT_BIN
+    cmd = ["gcc", "-O2", "-std=c11", "-Wall", "-I" + os.path.join(ROOT, "include"), CLIENT_SRC,
+           "-L" + PKG, "-loo", "-Wl,-rpath," + PKG, "-lpthread", "-lm", "-o", CLIENT_BIN]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("C client build failed: %s\n%s" % (r.stdout, r.stderr))
+    return CLIENT_BIN
+
+
 def clean():
     shutil.rmtree(BUILD, ignore_errors=True)
     if os.path.exists(LIB):

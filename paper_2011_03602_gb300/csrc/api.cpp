@@ -127,6 +127,10 @@ void oo_destroy(oo_ctx *ctx) {
         return;
     }
     cudaSetDevice(ctx->c.device);
+    if (ctx->c.server) {
+        server_stop(ctx->c.server);
+        ctx->c.server = nullptr;
+    }
     if (ctx->c.stream) cudaStreamSynchronize(ctx->c.stream);
     stencil_plan_destroy(ctx->user_plan);
     jacobi_work_free(ctx->c.jw);

@@ -729,14 +729,13 @@ struct StencilPlan {
     StencilArgs args{};
     int grid = 0;
     void *scratch = nullptr;
+    bool own_scratch = true;
 };
 
-StencilPlan *stencil_plan_create(const JacobiDims &d, const float *const coef[NCOEF], const float *p,
-                                 float *wrk2, int num_sms) {
-    OO_REQUIRE(d.I >= 3 && d.J >= 3 && d.K >= 3, OO_EINVAL, "grid must be at least 3 x 3 x 3");
-    OO_REQUIRE(d.pitch >= d.K && d.pitch % 4 == 0, OO_EINVAL, "pitch must be >= K and a multiple of 4");
-    OO_REQUIRE(((uintptr_t)wrk2 & 15u) == 0, OO_EINVAL, "wrk2 must be 16-byte aligned");
-    auto sp = new StencilPlan();
+namespace {
+// tensor maps, tile shape and the i-segment split of a plan (no scratch yet)
+void fill_stencil_plan(StencilPlan *sp, const JacobiDims &d, const float *const coef[NCOEF], const float *p,
+                       float *wrk2, int num_sms) {
     sp->d = d;
     // default tile shape by row length; OO_STENCIL_VARIANT overrides (tuning sweeps)
     sp->variant = d.K - 1 > 64 ? 0 : 4;
@@ -746,44 +745,88 @@ StencilPlan *stencil_plan_create(const JacobiDims &d, const float *const coef[NC
     }
     sp->TK = variant(sp->variant).TK;
     sp->TJ = variant(sp->variant).TJ;
-    try {
-        for (int c = 0; c < NCOEF; ++c) make_map(&sp->maps.coef[c], coef[c], d, sp->TK, sp->TJ);
-        make_map(&sp->maps.p, p, d, sp->TK + 8, sp->TJ + 2);
-        StencilArgs &a = sp->args;
-        a.I = d.I;
-        a.J = d.J;
-        a.K = d.K;
-        a.pitch = d.pitch;
-        a.n_kt = (d.K - 1 + sp->TK - 1) / sp->TK;
-        a.n_jt = (d.J - 2 + sp->TJ - 1) / sp->TJ;
-        const int cols = a.n_kt * a.n_jt;
-        const int span = d.I - 2;
-        // segments of the i range: balance units over one CTA per SM, with
-        // a small charge for the two halo planes every unit reloads
-        const int G = std::max(1, num_sms * variant(sp->variant).ctas_per_sm);
-        double best = 1e300;
-        int best_seg = 1;
-        for (int ns = 1; ns <= span; ++ns) {
-            const int smax = (span + ns - 1) / ns;
-            const long long units = (long long)cols * ns;
-            const long long rounds = (units + G - 1) / G;
-            const double cost = (double)rounds * (smax + 0.6);
-            if (cost < best - 1e-9) {
-                best = cost;
-                best_seg = ns;
-            }
+    for (int c = 0; c < NCOEF; ++c) make_map(&sp->maps.coef[c], coef[c], d, sp->TK, sp->TJ);
+    make_map(&sp->maps.p, p, d, sp->TK + 8, sp->TJ + 2);
+    StencilArgs &a = sp->args;
+    a.I = d.I;
+    a.J = d.J;
+    a.K = d.K;
+    a.pitch = d.pitch;
+    a.n_kt = (d.K - 1 + sp->TK - 1) / sp->TK;
+    a.n_jt = (d.J - 2 + sp->TJ - 1) / sp->TJ;
+    const int cols = a.n_kt * a.n_jt;
+    const int span = d.I - 2;
+    // segments of the i range: balance units over one CTA per SM, with a
+    // charge for the two halo planes and the prologue every unit pays
+    const int G = std::max(1, num_sms * variant(sp->variant).ctas_per_sm);
+    double best = 1e300;
+    int best_seg = 1;
+    for (int ns = 1; ns <= span; ++ns) {
+        const int smax = (span + ns - 1) / ns;
+        const long long units = (long long)cols * ns;
+        const long long rounds = (units + G - 1) / G;
+        const double cost = (double)rounds * (smax + 0.6);
+        if (cost < best - 1e-9) {
+            best = cost;
+            best_seg = ns;
         }
-        a.n_seg = best_seg;
-        a.n_units = cols * best_seg;
-        sp->grid = std::min(a.n_units, G);
-        a.wrk2 = wrk2;
-        const size_t bytes = (size_t)a.n_units * 16 * 8 + 256;  // up to 16 consumer warps
-        OO_CUDA_TRY(cudaMalloc(&sp->scratch, bytes));
+    }
+    a.n_seg = best_seg;
+    a.n_units = cols * best_seg;
+    sp->grid = std::min(a.n_units, G);
+    a.wrk2 = wrk2;
+}
+void attach_scratch(StencilPlan *sp, void *scratch) {
+    StencilArgs &a = sp->args;
+    sp->scratch = scratch;
+    a.partials = reinterpret_cast<double *>(scratch);
+    a.counter = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(scratch) + (size_t)a.n_units * 16 * 8);
+    a.err = a.counter + 1;
+}
+size_t plan_scratch_bytes(const StencilPlan *sp) { return (size_t)sp->args.n_units * 16 * 8 + 256; }
+}  // namespace
+
+size_t stencil_scratch_bytes(const JacobiDims &d, int num_sms) {
+    // upper bound over the tile variants (smallest tile 64 x 4) and every
+    // i-segment split (at most one unit per plane)
+    (void)num_sms;
+    const long long kt = (d.K - 1 + 63) / 64, jt = (d.J - 2 + 3) / 4;
+    return (size_t)(kt * jt * std::max(1, d.I - 2)) * 16 * 8 + 256;
+}
+
+StencilPlan *stencil_plan_create_ext(const JacobiDims &d, const float *const coef[NCOEF], const float *p, float *wrk2,
+                                     int num_sms, void *scratch, size_t scratch_bytes, cudaStream_t s) {
+    OO_REQUIRE(d.I >= 3 && d.J >= 3 && d.K >= 3, OO_EINVAL, "grid must be at least 3 x 3 x 3");
+    OO_REQUIRE(d.pitch >= d.K && d.pitch % 4 == 0, OO_EINVAL, "pitch must be >= K and a multiple of 4");
+    OO_REQUIRE(((uintptr_t)wrk2 & 15u) == 0 && ((uintptr_t)scratch & 15u) == 0, OO_EINVAL,
+               "wrk2 and scratch must be 16-byte aligned");
+    auto sp = new StencilPlan();
+    try {
+        fill_stencil_plan(sp, d, coef, p, wrk2, num_sms);
+        OO_REQUIRE(plan_scratch_bytes(sp) <= scratch_bytes, OO_EINVAL, "stencil scratch too small");
+        attach_scratch(sp, scratch);
+        sp->own_scratch = false;
+        OO_CUDA_TRY(cudaMemsetAsync(sp->args.counter, 0, 8, s));
+    } catch (...) {
+        delete sp;
+        throw;
+    }
+    return sp;
+}
+
+StencilPlan *stencil_plan_create(const JacobiDims &d, const float *const coef[NCOEF], const float *p,
+                                 float *wrk2, int num_sms) {
+    OO_REQUIRE(d.I >= 3 && d.J >= 3 && d.K >= 3, OO_EINVAL, "grid must be at least 3 x 3 x 3");
+    OO_REQUIRE(d.pitch >= d.K && d.pitch % 4 == 0, OO_EINVAL, "pitch must be >= K and a multiple of 4");
+    OO_REQUIRE(((uintptr_t)wrk2 & 15u) == 0, OO_EINVAL, "wrk2 must be 16-byte aligned");
+    auto sp = new StencilPlan();
+    try {
+        fill_stencil_plan(sp, d, coef, p, wrk2, num_sms);
+        const size_t bytes = plan_scratch_bytes(sp);  // up to 16 consumer warps
+        void *scr = nullptr;
+        OO_CUDA_TRY(cudaMalloc(&scr, bytes));
+        attach_scratch(sp, scr);
         OO_CUDA_TRY(cudaMemset(sp->scratch, 0, bytes));
-        a.partials = reinterpret_cast<double *>(sp->scratch);
-        a.counter = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(sp->scratch) +
-                                                 (size_t)a.n_units * 16 * 8);
-        a.err = a.counter + 1;
     } catch (...) {
         if (sp->scratch) cudaFree(sp->scratch);
         delete sp;
@@ -794,7 +837,7 @@ StencilPlan *stencil_plan_create(const JacobiDims &d, const float *const coef[NC
 
 void stencil_plan_destroy(StencilPlan *sp) {
     if (!sp) return;
-    if (sp->scratch) cudaFree(sp->scratch);
+    if (sp->scratch && sp->own_scratch) cudaFree(sp->scratch);
     delete sp;
 }
 
@@ -803,6 +846,8 @@ void launch_stencil(StencilPlan *sp, float omega, double *res_dev, cudaStream_t 
     sp->args.res = res_dev;
     variant(sp->variant).launch(sp->grid, sp->maps, sp->args, s);
 }
+
+const unsigned *stencil_plan_err_ptr(const StencilPlan *sp) { return sp->args.err; }
 
 unsigned stencil_plan_check(StencilPlan *sp, cudaStream_t s) {
     unsigned e = 0;

@@ -90,6 +90,7 @@ struct FftPlan;
 FftPlan *fft_plan_create(long long n);
 void fft_plan_destroy(FftPlan *p);
 size_t fft_scratch_bytes(const FftPlan *p, int batch);
+// Serving works on a (thread-safe) context-owned plan cache; see Ctx::fft_plan.
 // batch transforms of length n (contiguous, interleaved complex128); dir -1
 // forward, +1 inverse (1/n scaled); in may equal out; async on s
 void launch_fft(const FftPlan *p, int batch, int dir, const double *in, double *out, void *scratch,
@@ -158,6 +159,10 @@ struct DevBuf {
     }
 };
 
+// Serving loop state (serve.cpp).
+struct Server;
+void server_stop(Server *S);
+
 // --------------------------------------------------------------- context
 struct Ctx {
     int device = 0;
@@ -179,6 +184,7 @@ struct Ctx {
     // function blocks
     std::vector<std::pair<long long, FftPlan *>> fft_plans;
     DevBuf fft_scratch, stage_a, stage_b, stage_c, gemm_scratch;
+    Server *server = nullptr;
     FftPlan *fft_plan(long long n) {
         for (auto &kv : fft_plans)
             if (kv.first == n) return kv.second;
@@ -200,9 +206,16 @@ void launch_bc_k(const JacobiDims &d, float *p, cudaStream_t s);
 
 StencilPlan *stencil_plan_create(const JacobiDims &d, const float *const coef[NCOEF],
                                  const float *p, float *wrk2, int num_sms);
+// A plan whose scratch (partial residuals, counter, error word) lives in
+// caller-provided device memory of at least stencil_scratch_bytes(d, sms).
+StencilPlan *stencil_plan_create_ext(const JacobiDims &d, const float *const coef[NCOEF], const float *p, float *wrk2,
+                                     int num_sms, void *scratch, size_t scratch_bytes, cudaStream_t s);
+size_t stencil_scratch_bytes(const JacobiDims &d, int num_sms);
 void stencil_plan_destroy(StencilPlan *sp);
 // One stencil sweep; the residual (FP64) lands in *res_dev.
 void launch_stencil(StencilPlan *sp, float omega, double *res_dev, cudaStream_t s);
+// Device address of the plan's error word (0 = fine).
+const unsigned *stencil_plan_err_ptr(const StencilPlan *sp);
 // Reads and clears the device-side error word of the plan (0 = fine).
 unsigned stencil_plan_check(StencilPlan *sp, cudaStream_t s);
 

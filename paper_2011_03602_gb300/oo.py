@@ -53,6 +53,17 @@ class oo_req(_c.Structure):
                 ("in0", _vp), ("in1", _vp), ("out", _vp), ("dir", _i32), ("pad", _i32)]
 
 
+class oo_serve_req(_c.Structure):
+    _fields_ = [("kind", _i32), ("prec", _i32), ("m", _c.c_int64), ("n", _c.c_int64), ("k", _c.c_int64),
+                ("dir", _i32), ("iters", _i32), ("omega", _c.c_float), ("client", _i32),
+                ("in0", _vp), ("in1", _vp), ("out", _vp), ("res", _vp)]
+
+
+class oo_serve_stats_t(_c.Structure):
+    _fields_ = [(n, _u64) for n in ("submitted", "completed", "rejected_busy", "failed", "queued", "running",
+                                    "device_free_bytes", "device_budget_bytes")]
+
+
 class oo_run_stats(_c.Structure):
     _fields_ = [("wall_ms", _dbl), ("nest_ms", _dbl * 6), ("xfer_ms", _dbl),
                 ("h2d_bytes", _u64), ("d2h_bytes", _u64), ("n_xfers", _i32),
@@ -109,6 +120,11 @@ def lib():
         "oo_batch_check": (_c.c_int, [_vp]),
         "oo_batch_info": (_c.c_int, [_vp, P(_dbl), P(_dbl), P(_c.c_int), P(_c.c_int)]),
         "oo_batch_destroy": (None, [_vp]),
+        "oo_serve_start": (_c.c_int, [_vp, _c.c_int, _u64, _c.c_int]),
+        "oo_submit": (_c.c_int, [_vp, P(oo_serve_req), P(_u64)]),
+        "oo_wait": (_c.c_int, [_vp, _u64, _c.c_int, P(_dbl)]),
+        "oo_serve_stats": (_c.c_int, [_vp, P(oo_serve_stats_t)]),
+        "oo_serve_stop": (_c.c_int, [_vp]),
         "oo_fft_c128_dev": (_c.c_int, [_vp, _c.c_int64, _c.c_int, _c.c_int, _vp, _vp]),
     }
     for name, (res, args) in sig.items():
@@ -360,6 +376,70 @@ def oo_batch_info(b):
 
 def oo_batch_destroy(b):
     lib().oo_batch_destroy(b)
+
+
+# ------------------------------------------------------------------- serving
+OO_BLOCK_JACOBI = 3
+
+
+def oo_serve_start(ctx, slots=8, hbm_budget_bytes=8 << 30, queue_cap=4096):
+    _check(ctx, lib().oo_serve_start(ctx, slots, hbm_budget_bytes, queue_cap))
+
+
+def serve_request(kind, **kw):
+    """Build an oo_serve_req from numpy host arrays (kept alive by the caller
+    until oo_wait returns): gemm(A, B, C), fft(x, X, dir), jacobi(I, J, K,
+    iters, p, res, omega)."""
+    r = oo_serve_req()
+    r.client = kw.get("client", OO_LANG_PYTHON)
+    if kind == "gemm":
+        A, B, C = kw["A"], kw["B"], kw["C"]
+        r.kind, r.prec, (r.m, r.k), r.n = OO_BLOCK_GEMM, kw.get("prec", 0), A.shape, B.shape[1]
+        r.in0, r.in1, r.out = _host_ptr(A, np.float64), _host_ptr(B, np.float64), _host_ptr(C, np.float64)
+    elif kind == "fft":
+        x, X = kw["x"], kw["X"]
+        r.kind, r.n, r.dir = OO_BLOCK_FFT, x.size, kw.get("dir", -1)
+        r.in0, r.out = _host_ptr(x, np.complex128), _host_ptr(X, np.complex128)
+    else:
+        r.kind, r.m, r.n, r.k = OO_BLOCK_JACOBI, kw["I"], kw["J"], kw["K"]
+        r.iters, r.omega = kw["iters"], kw.get("omega", 0.8)
+        r.out = _host_ptr(kw["p"], np.float32, kw["I"] * kw["J"] * kw["K"])
+        res = kw.get("res")
+        if res is not None and res.size < kw["iters"]:
+            raise ValueError("res needs at least iters elements")
+        r.res = None if res is None else _host_ptr(res, np.float64)
+    return r
+
+
+def oo_submit(ctx, req):
+    """-> ticket; raises OOError (status OO_EBUSY when back-pressured)."""
+    t = _u64()
+    _check(ctx, lib().oo_submit(ctx, _c.byref(req), _c.byref(t)))
+    return t.value
+
+
+def oo_submit_status(ctx, req):
+    """-> (status, ticket) without raising (for load generators)."""
+    t = _u64()
+    st = lib().oo_submit(ctx, _c.byref(req), _c.byref(t))
+    return st, t.value
+
+
+def oo_wait(ctx, ticket, timeout_ms=60000):
+    """-> latency in ms; raises OOError (OO_ETIMEOUT if not done in time)."""
+    lat = _dbl()
+    _check(ctx, lib().oo_wait(ctx, ticket, timeout_ms, _c.byref(lat)))
+    return lat.value
+
+
+def oo_serve_stats(ctx):
+    st = oo_serve_stats_t()
+    _check(ctx, lib().oo_serve_stats(ctx, _c.byref(st)))
+    return {n: getattr(st, n) for n, _ in oo_serve_stats_t._fields_}
+
+
+def oo_serve_stop(ctx):
+    _check(ctx, lib().oo_serve_stop(ctx))
 
 
 def oo_lookup_block(callee, lang):
