@@ -159,6 +159,26 @@ def run_reference(args):
     return 0
 
 
+def stencil_traffic():
+    """DRAM bytes (read + write) of one full-size stencil launch from the
+    committed ncu summary, or None when the stencil sources have changed
+    since that capture (the summary records a hash of them)."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", "stencil_jacobi19_257x257x513.md")
+    try:
+        text = open(path).read()
+        nbytes = int(re.search(r"dram_bytes_per_launch: (\d+)", text).group(1))
+        want = re.search(r"sources_sha256_16: ([0-9a-f]+)", text).group(1)
+    except (OSError, AttributeError, ValueError):
+        return None
+    h = hashlib.sha256()
+    for f in ("jacobi.cu", "ff.cuh"):
+        with open(os.path.join(ROOT, "paper_2011_03602_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return nbytes if h.hexdigest()[:16] == want else None
+
+
 def load_bf16_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -168,35 +188,32 @@ def load_bf16_peak():
         return 1900.0, 1700.0, "fallback"
 
 
-def bench_blocks(oo, ctx, torch, with_errors=True):
-    """Function blocks (Sec. 3.2.2): split-BF16 GEMM at n = 4096 and the
-    complex128 FFT at N = 2^22, device-resident inputs, CUDA events on the
-    context's stream; errors against the oracle on a bounded sample."""
-    from paper_2011_03602_gb300 import synth
-    out = {}
-    stream = torch.cuda.current_stream()
-    n = 4096
-    A_h, B_h = synth.gemm_matrix(41, n, n), synth.gemm_matrix(42, n, n)
-    A, B = torch.from_numpy(A_h).cuda(), torch.from_numpy(B_h).cuda()
-    C = torch.empty(n, n, dtype=torch.float64, device="cuda")
+def gemm_component(oo, ctx, torch, prec, A_h, B_h, A, B, C, with_errors):
+    """One n x n x n product in precision pattern prec, timed with CUDA events
+    on the context's stream (splits included); error against the oracle on
+    sampled rows."""
+    n = A_h.shape[0]
     for _ in range(3):
-        oo.oo_gemm_f64_dev(ctx, n, n, n, A, n, B, n, C, n)
+        oo.oo_gemm_f64_dev(ctx, n, n, n, A, n, B, n, C, n, prec=prec)
     oo.oo_sync(ctx)
-    reps = 10
+    reps = 10 if prec == oo.OO_PREC_SPLIT3_BF16 else 4
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(ctx_stream_holder[0])
     for _ in range(reps):
-        oo.oo_gemm_f64_dev(ctx, n, n, n, A, n, B, n, C, n)
+        oo.oo_gemm_f64_dev(ctx, n, n, n, A, n, B, n, C, n, prec=prec)
     e1.record(ctx_stream_holder[0])
     e1.synchronize()
     oo.oo_gemm_check(ctx, n, n, n)
     ms = e0.elapsed_time(e1) / reps
     peak, peak_s, src = load_bf16_peak()
-    tensor = 3 * 2 * n ** 3 / (ms * 1e-3) / 1e12
+    products, beta, levels, kb = oo.oo_gemm_plan(prec, n)
+    tensor = products * 2 * n ** 3 / (ms * 1e-3) / 1e12
     g = {"n": n, "ms": round(ms, 4), "solves_per_s": round(1e3 / ms, 2),
          "fp64_equiv_tflops": round(2 * n ** 3 / (ms * 1e-3) / 1e12, 2),
-         "tensor_tflops": round(tensor, 1), "peak_bf16_tflops": peak, "peak_source": src,
-         "frac_of_bf16_peak": round(tensor / peak, 4), "precision": "split3_bf16"}
+         "bf16_products": products, "tensor_tflops": round(tensor, 1), "peak_bf16_tflops": peak,
+         "peak_source": src, "frac_of_bf16_peak": round(tensor / peak, 4),
+         "precision": "split3_bf16" if prec == oo.OO_PREC_SPLIT3_BF16 else
+         "fp64eq_ozaki_bf16_beta%d_L%d_kblock%d" % (beta, levels, kb)}
     if with_errors:
         import oracle
         Ch = C.cpu().numpy()
@@ -207,8 +224,24 @@ def bench_blocks(oo, ctx, torch, with_errors=True):
             errs.append(float(np.max(np.abs(Ch[r] - ref) / (np.abs(A_h[r]) @ np.abs(B_h)))))
         g["max_err_vs_oracle"] = max(errs)
         g["err_metric"] = "max |C-C*| / (|A||B|) over rows %s" % rows
-    out["gemm"] = g
+    return g
+
+
+def bench_blocks(oo, ctx, torch, with_errors=True):
+    """Function blocks (Sec. 3.2.2): the GEMM at n = 4096 in both precision
+    patterns (split-BF16 and FP64-equivalent) and the complex128 FFT at
+    N = 2^22, device-resident inputs, CUDA events on the context's stream;
+    errors against the oracle on a bounded sample."""
+    from paper_2011_03602_gb300 import synth
+    out = {}
+    n = 4096
+    A_h, B_h = synth.gemm_matrix(41, n, n), synth.gemm_matrix(42, n, n)
+    A, B = torch.from_numpy(A_h).cuda(), torch.from_numpy(B_h).cuda()
+    C = torch.empty(n, n, dtype=torch.float64, device="cuda")
+    out["gemm"] = gemm_component(oo, ctx, torch, oo.OO_PREC_SPLIT3_BF16, A_h, B_h, A, B, C, with_errors)
+    out["gemm_fp64eq"] = gemm_component(oo, ctx, torch, oo.OO_PREC_FP64EQ, A_h, B_h, A, B, C, with_errors)
     del A, B, C
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     logn = 22
     N = 1 << logn
     x_h = synth.complex_normal(43, N)
@@ -318,13 +351,7 @@ def run_gpu(args):
             cpu = {"value": round(v, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
                    "sample": "%dx%dx%d grid, 2 of %d iterations, whole program, FP64 C oracle, %.1f s"
                              % (I, J, K, ITERS, dt)}
-        traffic = None
-        tpath = os.path.join(ROOT, "profiles", "stencil_traffic.json")
-        if os.path.exists(tpath):
-            try:
-                traffic = json.load(open(tpath)).get("bytes_per_full_launch")
-            except Exception:
-                traffic = None
+        traffic = stencil_traffic() if (I, J, K) == (257, 257, 513) else None
         line = {
             "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
@@ -396,8 +423,9 @@ def run_block(args):
         A = torch.from_numpy(synth.gemm_matrix(1, n, n)).cuda()
         B = torch.from_numpy(synth.gemm_matrix(2, n, n)).cuda()
         C = torch.empty(n, n, dtype=torch.float64, device="cuda")
+        prec = oo.OO_PREC_FP64EQ if args.prec == "fp64eq" else oo.OO_PREC_SPLIT3_BF16
         for _ in range(args.steps):
-            oo.oo_gemm_f64_dev(ctx, n, n, n, A, n, B, n, C, n)
+            oo.oo_gemm_f64_dev(ctx, n, n, n, A, n, B, n, C, n, prec=prec)
         oo.oo_gemm_check(ctx, n, n, n)
     else:
         batch = max(1, args.batch)
@@ -621,6 +649,7 @@ def main():
     ap.add_argument("--batch-ffts", type=int, default=2048)
     ap.add_argument("--n", type=int, default=4096, help="profiling: GEMM size or FFT length")
     ap.add_argument("--batch", type=int, default=1, help="profiling: FFT batch")
+    ap.add_argument("--prec", choices=["split3", "fp64eq"], default="split3", help="profiling: GEMM pattern")
     ap.add_argument("--ga-seed", type=int, default=2011)
     ap.add_argument("--ga-timeout-ms", type=float, default=3000.0)
     ap.add_argument("--grid", type=int, nargs=3, default=None,

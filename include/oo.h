@@ -247,7 +247,7 @@ oo_status oo_lookup_block(const char *callee, int lang, int *block_id);
 
 /* Sec. 3.2.2 matrix-product block: C = A B for FP64 row-major A (m x k,
  * leading dimension lda >= k), B (k x n, ldb >= n), C (m x n, ldc >= n).
- * prec selects the precision pattern:
+ * Inputs must be finite.  prec selects the precision pattern:
  *   OO_PREC_SPLIT3_BF16  A and B are scaled per row / column by powers of
  *                        two and split into BF16 hi + lo; C = A1 B1 +
  *                        (A1 B2 + A2 B1) on the tensor cores (FP32
@@ -255,17 +255,37 @@ oo_status oo_lookup_block(const char *callee, int lang, int *block_id);
  *                        products summed in FP64.  Error about 5e-5 of
  *                        sum_l |a_il b_lj| per element; callers needing
  *                        FP64 accuracy must not use this mode.
+ *   OO_PREC_FP64EQ       FP64-equivalent (Ozaki-type splitting): every row
+ *                        of A / column of B is cut into s signed BF16 digit
+ *                        slices of beta bits relative to its power-of-two
+ *                        scale; the products of slices with level p + q <= L
+ *                        are formed on the tensor cores in K-blocks small
+ *                        enough that FP32 accumulation is exact, and summed
+ *                        in float-float before widening to FP64.  Error at
+ *                        most ~2.3e-13 of sum_l |a_il b_lj| when the entries
+ *                        of each row of A and column of B are of comparable
+ *                        magnitude (bound ~4 (L+2) 2^(-beta (L-1)) of
+ *                        k max_l|a_il| max_l|b_lj| in general).  oo_gemm_plan
+ *                        reports beta, L and the number of BF16 products.
+ * (Value 1 is reserved for a TF32 split; it is not provided.)
  * oo_gemm_f64: host buffers, synchronous.                                 */
-enum { OO_PREC_SPLIT3_BF16 = 0 };
+enum { OO_PREC_SPLIT3_BF16 = 0, OO_PREC_FP64EQ = 2 };
 oo_status oo_gemm_f64(oo_ctx *ctx, int prec, int m, int n, int k, const double *A, int lda,
                       const double *B, int ldb, double *C, int ldc);
 /* Device buffers (caller-owned), asynchronous on the context's stream; the
  * library's scratch for the split operands is reused across calls.        */
 oo_status oo_gemm_f64_dev(oo_ctx *ctx, int prec, int m, int n, int k, const double *dA, int lda,
                           const double *dB, int ldb, double *dC, int ldc);
-/* After oo_gemm_f64_dev calls of shape (m, n, k): synchronise and report
- * OO_ETIMEOUT if a bounded pipeline wait inside the kernel ran out.       */
+/* After oo_gemm_f64_dev calls of shape (m, n, k) in the precision pattern
+ * last used on this context: synchronise and report OO_ETIMEOUT if a
+ * bounded pipeline wait inside the kernel ran out.                        */
 oo_status oo_gemm_check(oo_ctx *ctx, int m, int n, int k);
+/* The tensor-core work of a product with inner dimension k in pattern prec:
+ * number of BF16 products (each 2 m n k flops; 3 for SPLIT3), digit width
+ * beta (bits, 0 for SPLIT3), level bound L (0 for SPLIT3) and the K-block
+ * over which FP32 accumulation is exact (0 for SPLIT3).  No context needed;
+ * any output pointer may be NULL.                                         */
+oo_status oo_gemm_plan(int prec, int k, int *products, int *beta, int *levels, int *k_block);
 
 /* Sec. 3.2.2 Fourier-transform block: complex128 FFT of length n = 2^k,
  * 0 <= k <= 24, interleaved (re, im) doubles.  dir -1: forward,
@@ -282,6 +302,47 @@ oo_status oo_fft_c128(oo_ctx *ctx, int64_t n, int dir, const double *in, double 
  * context's stream.  batch <= 65535.                                      */
 oo_status oo_fft_c128_dev(oo_ctx *ctx, int64_t n, int batch, int dir, const double *din,
                           double *dout);
+
+/* ------------------------------------ function-block trial (Sec. 4.2.1) */
+/* One call site of a library function in the source, as the code analysis
+ * finds it: the callee's name (matched against the code-pattern table for
+ * `lang`, oo_lookup_block), how often one program run calls it, and the
+ * shape of its arguments.                                                  */
+typedef struct {
+    const char *callee;
+    int32_t lang;        /* OO_LANG_*                                        */
+    int32_t calls;       /* calls per program run, 1..1000                   */
+    int64_t m, n, k;     /* GEMM: C (m x n) = A (m x k) B (k x n), each
+                            1..8192; FFT: forward length n = 2^e <= 2^22     */
+} oo_fb_site;
+
+/* Sec. 4.2.1: every site whose callee the table knows is a candidate; each
+ * combination of candidates offloaded (bit i of a mask = site i runs the
+ * GPU block in precision pattern `prec`, host buffers, synchronous; the
+ * other sites run the original CPU code, an OpenMP DGEMM / radix-2 FFT in
+ * FP64) is run on seeded inputs of the sites' shapes (seed) and timed (wall
+ * ms of all calls of the known sites).  An offloaded result that differs
+ * from the all-CPU result by more than tol (GEMM: max |C-C*|/(|A||B|);
+ * FFT: relative L2) makes that combination infinitely slow.
+ * n_sites 1..12.  Outputs: block_ids[n_sites] (0 = not in the table; may
+ * be NULL), mask_ms[2^n_sites] (infinity for masks that offload an unknown
+ * site or fail tol; may be NULL), the fastest mask (ties: the lower mask)
+ * and its time.                                                            */
+oo_status oo_fb_search(oo_ctx *ctx, const oo_fb_site *sites, int n_sites, int prec, double tol,
+                       uint64_t seed, int32_t *block_ids, double *mask_ms, uint32_t *best_mask,
+                       double *best_ms);
+/* The decision of oo_fb_search on a given table mask_ms[2^n_sites]
+ * (infinity = not allowed), without measuring.  No context needed.         */
+oo_status oo_fb_best(int n_sites, const double *mask_ms, uint32_t *best_mask, double *best_ms);
+/* Sec. 4.2 trial order: function blocks first (oo_fb_search on the sites;
+ * n_sites may be 0), then the loop GA (oo_ga_search) on the Jacobi
+ * program's loop nests, which lie outside every library call site.
+ * Outputs the fastest site mask with its time and the fastest loop gene
+ * with its time.                                                           */
+oo_status oo_offload_search(oo_ctx *ctx, const oo_fb_site *sites, int n_sites, int prec, double tol,
+                            uint64_t seed, const oo_jacobi *prob, int hoist, int pop, int gens, double pc,
+                            double pm, uint64_t ga_seed, double eval_timeout_ms, uint32_t *best_mask,
+                            uint64_t *best_gene, double *fb_ms, double *loop_ms);
 
 /* ----------------------------------------------------------------- serving */
 /* Mixed requests from any number of client threads (C, Python ctypes, Java

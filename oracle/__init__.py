@@ -42,6 +42,8 @@ def lib():
         _lib.oracle_dft.argtypes = [ctypes.c_int64, i, vp, vp]
         _lib.oracle_fft.argtypes = [ctypes.c_int64, i, vp, vp]
         _lib.oracle_fft.restype = i
+        _lib.oracle_fb_best.argtypes = [i, vp, ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(d)]
+        _lib.oracle_fb_best.restype = i
     return _lib
 
 
@@ -163,3 +165,13 @@ def fft(x, direction=-1):
     if lib().oracle_fft(x.size, direction, _p(x), _p(out)) != 0:
         raise ValueError("oracle_fft: length must be a power of two")
     return out
+
+
+# ------------------------------------------------- function-block decision
+def fb_best(times):
+    t = np.ascontiguousarray(times, np.float64)
+    n = t.size.bit_length() - 1
+    bm, bt = ctypes.c_uint32(), ctypes.c_double()
+    if t.size != (1 << n) or lib().oracle_fb_best(n, _p(t), ctypes.byref(bm), ctypes.byref(bt)) != 0:
+        raise ValueError("oracle_fb_best: bad arguments")
+    return bm.value, bt.value

@@ -7,7 +7,7 @@ import os
 import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SOURCES = ["jacobi.c", "plan.c", "ga.c", "gemm.c", "fft.c"]
+SOURCES = ["jacobi.c", "plan.c", "ga.c", "gemm.c", "fft.c", "fb.c"]
 LIB = os.path.join(HERE, "liboracle.so")
 
 

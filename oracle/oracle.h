@@ -112,6 +112,14 @@ void oracle_dft(int64_t n, int dir, const double *in, double *out);
 /* Recursive radix-2 FFT, n a power of two, same conventions.  0 / -1.    */
 int oracle_fft(int64_t n, int dir, const double *in, double *out);
 
+/* --------------------------------------------- function-block decision */
+/* Sec. 4.2.1: given times[2^n_sites] of every combination of offloaded
+ * blocks (bit i = block i on the GPU; INFINITY = result failed the check or
+ * not replaceable), the fastest combination, the lowest mask on ties.
+ * Returns -1 on bad arguments or a NaN entry.  Parity: pinned by hand-made
+ * tables (tests/test_oracle_fb.py).                                       */
+int oracle_fb_best(int n_sites, const double *times, uint32_t *best_mask, double *best_time);
+
 #ifdef __cplusplus
 }
 #endif

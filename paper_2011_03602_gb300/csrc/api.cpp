@@ -13,6 +13,7 @@ struct oo_ctx {
     // cached stencil launch state for oo_stencil_dev (keyed by its arguments)
     StencilPlan *user_plan = nullptr;
     std::vector<const void *> user_key;
+    int gemm_prec = -1;  // precision pattern of the last GEMM launch
 };
 
 namespace oo {
@@ -315,28 +316,52 @@ oo_status oo_fft_c128_dev(oo_ctx *ctx, int64_t n, int batch, int dir, const doub
     });
 }
 
+namespace {
+// host buffers in / out through the context's staging buffers, synchronous
+void fft_host(oo_ctx *ctx, int64_t n, int dir, const double *in, double *out) {
+    FftPlan *p = ctx->c.fft_plan(n);
+    const size_t bytes = (size_t)n * 16;
+    double *d = static_cast<double *>(ctx->c.stage_a.get(bytes));
+    void *scratch = ctx->c.fft_scratch.get(fft_scratch_bytes(p, 1));
+    OO_CUDA_TRY(cudaMemcpyAsync(d, in, bytes, cudaMemcpyHostToDevice, ctx->c.stream));
+    launch_fft(p, 1, dir, d, d, scratch, ctx->c.stream);
+    OO_CUDA_TRY(cudaMemcpyAsync(out, d, bytes, cudaMemcpyDeviceToHost, ctx->c.stream));
+    OO_CUDA_TRY(cudaStreamSynchronize(ctx->c.stream));
+}
+}  // namespace
+
 oo_status oo_fft_c128(oo_ctx *ctx, int64_t n, int dir, const double *in, double *out) {
     if (!ctx) return OO_EINVAL;
     return guarded(ctx, [&] {
         OO_REQUIRE(in && out, OO_EINVAL, "null pointer");
         use_device(ctx->c);
-        FftPlan *p = ctx->c.fft_plan(n);
-        const size_t bytes = (size_t)n * 16;
-        double *d = static_cast<double *>(ctx->c.stage_a.get(bytes));
-        void *scratch = ctx->c.fft_scratch.get(fft_scratch_bytes(p, 1));
-        OO_CUDA_TRY(cudaMemcpyAsync(d, in, bytes, cudaMemcpyHostToDevice, ctx->c.stream));
-        launch_fft(p, 1, dir, d, d, scratch, ctx->c.stream);
-        OO_CUDA_TRY(cudaMemcpyAsync(out, d, bytes, cudaMemcpyDeviceToHost, ctx->c.stream));
-        OO_CUDA_TRY(cudaStreamSynchronize(ctx->c.stream));
+        fft_host(ctx, n, dir, in, out);
     });
 }
 
 namespace {
 void gemm_checks(int prec, int m, int n, int k, int lda, int ldb, int ldc) {
-    OO_REQUIRE(prec == OO_PREC_SPLIT3_BF16, OO_EINVAL, "unsupported precision pattern");
+    OO_REQUIRE(prec == OO_PREC_SPLIT3_BF16 || prec == OO_PREC_FP64EQ, OO_EINVAL, "unsupported precision pattern");
     OO_REQUIRE(m >= 1 && n >= 1 && k >= 1, OO_EINVAL, "m, n, k must be >= 1");
     OO_REQUIRE(m <= (1 << 20) && n <= (1 << 20) && k <= (1 << 21), OO_EINVAL, "matrix too large");
     OO_REQUIRE(lda >= k && ldb >= n && ldc >= n, OO_EINVAL, "leading dimension too small");
+}
+size_t gemm_scratch(int prec, int m, int n, int k) {
+    return prec == OO_PREC_FP64EQ ? gemm_fp64eq_scratch_bytes(m, n, k) : gemm_scratch_bytes(m, n, k);
+}
+void gemm_launch(oo_ctx *ctx, int prec, int m, int n, int k, const double *dA, long long lda, const double *dB,
+                 long long ldb, double *dC, long long ldc, cudaStream_t s) {
+    void *scratch = ctx->c.gemm_scratch.get(gemm_scratch(prec, m, n, k));
+    ctx->gemm_prec = prec;
+    if (prec == OO_PREC_FP64EQ)
+        launch_gemm_fp64eq(m, n, k, dA, lda, dB, ldb, dC, ldc, scratch, s);
+    else
+        launch_gemm_split3(m, n, k, dA, lda, dB, ldb, dC, ldc, scratch, s);
+}
+unsigned gemm_error(oo_ctx *ctx, int m, int n, int k) {
+    void *scratch = ctx->c.gemm_scratch.ptr;
+    if (ctx->gemm_prec == OO_PREC_FP64EQ) return gemm_fp64eq_check_error(scratch, ctx->c.stream);
+    return gemm_check_error(scratch, m, n, k, ctx->c.stream);
 }
 }  // namespace
 
@@ -347,10 +372,37 @@ oo_status oo_gemm_f64_dev(oo_ctx *ctx, int prec, int m, int n, int k, const doub
         OO_REQUIRE(dA && dB && dC, OO_EINVAL, "null pointer");
         gemm_checks(prec, m, n, k, lda, ldb, ldc);
         use_device(ctx->c);
-        void *scratch = ctx->c.gemm_scratch.get(gemm_scratch_bytes(m, n, k));
-        launch_gemm_split3(m, n, k, dA, lda, dB, ldb, dC, ldc, scratch, ctx->c.stream);
+        gemm_launch(ctx, prec, m, n, k, dA, lda, dB, ldb, dC, ldc, ctx->c.stream);
     });
 }
+
+namespace {
+void gemm_host(oo_ctx *ctx, int prec, int m, int n, int k, const double *A, int lda, const double *B, int ldb,
+               double *C, int ldc) {
+    cudaStream_t s = ctx->c.stream;
+    double *dA = static_cast<double *>(ctx->c.stage_a.get((size_t)m * k * 8));
+    double *dB = static_cast<double *>(ctx->c.stage_b.get((size_t)k * n * 8));
+    double *dC = static_cast<double *>(ctx->c.stage_c.get((size_t)m * n * 8));
+    OO_CUDA_TRY(cudaMemcpy2DAsync(dA, (size_t)k * 8, A, (size_t)lda * 8, (size_t)k * 8, m, cudaMemcpyHostToDevice, s));
+    OO_CUDA_TRY(cudaMemcpy2DAsync(dB, (size_t)n * 8, B, (size_t)ldb * 8, (size_t)n * 8, k, cudaMemcpyHostToDevice, s));
+    gemm_launch(ctx, prec, m, n, k, dA, k, dB, n, dC, n, s);
+    OO_CUDA_TRY(cudaMemcpy2DAsync(C, (size_t)ldc * 8, dC, (size_t)n * 8, (size_t)n * 8, m, cudaMemcpyDeviceToHost, s));
+    const unsigned e = gemm_error(ctx, m, n, k);
+    OO_REQUIRE(e == 0, OO_ETIMEOUT, "GEMM pipeline wait ran out (error bits " + std::to_string(e) + ")");
+}
+}  // namespace
+
+namespace {
+// the offloaded form of a function-block site (host buffers, synchronous)
+FbGpu fb_gpu(oo_ctx *ctx) {
+    return [ctx](int prec, int block, const oo_fb_site &s, const double *a, const double *b, double *out) {
+        if (block == OO_BLOCK_GEMM)
+            gemm_host(ctx, prec, (int)s.m, (int)s.n, (int)s.k, a, (int)s.k, b, (int)s.n, out, (int)s.n);
+        else
+            fft_host(ctx, s.n, -1, a, out);
+    };
+}
+}  // namespace
 
 oo_status oo_gemm_f64(oo_ctx *ctx, int prec, int m, int n, int k, const double *A, int lda, const double *B,
                       int ldb, double *C, int ldc) {
@@ -359,17 +411,7 @@ oo_status oo_gemm_f64(oo_ctx *ctx, int prec, int m, int n, int k, const double *
         OO_REQUIRE(A && B && C, OO_EINVAL, "null pointer");
         gemm_checks(prec, m, n, k, lda, ldb, ldc);
         use_device(ctx->c);
-        cudaStream_t s = ctx->c.stream;
-        double *dA = static_cast<double *>(ctx->c.stage_a.get((size_t)m * k * 8));
-        double *dB = static_cast<double *>(ctx->c.stage_b.get((size_t)k * n * 8));
-        double *dC = static_cast<double *>(ctx->c.stage_c.get((size_t)m * n * 8));
-        OO_CUDA_TRY(cudaMemcpy2DAsync(dA, (size_t)k * 8, A, (size_t)lda * 8, (size_t)k * 8, m, cudaMemcpyHostToDevice, s));
-        OO_CUDA_TRY(cudaMemcpy2DAsync(dB, (size_t)n * 8, B, (size_t)ldb * 8, (size_t)n * 8, k, cudaMemcpyHostToDevice, s));
-        void *scratch = ctx->c.gemm_scratch.get(gemm_scratch_bytes(m, n, k));
-        launch_gemm_split3(m, n, k, dA, k, dB, n, dC, n, scratch, s);
-        OO_CUDA_TRY(cudaMemcpy2DAsync(C, (size_t)ldc * 8, dC, (size_t)n * 8, (size_t)n * 8, m, cudaMemcpyDeviceToHost, s));
-        const unsigned e = gemm_check_error(scratch, m, n, k, s);
-        OO_REQUIRE(e == 0, OO_ETIMEOUT, "GEMM pipeline wait ran out (error bits " + std::to_string(e) + ")");
+        gemm_host(ctx, prec, m, n, k, A, lda, B, ldb, C, ldc);
     });
 }
 
@@ -377,10 +419,27 @@ oo_status oo_gemm_check(oo_ctx *ctx, int m, int n, int k) {
     if (!ctx) return OO_EINVAL;
     return guarded(ctx, [&] {
         use_device(ctx->c);
-        OO_REQUIRE(ctx->c.gemm_scratch.ptr && ctx->c.gemm_scratch.bytes >= gemm_scratch_bytes(m, n, k), OO_ESTATE,
-                   "no GEMM of that shape has run on this context");
-        const unsigned e = gemm_check_error(ctx->c.gemm_scratch.ptr, m, n, k, ctx->c.stream);
+        OO_REQUIRE(ctx->gemm_prec >= 0 && ctx->c.gemm_scratch.ptr &&
+                       ctx->c.gemm_scratch.bytes >= gemm_scratch(ctx->gemm_prec, m, n, k),
+                   OO_ESTATE, "no GEMM of that shape has run on this context");
+        const unsigned e = gemm_error(ctx, m, n, k);
         OO_REQUIRE(e == 0, OO_ETIMEOUT, "GEMM pipeline wait ran out (error bits " + std::to_string(e) + ")");
+    });
+}
+
+oo_status oo_gemm_plan(int prec, int k, int *products, int *beta, int *levels, int *k_block) {
+    return guarded(nullptr, [&] {
+        OO_REQUIRE(prec == OO_PREC_SPLIT3_BF16 || prec == OO_PREC_FP64EQ, OO_EINVAL, "unsupported precision pattern");
+        OO_REQUIRE(k >= 1 && k <= (1 << 21), OO_EINVAL, "k out of range");
+        int pr = 3, b = 0, l = 0, kb = 0;
+        if (prec == OO_PREC_FP64EQ) {
+            pr = gemm_fp64eq_products(k);
+            gemm_fp64eq_shape(k, &b, &l, &kb);
+        }
+        if (products) *products = pr;
+        if (beta) *beta = b;
+        if (levels) *levels = l;
+        if (k_block) *k_block = kb;
     });
 }
 
@@ -392,6 +451,54 @@ oo_status oo_lookup_block(const char *callee, int lang, int *block_id) {
         OO_REQUIRE(b != 0, OO_ENOTFOUND, std::string("no code pattern for ") + callee);
         *block_id = b;
     });
+}
+
+oo_status oo_fb_search(oo_ctx *ctx, const oo_fb_site *sites, int n_sites, int prec, double tol, uint64_t seed,
+                       int32_t *block_ids, double *mask_ms, uint32_t *best_mask, double *best_ms) {
+    if (!ctx) return OO_EINVAL;
+    return guarded(ctx, [&] {
+        OO_REQUIRE(best_mask && best_ms, OO_EINVAL, "null pointer");
+        OO_REQUIRE(prec == OO_PREC_SPLIT3_BF16 || prec == OO_PREC_FP64EQ, OO_EINVAL, "unsupported precision pattern");
+        use_device(ctx->c);
+        std::vector<double> ms;
+        std::vector<int> ids;
+        fb_trial(sites, n_sites, prec, tol, seed, ms, ids, fb_gpu(ctx));
+        if (block_ids)
+            for (int i = 0; i < n_sites; ++i) block_ids[i] = ids[i];
+        if (mask_ms) std::memcpy(mask_ms, ms.data(), ms.size() * sizeof(double));
+        *best_mask = fb_best(ms.data(), n_sites, best_ms);
+    });
+}
+
+oo_status oo_fb_best(int n_sites, const double *mask_ms, uint32_t *best_mask, double *best_ms) {
+    return guarded(nullptr, [&] {
+        OO_REQUIRE(n_sites >= 1 && n_sites <= 12, OO_EINVAL, "1..12 function-block sites");
+        OO_REQUIRE(mask_ms && best_mask, OO_EINVAL, "null pointer");
+        for (uint32_t m = 0; m < (1u << n_sites); ++m)
+            OO_REQUIRE(!std::isnan(mask_ms[m]), OO_EINVAL, "NaN in the time table");
+        *best_mask = fb_best(mask_ms, n_sites, best_ms);
+    });
+}
+
+oo_status oo_offload_search(oo_ctx *ctx, const oo_fb_site *sites, int n_sites, int prec, double tol,
+                            uint64_t seed, const oo_jacobi *prob, int hoist, int pop, int gens, double pc,
+                            double pm, uint64_t ga_seed, double eval_timeout_ms, uint32_t *best_mask,
+                            uint64_t *best_gene, double *fb_ms, double *loop_ms) {
+    if (!ctx || !prob) return OO_EINVAL;
+    // Sec. 4.2: function blocks first ...
+    oo_status st = OO_OK;
+    if (n_sites > 0) {
+        st = oo_fb_search(ctx, sites, n_sites, prec, tol, seed, nullptr, nullptr, best_mask, fb_ms);
+        if (st != OO_OK) return st;
+    } else {
+        if (!best_mask || !fb_ms) return OO_EINVAL;
+        *best_mask = 0;
+        *fb_ms = 0.0;
+    }
+    // ... then the loop GA on the code outside them (the program's loop
+    // nests are not part of any library call site)
+    return oo_ga_search(ctx, prob, hoist, pop, gens, pc, pm, ga_seed, eval_timeout_ms, best_gene, loop_ms, nullptr,
+                        nullptr);
 }
 
 }  // extern "C"

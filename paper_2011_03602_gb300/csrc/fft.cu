@@ -257,16 +257,36 @@ __global__ void __launch_bounds__(kFftThreads, 1) fft_pass_kernel(FftArgs a) {
     }
 }
 
-// biased exponent of the largest |re|, |im| of every transform
+// largest biased exponent among the 64-bit words [x0, x1) of p (stride
+// `step` between a thread's 16-byte loads, four loads in flight per thread)
+__device__ __forceinline__ int max_exponent(const ulonglong2 *p, long long x0, long long x1, long long step) {
+    int m = 0;
+    auto ex = [](unsigned long long w) {
+        const int e = (int)((w >> 52) & 0x7ffu);
+        return e == 0x7ff ? 0x7fe : e;
+    };
+    long long x = x0;
+    for (; x + 3 * step < x1; x += 4 * step) {
+        ulonglong2 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = p[x + u * step];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) m = max(m, max(ex(v[u].x), ex(v[u].y)));
+    }
+    for (; x < x1; x += step) {
+        const ulonglong2 v = p[x];
+        m = max(m, max(ex(v.x), ex(v.y)));
+    }
+    return m;
+}
+
+// biased exponent of the largest |re|, |im| of every transform (one complex
+// value = one 16-byte load)
 __global__ void fft_maxexp_kernel(const double *in, long long n, int *expo) {
     const int b = blockIdx.y;
-    const unsigned long long *p = reinterpret_cast<const unsigned long long *>(in) + (long long)b * 2 * n;
-    int m = 0;
-    for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < 2 * n;
-         x += (long long)gridDim.x * blockDim.x) {
-        const int e = (int)((p[x] >> 52) & 0x7ffu);
-        m = max(m, e == 0x7ff ? 0x7fe : e);
-    }
+    const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(in) + (long long)b * n;
+    const long long step = (long long)gridDim.x * blockDim.x;
+    int m = max_exponent(p, (long long)blockIdx.x * blockDim.x + threadIdx.x, n, step);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(expo + b, m);
@@ -303,13 +323,10 @@ struct FftGroupReq {
 
 __global__ void fft_maxexp_group_kernel(const FftGroupReq *reqs, int *expo) {
     const int r = blockIdx.y;
-    const long long cnt = 2ll << reqs[r].log2n;
-    const unsigned long long *p = reinterpret_cast<const unsigned long long *>(reqs[r].in);
-    int m = 0;
-    for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < cnt; x += (long long)gridDim.x * blockDim.x) {
-        const int e = (int)((p[x] >> 52) & 0x7ffu);
-        m = max(m, e == 0x7ff ? 0x7fe : e);
-    }
+    const long long cnt = 1ll << reqs[r].log2n;
+    const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(reqs[r].in);
+    const long long step = (long long)gridDim.x * blockDim.x;
+    int m = max_exponent(p, (long long)blockIdx.x * blockDim.x + threadIdx.x, cnt, step);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(expo + r, m);
@@ -476,10 +493,10 @@ void launch_fft(const FftPlan *p, int batch, int dir, const double *in, double *
                                         (four_step ? (size_t)n * batch * sizeof(float4) : 0));
     OO_CUDA_TRY(cudaMemsetAsync(expo, 0, (size_t)batch * sizeof(int), s));
     {
-        // enough blocks to stream the input at full bandwidth: ~8 doubles per thread
-        const long long per = 2 * n;
-        const int bx = (int)std::max<long long>(1, std::min<long long>(4096 / std::max(1, batch) + 1,
-                                                                         (per + 2047) / 2048));
+        // enough blocks to stream the input at full bandwidth: ~16 complex
+        // values (four 4-deep rounds of 16-byte loads) per thread
+        const int bx = (int)std::max<long long>(1, std::min<long long>(2048 / std::max(1, batch) + 1,
+                                                                         (n + 4095) / 4096));
         OO_REQUIRE(batch <= 65535, OO_EINVAL, "batch above 65535");
         fft_maxexp_kernel<<<dim3(bx, batch), 256, 0, s>>>(in, n, expo);
         OO_CUDA_TRY(cudaGetLastError());
@@ -634,7 +651,7 @@ FftGroup *fft_group_create(const std::vector<FftDesc> &v, const std::vector<cons
         g->nreq = (int)v.size();
         g->grid_a = std::max(1, std::min(g->n_items_a, num_sms));
         g->grid_b = std::max(1, std::min(g->n_items_b, num_sms));
-        g->maxexp_x = (int)std::max<long long>(1, std::min<long long>(16, (2 * maxn + 8191) / 8192));
+        g->maxexp_x = (int)std::max<long long>(1, std::min<long long>(16, (maxn + 4095) / 4096));
         g->elems = elems;
     } catch (...) {
         if (g->arena) cudaFree(g->arena);

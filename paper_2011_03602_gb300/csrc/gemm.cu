@@ -14,12 +14,14 @@
 // plus FP32 accumulation rounding; the result is reported against an FP64
 // oracle, not claimed to be FP64.
 //
-// Kernel: one CTA per 128 x 256 output tile; warp 0 issues TMA loads of the
-// four BF16 operand tiles (128B-swizzled, K-major) into a 2-stage ring,
-// warp 1 allocates 512 TMEM columns and one of its threads issues
-// tcgen05.mma (M=128, N=256, K=16, kind::f16, BF16 x BF16 -> FP32) and
-// tcgen05.commit to release stages; warps 4-7 read the accumulators with
-// tcgen05.ld and write FP64 C.  Every mbarrier wait is bounded.
+// Kernel: persistent, one CTA per SM walking 128 x 128 output tiles in a
+// grouped raster; warp 0 issues TMA loads of the four BF16 operand tiles
+// (128B-swizzled, K-major) into a 3-stage ring, warp 1 allocates 512 TMEM
+// columns (two double-buffered accumulator pairs) and one of its threads
+// issues tcgen05.mma (M=128, N=128, K=16, kind::f16, BF16 x BF16 -> FP32)
+// and tcgen05.commit to release stages; warps 4-7 read finished
+// accumulators with tcgen05.ld and write FP64 C while the next tile
+// accumulates.  Every mbarrier wait is bounded.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -29,6 +31,7 @@
 
 #include "ff.cuh"
 #include "oo_internal.h"
+#include "tc.cuh"
 
 namespace oo {
 
@@ -40,92 +43,9 @@ constexpr uint32_t kTileA = kBM * kBK * 2;   // 16 KB
 constexpr uint32_t kTileB = kBN * kBK * 2;   // 16 KB
 constexpr uint32_t kStageBytes = 2 * kTileA + 2 * kTileB;  // 64 KB
 constexpr int kGroupM = 8;                   // tile raster: groups of 8 m-tiles share B panels in L2
-constexpr long long kGemmWaitLimit = 2000000000ll;
 
-__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void bar_init(uint32_t b, uint32_t c) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b), "r"(c) : "memory");
-}
-__device__ __forceinline__ void bar_expect_tx(uint32_t b, uint32_t bytes) {
-    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(b),
-                 "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void bar_arrive(uint32_t b) {
-    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(b) : "memory");
-}
-__device__ __forceinline__ bool bar_try(uint32_t b, uint32_t par) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred P;\n\tmbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n\tselp.u32 %0, 1, 0, P;\n\t}"
-        : "=r"(ok)
-        : "r"(b), "r"(par)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ bool bar_wait(uint32_t b, uint32_t par, volatile int *abort_flag, unsigned *err,
-                                         unsigned code) {
-    if (bar_try(b, par)) return true;
-    const long long t0 = clock64();
-    while (true) {
-        if (bar_try(b, par)) return true;
-        if (*abort_flag) return false;
-        if (clock64() - t0 > kGemmWaitLimit) {
-            *abort_flag = 1;
-            atomicOr(err, code);
-            return false;
-        }
-    }
-}
-__device__ __forceinline__ void tma_2d(uint32_t dst, const CUtensorMap *map, int c0, int c1, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
-        : "memory");
-}
-
-// ---- tcgen05 helpers
-// Shared-memory matrix descriptor: K-major operand tile stored as rows of
-// 128 bytes (64 BF16) with the 128-byte swizzle that TMA SWIZZLE_128B writes;
-// 8-row core groups 1024 bytes apart (SBO); LBO unused for this layout.
-__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t addr) {
-    uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)1 << 16;                 // LBO (encoded 16 B; ignored)
-    d |= (uint64_t)(1024u >> 4) << 32;      // SBO = 1024 B
-    d |= (uint64_t)1 << 46;                 // descriptor version
-    d |= (uint64_t)2 << 61;                 // 128-byte swizzle
-    return d;
-}
-// Instruction descriptor, kind::f16: D=F32, A=B=BF16, both K-major, M=128, N=128
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBN >> 3) << 17) |
-                            ((uint32_t)(kBM >> 4) << 24);
-
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(a), "l"(b), "r"(kIdesc), "r"(acc)
-        : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                 : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-#define OO_TMEM_LD32(taddr, r)                                                                              \
-    asm volatile(                                                                                           \
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"   \
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"                           \
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),   \
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),          \
-          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),        \
-          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),        \
-          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])                                                             \
-        : "r"(taddr))
+using namespace tc;
+constexpr uint32_t kIdesc = idesc_bf16(kBM, kBN);
 
 struct GemmMaps {
     CUtensorMap a1, a2, b1, b2;
@@ -229,10 +149,10 @@ __device__ __forceinline__ void gemm_body(const Src &src, unsigned *err) {
                      "r"(512)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-        tc_fence_before();
+        fence_before();
     }
     __syncthreads();
-    tc_fence_after();
+    fence_after();
     const uint32_t tmem = *tmem_slot;
 
     int loaded = 0;          // producer: stages issued
@@ -269,7 +189,7 @@ __device__ __forceinline__ void gemm_body(const Src &src, unsigned *err) {
             const int b = lt & 1;
             const uint32_t buse = lt >> 1;
             if (buse > 0 && !bar_wait(su32(&tempty[b]), (buse - 1) & 1, abort_flag, err, 2u)) break;
-            tc_fence_after();
+            fence_after();
             const uint32_t d_hh = tmem + (uint32_t)(b * 256), d_x = d_hh + 128;
             const int ksteps = src.job(t).ksteps;
             for (int ks = 0; ks < ksteps; ++ks, ++it) {
@@ -279,16 +199,16 @@ __device__ __forceinline__ void gemm_body(const Src &src, unsigned *err) {
                     ok = false;
                     break;
                 }
-                tc_fence_after();
+                fence_after();
                 const uint32_t base = su32(gsm + (size_t)s * kStageBytes);
                 const uint32_t a1 = base, a2 = base + kTileA, b1 = base + 2 * kTileA, b2 = b1 + kTileB;
 #pragma unroll
                 for (int kk = 0; kk < kBK / 16; ++kk) {
                     const uint32_t off = kk * 32;  // 16 BF16 along K inside the 128-byte row
                     const uint32_t acc = (ks == 0 && kk == 0) ? 0u : 1u;
-                    mma_bf16(d_hh, sdesc_sw128(a1 + off), sdesc_sw128(b1 + off), acc);
-                    mma_bf16(d_x, sdesc_sw128(a1 + off), sdesc_sw128(b2 + off), acc);
-                    mma_bf16(d_x, sdesc_sw128(a2 + off), sdesc_sw128(b1 + off), 1u);
+                    mma_bf16<kIdesc>(d_hh, sdesc_sw128(a1 + off), sdesc_sw128(b1 + off), acc);
+                    mma_bf16<kIdesc>(d_x, sdesc_sw128(a1 + off), sdesc_sw128(b2 + off), acc);
+                    mma_bf16<kIdesc>(d_x, sdesc_sw128(a2 + off), sdesc_sw128(b1 + off), 1u);
                 }
                 mma_commit(su32(&empty[s]));
             }
@@ -302,7 +222,7 @@ __device__ __forceinline__ void gemm_body(const Src &src, unsigned *err) {
         for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++lt) {
             const int b = lt & 1;
             if (!bar_wait(su32(&tfull[b]), (lt >> 1) & 1, abort_flag, err, 4u)) break;
-            tc_fence_after();
+            fence_after();
             const TileJob jb = src.job(t);
             const int n0 = jb.n0;
             const int row = jb.m0 + q * 32 + lane;
@@ -328,7 +248,7 @@ __device__ __forceinline__ void gemm_body(const Src &src, unsigned *err) {
                     }
                 }
             }
-            tc_fence_before();
+            fence_before();
             __syncwarp();
             if (lane == 0) bar_arrive(su32(&tempty[b]));
         }
@@ -339,21 +259,21 @@ __device__ __forceinline__ void gemm_body(const Src &src, unsigned *err) {
         if (warp == 1 && lane == 0 && tiles_mma > 0) {
             const int lb = (tiles_mma - 1) & 1;
             const long long t0 = clock64();
-            while (!bar_try(su32(&tfull[lb]), ((tiles_mma - 1) >> 1) & 1) && clock64() - t0 < kGemmWaitLimit) {
+            while (!bar_try(su32(&tfull[lb]), ((tiles_mma - 1) >> 1) & 1) && clock64() - t0 < kWaitLimit) {
             }
         }
         if (warp == 0 && lane == 0) {
             for (int it = (loaded > kStages ? loaded - kStages : 0); it < loaded; ++it) {
                 const long long t0 = clock64();
-                while (!bar_try(su32(&full[it % kStages]), (it / kStages) & 1) && clock64() - t0 < kGemmWaitLimit) {
+                while (!bar_try(su32(&full[it % kStages]), (it / kStages) & 1) && clock64() - t0 < kWaitLimit) {
                 }
             }
         }
     }
-    tc_fence_before();
+    fence_before();
     __syncthreads();
     if (warp == 1) {
-        tc_fence_after();
+        fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
     }
 }
@@ -532,30 +452,6 @@ __global__ void split_b_group_kernel(const GroupSplit *gs, const int3 *jobs) {
     const int3 jb = jobs[blockIdx.x];
     const GroupSplit &G = gs[jb.x];
     split_b_tile(G.B, G.ldb, G.k, G.n, G.kp, G.eb, G.B1, G.B2, jb.z, jb.y);
-}
-
-PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    if (!fn) {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q{};
-        OO_CUDA_TRY(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
-        OO_REQUIRE(q == cudaDriverEntryPointSuccess && p != nullptr, OO_ECUDA, "driver has no cuTensorMapEncodeTiled");
-        fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    }
-    return fn;
-}
-
-void map_bf16(CUtensorMap *m, const void *base, int rows, int kp, int box_rows) {
-    OO_REQUIRE(((uintptr_t)base & 15u) == 0, OO_EINVAL, "split operand must be 16-byte aligned");
-    const cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
-    const cuuint64_t strides[1] = {(cuuint64_t)kp * 2};
-    const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
-    const cuuint32_t es[2] = {1, 1};
-    const CUresult r = encode_tiled()(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims,
-                                      strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    OO_REQUIRE(r == CUDA_SUCCESS, OO_ECUDA, "cuTensorMapEncodeTiled (GEMM) failed: " + std::to_string((int)r));
 }
 
 size_t smem_gemm() { return 1024 + (size_t)kStages * kStageBytes + 256; }

@@ -1,0 +1,512 @@
+// FP64-equivalent matrix product (precision pattern OO_PREC_FP64EQ) for the
+// matrix-product function block (Sec. 3.2.2): C = A B for FP64 row-major
+// A (m x k) and B (k x n), computed on the BF16 tensor cores by an
+// Ozaki-type error-free splitting (Ozaki, Ogita, Oishi, Rump 2012):
+//
+//   a_il = 2^ea_i * sum_{p=1..s} d^A_p(i,l) 2^(-beta p) + r   (|r| < 2^(ea_i - beta s))
+//   b_lj = 2^eb_j * sum_{q=1..s} d^B_q(l,j) 2^(-beta q) + r'
+//
+// Each digit d is a signed integer with |d| <= 2^beta - 1, read directly
+// as a beta-bit group of the entry's fixed-point mantissa relative to its
+// row (A) or column (B) scale 2^e (no floating-point arithmetic in the
+// split).  Digits are exact in BF16 (beta <= 8), their products exact in
+// FP32, and with K-blocks of kb terms, kb (2^beta - 1)^2 < 2^24, every
+// product's K-block sum D_pq = sum_l d^A_p d^B_q accumulates exactly in the
+// FP32 accumulators of tensor memory, whatever order the hardware adds in.
+//
+//   C_ij = 2^(ea_i + eb_j) sum_{p + q <= L} 2^(-beta (p + q)) D_pq(i, j)
+//
+// The terms are summed in float-float (about 48 bits) in tensor memory,
+// smallest level first, then widened to FP64 and scaled.  Dropping the
+// levels p + q > L and the split remainders costs at most about
+// (L + 2) 2^(-beta (L - 1)) 2^(ea_i + eb_j) k per element; L is the
+// smallest level for which 4 (L + 2) 2^(-beta (L - 1)) <= 2^-42, i.e. at
+// most ~2.3e-13 of sum_l |a_il| |b_lj| when the entries of a row (column)
+// are of comparable size.
+//
+//   K-block kb = min(roundup64(k), 1024);  beta = 8 (kb <= 256) or 7;
+//   beta 8: L = 7 (21 products); beta 7: L = 8 (28 products).
+//
+// Kernel: persistent, one CTA per SM over 128 x 128 output tiles.  A unit
+// of work is one (product, K-block): warp 0 streams the A_p and B_q tiles of
+// the unit (TMA, 128-byte swizzle) through a 7-stage ring, warp 1 issues
+// tcgen05.mma (M = N = 128, K = 16) into one of two FP32 accumulators in
+// tensor memory (columns 0-255), warps 4-7 add each finished accumulator,
+// scaled by 2^(-beta (p + q)), into a float-float running sum held in
+// tensor memory (columns 256-511) and, after the tile's last unit, write
+// FP64 C.  Every mbarrier wait is bounded.
+// Inputs must be finite.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "ff.cuh"
+#include "oo_internal.h"
+#include "tc.cuh"
+
+namespace oo {
+
+namespace {
+
+using namespace tc;
+
+constexpr int kBM = 128, kBN = 128, kBK = 64, kStages = 7;
+constexpr int kThreads = 256;
+constexpr uint32_t kTile = kBM * kBK * 2;  // 16 KB, A and B tiles alike
+constexpr uint32_t kStageBytes = 2 * kTile;
+constexpr int kGroupM = 8;
+constexpr int kMaxProducts = 36;
+constexpr uint32_t kIdesc = idesc_bf16(kBM, kBN);
+
+struct EqShape {
+    int beta, levels, slices, kb, nkb, nprod;
+};
+
+EqShape eq_shape(int k) {
+    EqShape e{};
+    const int kp = (k + kBK - 1) / kBK * kBK;
+    e.kb = std::min(kp, 1024);
+    e.beta = e.kb <= 256 ? 8 : 7;
+    // smallest L with 4 (L + 2) 2^(-beta (L - 1)) <= 2^-42
+    int L = 2;
+    while (std::log2(4.0 * (L + 2)) - e.beta * (L - 1) > -42.0) ++L;
+    e.levels = L;
+    e.slices = L - 1;
+    e.nkb = (kp + e.kb - 1) / e.kb;
+    e.nprod = L * (L - 1) / 2;
+    return e;
+}
+
+struct EqMaps {
+    CUtensorMap a, b;  // all slices stacked: slice p at rows [p m, (p + 1) m)
+};
+
+struct EqArgs {
+    int m, n, ksteps, kb_steps, nkb, nprod;
+    int m_tiles, n_tiles;
+    double *C;
+    long long ldc;
+    const int *ea, *eb;
+    unsigned *err;
+    unsigned char prod_p[kMaxProducts], prod_q[kMaxProducts];  // 0-based slice indices
+    float prod_scale[kMaxProducts];                             // 2^(-beta (p + q)), 1-based p, q
+};
+
+__device__ __forceinline__ void eq_tile(const EqArgs &a, int t, int &m0, int &n0) {
+    const int per_group = kGroupM * a.n_tiles;
+    const int g = t / per_group, r = t % per_group;
+    const int rows = min(kGroupM, a.m_tiles - g * kGroupM);
+    m0 = (g * kGroupM + r % rows) * kBM;
+    n0 = (r / rows) * kBN;
+}
+
+__global__ void __launch_bounds__(kThreads, 1) gemm_fp64eq_kernel(const __grid_constant__ EqMaps maps,
+                                                                 const __grid_constant__ EqArgs a) {
+    extern __shared__ __align__(1024) unsigned char esm_raw[];
+    unsigned char *sm = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(esm_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + kStages * kStageBytes);
+    uint64_t *full = bars, *empty = bars + kStages;
+    uint64_t *tfull = bars + 2 * kStages, *tempty = bars + 2 * kStages + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * kStages + 4);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tiles = a.m_tiles * a.n_tiles;
+    const int units = a.nprod * a.nkb;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            bar_init(su32(&full[s]), 1);
+            bar_init(su32(&empty[s]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            bar_init(su32(&tfull[b]), 1);
+            bar_init(su32(&tempty[b]), 4);  // one arrival per epilogue warp
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        tmem_alloc(su32(tmem_slot), 512);
+        fence_before();
+    }
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    int loaded = 0;      // producer: stages issued
+    int units_mma = 0;   // MMA issuer: units whose accumulation was issued
+    if (warp == 0 && lane == 0) {
+        // ---------------------------------------------------- TMA producer
+        int it = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; ok && t < tiles; t += gridDim.x) {
+            int m0, n0;
+            eq_tile(a, t, m0, n0);
+            for (int u = 0; ok && u < units; ++u) {
+                const int pr = u / a.nkb, kbi = u % a.nkb;
+                const int rowA = a.prod_p[pr] * a.m + m0, rowB = a.prod_q[pr] * a.n + n0;
+                const int ks1 = min(a.ksteps, (kbi + 1) * a.kb_steps);
+                for (int ks = kbi * a.kb_steps; ks < ks1; ++ks, ++it) {
+                    const int s = it % kStages;
+                    const uint32_t use = it / kStages;
+                    if (use > 0 && !bar_wait(su32(&empty[s]), (use - 1) & 1, abort_flag, a.err, 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    unsigned char *st = sm + (size_t)s * kStageBytes;
+                    const uint32_t fb = su32(&full[s]);
+                    bar_expect_tx(fb, kStageBytes);
+                    tma_2d(su32(st), &maps.a, ks * kBK, rowA, fb);
+                    tma_2d(su32(st + kTile), &maps.b, ks * kBK, rowB, fb);
+                    ++loaded;
+                }
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------------------------------------------- MMA issuer
+        int it = 0, gu = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; ok && t < tiles; t += gridDim.x) {
+            for (int u = 0; ok && u < units; ++u, ++gu) {
+                const int b = gu & 1;
+                const uint32_t buse = gu >> 1;
+                if (buse > 0 && !bar_wait(su32(&tempty[b]), (buse - 1) & 1, abort_flag, a.err, 2u)) {
+                    ok = false;
+                    break;
+                }
+                fence_after();
+                const uint32_t d = tmem + (uint32_t)(b * kBN);
+                const int kbi = u % a.nkb;
+                const int ks0 = kbi * a.kb_steps, ks1 = min(a.ksteps, (kbi + 1) * a.kb_steps);
+                for (int ks = ks0; ks < ks1; ++ks, ++it) {
+                    const int s = it % kStages;
+                    if (!bar_wait(su32(&full[s]), (it / kStages) & 1, abort_flag, a.err, 2u)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    const uint32_t sa = su32(sm + (size_t)s * kStageBytes), sb = sa + kTile;
+#pragma unroll
+                    for (int kk = 0; kk < kBK / 16; ++kk) {
+                        const uint32_t off = kk * 32;  // 16 BF16 along K inside the 128-byte row
+                        mma_bf16<kIdesc>(d, sdesc_sw128(sa + off), sdesc_sw128(sb + off),
+                                         (ks == ks0 && kk == 0) ? 0u : 1u);
+                    }
+                    mma_commit(su32(&empty[s]));
+                }
+                if (!ok) break;
+                mma_commit(su32(&tfull[b]));  // this unit's accumulator is complete
+                ++units_mma;
+            }
+        }
+    } else if (warp >= 4) {
+        // ---------------------------------------------------- epilogue
+        const int q = warp - 4;  // TMEM lane quarter
+        const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+        const uint32_t sum_hi = tmem + 256 + lane_off, sum_lo = tmem + 384 + lane_off;
+        int gu = 0;
+        bool ok = true;
+        for (int t = blockIdx.x; ok && t < tiles; t += gridDim.x) {
+            int m0, n0;
+            eq_tile(a, t, m0, n0);
+            const int row = m0 + q * 32 + lane;
+            const bool row_ok = row < a.m;
+            const int sa = row_ok ? a.ea[row] : 0;
+            double *crow = a.C + (long long)row * a.ldc;
+            for (int u = 0; u < units; ++u, ++gu) {
+                const int b = gu & 1;
+                if (!bar_wait(su32(&tfull[b]), (gu >> 1) & 1, abort_flag, a.err, 4u)) {
+                    ok = false;
+                    break;
+                }
+                fence_after();
+                const bool first = u == 0, last = u == units - 1;
+                const float f = a.prod_scale[u / a.nkb];
+                const uint32_t acc = tmem + (uint32_t)(b * kBN) + lane_off;
+                for (int c = 0; c < kBN; c += 32) {
+                    uint32_t v[32], h[32], l[32];
+                    OO_TMEM_LD32(acc + c, v);
+                    if (!first) {
+                        OO_TMEM_LD32(sum_hi + c, h);
+                        OO_TMEM_LD32(sum_lo + c, l);
+                    }
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const float w = __fmul_rn(__uint_as_float(v[j]), f);  // exact: power-of-two scale
+                        float H = w, L = 0.0f;
+                        if (!first) ff::add(__uint_as_float(h[j]), __uint_as_float(l[j]), w, 0.0f, H, L);
+                        h[j] = __float_as_uint(H);
+                        l[j] = __float_as_uint(L);
+                    }
+                    if (last) {
+                        if (row_ok) {
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) {
+                                const int col = n0 + c + j;
+                                if (col < a.n) {
+                                    const double x = ff::to_double(__uint_as_float(h[j]), __uint_as_float(l[j]));
+                                    crow[col] = ff::scale_pow2(x, sa + a.eb[col]);
+                                }
+                            }
+                        }
+                    } else {
+                        OO_TMEM_ST32(sum_hi + c, h);
+                        OO_TMEM_ST32(sum_lo + c, l);
+                    }
+                }
+                if (!last) tmem_wait_st();
+                fence_before();
+                __syncwarp();
+                if (lane == 0) bar_arrive(su32(&tempty[b]));
+            }
+        }
+    }
+    // drain on abort: wait (bounded) for issued MMAs and copies before TMEM
+    // is released and the CTA exits
+    if (*abort_flag) {
+        if (warp == 1 && lane == 0 && units_mma > 0)
+            bar_drain(su32(&tfull[(units_mma - 1) & 1]), ((units_mma - 1) >> 1) & 1);
+        if (warp == 0 && lane == 0)
+            for (int it = (loaded > kStages ? loaded - kStages : 0); it < loaded; ++it)
+                bar_drain(su32(&full[it % kStages]), (it / kStages) & 1);
+    }
+    fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
+// ------------------------------------------------------------ splitting
+// Exponent field used for the scale: subnormals count as exponent 1, zero
+// as 0 (no contribution).
+__device__ __forceinline__ int eff_exp(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ff);
+    if (e != 0) return e == 0x7ff ? 0x7fe : e;
+    return (b & 0x000fffffffffffffull) ? 1 : 0;
+}
+
+// |x| * 2^(64 - E) as a 64-bit fixed-point fraction (truncated), where
+// 2^E = 2^(mx - 1022) bounds the row / column; the sign separately.
+__device__ __forceinline__ unsigned long long fixed_frac(double x, int mx, unsigned &neg) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    neg = (unsigned)(b >> 63);
+    int e = (int)((b >> 52) & 0x7ff);
+    unsigned long long m = b & 0x000fffffffffffffull;
+    if (e == 0) {
+        if (m == 0) return 0ull;
+        e = 1;
+    } else {
+        m |= 1ull << 52;
+    }
+    // x = m 2^(e - 1075), X = x 2^(64 - (mx - 1022)) = m 2^(e - mx + 11)
+    const int sh = e - mx + 11;
+    if (sh >= 0) return m << sh;  // sh <= 11: m < 2^53 keeps X < 2^64
+    if (sh <= -64) return 0ull;
+    return m >> (-sh);
+}
+
+// digit p (0-based) of X as a signed BF16 integer
+__device__ __forceinline__ __nv_bfloat16 digit(unsigned long long X, unsigned neg, int beta, int p) {
+    const unsigned d = (unsigned)(X >> (64 - beta * (p + 1))) & ((1u << beta) - 1u);
+    const float f = __uint2float_rn(d);
+    return __float2bfloat16_rn(neg ? -f : f);
+}
+
+// A (m x k, lda) -> ea and slices As[p] (m x kp each, p < s); one warp per row
+__global__ void eq_split_rows_kernel(const double *A, long long lda, int m, int k, int kp, int beta, int s,
+                                     int *ea, __nv_bfloat16 *As) {
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (row >= m) return;
+    const int lane = threadIdx.x & 31;
+    const double *src = A + (long long)row * lda;
+    int mx = 0;
+#pragma unroll 4
+    for (int l = lane; l < k; l += 32) mx = max(mx, eff_exp(src[l]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) ea[row] = mx == 0 ? 0 : mx - 1022;
+    const size_t plane = (size_t)m * kp;
+    __nv_bfloat162 *dst = reinterpret_cast<__nv_bfloat162 *>(As + (size_t)row * kp);
+    for (int l2 = lane; l2 < kp / 2; l2 += 32) {
+        const int l = 2 * l2;
+        unsigned n0 = 0, n1 = 0;
+        const unsigned long long X0 = (mx != 0 && l < k) ? fixed_frac(src[l], mx, n0) : 0ull;
+        const unsigned long long X1 = (mx != 0 && l + 1 < k) ? fixed_frac(src[l + 1], mx, n1) : 0ull;
+        for (int p = 0; p < s; ++p)
+            dst[p * (plane / 2) + l2] = __halves2bfloat162(digit(X0, n0, beta, p), digit(X1, n1, beta, p));
+    }
+}
+
+// largest effective exponent of each column of B (k x n); grid.x column
+// blocks of 32, grid.y row chunks
+__global__ void eq_col_maxexp_kernel(const double *B, long long ldb, int k, int n, int rows_per, int *mxo) {
+    const int col = blockIdx.x * 32 + threadIdx.x;
+    const int r0 = blockIdx.y * rows_per, r1 = min(k, r0 + rows_per);
+    if (col >= n) return;
+    int mx = 0;
+#pragma unroll 8
+    for (int l = r0 + threadIdx.y; l < r1; l += blockDim.y) mx = max(mx, eff_exp(B[(long long)l * ldb + col]));
+    if (mx > 0) atomicMax(mxo + col, mx);
+}
+
+// B tile of 64 (k) x 64 (columns) -> transposed slices Bs[q] (n x kp each);
+// mxo holds the column maxima (exponent fields); 256 threads
+__global__ void eq_split_cols_t_kernel(const double *B, long long ldb, int k, int n, int kp, int beta, int s,
+                                       const int *mxo, __nv_bfloat16 *Bs) {
+    __shared__ double t[64][65];
+    const int c0 = blockIdx.x * 64, l0 = blockIdx.y * 64;
+    const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
+#pragma unroll 4
+    for (int yy = ty; yy < 64; yy += 4) {
+        const int l = l0 + yy, c = c0 + tx;
+        t[yy][tx] = (l < k && c < n) ? B[(long long)l * ldb + c] : 0.0;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const size_t plane = (size_t)n * kp;
+    for (int cc = w * 8; cc < w * 8 + 8; ++cc) {
+        const int c = c0 + cc;
+        if (c >= n) break;
+        const int mx = mxo[c];
+        unsigned n0 = 0, n1 = 0;
+        const unsigned long long X0 = mx != 0 ? fixed_frac(t[2 * lane][cc], mx, n0) : 0ull;
+        const unsigned long long X1 = mx != 0 ? fixed_frac(t[2 * lane + 1][cc], mx, n1) : 0ull;
+        __nv_bfloat162 *dst = reinterpret_cast<__nv_bfloat162 *>(Bs + (size_t)c * kp + l0) + lane;
+        for (int p = 0; p < s; ++p)
+            dst[p * (plane / 2)] = __halves2bfloat162(digit(X0, n0, beta, p), digit(X1, n1, beta, p));
+    }
+}
+
+__global__ void eq_col_scale_kernel(const int *mxo, int *eb, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) eb[i] = mxo[i] == 0 ? 0 : mxo[i] - 1022;
+}
+
+size_t smem_eq() { return 1024 + (size_t)kStages * kStageBytes + 256; }
+
+struct EqLayout {
+    size_t err, ea, eb, mxo, as, bs, total;
+};
+EqLayout eq_layout(int m, int n, int k) {
+    const EqShape e = eq_shape(k);
+    const size_t kp = (size_t)(k + kBK - 1) / kBK * kBK;
+    auto up = [](size_t x) { return (x + 255) / 256 * 256; };
+    EqLayout L{};
+    L.err = 0;
+    L.ea = 256;
+    L.eb = L.ea + up((size_t)m * 4);
+    L.mxo = L.eb + up((size_t)n * 4);
+    L.as = L.mxo + up((size_t)n * 4);
+    L.bs = L.as + up((size_t)e.slices * m * kp * 2);
+    L.total = L.bs + up((size_t)e.slices * n * kp * 2);
+    return L;
+}
+
+}  // namespace
+
+size_t gemm_fp64eq_scratch_bytes(int m, int n, int k) { return eq_layout(m, n, k).total; }
+
+int gemm_fp64eq_products(int k) { return eq_shape(k).nprod; }
+
+void gemm_fp64eq_shape(int k, int *beta, int *levels, int *k_block) {
+    const EqShape e = eq_shape(k);
+    if (beta) *beta = e.beta;
+    if (levels) *levels = e.levels;
+    if (k_block) *k_block = e.kb;
+}
+
+void launch_gemm_fp64eq(int m, int n, int k, const double *A, long long lda, const double *B, long long ldb,
+                        double *C, long long ldc, void *scratch, cudaStream_t s) {
+    OO_REQUIRE(m >= 1 && n >= 1 && k >= 1, OO_EINVAL, "m, n, k must be >= 1");
+    OO_REQUIRE(lda >= k && ldb >= n && ldc >= n, OO_EINVAL, "leading dimensions too small");
+    const EqShape e = eq_shape(k);
+    OO_REQUIRE(e.nprod <= kMaxProducts, OO_EINVAL, "too many products");
+    OO_REQUIRE((long long)e.slices * m < (1ll << 31) && (long long)e.slices * n < (1ll << 31), OO_EINVAL,
+               "matrix too large for the FP64-equivalent mode");
+    const int kp = (k + kBK - 1) / kBK * kBK;
+    const EqLayout L = eq_layout(m, n, k);
+    char *p = static_cast<char *>(scratch);
+    unsigned *err = reinterpret_cast<unsigned *>(p + L.err);
+    int *ea = reinterpret_cast<int *>(p + L.ea), *eb = reinterpret_cast<int *>(p + L.eb);
+    int *mxo = reinterpret_cast<int *>(p + L.mxo);
+    auto *As = reinterpret_cast<__nv_bfloat16 *>(p + L.as);
+    auto *Bs = reinterpret_cast<__nv_bfloat16 *>(p + L.bs);
+    OO_CUDA_TRY(cudaMemsetAsync(err, 0, 4, s));
+    OO_CUDA_TRY(cudaMemsetAsync(mxo, 0, (size_t)n * 4, s));
+    {
+        const int rows_per = 256;
+        dim3 grid((n + 31) / 32, (k + rows_per - 1) / rows_per), block(32, 8);
+        OO_REQUIRE(grid.y <= 65535, OO_EINVAL, "k too large");
+        eq_col_maxexp_kernel<<<grid, block, 0, s>>>(B, ldb, k, n, rows_per, mxo);
+        OO_CUDA_TRY(cudaGetLastError());
+        eq_col_scale_kernel<<<(n + 255) / 256, 256, 0, s>>>(mxo, eb, n);
+        OO_CUDA_TRY(cudaGetLastError());
+    }
+    eq_split_rows_kernel<<<(m + 7) / 8, 256, 0, s>>>(A, lda, m, k, kp, e.beta, e.slices, ea, As);
+    OO_CUDA_TRY(cudaGetLastError());
+    {
+        dim3 grid((n + 63) / 64, kp / 64);
+        OO_REQUIRE(grid.y <= 65535, OO_EINVAL, "k too large");
+        eq_split_cols_t_kernel<<<grid, 256, 0, s>>>(B, ldb, k, n, kp, e.beta, e.slices, mxo, Bs);
+        OO_CUDA_TRY(cudaGetLastError());
+    }
+    EqMaps maps;
+    map_bf16(&maps.a, As, (long long)e.slices * m, kp, kBM);
+    map_bf16(&maps.b, Bs, (long long)e.slices * n, kp, kBN);
+    EqArgs ga{};
+    ga.m = m;
+    ga.n = n;
+    ga.ksteps = kp / kBK;
+    ga.kb_steps = e.kb / kBK;
+    ga.nkb = e.nkb;
+    ga.nprod = e.nprod;
+    ga.m_tiles = (m + kBM - 1) / kBM;
+    ga.n_tiles = (n + kBN - 1) / kBN;
+    ga.C = C;
+    ga.ldc = ldc;
+    ga.ea = ea;
+    ga.eb = eb;
+    ga.err = err;
+    // products (p, q), 1-based, p + q <= L, ordered from the smallest level up
+    int np = 0;
+    for (int lev = e.levels; lev >= 2; --lev)
+        for (int pp = 1; pp < lev; ++pp) {
+            ga.prod_p[np] = (unsigned char)(pp - 1);
+            ga.prod_q[np] = (unsigned char)(lev - pp - 1);
+            ga.prod_scale[np] = std::ldexp(1.0f, -e.beta * lev);
+            ++np;
+        }
+    static bool attr = false;
+    if (!attr) {
+        OO_CUDA_TRY(cudaFuncSetAttribute(gemm_fp64eq_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_eq()));
+        attr = true;
+    }
+    const long long tiles = (long long)ga.m_tiles * ga.n_tiles;
+    OO_REQUIRE(tiles < (1ll << 31), OO_EINVAL, "too many tiles");
+    int dev = 0, sms = 148;
+    OO_CUDA_TRY(cudaGetDevice(&dev));
+    OO_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int grid = (int)std::min<long long>(tiles, sms);
+    gemm_fp64eq_kernel<<<grid, kThreads, smem_eq(), s>>>(maps, ga);
+    OO_CUDA_TRY(cudaGetLastError());
+}
+
+unsigned gemm_fp64eq_check_error(void *scratch, cudaStream_t s) {
+    unsigned *err = static_cast<unsigned *>(scratch);
+    unsigned e = 0;
+    OO_CUDA_TRY(cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, s));
+    OO_CUDA_TRY(cudaStreamSynchronize(s));
+    if (e) OO_CUDA_TRY(cudaMemsetAsync(err, 0, 4, s));
+    return e;
+}
+
+}  // namespace oo

@@ -103,6 +103,13 @@ void launch_gemm_split3(int m, int n, int k, const double *A, long long lda, con
                         double *C, long long ldc, void *scratch, cudaStream_t s);
 // reads and clears the kernel's error word (0 = fine); synchronises s
 unsigned gemm_check_error(void *scratch, int m, int n, int k, cudaStream_t s);
+// FP64-equivalent mode (gemm_fp64eq.cu): Ozaki-type BF16 digit slices
+size_t gemm_fp64eq_scratch_bytes(int m, int n, int k);
+int gemm_fp64eq_products(int k);
+void gemm_fp64eq_shape(int k, int *beta, int *levels, int *k_block);
+void launch_gemm_fp64eq(int m, int n, int k, const double *A, long long lda, const double *B, long long ldb,
+                        double *C, long long ldc, void *scratch, cudaStream_t s);
+unsigned gemm_fp64eq_check_error(void *scratch, cudaStream_t s);
 
 // Grouped FFTs (batched function blocks): transforms of different lengths
 // and directions in two persistent launches.
@@ -255,5 +262,14 @@ GaResult ga_run(int L, int pop, int gens, double pc, double pm, uint64_t seed,
 
 // Function-block lookup (blocks.cpp).
 int lookup_block(const char *callee, int lang);
+
+// Function-block trial (fb_search.cpp): per-combination wall times of the
+// known sites (infinity where a result fails the tolerance or the mask
+// offloads an unknown site) and the decision on such a table.
+using FbGpu = std::function<void(int prec, int block, const oo_fb_site &, const double *a, const double *b,
+                                 double *out)>;
+void fb_trial(const oo_fb_site *sites, int n_sites, int prec, double tol, uint64_t seed,
+              std::vector<double> &mask_ms, std::vector<int> &block_ids, const FbGpu &gpu);
+uint32_t fb_best(const double *mask_ms, int n_sites, double *best_ms);
 
 }  // namespace oo

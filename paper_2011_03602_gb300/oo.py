@@ -59,6 +59,11 @@ class oo_serve_req(_c.Structure):
                 ("in0", _vp), ("in1", _vp), ("out", _vp), ("res", _vp)]
 
 
+class oo_fb_site(_c.Structure):
+    _fields_ = [("callee", _c.c_char_p), ("lang", _i32), ("calls", _i32),
+                ("m", _c.c_int64), ("n", _c.c_int64), ("k", _c.c_int64)]
+
+
 class oo_serve_stats_t(_c.Structure):
     _fields_ = [(n, _u64) for n in ("submitted", "completed", "rejected_busy", "failed", "queued", "running",
                                     "device_free_bytes", "device_budget_bytes")]
@@ -115,6 +120,12 @@ def lib():
         "oo_gemm_f64_dev": (_c.c_int, [_vp, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _vp, _c.c_int, _vp,
                                        _c.c_int, _vp, _c.c_int]),
         "oo_gemm_check": (_c.c_int, [_vp, _c.c_int, _c.c_int, _c.c_int]),
+        "oo_fb_search": (_c.c_int, [_vp, _vp, _c.c_int, _c.c_int, _dbl, _u64, _vp, _vp, P(_c.c_uint32), P(_dbl)]),
+        "oo_fb_best": (_c.c_int, [_c.c_int, _vp, P(_c.c_uint32), P(_dbl)]),
+        "oo_offload_search": (_c.c_int, [_vp, _vp, _c.c_int, _c.c_int, _dbl, _u64, P(oo_jacobi), _c.c_int,
+                                         _c.c_int, _c.c_int, _dbl, _dbl, _u64, _dbl, P(_c.c_uint32), P(_u64),
+                                         P(_dbl), P(_dbl)]),
+        "oo_gemm_plan": (_c.c_int, [_c.c_int, _c.c_int, P(_c.c_int), P(_c.c_int), P(_c.c_int), P(_c.c_int)]),
         "oo_batch_create": (_c.c_int, [_vp, P(oo_req), _c.c_int, P(_vp)]),
         "oo_batch_run": (_c.c_int, [_vp, _c.c_int]),
         "oo_batch_check": (_c.c_int, [_vp]),
@@ -301,6 +312,55 @@ def oo_ga_search(ctx, prob, hoist, pop, gens, pc, pm, seed, eval_timeout_ms=0.0)
             "gene_ms": gene_ms}
 
 
+# ------------------------------------------- function-block trial order
+def fb_sites(sites):
+    """[(callee, lang, calls, m, n, k), ...] -> ctypes array of oo_fb_site
+    (the callee byte strings are kept alive on the array)."""
+    arr = (oo_fb_site * len(sites))()
+    keep = []
+    for i, (callee, lang, calls, m, n, k) in enumerate(sites):
+        b = callee.encode() if isinstance(callee, str) else callee
+        keep.append(b)
+        arr[i] = oo_fb_site(b, lang, calls, m, n, k)
+    arr._keep = keep
+    return arr
+
+
+def oo_fb_search(ctx, sites, prec=None, tol=1e-10, seed=1):
+    """Sec. 4.2.1 trial over every combination of the known sites."""
+    prec = OO_PREC_FP64EQ if prec is None else prec
+    arr = fb_sites(sites)
+    n = len(sites)
+    ids = np.zeros(n, np.int32)
+    ms = np.empty(1 << n, np.float64)
+    bm, bt = _c.c_uint32(), _dbl()
+    _check(ctx, lib().oo_fb_search(ctx, arr, n, prec, tol, seed, ids.ctypes.data_as(_vp), ms.ctypes.data_as(_vp),
+                                   _c.byref(bm), _c.byref(bt)))
+    return {"block_ids": ids, "mask_ms": ms, "best_mask": bm.value, "best_ms": bt.value}
+
+
+def oo_fb_best(mask_ms):
+    ms = np.ascontiguousarray(mask_ms, np.float64)
+    n = ms.size.bit_length() - 1
+    if ms.size != (1 << n):
+        raise ValueError("need 2^n times")
+    bm, bt = _c.c_uint32(), _dbl()
+    _check(None, lib().oo_fb_best(n, ms.ctypes.data_as(_vp), _c.byref(bm), _c.byref(bt)))
+    return bm.value, bt.value
+
+
+def oo_offload_search(ctx, sites, prob, hoist, pop, gens, pc, pm, ga_seed, eval_timeout_ms=0.0, prec=None,
+                      tol=1e-10, seed=1):
+    """Sec. 4.2: function blocks first, then the loop GA."""
+    prec = OO_PREC_FP64EQ if prec is None else prec
+    arr = fb_sites(sites) if sites else None
+    bm, bg, fms, lms = _c.c_uint32(), _u64(), _dbl(), _dbl()
+    _check(ctx, lib().oo_offload_search(ctx, arr, len(sites), prec, tol, seed, _c.byref(prob), hoist, pop, gens,
+                                        pc, pm, ga_seed, eval_timeout_ms, _c.byref(bm), _c.byref(bg),
+                                        _c.byref(fms), _c.byref(lms)))
+    return {"best_mask": bm.value, "best_gene": bg.value, "fb_ms": fms.value, "loop_ms": lms.value}
+
+
 # --------------------------------------------------------- function blocks
 def oo_fft_c128(ctx, x, direction=-1, out=None):
     """Host complex128 array -> its FFT (new array unless out is given)."""
@@ -312,6 +372,7 @@ def oo_fft_c128(ctx, x, direction=-1, out=None):
 
 
 OO_PREC_SPLIT3_BF16 = 0
+OO_PREC_FP64EQ = 2
 
 
 def oo_gemm_f64(ctx, A, B, prec=OO_PREC_SPLIT3_BF16, out=None):
@@ -335,6 +396,14 @@ def oo_gemm_f64_dev(ctx, m, n, k, dA, lda, dB, ldb, dC, ldc, prec=OO_PREC_SPLIT3
 
 def oo_gemm_check(ctx, m, n, k):
     _check(ctx, lib().oo_gemm_check(ctx, m, n, k))
+
+
+def oo_gemm_plan(prec, k):
+    """(BF16 products, digit bits beta, level bound L, exact K-block) of a
+    product with inner dimension k in precision pattern prec."""
+    v = [_c.c_int() for _ in range(4)]
+    _check(None, lib().oo_gemm_plan(prec, k, *[_c.byref(x) for x in v]))
+    return tuple(x.value for x in v)
 
 
 def oo_fft_c128_dev(ctx, n, batch, direction, din, dout):

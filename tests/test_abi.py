@@ -86,3 +86,21 @@ def test_missing_gpu_fails_loudly_or_creates():
     with pytest.raises(oo.OOError) as e:
         oo.oo_create(0)
     assert e.value.status in (oo.OO_ECUDA, oo.OO_EINVAL)
+
+
+def test_gemm_plan_follows_the_exactness_rule():
+    """FP64-equivalent split: K-block kb and digit width beta keep every
+    FP32 K-block sum exact, kb (2^beta - 1)^2 < 2^24, and the level bound L
+    is the smallest with 4 (L + 2) 2^(-beta (L - 1)) <= 2^-42."""
+    assert oo.oo_gemm_plan(oo.OO_PREC_SPLIT3_BF16, 4096) == (3, 0, 0, 0)
+    for k in (1, 63, 64, 200, 256, 257, 1000, 1024, 1025, 4096, 10000):
+        prods, beta, L, kb = oo.oo_gemm_plan(oo.OO_PREC_FP64EQ, k)
+        assert kb % 64 == 0 and kb >= min(k, 1024) and kb <= 1024
+        assert kb * (2 ** beta - 1) ** 2 < 2 ** 24 and beta <= 8
+        assert 4 * (L + 2) * 2.0 ** (-beta * (L - 1)) <= 2.0 ** -42
+        assert 4 * (L + 1) * 2.0 ** (-beta * (L - 2)) > 2.0 ** -42
+        assert prods == L * (L - 1) // 2
+    assert oo.oo_gemm_plan(oo.OO_PREC_FP64EQ, 256)[:3] == (21, 8, 7)
+    assert oo.oo_gemm_plan(oo.OO_PREC_FP64EQ, 4096)[:3] == (28, 7, 8)
+    with pytest.raises(oo.OOError):
+        oo.oo_gemm_plan(1, 64)
