@@ -27,19 +27,26 @@
 //   K-block kb = min(roundup64(k), 1024);  beta = 8 (kb <= 256) or 7;
 //   beta 8: L = 7 (21 products); beta 7: L = 8 (28 products).
 //
-// Kernel: persistent, one CTA per SM over 128 x 128 output tiles.  A unit
-// of work is one (product, K-block): warp 0 streams the A_p and B_q tiles of
-// the unit (TMA, 128-byte swizzle) through a 7-stage ring, warp 1 issues
-// tcgen05.mma (M = N = 128, K = 16) into one of two FP32 accumulators in
-// tensor memory (columns 0-255), warps 4-7 add each finished accumulator,
-// scaled by 2^(-beta (p + q)), into a float-float running sum held in
-// tensor memory (columns 256-511) and, after the tile's last unit, write
-// FP64 C.  Every mbarrier wait is bounded.
+// Kernel: persistent, one CTA per SM over 128 x 128 output tiles.  The
+// products are grouped in units that share the A slice: (p, q1) and
+// (p, q2) become one M = 128, N = 256 MMA whose B operand is the two B
+// slices' tiles stacked (a product without a partner runs alone at
+// N = 128).  A unit of work is one such group over one K-block: warp 0
+// streams its A_p and B_q tiles (TMA, 128-byte swizzle) through a 4-stage
+// ring, warp 1 issues tcgen05.mma (K = 16) into one of two 256-column FP32
+// accumulators in tensor memory (double-buffered), and eight epilogue warps
+// (two per tensor-memory lane quarter, one per 64-column half) add each
+// finished accumulator, scaled by 2^(-beta (p + q)), into a float-float
+// running sum held in registers; after the tile's last unit they write
+// FP64 C.  Sharing A_p raises the MMA work per staged byte by a third,
+// which is what bounds this kernel (operand latency, not tensor rate).
+// Every mbarrier wait is bounded.
 // Inputs must be finite.
 #include <cuda_bf16.h>
 
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "ff.cuh"
 #include "oo_internal.h"
@@ -51,13 +58,16 @@ namespace {
 
 using namespace tc;
 
-constexpr int kBM = 128, kBN = 128, kBK = 64, kStages = 7;
-constexpr int kThreads = 256;
+constexpr int kBM = 128, kBN = 128, kBK = 64, kStages = 4;
+constexpr int kThreads = 320;              // producer, MMA issuer, 8 epilogue warps
+constexpr int kEpiWarps = 8;
 constexpr uint32_t kTile = kBM * kBK * 2;  // 16 KB, A and B tiles alike
-constexpr uint32_t kStageBytes = 2 * kTile;
+constexpr uint32_t kStageBytes = 3 * kTile;  // A_p, B_q1, B_q2
 constexpr int kGroupM = 8;
-constexpr int kMaxProducts = 36;
-constexpr uint32_t kIdesc = idesc_bf16(kBM, kBN);
+constexpr int kMaxUnits = 24;
+constexpr uint32_t kIdescPair = idesc_bf16(kBM, 2 * kBN);
+constexpr uint32_t kIdescOne = idesc_bf16(kBM, kBN);
+constexpr unsigned char kNone = 0xff;
 
 struct EqShape {
     int beta, levels, slices, kb, nkb, nprod;
@@ -78,19 +88,34 @@ EqShape eq_shape(int k) {
     return e;
 }
 
+// A unit: slice p of A against slices q1 and q2 (q2 = kNone: alone) of B
+struct EqUnit {
+    int p, q1, q2;
+};
+// Products (p, q), 1-based, p + q <= L, grouped by p in pairs of
+// consecutive q; ordered from the smallest contributions up.
+std::vector<EqUnit> eq_units(const EqShape &e) {
+    std::vector<EqUnit> u;
+    for (int p = 1; p <= e.slices; ++p)
+        for (int q = 1; q <= e.levels - p; q += 2)
+            u.push_back({p - 1, q - 1, q + 1 <= e.levels - p ? q : (int)kNone});
+    std::stable_sort(u.begin(), u.end(), [](const EqUnit &a, const EqUnit &b) { return a.p + a.q1 > b.p + b.q1; });
+    return u;
+}
+
 struct EqMaps {
     CUtensorMap a, b;  // all slices stacked: slice p at rows [p m, (p + 1) m)
 };
 
 struct EqArgs {
-    int m, n, ksteps, kb_steps, nkb, nprod;
+    int m, n, ksteps, kb_steps, nkb, nunits;
     int m_tiles, n_tiles;
     double *C;
     long long ldc;
     const int *ea, *eb;
     unsigned *err;
-    unsigned char prod_p[kMaxProducts], prod_q[kMaxProducts];  // 0-based slice indices
-    float prod_scale[kMaxProducts];                             // 2^(-beta (p + q)), 1-based p, q
+    unsigned char up[kMaxUnits], uq1[kMaxUnits], uq2[kMaxUnits];  // 0-based slices; uq2 kNone: alone
+    float us1[kMaxUnits], us2[kMaxUnits];                           // 2^(-beta (p + q)), 1-based p, q
 };
 
 __device__ __forceinline__ void eq_tile(const EqArgs &a, int t, int &m0, int &n0) {
@@ -100,6 +125,15 @@ __device__ __forceinline__ void eq_tile(const EqArgs &a, int t, int &m0, int &n0
     m0 = (g * kGroupM + r % rows) * kBM;
     n0 = (r / rows) * kBN;
 }
+
+#define OO_TMEM_LD16(taddr, r)                                                                              \
+    asm volatile(                                                                                           \
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "  \
+        "[%16];"                                                                                            \
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),   \
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),          \
+          "=r"(r[15])                                                                                       \
+        : "r"(taddr))
 
 __global__ void __launch_bounds__(kThreads, 1) gemm_fp64eq_kernel(const __grid_constant__ EqMaps maps,
                                                                  const __grid_constant__ EqArgs a) {
@@ -114,7 +148,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_fp64eq_kernel(const __grid_c
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tiles = a.m_tiles * a.n_tiles;
-    const int units = a.nprod * a.nkb;
+    const int units = a.nunits * a.nkb;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -123,7 +157,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_fp64eq_kernel(const __grid_c
         }
         for (int b = 0; b < 2; ++b) {
             bar_init(su32(&tfull[b]), 1);
-            bar_init(su32(&tempty[b]), 4);  // one arrival per epilogue warp
+            bar_init(su32(&tempty[b]), kEpiWarps);  // one arrival per epilogue warp
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -148,7 +182,9 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_fp64eq_kernel(const __grid_c
             eq_tile(a, t, m0, n0);
             for (int u = 0; ok && u < units; ++u) {
                 const int pr = u / a.nkb, kbi = u % a.nkb;
-                const int rowA = a.prod_p[pr] * a.m + m0, rowB = a.prod_q[pr] * a.n + n0;
+                const bool pair = a.uq2[pr] != kNone;
+                const int rowA = a.up[pr] * a.m + m0, rowB1 = a.uq1[pr] * a.n + n0;
+                const int rowB2 = pair ? a.uq2[pr] * a.n + n0 : 0;
                 const int ks1 = min(a.ksteps, (kbi + 1) * a.kb_steps);
                 for (int ks = kbi * a.kb_steps; ks < ks1; ++ks, ++it) {
                     const int s = it % kStages;
@@ -159,9 +195,10 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_fp64eq_kernel(const __grid_c
                     }
                     unsigned char *st = sm + (size_t)s * kStageBytes;
                     const uint32_t fb = su32(&full[s]);
-                    bar_expect_tx(fb, kStageBytes);
+                    bar_expect_tx(fb, pair ? 3 * kTile : 2 * kTile);
                     tma_2d(su32(st), &maps.a, ks * kBK, rowA, fb);
-                    tma_2d(su32(st + kTile), &maps.b, ks * kBK, rowB, fb);
+                    tma_2d(su32(st + kTile), &maps.b, ks * kBK, rowB1, fb);
+                    if (pair) tma_2d(su32(st + 2 * kTile), &maps.b, ks * kBK, rowB2, fb);
                     ++loaded;
                 }
             }
@@ -179,8 +216,9 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_fp64eq_kernel(const __grid_c
                     break;
                 }
                 fence_after();
-                const uint32_t d = tmem + (uint32_t)(b * kBN);
-                const int kbi = u % a.nkb;
+                const uint32_t d = tmem + (uint32_t)(b * 2 * kBN);
+                const int pr = u / a.nkb, kbi = u % a.nkb;
+                const bool pair = a.uq2[pr] != kNone;
                 const int ks0 = kbi * a.kb_steps, ks1 = min(a.ksteps, (kbi + 1) * a.kb_steps);
                 for (int ks = ks0; ks < ks1; ++ks, ++it) {
                     const int s = it % kStages;
@@ -193,8 +231,11 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_fp64eq_kernel(const __grid_c
 #pragma unroll
                     for (int kk = 0; kk < kBK / 16; ++kk) {
                         const uint32_t off = kk * 32;  // 16 BF16 along K inside the 128-byte row
-                        mma_bf16<kIdesc>(d, sdesc_sw128(sa + off), sdesc_sw128(sb + off),
-                                         (ks == ks0 && kk == 0) ? 0u : 1u);
+                        const uint32_t acc = (ks == ks0 && kk == 0) ? 0u : 1u;
+                        if (pair)  // B_q1 and B_q2 tiles stacked: one N = 256 operand
+                            mma_bf16<kIdescPair>(d, sdesc_sw128(sa + off), sdesc_sw128(sb + off), acc);
+                        else
+                            mma_bf16<kIdescOne>(d, sdesc_sw128(sa + off), sdesc_sw128(sb + off), acc);
                     }
                     mma_commit(su32(&empty[s]));
                 }
@@ -203,20 +244,17 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_fp64eq_kernel(const __grid_c
                 ++units_mma;
             }
         }
-    } else if (warp >= 4) {
+    } else if (warp >= 2) {
         // ---------------------------------------------------- epilogue
-        const int q = warp - 4;  // TMEM lane quarter
+        const int q = warp & 3;              // TMEM lane quarter this warp may access
+        const int h = (warp - 2) >> 2;       // 64-column half of the tile
         const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-        const uint32_t sum_hi = tmem + 256 + lane_off, sum_lo = tmem + 384 + lane_off;
+        float Sh[64], Sl[64];                // running float-float sum of this row's 64 columns
         int gu = 0;
         bool ok = true;
         for (int t = blockIdx.x; ok && t < tiles; t += gridDim.x) {
             int m0, n0;
             eq_tile(a, t, m0, n0);
-            const int row = m0 + q * 32 + lane;
-            const bool row_ok = row < a.m;
-            const int sa = row_ok ? a.ea[row] : 0;
-            double *crow = a.C + (long long)row * a.ldc;
             for (int u = 0; u < units; ++u, ++gu) {
                 const int b = gu & 1;
                 if (!bar_wait(su32(&tfull[b]), (gu >> 1) & 1, abort_flag, a.err, 4u)) {
@@ -224,45 +262,46 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_fp64eq_kernel(const __grid_c
                     break;
                 }
                 fence_after();
-                const bool first = u == 0, last = u == units - 1;
-                const float f = a.prod_scale[u / a.nkb];
-                const uint32_t acc = tmem + (uint32_t)(b * kBN) + lane_off;
-                for (int c = 0; c < kBN; c += 32) {
-                    uint32_t v[32], h[32], l[32];
-                    OO_TMEM_LD32(acc + c, v);
-                    if (!first) {
-                        OO_TMEM_LD32(sum_hi + c, h);
-                        OO_TMEM_LD32(sum_lo + c, l);
-                    }
-                    tmem_wait_ld();
+                const int pr = u / a.nkb;
+                const bool pair = a.uq2[pr] != kNone, first = u == 0;
+                const float f1 = a.us1[pr], f2 = a.us2[pr];
+                const uint32_t acc = tmem + (uint32_t)(b * 2 * kBN) + lane_off + (uint32_t)(h * 64);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const float w = __fmul_rn(__uint_as_float(v[j]), f);  // exact: power-of-two scale
-                        float H = w, L = 0.0f;
-                        if (!first) ff::add(__uint_as_float(h[j]), __uint_as_float(l[j]), w, 0.0f, H, L);
-                        h[j] = __float_as_uint(H);
-                        l[j] = __float_as_uint(L);
-                    }
-                    if (last) {
-                        if (row_ok) {
+                for (int c = 0; c < 64; c += 16) {
+                    uint32_t v[16];
 #pragma unroll
-                            for (int j = 0; j < 32; ++j) {
-                                const int col = n0 + c + j;
-                                if (col < a.n) {
-                                    const double x = ff::to_double(__uint_as_float(h[j]), __uint_as_float(l[j]));
-                                    crow[col] = ff::scale_pow2(x, sa + a.eb[col]);
-                                }
+                    for (int half = 0; half < 2; ++half) {
+                        if (half == 1 && !pair) break;
+                        OO_TMEM_LD16(acc + half * kBN + c, v);
+                        tmem_wait_ld();
+                        const float f = half ? f2 : f1;
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const float w = __fmul_rn(__uint_as_float(v[j]), f);  // exact: power-of-two scale
+                            if (first && half == 0) {
+                                Sh[c + j] = w;
+                                Sl[c + j] = 0.0f;
+                            } else {
+                                ff::add(Sh[c + j], Sl[c + j], w, 0.0f, Sh[c + j], Sl[c + j]);
                             }
                         }
-                    } else {
-                        OO_TMEM_ST32(sum_hi + c, h);
-                        OO_TMEM_ST32(sum_lo + c, l);
                     }
                 }
-                if (!last) tmem_wait_st();
                 fence_before();
                 __syncwarp();
                 if (lane == 0) bar_arrive(su32(&tempty[b]));
+                if (u == units - 1) {
+                    const int row = m0 + q * 32 + lane;
+                    if (row < a.m) {
+                        const int sa = a.ea[row];
+                        double *crow = a.C + (long long)row * a.ldc + n0 + h * 64;
+                        const int ncol = a.n - (n0 + h * 64);
+#pragma unroll
+                        for (int j = 0; j < 64; ++j)
+                            if (j < ncol)
+                                crow[j] = ff::scale_pow2(ff::to_double(Sh[j], Sl[j]), sa + a.eb[n0 + h * 64 + j]);
+                    }
+                }
             }
         }
     }
@@ -428,7 +467,6 @@ void launch_gemm_fp64eq(int m, int n, int k, const double *A, long long lda, con
     OO_REQUIRE(m >= 1 && n >= 1 && k >= 1, OO_EINVAL, "m, n, k must be >= 1");
     OO_REQUIRE(lda >= k && ldb >= n && ldc >= n, OO_EINVAL, "leading dimensions too small");
     const EqShape e = eq_shape(k);
-    OO_REQUIRE(e.nprod <= kMaxProducts, OO_EINVAL, "too many products");
     OO_REQUIRE((long long)e.slices * m < (1ll << 31) && (long long)e.slices * n < (1ll << 31), OO_EINVAL,
                "matrix too large for the FP64-equivalent mode");
     const int kp = (k + kBK - 1) / kBK * kBK;
@@ -467,7 +505,6 @@ void launch_gemm_fp64eq(int m, int n, int k, const double *A, long long lda, con
     ga.ksteps = kp / kBK;
     ga.kb_steps = e.kb / kBK;
     ga.nkb = e.nkb;
-    ga.nprod = e.nprod;
     ga.m_tiles = (m + kBM - 1) / kBM;
     ga.n_tiles = (n + kBN - 1) / kBN;
     ga.C = C;
@@ -475,15 +512,16 @@ void launch_gemm_fp64eq(int m, int n, int k, const double *A, long long lda, con
     ga.ea = ea;
     ga.eb = eb;
     ga.err = err;
-    // products (p, q), 1-based, p + q <= L, ordered from the smallest level up
-    int np = 0;
-    for (int lev = e.levels; lev >= 2; --lev)
-        for (int pp = 1; pp < lev; ++pp) {
-            ga.prod_p[np] = (unsigned char)(pp - 1);
-            ga.prod_q[np] = (unsigned char)(lev - pp - 1);
-            ga.prod_scale[np] = std::ldexp(1.0f, -e.beta * lev);
-            ++np;
-        }
+    const std::vector<EqUnit> U = eq_units(e);
+    OO_REQUIRE((int)U.size() <= kMaxUnits, OO_EINVAL, "too many product groups");
+    ga.nunits = (int)U.size();
+    for (size_t i = 0; i < U.size(); ++i) {
+        ga.up[i] = (unsigned char)U[i].p;
+        ga.uq1[i] = (unsigned char)U[i].q1;
+        ga.uq2[i] = (unsigned char)U[i].q2;
+        ga.us1[i] = std::ldexp(1.0f, -e.beta * (U[i].p + U[i].q1 + 2));
+        ga.us2[i] = U[i].q2 == kNone ? 0.0f : std::ldexp(1.0f, -e.beta * (U[i].p + U[i].q2 + 2));
+    }
     static bool attr = false;
     if (!attr) {
         OO_CUDA_TRY(cudaFuncSetAttribute(gemm_fp64eq_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -496,6 +534,7 @@ void launch_gemm_fp64eq(int m, int n, int k, const double *A, long long lda, con
     OO_CUDA_TRY(cudaGetDevice(&dev));
     OO_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int grid = (int)std::min<long long>(tiles, sms);
+    OO_REQUIRE(grid >= 1, OO_EINVAL, "empty product");
     gemm_fp64eq_kernel<<<grid, kThreads, smem_eq(), s>>>(maps, ga);
     OO_CUDA_TRY(cudaGetLastError());
 }
