@@ -94,8 +94,9 @@ __device__ __forceinline__ cplx twiddle(const float4 *stw, int idx, bool inv) {
     return inv ? ff::conj(w) : w;
 }
 
-// Stockham radix-2 stage with sub-length Ls on C columns of length L.
-__device__ __forceinline__ void stage_r2(float4 *sd, const float4 *stw, int log2L, int Ls, bool inv) {
+// Stockham radix-2 stage with sub-length Ls on C columns of length L; used
+// only as the first stage (Ls = 1), which needs no twiddles.
+__device__ __forceinline__ void stage_r2(float4 *sd, const float4 *, int log2L, int Ls, bool) {
     const int L = 1 << log2L, half = L >> 1;
     cplx y0[2 * kFftBpt], y1[2 * kFftBpt];
     int base_c[2 * kFftBpt], jj[2 * kFftBpt];
@@ -107,7 +108,6 @@ __device__ __forceinline__ void stage_r2(float4 *sd, const float4 *stw, int log2
         jj[r] = j;
         y0[r] = ld_cplx(sd + base_c[r] + j);
         cplx x1 = ld_cplx(sd + base_c[r] + j + half);
-        if (Ls > 1) x1 = ff::cmul(x1, twiddle(stw, (j & (Ls - 1)) * (L / (2 * Ls)), inv));
         y1[r] = x1;
     }
     __syncthreads();
@@ -121,7 +121,11 @@ __device__ __forceinline__ void stage_r2(float4 *sd, const float4 *stw, int log2
     __syncthreads();
 }
 
-// Stockham radix-4 stage with sub-length Ls.
+// Stockham radix-4 stage with sub-length Ls.  Twiddles come from this
+// stage's slice of the per-stage table: stw[(q - 1) Ls + k] = W_{4Ls}^{k q}
+// (= W_L^{k q L / (4 Ls)}), so lanes with consecutive k read consecutive
+// entries (no shared-memory bank conflicts, unlike strided reads of one
+// W_L table).
 __device__ __forceinline__ void stage_r4(float4 *sd, const float4 *stw, int log2L, int Ls, bool inv) {
     const int L = 1 << log2L, q4 = L >> 2;
     cplx Y[kFftBpt][4];
@@ -136,9 +140,9 @@ __device__ __forceinline__ void stage_r4(float4 *sd, const float4 *stw, int log2
 #pragma unroll
         for (int q = 0; q < 4; ++q) x[q] = ld_cplx(sd + base_c[r] + j + q * q4);
         if (Ls > 1) {
-            const int k = j & (Ls - 1), step = L / (4 * Ls);
+            const int k = j & (Ls - 1);
 #pragma unroll
-            for (int q = 1; q < 4; ++q) x[q] = ff::cmul(x[q], twiddle(stw, k * q * step, inv));
+            for (int q = 1; q < 4; ++q) x[q] = ff::cmul(x[q], twiddle(stw, (q - 1) * Ls + k, inv));
         }
         const cplx a0 = ff::cadd(x[0], x[2]), a1 = ff::csub(x[0], x[2]);
         const cplx b0 = ff::cadd(x[1], x[3]), b1 = ff::csub(x[1], x[3]);
@@ -159,13 +163,23 @@ __device__ __forceinline__ void stage_r4(float4 *sd, const float4 *stw, int log2
     __syncthreads();
 }
 
+// A radix-2 stage (Ls = 1, no twiddles) first when log2 L is odd, then
+// radix-4 stages; stw holds the radix-4 stages' twiddle slices in order.
 __device__ void fft_in_smem(float4 *sd, const float4 *stw, int log2L, bool inv) {
     int Ls = 1;
     if (log2L & 1) {
         stage_r2(sd, stw, log2L, 1, inv);
         Ls = 2;
     }
-    for (; Ls < (1 << log2L); Ls *= 4) stage_r4(sd, stw, log2L, Ls, inv);
+    for (; Ls < (1 << log2L); Ls *= 4) {
+        stage_r4(sd, stw, log2L, Ls, inv);
+        if (Ls > 1) stw += 3 * Ls;
+    }
+}
+
+// entries of the per-stage twiddle table of a length-2^log2L transform
+__host__ __device__ __forceinline__ int stage_table_count(int log2L) {
+    return log2L < 3 ? 0 : (1 << log2L) - ((log2L & 1) ? 2 : 4);
 }
 
 // MODE 0: whole transforms of length L = n, several per CTA (double in/out)
@@ -180,7 +194,7 @@ __global__ void __launch_bounds__(kFftThreads, 1) fft_pass_kernel(FftArgs a) {
     const int L = 1 << log2L;
     const int C = kFftElems >> log2L;  // columns (transforms / rows) in this CTA
     const bool inv = a.inverse != 0;
-    for (int t = threadIdx.x; t < L; t += kFftThreads) stw[t] = a.tw[t];
+    for (int t = threadIdx.x; t < stage_table_count(log2L); t += kFftThreads) stw[t] = a.tw[t];
 
     const long long n = a.n;
     const int N1 = 1 << a.log2n1, N2 = 1 << a.log2n2;
@@ -193,34 +207,49 @@ __global__ void __launch_bounds__(kFftThreads, 1) fft_pass_kernel(FftArgs a) {
         c0 = (blockIdx.x % per) * C;
     }
 
-    // ---- load
-    for (int q = threadIdx.x; q < kFftElems; q += kFftThreads) {
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        int c, t;
-        if (MODE == 1) {  // column-fastest for coalescing
-            c = q & (C - 1);
-            t = q >> (31 - __clz(C));
-        } else {
-            c = q >> log2L;
-            t = q & (L - 1);
-        }
-        if (MODE == 0) {
-            const int tb = c0 + c;
-            if (tb < a.batch) {
-                const int S = scale_of(a, tb);
-                const double2 x = reinterpret_cast<const double2 *>(a.in_d)[(long long)tb * n + t];
-                split_scaled(x.x, S, v.x, v.y);
-                split_scaled(x.y, S, v.z, v.w);
+    // ---- load: all of this thread's 16-byte loads are issued before any is
+    // used (eight in flight), then split and stored to shared memory
+    constexpr int kPer = kFftElems / kFftThreads;
+    {
+        double2 raw[kPer];
+        int dst[kPer];
+#pragma unroll
+        for (int r = 0; r < kPer; ++r) {
+            const int q = threadIdx.x + r * kFftThreads;
+            int c, t;
+            if (MODE == 1) {  // column-fastest for coalescing
+                c = q & (C - 1);
+                t = q >> (31 - __clz(C));
+            } else {
+                c = q >> log2L;
+                t = q & (L - 1);
             }
-        } else if (MODE == 1) {
-            const int S = scale_of(a, b);
-            const double2 x = reinterpret_cast<const double2 *>(a.in_d)[(long long)b * n + (long long)t * N2 + c0 + c];
-            split_scaled(x.x, S, v.x, v.y);
-            split_scaled(x.y, S, v.z, v.w);
-        } else {
-            v = a.in_ff[(long long)b * n + (long long)(c0 + c) * N2 + t];
+            dst[r] = (c << log2L) + t;
+            raw[r] = make_double2(0.0, 0.0);
+            if (MODE == 0) {
+                if (c0 + c < a.batch) raw[r] = reinterpret_cast<const double2 *>(a.in_d)[(long long)(c0 + c) * n + t];
+            } else if (MODE == 1) {
+                raw[r] = reinterpret_cast<const double2 *>(a.in_d)[(long long)b * n + (long long)t * N2 + c0 + c];
+            } else {
+                const float4 f = a.in_ff[(long long)b * n + (long long)(c0 + c) * N2 + t];
+                raw[r] = make_double2(__hiloint2double(__float_as_int(f.y), __float_as_int(f.x)),
+                                      __hiloint2double(__float_as_int(f.w), __float_as_int(f.z)));
+            }
         }
-        sd[(c << log2L) + t] = v;
+#pragma unroll
+        for (int r = 0; r < kPer; ++r) {
+            float4 v;
+            if (MODE == 2) {  // float-float intermediates: the 16 bytes as they were
+                v = make_float4(__int_as_float(__double2loint(raw[r].x)), __int_as_float(__double2hiint(raw[r].x)),
+                                __int_as_float(__double2loint(raw[r].y)), __int_as_float(__double2hiint(raw[r].y)));
+            } else {
+                const int tb = MODE == 0 ? c0 + (dst[r] >> log2L) : b;
+                const int S = (MODE == 0 && tb >= a.batch) ? 0 : scale_of(a, tb);
+                split_scaled(raw[r].x, S, v.x, v.y);
+                split_scaled(raw[r].y, S, v.z, v.w);
+            }
+            sd[dst[r]] = v;
+        }
     }
     __syncthreads();
 
@@ -305,6 +334,28 @@ __global__ void fft_twiddle_kernel(float4 *table, int count, long long stride, i
     }
 }
 
+// per-stage twiddle table of a length-2^log2L transform: for each radix-4
+// stage with sub-length Ls > 1 (in execution order), 3 Ls entries
+// W_{4Ls}^{k q}, q = 1..3, k < Ls, computed in FP64 and split to float pairs
+__global__ void fft_stage_twiddle_kernel(float4 *table, int log2L) {
+    const int count = stage_table_count(log2L);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x) {
+        int Ls = (log2L & 1) ? 2 : 4, off = 0, lg = (log2L & 1) ? 1 : 2;  // lg = log2 Ls
+        while (t >= off + 3 * Ls) {
+            off += 3 * Ls;
+            Ls *= 4;
+            lg += 2;
+        }
+        const int r = t - off, q = r / Ls + 1, k = r % Ls;
+        const long long m = ((long long)k * q) & ((4ll << lg) - 1);  // W_{4Ls}^m, 4Ls = 2^(lg + 2)
+        double sn, cs;
+        sincospi(ldexp((double)(2 * m), -(lg + 2)), &sn, &cs);    // angle 2 pi m / (4 Ls)
+        const double re = cs, im = -sn;
+        const float rh = (float)re, ih = (float)im;
+        table[t] = make_float4(rh, (float)(re - (double)rh), ih, (float)(im - (double)ih));
+    }
+}
+
 // ------------------------------------------------- grouped transforms
 // A CTA's worth of work in a batch of transforms of different lengths:
 // mode 0: `count` whole transforms of length 2^log2L (request ids at
@@ -347,7 +398,7 @@ __global__ void __launch_bounds__(kFftThreads, 1)
         const float4 *tw = item.mode == 0 ? R0.tw : (item.mode == 1 ? R0.tw_n1 : R0.tw_n2);
         const bool inv = R0.inverse != 0;
         __syncthreads();  // previous item's shared-memory reads are done
-        for (int t = threadIdx.x; t < L; t += kFftThreads) stw[t] = tw[t];
+        for (int t = threadIdx.x; t < stage_table_count(log2L); t += kFftThreads) stw[t] = tw[t];
         const int N1 = 1 << R0.log2n1, N2 = 1 << R0.log2n2;
         // ---- load
         for (int q = threadIdx.x; q < kFftElems; q += kFftThreads) {
@@ -454,11 +505,21 @@ FftPlan *fft_plan_create(long long n) {
             t += cnt;
             return r;
         };
+        auto gen_stages = [&](int lg) {
+            const int cnt = stage_table_count(lg);
+            if (cnt > 0) {
+                fft_stage_twiddle_kernel<<<std::max(1, std::min(1024, (cnt + 255) / 256)), 256>>>(t, lg);
+                OO_CUDA_TRY(cudaGetLastError());
+            }
+            const float4 *r = t;
+            t += (size_t)1 << lg;  // a table slot of 2^lg entries (count < 2^lg)
+            return r;
+        };
         if (!four_step) {
-            p->tw_single = gen(1 << k, 1, k);
+            p->tw_single = gen_stages(k);
         } else {
-            p->tw_n1 = gen(1 << p->log2n1, 1, p->log2n1);
-            p->tw_n2 = gen(1 << p->log2n2, 1, p->log2n2);
+            p->tw_n1 = gen_stages(p->log2n1);
+            p->tw_n2 = gen_stages(p->log2n2);
             p->tw_hi = gen(1 << std::max(0, k - kTwSplit), 1ll << kTwSplit, k);
             p->tw_lo = gen(1 << kTwSplit, 1, k);
         }
