@@ -454,6 +454,40 @@ def run_fb(args):
     return 0
 
 
+def run_hoist(args):
+    """Transfer hoisting (Sec. 3.2.1) measured: for a few genes, the pattern's
+    wall time and CPU<->GPU traffic with copies hoisted to the outermost
+    level each variable allows (lazy per-side validity) and with every GPU
+    nest copying its data in and out at each invocation."""
+    import torch
+    from paper_2011_03602_gb300 import oo
+    torch.cuda.set_device(0)
+    ctx = oo.oo_create(0)
+    genes = {"all_cpu": 0, "stencil_only": 4, "iteration_nests": 60, "all_gpu": 63}
+    rows = []
+    for (gI, gJ, gK, gIt) in ((65, 65, 129, 50), (129, 129, 257, 20)):
+        prob = oo.jacobi(gI, gJ, gK, gIt)
+        p = np.empty(gI * gJ * gK, np.float32)
+        r = np.empty(gIt)
+        for name, g in genes.items():
+            for hoist in (1, 0):
+                oo.oo_run_pattern(ctx, g, hoist, prob, p, r)  # warm-up
+                best = None
+                for _ in range(3):
+                    st = oo.oo_run_pattern(ctx, g, hoist, prob, p, r)
+                    if best is None or st["wall_ms"] < best["wall_ms"]:
+                        best = st
+                rows.append({"grid": [gI, gJ, gK], "iters": gIt, "gene": format(g, "06b"), "name": name,
+                             "hoist": hoist, "wall_ms": round(best["wall_ms"], 3),
+                             "h2d_bytes": int(best["h2d_bytes"]), "d2h_bytes": int(best["d2h_bytes"]),
+                             "n_xfers": int(best["n_xfers"]), "xfer_ms": round(best["xfer_ms"], 3)})
+    oo.oo_destroy(ctx)
+    print(json.dumps({"metric": "pattern wall time with and without transfer hoisting", "unit": "ms",
+                      "config": {"workload": "jacobi19_hoist_on_off", "timing": "best of 3 after 1 warm-up"},
+                      "rows": rows}))
+    return 0
+
+
 def run_block(args):
     """Profiling helper: warm up and run one function block a few times
     (no oracle, no timing claims) so ncu can capture its kernels."""
@@ -682,6 +716,7 @@ def main():
     ap.add_argument("--ga", action="store_true", help="run the GA search at scale instead of the step benchmark")
     ap.add_argument("--block", choices=["gemm", "fft"], default=None, help="profiling: run one function block")
     ap.add_argument("--fb", action="store_true", help="function-block + loop offload trial order")
+    ap.add_argument("--hoist", action="store_true", help="pattern times with transfer hoisting on and off")
     ap.add_argument("--batched", action="store_true", help="batched uneven GEMM/FFT configuration")
     ap.add_argument("--serve", action="store_true", help="serving-loop configuration")
     ap.add_argument("--serve-rates", default="2000,5000,10000,20000")
@@ -712,6 +747,8 @@ def main():
         return run_reference(args)
     if args.fb:
         return run_fb(args)
+    if args.hoist:
+        return run_hoist(args)
     if args.ga:
         return run_ga(args)
     if args.block:

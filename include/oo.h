@@ -354,7 +354,8 @@ oo_status oo_offload_search(oo_ctx *ctx, const oo_fb_site *sites, int n_sites, i
  * copied into a pinned staging pool (as large as the budget) by oo_submit;
  * results are copied into the caller's buffer by oo_wait.
  *   kind OO_BLOCK_GEMM   : C (m x n) = A (m x k) B (k x n), host row-major
- *                          contiguous; in0 = A, in1 = B, out = C; prec.
+ *                          contiguous; in0 = A, in1 = B, out = C; prec
+ *                          OO_PREC_SPLIT3_BF16 or OO_PREC_FP64EQ.
  *   kind OO_BLOCK_FFT    : length n, dir; in0 = x, out = X (complex128).
  *   kind OO_BLOCK_JACOBI : the Jacobi program on an m x n x k grid (I, J, K)
  *                          for `iters` iterations with `omega`, every nest
@@ -400,7 +401,9 @@ oo_status oo_serve_stop(oo_ctx *ctx);
 /* Many GEMM and FFT requests of uneven sizes, on caller-owned device buffers.
  *   GEMM (kind OO_BLOCK_GEMM): C (m x n) = A (m x k) B (k x n), row-major,
  *        contiguous (leading dimensions k, n, n); in0 = A, in1 = B, out = C;
- *        prec as for oo_gemm_f64.
+ *        prec must be OO_PREC_SPLIT3_BF16 (the grouped tensor-core kernel
+ *        implements that pattern; FP64-equivalent products go through
+ *        oo_gemm_f64_dev or the serving loop).
  *   FFT  (kind OO_BLOCK_FFT): length n = 2^e (e <= 24), in0 = x, out = X
  *        (interleaved complex128, 16-byte aligned), dir -1 / +1; m, k unused.
  * oo_batch_create builds the grouped plan once (tensor maps, split-operand

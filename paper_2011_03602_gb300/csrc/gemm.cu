@@ -690,11 +690,15 @@ void gemm_group_destroy(GemmGroup *g) {
     delete g;
 }
 
-unsigned gemm_check_error(void *scratch, int m, int n, int k, cudaStream_t s) {
+unsigned *gemm_error_word(void *scratch, int m, int n, int k) {
     const int kp = (k + kBK - 1) / kBK * kBK;
     const size_t a_bytes = ((size_t)m * kp * 2 + 255) / 256 * 256, b_bytes = ((size_t)n * kp * 2 + 255) / 256 * 256;
-    unsigned *err = reinterpret_cast<unsigned *>(static_cast<char *>(scratch) + 2 * a_bytes + 2 * b_bytes +
-                                                 ((size_t)m + n) * 4);
+    return reinterpret_cast<unsigned *>(static_cast<char *>(scratch) + 2 * a_bytes + 2 * b_bytes +
+                                        ((size_t)m + n) * 4);
+}
+
+unsigned gemm_check_error(void *scratch, int m, int n, int k, cudaStream_t s) {
+    unsigned *err = gemm_error_word(scratch, m, n, k);
     unsigned e = 0;
     OO_CUDA_TRY(cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, s));
     OO_CUDA_TRY(cudaStreamSynchronize(s));

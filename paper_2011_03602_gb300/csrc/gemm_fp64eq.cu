@@ -539,6 +539,8 @@ void launch_gemm_fp64eq(int m, int n, int k, const double *A, long long lda, con
     OO_CUDA_TRY(cudaGetLastError());
 }
 
+unsigned *gemm_fp64eq_error_word(void *scratch) { return static_cast<unsigned *>(scratch); }
+
 unsigned gemm_fp64eq_check_error(void *scratch, cudaStream_t s) {
     unsigned *err = static_cast<unsigned *>(scratch);
     unsigned e = 0;

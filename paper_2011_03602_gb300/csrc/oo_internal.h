@@ -103,6 +103,8 @@ void launch_gemm_split3(int m, int n, int k, const double *A, long long lda, con
                         double *C, long long ldc, void *scratch, cudaStream_t s);
 // reads and clears the kernel's error word (0 = fine); synchronises s
 unsigned gemm_check_error(void *scratch, int m, int n, int k, cudaStream_t s);
+// the kernel's device error word inside its scratch (for asynchronous reads)
+unsigned *gemm_error_word(void *scratch, int m, int n, int k);
 // FP64-equivalent mode (gemm_fp64eq.cu): Ozaki-type BF16 digit slices
 size_t gemm_fp64eq_scratch_bytes(int m, int n, int k);
 int gemm_fp64eq_products(int k);
@@ -110,6 +112,7 @@ void gemm_fp64eq_shape(int k, int *beta, int *levels, int *k_block);
 void launch_gemm_fp64eq(int m, int n, int k, const double *A, long long lda, const double *B, long long ldb,
                         double *C, long long ldc, void *scratch, cudaStream_t s);
 unsigned gemm_fp64eq_check_error(void *scratch, cudaStream_t s);
+unsigned *gemm_fp64eq_error_word(void *scratch);
 
 // Grouped FFTs (batched function blocks): transforms of different lengths
 // and directions in two persistent launches.

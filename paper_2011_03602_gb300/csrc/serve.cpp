@@ -142,7 +142,8 @@ void plan_sizes(Server &S, SReq &q) {
         q.h_in1 = hput((size_t)r.k * r.n * 8);
         q.h_out = hput((size_t)r.m * r.n * 8);
         d = up256((size_t)r.m * r.k * 8) + up256((size_t)r.k * r.n * 8) + up256((size_t)r.m * r.n * 8) +
-            up256(gemm_scratch_bytes((int)r.m, (int)r.n, (int)r.k));
+            up256(r.prec == OO_PREC_FP64EQ ? gemm_fp64eq_scratch_bytes((int)r.m, (int)r.n, (int)r.k)
+                                           : gemm_scratch_bytes((int)r.m, (int)r.n, (int)r.k));
     } else if (r.kind == OO_BLOCK_FFT) {
         q.h_in0 = hput((size_t)r.n * 16);
         q.h_out = hput((size_t)r.n * 16);
@@ -162,7 +163,8 @@ void plan_sizes(Server &S, SReq &q) {
 
 void validate(const oo_serve_req &r) {
     if (r.kind == OO_BLOCK_GEMM) {
-        OO_REQUIRE(r.prec == OO_PREC_SPLIT3_BF16, OO_EINVAL, "unsupported precision pattern");
+        OO_REQUIRE(r.prec == OO_PREC_SPLIT3_BF16 || r.prec == OO_PREC_FP64EQ, OO_EINVAL,
+                   "unsupported precision pattern");
         OO_REQUIRE(r.m >= 1 && r.n >= 1 && r.k >= 1 && r.m <= 65536 && r.n <= 65536 && r.k <= 65536, OO_EINVAL,
                    "bad GEMM dimensions");
         OO_REQUIRE(r.in0 && r.in1 && r.out, OO_EINVAL, "null pointer");
@@ -198,12 +200,15 @@ void start(Server &S, SReq &q) {
         void *scratch = dev + a + b + cc;
         OO_CUDA_TRY(cudaMemcpyAsync(dA, hst + q.h_in0, (size_t)r.m * r.k * 8, cudaMemcpyHostToDevice, s));
         OO_CUDA_TRY(cudaMemcpyAsync(dB, hst + q.h_in1, (size_t)r.k * r.n * 8, cudaMemcpyHostToDevice, s));
-        launch_gemm_split3((int)r.m, (int)r.n, (int)r.k, dA, r.k, dB, r.n, dC, r.n, scratch, s);
+        const unsigned *err_d;
+        if (r.prec == OO_PREC_FP64EQ) {
+            launch_gemm_fp64eq((int)r.m, (int)r.n, (int)r.k, dA, r.k, dB, r.n, dC, r.n, scratch, s);
+            err_d = gemm_fp64eq_error_word(scratch);
+        } else {
+            launch_gemm_split3((int)r.m, (int)r.n, (int)r.k, dA, r.k, dB, r.n, dC, r.n, scratch, s);
+            err_d = gemm_error_word(scratch, (int)r.m, (int)r.n, (int)r.k);
+        }
         OO_CUDA_TRY(cudaMemcpyAsync(hst + q.h_out, dC, (size_t)r.m * r.n * 8, cudaMemcpyDeviceToHost, s));
-        // the GEMM kernel's error word sits after the split operands in its scratch
-        const int kp = (int)((r.k + 63) / 64 * 64);
-        const size_t ab = ((size_t)r.m * kp * 2 + 255) / 256 * 256, bb = ((size_t)r.n * kp * 2 + 255) / 256 * 256;
-        const char *err_d = static_cast<char *>(scratch) + 2 * ab + 2 * bb + ((size_t)r.m + r.n) * 4;
         OO_CUDA_TRY(cudaMemcpyAsync(err_h, err_d, 4, cudaMemcpyDeviceToHost, s));
     } else if (r.kind == OO_BLOCK_FFT) {
         double *dx = reinterpret_cast<double *>(dev);

@@ -94,3 +94,13 @@ def test_bad_lengths(oo_mod, ctx):
         oo_mod.oo_fft_c128(ctx, np.ones(12, complex))
     with pytest.raises(oo_mod.OOError):
         oo_mod.oo_fft_c128(ctx, np.ones(8, complex), 0)
+
+
+@pytest.mark.parametrize("logn", [23, 24])
+def test_maximum_lengths(oo_mod, ctx, logn):
+    """The two largest lengths (four-step with 2^12-point passes at 2^24)."""
+    n = 1 << logn
+    x = synth.complex_normal(3000 + logn, n)
+    got = oo_mod.oo_fft_c128(ctx, x, -1)
+    ref = oracle.fft(x, -1)
+    assert rel(got, ref) <= TOL, rel(got, ref)

@@ -133,3 +133,13 @@ def test_full_size_sampled_rows(oo_mod, ctx):
         ref = oracle.gemm(A[r:r + 1], B)
         e = np.max(np.abs(C[r] - ref[0]) / (np.abs(A[r]) @ np.abs(B)))
         assert e <= FP64EQ_TOL, (r, e)
+
+
+def test_long_inner_dimension(oo_mod, ctx):
+    """k = 20000: twenty exact K-blocks summed in float-float."""
+    m, n, k = 130, 70, 20000
+    A = synth.gemm_matrix(51, m, k)
+    B = synth.gemm_matrix(52, k, n)
+    C = gemm(oo_mod, ctx, A, B)
+    e = err_metric(C, oracle.gemm(A, B), A, B)
+    assert e <= FP64EQ_TOL, e

@@ -102,3 +102,11 @@ def test_full_size_sampled_rows(oo_mod, ctx):
 def test_bad_arguments(oo_mod, ctx):
     with pytest.raises(oo_mod.OOError):
         oo_mod.oo_gemm_f64(ctx, np.ones((3, 4)), np.ones((4, 5)), prec=7)
+
+
+def test_long_inner_dimension(oo_mod, ctx):
+    m, n, k = 130, 70, 20000
+    A = synth.gemm_matrix(53, m, k)
+    B = synth.gemm_matrix(54, k, n)
+    C = oo_mod.oo_gemm_f64(ctx, A, B)
+    assert err_metric(C, oracle.gemm(A, B), A, B) <= SPLIT3_TOL

@@ -29,7 +29,8 @@ def make_mix(seed, count):
         if u < 0.5:
             n = int(rng.integers(16, 300))
             A, B = synth.gemm_matrix(seed * 1000 + 2 * i, n, n + 3), synth.gemm_matrix(seed * 1000 + 2 * i + 1, n + 3, n)
-            out.append(("gemm", dict(A=A, B=B, C=np.empty((n, n)))))
+            prec = 2 if i % 2 else 0  # both precision patterns (FP64-equivalent, split-BF16)
+            out.append(("gemm", dict(A=A, B=B, C=np.empty((n, n)), prec=prec)))
         elif u < 0.8:
             n = 1 << int(rng.integers(0, 15))
             x = synth.complex_normal(seed * 1000 + i, n)
@@ -44,7 +45,7 @@ def make_mix(seed, count):
 
 def alone(oo, ctx, kind, kw):
     if kind == "gemm":
-        return oo.oo_gemm_f64(ctx, kw["A"], kw["B"])
+        return oo.oo_gemm_f64(ctx, kw["A"], kw["B"], prec=kw["prec"])
     if kind == "fft":
         return oo.oo_fft_c128(ctx, kw["x"], kw["dir"])
     p = np.empty(kw["I"] * kw["J"] * kw["K"], np.float32)
@@ -84,7 +85,8 @@ def test_each_result_same_alone_and_in_the_mix(oo_mod):
             if k == "gemm":
                 assert np.array_equal(kw["C"], r)
                 ref_o = oracle.gemm(kw["A"], kw["B"])
-                assert np.max(np.abs(kw["C"] - ref_o) / (np.abs(kw["A"]) @ np.abs(kw["B"]))) <= 1e-4
+                tol = 1e-12 if kw["prec"] == oo.OO_PREC_FP64EQ else 1e-4
+                assert np.max(np.abs(kw["C"] - ref_o) / (np.abs(kw["A"]) @ np.abs(kw["B"]))) <= tol
             elif k == "fft":
                 assert np.array_equal(kw["X"], r)
                 ref_o = oracle.fft(kw["x"], kw["dir"])
