@@ -52,7 +52,8 @@ enum {
     OO_ETOLERANCE = -5,  /* result outside the correctness tolerance          */
     OO_EBUSY = -6,       /* no slot / memory free right now (back-pressure)   */
     OO_ENOTFOUND = -7,   /* name not in the code-pattern table                */
-    OO_ESTATE = -8       /* call not valid in the context's current state     */
+    OO_ESTATE = -8,      /* call not valid in the context's current state     */
+    OO_EUSER = -9        /* a caller-supplied nest function reported failure  */
 };
 
 typedef struct oo_ctx oo_ctx;
@@ -180,6 +181,45 @@ oo_status oo_run_pattern(oo_ctx *ctx, uint64_t gene, int hoist,
 oo_status oo_run_pattern_dev(oo_ctx *ctx, uint64_t gene, int hoist,
                              const oo_jacobi *prob, float *p_dev,
                              double *res_dev, oo_run_stats *stats);
+
+/* ------------------------------------------------- generic loop programs */
+/* Sec. 4.3: the method on any program described by the loaded table
+ * (oo_load_nests).  The caller supplies the nests' bodies as one function:
+ *   fn(user, nest, on_gpu, iter, vars, stream) runs nest `nest` (index in
+ *   the table) for iteration `iter` (-1 for setup nests); on_gpu = 1: vars
+ *   are the DEVICE buffers and the work must be enqueued on `stream` (the
+ *   context's CUDA stream, a cudaStream_t), asynchronously; on_gpu = 0:
+ *   vars are the HOST buffers and the work is done before returning.
+ *   Returns 0, or nonzero to abort the run (OO_EUSER).                     */
+typedef int (*oo_nest_fn)(void *user, int nest, int on_gpu, int64_t iter, void *const *vars,
+                          void *stream);
+/* Result check of a finished run on the host buffers: 0 = acceptable.    */
+typedef int (*oo_check_fn)(void *user, void *const *host_vars);
+
+/* Run the loaded program once: setup nests (level 0) once, then level-1
+ * nests `iters` times, each on the side its gene bit chooses
+ * (non-parallelisable nests on the CPU), with the copies of
+ * oo_transfer_plan(gene, hoist, iters) made before each program point
+ * between host_vars[v] and dev_vars[v] (caller-owned, vars[v].bytes each;
+ * pinned host memory makes the copies asynchronous).  At the start the
+ * host buffers hold the current values; at the end every table output is
+ * current on the host.  A buffer may be NULL only for a variable no copy
+ * and no nest on that side uses.  Synchronous; stats (may be NULL) gets the
+ * wall time, copy bytes and count, and the number of GPU nest calls.       */
+oo_status oo_run_program(oo_ctx *ctx, uint64_t gene, int hoist, int iters, oo_nest_fn fn, void *user,
+                         void *const *host_vars, void *const *dev_vars, oo_run_stats *stats);
+
+/* Sec. 4.2.2 GA over the loaded program's genes (gene length 1..20):
+ * fitness from the measured wall time of oo_run_program, a gene whose
+ * result fails `check` (may be NULL) counting as infinitely slow.  The host
+ * buffers are re-initialised by the program's setup nests on every run, so
+ * the program must compute all of its state from its setup nests.
+ * history (gens x pop genes) and gene_ms (2^L, infinity = not measured or
+ * failed) may be NULL.                                                    */
+oo_status oo_ga_program(oo_ctx *ctx, int hoist, int iters, oo_nest_fn fn, oo_check_fn check, void *user,
+                        void *const *host_vars, void *const *dev_vars, int pop, int gens, double pc,
+                        double pm, uint64_t seed, uint64_t *best_gene, double *best_ms, uint64_t *history,
+                        double *gene_ms);
 
 /* One stencil sweep (nest N2) on caller-owned device arrays.  Every array is
  * I x J x pitch floats (pitch >= K, pitch % 4 == 0, k fastest, base 16-byte

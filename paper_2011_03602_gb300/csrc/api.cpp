@@ -81,6 +81,7 @@ const char *oo_status_str(oo_status s) {
         case OO_EBUSY: return "busy";
         case OO_ENOTFOUND: return "not found";
         case OO_ESTATE: return "invalid state";
+        case OO_EUSER: return "nest function failed";
         default: return "unknown status";
     }
 }
@@ -499,6 +500,33 @@ oo_status oo_offload_search(oo_ctx *ctx, const oo_fb_site *sites, int n_sites, i
     // nests are not part of any library call site)
     return oo_ga_search(ctx, prob, hoist, pop, gens, pc, pm, ga_seed, eval_timeout_ms, best_gene, loop_ms, nullptr,
                         nullptr);
+}
+
+oo_status oo_run_program(oo_ctx *ctx, uint64_t gene, int hoist, int iters, oo_nest_fn fn, void *user,
+                         void *const *host_vars, void *const *dev_vars, oo_run_stats *stats) {
+    if (!ctx) return OO_EINVAL;
+    return guarded(ctx, [&] {
+        use_device(ctx->c);
+        run_program(ctx->c, gene, hoist, iters, fn, user, host_vars, dev_vars, stats);
+    });
+}
+
+oo_status oo_ga_program(oo_ctx *ctx, int hoist, int iters, oo_nest_fn fn, oo_check_fn check, void *user,
+                        void *const *host_vars, void *const *dev_vars, int pop, int gens, double pc,
+                        double pm, uint64_t seed, uint64_t *best_gene, double *best_ms, uint64_t *history,
+                        double *gene_ms) {
+    if (!ctx) return OO_EINVAL;
+    return guarded(ctx, [&] {
+        OO_REQUIRE(best_gene && best_ms, OO_EINVAL, "null pointer");
+        use_device(ctx->c);
+        std::vector<double> gm;
+        const GaResult r = ga_program(ctx->c, hoist, iters, fn, check, user, host_vars, dev_vars, pop, gens, pc,
+                                      pm, seed, gene_ms ? &gm : nullptr);
+        if (history) std::memcpy(history, r.history.data(), r.history.size() * 8);
+        if (gene_ms) std::memcpy(gene_ms, gm.data(), gm.size() * sizeof(double));
+        *best_gene = r.best_gene;
+        *best_ms = r.best_time;
+    });
 }
 
 }  // extern "C"

@@ -263,6 +263,13 @@ struct GaResult {
 GaResult ga_run(int L, int pop, int gens, double pc, double pm, uint64_t seed,
                 const std::function<double(uint64_t)> &time_of);
 
+// Generic loop programs (program.cpp).
+void run_program(Ctx &c, uint64_t gene, int hoist, int iters, oo_nest_fn fn, void *user, void *const *host_vars,
+                 void *const *dev_vars, oo_run_stats *stats);
+GaResult ga_program(Ctx &c, int hoist, int iters, oo_nest_fn fn, oo_check_fn check, void *user,
+                    void *const *host_vars, void *const *dev_vars, int pop, int gens, double pc, double pm,
+                    uint64_t seed, std::vector<double> *gene_ms);
+
 // Function-block lookup (blocks.cpp).
 int lookup_block(const char *callee, int lang);
 

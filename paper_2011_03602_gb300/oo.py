@@ -16,7 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liboo.so")
 
 OO_OK, OO_EINVAL, OO_ENOMEM, OO_ECUDA, OO_ETIMEOUT = 0, -1, -2, -3, -4
-OO_ETOLERANCE, OO_EBUSY, OO_ENOTFOUND, OO_ESTATE = -5, -6, -7, -8
+OO_ETOLERANCE, OO_EBUSY, OO_ENOTFOUND, OO_ESTATE, OO_EUSER = -5, -6, -7, -8, -9
 OO_BLOCK_GEMM, OO_BLOCK_FFT = 1, 2
 OO_LANG_C, OO_LANG_PYTHON, OO_LANG_JAVA = 0, 1, 2
 
@@ -80,6 +80,10 @@ class oo_run_stats(_c.Structure):
                 "n_xfers": self.n_xfers, "n_launches": self.n_launches}
 
 
+# generic loop programs: nest body and result check callbacks
+OO_NEST_FN = _c.CFUNCTYPE(_c.c_int, _vp, _c.c_int, _c.c_int, _c.c_int64, _c.POINTER(_vp), _vp)
+OO_CHECK_FN = _c.CFUNCTYPE(_c.c_int, _vp, _c.POINTER(_vp))
+
 _lib = None
 
 
@@ -125,6 +129,9 @@ def lib():
         "oo_offload_search": (_c.c_int, [_vp, _vp, _c.c_int, _c.c_int, _dbl, _u64, P(oo_jacobi), _c.c_int,
                                          _c.c_int, _c.c_int, _dbl, _dbl, _u64, _dbl, P(_c.c_uint32), P(_u64),
                                          P(_dbl), P(_dbl)]),
+        "oo_run_program": (_c.c_int, [_vp, _u64, _c.c_int, _c.c_int, OO_NEST_FN, _vp, _vp, _vp, P(oo_run_stats)]),
+        "oo_ga_program": (_c.c_int, [_vp, _c.c_int, _c.c_int, OO_NEST_FN, OO_CHECK_FN, _vp, _vp, _vp, _c.c_int,
+                                     _c.c_int, _dbl, _dbl, _u64, P(_u64), P(_dbl), _vp, _vp]),
         "oo_gemm_plan": (_c.c_int, [_c.c_int, _c.c_int, P(_c.c_int), P(_c.c_int), P(_c.c_int), P(_c.c_int)]),
         "oo_batch_create": (_c.c_int, [_vp, P(oo_req), _c.c_int, P(_vp)]),
         "oo_batch_run": (_c.c_int, [_vp, _c.c_int]),
@@ -310,6 +317,64 @@ def oo_ga_search(ctx, prob, hoist, pop, gens, pc, pm, seed, eval_timeout_ms=0.0)
                                    hist.ctypes.data_as(_vp), gene_ms.ctypes.data_as(_vp)))
     return {"best_gene": bg.value, "best_ms": bt.value, "history": hist.reshape(gens, pop),
             "gene_ms": gene_ms}
+
+
+# ------------------------------------------------- generic loop programs
+def _addr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise TypeError("host buffers must be C-contiguous")
+        return x.ctypes.data
+    return _dev_ptr(x).value
+
+
+def _ptr_array(bufs):
+    arr = (_vp * len(bufs))()
+    for i, b in enumerate(bufs):
+        arr[i] = _addr(b)
+    return arr
+
+
+def _nest_callback(body):
+    """body(nest, on_gpu, iteration, stream_handle) -> None; exceptions abort the run."""
+    def cb(user, nest, on_gpu, it, vars_, stream):
+        try:
+            body(nest, bool(on_gpu), it, stream)
+            return 0
+        except Exception:  # reported to the library as a failed nest
+            import traceback
+            traceback.print_exc()
+            return 1
+    return OO_NEST_FN(cb)
+
+
+def oo_run_program(ctx, gene, hoist, iters, body, host_vars, dev_vars):
+    """Run the loaded table's program; body(nest, on_gpu, iteration, stream)
+    executes a nest on the caller's own host / device buffers (the same
+    objects passed here, in table order).  Returns the stats dict."""
+    cb = _nest_callback(body)
+    st = oo_run_stats()
+    _check(ctx, lib().oo_run_program(ctx, gene, hoist, iters, cb, None, _ptr_array(host_vars),
+                                     _ptr_array(dev_vars), _c.byref(st)))
+    return st.as_dict()
+
+
+def oo_ga_program(ctx, gene_len, hoist, iters, body, host_vars, dev_vars, pop, gens, pc, pm, seed, check=None):
+    """GA over the loaded program's genes (gene_len as oo_load_nests returned
+    it); check() -> bool judges the result left in the host buffers."""
+    cb = _nest_callback(body)
+    ck = OO_CHECK_FN(lambda user, hv: 0 if check is None or check() else 1)
+    hist = np.empty(gens * pop, np.uint64)
+    bg, bt = _u64(), _dbl()
+    gm = np.empty(1 << gene_len, np.float64)
+    _check(ctx, lib().oo_ga_program(ctx, hoist, iters, cb, ck, None, _ptr_array(host_vars), _ptr_array(dev_vars),
+                                    pop, gens, pc, pm, seed, _c.byref(bg), _c.byref(bt),
+                                    hist.ctypes.data_as(_vp), gm.ctypes.data_as(_vp)))
+    return {"best_gene": bg.value, "best_ms": bt.value, "history": hist.reshape(gens, pop), "gene_ms": gm}
 
 
 # ------------------------------------------- function-block trial order

@@ -104,3 +104,15 @@ def test_gemm_plan_follows_the_exactness_rule():
     assert oo.oo_gemm_plan(oo.OO_PREC_FP64EQ, 4096)[:3] == (28, 7, 8)
     with pytest.raises(oo.OOError):
         oo.oo_gemm_plan(1, 64)
+
+
+def test_generic_program_needs_a_device_and_a_table():
+    ctx = oo.oo_create(-1)
+    try:
+        body = lambda nest, on_gpu, it, stream: None  # noqa: E731
+        with pytest.raises(oo.OOError) as e:
+            oo.oo_run_program(ctx, 0, 1, 1, body, [None], [None])
+        assert e.value.status == oo.OO_ESTATE
+    finally:
+        oo.oo_destroy(ctx)
+    assert oo.oo_status_str(oo.OO_EUSER) == "nest function failed"
