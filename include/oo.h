@@ -282,7 +282,10 @@ enum { OO_BLOCK_GEMM = 1, OO_BLOCK_FFT = 2 };
 enum { OO_LANG_C = 0, OO_LANG_PYTHON = 1, OO_LANG_JAVA = 2 };
 
 /* Sec. 3.2.2 / Sec. 4.2.1 name match: look a callee name up in the
- * code-pattern table for language `lang`.  OO_ENOTFOUND if absent.       */
+ * code-pattern table for language `lang`.  Spelling variants of a table
+ * entry are accepted: Python import aliases (np., sp., la.) and module
+ * re-exports, C BLAS names in any case, Java Class.method without its
+ * package when that suffix names one block.  OO_ENOTFOUND if absent.     */
 oo_status oo_lookup_block(const char *callee, int lang, int *block_id);
 
 /* Sec. 3.2.2 matrix-product block: C = A B for FP64 row-major A (m x k,

@@ -50,6 +50,21 @@ def test_lookup_block_by_language():
     assert e.value.status == oo.OO_ENOTFOUND
 
 
+def test_lookup_accepts_spelling_variants():
+    assert oo.oo_lookup_block("np.dot", oo.OO_LANG_PYTHON) == oo.OO_BLOCK_GEMM
+    assert oo.oo_lookup_block("np.fft.fft", oo.OO_LANG_PYTHON) == oo.OO_BLOCK_FFT
+    assert oo.oo_lookup_block("sp.fft.fft", oo.OO_LANG_PYTHON) == oo.OO_BLOCK_FFT
+    assert oo.oo_lookup_block("la.blas.dgemm", oo.OO_LANG_PYTHON) == oo.OO_BLOCK_GEMM
+    assert oo.oo_lookup_block("DGEMM", oo.OO_LANG_C) == oo.OO_BLOCK_GEMM
+    assert oo.oo_lookup_block("DoubleFFT_1D.complexForward", oo.OO_LANG_JAVA) == oo.OO_BLOCK_FFT
+    assert oo.oo_lookup_block("CommonOps_DDRM.mult", oo.OO_LANG_JAVA) == oo.OO_BLOCK_GEMM
+    for name, lang in (("np.linalg.svd", oo.OO_LANG_PYTHON), ("FFT_1D.complexForward", oo.OO_LANG_JAVA),
+                       ("multiply", oo.OO_LANG_JAVA), ("dgemm", oo.OO_LANG_PYTHON)):
+        with pytest.raises(oo.OOError) as e:
+            oo.oo_lookup_block(name, lang)
+        assert e.value.status == oo.OO_ENOTFOUND
+
+
 def test_host_only_context_rejects_gpu_work():
     ctx = oo.oo_create(-1)
     try:
