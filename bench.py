@@ -120,6 +120,19 @@ def dist_env():
     return ws, rank, local
 
 
+def replica_max(pg, seconds, device):
+    """Slowest rank's duration.  Every rank runs the same independent replica
+    (patterns, GEMMs, FFTs and requests are independent problems: no
+    data-path collective), so whole-job throughput is world_size x the
+    per-rank work divided by this."""
+    if pg is None:
+        return seconds
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
 def oracle_sample(iters):
     """The oracle as it stands on a bounded sample: the whole program at full
     grid size for `iters` iterations, single-threaded FP64 C."""
@@ -309,11 +322,7 @@ def run_gpu(args):
             oo.oo_run_pattern_dev(ctx, GENE, HOIST, prob, p_dev, r_dev)
         e1.record(stream)
         barrier()
-    ms = e0.elapsed_time(e1)
-    if pg is not None:
-        t = torch.tensor([ms], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = replica_max(pg, e0.elapsed_time(e1), "cuda")
     ms_step = ms / args.steps
     value = ws * pattern_bytes() / (ms_step * 1e-3) / 1e9
     res_check = r_dev.cpu().numpy()
@@ -333,11 +342,7 @@ def run_gpu(args):
     t0 = time.perf_counter()
     for _ in range(args.steps):
         oo.oo_run_pattern(ctx, GENE, HOIST, prob, p_host, r_host)
-    e2e_s = time.perf_counter() - t0
-    if pg is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = replica_max(pg, time.perf_counter() - t0, "cuda")
     e2e = ws * pattern_bytes() * args.steps / e2e_s / 1e9
     blocks = None
     if not args.no_blocks:

@@ -368,6 +368,55 @@ __global__ void split_rows_fused_kernel(const double *A, long long lda, int m, i
     split_row_warp(A + (long long)row * lda, k, kp, ea + row, A1 + (long long)row * kp, A2 + (long long)row * kp);
 }
 
+// Same, one 256-thread CTA per row with 16-byte loads (lda even, A 16-byte
+// aligned): the second read of the row hits L1 and each thread keeps eight
+// loads in flight in the exponent pass.
+__global__ void __launch_bounds__(256) split_rows_v2_kernel(const double *A, long long lda, int m, int k, int kp,
+                                                          int *ea, __nv_bfloat16 *A1, __nv_bfloat16 *A2) {
+    const int row = blockIdx.x;
+    const double *base = A + (long long)row * lda;
+    const double2 *src = reinterpret_cast<const double2 *>(base);
+    const int k2 = k >> 1;
+    int mx = 0;
+    auto ex = [](double x) {
+        const int e = (int)((__double_as_longlong(x) >> 52) & 0x7ff);
+        return e == 0x7ff ? 0x7fe : e;
+    };
+#pragma unroll 8
+    for (int l2 = threadIdx.x; l2 < k2; l2 += 256) {
+        const double2 v = src[l2];
+        mx = max(mx, max(ex(v.x), ex(v.y)));
+    }
+    if ((k & 1) && threadIdx.x == 0) mx = max(mx, ex(base[k - 1]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    __shared__ int red[8];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    mx = red[0];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) mx = max(mx, red[w]);
+    const int S = mx == 0 ? 0 : mx - 1023 + 1;
+    if (threadIdx.x == 0) ea[row] = S;
+    __nv_bfloat162 *d1 = reinterpret_cast<__nv_bfloat162 *>(A1 + (long long)row * kp);
+    __nv_bfloat162 *d2 = reinterpret_cast<__nv_bfloat162 *>(A2 + (long long)row * kp);
+#pragma unroll 2
+    for (int l2 = threadIdx.x; l2 < kp / 2; l2 += 256) {
+        const int l = 2 * l2;
+        double2 v = make_double2(0.0, 0.0);
+        if (l + 1 < k) {
+            v = src[l2];
+        } else if (l < k) {
+            v.x = base[l];
+        }
+        __nv_bfloat16 h0, o0, h1, o1;
+        split_bf16(v.x, S, h0, o0);
+        split_bf16(v.y, S, h1, o1);
+        d1[l2] = __halves2bfloat162(h0, h1);
+        d2[l2] = __halves2bfloat162(o0, o1);
+    }
+}
+
 // One 64 (k) x 64 (column) tile of B -> transposed BF16 hi / lo tiles of
 // B1t, B2t (n x kp); 256 threads, through shared memory.
 __device__ __forceinline__ void split_b_tile(const double *B, long long ldb, int k, int n, int kp, const int *eb,
@@ -376,7 +425,7 @@ __device__ __forceinline__ void split_b_tile(const double *B, long long ldb, int
     const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;  // 64 x 4
     const int col = c0 + tx;
     const int S = col < n ? eb[col] : 0;
-#pragma unroll 4
+#pragma unroll
     for (int yy = ty; yy < 64; yy += 4) {
         const int l = l0 + yy;
         __nv_bfloat16 h = __float2bfloat16_rn(0.0f), lo = h;
@@ -495,7 +544,10 @@ void launch_gemm_split3(int m, int n, int k, const double *A, long long lda, con
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         (void)sms;
-        split_rows_fused_kernel<<<(m + 7) / 8, 256, 0, s>>>(A, lda, m, k, kp, ea, A1, A2);
+        if (lda % 2 == 0 && ((uintptr_t)A & 15u) == 0)
+            split_rows_v2_kernel<<<m, 256, 0, s>>>(A, lda, m, k, kp, ea, A1, A2);
+        else
+            split_rows_fused_kernel<<<(m + 7) / 8, 256, 0, s>>>(A, lda, m, k, kp, ea, A1, A2);
         OO_CUDA_TRY(cudaGetLastError());
         dim3 grid((n + 63) / 64, kp / 64);
         OO_REQUIRE(grid.y <= 65535, OO_EINVAL, "k too large");

@@ -384,6 +384,49 @@ __global__ void eq_split_rows_kernel(const double *A, long long lda, int m, int 
     }
 }
 
+// Same split, one 256-thread CTA per row and 16-byte loads (lda even, A
+// 16-byte aligned): the row's second read hits L1, and each thread keeps
+// eight loads in flight in the exponent pass.
+__global__ void __launch_bounds__(256) eq_split_rows_v2_kernel(const double *A, long long lda, int m, int k, int kp,
+                                                             int beta, int s, int *ea, __nv_bfloat16 *As) {
+    const int row = blockIdx.x;
+    const double2 *src = reinterpret_cast<const double2 *>(A + (long long)row * lda);
+    const int k2 = k >> 1;
+    int mx = 0;
+#pragma unroll 8
+    for (int l2 = threadIdx.x; l2 < k2; l2 += 256) {
+        const double2 v = src[l2];
+        mx = max(mx, max(eff_exp(v.x), eff_exp(v.y)));
+    }
+    if ((k & 1) && threadIdx.x == 0) mx = max(mx, eff_exp(A[(long long)row * lda + k - 1]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    __shared__ int red[8];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    mx = red[0];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) mx = max(mx, red[w]);
+    if (threadIdx.x == 0) ea[row] = mx == 0 ? 0 : mx - 1022;
+    const size_t plane2 = (size_t)m * kp / 2;
+    __nv_bfloat162 *dst = reinterpret_cast<__nv_bfloat162 *>(As + (size_t)row * kp);
+#pragma unroll 2
+    for (int l2 = threadIdx.x; l2 < kp / 2; l2 += 256) {
+        const int l = 2 * l2;
+        double2 v = make_double2(0.0, 0.0);
+        if (l + 1 < k) {
+            v = src[l2];
+        } else if (l < k) {
+            v.x = A[(long long)row * lda + l];
+        }
+        unsigned n0 = 0, n1 = 0;
+        const unsigned long long X0 = mx != 0 ? fixed_frac(v.x, mx, n0) : 0ull;
+        const unsigned long long X1 = mx != 0 ? fixed_frac(v.y, mx, n1) : 0ull;
+        for (int p = 0; p < s; ++p)
+            dst[p * plane2 + l2] = __halves2bfloat162(digit(X0, n0, beta, p), digit(X1, n1, beta, p));
+    }
+}
+
 // largest effective exponent of each column of B (k x n); grid.x column
 // blocks of 32, grid.y row chunks
 __global__ void eq_col_maxexp_kernel(const double *B, long long ldb, int k, int n, int rows_per, int *mxo) {
@@ -403,7 +446,7 @@ __global__ void eq_split_cols_t_kernel(const double *B, long long ldb, int k, in
     __shared__ double t[64][65];
     const int c0 = blockIdx.x * 64, l0 = blockIdx.y * 64;
     const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
-#pragma unroll 4
+#pragma unroll
     for (int yy = ty; yy < 64; yy += 4) {
         const int l = l0 + yy, c = c0 + tx;
         t[yy][tx] = (l < k && c < n) ? B[(long long)l * ldb + c] : 0.0;
@@ -488,7 +531,10 @@ void launch_gemm_fp64eq(int m, int n, int k, const double *A, long long lda, con
         eq_col_scale_kernel<<<(n + 255) / 256, 256, 0, s>>>(mxo, eb, n);
         OO_CUDA_TRY(cudaGetLastError());
     }
-    eq_split_rows_kernel<<<(m + 7) / 8, 256, 0, s>>>(A, lda, m, k, kp, e.beta, e.slices, ea, As);
+    if (lda % 2 == 0 && ((uintptr_t)A & 15u) == 0)
+        eq_split_rows_v2_kernel<<<m, 256, 0, s>>>(A, lda, m, k, kp, e.beta, e.slices, ea, As);
+    else
+        eq_split_rows_kernel<<<(m + 7) / 8, 256, 0, s>>>(A, lda, m, k, kp, e.beta, e.slices, ea, As);
     OO_CUDA_TRY(cudaGetLastError());
     {
         dim3 grid((n + 63) / 64, kp / 64);
