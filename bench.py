@@ -68,7 +68,11 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_bench_%d.csv" % index)
+        # raw samples (the JSON line carries their summary); directory from
+        # OO_CLOCKS_DIR, else the system temporary directory
+        import tempfile
+        self.path = os.path.join(os.environ.get("OO_CLOCKS_DIR", tempfile.gettempdir()),
+                                 "clocks_bench_%d.csv" % index)
 
     def __enter__(self):
         try:
