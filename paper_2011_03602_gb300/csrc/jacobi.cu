@@ -158,24 +158,28 @@ __global__ void pinit_kernel(float *p, float *wrk2, int rows, int pitch, int K) 
     }
 }
 
-// interior rows (I-2)*(J-2); chunks cover k in [0, 4*ceil((K-1)/4))
-__global__ void copyback_kernel(float *p, const float *wrk2, int I, int J, int K, int pitch) {
-    const unsigned chunks = (unsigned)(K - 1 + 3) / 4u;
-    const unsigned jr = (unsigned)(J - 2);
-    const size_t total = (size_t)(I - 2) * jr * chunks;
-    const size_t step = (size_t)gridDim.x * blockDim.x;
-    for (size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x; x < total; x += step) {
-        const unsigned c = (unsigned)(x % chunks);
-        const size_t row = x / chunks;
-        const int i = 1 + (int)(row / jr), j = 1 + (int)(row % jr);
-        const size_t off = ((size_t)i * J + j) * pitch + 4u * c;
-        const int k = 4 * (int)c;
-        if (k >= 1 && k + 3 <= K - 2) {
-            reinterpret_cast<float4 *>(p + off)[0] = reinterpret_cast<const float4 *>(wrk2 + off)[0];
-        } else {
+// One warp per interior row (i, j): its lanes copy the row's float4 chunks
+// (k in [0, 4 ceil((K-1)/4))), interior k only; one division per row.
+__global__ void copyback_kernel(float *__restrict__ p, const float *__restrict__ wrk2, int I, int J, int K,
+                                int pitch) {
+    const long long jr = J - 2, rows = (long long)(I - 2) * jr;
+    const int chunks = (K - 1 + 3) / 4;
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    for (long long r = (long long)blockIdx.x * wpb + (threadIdx.x >> 5); r < rows; r += (long long)gridDim.x * wpb) {
+        const long long i = 1 + r / jr, j = 1 + r % jr;
+        const size_t off = ((size_t)i * J + (size_t)j) * pitch;
+        const float4 *src = reinterpret_cast<const float4 *>(wrk2 + off);
+        float4 *dst = reinterpret_cast<float4 *>(p + off);
+#pragma unroll 4
+        for (int c = lane; c < chunks; c += 32) {
+            const int k = 4 * c;
+            if (k >= 1 && k + 3 <= K - 2) {
+                dst[c] = src[c];
+            } else {
 #pragma unroll
-            for (int e = 0; e < 4; ++e)
-                if (k + e >= 1 && k + e <= K - 2) p[off + e] = wrk2[off + e];
+                for (int e = 0; e < 4; ++e)
+                    if (k + e >= 1 && k + e <= K - 2) p[off + k + e] = wrk2[off + k + e];
+            }
         }
     }
 }
@@ -249,9 +253,8 @@ void launch_pinit(const JacobiDims &d, float *p, float *wrk2, cudaStream_t s) {
 }
 
 void launch_copyback(const JacobiDims &d, float *p, const float *wrk2, cudaStream_t s) {
-    const size_t work = (size_t)(d.I - 2) * (d.J - 2) * ((d.K + 2) / 4);
-    copyback_kernel<<<grid_for(work, 256, sm_count() * 8), 256, 0, s>>>(p, wrk2, d.I, d.J, d.K,
-                                                                          d.pitch);
+    const size_t rows = (size_t)(d.I - 2) * (d.J - 2);  // one warp each, 8 warps per block
+    copyback_kernel<<<grid_for(rows, 8, sm_count() * 16), 256, 0, s>>>(p, wrk2, d.I, d.J, d.K, d.pitch);
     OO_CUDA_TRY(cudaGetLastError());
 }
 
