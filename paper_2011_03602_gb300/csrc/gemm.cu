@@ -80,6 +80,7 @@ struct TileJob {
     long long ldc;
     const int *ea, *eb;
     int m, n, m0, n0, ksteps;
+    int ra, rb;  // first row of this problem's A / B operands in the tensor maps
 };
 
 // Single problem: tensor maps are kernel parameters, tiles in grouped raster order.
@@ -91,21 +92,26 @@ struct SingleSrc {
         int m0, n0;
         tile_coords(*a, t, m0, n0);
         return TileJob{&maps->a1, &maps->a2, &maps->b1, &maps->b2, a->C, a->ldc, a->ea, a->eb,
-                       a->m, a->n, m0, n0, a->kp / kBK};
+                       a->m, a->n, m0, n0, a->kp / kBK, 0, 0};
     }
 };
 
-// Many problems: each has its own tensor maps in global memory; the tile
-// list (problem, m0, n0, k steps) is sorted by work so the round-robin
-// assignment to persistent CTAs stays balanced.
-struct alignas(128) GroupProblem {
-    CUtensorMap a1, a2, b1, b2;
+// Many problems: every problem's split operands are stacked in four shared
+// arrays (row pitch = the group's largest padded K), so four tensor maps,
+// passed as kernel parameters like the single-problem ones, cover them
+// all and a problem is a row offset.  (Per-problem tensor maps read from
+// global memory starved the TMA unit: ~0.76 TB/s of operand traffic.)  The
+// tile list (problem, m0, n0, k steps) is sorted by work so the
+// round-robin assignment to persistent CTAs stays balanced.
+struct GroupProblem {
     double *C;
     long long ldc;
     const int *ea, *eb;
     int m, n, k, kp;
+    int ra, rb;
 };
 struct GroupSrc {
+    const GemmMaps *maps;
     const GroupProblem *probs;
     const int4 *tiles;
     int ntiles;
@@ -113,7 +119,8 @@ struct GroupSrc {
     __device__ __forceinline__ TileJob job(int t) const {
         const int4 td = tiles[t];
         const GroupProblem &P = probs[td.x];
-        return TileJob{&P.a1, &P.a2, &P.b1, &P.b2, P.C, P.ldc, P.ea, P.eb, P.m, P.n, td.y, td.z, td.w};
+        return TileJob{&maps->a1, &maps->a2, &maps->b1, &maps->b2, P.C, P.ldc, P.ea, P.eb,
+                       P.m, P.n, td.y, td.z, td.w, P.ra, P.rb};
     }
 };
 
@@ -174,10 +181,10 @@ __device__ __forceinline__ void gemm_body(const Src &src, unsigned *err) {
                 const uint32_t fb = su32(&full[s]);
                 bar_expect_tx(fb, kStageBytes);
                 const int k0 = ks * kBK;
-                tma_2d(su32(st), jb.a1, k0, jb.m0, fb);
-                tma_2d(su32(st + kTileA), jb.a2, k0, jb.m0, fb);
-                tma_2d(su32(st + 2 * kTileA), jb.b1, k0, jb.n0, fb);
-                tma_2d(su32(st + 2 * kTileA + kTileB), jb.b2, k0, jb.n0, fb);
+                tma_2d(su32(st), jb.a1, k0, jb.ra + jb.m0, fb);
+                tma_2d(su32(st + kTileA), jb.a2, k0, jb.ra + jb.m0, fb);
+                tma_2d(su32(st + 2 * kTileA), jb.b1, k0, jb.rb + jb.n0, fb);
+                tma_2d(su32(st + 2 * kTileA + kTileB), jb.b2, k0, jb.rb + jb.n0, fb);
                 ++loaded;
             }
         }
@@ -221,32 +228,52 @@ __device__ __forceinline__ void gemm_body(const Src &src, unsigned *err) {
         int lt = 0;
         for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++lt) {
             const int b = lt & 1;
-            if (!bar_wait(su32(&tfull[b]), (lt >> 1) & 1, abort_flag, err, 4u)) break;
-            fence_after();
+            // the tile's descriptor and scales are fetched before waiting for
+            // its accumulators, so their latency overlaps the MMAs: lane l
+            // holds the column scales of columns l, l + 32, l + 64, l + 96
+            // (coalesced) and hands them out by shuffle
             const TileJob jb = src.job(t);
             const int n0 = jb.n0;
             const int row = jb.m0 + q * 32 + lane;
             const bool row_ok = row < jb.m;
             const int sa = row_ok ? jb.ea[row] : 0;
+            static_assert(kBN == 128, "four 32-column chunks");
+            int e_cur, e_n1, e_n2, e_n3;  // column scales of chunks 0..3 (rotated per chunk)
+            {
+                auto ld = [&](int c4) {
+                    const int col = n0 + c4 * 32 + lane;
+                    return col < jb.n ? jb.eb[col] : 0;
+                };
+                e_cur = ld(0);
+                e_n1 = ld(1);
+                e_n2 = ld(2);
+                e_n3 = ld(3);
+            }
+            if (!bar_wait(su32(&tfull[b]), (lt >> 1) & 1, abort_flag, err, 4u)) break;
+            fence_after();
             double *crow = jb.C + (long long)row * jb.ldc;
             const uint32_t lane_off = (uint32_t)(q * 32) << 16;
             const uint32_t d_hh = tmem + (uint32_t)(b * 256), d_x = d_hh + 128;
+#pragma unroll 1
             for (int c = 0; c < kBN; c += 32) {
                 uint32_t h[32], x[32];
                 OO_TMEM_LD32(d_hh + lane_off + c, h);
                 OO_TMEM_LD32(d_x + lane_off + c, x);
                 asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (!row_ok) continue;
 #pragma unroll
                 for (int t2 = 0; t2 < 32; ++t2) {
+                    const int sb = __shfl_sync(0xffffffffu, e_cur, t2);
                     const int col = n0 + c + t2;
-                    if (col < jb.n) {
+                    if (row_ok && col < jb.n) {
                         // exact two-sum of the partial products, widened and scaled
                         // without the (slow) FP64 pipe
                         const double v = ff::to_double(__uint_as_float(h[t2]), __uint_as_float(x[t2]));
-                        crow[col] = ff::scale_pow2(v, sa + jb.eb[col]);
+                        crow[col] = ff::scale_pow2(v, sa + sb);
                     }
                 }
+                e_cur = e_n1;
+                e_n1 = e_n2;
+                e_n2 = e_n3;
             }
             fence_before();
             __syncwarp();
@@ -284,9 +311,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_split3_kernel(const __gr
     gemm_body(src, a.err);
 }
 
-__global__ void __launch_bounds__(kGemmThreads, 1) gemm_group_kernel(const GroupProblem *probs, const int4 *tiles,
+__global__ void __launch_bounds__(kGemmThreads, 1) gemm_group_kernel(const __grid_constant__ GemmMaps maps,
+                                                                    const GroupProblem *probs, const int4 *tiles,
                                                                     int ntiles, unsigned *err) {
-    const GroupSrc src{probs, tiles, ntiles};
+    const GroupSrc src{&maps, probs, tiles, ntiles};
     gemm_body(src, err);
 }
 
@@ -419,8 +447,9 @@ __global__ void __launch_bounds__(256) split_rows_v2_kernel(const double *A, lon
 
 // One 64 (k) x 64 (column) tile of B -> transposed BF16 hi / lo tiles of
 // B1t, B2t (n x kp); 256 threads, through shared memory.
-__device__ __forceinline__ void split_b_tile(const double *B, long long ldb, int k, int n, int kp, const int *eb,
-                                             __nv_bfloat16 *B1t, __nv_bfloat16 *B2t, int l0, int c0) {
+// (B1t, B2t rows `pitch` elements apart; columns [0, kp) written)
+__device__ __forceinline__ void split_b_tile(const double *B, long long ldb, int k, int n, int kp, long long pitch,
+                                             const int *eb, __nv_bfloat16 *B1t, __nv_bfloat16 *B2t, int l0, int c0) {
     __shared__ __nv_bfloat16 th[64][66], tl[64][66];
     const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;  // 64 x 4
     const int col = c0 + tx;
@@ -441,8 +470,8 @@ __device__ __forceinline__ void split_b_tile(const double *B, long long ldb, int
         const int c = c0 + cc;
         const int l = l0 + 2 * lane;
         if (c < n && l < kp) {
-            __nv_bfloat162 *o1 = reinterpret_cast<__nv_bfloat162 *>(B1t + (long long)c * kp + l);
-            __nv_bfloat162 *o2 = reinterpret_cast<__nv_bfloat162 *>(B2t + (long long)c * kp + l);
+            __nv_bfloat162 *o1 = reinterpret_cast<__nv_bfloat162 *>(B1t + (long long)c * pitch + l);
+            __nv_bfloat162 *o2 = reinterpret_cast<__nv_bfloat162 *>(B2t + (long long)c * pitch + l);
             *o1 = __halves2bfloat162(th[2 * lane][cc], th[2 * lane + 1][cc]);
             *o2 = __halves2bfloat162(tl[2 * lane][cc], tl[2 * lane + 1][cc]);
         }
@@ -452,7 +481,7 @@ __device__ __forceinline__ void split_b_tile(const double *B, long long ldb, int
 // B (k x n, ldb) -> B1t, B2t (n x kp, transposed), zero padding in [k, kp)
 __global__ void split_cols_t_kernel(const double *B, long long ldb, int k, int n, int kp, const int *eb,
                                     __nv_bfloat16 *B1t, __nv_bfloat16 *B2t) {
-    split_b_tile(B, ldb, k, n, kp, eb, B1t, B2t, blockIdx.y * 64, blockIdx.x * 64);
+    split_b_tile(B, ldb, k, n, kp, kp, eb, B1t, B2t, blockIdx.y * 64, blockIdx.x * 64);
 }
 
 // ------------------------------------------------------- grouped splitting
@@ -460,7 +489,8 @@ struct GroupSplit {
     const double *A, *B;
     long long lda, ldb;
     int m, n, k, kp;
-    __nv_bfloat16 *A1, *A2, *B1, *B2;
+    long long pitch;                    // row pitch of the stacked split operands
+    __nv_bfloat16 *A1, *A2, *B1, *B2;   // this problem's first rows in them
     int *ea, *eb;
 };
 
@@ -470,8 +500,8 @@ __global__ void split_a_group_kernel(const GroupSplit *gs, const int2 *jobs) {
     const GroupSplit &G = gs[jb.x];
     const int row = jb.y + (threadIdx.x >> 5);
     if (row >= G.m) return;
-    split_row_warp(G.A + (long long)row * G.lda, G.k, G.kp, G.ea + row, G.A1 + (long long)row * G.kp,
-                   G.A2 + (long long)row * G.kp);
+    split_row_warp(G.A + (long long)row * G.lda, G.k, G.kp, G.ea + row, G.A1 + (long long)row * G.pitch,
+                   G.A2 + (long long)row * G.pitch);
 }
 
 // job (problem, first column): 32 x 8 threads, the whole k range of 32 columns
@@ -500,7 +530,7 @@ __global__ void colmax_b_group_kernel(const GroupSplit *gs, const int2 *jobs) {
 __global__ void split_b_group_kernel(const GroupSplit *gs, const int3 *jobs) {
     const int3 jb = jobs[blockIdx.x];
     const GroupSplit &G = gs[jb.x];
-    split_b_tile(G.B, G.ldb, G.k, G.n, G.kp, G.eb, G.B1, G.B2, jb.z, jb.y);
+    split_b_tile(G.B, G.ldb, G.k, G.n, G.kp, G.pitch, G.eb, G.B1, G.B2, jb.z, jb.y);
 }
 
 size_t smem_gemm() { return 1024 + (size_t)kStages * kStageBytes + 256; }
@@ -590,6 +620,7 @@ void launch_gemm_split3(int m, int n, int k, const double *A, long long lda, con
 // ------------------------------------------------------------ group plans
 struct GemmGroup {
     void *arena = nullptr;
+    GemmMaps maps;
     GroupProblem *d_probs = nullptr;
     GroupSplit *d_split = nullptr;
     int4 *d_tiles = nullptr;
@@ -603,28 +634,36 @@ struct GemmGroup {
 GemmGroup *gemm_group_create(const std::vector<GemmDesc> &v, int num_sms) {
     OO_REQUIRE(!v.empty(), OO_EINVAL, "empty GEMM group");
     auto up = [](size_t x, size_t a) { return (x + a - 1) / a * a; };
-    // arena layout: split operands | scale exponents | descriptors | job lists | error word
-    std::vector<size_t> off_a1(v.size()), off_a2(v.size()), off_b1(v.size()), off_b2(v.size()), off_ea(v.size()),
-        off_eb(v.size());
-    size_t at = 0;
-    std::vector<int> kp(v.size());
+    // arena layout: A1 | A2 | B1 | B2 (every problem's rows stacked, row pitch
+    // KP = the largest padded K) | scale exponents | descriptors | job lists | error word
+    std::vector<int> kp(v.size()), ra(v.size()), rb(v.size());
+    long long rows_a = 0, rows_b = 0;
+    int KP = kBK;
     for (size_t i = 0; i < v.size(); ++i) {
         const GemmDesc &d = v[i];
         OO_REQUIRE(d.m >= 1 && d.n >= 1 && d.k >= 1 && d.lda >= d.k && d.ldb >= d.n && d.ldc >= d.n, OO_EINVAL,
                    "bad GEMM in group");
         kp[i] = (d.k + kBK - 1) / kBK * kBK;
-        const size_t ab = up((size_t)d.m * kp[i] * 2, 256), bb = up((size_t)d.n * kp[i] * 2, 256);
-        off_a1[i] = at; at += ab;
-        off_a2[i] = at; at += ab;
-        off_b1[i] = at; at += bb;
-        off_b2[i] = at; at += bb;
+        KP = std::max(KP, kp[i]);
+        ra[i] = (int)rows_a;
+        rb[i] = (int)rows_b;
+        rows_a += d.m;
+        rows_b += d.n;
+        OO_REQUIRE(rows_a < (1ll << 30) && rows_b < (1ll << 30), OO_EINVAL, "GEMM group too large");
     }
+    const size_t a_bytes = up((size_t)rows_a * KP * 2, 256), b_bytes = up((size_t)rows_b * KP * 2, 256);
+    size_t at = 0;
+    const size_t off_a1 = at; at += a_bytes;
+    const size_t off_a2 = at; at += a_bytes;
+    const size_t off_b1 = at; at += b_bytes;
+    const size_t off_b2 = at; at += b_bytes;
+    std::vector<size_t> off_ea(v.size()), off_eb(v.size());
     for (size_t i = 0; i < v.size(); ++i) {
         off_ea[i] = at; at += up((size_t)v[i].m * 4, 16);
         off_eb[i] = at; at += up((size_t)v[i].n * 4, 16);
     }
     at = up(at, 128);
-    const size_t off_probs = at; at += v.size() * sizeof(GroupProblem);
+    const size_t off_probs = at; at += up(v.size() * sizeof(GroupProblem), 16);
     const size_t off_split = at; at += up(v.size() * sizeof(GroupSplit), 16);
     std::vector<int4> tiles;
     std::vector<int2> ajobs, cjobs;
@@ -653,31 +692,24 @@ GemmGroup *gemm_group_create(const std::vector<GemmDesc> &v, int num_sms) {
             throw Error{OO_ENOMEM, "GEMM group arena of " + std::to_string(at) + " bytes"};
         }
         char *base = static_cast<char *>(g->arena);
+        auto *A1 = reinterpret_cast<__nv_bfloat16 *>(base + off_a1);
+        auto *A2 = reinterpret_cast<__nv_bfloat16 *>(base + off_a2);
+        auto *B1 = reinterpret_cast<__nv_bfloat16 *>(base + off_b1);
+        auto *B2 = reinterpret_cast<__nv_bfloat16 *>(base + off_b2);
+        map_bf16(&g->maps.a1, A1, rows_a, KP, kBM);
+        map_bf16(&g->maps.a2, A2, rows_a, KP, kBM);
+        map_bf16(&g->maps.b1, B1, rows_b, KP, kBN);
+        map_bf16(&g->maps.b2, B2, rows_b, KP, kBN);
         std::vector<GroupProblem> probs(v.size());
         std::vector<GroupSplit> splits(v.size());
         for (size_t i = 0; i < v.size(); ++i) {
             const GemmDesc &d = v[i];
-            auto *A1 = reinterpret_cast<__nv_bfloat16 *>(base + off_a1[i]);
-            auto *A2 = reinterpret_cast<__nv_bfloat16 *>(base + off_a2[i]);
-            auto *B1 = reinterpret_cast<__nv_bfloat16 *>(base + off_b1[i]);
-            auto *B2 = reinterpret_cast<__nv_bfloat16 *>(base + off_b2[i]);
             int *ea = reinterpret_cast<int *>(base + off_ea[i]);
             int *eb = reinterpret_cast<int *>(base + off_eb[i]);
-            GroupProblem &P = probs[i];
-            std::memset(&P, 0, sizeof(P));
-            map_bf16(&P.a1, A1, d.m, kp[i], kBM);
-            map_bf16(&P.a2, A2, d.m, kp[i], kBM);
-            map_bf16(&P.b1, B1, d.n, kp[i], kBN);
-            map_bf16(&P.b2, B2, d.n, kp[i], kBN);
-            P.C = d.C;
-            P.ldc = d.ldc;
-            P.ea = ea;
-            P.eb = eb;
-            P.m = d.m;
-            P.n = d.n;
-            P.k = d.k;
-            P.kp = kp[i];
-            splits[i] = GroupSplit{d.A, d.B, d.lda, d.ldb, d.m, d.n, d.k, kp[i], A1, A2, B1, B2, ea, eb};
+            probs[i] = GroupProblem{d.C, d.ldc, ea, eb, d.m, d.n, d.k, kp[i], ra[i], rb[i]};
+            splits[i] = GroupSplit{d.A, d.B, d.lda, d.ldb, d.m, d.n, d.k, kp[i], (long long)KP,
+                                   A1 + (size_t)ra[i] * KP, A2 + (size_t)ra[i] * KP,
+                                   B1 + (size_t)rb[i] * KP, B2 + (size_t)rb[i] * KP, ea, eb};
         }
         OO_CUDA_TRY(cudaMemcpy(base + off_probs, probs.data(), probs.size() * sizeof(GroupProblem),
                                cudaMemcpyHostToDevice));
@@ -722,7 +754,8 @@ void gemm_group_launch(GemmGroup *g, cudaStream_t s) {
                                          (int)smem_gemm()));
         attr = true;
     }
-    gemm_group_kernel<<<g->grid, kGemmThreads, smem_gemm(), s>>>(g->d_probs, g->d_tiles, g->ntiles, g->d_err);
+    gemm_group_kernel<<<g->grid, kGemmThreads, smem_gemm(), s>>>(g->maps, g->d_probs, g->d_tiles, g->ntiles,
+                                                                  g->d_err);
     OO_CUDA_TRY(cudaGetLastError());
 }
 

@@ -291,15 +291,20 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_fp64eq_kernel(const __grid_c
                 __syncwarp();
                 if (lane == 0) bar_arrive(su32(&tempty[b]));
                 if (u == units - 1) {
+                    // column scales: lane l holds columns l and l + 32 of this
+                    // half (coalesced) and hands them out by shuffle
                     const int row = m0 + q * 32 + lane;
-                    if (row < a.m) {
-                        const int sa = a.ea[row];
-                        double *crow = a.C + (long long)row * a.ldc + n0 + h * 64;
-                        const int ncol = a.n - (n0 + h * 64);
+                    const int c0 = n0 + h * 64;
+                    const int e0 = c0 + lane < a.n ? a.eb[c0 + lane] : 0;
+                    const int e1 = c0 + 32 + lane < a.n ? a.eb[c0 + 32 + lane] : 0;
+                    const bool row_ok = row < a.m;
+                    const int sa = row_ok ? a.ea[row] : 0;
+                    double *crow = a.C + (long long)row * a.ldc + c0;
 #pragma unroll
-                        for (int j = 0; j < 64; ++j)
-                            if (j < ncol)
-                                crow[j] = ff::scale_pow2(ff::to_double(Sh[j], Sl[j]), sa + a.eb[n0 + h * 64 + j]);
+                    for (int j = 0; j < 64; ++j) {
+                        const int sb = __shfl_sync(0xffffffffu, j < 32 ? e0 : e1, j & 31);
+                        if (row_ok && c0 + j < a.n)
+                            crow[j] = ff::scale_pow2(ff::to_double(Sh[j], Sl[j]), sa + sb);
                     }
                 }
             }
