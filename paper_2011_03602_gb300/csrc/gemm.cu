@@ -38,7 +38,9 @@ namespace oo {
 namespace {
 
 constexpr int kBM = 128, kBN = 128, kBK = 64, kStages = 3;
-constexpr int kGemmThreads = 256;
+constexpr int kGemmThreads = 384;  // producer, MMA issuer, 2 idle, 8 epilogue warps
+constexpr int kEpiWarps = 8;
+constexpr uint32_t kStageOut = kEpiWarps * 32 * 16 * 8;  // per epilogue warp: 32 rows x 16 FP64 staging
 constexpr uint32_t kTileA = kBM * kBK * 2;   // 16 KB
 constexpr uint32_t kTileB = kBN * kBK * 2;   // 16 KB
 constexpr uint32_t kStageBytes = 2 * kTileA + 2 * kTileB;  // 64 KB
@@ -129,7 +131,8 @@ __device__ __forceinline__ void gemm_body(const Src &src, unsigned *err) {
     extern __shared__ __align__(1024) unsigned char gsm_raw[];
     unsigned char *gsm = reinterpret_cast<unsigned char *>(
         (reinterpret_cast<uintptr_t>(gsm_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-    uint64_t *bars = reinterpret_cast<uint64_t *>(gsm + kStages * kStageBytes);
+    double *stg_all = reinterpret_cast<double *>(gsm + kStages * kStageBytes);  // epilogue store staging
+    uint64_t *bars = reinterpret_cast<uint64_t *>(gsm + kStages * kStageBytes + kStageOut);
     uint64_t *full = bars, *empty = bars + kStages;
     uint64_t *tfull = bars + 2 * kStages, *tempty = bars + 2 * kStages + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * kStages + 4);
@@ -145,7 +148,7 @@ __device__ __forceinline__ void gemm_body(const Src &src, unsigned *err) {
         }
         for (int b = 0; b < 2; ++b) {
             bar_init(su32(&tfull[b]), 1);
-            bar_init(su32(&tempty[b]), 4);  // one arrival per epilogue warp
+            bar_init(su32(&tempty[b]), kEpiWarps);  // one arrival per epilogue warp
         }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -224,56 +227,61 @@ __device__ __forceinline__ void gemm_body(const Src &src, unsigned *err) {
         }
     } else if (warp >= 4) {
         // ---------------------------------------------------- epilogue
-        const int q = warp - 4;  // TMEM lane quarter
+        // Eight warps: warp w reads TMEM lane quarter (w & 3), i.e. rows
+        // 32 (w & 3) .. +31 of the tile, and column half (w - 4) >> 2.  Each
+        // thread widens its row's values; 16-column blocks go through a
+        // per-warp shared-memory transpose (XOR-swizzled: no bank conflicts)
+        // so every global store writes two whole 128-byte row segments.
+        // Chunks with no valid row or column are skipped.
+        const int q = warp & 3, hcol = ((warp - 4) >> 2) * 64;
+        double *stg = stg_all + (size_t)(warp - 4) * 32 * 16;
         int lt = 0;
         for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++lt) {
             const int b = lt & 1;
-            // the tile's descriptor and scales are fetched before waiting for
-            // its accumulators, so their latency overlaps the MMAs: lane l
-            // holds the column scales of columns l, l + 32, l + 64, l + 96
-            // (coalesced) and hands them out by shuffle
+            // descriptor and scales before the accumulator wait (overlaps the
+            // MMAs); lane l holds the scales of columns hcol + l and hcol + 32 + l
             const TileJob jb = src.job(t);
-            const int n0 = jb.n0;
-            const int row = jb.m0 + q * 32 + lane;
-            const bool row_ok = row < jb.m;
-            const int sa = row_ok ? jb.ea[row] : 0;
-            static_assert(kBN == 128, "four 32-column chunks");
-            int e_cur, e_n1, e_n2, e_n3;  // column scales of chunks 0..3 (rotated per chunk)
-            {
-                auto ld = [&](int c4) {
-                    const int col = n0 + c4 * 32 + lane;
-                    return col < jb.n ? jb.eb[col] : 0;
-                };
-                e_cur = ld(0);
-                e_n1 = ld(1);
-                e_n2 = ld(2);
-                e_n3 = ld(3);
-            }
+            const int n0 = jb.n0, row0 = jb.m0 + q * 32;
+            const int ncols = jb.n - n0;  // valid columns of the tile (may exceed 128)
+            const int sa = row0 + lane < jb.m ? jb.ea[row0 + lane] : 0;
+            const int e0 = hcol + lane < ncols ? jb.eb[n0 + hcol + lane] : 0;
+            const int e1 = hcol + 32 + lane < ncols ? jb.eb[n0 + hcol + 32 + lane] : 0;
             if (!bar_wait(su32(&tfull[b]), (lt >> 1) & 1, abort_flag, err, 4u)) break;
             fence_after();
-            double *crow = jb.C + (long long)row * jb.ldc;
-            const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-            const uint32_t d_hh = tmem + (uint32_t)(b * 256), d_x = d_hh + 128;
+            if (row0 < jb.m) {
+                const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+                const uint32_t d_hh = tmem + (uint32_t)(b * 256), d_x = d_hh + 128;
 #pragma unroll 1
-            for (int c = 0; c < kBN; c += 32) {
-                uint32_t h[32], x[32];
-                OO_TMEM_LD32(d_hh + lane_off + c, h);
-                OO_TMEM_LD32(d_x + lane_off + c, x);
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                for (int cc = 0; cc < 2; ++cc) {
+                    const int c = hcol + cc * 32;
+                    if (c >= ncols) break;
+                    uint32_t h[32], x[32];
+                    OO_TMEM_LD32(d_hh + lane_off + c, h);
+                    OO_TMEM_LD32(d_x + lane_off + c, x);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                    const int ecur = cc ? e1 : e0;
 #pragma unroll
-                for (int t2 = 0; t2 < 32; ++t2) {
-                    const int sb = __shfl_sync(0xffffffffu, e_cur, t2);
-                    const int col = n0 + c + t2;
-                    if (row_ok && col < jb.n) {
-                        // exact two-sum of the partial products, widened and scaled
-                        // without the (slow) FP64 pipe
-                        const double v = ff::to_double(__uint_as_float(h[t2]), __uint_as_float(x[t2]));
-                        crow[col] = ff::scale_pow2(v, sa + sb);
+                    for (int sub = 0; sub < 2; ++sub) {
+                        if (c + sub * 16 >= ncols) break;
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            // exact two-sum of the partial products, widened and
+                            // scaled without the (slow) FP64 pipe
+                            const int t2 = sub * 16 + j;
+                            const int sb = __shfl_sync(0xffffffffu, ecur, t2);
+                            const double v = ff::to_double(__uint_as_float(h[t2]), __uint_as_float(x[t2]));
+                            stg[lane * 16 + (j ^ (lane & 15))] = ff::scale_pow2(v, sa + sb);
+                        }
+                        __syncwarp();
+                        const int cl = lane & 15, col = c + sub * 16 + cl;
+#pragma unroll 4
+                        for (int r = lane >> 4; r < 32; r += 2) {
+                            const double v = stg[r * 16 + (cl ^ (r & 15))];
+                            if (row0 + r < jb.m && col < ncols) jb.C[(long long)(row0 + r) * jb.ldc + n0 + col] = v;
+                        }
+                        __syncwarp();
                     }
                 }
-                e_cur = e_n1;
-                e_n1 = e_n2;
-                e_n2 = e_n3;
             }
             fence_before();
             __syncwarp();
@@ -533,7 +541,7 @@ __global__ void split_b_group_kernel(const GroupSplit *gs, const int3 *jobs) {
     split_b_tile(G.B, G.ldb, G.k, G.n, G.kp, G.pitch, G.eb, G.B1, G.B2, jb.z, jb.y);
 }
 
-size_t smem_gemm() { return 1024 + (size_t)kStages * kStageBytes + 256; }
+size_t smem_gemm() { return 1024 + (size_t)kStages * kStageBytes + kStageOut + 256; }
 
 }  // namespace
 
