@@ -90,6 +90,7 @@ struct SingleSrc {
     const GemmMaps *maps;
     const GemmArgs *a;
     __device__ __forceinline__ int count() const { return a->m_tiles * a->n_tiles; }
+    __device__ __forceinline__ int ksteps(int) const { return a->kp / kBK; }
     __device__ __forceinline__ TileJob job(int t) const {
         int m0, n0;
         tile_coords(*a, t, m0, n0);
@@ -118,6 +119,7 @@ struct GroupSrc {
     const int4 *tiles;
     int ntiles;
     __device__ __forceinline__ int count() const { return ntiles; }
+    __device__ __forceinline__ int ksteps(int t) const { return tiles[t].w; }
     __device__ __forceinline__ TileJob job(int t) const {
         const int4 td = tiles[t];
         const GroupProblem &P = probs[td.x];
@@ -171,8 +173,12 @@ __device__ __forceinline__ void gemm_body(const Src &src, unsigned *err) {
         // ---------------------------------------------------- TMA producer
         int it = 0;
         bool ok = true;
+        // the next tile's descriptor is fetched one tile ahead so that its
+        // (dependent) global loads stay off the critical path
+        TileJob nx = blockIdx.x < (unsigned)tiles ? src.job(blockIdx.x) : TileJob{};
         for (int t = blockIdx.x; ok && t < tiles; t += gridDim.x) {
-            const TileJob jb = src.job(t);
+            const TileJob jb = nx;
+            if (t + (int)gridDim.x < tiles) nx = src.job(t + gridDim.x);
             for (int ks = 0; ks < jb.ksteps; ++ks, ++it) {
                 const int s = it % kStages;
                 const uint32_t use = it / kStages;
@@ -195,13 +201,15 @@ __device__ __forceinline__ void gemm_body(const Src &src, unsigned *err) {
         // ---------------------------------------------------- MMA issuer
         int it = 0, lt = 0;
         bool ok = true;
+        int ks_next = blockIdx.x < (unsigned)tiles ? src.ksteps(blockIdx.x) : 0;
         for (int t = blockIdx.x; ok && t < tiles; t += gridDim.x, ++lt) {
+            const int ksteps = ks_next;
+            if (t + (int)gridDim.x < tiles) ks_next = src.ksteps(t + gridDim.x);
             const int b = lt & 1;
             const uint32_t buse = lt >> 1;
             if (buse > 0 && !bar_wait(su32(&tempty[b]), (buse - 1) & 1, abort_flag, err, 2u)) break;
             fence_after();
             const uint32_t d_hh = tmem + (uint32_t)(b * 256), d_x = d_hh + 128;
-            const int ksteps = src.job(t).ksteps;
             for (int ks = 0; ks < ksteps; ++ks, ++it) {
                 const int s = it % kStages;
                 const uint32_t use = it / kStages;
