@@ -511,52 +511,42 @@ struct GroupSplit {
 };
 
 // job (problem, first row): 8 warps, one row each
-// Persistent: block b takes jobs b, b + grid, ... (many small problems make
-// many tiny jobs; one block per job paid its launch and drain every time).
-__global__ void split_a_group_kernel(const GroupSplit *gs, const int2 *jobs, int njobs) {
-    for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
-        const int2 jb = jobs[j];
-        const GroupSplit &G = gs[jb.x];
-        const int row = jb.y + (threadIdx.x >> 5);
-        if (row < G.m)
-            split_row_warp(G.A + (long long)row * G.lda, G.k, G.kp, G.ea + row, G.A1 + (long long)row * G.pitch,
-                           G.A2 + (long long)row * G.pitch);
-    }
+__global__ void split_a_group_kernel(const GroupSplit *gs, const int2 *jobs) {
+    const int2 jb = jobs[blockIdx.x];
+    const GroupSplit &G = gs[jb.x];
+    const int row = jb.y + (threadIdx.x >> 5);
+    if (row >= G.m) return;
+    split_row_warp(G.A + (long long)row * G.lda, G.k, G.kp, G.ea + row, G.A1 + (long long)row * G.pitch,
+                   G.A2 + (long long)row * G.pitch);
 }
 
 // job (problem, first column): 32 x 8 threads, the whole k range of 32 columns
-__global__ void colmax_b_group_kernel(const GroupSplit *gs, const int2 *jobs, int njobs) {
-    __shared__ int red[8][33];
-    for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
-        const int2 jb = jobs[j];
-        const GroupSplit &G = gs[jb.x];
-        const int col = jb.y + threadIdx.x;
-        int mx = 0;
-        if (col < G.n) {
+__global__ void colmax_b_group_kernel(const GroupSplit *gs, const int2 *jobs) {
+    const int2 jb = jobs[blockIdx.x];
+    const GroupSplit &G = gs[jb.x];
+    const int col = jb.y + threadIdx.x;
+    int mx = 0;
+    if (col < G.n) {
 #pragma unroll 8
-            for (int l = threadIdx.y; l < G.k; l += blockDim.y) {
-                const int ex = (int)((__double_as_longlong(G.B[(long long)l * G.ldb + col]) >> 52) & 0x7ff);
-                mx = max(mx, ex == 0x7ff ? 0x7fe : ex);
-            }
+        for (int l = threadIdx.y; l < G.k; l += blockDim.y) {
+            const int ex = (int)((__double_as_longlong(G.B[(long long)l * G.ldb + col]) >> 52) & 0x7ff);
+            mx = max(mx, ex == 0x7ff ? 0x7fe : ex);
         }
-        red[threadIdx.y][threadIdx.x] = mx;
-        __syncthreads();
-        if (threadIdx.y == 0 && col < G.n) {
-            for (int y = 1; y < (int)blockDim.y; ++y) mx = max(mx, red[y][threadIdx.x]);
-            G.eb[col] = mx == 0 ? 0 : mx - 1023 + 1;
-        }
-        __syncthreads();
+    }
+    __shared__ int red[8][33];
+    red[threadIdx.y][threadIdx.x] = mx;
+    __syncthreads();
+    if (threadIdx.y == 0 && col < G.n) {
+        for (int y = 1; y < (int)blockDim.y; ++y) mx = max(mx, red[y][threadIdx.x]);
+        G.eb[col] = mx == 0 ? 0 : mx - 1023 + 1;
     }
 }
 
 // job (problem, first column, first k): one 64 x 64 tile
-__global__ void split_b_group_kernel(const GroupSplit *gs, const int3 *jobs, int njobs) {
-    for (int j = blockIdx.x; j < njobs; j += gridDim.x) {
-        const int3 jb = jobs[j];
-        const GroupSplit &G = gs[jb.x];
-        split_b_tile(G.B, G.ldb, G.k, G.n, G.kp, G.pitch, G.eb, G.B1, G.B2, jb.z, jb.y);
-        __syncthreads();  // the tile's shared staging is reused by the next job
-    }
+__global__ void split_b_group_kernel(const GroupSplit *gs, const int3 *jobs) {
+    const int3 jb = jobs[blockIdx.x];
+    const GroupSplit &G = gs[jb.x];
+    split_b_tile(G.B, G.ldb, G.k, G.n, G.kp, G.pitch, G.eb, G.B1, G.B2, jb.z, jb.y);
 }
 
 size_t smem_gemm() { return 1024 + (size_t)kStages * kStageBytes + kStageOut + 256; }
@@ -653,7 +643,7 @@ struct GemmGroup {
     int2 *d_ajobs = nullptr, *d_cjobs = nullptr;
     int3 *d_bjobs = nullptr;
     unsigned *d_err = nullptr;
-    int ntiles = 0, na = 0, nc = 0, nb = 0, grid = 1, num_sms = 1;
+    int ntiles = 0, na = 0, nc = 0, nb = 0, grid = 1;
     double flops = 0;
 };
 
@@ -758,7 +748,6 @@ GemmGroup *gemm_group_create(const std::vector<GemmDesc> &v, int num_sms) {
         g->nc = (int)cjobs.size();
         g->nb = (int)bjobs.size();
         g->grid = std::max(1, std::min(g->ntiles, num_sms));
-        g->num_sms = std::max(1, num_sms);
         g->flops = flops;
     } catch (...) {
         if (g->arena) cudaFree(g->arena);
@@ -769,12 +758,11 @@ GemmGroup *gemm_group_create(const std::vector<GemmDesc> &v, int num_sms) {
 }
 
 void gemm_group_launch(GemmGroup *g, cudaStream_t s) {
-    const int pgrid = std::max(1, g->num_sms * 8);
-    split_a_group_kernel<<<std::min(g->na, pgrid), 256, 0, s>>>(g->d_split, g->d_ajobs, g->na);
+    split_a_group_kernel<<<g->na, 256, 0, s>>>(g->d_split, g->d_ajobs);
     OO_CUDA_TRY(cudaGetLastError());
-    colmax_b_group_kernel<<<std::min(g->nc, pgrid), dim3(32, 8), 0, s>>>(g->d_split, g->d_cjobs, g->nc);
+    colmax_b_group_kernel<<<g->nc, dim3(32, 8), 0, s>>>(g->d_split, g->d_cjobs);
     OO_CUDA_TRY(cudaGetLastError());
-    split_b_group_kernel<<<std::min(g->nb, pgrid), 256, 0, s>>>(g->d_split, g->d_bjobs, g->nb);
+    split_b_group_kernel<<<g->nb, 256, 0, s>>>(g->d_split, g->d_bjobs);
     OO_CUDA_TRY(cudaGetLastError());
     static bool attr = false;
     if (!attr) {
