@@ -107,3 +107,53 @@ def test_bad_requests(oo_mod):
             oo_mod.oo_batch_create(ctx, [dict(kind="gemm", m=0, n=2, k=2, A=x, B=x, C=x)])
     finally:
         oo_mod.oo_destroy(ctx)
+
+
+def test_full_size_batch_sampled(oo_mod):
+    """The benchmark's batch (4096 GEMMs, m, n, k log-uniform in [16, 512];
+    2048 FFTs, 2^8..2^16, alternating directions; same seeds): the CUDA-graph
+    replay equals one call per request for every request, and sampled
+    requests match the oracle."""
+    n_gemm, n_fft = 4096, 2048
+    dims = synth.log_uniform_int(4, 3 * n_gemm, 16, 512).reshape(n_gemm, 3)
+    expo = 8 + np.floor(synth.uniform(5, n_fft) * 9).astype(int)
+    ctx = oo_mod.oo_create(0)
+    try:
+        reqs = []
+        for i, (m, n, k) in enumerate(dims.tolist()):
+            reqs.append(dict(kind="gemm", m=m, n=n, k=k,
+                             A=torch.from_numpy(synth.gemm_matrix(100 + i, m, k)).cuda(),
+                             B=torch.from_numpy(synth.gemm_matrix(200000 + i, k, n)).cuda(),
+                             C=torch.full((m, n), np.nan, dtype=torch.float64, device="cuda")))
+        for i, e in enumerate(expo.tolist()):
+            x = synth.complex_normal(400000 + i, 1 << e)
+            reqs.append(dict(kind="fft", n=1 << e, dir=-1 if i % 2 == 0 else 1,
+                             x=torch.from_numpy(x.view(np.float64).copy()).cuda(),
+                             X=torch.full((2 << e,), np.nan, dtype=torch.float64, device="cuda")))
+        b = oo_mod.oo_batch_create(ctx, reqs)
+        try:
+            oo_mod.oo_batch_run(ctx, b, 2)
+            oo_mod.oo_batch_check(ctx, b)
+            per_call = outputs(reqs)
+            for r in reqs:
+                (r["C"] if r["kind"] == "gemm" else r["X"]).fill_(np.nan)
+            oo_mod.oo_batch_run(ctx, b, 1)
+            oo_mod.oo_batch_check(ctx, b)
+            graph = outputs(reqs)
+        finally:
+            oo_mod.oo_batch_destroy(b)
+        for i in range(len(reqs)):
+            assert np.array_equal(graph[i], per_call[i]), i
+        rng = np.random.default_rng(7)
+        for i in rng.choice(n_gemm, 48, replace=False):
+            m, n, k = (int(v) for v in dims[i])
+            A, B = synth.gemm_matrix(100 + int(i), m, k), synth.gemm_matrix(200000 + int(i), k, n)
+            e = np.max(np.abs(graph[i] - oracle.gemm(A, B)) / (np.abs(A) @ np.abs(B)))
+            assert e <= 1e-4, (i, e)
+        for j in rng.choice(n_fft, 48, replace=False):
+            x = synth.complex_normal(400000 + int(j), 1 << int(expo[j]))
+            ref = oracle.fft(x, -1 if j % 2 == 0 else 1)
+            X = graph[n_gemm + int(j)].view(np.complex128)
+            assert np.linalg.norm(X - ref) <= 1e-12 * np.linalg.norm(ref), j
+    finally:
+        oo_mod.oo_destroy(ctx)
