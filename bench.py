@@ -152,7 +152,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     iters = 2
-    for _ in range(args.warmup if args.warmup < 1 else 1):
+    for _ in range(args.warmup):
         oracle_sample(iters)
     vals, times = [], []
     for _ in range(args.steps):

@@ -570,14 +570,10 @@ void launch_fft(const FftPlan *p, int batch, int dir, const double *in, double *
     a.batch = batch;
     a.inverse = dir > 0 ? 1 : 0;
     a.expo = expo;
-    static bool attr_done[3] = {false, false, false};
+    static std::atomic<uint64_t> attr_done[3];
     auto smem_for = [&](int log2L) { return (size_t)(kFftElems + (1 << log2L)) * sizeof(float4); };
     auto prep = [&](int mode, const void *fn, size_t smem) {
-        if (!attr_done[mode]) {
-            OO_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem_for(12)));
-            attr_done[mode] = true;
-        }
+        set_smem_limit_once(fn, smem_for(12), attr_done[mode]);
         (void)smem;
     };
     if (!four_step) {
@@ -727,11 +723,8 @@ void fft_group_launch(FftGroup *g, cudaStream_t s) {
     fft_maxexp_group_kernel<<<dim3(g->maxexp_x, g->nreq), 256, 0, s>>>(g->d_reqs, g->d_expo);
     OO_CUDA_TRY(cudaGetLastError());
     const size_t smem = (size_t)(kFftElems + 4096) * sizeof(float4);
-    static bool attr = false;
-    if (!attr) {
-        OO_CUDA_TRY(cudaFuncSetAttribute(fft_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    set_smem_limit_once((const void *)fft_group_kernel, smem, attr);
     if (g->n_items_a > 0) {
         fft_group_kernel<<<g->grid_a, kFftThreads, smem, s>>>(g->d_items, g->n_items_a, g->d_reqs, g->d_tlist,
                                                                g->d_expo);

@@ -617,12 +617,8 @@ void launch_gemm_split3(int m, int n, int k, const double *A, long long lda, con
     ga.ea = ea;
     ga.eb = eb;
     ga.err = err;
-    static bool attr = false;
-    if (!attr) {
-        OO_CUDA_TRY(cudaFuncSetAttribute(gemm_split3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem_gemm()));
-        attr = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    set_smem_limit_once((const void *)gemm_split3_kernel, smem_gemm(), attr);
     const long long tiles = (long long)ga.m_tiles * ga.n_tiles;
     OO_REQUIRE(tiles < (1ll << 31), OO_EINVAL, "too many tiles");
     int dev2 = 0, sms2 = 148;
@@ -764,12 +760,8 @@ void gemm_group_launch(GemmGroup *g, cudaStream_t s) {
     OO_CUDA_TRY(cudaGetLastError());
     split_b_group_kernel<<<g->nb, 256, 0, s>>>(g->d_split, g->d_bjobs);
     OO_CUDA_TRY(cudaGetLastError());
-    static bool attr = false;
-    if (!attr) {
-        OO_CUDA_TRY(cudaFuncSetAttribute(gemm_group_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem_gemm()));
-        attr = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    set_smem_limit_once((const void *)gemm_group_kernel, smem_gemm(), attr);
     gemm_group_kernel<<<g->grid, kGemmThreads, smem_gemm(), s>>>(g->maps, g->d_probs, g->d_tiles, g->ntiles,
                                                                   g->d_err);
     OO_CUDA_TRY(cudaGetLastError());

@@ -573,12 +573,8 @@ void launch_gemm_fp64eq(int m, int n, int k, const double *A, long long lda, con
         ga.us1[i] = std::ldexp(1.0f, -e.beta * (U[i].p + U[i].q1 + 2));
         ga.us2[i] = U[i].q2 == kNone ? 0.0f : std::ldexp(1.0f, -e.beta * (U[i].p + U[i].q2 + 2));
     }
-    static bool attr = false;
-    if (!attr) {
-        OO_CUDA_TRY(cudaFuncSetAttribute(gemm_fp64eq_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem_eq()));
-        attr = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    set_smem_limit_once((const void *)gemm_fp64eq_kernel, smem_eq(), attr);
     const long long tiles = (long long)ga.m_tiles * ga.n_tiles;
     OO_REQUIRE(tiles < (1ll << 31), OO_EINVAL, "too many tiles");
     int dev = 0, sms = 148;

@@ -664,13 +664,8 @@ struct Variant {
                2 * (DC + DP) * 8 + 32 * 8 + 16;
     }
     static void launch(int grid, const StencilMaps &m, const StencilArgs &a, cudaStream_t s) {
-        static bool done = false;
-        if (!done) {
-            OO_CUDA_TRY(cudaFuncSetAttribute(stencil_kernel<TK, TJ, NCW, DC, DP, PPT, MINB>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem_bytes()));
-            done = true;
-        }
+        static std::atomic<uint64_t> done{0};
+        set_smem_limit_once((const void *)stencil_kernel<TK, TJ, NCW, DC, DP, PPT, MINB>, smem_bytes(), done);
         stencil_kernel<TK, TJ, NCW, DC, DP, PPT, MINB><<<grid, kThreads, smem_bytes(), s>>>(m, a);
         OO_CUDA_TRY(cudaGetLastError());
     }

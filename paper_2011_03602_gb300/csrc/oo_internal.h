@@ -2,6 +2,8 @@
 #pragma once
 
 #include <cuda_runtime.h>
+
+#include <atomic>
 #include <cstdint>
 #include <functional>
 #include <string>
@@ -145,6 +147,18 @@ void gemm_group_launch(GemmGroup *g, cudaStream_t s);
 unsigned gemm_group_check(GemmGroup *g, cudaStream_t s);
 double gemm_group_flops(const GemmGroup *g);
 void gemm_group_destroy(GemmGroup *g);
+
+// Raise a kernel's dynamic shared-memory limit on the current device once
+// (the attribute is per device and a process may drive several; `done`
+// holds one bit per device and is safe to share between threads).
+inline void set_smem_limit_once(const void *fn, size_t bytes, std::atomic<uint64_t> &done) {
+    int dev = 0;
+    OO_CUDA_TRY(cudaGetDevice(&dev));
+    const uint64_t bit = 1ull << (dev & 63);
+    if (done.load(std::memory_order_acquire) & bit) return;
+    OO_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    done.fetch_or(bit, std::memory_order_acq_rel);
+}
 
 // Grow-only device buffer owned by a context.
 struct DevBuf {
