@@ -177,6 +177,14 @@ __device__ void fft_in_smem(float4 *sd, const float4 *stw, int log2L, bool inv) 
     }
 }
 
+// the same, for odd log2 L, when the radix-2 stage has already been done
+__device__ void fft_in_smem_after_r2(float4 *sd, const float4 *stw, int log2L, bool inv) {
+    for (int Ls = 2; Ls < (1 << log2L); Ls *= 4) {
+        stage_r4(sd, stw, log2L, Ls, inv);
+        stw += 3 * Ls;
+    }
+}
+
 // entries of the per-stage twiddle table of a length-2^log2L transform
 __host__ __device__ __forceinline__ int stage_table_count(int log2L) {
     return log2L < 3 ? 0 : (1 << log2L) - ((log2L & 1) ? 2 : 4);
@@ -236,24 +244,46 @@ __global__ void __launch_bounds__(kFftThreads, 1) fft_pass_kernel(FftArgs a) {
                                       __hiloint2double(__float_as_int(f.w), __float_as_int(f.z)));
             }
         }
+        float4 v[kPer];
 #pragma unroll
         for (int r = 0; r < kPer; ++r) {
-            float4 v;
             if (MODE == 2) {  // float-float intermediates: the 16 bytes as they were
-                v = make_float4(__int_as_float(__double2loint(raw[r].x)), __int_as_float(__double2hiint(raw[r].x)),
-                                __int_as_float(__double2loint(raw[r].y)), __int_as_float(__double2hiint(raw[r].y)));
+                v[r] = make_float4(__int_as_float(__double2loint(raw[r].x)), __int_as_float(__double2hiint(raw[r].x)),
+                                   __int_as_float(__double2loint(raw[r].y)), __int_as_float(__double2hiint(raw[r].y)));
             } else {
                 const int tb = MODE == 0 ? c0 + (dst[r] >> log2L) : b;
                 const int S = (MODE == 0 && tb >= a.batch) ? 0 : scale_of(a, tb);
-                split_scaled(raw[r].x, S, v.x, v.y);
-                split_scaled(raw[r].y, S, v.z, v.w);
+                split_scaled(raw[r].x, S, v[r].x, v[r].y);
+                split_scaled(raw[r].y, S, v[r].z, v[r].w);
             }
-            sd[dst[r]] = v;
+        }
+        if (log2L == 11) {
+            // L = 2048: the first (radix-2, twiddle-free) stage pairs t with
+            // t + 1024 of the same column, and both are in this thread's
+            // registers (loads r and r + 4 column-fastest, r and r + 2
+            // row-fastest); do it here and store in Stockham order (y0 at
+            // 2t, y1 at 2t + 1 of the column).
+            static_assert(kPer == 8 && kFftThreads == 512, "pairing below assumes 8 loads of 512 threads");
+#pragma unroll
+            for (int pr = 0; pr < 4; ++pr) {
+                const int r0 = MODE == 1 ? pr : (pr & 1) + 4 * (pr >> 1), r1 = r0 + (MODE == 1 ? 4 : 2);
+                const cplx x0 = ld_cplx(&v[r0]), x1 = ld_cplx(&v[r1]);
+                const int col = dst[r0] >> 11, t = dst[r0] & 2047;  // t < 1024
+                float4 *o = sd + (col << 11) + 2 * t;
+                st_cplx(o, ff::cadd(x0, x1));
+                st_cplx(o + 1, ff::csub(x0, x1));
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < kPer; ++r) sd[dst[r]] = v[r];
         }
     }
     __syncthreads();
 
-    fft_in_smem(sd, stw, log2L, inv);
+    if (log2L == 11)
+        fft_in_smem_after_r2(sd, stw, log2L, inv);
+    else
+        fft_in_smem(sd, stw, log2L, inv);
 
     // ---- store
     for (int q = threadIdx.x; q < kFftElems; q += kFftThreads) {
