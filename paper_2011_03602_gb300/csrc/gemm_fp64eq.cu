@@ -31,7 +31,8 @@
 // products are grouped in units that share the A slice: (p, q1) and
 // (p, q2) become one M = 128, N = 256 MMA whose B operand is the two B
 // slices' tiles stacked (a product without a partner runs alone at
-// N = 128).  A unit of work is one such group over one K-block: warp 0
+// N = 128).  A unit of work is one such group over one K-block (K-blocks
+// outermost, so one K-block's slices serve all groups while in L2): warp 0
 // streams its A_p and B_q tiles (TMA, 128-byte swizzle) through a 4-stage
 // ring, warp 1 issues tcgen05.mma (K = 16) into one of two 256-column FP32
 // accumulators in tensor memory (double-buffered), and eight epilogue warps
@@ -181,7 +182,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_fp64eq_kernel(const __grid_c
             int m0, n0;
             eq_tile(a, t, m0, n0);
             for (int u = 0; ok && u < units; ++u) {
-                const int pr = u / a.nkb, kbi = u % a.nkb;
+                const int kbi = u / a.nunits, pr = u % a.nunits;  // K-block outer: its slices stay in L2
                 const bool pair = a.uq2[pr] != kNone;
                 const int rowA = a.up[pr] * a.m + m0, rowB1 = a.uq1[pr] * a.n + n0;
                 const int rowB2 = pair ? a.uq2[pr] * a.n + n0 : 0;
@@ -217,7 +218,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_fp64eq_kernel(const __grid_c
                 }
                 fence_after();
                 const uint32_t d = tmem + (uint32_t)(b * 2 * kBN);
-                const int pr = u / a.nkb, kbi = u % a.nkb;
+                const int kbi = u / a.nunits, pr = u % a.nunits;  // K-block outer: its slices stay in L2
                 const bool pair = a.uq2[pr] != kNone;
                 const int ks0 = kbi * a.kb_steps, ks1 = min(a.ksteps, (kbi + 1) * a.kb_steps);
                 for (int ks = ks0; ks < ks1; ++ks, ++it) {
@@ -262,7 +263,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_fp64eq_kernel(const __grid_c
                     break;
                 }
                 fence_after();
-                const int pr = u / a.nkb;
+                const int pr = u % a.nunits;
                 const bool pair = a.uq2[pr] != kNone, first = u == 0;
                 const float f1 = a.us1[pr], f2 = a.us2[pr];
                 const uint32_t acc = tmem + (uint32_t)(b * 2 * kBN) + lane_off + (uint32_t)(h * 64);
