@@ -270,6 +270,216 @@ void launch_bc_k(const JacobiDims &d, float *p, cudaStream_t s) {
     OO_CUDA_TRY(cudaGetLastError());
 }
 
+// ======================================================= fused iterations
+// All iterations of the all-GPU iteration nests (N2 stencil, N3 copy-back,
+// N4 / N5 boundary) in one cooperative launch, for grids small enough that
+// launch latency, not HBM, bounds the separate kernels.  Per iteration:
+// the stencil over the interior (each thread a strided set of points, the
+// same float-float arithmetic as the tiled kernel, term by term), a grid
+// barrier, block 0 sums the per-block FP64 residual partials in block
+// order, every point of p is rewritten (interior = wrk2, faces = g(k), i.e.
+// N3, N4 and N5), a second grid barrier.  Barrier waits are bounded: a wait
+// that runs out sets the error word and every block leaves at its next
+// barrier.
+namespace {
+
+struct FusedArgs {
+    const float *coef[NCOEF];
+    float *p, *wrk2;
+    double *res;
+    double *partials;       // gridDim.x
+    unsigned *ctl;          // [0] arrivals, [1] generation, [2] error
+    int I, J, K, pitch, iters;
+    float omega;
+};
+
+__device__ __forceinline__ bool fused_grid_barrier(unsigned *ctl) {
+    __syncthreads();
+    __shared__ int ok_s;
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = ctl + 1, *err = ctl + 2;
+        const unsigned g = *gen;
+        __threadfence();
+        if (atomicAdd(ctl, 1u) == gridDim.x - 1) {
+            atomicExch(ctl, 0u);
+            __threadfence();
+            atomicAdd(ctl + 1, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*gen == g) {
+                if (*err) break;
+                if (clock64() - t0 > kWaitLimitCycles) {
+                    atomicOr(ctl + 2, 1u);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        ok_s = *err == 0;
+    }
+    __syncthreads();
+    return ok_s != 0;
+}
+
+__global__ void __launch_bounds__(512, 1) jacobi_fused_kernel(FusedArgs a) {
+    __shared__ double red[16];
+    const int I = a.I, J = a.J, K = a.K, Ji = J - 2, Ki = K - 2;
+    const int nint = (I - 2) * Ji * Ki, nall = I * J * K;
+    const int stride = gridDim.x * blockDim.x, tid0 = blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t sj = a.pitch, si = (size_t)J * a.pitch;
+    const float omega = a.omega;
+    for (int it = 0; it < a.iters; ++it) {
+        // ---- N2: stencil on the interior
+        float RH = 0.0f, RL = 0.0f;
+        for (int x = tid0; x < nint; x += stride) {
+            const int k = 1 + x % Ki, r = x / Ki, j = 1 + r % Ji, i = 1 + r / Ji;
+            const size_t c = (size_t)i * si + (size_t)j * sj + k;
+            // p is rewritten by other SMs between iterations: read it from L2
+            // (never a stale L1 line); the coefficients never change in here
+            const float *P = a.p;
+            auto ld = [&](size_t o) { return __ldcg(P + o); };
+            float cf[NCOEF];
+#pragma unroll
+            for (int q = 0; q < NCOEF; ++q) cf[q] = a.coef[q][c];
+            const float pc = ld(c), pE = ld(c + si), pW = ld(c - si), pN = ld(c + sj), pS = ld(c - sj);
+            const float pKp = ld(c + 1), pKm = ld(c - 1);
+            float H, L, th, tl, t1, xh, xl, e;
+            two_prod(cf[0], pE, H, L);                                   // a0 p[i+1]
+            two_prod(cf[1], pN, th, tl); ff_acc(H, L, th, tl);           // a1 p[j+1]
+            two_prod(cf[2], pKp, th, tl); ff_acc(H, L, th, tl);          // a2 p[k+1]
+            {   // b0 Xij: D(i+1) - D(i-1), D = p(j+1) - p(j-1) exact pairs
+                float dnh, dnl, gh, gl;
+                two_sum(ld(c + si + sj), -ld(c + si - sj), dnh, dnl);
+                two_sum(ld(c - si + sj), -ld(c - si - sj), gh, gl);
+                two_sum(dnh, -gh, xh, e);
+                xl = __fadd_rn(e, __fsub_rn(dnl, gl));
+                two_prod(cf[4], xh, th, t1);
+                tl = __fmaf_rn(cf[4], xl, t1);
+                ff_acc(H, L, th, tl);
+            }
+            {   // b1 Xjk: D(k+1) - D(k-1) on plane i
+                float dph, dpl, dmh, dml;
+                two_sum(ld(c + sj + 1), -ld(c - sj + 1), dph, dpl);
+                two_sum(ld(c + sj - 1), -ld(c - sj - 1), dmh, dml);
+                two_sum(dph, -dmh, xh, e);
+                xl = __fadd_rn(e, __fsub_rn(dpl, dml));
+                two_prod(cf[5], xh, th, t1);
+                tl = __fmaf_rn(cf[5], xl, t1);
+                ff_acc(H, L, th, tl);
+            }
+            {   // b2 Xik: F(k+1) - F(k-1), F = p(i+1) - p(i-1) on row j
+                float fph, fpl, fmh, fml;
+                two_sum(ld(c + si + 1), -ld(c - si + 1), fph, fpl);
+                two_sum(ld(c + si - 1), -ld(c - si - 1), fmh, fml);
+                two_sum(fph, -fmh, xh, e);
+                xl = __fadd_rn(e, __fsub_rn(fpl, fml));
+                two_prod(cf[6], xh, th, t1);
+                tl = __fmaf_rn(cf[6], xl, t1);
+                ff_acc(H, L, th, tl);
+            }
+            two_prod(cf[7], pW, th, tl); ff_acc(H, L, th, tl);           // c0 p[i-1]
+            two_prod(cf[8], pS, th, tl); ff_acc(H, L, th, tl);           // c1 p[j-1]
+            two_prod(cf[9], pKm, th, tl); ff_acc(H, L, th, tl);          // c2 p[k-1]
+            ff_acc(H, L, cf[11], 0.0f);                                  // wrk1
+            // ss = (s0 a3 - p) bnd; wrk2 = p + omega ss, rounded once
+            float dh, dl, e1, sh, s1;
+            two_prod(H, cf[3], th, t1);
+            tl = __fmaf_rn(L, cf[3], t1);
+            two_sum(th, -pc, dh, e1);
+            dl = __fadd_rn(e1, tl);
+            two_prod(dh, cf[10], sh, s1);
+            const float sl = __fmaf_rn(dl, cf[10], s1);
+            float wh, w1, yh, e2;
+            two_prod(omega, sh, wh, w1);
+            const float wl = __fmaf_rn(omega, sl, w1);
+            two_sum(pc, wh, yh, e2);
+            a.wrk2[c] = __fadd_rn(yh, __fadd_rn(e2, wl));
+            float nh, nl, qh, q1;
+            two_sum(sh, sl, nh, nl);
+            two_prod(nh, nh, qh, q1);
+            const float ql = __fmaf_rn(__fadd_rn(nh, nh), nl, q1);
+            ff_acc(RH, RL, qh, ql);
+        }
+        double v = (double)RH + (double)RL;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double b = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += red[w];
+            a.partials[blockIdx.x] = b;
+        }
+        if (!fused_grid_barrier(a.ctl)) return;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            double sum = 0.0;
+            for (int b = 0; b < (int)gridDim.x; ++b) sum += __ldcg(&a.partials[b]);
+            a.res[it] = sum;
+        }
+        // ---- N3 copy-back (interior), N4 / N5 faces = g(k)
+        for (int x = tid0; x < nall; x += stride) {
+            const int k = x % K, r = x / K, j = r % J, i = r / J;
+            const size_t c = (size_t)i * si + (size_t)j * sj + k;
+            const bool interior = i >= 1 && i <= I - 2 && j >= 1 && j <= J - 2 && k >= 1 && k <= K - 2;
+            a.p[c] = interior ? __ldcg(&a.wrk2[c]) : dirichlet_dev(k, K);
+        }
+        if (!fused_grid_barrier(a.ctl)) return;
+    }
+}
+
+}  // namespace
+
+size_t jacobi_fused_ctl_bytes() { return 256 + (size_t)sm_count() * 8; }
+
+bool jacobi_fused_eligible(const JacobiDims &d) {
+    if (const char *ev = std::getenv("OO_JACOBI_FUSED")) return ev[0] == '1';
+    const long long nall = (long long)d.I * d.J * d.K;
+    // measured (all iteration nests, 100 iterations): fused 0.74 vs 1.17 ms at
+    // 33 x 33 x 65, 2.73 vs 2.87 ms at 65 x 65 x 129, but 5.36 vs 4.83 ms at
+    // 97 x 97 x 193, where the tiled kernels' bandwidth wins
+    return nall <= (1ll << 20);
+}
+
+void launch_jacobi_fused(const JacobiDims &d, const float *const coef[NCOEF], float *p, float *wrk2, float omega,
+                         int iters, double *res_dev, void *ctl, cudaStream_t s) {
+    OO_REQUIRE((long long)d.I * d.J * d.K < (1ll << 31), OO_EINVAL, "grid too large for the fused iterations");
+    if (iters <= 0) return;
+    // one 512-thread block per SM: every grid barrier is sm_count() arrivals
+    // on one counter (thousands of small blocks made the barriers the cost)
+    static std::atomic<int> fits{-1};
+    if (fits.load() < 0) {
+        int b = 0;
+        OO_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, jacobi_fused_kernel, 512, 0));
+        fits.store(b >= 1 ? 1 : 0);
+    }
+    OO_REQUIRE(fits.load() == 1, OO_ECUDA, "fused Jacobi kernel does not fit an SM");
+    const long long nall = (long long)d.I * d.J * d.K;
+    const int grid = (int)std::max<long long>(1, std::min<long long>(sm_count(), (nall + 511) / 512));
+    FusedArgs a{};
+    for (int q = 0; q < NCOEF; ++q) a.coef[q] = coef[q];
+    a.p = p;
+    a.wrk2 = wrk2;
+    a.res = res_dev;
+    a.ctl = static_cast<unsigned *>(ctl);
+    a.partials = reinterpret_cast<double *>(static_cast<char *>(ctl) + 256);
+    a.I = d.I;
+    a.J = d.J;
+    a.K = d.K;
+    a.pitch = d.pitch;
+    a.iters = iters;
+    a.omega = omega;
+    OO_CUDA_TRY(cudaMemsetAsync(ctl, 0, 16, s));
+    void *args[] = {&a};
+    OO_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)jacobi_fused_kernel, dim3(grid), dim3(512), args, 0, s));
+}
+
+unsigned jacobi_fused_check(void *ctl, cudaStream_t s) {
+    unsigned e = 0;
+    OO_CUDA_TRY(cudaMemcpyAsync(&e, static_cast<char *>(ctl) + 8, 4, cudaMemcpyDeviceToHost, s));
+    OO_CUDA_TRY(cudaStreamSynchronize(s));
+    return e;
+}
+
 // ================================================================== stencil
 struct StencilMaps {
     CUtensorMap coef[NCOEF];

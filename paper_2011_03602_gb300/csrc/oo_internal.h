@@ -83,6 +83,7 @@ struct JacobiWork {
     float *host = nullptr;            // NARR arrays, each n_host() floats (pinned)
     double *res_host = nullptr;       // iters_cap doubles (pinned)
     StencilPlan *splan = nullptr;
+    void *fused_ctl = nullptr;        // fused-iteration barrier words + residual partials
     float *dptr(int v) const { return dev + (size_t)v * dev_stride; }
     float *hptr(int v) const { return host + (size_t)v * d.n_host(); }
 };
@@ -238,6 +239,13 @@ size_t stencil_scratch_bytes(const JacobiDims &d, int num_sms);
 void stencil_plan_destroy(StencilPlan *sp);
 // One stencil sweep; the residual (FP64) lands in *res_dev.
 void launch_stencil(StencilPlan *sp, float omega, double *res_dev, cudaStream_t s);
+// All iterations of the all-GPU iteration nests in one cooperative launch
+// (small grids): ctl is jacobi_fused_ctl_bytes() of device scratch.
+size_t jacobi_fused_ctl_bytes();
+bool jacobi_fused_eligible(const JacobiDims &d);
+void launch_jacobi_fused(const JacobiDims &d, const float *const coef[NCOEF], float *p, float *wrk2, float omega,
+                         int iters, double *res_dev, void *ctl, cudaStream_t s);
+unsigned jacobi_fused_check(void *ctl, cudaStream_t s);
 // Device address of the plan's error word (0 = fine).
 const unsigned *stencil_plan_err_ptr(const StencilPlan *sp);
 // Reads and clears the device-side error word of the plan (0 = fine).

@@ -27,6 +27,7 @@ double ms_since(Clock::time_point t0) {
 void free_work(JacobiWork *w) {
     if (!w) return;
     stencil_plan_destroy(w->splan);
+    if (w->fused_ctl) cudaFree(w->fused_ctl);
     if (w->dev) cudaFree(w->dev);
     if (w->res_dev) cudaFree(w->res_dev);
     if (w->host) cudaFreeHost(w->host);
@@ -74,6 +75,7 @@ JacobiWork *ensure_work(Ctx &c, int I, int J, int K, int iters) {
         const float *coef[NCOEF];
         for (int a = 0; a < NCOEF; ++a) coef[a] = w->dptr(a);
         w->splan = stencil_plan_create(w->d, coef, w->dptr(VAR_P), w->dptr(VAR_WRK2), c.num_sms);
+        OO_CUDA_TRY(cudaMalloc(&w->fused_ctl, jacobi_fused_ctl_bytes()));
     } catch (...) {
         free_work(w);
         throw;
@@ -208,7 +210,23 @@ void run_pattern(Ctx &c, uint64_t gene, int hoist, const oo_jacobi &prob, float 
         run_transfers(point++);
         run_nest(n, 0);
     }
-    for (int it = 0; it < iters && !stop; ++it) {
+    // All four iteration nests on the GPU with no copy inside the loop (the
+    // hoisted plan): small grids run every iteration in one cooperative
+    // launch instead of 4 x iters launches (per-nest timing keeps the
+    // separate kernels).
+    bool fused = false;
+    if (!timing && iters > 0 && gpu[2] && gpu[3] && gpu[4] && gpu[5] && jacobi_fused_eligible(d)) {
+        fused = true;
+        for (const auto &x : plan)
+            if (x.point > 2 && x.point < n_points) fused = false;
+    }
+    if (fused) {
+        run_transfers(point);
+        launch_jacobi_fused(d, dc, w.dptr(VAR_P), w.dptr(VAR_WRK2), prob.omega, iters, w.res_dev, w.fused_ctl, s);
+        ++launches;
+        point = n_points;
+    }
+    for (int it = 0; it < iters && !stop && !fused; ++it) {
         for (int n = 2; n < 6; ++n) {
             run_transfers(point++);
             run_nest(n, it);
@@ -261,6 +279,10 @@ void run_pattern(Ctx &c, uint64_t gene, int hoist, const oo_jacobi &prob, float 
         const unsigned e = stencil_plan_check(w.splan, s);
         OO_REQUIRE(e == 0, OO_ETIMEOUT,
                    "stencil kernel pipeline wait ran out (error bits " + std::to_string(e) + ")");
+    }
+    if (fused) {
+        const unsigned e = jacobi_fused_check(w.fused_ctl, s);
+        OO_REQUIRE(e == 0, OO_ETIMEOUT, "fused Jacobi iterations: a grid barrier wait ran out");
     }
     OO_CUDA_TRY(cudaGetLastError());
     if (timing) {

@@ -131,6 +131,9 @@ def test_all_64_genes_small_config(oo_mod, ctx, small_ref, hoist):
         _, h2d, d2h = oracle.plan(NESTS, vb, OUTPUTS, gene, hoist, iters)
         assert (st["h2d_bytes"], st["d2h_bytes"]) == (h2d, d2h), gene
         launches = sum(((gene >> n) & 1) * (1 if n < 2 else iters) for n in range(6))
+        if hoist and (gene >> 2) == 0b1111:
+            # all iteration nests on the GPU, hoisted: one cooperative launch
+            launches = (gene & 1) + ((gene >> 1) & 1) + 1
         assert st["n_launches"] == launches, gene
 
 
@@ -201,3 +204,25 @@ def test_bad_arguments(oo_mod, ctx):
         oo_mod.oo_run_pattern(ctx, 1, 1, oo_mod.jacobi(2, 5, 5, 1))
     with pytest.raises(oo_mod.OOError):
         oo_mod.oo_run_pattern(ctx, 1, 2, oo_mod.jacobi(5, 5, 5, 1))
+
+
+@pytest.mark.parametrize("shape,iters", [((33, 33, 65), 20), ((9, 10, 131), 5), ((65, 65, 129), 7)])
+def test_fused_iterations_equal_separate_kernels(oo_mod, shape, iters, monkeypatch):
+    """The cooperative all-iterations kernel (small grids) against the separate
+    nest kernels: p bit-identical (the same float-float arithmetic), residuals
+    to summation order, both against the float-store oracle."""
+    ref_res, ref_p = oracle.jacobi_run(*shape, iters, mode=1)
+    out = {}
+    for flag in ("1", "0"):
+        monkeypatch.setenv("OO_JACOBI_FUSED", flag)
+        ctx = oo_mod.oo_create(0)
+        try:
+            p, res, st = run(oo_mod, ctx, shape, iters, 63, 1)
+        finally:
+            oo_mod.oo_destroy(ctx)
+        assert st["n_launches"] == (3 if flag == "1" else 2 + 4 * iters)
+        out[flag] = (p, res)
+    assert np.array_equal(out["1"][0], out["0"][0])
+    assert np.max(np.abs(out["1"][1] - out["0"][1]) / out["0"][1]) <= 1e-12
+    assert np.array_equal(out["1"][0], ref_p.astype(np.float32))
+    assert np.max(np.abs(out["1"][1] - ref_res) / ref_res) <= 1e-9
