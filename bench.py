@@ -564,6 +564,67 @@ def run_block(args):
     return 0
 
 
+def run_vendor(args):
+    """Context only, not the product path: the function blocks beside the
+    FP64 library calls a function-block offload would otherwise make
+    (cuBLAS DGEMM through torch.matmul, cuFFT Z2Z through torch.fft.fft), on
+    the same stream, the same device-resident inputs (larger than L2 at the
+    largest sizes; no flush) and CUDA-event timing.  max_rel_diff is
+    max |ours - library| / max |library| per result."""
+    import torch
+    from paper_2011_03602_gb300 import oo, synth
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    ctx = oo.oo_create(0, stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    out = {"gemm": {}, "fft": {}}
+    with torch.cuda.stream(stream):
+        for n in (1024, 4096):
+            A = torch.from_numpy(synth.gemm_matrix(1, n, n)).cuda()
+            B = torch.from_numpy(synth.gemm_matrix(2, n, n)).cuda()
+            C = torch.empty(n, n, dtype=torch.float64, device="cuda")
+            ref = torch.empty_like(C)
+            t_lib = timed(lambda: torch.matmul(A, B, out=ref))
+            row = {"cublas_dgemm_ms": round(t_lib, 4),
+                   "cublas_dgemm_fp64_tflops": round(2 * n ** 3 / (t_lib * 1e-3) / 1e12, 2)}
+            for name, prec in (("split3", oo.OO_PREC_SPLIT3_BF16), ("fp64eq", oo.OO_PREC_FP64EQ)):
+                t = timed(lambda: oo.oo_gemm_f64_dev(ctx, n, n, n, A, n, B, n, C, n, prec=prec))
+                oo.oo_gemm_check(ctx, n, n, n)
+                d = float((C - ref).abs().max() / ref.abs().max())
+                row[name] = {"ms": round(t, 4), "speedup_vs_cublas": round(t_lib / t, 2), "max_rel_diff": d}
+            out["gemm"][str(n)] = row
+            del A, B, C, ref
+        for log2n, batch in ((22, 1), (20, 4), (10, 4096)):
+            n = 1 << log2n
+            xr = torch.from_numpy(synth.complex_normal(3, n * batch).view(np.float64).copy()).cuda()
+            y = torch.empty_like(xr)
+            xc = torch.view_as_complex(xr.view(-1, 2)).view(batch, n)
+            ref = torch.empty_like(xc)
+            t_lib = timed(lambda: ref.copy_(torch.fft.fft(xc, dim=-1)))
+            t = timed(lambda: oo.oo_fft_c128_dev(ctx, n, batch, -1, xr, y))
+            yc = torch.view_as_complex(y.view(-1, 2)).view(batch, n)
+            d = float((yc - ref).abs().max() / ref.abs().max())
+            out["fft"][f"2^{log2n}x{batch}"] = {"cufft_z2z_ms": round(t_lib, 4), "ours_ms": round(t, 4),
+                                                "speedup_vs_cufft": round(t_lib / t, 2), "max_rel_diff": d}
+            del xr, y, xc, ref
+    oo.oo_sync(ctx)
+    oo.oo_destroy(ctx)
+    print(json.dumps({"mode": "vendor_context", "steps": args.steps, "warmup": max(args.warmup, 3),
+                      "note": "library calls timed for context; not on the product path", **out}))
+    return 0
+
+
 def run_batched(args):
     """Batched uneven function blocks: 4096 split-BF16 GEMMs with m, n, k
     log-uniform in [16, 512] and 2048 complex FFTs with lengths 2^8..2^16
@@ -770,6 +831,8 @@ def main():
     ap.add_argument("--hoist", action="store_true", help="pattern times with transfer hoisting on and off")
     ap.add_argument("--genes", action="store_true", help="all 64 genes x hoisting on/off, 33x33x65, 50 iterations")
     ap.add_argument("--batched", action="store_true", help="batched uneven GEMM/FFT configuration")
+    ap.add_argument("--vendor", action="store_true",
+                    help="context: function blocks beside cuBLAS DGEMM / cuFFT Z2Z on the same GPU")
     ap.add_argument("--serve", action="store_true", help="serving-loop configuration")
     ap.add_argument("--serve-rates", default="2000,5000,10000,20000")
     ap.add_argument("--serve-window", type=float, default=0.5, help="seconds of arrivals per rate")
@@ -809,6 +872,8 @@ def main():
         return run_ga(args)
     if args.block:
         return run_block(args)
+    if args.vendor:
+        return run_vendor(args)
     if args.batched:
         return run_batched(args)
     if args.serve:
