@@ -499,6 +499,10 @@ struct StencilArgs {
 
 namespace {
 
+// residual partial slots per work unit in the scratch array: one per
+// consumer warp, so no variant may have more consumer warps than this
+constexpr int kMaxConsumerWarps = 16;
+
 template <int TK, int TJ>
 struct Tile {
     static constexpr int PW = TK + 8;                   // p tile row: k0-4 .. k0+TK+3
@@ -525,6 +529,7 @@ template <int TK, int TJ, int NCW, int DC, int DP, int PPT, int MINB>
 __global__ void __launch_bounds__((NCW + 1) * 32, MINB)
     stencil_kernel(const __grid_constant__ StencilMaps maps, const StencilArgs a) {
     using T = Tile<TK, TJ>;
+    static_assert(NCW <= kMaxConsumerWarps, "more consumer warps than partial slots per unit");
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // TMA destinations need 128-byte alignment; the launch adds 128 bytes of slack
     unsigned char *smem_base = reinterpret_cast<unsigned char *>(
@@ -990,10 +995,13 @@ void attach_scratch(StencilPlan *sp, void *scratch) {
     StencilArgs &a = sp->args;
     sp->scratch = scratch;
     a.partials = reinterpret_cast<double *>(scratch);
-    a.counter = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(scratch) + (size_t)a.n_units * 16 * 8);
+    a.counter = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(scratch) +
+                                             (size_t)a.n_units * kMaxConsumerWarps * 8);
     a.err = a.counter + 1;
 }
-size_t plan_scratch_bytes(const StencilPlan *sp) { return (size_t)sp->args.n_units * 16 * 8 + 256; }
+size_t plan_scratch_bytes(const StencilPlan *sp) {
+    return (size_t)sp->args.n_units * kMaxConsumerWarps * 8 + 256;
+}
 }  // namespace
 
 size_t stencil_scratch_bytes(const JacobiDims &d, int num_sms) {
@@ -1001,7 +1009,7 @@ size_t stencil_scratch_bytes(const JacobiDims &d, int num_sms) {
     // i-segment split (at most one unit per plane)
     (void)num_sms;
     const long long kt = (d.K - 1 + 63) / 64, jt = (d.J - 2 + 3) / 4;
-    return (size_t)(kt * jt * std::max(1, d.I - 2)) * 16 * 8 + 256;
+    return (size_t)(kt * jt * std::max(1, d.I - 2)) * kMaxConsumerWarps * 8 + 256;
 }
 
 StencilPlan *stencil_plan_create_ext(const JacobiDims &d, const float *const coef[NCOEF], const float *p, float *wrk2,

@@ -57,9 +57,9 @@ def _pad(a, pitch):
     return out
 
 
-@pytest.mark.parametrize("shape", [(3, 3, 3), (5, 7, 9), (12, 19, 70), (33, 33, 65), (20, 21, 300),
-                                   (11, 10, 130), (6, 40, 517)])
-def test_stencil_random_fields(oo_mod, ctx, shape):
+def _stencil_random(oo_mod, ctx, shape):
+    """One stencil sweep on random coefficient and p fields, checked against
+    the oracle; returns the written wrk2 (interior) and the residual."""
     from paper_2011_03602_gb300 import synth
     I, J, K = shape
     coef = np.stack([synth.field(100 + a, shape, -1.0, 1.0) for a in range(12)])
@@ -90,6 +90,34 @@ def test_stencil_random_fields(oo_mod, ctx, shape):
     assert np.all(w[mask] == sentinel)
     r = float(dres.item())
     assert abs(r - r_ref) <= 1e-11 * abs(r_ref)
+    return w[inner], r
+
+
+@pytest.mark.parametrize("shape", [(3, 3, 3), (5, 7, 9), (12, 19, 70), (33, 33, 65), (20, 21, 300),
+                                   (11, 10, 130), (6, 40, 517)])
+def test_stencil_random_fields(oo_mod, ctx, shape):
+    _stencil_random(oo_mod, ctx, shape)
+
+
+N_VARIANTS = 5
+
+
+@pytest.mark.parametrize("variant", range(N_VARIANTS))
+def test_every_tile_variant(oo_mod, variant, monkeypatch):
+    """Every stencil tile variant (tile shape, consumer warps, points per
+    thread, CTAs per SM; OO_STENCIL_VARIANT, read when a plan is made) against the oracle on ragged grids, and point for point
+    equal to the default variant: the per-point arithmetic does not depend
+    on the tiling."""
+    for shape in [(12, 19, 70), (6, 40, 517), (20, 21, 300), (9, 66, 131)]:
+        out = {}
+        for v in (variant, 1):
+            monkeypatch.setenv("OO_STENCIL_VARIANT", str(v))
+            c = oo_mod.oo_create(0)
+            try:
+                out[v] = _stencil_random(oo_mod, c, shape)
+            finally:
+                oo_mod.oo_destroy(c)
+        assert np.array_equal(out[variant][0], out[1][0]), (variant, shape)
 
 
 def test_stencil_repeatable(oo_mod, ctx):
