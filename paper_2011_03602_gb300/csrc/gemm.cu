@@ -500,6 +500,170 @@ __global__ void split_cols_t_kernel(const double *B, long long ldb, int k, int n
     split_b_tile(B, ldb, k, n, kp, kp, eb, B1t, B2t, blockIdx.y * 64, blockIdx.x * 64);
 }
 
+// B (k x n, ldb even, 16-byte aligned) -> column scales eb and B1t, B2t
+// (n x kp, transposed), zero padding in [k, kp).  One CTA per strip of 16
+// columns: pass 1 reads the strip for the columns' largest exponents, pass 2
+// reads it again -- mostly from L2, since the strips of the CTAs in flight
+// (k x 128 bytes each) fit in it -- and writes the splits through a
+// shared-memory transpose.  Same scales and splits as col_maxexp +
+// split_cols_t, with B read from DRAM about once instead of twice.
+constexpr int kStripThreads = 512;
+__device__ __forceinline__ void split_cols_strip(const double *B, long long ldb, int k, int n, int kp, int *eb,
+                                                 __nv_bfloat16 *B1t, __nv_bfloat16 *B2t, int strip) {
+    __shared__ int red[64][17];
+    __shared__ int Ssh[16];
+    __shared__ __nv_bfloat16 th[16][258], tl[16][258];
+    const int c0 = strip * 16;
+    const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;  // 8 column pairs x 64 rows
+    const int col = c0 + 2 * tx;
+    const bool in0 = col < n, in1 = col + 1 < n;
+    auto ex = [](double x) {
+        const int e = (int)((__double_as_longlong(x) >> 52) & 0x7ff);
+        return e == 0x7ff ? 0x7fe : e;
+    };
+    auto load = [&](int l) {
+        double2 v = make_double2(0.0, 0.0);
+        if (l < k) {
+            const double *src = B + (long long)l * ldb + col;
+            if (in1)
+                v = *reinterpret_cast<const double2 *>(src);
+            else if (in0)
+                v.x = *src;
+        }
+        return v;
+    };
+    // pass 1: largest biased exponent of each column
+    int m0 = 0, m1 = 0;
+#pragma unroll 8
+    for (int l = ty; l < k; l += 64) {
+        const double2 v = load(l);
+        m0 = max(m0, ex(v.x));
+        m1 = max(m1, ex(v.y));
+    }
+    red[ty][2 * tx] = m0;
+    red[ty][2 * tx + 1] = m1;
+    __syncthreads();
+    if (threadIdx.x < 16) {
+        int mx = 0;
+        for (int y = 0; y < 64; ++y) mx = max(mx, red[y][threadIdx.x]);
+        const int S = mx == 0 ? 0 : mx - 1023 + 1;
+        Ssh[threadIdx.x] = S;
+        if (c0 + (int)threadIdx.x < n) eb[c0 + threadIdx.x] = S;
+    }
+    __syncthreads();
+    const int S0 = Ssh[2 * tx], S1 = Ssh[2 * tx + 1];
+    // pass 2: 256 k values per step, last rows first (the most recently
+    // read into L2); the next step's four loads are issued before this
+    // step's stores
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;  // warp w writes column c0 + w
+    const int last = (kp - 1) / 256 * 256;
+    double2 nv[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) nv[q] = load(last + 64 * q + ty);
+    for (int l0 = last; l0 >= 0; l0 -= 256) {
+        double2 v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = nv[q];
+        if (l0 >= 256) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) nv[q] = load(l0 - 256 + 64 * q + ty);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            split_bf16(v[q].x, S0, th[2 * tx][64 * q + ty], tl[2 * tx][64 * q + ty]);
+            split_bf16(v[q].y, S1, th[2 * tx + 1][64 * q + ty], tl[2 * tx + 1][64 * q + ty]);
+        }
+        __syncthreads();
+        const int c = c0 + w;
+        if (c < n) {
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int l = l0 + 64 * h + 2 * lane;
+                if (l < kp) {
+                    const int q = 64 * h + 2 * lane;
+                    *reinterpret_cast<__nv_bfloat162 *>(B1t + (long long)c * kp + l) =
+                        __halves2bfloat162(th[w][q], th[w][q + 1]);
+                    *reinterpret_cast<__nv_bfloat162 *>(B2t + (long long)c * kp + l) =
+                        __halves2bfloat162(tl[w][q], tl[w][q + 1]);
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kStripThreads) split_cols_strip_kernel(const double *B, long long ldb, int k, int n,
+                                                                        int kp, int *eb, __nv_bfloat16 *B1t,
+                                                                        __nv_bfloat16 *B2t) {
+    split_cols_strip(B, ldb, k, n, kp, eb, B1t, B2t, blockIdx.x);
+}
+
+// One row of A -> its scale exponent and BF16 hi / lo rows, by 256 threads
+// (half of a 512-thread CTA) synchronising on named barrier `bar`; row
+// 16-byte aligned, lda even.  Same results as split_rows_v2_kernel.
+__device__ __forceinline__ void split_row_half(const double *base, int k, int kp, int *ea_row, __nv_bfloat16 *a1,
+                                               __nv_bfloat16 *a2, int t, int bar, int *red8) {
+    const double2 *src = reinterpret_cast<const double2 *>(base);
+    const int k2 = k >> 1;
+    auto ex = [](double x) {
+        const int e = (int)((__double_as_longlong(x) >> 52) & 0x7ff);
+        return e == 0x7ff ? 0x7fe : e;
+    };
+    int mx = 0;
+#pragma unroll 8
+    for (int l2 = t; l2 < k2; l2 += 256) {
+        const double2 v = src[l2];
+        mx = max(mx, max(ex(v.x), ex(v.y)));
+    }
+    if ((k & 1) && t == 0) mx = max(mx, ex(base[k - 1]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((t & 31) == 0) red8[t >> 5] = mx;
+    asm volatile("bar.sync %0, 256;" ::"r"(bar) : "memory");
+    mx = red8[0];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) mx = max(mx, red8[w]);
+    const int S = mx == 0 ? 0 : mx - 1023 + 1;
+    if (t == 0) *ea_row = S;
+    __nv_bfloat162 *d1 = reinterpret_cast<__nv_bfloat162 *>(a1);
+    __nv_bfloat162 *d2 = reinterpret_cast<__nv_bfloat162 *>(a2);
+#pragma unroll 2
+    for (int l2 = t; l2 < kp / 2; l2 += 256) {
+        const int l = 2 * l2;
+        double2 v = make_double2(0.0, 0.0);
+        if (l + 1 < k) {
+            v = src[l2];
+        } else if (l < k) {
+            v.x = base[l];
+        }
+        __nv_bfloat16 h0, o0, h1, o1;
+        split_bf16(v.x, S, h0, o0);
+        split_bf16(v.y, S, h1, o1);
+        d1[l2] = __halves2bfloat162(h0, h1);
+        d2[l2] = __halves2bfloat162(o0, o1);
+    }
+}
+
+// Both operands in one launch: CTAs [0, nstrip) split 16-column strips of
+// B, the rest split two rows of A each, so the bandwidth-bound row splits
+// run while the strips wait on their loads.
+__global__ void __launch_bounds__(kStripThreads) split_ab_kernel(const double *A, long long lda, int m,
+                                                                const double *B, long long ldb, int n, int k, int kp,
+                                                                int nstrip, int *ea, int *eb, __nv_bfloat16 *A1,
+                                                                __nv_bfloat16 *A2, __nv_bfloat16 *B1t,
+                                                                __nv_bfloat16 *B2t) {
+    if ((int)blockIdx.x < nstrip) {
+        split_cols_strip(B, ldb, k, n, kp, eb, B1t, B2t, blockIdx.x);
+        return;
+    }
+    __shared__ int red8[2][8];
+    const int half = threadIdx.x >> 8;
+    const int row = 2 * ((int)blockIdx.x - nstrip) + half;
+    if (row >= m) return;
+    split_row_half(A + (long long)row * lda, k, kp, ea + row, A1 + (long long)row * kp, A2 + (long long)row * kp,
+                   threadIdx.x & 255, 1 + half, red8[half]);
+}
+
 // ------------------------------------------------------- grouped splitting
 struct GroupSplit {
     const double *A, *B;
@@ -575,8 +739,17 @@ void launch_gemm_split3(int m, int n, int k, const double *A, long long lda, con
     unsigned *err = reinterpret_cast<unsigned *>(eb + n);
     OO_CUDA_TRY(cudaMemsetAsync(err, 0, 4, s));
 
-    OO_CUDA_TRY(cudaMemsetAsync(eb, 0, (size_t)n * 4, s));
-    {
+    const bool strip_b = ldb % 2 == 0 && ((uintptr_t)B & 15u) == 0;
+    const bool rows_v2 = lda % 2 == 0 && ((uintptr_t)A & 15u) == 0;
+    if (strip_b && rows_v2) {
+        const int nstrip = (n + 15) / 16;
+        const long long grid = (long long)nstrip + (m + 1) / 2;
+        OO_REQUIRE(grid < (1ll << 31), OO_EINVAL, "problem too large");
+        split_ab_kernel<<<(unsigned)grid, kStripThreads, 0, s>>>(A, lda, m, B, ldb, n, k, kp, nstrip, ea, eb, A1, A2,
+                                                                B1, B2);
+        OO_CUDA_TRY(cudaGetLastError());
+    } else if (!strip_b) {
+        OO_CUDA_TRY(cudaMemsetAsync(eb, 0, (size_t)n * 4, s));
         const int rows_per = 256;
         dim3 grid((n + 31) / 32, (k + rows_per - 1) / rows_per), block(32, 8);
         OO_REQUIRE(grid.y <= 65535, OO_EINVAL, "k too large");
@@ -585,19 +758,19 @@ void launch_gemm_split3(int m, int n, int k, const double *A, long long lda, con
         exp_to_scale_kernel<<<(n + 255) / 256, 256, 0, s>>>(eb, n);
         OO_CUDA_TRY(cudaGetLastError());
     }
-    {
-        int dev = 0, sms = 148;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        (void)sms;
-        if (lda % 2 == 0 && ((uintptr_t)A & 15u) == 0)
+    if (!(strip_b && rows_v2)) {
+        if (rows_v2)
             split_rows_v2_kernel<<<m, 256, 0, s>>>(A, lda, m, k, kp, ea, A1, A2);
         else
             split_rows_fused_kernel<<<(m + 7) / 8, 256, 0, s>>>(A, lda, m, k, kp, ea, A1, A2);
         OO_CUDA_TRY(cudaGetLastError());
-        dim3 grid((n + 63) / 64, kp / 64);
-        OO_REQUIRE(grid.y <= 65535, OO_EINVAL, "k too large");
-        split_cols_t_kernel<<<grid, 256, 0, s>>>(B, ldb, k, n, kp, eb, B1, B2);
+        if (strip_b) {
+            split_cols_strip_kernel<<<(n + 15) / 16, kStripThreads, 0, s>>>(B, ldb, k, n, kp, eb, B1, B2);
+        } else {
+            dim3 grid((n + 63) / 64, kp / 64);
+            OO_REQUIRE(grid.y <= 65535, OO_EINVAL, "k too large");
+            split_cols_t_kernel<<<grid, 256, 0, s>>>(B, ldb, k, n, kp, eb, B1, B2);
+        }
         OO_CUDA_TRY(cudaGetLastError());
     }
     GemmMaps maps;
