@@ -418,7 +418,7 @@ __global__ void fft_maxexp_group_kernel(const FftGroupReq *reqs, int *expo) {
 
 __device__ __forceinline__ int scale_from(int e) { return e == 0 ? 0 : e - 1023 + 1; }
 
-__global__ void __launch_bounds__(kFftThreads, 1)
+__global__ void __launch_bounds__(kFftThreads, 2)
     fft_group_kernel(const FftItem *items, int nitems, const FftGroupReq *reqs, const int *tlist, const int *expo) {
     extern __shared__ __align__(16) float4 fsmem[];
     float4 *sd = fsmem;
@@ -654,7 +654,12 @@ struct FftGroup {
     FftItem *d_items = nullptr;
     FftGroupReq *d_reqs = nullptr;
     int *d_tlist = nullptr, *d_expo = nullptr;
-    int n_items_a = 0, n_items_b = 0, nreq = 0, grid_a = 1, grid_b = 1, maxexp_x = 1;
+    // three launches: [0] whole transforms and column passes with L <= 2048,
+    // [1] whole transforms of 4096 points (a 64 KB twiddle table: one CTA per
+    // SM), [2] row passes (after every column pass); items stored in that order
+    int n_items[3] = {0, 0, 0}, grid[3] = {1, 1, 1};
+    size_t smem[3] = {0, 0, 0};
+    int nreq = 0, maxexp_x = 1;
     double elems = 0;
 };
 
@@ -726,8 +731,20 @@ FftGroup *fft_group_create(const std::vector<FftDesc> &v, const std::vector<cons
                                   p->log2n, p->log2n1, p->log2n2, v[i].dir > 0 ? 1 : 0};
             elems += (double)(1ll << p->log2n);
         }
-        std::vector<FftItem> all(items_a);
-        all.insert(all.end(), items_b.begin(), items_b.end());
+        std::vector<FftItem> part[3];
+        for (const FftItem &it : items_a) part[it.log2L == 12 ? 1 : 0].push_back(it);
+        part[2] = items_b;
+        std::vector<FftItem> all;
+        for (int q = 0; q < 3; ++q) {
+            int maxl = 0;
+            for (const FftItem &it : part[q]) maxl = std::max(maxl, it.log2L);
+            all.insert(all.end(), part[q].begin(), part[q].end());
+            g->n_items[q] = (int)part[q].size();
+            // data + this launch's largest per-stage twiddle table
+            g->smem[q] = (size_t)(kFftElems + (1 << maxl)) * sizeof(float4);
+            const int per_sm = g->smem[q] <= (size_t)110 * 1024 ? 2 : 1;
+            g->grid[q] = std::max(1, std::min(g->n_items[q], num_sms * per_sm));
+        }
         OO_CUDA_TRY(cudaMemcpy(base + off_items, all.data(), all.size() * sizeof(FftItem), cudaMemcpyHostToDevice));
         OO_CUDA_TRY(cudaMemcpy(base + off_reqs, reqs.data(), reqs.size() * sizeof(FftGroupReq), cudaMemcpyHostToDevice));
         if (!tlist.empty())
@@ -736,11 +753,7 @@ FftGroup *fft_group_create(const std::vector<FftDesc> &v, const std::vector<cons
         g->d_reqs = reinterpret_cast<FftGroupReq *>(base + off_reqs);
         g->d_tlist = reinterpret_cast<int *>(base + off_tlist);
         g->d_expo = reinterpret_cast<int *>(base + off_expo);
-        g->n_items_a = (int)items_a.size();
-        g->n_items_b = (int)items_b.size();
         g->nreq = (int)v.size();
-        g->grid_a = std::max(1, std::min(g->n_items_a, num_sms));
-        g->grid_b = std::max(1, std::min(g->n_items_b, num_sms));
         g->maxexp_x = (int)std::max<long long>(1, std::min<long long>(16, (maxn + 4095) / 4096));
         g->elems = elems;
     } catch (...) {
@@ -755,18 +768,16 @@ void fft_group_launch(FftGroup *g, cudaStream_t s) {
     OO_CUDA_TRY(cudaMemsetAsync(g->d_expo, 0, (size_t)g->nreq * 4, s));
     fft_maxexp_group_kernel<<<dim3(g->maxexp_x, g->nreq), 256, 0, s>>>(g->d_reqs, g->d_expo);
     OO_CUDA_TRY(cudaGetLastError());
-    const size_t smem = (size_t)(kFftElems + 4096) * sizeof(float4);
     static std::atomic<uint64_t> attr{0};
-    set_smem_limit_once((const void *)fft_group_kernel, smem, attr);
-    if (g->n_items_a > 0) {
-        fft_group_kernel<<<g->grid_a, kFftThreads, smem, s>>>(g->d_items, g->n_items_a, g->d_reqs, g->d_tlist,
-                                                               g->d_expo);
-        OO_CUDA_TRY(cudaGetLastError());
-    }
-    if (g->n_items_b > 0) {
-        fft_group_kernel<<<g->grid_b, kFftThreads, smem, s>>>(g->d_items + g->n_items_a, g->n_items_b, g->d_reqs,
-                                                               g->d_tlist, g->d_expo);
-        OO_CUDA_TRY(cudaGetLastError());
+    set_smem_limit_once((const void *)fft_group_kernel, (size_t)(kFftElems + 4096) * sizeof(float4), attr);
+    int first = 0;
+    for (int q = 0; q < 3; ++q) {
+        if (g->n_items[q] > 0) {
+            fft_group_kernel<<<g->grid[q], kFftThreads, g->smem[q], s>>>(g->d_items + first, g->n_items[q],
+                                                                          g->d_reqs, g->d_tlist, g->d_expo);
+            OO_CUDA_TRY(cudaGetLastError());
+        }
+        first += g->n_items[q];
     }
 }
 
