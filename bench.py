@@ -457,7 +457,12 @@ def run_fb(args):
            "loop_best_ms": float(ga["best_ms"]), "loop_all_cpu_ms": st["wall_ms"],
            "program_all_cpu_ms": round(all_cpu, 2), "program_best_ms": round(best, 2),
            "speedup_vs_all_cpu": round(all_cpu / best, 2), "fb_trial_s": round(t_fb, 1),
-           "loop_ga_s": round(t_ga, 1)}
+           "loop_ga_s": round(t_ga, 1),
+           # every gene the GA measured: wall ms, or None where it failed the
+           # result gate or ran past the evaluation time limit
+           "loop_gene_ms": {format(int(g), "06b"): (round(float(ga["gene_ms"][g]), 3)
+                                                    if np.isfinite(ga["gene_ms"][g]) else None)
+                            for g in sorted(set(int(x) for x in ga["history"].reshape(-1)))}}
     oo.oo_destroy(ctx)
     print(json.dumps(out))
     return 0
