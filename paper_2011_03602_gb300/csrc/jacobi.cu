@@ -184,6 +184,53 @@ __global__ void copyback_kernel(float *__restrict__ p, const float *__restrict__
     }
 }
 
+// N3, N4 and N5 in one pass, for patterns that run all three on the GPU
+// with no copy between them: one warp per (i, j) row of p; an interior row
+// takes wrk2 on 1 <= k <= K-2 and g(0), g(K-1) at its ends, a face row g(k)
+// everywhere.  Every element is written once, with the values the three
+// nests leave in sequence (interior copy, then the i / j faces, then the k
+// faces, which all hold g).
+__global__ void copyback_faces_kernel(float *__restrict__ p, const float *__restrict__ wrk2, int I, int J, int K,
+                                      int pitch) {
+    const long long rows = (long long)I * J;
+    const int chunks = (K + 3) / 4;
+    const float g0 = dirichlet_dev(0, K), g1 = dirichlet_dev(K - 1, K);
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    for (long long r = (long long)blockIdx.x * wpb + (threadIdx.x >> 5); r < rows; r += (long long)gridDim.x * wpb) {
+        const int i = (int)(r / J), j = (int)(r % J);
+        const size_t off = (size_t)r * pitch;
+        float4 *dst = reinterpret_cast<float4 *>(p + off);
+        if (i == 0 || i == I - 1 || j == 0 || j == J - 1) {
+            for (int c = lane; c < chunks; c += 32) {
+                const int k = 4 * c;
+                if (k + 3 < K) {
+                    dst[c] = make_float4(dirichlet_dev(k, K), dirichlet_dev(k + 1, K), dirichlet_dev(k + 2, K),
+                                         dirichlet_dev(k + 3, K));
+                } else {
+                    for (int e = 0; e < 4 && k + e < K; ++e) p[off + k + e] = dirichlet_dev(k + e, K);
+                }
+            }
+            continue;
+        }
+        const float4 *src = reinterpret_cast<const float4 *>(wrk2 + off);
+#pragma unroll 4
+        for (int c = lane; c < chunks; c += 32) {
+            const int k = 4 * c;
+            if (k + 3 < K) {
+                float4 v = src[c];
+                if (k == 0) v.x = g0;
+                if (k + 3 == K - 1) v.w = g1;
+                dst[c] = v;
+            } else {
+                for (int e = 0; e < 4 && k + e < K; ++e) {
+                    const int kk = k + e;
+                    p[off + kk] = kk == 0 ? g0 : (kk == K - 1 ? g1 : wrk2[off + kk]);
+                }
+            }
+        }
+    }
+}
+
 __global__ void bc_ij_kernel(float *p, int I, int J, int K, int pitch) {
     const unsigned chunks = (unsigned)(K + 3) / 4u;
     const unsigned face_rows = 2u * J + 2u * (I - 2);
@@ -255,6 +302,12 @@ void launch_pinit(const JacobiDims &d, float *p, float *wrk2, cudaStream_t s) {
 void launch_copyback(const JacobiDims &d, float *p, const float *wrk2, cudaStream_t s) {
     const size_t rows = (size_t)(d.I - 2) * (d.J - 2);  // one warp each, 8 warps per block
     copyback_kernel<<<grid_for(rows, 8, sm_count() * 16), 256, 0, s>>>(p, wrk2, d.I, d.J, d.K, d.pitch);
+    OO_CUDA_TRY(cudaGetLastError());
+}
+
+void launch_copyback_faces(const JacobiDims &d, float *p, const float *wrk2, cudaStream_t s) {
+    const size_t rows = (size_t)d.I * d.J;  // one warp each, 8 warps per block
+    copyback_faces_kernel<<<grid_for(rows, 8, sm_count() * 16), 256, 0, s>>>(p, wrk2, d.I, d.J, d.K, d.pitch);
     OO_CUDA_TRY(cudaGetLastError());
 }
 

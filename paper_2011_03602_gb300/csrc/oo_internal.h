@@ -226,6 +226,8 @@ Ctx &ctx_state(oo_ctx *ctx);
 void launch_coef(const JacobiDims &d, float *const coef[NCOEF], cudaStream_t s);
 void launch_pinit(const JacobiDims &d, float *p, float *wrk2, cudaStream_t s);
 void launch_copyback(const JacobiDims &d, float *p, const float *wrk2, cudaStream_t s);
+// N3 + N4 + N5 in one pass (all three on the GPU, no copy between them)
+void launch_copyback_faces(const JacobiDims &d, float *p, const float *wrk2, cudaStream_t s);
 void launch_bc_ij(const JacobiDims &d, float *p, cudaStream_t s);
 void launch_bc_k(const JacobiDims &d, float *p, cudaStream_t s);
 

@@ -226,8 +226,22 @@ void run_pattern(Ctx &c, uint64_t gene, int hoist, const oo_jacobi &prob, float 
         ++launches;
         point = n_points;
     }
+    // N3, N4 and N5 on the GPU with no copy between them: one pass writes
+    // what the three leave (interior from wrk2, faces g), instead of three
+    // launches; per-nest timing keeps them apart
+    std::vector<char> xfer_at((size_t)n_points + 1, 0);
+    for (const auto &x : plan)
+        if (x.point <= (uint32_t)n_points) xfer_at[x.point] = 1;
+    const bool tail_on_gpu = !timing && gpu[3] && gpu[4] && gpu[5];
     for (int it = 0; it < iters && !stop && !fused; ++it) {
         for (int n = 2; n < 6; ++n) {
+            if (n == 3 && tail_on_gpu && !xfer_at[point + 1] && !xfer_at[point + 2]) {
+                run_transfers(point);
+                launch_copyback_faces(d, w.dptr(VAR_P), w.dptr(VAR_WRK2), s);
+                ++launches;
+                point += 3;
+                break;
+            }
             run_transfers(point++);
             run_nest(n, it);
         }

@@ -238,9 +238,7 @@ void start(Server &S, SReq &q) {
         launch_pinit(d, a[VAR_P], a[VAR_WRK2], s);
         for (int it = 0; it < r.iters; ++it) {
             launch_stencil(q.splan, r.omega, res + it, s);
-            launch_copyback(d, a[VAR_P], a[VAR_WRK2], s);
-            launch_bc_ij(d, a[VAR_P], s);
-            launch_bc_k(d, a[VAR_P], s);
+            launch_copyback_faces(d, a[VAR_P], a[VAR_WRK2], s);  // N3 + N4 + N5
         }
         const size_t wb = (size_t)d.K * 4;
         OO_CUDA_TRY(cudaMemcpy2DAsync(hst + q.h_out, wb, a[VAR_P], (size_t)d.pitch * 4, wb, (size_t)d.I * d.J,

@@ -23,6 +23,27 @@ def oo_mod():
     return oo
 
 
+def expected_launches(gene, hoist, iters, xs, fused_ok=True):
+    """Kernel launches of a pattern run (per-nest timing off): one per GPU
+    setup nest; per iteration one per GPU nest, except that N3, N4 and N5
+    on the GPU with no planned copy before N4 or N5 share one launch; and
+    all iteration nests on the GPU, hoisted, on a small grid (every grid
+    these tests count launches on), one cooperative launch in all."""
+    on = [(gene >> n) & 1 for n in range(6)]
+    points = {x[0] for x in xs}
+    if fused_ok and all(on[2:]) and not any(2 < q < 2 + 4 * iters for q in points):
+        return on[0] + on[1] + 1
+    n = on[0] + on[1]
+    for it in range(iters):
+        p3 = 2 + 4 * it + 1
+        n += on[2]
+        if on[3] and on[4] and on[5] and p3 + 1 not in points and p3 + 2 not in points:
+            n += 1
+        else:
+            n += on[3] + on[4] + on[5]
+    return n
+
+
 @pytest.fixture(scope="module")
 def ctx(oo_mod):
     c = oo_mod.oo_create(0)
@@ -156,13 +177,9 @@ def test_all_64_genes_small_config(oo_mod, ctx, small_ref, hoist):
         assert np.max(np.abs(p - ref_p)) <= 1e-6, gene
         assert np.mean(p != ref_p.astype(np.float32)) <= 1e-3, gene
         assert np.max(np.abs(res - res64) / res64) <= RES_TOL, gene
-        _, h2d, d2h = oracle.plan(NESTS, vb, OUTPUTS, gene, hoist, iters)
+        xs, h2d, d2h = oracle.plan(NESTS, vb, OUTPUTS, gene, hoist, iters)
         assert (st["h2d_bytes"], st["d2h_bytes"]) == (h2d, d2h), gene
-        launches = sum(((gene >> n) & 1) * (1 if n < 2 else iters) for n in range(6))
-        if hoist and (gene >> 2) == 0b1111:
-            # all iteration nests on the GPU, hoisted: one cooperative launch
-            launches = (gene & 1) + ((gene >> 1) & 1) + 1
-        assert st["n_launches"] == launches, gene
+        assert st["n_launches"] == expected_launches(gene, hoist, iters, xs), gene
 
 
 @pytest.mark.parametrize("shape,iters", [((3, 3, 3), 4), ((4, 4, 4), 2), ((5, 7, 9), 7),
@@ -248,9 +265,34 @@ def test_fused_iterations_equal_separate_kernels(oo_mod, shape, iters, monkeypat
             p, res, st = run(oo_mod, ctx, shape, iters, 63, 1)
         finally:
             oo_mod.oo_destroy(ctx)
-        assert st["n_launches"] == (3 if flag == "1" else 2 + 4 * iters)
+        assert st["n_launches"] == (3 if flag == "1" else 2 + 2 * iters)
         out[flag] = (p, res)
     assert np.array_equal(out["1"][0], out["0"][0])
     assert np.max(np.abs(out["1"][1] - out["0"][1]) / out["0"][1]) <= 1e-12
     assert np.array_equal(out["1"][0], ref_p.astype(np.float32))
     assert np.max(np.abs(out["1"][1] - ref_res) / ref_res) <= 1e-9
+
+
+@pytest.mark.parametrize("shape,iters", [((3, 3, 3), 3), ((4, 4, 4), 2), ((5, 7, 5), 4), ((5, 7, 9), 3),
+                                         ((9, 10, 131), 3), ((18, 66, 34), 2), ((6, 40, 517), 2)])
+def test_copyback_faces_pass_equals_separate_nests(oo_mod, shape, iters, monkeypatch):
+    """N3 + N4 + N5 in one pass (all three on the GPU, no copy between them)
+    against the three nest kernels (per-nest timing keeps them apart): p and
+    the residuals bit-identical, and p equal to the float-store oracle."""
+    monkeypatch.setenv("OO_JACOBI_FUSED", "0")
+    I, J, K = shape
+    ctx = oo_mod.oo_create(0)
+    try:
+        out = {}
+        for timing in (False, True):
+            p = np.empty(I * J * K, np.float32)
+            res = np.empty(iters)
+            st = oo_mod.oo_run_pattern(ctx, 63, 1, oo_mod.jacobi(I, J, K, iters, timing=timing), p, res)
+            assert st["n_launches"] == 2 + (4 if timing else 2) * iters
+            out[timing] = (p, res)
+    finally:
+        oo_mod.oo_destroy(ctx)
+    assert np.array_equal(out[False][0], out[True][0])
+    assert np.array_equal(out[False][1], out[True][1])
+    _, ref_p = oracle.jacobi_run(I, J, K, iters, mode=1)
+    assert np.array_equal(out[False][0], ref_p.reshape(-1).astype(np.float32))
