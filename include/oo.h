@@ -253,6 +253,21 @@ oo_status oo_stencil_noalloc_dev(oo_ctx *ctx, int I, int J, int K, int pitch,
                                  const float *const *coef, const float *p, float omega,
                                  float *wrk2, double *res_dev);
 
+/* Fault injection for tests of the bounded device waits; nothing faults,
+ * traps or hangs.  Arms a one-shot failure on the context:
+ *   OO_INJECT_STENCIL_LOAD  the next stencil sweep launched by
+ *                           oo_run_pattern / oo_run_pattern_dev never issues
+ *                           its first p-tile copy, so the consumer warps'
+ *                           bounded wait (about one second) runs out;
+ *   OO_INJECT_FUSED_BARRIER the next fused-iteration launch (small grids,
+ *                           all iteration nests on the GPU) waits at its first
+ *                           grid barrier for one block more than it launched.
+ * Either kernel then sets its error word, waits (bounded) for its own copies
+ * in flight and returns; the pattern call returns OO_ETIMEOUT and the
+ * context stays usable.  OO_INJECT_NONE disarms; OO_EINVAL for other values. */
+enum { OO_INJECT_NONE = 0, OO_INJECT_STENCIL_LOAD = 1, OO_INJECT_FUSED_BARRIER = 2 };
+oo_status oo_inject_wait_timeout(oo_ctx *ctx, int what);
+
 /* Device row pitch (floats) the library uses for a row of K floats. */
 int oo_jacobi_pitch(int K);
 

@@ -154,6 +154,15 @@ oo_status oo_sync(oo_ctx *ctx) {
     });
 }
 
+oo_status oo_inject_wait_timeout(oo_ctx *ctx, int what) {
+    if (!ctx) return OO_EINVAL;
+    return guarded(ctx, [&] {
+        OO_REQUIRE(what == OO_INJECT_NONE || what == OO_INJECT_STENCIL_LOAD || what == OO_INJECT_FUSED_BARRIER,
+                   OO_EINVAL, "unknown fault injection " + std::to_string(what));
+        ctx->c.inject_wait = what;
+    });
+}
+
 oo_status oo_load_nests(oo_ctx *ctx, const oo_nest *nests, int n_nests, const oo_var *vars,
                         int n_vars, uint64_t outputs, int *gene_len_out) {
     if (!ctx) return OO_EINVAL;

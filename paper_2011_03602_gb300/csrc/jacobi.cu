@@ -344,16 +344,17 @@ struct FusedArgs {
     unsigned *ctl;          // [0] arrivals, [1] generation, [2] error
     int I, J, K, pitch, iters;
     float omega;
+    unsigned barrier_extra;  // fault injection: arrivals awaited beyond the grid (0 in normal runs)
 };
 
-__device__ __forceinline__ bool fused_grid_barrier(unsigned *ctl) {
+__device__ __forceinline__ bool fused_grid_barrier(unsigned *ctl, unsigned extra) {
     __syncthreads();
     __shared__ int ok_s;
     if (threadIdx.x == 0) {
         volatile unsigned *gen = ctl + 1, *err = ctl + 2;
         const unsigned g = *gen;
         __threadfence();
-        if (atomicAdd(ctl, 1u) == gridDim.x - 1) {
+        if (atomicAdd(ctl, 1u) == gridDim.x - 1 + extra) {
             atomicExch(ctl, 0u);
             __threadfence();
             atomicAdd(ctl + 1, 1u);
@@ -463,7 +464,7 @@ __global__ void __launch_bounds__(512, 1) jacobi_fused_kernel(FusedArgs a) {
             for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += red[w];
             a.partials[blockIdx.x] = b;
         }
-        if (!fused_grid_barrier(a.ctl)) return;
+        if (!fused_grid_barrier(a.ctl, a.barrier_extra)) return;
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             double sum = 0.0;
             for (int b = 0; b < (int)gridDim.x; ++b) sum += __ldcg(&a.partials[b]);
@@ -476,7 +477,7 @@ __global__ void __launch_bounds__(512, 1) jacobi_fused_kernel(FusedArgs a) {
             const bool interior = i >= 1 && i <= I - 2 && j >= 1 && j <= J - 2 && k >= 1 && k <= K - 2;
             a.p[c] = interior ? __ldcg(&a.wrk2[c]) : dirichlet_dev(k, K);
         }
-        if (!fused_grid_barrier(a.ctl)) return;
+        if (!fused_grid_barrier(a.ctl, a.barrier_extra)) return;
     }
 }
 
@@ -494,7 +495,7 @@ bool jacobi_fused_eligible(const JacobiDims &d) {
 }
 
 void launch_jacobi_fused(const JacobiDims &d, const float *const coef[NCOEF], float *p, float *wrk2, float omega,
-                         int iters, double *res_dev, void *ctl, cudaStream_t s) {
+                         int iters, double *res_dev, void *ctl, cudaStream_t s, bool inject_timeout) {
     OO_REQUIRE((long long)d.I * d.J * d.K < (1ll << 31), OO_EINVAL, "grid too large for the fused iterations");
     if (iters <= 0) return;
     // one 512-thread block per SM: every grid barrier is sm_count() arrivals
@@ -521,6 +522,7 @@ void launch_jacobi_fused(const JacobiDims &d, const float *const coef[NCOEF], fl
     a.pitch = d.pitch;
     a.iters = iters;
     a.omega = omega;
+    a.barrier_extra = inject_timeout ? 1u : 0u;  // one arrival that never comes
     OO_CUDA_TRY(cudaMemsetAsync(ctl, 0, 16, s));
     void *args[] = {&a};
     OO_CUDA_TRY(cudaLaunchCooperativeKernel((const void *)jacobi_fused_kernel, dim3(grid), dim3(512), args, 0, s));
@@ -578,7 +580,10 @@ __device__ __forceinline__ void decode_unit(const StencilArgs &a, int u, int I, 
     ie = 1 + (int)(span * (sg + 1) / a.n_seg);
 }
 
-template <int TK, int TJ, int NCW, int DC, int DP, int PPT, int MINB>
+// INJ (tests of the bounded waits only): the producer never issues its first
+// p-tile copy, so the consumers' wait for it runs out; a separate
+// instantiation, so the kernel that runs normally carries no trace of it.
+template <int TK, int TJ, int NCW, int DC, int DP, int PPT, int MINB, bool INJ>
 __global__ void __launch_bounds__((NCW + 1) * 32, MINB)
     stencil_kernel(const __grid_constant__ StencilMaps maps, const StencilArgs a) {
     using T = Tile<TK, TJ>;
@@ -633,9 +638,11 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB)
                             break;
                         }
                         const uint32_t bar = smem_u32(&full_p[slot]);
-                        mbar_expect_tx(bar, T::PBYTES);
-                        tma_load_3d(smem_u32(p_s + (size_t)slot * T::PSLOT), &maps.p, k0 - 4, j0 - 1, q,
-                                    bar, pol_p);
+                        if (!(INJ && pfill == 0)) {
+                            mbar_expect_tx(bar, T::PBYTES);
+                            tma_load_3d(smem_u32(p_s + (size_t)slot * T::PSLOT), &maps.p, k0 - 4, j0 - 1, q,
+                                        bar, pol_p);
+                        }
                         ++pfill;
                     }
                     if (q >= ib + 1) {
@@ -920,7 +927,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB)
 // variants: (TK, TJ, NCW, DC, DP, PPT, MINB)
 struct VariantInfo {
     int TK, TJ, ctas_per_sm;
-    void (*launch)(int grid, const StencilMaps &m, const StencilArgs &a, cudaStream_t s);
+    void (*launch)(int grid, const StencilMaps &m, const StencilArgs &a, cudaStream_t s, bool inject);
 };
 
 template <int TK, int TJ, int NCW, int DC, int DP, int PPT, int MINB>
@@ -931,10 +938,17 @@ struct Variant {
         return 128 + (size_t)DC * NCOEF * T::CTILE * 4 + (size_t)DP * T::PSLOT * 4 +
                2 * (DC + DP) * 8 + 32 * 8 + 16;
     }
-    static void launch(int grid, const StencilMaps &m, const StencilArgs &a, cudaStream_t s) {
-        static std::atomic<uint64_t> done{0};
-        set_smem_limit_once((const void *)stencil_kernel<TK, TJ, NCW, DC, DP, PPT, MINB>, smem_bytes(), done);
-        stencil_kernel<TK, TJ, NCW, DC, DP, PPT, MINB><<<grid, kThreads, smem_bytes(), s>>>(m, a);
+    static void launch(int grid, const StencilMaps &m, const StencilArgs &a, cudaStream_t s, bool inject) {
+        static std::atomic<uint64_t> done{0}, done_inj{0};
+        if (inject) {
+            set_smem_limit_once((const void *)stencil_kernel<TK, TJ, NCW, DC, DP, PPT, MINB, true>, smem_bytes(),
+                                done_inj);
+            stencil_kernel<TK, TJ, NCW, DC, DP, PPT, MINB, true><<<grid, kThreads, smem_bytes(), s>>>(m, a);
+        } else {
+            set_smem_limit_once((const void *)stencil_kernel<TK, TJ, NCW, DC, DP, PPT, MINB, false>, smem_bytes(),
+                                done);
+            stencil_kernel<TK, TJ, NCW, DC, DP, PPT, MINB, false><<<grid, kThreads, smem_bytes(), s>>>(m, a);
+        }
         OO_CUDA_TRY(cudaGetLastError());
     }
     static VariantInfo info() { return VariantInfo{TK, TJ, MINB, &launch}; }
@@ -1112,10 +1126,10 @@ void stencil_plan_destroy(StencilPlan *sp) {
     delete sp;
 }
 
-void launch_stencil(StencilPlan *sp, float omega, double *res_dev, cudaStream_t s) {
+void launch_stencil(StencilPlan *sp, float omega, double *res_dev, cudaStream_t s, bool inject_timeout) {
     sp->args.omega = omega;
     sp->args.res = res_dev;
-    variant(sp->variant).launch(sp->grid, sp->maps, sp->args, s);
+    variant(sp->variant).launch(sp->grid, sp->maps, sp->args, s, inject_timeout);
 }
 
 const unsigned *stencil_plan_err_ptr(const StencilPlan *sp) { return sp->args.err; }
@@ -1221,7 +1235,7 @@ extern "C" oo_status oo_stencil_noalloc_dev(oo_ctx *ctx, int I, int J, int K, in
         // the array keeps the previous call's contents: the CTA counter and
         // the error word must start at zero
         OO_CUDA_TRY(cudaMemsetAsync(sa.counter, 0, 8, c.stream));
-        vi.launch(std::min(sa.n_units, G), maps, sa, c.stream);
+        vi.launch(std::min(sa.n_units, G), maps, sa, c.stream, false);
         c.last_error.clear();
         return OO_OK;
     } catch (const Error &e) {

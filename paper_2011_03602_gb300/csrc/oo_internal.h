@@ -210,6 +210,8 @@ struct Ctx {
     std::vector<std::pair<long long, FftPlan *>> fft_plans;
     DevBuf fft_scratch, stage_a, stage_b, stage_c, gemm_scratch;
     Server *server = nullptr;
+    // fault injection armed by oo_inject_wait_timeout (one-shot; 0 = none)
+    int inject_wait = 0;
     FftPlan *fft_plan(long long n) {
         for (auto &kv : fft_plans)
             if (kv.first == n) return kv.second;
@@ -240,13 +242,17 @@ StencilPlan *stencil_plan_create_ext(const JacobiDims &d, const float *const coe
 size_t stencil_scratch_bytes(const JacobiDims &d, int num_sms);
 void stencil_plan_destroy(StencilPlan *sp);
 // One stencil sweep; the residual (FP64) lands in *res_dev.
-void launch_stencil(StencilPlan *sp, float omega, double *res_dev, cudaStream_t s);
+// inject_timeout: fault injection for tests -- the producer never issues the
+// first p-tile fill, so the consumers' bounded wait runs out (~1 s) and the
+// sweep reports an error bit instead of a result
+void launch_stencil(StencilPlan *sp, float omega, double *res_dev, cudaStream_t s, bool inject_timeout = false);
 // All iterations of the all-GPU iteration nests in one cooperative launch
 // (small grids): ctl is jacobi_fused_ctl_bytes() of device scratch.
 size_t jacobi_fused_ctl_bytes();
 bool jacobi_fused_eligible(const JacobiDims &d);
 void launch_jacobi_fused(const JacobiDims &d, const float *const coef[NCOEF], float *p, float *wrk2, float omega,
-                         int iters, double *res_dev, void *ctl, cudaStream_t s);
+                         int iters, double *res_dev, void *ctl, cudaStream_t s,
+                         bool inject_timeout = false);
 unsigned jacobi_fused_check(void *ctl, cudaStream_t s);
 // Device address of the plan's error word (0 = fine).
 const unsigned *stencil_plan_err_ptr(const StencilPlan *sp);

@@ -164,8 +164,12 @@ void run_pattern(Ctx &c, uint64_t gene, int hoist, const oo_jacobi &prob, float 
             switch (n) {
                 case 0: launch_coef(d, dc, s); break;
                 case 1: launch_pinit(d, w.dptr(VAR_P), w.dptr(VAR_WRK2), s); break;
-                case 2:
-                    launch_stencil(w.splan, prob.omega, w.res_dev + it, s);
+                case 2: {
+                    // a fault injection armed on the context (one-shot)
+                    // applies to the next stencil sweep launched
+                    const bool inject = c.inject_wait == OO_INJECT_STENCIL_LOAD;
+                    if (inject) c.inject_wait = OO_INJECT_NONE;
+                    launch_stencil(w.splan, prob.omega, w.res_dev + it, s, inject);
                     if (!stencil_on_gpu) {
                         // a pipeline wait that ran out would repeat in every
                         // sweep: check the first one before queueing the rest
@@ -176,6 +180,7 @@ void run_pattern(Ctx &c, uint64_t gene, int hoist, const oo_jacobi &prob, float 
                     }
                     stencil_on_gpu = true;
                     break;
+                }
                 case 3: launch_copyback(d, w.dptr(VAR_P), w.dptr(VAR_WRK2), s); break;
                 case 4: launch_bc_ij(d, w.dptr(VAR_P), s); break;
                 case 5: launch_bc_k(d, w.dptr(VAR_P), s); break;
@@ -222,9 +227,18 @@ void run_pattern(Ctx &c, uint64_t gene, int hoist, const oo_jacobi &prob, float 
     }
     if (fused) {
         run_transfers(point);
-        launch_jacobi_fused(d, dc, w.dptr(VAR_P), w.dptr(VAR_WRK2), prob.omega, iters, w.res_dev, w.fused_ctl, s);
+        const bool inject = c.inject_wait == OO_INJECT_FUSED_BARRIER;
+        if (inject) c.inject_wait = OO_INJECT_NONE;
+        launch_jacobi_fused(d, dc, w.dptr(VAR_P), w.dptr(VAR_WRK2), prob.omega, iters, w.res_dev, w.fused_ctl, s,
+                            inject);
         ++launches;
         point = n_points;
+        // one launch holds every iteration, so an evaluation time limit can
+        // only judge it as a whole
+        if (abort_after_ms > 0.0) {
+            OO_CUDA_TRY(cudaStreamSynchronize(s));
+            if (ms_since(t0) > abort_after_ms) stop = true;
+        }
     }
     // N3, N4 and N5 on the GPU with no copy between them: one pass writes
     // what the three leave (interior from wrk2, faces g), instead of three

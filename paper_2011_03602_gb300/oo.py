@@ -102,6 +102,7 @@ def lib():
         "oo_status_str": (_c.c_char_p, [_c.c_int]),
         "oo_last_error": (_c.c_char_p, [_vp]),
         "oo_sync": (_c.c_int, [_vp]),
+        "oo_inject_wait_timeout": (_c.c_int, [_vp, _c.c_int]),
         "oo_load_nests": (_c.c_int, [_vp, P(oo_nest), _c.c_int, P(oo_var), _c.c_int, _u64, P(_c.c_int)]),
         "oo_load_jacobi_nests": (_c.c_int, [_vp, _c.c_int, _c.c_int, _c.c_int, _c.c_int, P(_c.c_int)]),
         "oo_transfer_plan": (_c.c_int, [_vp, _u64, _c.c_int, _c.c_int, P(oo_xfer), _c.c_int,
@@ -213,6 +214,14 @@ def oo_last_error(ctx):
 
 def oo_sync(ctx):
     _check(ctx, lib().oo_sync(ctx))
+
+
+OO_INJECT_NONE, OO_INJECT_STENCIL_LOAD, OO_INJECT_FUSED_BARRIER = 0, 1, 2
+
+
+def oo_inject_wait_timeout(ctx, what):
+    """Arm a one-shot bounded-wait failure (tests of the timeout paths)."""
+    _check(ctx, lib().oo_inject_wait_timeout(ctx, what))
 
 
 # -------------------------------------------------------------- nest table
