@@ -285,6 +285,21 @@ oo_status oo_ga_search(oo_ctx *ctx, const oo_jacobi *prob, int hoist, int pop,
                        double eval_timeout_ms, uint64_t *best_gene,
                        double *best_ms, uint64_t *history, double *gene_ms);
 
+/* oo_ga_search resumed from a saved table (checkpoint / resume): known_ms
+ * has 2^6 entries, the gene_ms output of an earlier search (or any
+ * measured times): a finite time or INFINITY is taken as that gene's
+ * measured time and the gene is not run again; NaN marks a gene still to
+ * be measured.  With the same seed and the same times the GA makes the same
+ * choices, so a search interrupted after some evaluations continues where
+ * it stopped.  A table that leaves no gene to measure needs no GPU (a
+ * host-only context, device -1, will do).  OO_EINVAL for a NULL table or a
+ * time <= 0.  Other arguments and outputs as for oo_ga_search.            */
+oo_status oo_ga_search_resume(oo_ctx *ctx, const oo_jacobi *prob, int hoist, int pop,
+                              int gens, double pc, double pm, uint64_t seed,
+                              double eval_timeout_ms, const double *known_ms,
+                              uint64_t *best_gene, double *best_ms,
+                              uint64_t *history, double *gene_ms);
+
 /* The same GA driven by a given time table time_of_gene[2^L] instead of
  * measurements (L <= 20).  No context needed.                             */
 oo_status oo_ga_table(int L, int pop, int gens, double pc, double pm,

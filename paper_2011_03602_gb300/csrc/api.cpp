@@ -270,21 +270,34 @@ oo_status oo_ga_table(int L, int pop, int gens, double pc, double pm, uint64_t s
     });
 }
 
-oo_status oo_ga_search(oo_ctx *ctx, const oo_jacobi *prob, int hoist, int pop, int gens, double pc,
-                       double pm, uint64_t seed, double eval_timeout_ms, uint64_t *best_gene,
-                       double *best_ms, uint64_t *history, double *gene_ms) {
+namespace {
+// Sec. 4.2.2 GA over measured patterns; known_ms (2^6 entries, NaN =
+// not known) seeds the per-gene memo, so a search can resume from a saved
+// table: genes with a known time are not measured again, and with the same
+// seed and times the GA makes the same choices.
+oo_status ga_search(oo_ctx *ctx, const oo_jacobi *prob, int hoist, int pop, int gens, double pc, double pm,
+                    uint64_t seed, double eval_timeout_ms, const double *known_ms, uint64_t *best_gene,
+                    double *best_ms, uint64_t *history, double *gene_ms) {
     if (!ctx || !prob) return OO_EINVAL;
     return guarded(ctx, [&] {
         OO_REQUIRE(best_gene && best_ms, OO_EINVAL, "null pointer");
-        use_device(ctx->c);
-        const Ctx::Ref &ref = cpu_reference(ctx->c, *prob);
         const int L = 6;
         std::map<uint64_t, double> memo;
-        std::vector<float> p((size_t)prob->I * prob->J * prob->K);
-        std::vector<double> res((size_t)prob->iters);
+        if (known_ms)
+            for (int g = 0; g < (1 << L); ++g)
+                if (!std::isnan(known_ms[g])) {
+                    OO_REQUIRE(known_ms[g] > 0.0, OO_EINVAL, "known times must be positive, INFINITY or NaN");
+                    memo[(uint64_t)g] = known_ms[g];
+                }
+        std::vector<float> p;
+        std::vector<double> res;
         auto measure = [&](uint64_t g) -> double {
             auto it = memo.find(g);
             if (it != memo.end()) return it->second;
+            use_device(ctx->c);
+            const Ctx::Ref &ref = cpu_reference(ctx->c, *prob);
+            p.resize((size_t)prob->I * prob->J * prob->K);
+            res.resize((size_t)prob->iters);
             oo_run_stats st{};
             bool aborted = false;
             oo_jacobi q = *prob;
@@ -311,6 +324,22 @@ oo_status oo_ga_search(oo_ctx *ctx, const oo_jacobi *prob, int hoist, int pop, i
         *best_gene = r.best_gene;
         *best_ms = r.best_time;
     });
+}
+}  // namespace
+
+oo_status oo_ga_search(oo_ctx *ctx, const oo_jacobi *prob, int hoist, int pop, int gens, double pc, double pm,
+                       uint64_t seed, double eval_timeout_ms, uint64_t *best_gene, double *best_ms,
+                       uint64_t *history, double *gene_ms) {
+    return ga_search(ctx, prob, hoist, pop, gens, pc, pm, seed, eval_timeout_ms, nullptr, best_gene, best_ms,
+                     history, gene_ms);
+}
+
+oo_status oo_ga_search_resume(oo_ctx *ctx, const oo_jacobi *prob, int hoist, int pop, int gens, double pc,
+                              double pm, uint64_t seed, double eval_timeout_ms, const double *known_ms,
+                              uint64_t *best_gene, double *best_ms, uint64_t *history, double *gene_ms) {
+    if (!known_ms) return OO_EINVAL;
+    return ga_search(ctx, prob, hoist, pop, gens, pc, pm, seed, eval_timeout_ms, known_ms, best_gene, best_ms,
+                     history, gene_ms);
 }
 
 oo_status oo_fft_c128_dev(oo_ctx *ctx, int64_t n, int batch, int dir, const double *din, double *dout) {

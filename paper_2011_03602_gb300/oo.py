@@ -116,6 +116,8 @@ def lib():
         "oo_jacobi_pitch": (_c.c_int, [_c.c_int]),
         "oo_ga_search": (_c.c_int, [_vp, P(oo_jacobi), _c.c_int, _c.c_int, _c.c_int, _dbl, _dbl, _u64,
                                     _dbl, P(_u64), P(_dbl), _vp, _vp]),
+        "oo_ga_search_resume": (_c.c_int, [_vp, P(oo_jacobi), _c.c_int, _c.c_int, _c.c_int, _dbl, _dbl, _u64,
+                                           _dbl, _vp, P(_u64), P(_dbl), _vp, _vp]),
         "oo_ga_table": (_c.c_int, [_c.c_int, _c.c_int, _c.c_int, _dbl, _dbl, _u64, _vp, _vp,
                                    P(_u64), P(_dbl)]),
         "oo_lookup_block": (_c.c_int, [_c.c_char_p, _c.c_int, P(_c.c_int)]),
@@ -317,13 +319,23 @@ def oo_ga_table(L, pop, gens, pc, pm, seed, times):
     return hist.reshape(gens, pop), bg.value, bt.value
 
 
-def oo_ga_search(ctx, prob, hoist, pop, gens, pc, pm, seed, eval_timeout_ms=0.0):
+def oo_ga_search(ctx, prob, hoist, pop, gens, pc, pm, seed, eval_timeout_ms=0.0, known_ms=None):
+    """known_ms (64 floats, NaN = not measured yet): resume from a saved
+    gene_ms table (oo_ga_search_resume)."""
     hist = np.empty(gens * pop, np.uint64)
     gene_ms = np.empty(64, np.float64)
     bg, bt = _u64(), _dbl()
-    _check(ctx, lib().oo_ga_search(ctx, _c.byref(prob), hoist, pop, gens, pc, pm, seed,
-                                   eval_timeout_ms, _c.byref(bg), _c.byref(bt),
-                                   hist.ctypes.data_as(_vp), gene_ms.ctypes.data_as(_vp)))
+    if known_ms is None:
+        st = lib().oo_ga_search(ctx, _c.byref(prob), hoist, pop, gens, pc, pm, seed, eval_timeout_ms,
+                                _c.byref(bg), _c.byref(bt), hist.ctypes.data_as(_vp), gene_ms.ctypes.data_as(_vp))
+    else:
+        known = np.ascontiguousarray(known_ms, dtype=np.float64)
+        if known.shape != (64,):
+            raise ValueError("known_ms must have 64 entries")
+        st = lib().oo_ga_search_resume(ctx, _c.byref(prob), hoist, pop, gens, pc, pm, seed, eval_timeout_ms,
+                                       known.ctypes.data_as(_vp), _c.byref(bg), _c.byref(bt),
+                                       hist.ctypes.data_as(_vp), gene_ms.ctypes.data_as(_vp))
+    _check(ctx, st)
     return {"best_gene": bg.value, "best_ms": bt.value, "history": hist.reshape(gens, pop),
             "gene_ms": gene_ms}
 

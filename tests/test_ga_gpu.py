@@ -59,3 +59,24 @@ def test_ga_after_function_block_trial(oo_mod):
         assert np.isfinite(r["best_ms"])
     finally:
         oo.oo_destroy(ctx)
+
+
+def test_ga_resumes_from_a_saved_table(oo_mod):
+    """Checkpoint / resume: a search stopped after 3 generations and resumed
+    with its saved table for 6 makes the same first 3 generations without
+    measuring those genes again, and every gene it visits has a time."""
+    oo = oo_mod
+    ctx = oo.oo_create(0)
+    try:
+        prob = oo.jacobi(33, 33, 65, 8)
+        first = oo.oo_ga_search(ctx, prob, 1, 8, 3, 0.9, 0.05, 19)
+        seen = set(int(g) for g in first["history"].reshape(-1))
+        saved = np.array([first["gene_ms"][g] if g in seen else np.nan for g in range(64)])
+        full = oo.oo_ga_search(ctx, prob, 1, 8, 6, 0.9, 0.05, 19, known_ms=saved)
+        assert np.array_equal(full["history"][:3], first["history"])
+        for g in seen:
+            assert full["gene_ms"][g] == saved[g]
+        for g in set(int(x) for x in full["history"].reshape(-1)):
+            assert np.isfinite(full["gene_ms"][g])
+    finally:
+        oo.oo_destroy(ctx)
