@@ -360,9 +360,10 @@ def run_gpu(args):
     peak, peak_src = load_peaks()
     achieved = STENCIL_BYTES / (stencil_ms * 1e-3) / 1e9
 
-    # ---- end to end through the C ABI with host buffers
-    p_host = np.empty(I * J * K, np.float32)
-    r_host = np.empty(ITERS, np.float64)
+    # ---- end to end through the C ABI with (pinned) host buffers
+    p_pin = torch.empty(I * J * K, dtype=torch.float32, pin_memory=True)
+    r_pin = torch.empty(ITERS, dtype=torch.float64, pin_memory=True)
+    p_host, r_host = p_pin.numpy(), r_pin.numpy()
     oo.oo_run_pattern(ctx, GENE, HOIST, prob, p_host, r_host)
     barrier()
     t0 = time.perf_counter()
