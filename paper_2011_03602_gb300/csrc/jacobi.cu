@@ -761,6 +761,10 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB)
                     Sc[e] = s6[e + 1];
                 }
             }
+            // unrolled by two: the compiler renames the plane windows instead
+            // of moving them every plane (0.8 % faster at 257 x 257 x 513;
+            // by three is slower)
+#pragma unroll 2
             for (int i = ib; ok && i < ie; ++i) {
                 const uint32_t sprev = pbase + (uint32_t)(i - ib);
                 const uint32_t snext = sprev + 2;
