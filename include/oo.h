@@ -474,9 +474,10 @@ oo_status oo_serve_stop(oo_ctx *ctx);
 /* Many GEMM and FFT requests of uneven sizes, on caller-owned device buffers.
  *   GEMM (kind OO_BLOCK_GEMM): C (m x n) = A (m x k) B (k x n), row-major,
  *        contiguous (leading dimensions k, n, n); in0 = A, in1 = B, out = C;
- *        prec must be OO_PREC_SPLIT3_BF16 (the grouped tensor-core kernel
- *        implements that pattern; FP64-equivalent products go through
- *        oo_gemm_f64_dev or the serving loop).
+ *        prec OO_PREC_SPLIT3_BF16 (all such requests share the grouped
+ *        tensor-core kernel) or OO_PREC_FP64EQ (m, n, k <= 65536; one
+ *        FP64-equivalent launch per request, in the same stream and graph,
+ *        with its own part of a scratch arena the batch allocates).
  *   FFT  (kind OO_BLOCK_FFT): length n = 2^e (e <= 24), in0 = x, out = X
  *        (interleaved complex128, 16-byte aligned), dir -1 / +1; m, k unused.
  * oo_batch_create builds the grouped plan once (tensor maps, split-operand
@@ -493,16 +494,18 @@ typedef struct {
 } oo_req;
 typedef struct oo_batch oo_batch;
 oo_status oo_batch_create(oo_ctx *ctx, const oo_req *reqs, int n_req, oo_batch **out);
-/* mode 0: grouped persistent kernels (GEMM split pass + one tensor-core
- *         kernel over every tile; FFT maxima pass + two item passes), the
- *         GEMM and FFT groups on forked streams;
+/* mode 0: grouped persistent kernels (GEMM split passes + one tensor-core
+ *         kernel over every split-BF16 tile, then the FP64-equivalent
+ *         launches; FFT maxima pass + three item launches), the GEMM and
+ *         FFT groups on forked streams;
  * mode 1: the same, captured into a CUDA graph on first use and replayed;
  * mode 2: one library call per request (oo_gemm_f64_dev / oo_fft_c128_dev).
  * Asynchronous on the context's stream.                                  */
 oo_status oo_batch_run(oo_batch *b, int mode);
 /* Synchronise; OO_ETIMEOUT if a bounded wait in a grouped kernel ran out. */
 oo_status oo_batch_check(oo_batch *b);
-/* Totals of the batch: 2 m n k summed over GEMMs, points summed over FFTs. */
+/* Totals of the batch: 2 m n k summed over GEMMs (both patterns), points
+ * summed over FFTs. */
 oo_status oo_batch_info(const oo_batch *b, double *gemm_flops, double *fft_points, int *n_gemm,
                         int *n_fft);
 void oo_batch_destroy(oo_batch *b);

@@ -157,3 +157,47 @@ def test_full_size_batch_sampled(oo_mod):
             assert np.linalg.norm(X - ref) <= 1e-12 * np.linalg.norm(ref), j
     finally:
         oo_mod.oo_destroy(ctx)
+
+
+def test_fp64_equivalent_requests_in_a_batch(oo_mod):
+    """Both precision patterns in one batch: FP64-equivalent requests give
+    exactly what oo_gemm_f64_dev gives for them alone (grouped, graph and
+    per-call modes alike) and meet the 1e-12 bound; the split-BF16 requests
+    around them are unaffected."""
+    oo = oo_mod
+    ctx = oo.oo_create(0)
+    try:
+        reqs, host = make_requests(17, 10, 6, gemm_range=(1, 260))
+        eq = [i for i in range(10) if i % 3 != 1]
+        for i in eq:
+            reqs[i]["prec"] = oo.OO_PREC_FP64EQ
+        alone = {}
+        for i in range(10):
+            r = reqs[i]
+            C = torch.empty_like(r["C"])
+            oo.oo_gemm_f64_dev(ctx, r["m"], r["n"], r["k"], r["A"], r["k"], r["B"], r["n"], C, r["n"],
+                               prec=r.get("prec", oo.OO_PREC_SPLIT3_BF16))
+            oo.oo_gemm_check(ctx, r["m"], r["n"], r["k"])
+            alone[i] = C.cpu().numpy()
+        b = oo.oo_batch_create(ctx, reqs)
+        try:
+            info = oo.oo_batch_info(b)
+            assert info["n_gemm"] == 10
+            assert info["gemm_flops"] == sum(2.0 * r["m"] * r["n"] * r["k"] for r in reqs[:10])
+            for mode in (0, 1, 2, 1):
+                for r in reqs:
+                    (r["C"] if r["kind"] == "gemm" else r["X"]).fill_(np.nan)
+                oo.oo_batch_run(ctx, b, mode)
+                oo.oo_batch_check(ctx, b)
+                out = outputs(reqs)
+                for i in range(10):
+                    assert np.array_equal(out[i], alone[i]), (mode, i)
+        finally:
+            oo.oo_batch_destroy(b)
+        for i in eq:
+            A, B = host[i]
+            ref = oracle.gemm(A, B)
+            err = np.max(np.abs(alone[i] - ref) / np.maximum(np.abs(A) @ np.abs(B), 1e-300))
+            assert err <= 1e-12, (i, err)
+    finally:
+        oo.oo_destroy(ctx)
