@@ -49,18 +49,6 @@ using ff::two_prod;
 using ff::two_sum;
 // (H, L) += (th, tl)
 __device__ __forceinline__ void ff_acc(float &H, float &L, float th, float tl) { ff::acc(H, L, th, tl); }
-// b * (q1 - q2 - q3 + q4) as a float-float product term
-__device__ __forceinline__ void ff_cross(float b, float q1, float q2, float q3, float q4,
-                                         float &th, float &tl) {
-    float d1, e1, d2, e2, xh, e3;
-    two_sum(q1, -q2, d1, e1);
-    two_sum(q4, -q3, d2, e2);
-    two_sum(d1, d2, xh, e3);
-    const float xl = __fadd_rn(__fadd_rn(e1, e2), e3);
-    float t1;
-    two_prod(b, xh, th, t1);
-    tl = __fmaf_rn(b, xl, t1);
-}
 
 // -------- mbarrier / TMA (inline PTX)
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {

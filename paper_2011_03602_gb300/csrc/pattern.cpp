@@ -245,7 +245,7 @@ void run_pattern(Ctx &c, uint64_t gene, int hoist, const oo_jacobi &prob, float 
     // launches; per-nest timing keeps them apart
     std::vector<char> xfer_at((size_t)n_points + 1, 0);
     for (const auto &x : plan)
-        if (x.point <= (uint32_t)n_points) xfer_at[x.point] = 1;
+        if (x.point >= 0 && x.point <= n_points) xfer_at[x.point] = 1;
     const bool tail_on_gpu = !timing && gpu[3] && gpu[4] && gpu[5];
     for (int it = 0; it < iters && !stop && !fused; ++it) {
         for (int n = 2; n < 6; ++n) {
