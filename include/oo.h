@@ -253,6 +253,20 @@ oo_status oo_stencil_noalloc_dev(oo_ctx *ctx, int I, int J, int K, int pitch,
                                  const float *const *coef, const float *p, float omega,
                                  float *wrk2, double *res_dev);
 
+/* Tile-shape autotuner for the stencil nest: times each of the
+ * OO_STENCIL_VARIANTS tile variants (tile shape, consumer warps, points per
+ * thread, CTAs per SM) for an I x J x K grid on the context's workspace (one
+ * warm-up and three timed sweeps each, CUDA events on the context's
+ * stream), and keeps the fastest for that grid: every later pattern run of
+ * the context on that grid uses it.  All variants compute bit-identical
+ * results, so tuning changes speed only.  Outputs the chosen variant and,
+ * if ms_per_variant is not NULL, the mean sweep time of each variant
+ * (OO_STENCIL_VARIANTS entries).  Without tuning a grid uses the default
+ * rule (variant 1 when K - 1 > 64, else 4), which is the tuner's choice at
+ * the benchmarked sizes.  Synchronous.                                     */
+enum { OO_STENCIL_VARIANTS = 5 };
+oo_status oo_tune_stencil(oo_ctx *ctx, int I, int J, int K, int *variant, double *ms_per_variant);
+
 /* Fault injection for tests of the bounded device waits; nothing faults,
  * traps or hangs.  Arms a one-shot failure on the context:
  *   OO_INJECT_STENCIL_LOAD  the next stencil sweep launched by

@@ -154,6 +154,17 @@ oo_status oo_sync(oo_ctx *ctx) {
     });
 }
 
+oo_status oo_tune_stencil(oo_ctx *ctx, int I, int J, int K, int *variant, double *ms_per_variant) {
+    if (!ctx) return OO_EINVAL;
+    return guarded(ctx, [&] {
+        OO_REQUIRE(I >= 3 && J >= 3 && K >= 3 && K <= 4096 && (long long)I * J * K < (1ll << 31), OO_EINVAL,
+                   "bad grid");
+        use_device(ctx->c);
+        const int v = tune_stencil(ctx->c, I, J, K, ms_per_variant);
+        if (variant) *variant = v;
+    });
+}
+
 oo_status oo_inject_wait_timeout(oo_ctx *ctx, int what) {
     if (!ctx) return OO_EINVAL;
     return guarded(ctx, [&] {

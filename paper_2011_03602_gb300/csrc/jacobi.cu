@@ -995,7 +995,7 @@ void make_map(CUtensorMap *m, const float *base, const JacobiDims &d, uint32_t b
 
 struct StencilPlan {
     JacobiDims d{};
-    int variant = 0;
+    int variant = -1;  // tile variant; -1 on creation: the default rule picks
     int TK = 128, TJ = 8;
     StencilMaps maps;
     StencilArgs args{};
@@ -1010,9 +1010,9 @@ void fill_stencil_plan(StencilPlan *sp, const JacobiDims &d, const float *const 
                        float *wrk2, int num_sms) {
     sp->d = d;
     // default tile shape by row length (16 consumer warps x 2 points measured
-    // ~0.6 % faster than 8 x 4 at 257 x 257 x 513); OO_STENCIL_VARIANT
-    // overrides (tuning sweeps)
-    sp->variant = d.K - 1 > 64 ? 1 : 4;
+    // ~0.6 % faster than 8 x 4 at 257 x 257 x 513) unless the caller chose
+    // one (a tuned choice); OO_STENCIL_VARIANT overrides both (sweeps)
+    if (sp->variant < 0 || sp->variant >= kNumVariants) sp->variant = d.K - 1 > 64 ? 1 : 4;
     if (const char *ev = std::getenv("OO_STENCIL_VARIANT")) {
         const int v = std::atoi(ev);
         if (v >= 0 && v < kNumVariants) sp->variant = v;
@@ -1092,11 +1092,12 @@ StencilPlan *stencil_plan_create_ext(const JacobiDims &d, const float *const coe
 }
 
 StencilPlan *stencil_plan_create(const JacobiDims &d, const float *const coef[NCOEF], const float *p,
-                                 float *wrk2, int num_sms) {
+                                 float *wrk2, int num_sms, int variant) {
     OO_REQUIRE(d.I >= 3 && d.J >= 3 && d.K >= 3, OO_EINVAL, "grid must be at least 3 x 3 x 3");
     OO_REQUIRE(d.pitch >= d.K && d.pitch % 4 == 0, OO_EINVAL, "pitch must be >= K and a multiple of 4");
     OO_REQUIRE(((uintptr_t)wrk2 & 15u) == 0, OO_EINVAL, "wrk2 must be 16-byte aligned");
     auto sp = new StencilPlan();
+    sp->variant = variant;
     try {
         fill_stencil_plan(sp, d, coef, p, wrk2, num_sms);
         const size_t bytes = plan_scratch_bytes(sp);  // up to 16 consumer warps
@@ -1111,6 +1112,9 @@ StencilPlan *stencil_plan_create(const JacobiDims &d, const float *const coef[NC
     }
     return sp;
 }
+
+int stencil_plan_variant(const StencilPlan *sp) { return sp->variant; }
+int stencil_variant_count() { return kNumVariants; }
 
 void stencil_plan_destroy(StencilPlan *sp) {
     if (!sp) return;

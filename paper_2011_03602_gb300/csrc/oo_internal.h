@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <array>
 #include <atomic>
 #include <cstdint>
 #include <functional>
@@ -212,6 +213,13 @@ struct Ctx {
     Server *server = nullptr;
     // fault injection armed by oo_inject_wait_timeout (one-shot; 0 = none)
     int inject_wait = 0;
+    // stencil tile variant chosen by oo_tune_stencil per grid: {I, J, K, variant}
+    std::vector<std::array<int, 4>> stencil_choice;
+    int stencil_variant_for(int I, int J, int K) const {
+        for (const auto &x : stencil_choice)
+            if (x[0] == I && x[1] == J && x[2] == K) return x[3];
+        return -1;
+    }
     FftPlan *fft_plan(long long n) {
         for (auto &kv : fft_plans)
             if (kv.first == n) return kv.second;
@@ -233,8 +241,12 @@ void launch_copyback_faces(const JacobiDims &d, float *p, const float *wrk2, cud
 void launch_bc_ij(const JacobiDims &d, float *p, cudaStream_t s);
 void launch_bc_k(const JacobiDims &d, float *p, cudaStream_t s);
 
+// variant: tile variant to use (0 .. stencil_variant_count() - 1), or -1
+// for the default rule by row length
 StencilPlan *stencil_plan_create(const JacobiDims &d, const float *const coef[NCOEF],
-                                 const float *p, float *wrk2, int num_sms);
+                                 const float *p, float *wrk2, int num_sms, int variant = -1);
+int stencil_plan_variant(const StencilPlan *sp);
+int stencil_variant_count();
 // A plan whose scratch (partial residuals, counter, error word) lives in
 // caller-provided device memory of at least stencil_scratch_bytes(d, sms).
 StencilPlan *stencil_plan_create_ext(const JacobiDims &d, const float *const coef[NCOEF], const float *p, float *wrk2,
@@ -269,6 +281,10 @@ void host_bc_ij(const JacobiDims &d, float *p);
 void host_bc_k(const JacobiDims &d, float *p);
 
 // Pattern execution (pattern.cpp).
+// time every stencil tile variant for an I x J x K grid on the context's
+// workspace; the fastest is kept for the grid and returned (ms_out: one entry
+// per variant, may be null)
+int tune_stencil(Ctx &c, int I, int J, int K, double *ms_out);
 void run_pattern(Ctx &c, uint64_t gene, int hoist, const oo_jacobi &prob, float *p_out,
                  double *res_out, bool out_on_device, oo_run_stats *stats,
                  double abort_after_ms = 0.0, bool *aborted = nullptr);

@@ -74,7 +74,8 @@ JacobiWork *ensure_work(Ctx &c, int I, int J, int K, int iters) {
         OO_CUDA_TRY(cudaHostAlloc(&w->res_host, (size_t)w->iters_cap * 8, cudaHostAllocDefault));
         const float *coef[NCOEF];
         for (int a = 0; a < NCOEF; ++a) coef[a] = w->dptr(a);
-        w->splan = stencil_plan_create(w->d, coef, w->dptr(VAR_P), w->dptr(VAR_WRK2), c.num_sms);
+        w->splan = stencil_plan_create(w->d, coef, w->dptr(VAR_P), w->dptr(VAR_WRK2), c.num_sms,
+                                       c.stencil_variant_for(I, J, K));
         OO_CUDA_TRY(cudaMalloc(&w->fused_ctl, jacobi_fused_ctl_bytes()));
     } catch (...) {
         free_work(w);
@@ -107,6 +108,73 @@ void copy_var(JacobiWork &w, int v, int dir, int iters, cudaStream_t s) {
 }  // namespace
 
 void jacobi_work_free(JacobiWork *w) { free_work(w); }
+
+// Time every stencil tile variant on the context's workspace for this grid
+// (its arrays hold whatever the last run left; every pattern run rewrites
+// them with its setup nests, and the variants' timing does not depend on the
+// values) and keep the fastest for the grid: the workspace's plan is remade
+// with it now, and any later workspace for the grid uses it too.
+int tune_stencil(Ctx &c, int I, int J, int K, double *ms_out) {
+    JacobiWork &w = *ensure_work(c, I, J, K, 1);
+    cudaStream_t s = c.stream;
+    const float *coef[NCOEF];
+    for (int a = 0; a < NCOEF; ++a) coef[a] = w.dptr(a);
+    const int nv = stencil_variant_count();
+    OO_REQUIRE(nv == OO_STENCIL_VARIANTS, OO_ESTATE, "stencil variant table and OO_STENCIL_VARIANTS disagree");
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    OO_CUDA_TRY(cudaEventCreate(&e0));
+    OO_CUDA_TRY(cudaEventCreate(&e1));
+    int best = -1;
+    float best_ms = 0.f;
+    try {
+        for (int v = 0; v < nv; ++v) {
+            StencilPlan *sp = stencil_plan_create(w.d, coef, w.dptr(VAR_P), w.dptr(VAR_WRK2), c.num_sms, v);
+            float ms = 0.f;
+            try {
+                launch_stencil(sp, 0.8f, w.res_dev, s);  // warm-up (kernel attributes, caches)
+                const unsigned e = stencil_plan_check(sp, s);
+                OO_REQUIRE(e == 0, OO_ETIMEOUT, "stencil pipeline wait ran out while tuning variant " +
+                                                   std::to_string(v));
+                constexpr int kReps = 3;
+                OO_CUDA_TRY(cudaEventRecord(e0, s));
+                for (int r = 0; r < kReps; ++r) launch_stencil(sp, 0.8f, w.res_dev, s);
+                OO_CUDA_TRY(cudaEventRecord(e1, s));
+                OO_CUDA_TRY(cudaEventSynchronize(e1));
+                OO_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+                ms /= kReps;
+                const unsigned e2 = stencil_plan_check(sp, s);
+                OO_REQUIRE(e2 == 0, OO_ETIMEOUT, "stencil pipeline wait ran out while tuning variant " +
+                                                    std::to_string(v));
+            } catch (...) {
+                stencil_plan_destroy(sp);
+                throw;
+            }
+            stencil_plan_destroy(sp);
+            if (ms_out) ms_out[v] = ms;
+            if (best < 0 || ms < best_ms) {
+                best = v;
+                best_ms = ms;
+            }
+        }
+    } catch (...) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    bool found = false;
+    for (auto &x : c.stencil_choice)
+        if (x[0] == I && x[1] == J && x[2] == K) {
+            x[3] = best;
+            found = true;
+        }
+    if (!found) c.stencil_choice.push_back({I, J, K, best});
+    StencilPlan *np = stencil_plan_create(w.d, coef, w.dptr(VAR_P), w.dptr(VAR_WRK2), c.num_sms, best);
+    stencil_plan_destroy(w.splan);
+    w.splan = np;
+    return best;
+}
 
 void run_pattern(Ctx &c, uint64_t gene, int hoist, const oo_jacobi &prob, float *p_out,
                  double *res_out, bool out_on_device, oo_run_stats *stats, double abort_after_ms,
@@ -234,7 +302,7 @@ void run_pattern(Ctx &c, uint64_t gene, int hoist, const oo_jacobi &prob, float 
         ++launches;
         point = n_points;
         // one launch holds every iteration, so an evaluation time limit can
-        // only judge it as a whole
+        // only be measured as a whole
         if (abort_after_ms > 0.0) {
             OO_CUDA_TRY(cudaStreamSynchronize(s));
             if (ms_since(t0) > abort_after_ms) stop = true;

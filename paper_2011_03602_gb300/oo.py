@@ -103,6 +103,7 @@ def lib():
         "oo_last_error": (_c.c_char_p, [_vp]),
         "oo_sync": (_c.c_int, [_vp]),
         "oo_inject_wait_timeout": (_c.c_int, [_vp, _c.c_int]),
+        "oo_tune_stencil": (_c.c_int, [_vp, _c.c_int, _c.c_int, _c.c_int, P(_c.c_int), _vp]),
         "oo_load_nests": (_c.c_int, [_vp, P(oo_nest), _c.c_int, P(oo_var), _c.c_int, _u64, P(_c.c_int)]),
         "oo_load_jacobi_nests": (_c.c_int, [_vp, _c.c_int, _c.c_int, _c.c_int, _c.c_int, P(_c.c_int)]),
         "oo_transfer_plan": (_c.c_int, [_vp, _u64, _c.c_int, _c.c_int, P(oo_xfer), _c.c_int,
@@ -216,6 +217,18 @@ def oo_last_error(ctx):
 
 def oo_sync(ctx):
     _check(ctx, lib().oo_sync(ctx))
+
+
+OO_STENCIL_VARIANTS = 5
+
+
+def oo_tune_stencil(ctx, I, J, K):
+    """Time every stencil tile variant for the grid; the fastest is kept for
+    it.  Returns (variant, ms per variant)."""
+    v = _c.c_int()
+    ms = np.empty(OO_STENCIL_VARIANTS, np.float64)
+    _check(ctx, lib().oo_tune_stencil(ctx, I, J, K, _c.byref(v), ms.ctypes.data_as(_vp)))
+    return v.value, ms
 
 
 OO_INJECT_NONE, OO_INJECT_STENCIL_LOAD, OO_INJECT_FUSED_BARRIER = 0, 1, 2
@@ -386,7 +399,7 @@ def oo_run_program(ctx, gene, hoist, iters, body, host_vars, dev_vars):
 
 def oo_ga_program(ctx, gene_len, hoist, iters, body, host_vars, dev_vars, pop, gens, pc, pm, seed, check=None):
     """GA over the loaded program's genes (gene_len as oo_load_nests returned
-    it); check() -> bool judges the result left in the host buffers."""
+    it); check() -> bool accepts or rejects the result left in the host buffers."""
     cb = _nest_callback(body)
     ck = OO_CHECK_FN(lambda user, hv: 0 if check is None or check() else 1)
     hist = np.empty(gens * pop, np.uint64)

@@ -296,3 +296,34 @@ def test_copyback_faces_pass_equals_separate_nests(oo_mod, shape, iters, monkeyp
     assert np.array_equal(out[False][1], out[True][1])
     _, ref_p = oracle.jacobi_run(I, J, K, iters, mode=1)
     assert np.array_equal(out[False][0], ref_p.reshape(-1).astype(np.float32))
+
+
+def test_stencil_autotuner(oo_mod, monkeypatch):
+    """oo_tune_stencil times every tile variant for a grid, keeps the fastest
+    for it, and the pattern runs that follow give the same p bits as an
+    untuned context (every variant computes the same values; the residual's
+    partial sums follow the variant's work units)."""
+    monkeypatch.setenv("OO_JACOBI_FUSED", "0")  # the per-iteration kernels use the tuned plan
+    monkeypatch.delenv("OO_STENCIL_VARIANT", raising=False)
+    shape, iters = (40, 37, 140), 4
+    plain = oo_mod.oo_create(0)
+    tuned = oo_mod.oo_create(0)
+    try:
+        ref = run(oo_mod, plain, shape, iters)
+        v, ms = oo_mod.oo_tune_stencil(tuned, *shape)
+        assert 0 <= v < oo_mod.OO_STENCIL_VARIANTS
+        assert np.all(np.isfinite(ms)) and np.all(ms > 0)
+        assert ms[v] == ms.min()
+        got = run(oo_mod, tuned, shape, iters)
+        assert np.array_equal(got[0], ref[0])
+        assert np.max(np.abs(got[1] - ref[1]) / ref[1]) <= 1e-12
+        # tuning again (another grid in between) keeps working and stays exact
+        oo_mod.oo_tune_stencil(tuned, 9, 10, 131)
+        got2 = run(oo_mod, tuned, shape, iters)
+        assert np.array_equal(got2[0], ref[0])
+        with pytest.raises(oo_mod.OOError) as e:
+            oo_mod.oo_tune_stencil(tuned, 2, 10, 10)
+        assert e.value.status == oo_mod.OO_EINVAL
+    finally:
+        oo_mod.oo_destroy(plain)
+        oo_mod.oo_destroy(tuned)
