@@ -755,6 +755,7 @@ def run_serve(args):
         return dict(I=I, J=J, K=K, iters=100, p=np.empty(I * J * K, np.float32), res=np.empty(100))
 
     ctx = oo.oo_create(0)
+    tuned = {"%dx%dx%d" % g: oo.oo_tune_stencil(ctx, *g)[0] for g in grids}  # stencil tile per grid
     oo.oo_serve_start(ctx, slots=args.serve_slots, hbm_budget_bytes=args.serve_budget_gb << 30,
                       queue_cap=args.serve_queue)
     # warm-up: one of each kind
@@ -840,7 +841,7 @@ def run_serve(args):
                       "queue_cap": args.serve_queue, "window_s": window, "clients": 3},
            "served": results, "plain_one_call_per_solve": plain,
            "served_vs_plain_solves_per_s": round(results[0]["solves_per_s"] / plain["solves_per_s"], 2),
-           "failed": stats["failed"]}
+           "failed": stats["failed"], "stencil_variant_by_grid": tuned}
     print(json.dumps(out))
     return 0
 

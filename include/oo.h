@@ -258,7 +258,9 @@ oo_status oo_stencil_noalloc_dev(oo_ctx *ctx, int I, int J, int K, int pitch,
  * thread, CTAs per SM) for an I x J x K grid on the context's workspace (one
  * warm-up and three timed sweeps each, CUDA events on the context's
  * stream), and keeps the fastest for that grid: every later pattern run of
- * the context on that grid uses it.  All variants compute bit-identical
+ * the context on that grid uses it, and so do the context's served Jacobi
+ * requests (tune before oo_serve_start, not while serving).  All variants
+ * compute bit-identical
  * results, so tuning changes speed only.  Outputs the chosen variant and,
  * if ms_per_variant is not NULL, the mean sweep time of each variant
  * (OO_STENCIL_VARIANTS entries).  Without tuning a grid uses the default

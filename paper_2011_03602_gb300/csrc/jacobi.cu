@@ -1072,12 +1072,13 @@ size_t stencil_scratch_bytes(const JacobiDims &d, int num_sms) {
 }
 
 StencilPlan *stencil_plan_create_ext(const JacobiDims &d, const float *const coef[NCOEF], const float *p, float *wrk2,
-                                     int num_sms, void *scratch, size_t scratch_bytes, cudaStream_t s) {
+                                     int num_sms, void *scratch, size_t scratch_bytes, cudaStream_t s, int variant) {
     OO_REQUIRE(d.I >= 3 && d.J >= 3 && d.K >= 3, OO_EINVAL, "grid must be at least 3 x 3 x 3");
     OO_REQUIRE(d.pitch >= d.K && d.pitch % 4 == 0, OO_EINVAL, "pitch must be >= K and a multiple of 4");
     OO_REQUIRE(((uintptr_t)wrk2 & 15u) == 0 && ((uintptr_t)scratch & 15u) == 0, OO_EINVAL,
                "wrk2 and scratch must be 16-byte aligned");
     auto sp = new StencilPlan();
+    sp->variant = variant;
     try {
         fill_stencil_plan(sp, d, coef, p, wrk2, num_sms);
         OO_REQUIRE(plan_scratch_bytes(sp) <= scratch_bytes, OO_EINVAL, "stencil scratch too small");

@@ -250,7 +250,8 @@ int stencil_variant_count();
 // A plan whose scratch (partial residuals, counter, error word) lives in
 // caller-provided device memory of at least stencil_scratch_bytes(d, sms).
 StencilPlan *stencil_plan_create_ext(const JacobiDims &d, const float *const coef[NCOEF], const float *p, float *wrk2,
-                                     int num_sms, void *scratch, size_t scratch_bytes, cudaStream_t s);
+                                     int num_sms, void *scratch, size_t scratch_bytes, cudaStream_t s,
+                                     int variant = -1);
 size_t stencil_scratch_bytes(const JacobiDims &d, int num_sms);
 void stencil_plan_destroy(StencilPlan *sp);
 // One stencil sweep; the residual (FP64) lands in *res_dev.

@@ -230,8 +230,11 @@ void start(Server &S, SReq &q) {
             coefw[v] = a[v];
         }
         (void)c;
+        // a tile variant tuned for this grid on the context (oo_tune_stencil
+        // before oo_serve_start) applies here too
         q.splan = stencil_plan_create_ext(d, coef, a[VAR_P], a[VAR_WRK2], c.num_sms, scr,
-                                          stencil_scratch_bytes(d, c.num_sms), s);
+                                          stencil_scratch_bytes(d, c.num_sms), s,
+                                          c.stencil_variant_for((int)r.m, (int)r.n, (int)r.k));
         // the offload pattern with every nest on the GPU and hoisted copies:
         // nothing crosses until the final p and res
         launch_coef(d, coefw, s);
