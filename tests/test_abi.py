@@ -131,3 +131,20 @@ def test_generic_program_needs_a_device_and_a_table():
     finally:
         oo.oo_destroy(ctx)
     assert oo.oo_status_str(oo.OO_EUSER) == "nest function failed"
+
+
+def test_host_only_context_rejects_tuning_and_bad_injections():
+    """A host-only context (device -1) refuses the stencil tuner with
+    OO_ESTATE instead of touching CUDA; injection arguments are checked on
+    any context."""
+    ctx = oo.oo_create(-1)
+    try:
+        with pytest.raises(oo.OOError) as e:
+            oo.oo_tune_stencil(ctx, 9, 9, 9)
+        assert e.value.status == oo.OO_ESTATE
+        with pytest.raises(oo.OOError) as e:
+            oo.oo_inject_wait_timeout(ctx, 9)
+        assert e.value.status == oo.OO_EINVAL
+        oo.oo_inject_wait_timeout(ctx, oo.OO_INJECT_NONE)
+    finally:
+        oo.oo_destroy(ctx)
