@@ -19,9 +19,9 @@
 // (128B-swizzled, K-major) into a 3-stage ring, warp 1 allocates 512 TMEM
 // columns (two double-buffered accumulator pairs) and one of its threads
 // issues tcgen05.mma (M=128, N=128, K=16, kind::f16, BF16 x BF16 -> FP32)
-// and tcgen05.commit to release stages; warps 4-7 read finished
-// accumulators with tcgen05.ld and write FP64 C while the next tile
-// accumulates.  Every mbarrier wait is bounded.
+// and tcgen05.commit to release stages; eight epilogue warps (4-11, two per
+// TMEM lane quarter) read finished accumulators with tcgen05.ld and write
+// FP64 C while the next tile accumulates.  Every mbarrier wait is bounded.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>

@@ -7,6 +7,10 @@
 //   N3 copyback  p = wrk2 on the interior                      (copy)
 //   N4 bc_ij     Dirichlet faces i, j                          (tiny)
 //   N5 bc_k      Dirichlet faces k                             (tiny)
+// When N3, N4 and N5 all run on the GPU with no copy between them, one pass
+// (copyback_faces_kernel) writes what the three leave; on small grids with
+// every iteration nest on the GPU, one cooperative kernel runs all
+// iterations (jacobi_fused_kernel).
 //
 // Device layout: each array is I x J x pitch floats, k fastest, pitch a
 // multiple of 32 floats (128-byte rows) so every row starts on a TMA- and
@@ -19,9 +23,12 @@
 // march i through the unit with the three p planes i-1, i, i+1 resident in a
 // ring, compute the update in float-float arithmetic (error-free sums and
 // FMA products, about 44 significant bits, rounded once at the store), and
-// accumulate ss^2 in FP64.  Every unit's partial residual goes to scratch;
-// the last CTA to finish sums the partials in unit order, so the residual
-// is deterministic.  Every mbarrier wait is bounded; a wait that runs out
+// accumulate ss^2 in float-float per thread and in FP64 per warp and unit.
+// Every unit's partial residuals go to scratch; the last CTA to finish sums
+// them in unit order, so the residual is deterministic.  Five tile variants
+// (tile shape, consumer warps, points per thread, CTAs per SM) compute the
+// same values; a rule by row length picks one unless a plan is given one
+// (the autotuner, oo_tune_stencil).  Every mbarrier wait is bounded; a wait that runs out
 // sets an error word the host reads, drains the copies in flight and exits.
 #include <cuda.h>
 #include <cudaTypedefs.h>

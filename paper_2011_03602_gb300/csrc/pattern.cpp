@@ -8,6 +8,9 @@
 // after synchronising, then delivers the outputs p and res.  Host arrays are
 // the library's pinned buffers (unpadded, k fastest); device arrays use the
 // padded row pitch the kernels want; copies between the two are 2D.
+// Adjacent GPU nests with no copy between them share launches: N3 + N4 + N5
+// in one pass, and on small grids every iteration in one cooperative kernel
+// (per-nest timing keeps all nests apart).
 #include <chrono>
 #include <cmath>
 #include <cstring>
