@@ -226,10 +226,15 @@ oo_status oo_ga_program(oo_ctx *ctx, int hoist, int iters, oo_nest_fn fn, oo_che
  * aligned); coef points to 12 device pointers in the order a0 a1 a2 a3 b0
  * b1 b2 c0 c1 c2 bnd wrk1.  Writes wrk2 on the interior only and stores the
  * FP64 sum of ss^2 into *res_dev (device).  Asynchronous on the context's
- * stream.                                                                 */
+ * stream; the tile variant is the context's (OO_OPT_STENCIL_VARIANT, else
+ * the oo_tune_stencil choice for the grid, else the default rule).        */
 oo_status oo_stencil_dev(oo_ctx *ctx, int I, int J, int K, int pitch,
                          const float *const *coef, const float *p, float omega,
                          float *wrk2, double *res_dev);
+/* After oo_stencil_dev sweeps: synchronise the context's stream and report
+ * OO_ETIMEOUT if a bounded pipeline wait of the last plan's sweeps ran out
+ * (their wrk2 / residual are then incomplete); the error word is cleared. */
+oo_status oo_stencil_check(oo_ctx *ctx);
 
 /* The same stencil sweep as oo_stencil_dev, for callers that cannot
  * allocate device memory at the time they call: for example code being
@@ -243,15 +248,28 @@ oo_status oo_stencil_dev(oo_ctx *ctx, int I, int J, int K, int pitch,
  * loading the library holds until the process exits.  The first call on a
  * device looks up that array's device address (cudaGetSymbolAddress) with
  * the device current; make that first call before any stream capture.
+ * The first call looks the address up under a lock, so threads may make it
+ * together; a device reset between calls invalidates the cached address.
  * Every call shares the array and clears its counter and error word first,
  * so calls that overlap on the GPU (other streams, other contexts on the
- * same device) race and must not be issued.  Grids needing more than 65536
- * partial slots (ceil((K-1)/128) * ceil((J-2)/8) > 8192 for K > 65) are
- * rejected with OO_EINVAL.  Arguments, layout and results as for
- * oo_stencil_dev; asynchronous on the context's stream.                  */
+ * same device) race and must not be issued.  The tile variant and work
+ * split are oo_stencil_dev's (same wrk2 bits; the same residual bits while
+ * that split fits the array, else the residual is summed over fewer
+ * i-segments and agrees to about 1e-12 relative).  Grids whose tiles
+ * alone need more than 65536 partial slots (ceil((K-1)/TK) *
+ * ceil((J-2)/TJ) * consumer warps; TK x TJ = 128 x 8 with 16 warps by
+ * default for K > 65) are rejected with OO_EINVAL.  Arguments and layout as
+ * for oo_stencil_dev; asynchronous on the context's stream.  A bounded
+ * pipeline wait that runs out is reported by oo_stencil_noalloc_check, not
+ * by this call.                                                          */
 oo_status oo_stencil_noalloc_dev(oo_ctx *ctx, int I, int J, int K, int pitch,
                                  const float *const *coef, const float *p, float omega,
                                  float *wrk2, double *res_dev);
+/* Synchronise the context's stream and report OO_ETIMEOUT if a bounded
+ * pipeline wait of an oo_stencil_noalloc_dev sweep on this device ran out
+ * since the last check (that sweep's wrk2 / residual are incomplete); the
+ * word is cleared.  Allocates nothing.                                   */
+oo_status oo_stencil_noalloc_check(oo_ctx *ctx);
 
 /* Tile-shape autotuner for the stencil nest: times each of the
  * OO_STENCIL_VARIANTS tile variants (tile shape, consumer warps, points per
@@ -272,17 +290,35 @@ oo_status oo_tune_stencil(oo_ctx *ctx, int I, int J, int K, int *variant, double
 /* Fault injection for tests of the bounded device waits; nothing faults,
  * traps or hangs.  Arms a one-shot failure on the context:
  *   OO_INJECT_STENCIL_LOAD  the next stencil sweep launched by
- *                           oo_run_pattern / oo_run_pattern_dev never issues
- *                           its first p-tile copy, so the consumer warps'
- *                           bounded wait (about one second) runs out;
+ *                           oo_run_pattern / oo_run_pattern_dev /
+ *                           oo_stencil_dev / oo_stencil_noalloc_dev never
+ *                           issues its first p-tile copy, so the consumer
+ *                           warps' bounded wait (about one second) runs out;
  *   OO_INJECT_FUSED_BARRIER the next fused-iteration launch (small grids,
  *                           all iteration nests on the GPU) waits at its first
  *                           grid barrier for one block more than it launched.
  * Either kernel then sets its error word, waits (bounded) for its own copies
- * in flight and returns; the pattern call returns OO_ETIMEOUT and the
+ * in flight and returns; the pattern call (or oo_stencil_check /
+ * oo_stencil_noalloc_check after a single sweep) returns OO_ETIMEOUT and the
  * context stays usable.  OO_INJECT_NONE disarms; OO_EINVAL for other values. */
 enum { OO_INJECT_NONE = 0, OO_INJECT_STENCIL_LOAD = 1, OO_INJECT_FUSED_BARRIER = 2 };
 oo_status oo_inject_wait_timeout(oo_ctx *ctx, int what);
+
+/* Context options (per context, never read from the process environment):
+ *   OO_OPT_JACOBI_FUSED     -1 (default) fuse all iterations of the all-GPU
+ *                           iteration nests into one cooperative launch for
+ *                           grids of at most 2^20 points; 0 never; 1
+ *                           whenever the placement and copies allow it.
+ *   OO_OPT_STENCIL_VARIANT  -1 (default) the oo_tune_stencil choice for the
+ *                           grid, else the default rule; 0 ..
+ *                           OO_STENCIL_VARIANTS - 1 that tile variant for
+ *                           every stencil sweep of the context (pattern
+ *                           runs, oo_stencil_dev, oo_stencil_noalloc_dev,
+ *                           served Jacobi requests started afterwards).
+ * OO_EINVAL for an unknown option or value.                               */
+enum { OO_OPT_JACOBI_FUSED = 1, OO_OPT_STENCIL_VARIANT = 2 };
+oo_status oo_set_option(oo_ctx *ctx, int option, int value);
+oo_status oo_get_option(oo_ctx *ctx, int option, int *value);
 
 /* Device row pitch (floats) the library uses for a row of K floats. */
 int oo_jacobi_pitch(int K);
@@ -336,7 +372,9 @@ oo_status oo_lookup_block(const char *callee, int lang, int *block_id);
 
 /* Sec. 3.2.2 matrix-product block: C = A B for FP64 row-major A (m x k,
  * leading dimension lda >= k), B (k x n, ldb >= n), C (m x n, ldc >= n).
- * Inputs must be finite.  prec selects the precision pattern:
+ * An entry of C whose row of A or column of B holds a NaN or an infinity
+ * is NaN (as a compensated FP64 dot product gives it); the other entries
+ * are unaffected.  prec selects the precision pattern:
  *   OO_PREC_SPLIT3_BF16  A and B are scaled per row / column by powers of
  *                        two and split into BF16 hi + lo; C = A1 B1 +
  *                        (A1 B2 + A2 B1) on the tensor cores (FP32
@@ -382,8 +420,9 @@ oo_status oo_gemm_plan(int prec, int k, int *products, int *beta, int *levels, i
  * Butterflies run in float-float arithmetic (relative L2 error ~1e-14 for
  * normal inputs); each transform is scaled by a power of two internally, so
  * any finite input is accepted (components more than ~2^126 below the
- * transform's largest one are flushed).  Non-finite inputs give unspecified
- * output.
+ * transform's largest one are flushed).  A transform of length n >= 2 with
+ * a NaN or an infinity among its inputs gives NaN in every output component
+ * (as the FP64 definition does); n = 1 returns its input unchanged.
  * oo_fft_c128: host buffers, synchronous; in may equal out.               */
 oo_status oo_fft_c128(oo_ctx *ctx, int64_t n, int dir, const double *in, double *out);
 /* batch contiguous transforms on caller device buffers (16-byte aligned,

@@ -117,7 +117,7 @@ int oracle_fft(int64_t n, int dir, const double *in, double *out);
  * blocks (bit i = block i on the GPU; INFINITY = result failed the check or
  * not replaceable), the fastest combination, the lowest mask on ties.
  * Returns -1 on bad arguments or a NaN entry.  Parity: pinned by hand-made
- * tables (tests/test_oracle_fb.py).                                       */
+ * tables (tests/test_fb.py).                                             */
 int oracle_fb_best(int n_sites, const double *times, uint32_t *best_mask, double *best_time);
 
 #ifdef __cplusplus

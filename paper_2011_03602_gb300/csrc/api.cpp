@@ -254,16 +254,61 @@ oo_status oo_stencil_dev(oo_ctx *ctx, int I, int J, int K, int pitch, const floa
         key.push_back(reinterpret_cast<const void *>((uintptr_t)J));
         key.push_back(reinterpret_cast<const void *>((uintptr_t)K));
         key.push_back(reinterpret_cast<const void *>((uintptr_t)pitch));
+        const int want = ctx->c.stencil_variant_for(I, J, K);
+        key.push_back(reinterpret_cast<const void *>((intptr_t)want));
         if (!ctx->user_plan || ctx->user_key != key) {
             if (ctx->user_plan) {
                 OO_CUDA_TRY(cudaStreamSynchronize(ctx->c.stream));
                 stencil_plan_destroy(ctx->user_plan);
                 ctx->user_plan = nullptr;
             }
-            ctx->user_plan = stencil_plan_create(JacobiDims{I, J, K, pitch}, coef, p, wrk2, ctx->c.num_sms);
+            ctx->user_plan = stencil_plan_create(JacobiDims{I, J, K, pitch}, coef, p, wrk2, ctx->c.num_sms, want);
             ctx->user_key = key;
         }
-        launch_stencil(ctx->user_plan, omega, res_dev, ctx->c.stream);
+        const bool inject = ctx->c.inject_wait == OO_INJECT_STENCIL_LOAD;
+        if (inject) ctx->c.inject_wait = OO_INJECT_NONE;
+        launch_stencil(ctx->user_plan, omega, res_dev, ctx->c.stream, inject);
+    });
+}
+
+oo_status oo_stencil_check(oo_ctx *ctx) {
+    if (!ctx) return OO_EINVAL;
+    return guarded(ctx, [&] {
+        use_device(ctx->c);
+        OO_CUDA_TRY(cudaStreamSynchronize(ctx->c.stream));
+        if (!ctx->user_plan) return;
+        const unsigned e = stencil_plan_check(ctx->user_plan, ctx->c.stream);
+        OO_REQUIRE(e == 0, OO_ETIMEOUT, "stencil pipeline wait ran out (error bits " + std::to_string(e) +
+                                            "); wrk2 and the residual of that sweep are incomplete");
+    });
+}
+
+oo_status oo_set_option(oo_ctx *ctx, int option, int value) {
+    if (!ctx) return OO_EINVAL;
+    return guarded(ctx, [&] {
+        if (option == OO_OPT_JACOBI_FUSED) {
+            OO_REQUIRE(value >= -1 && value <= 1, OO_EINVAL, "OO_OPT_JACOBI_FUSED takes -1, 0 or 1");
+            ctx->c.opt_fused = value;
+        } else if (option == OO_OPT_STENCIL_VARIANT) {
+            OO_REQUIRE(value >= -1 && value < OO_STENCIL_VARIANTS, OO_EINVAL,
+                       "OO_OPT_STENCIL_VARIANT takes -1 or a variant below OO_STENCIL_VARIANTS");
+            ctx->c.opt_stencil_variant = value;
+        } else {
+            throw Error{OO_EINVAL, "unknown option " + std::to_string(option)};
+        }
+    });
+}
+
+oo_status oo_get_option(oo_ctx *ctx, int option, int *value) {
+    if (!ctx) return OO_EINVAL;
+    return guarded(ctx, [&] {
+        OO_REQUIRE(value, OO_EINVAL, "null pointer");
+        if (option == OO_OPT_JACOBI_FUSED)
+            *value = ctx->c.opt_fused;
+        else if (option == OO_OPT_STENCIL_VARIANT)
+            *value = ctx->c.opt_stencil_variant;
+        else
+            throw Error{OO_EINVAL, "unknown option " + std::to_string(option)};
     });
 }
 

@@ -85,6 +85,16 @@ struct FftArgs {
     const int *expo;      // per transform: biased double exponent of its largest component
 };
 
+// A transform holding a NaN or an infinity: its maximum exponent reads 0x7ff.
+// Every butterfly then sees zeros (split_scaled flushes non-finite values and
+// the scale flushes the rest) and every output component is written as NaN,
+// which is what the FP64 definition gives for any length above one.
+constexpr int kNonFiniteExpo = 0x7ff;
+__device__ __forceinline__ double2 nan2() {
+    const double q = __longlong_as_double(0x7ff8000000000000ll);
+    return make_double2(q, q);
+}
+
 __device__ __forceinline__ int scale_of(const FftArgs &a, int b) {
     const int e = a.expo[b];
     return e == 0 ? 0 : e - 1023 + 1;
@@ -315,19 +325,19 @@ __global__ void __launch_bounds__(kFftThreads, 2) fft_pass_kernel(FftArgs a) {
             const double re = widen_scaled(v.rh, v.rl, S), im = widen_scaled(v.ih, v.il, S);
             const long long idx = MODE == 0 ? (long long)tb * n + t
                                             : (long long)b * n + (c0 + c) + (long long)N1 * t;
-            reinterpret_cast<double2 *>(a.out_d)[idx] = make_double2(re, im);
+            reinterpret_cast<double2 *>(a.out_d)[idx] =
+                a.expo[tb] == kNonFiniteExpo ? nan2() : make_double2(re, im);
         }
     }
 }
 
 // largest biased exponent among the 64-bit words [x0, x1) of p (stride
-// `step` between a thread's 16-byte loads, four loads in flight per thread)
+// `step` between a thread's 16-byte loads, four loads in flight per thread);
+// kNonFiniteExpo (0x7ff, above every finite exponent) if any word is a NaN or
+// an infinity
 __device__ __forceinline__ int max_exponent(const ulonglong2 *p, long long x0, long long x1, long long step) {
     int m = 0;
-    auto ex = [](unsigned long long w) {
-        const int e = (int)((w >> 52) & 0x7ffu);
-        return e == 0x7ff ? 0x7fe : e;
-    };
+    auto ex = [](unsigned long long w) { return (int)((w >> 52) & 0x7ffu); };
     long long x = x0;
     for (; x + 3 * step < x1; x += 4 * step) {
         ulonglong2 v[4];
@@ -486,12 +496,18 @@ __global__ void __launch_bounds__(kFftThreads, 2)
                 if (c >= item.count) continue;
                 const int r = tlist[item.first + c];
                 const int S = scale_from(expo[r]) - (inv ? log2L : 0);
-                reinterpret_cast<double2 *>(reqs[r].out)[t] =
-                    make_double2(widen_scaled(v.rh, v.rl, S), widen_scaled(v.ih, v.il, S));
+                double2 y = make_double2(widen_scaled(v.rh, v.rl, S), widen_scaled(v.ih, v.il, S));
+                if (log2L == 0)  // length 1: the transform is the identity, exactly
+                    y = reinterpret_cast<const double2 *>(reqs[r].in)[0];
+                else if (expo[r] == kNonFiniteExpo)
+                    y = nan2();
+                reinterpret_cast<double2 *>(reqs[r].out)[t] = y;
             } else {
                 const int S = scale_from(expo[item.first]) - (inv ? R0.log2n : 0);
                 reinterpret_cast<double2 *>(R0.out)[(item.c0 + c) + (long long)N1 * t] =
-                    make_double2(widen_scaled(v.rh, v.rl, S), widen_scaled(v.ih, v.il, S));
+                    expo[item.first] == kNonFiniteExpo
+                        ? nan2()
+                        : make_double2(widen_scaled(v.rh, v.rl, S), widen_scaled(v.ih, v.il, S));
             }
         }
     }
@@ -583,6 +599,11 @@ void launch_fft(const FftPlan *p, int batch, int dir, const double *in, double *
     OO_REQUIRE(dir == -1 || dir == 1, OO_EINVAL, "dir must be -1 (forward) or +1 (inverse)");
     const long long n = 1ll << p->log2n;
     const bool four_step = p->log2n > 12;
+    if (n == 1) {  // the length-1 transform (either direction) is the identity, exactly
+        if (in != out)
+            OO_CUDA_TRY(cudaMemcpyAsync(out, in, (size_t)batch * 16, cudaMemcpyDeviceToDevice, s));
+        return;
+    }
     float4 *mid = reinterpret_cast<float4 *>(scratch);
     int *expo = reinterpret_cast<int *>(reinterpret_cast<char *>(scratch) +
                                         (four_step ? (size_t)n * batch * sizeof(float4) : 0));

@@ -278,7 +278,7 @@ __device__ __forceinline__ void gemm_body(const Src &src, unsigned *err) {
                             const int t2 = sub * 16 + j;
                             const int sb = __shfl_sync(0xffffffffu, ecur, t2);
                             const double v = ff::to_double(__uint_as_float(h[t2]), __uint_as_float(x[t2]));
-                            stg[lane * 16 + (j ^ (lane & 15))] = ff::scale_pow2(v, sa + sb);
+                            stg[lane * 16 + (j ^ (lane & 15))] = nan_or_scaled(v, sa + sb);
                         }
                         __syncwarp();
                         const int cl = lane & 15, col = c + sub * 16 + cl;
@@ -343,8 +343,7 @@ __global__ void col_maxexp_kernel(const double *B, long long ldb, int k, int n, 
     int mx = 0;
 #pragma unroll 8
     for (int l = r0 + threadIdx.y; l < r1; l += blockDim.y) {
-        const int ex = (int)((__double_as_longlong(B[(long long)l * ldb + col]) >> 52) & 0x7ff);
-        mx = max(mx, ex == 0x7ff ? 0x7fe : ex);
+        mx = max(mx, biased_exp_or_flag((unsigned long long)__double_as_longlong(B[(long long)l * ldb + col])));
     }
     if (mx > 0) atomicMax(e + col, mx);
 }
@@ -384,8 +383,7 @@ __device__ __forceinline__ void split_row_warp(const double *src, int k, int kp,
     int mx = 0;
 #pragma unroll 4
     for (int l = lane; l < k; l += 32) {
-        const int ex = (int)((__double_as_longlong(src[l]) >> 52) & 0x7ff);
-        mx = max(mx, ex == 0x7ff ? 0x7fe : ex);
+        mx = max(mx, biased_exp_or_flag((unsigned long long)__double_as_longlong(src[l])));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
@@ -422,10 +420,7 @@ __global__ void __launch_bounds__(256) split_rows_v2_kernel(const double *A, lon
     const double2 *src = reinterpret_cast<const double2 *>(base);
     const int k2 = k >> 1;
     int mx = 0;
-    auto ex = [](double x) {
-        const int e = (int)((__double_as_longlong(x) >> 52) & 0x7ff);
-        return e == 0x7ff ? 0x7fe : e;
-    };
+    auto ex = [](double x) { return biased_exp_or_flag((unsigned long long)__double_as_longlong(x)); };
 #pragma unroll 8
     for (int l2 = threadIdx.x; l2 < k2; l2 += 256) {
         const double2 v = src[l2];
@@ -517,10 +512,7 @@ __device__ __forceinline__ void split_cols_strip(const double *B, long long ldb,
     const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;  // 8 column pairs x 64 rows
     const int col = c0 + 2 * tx;
     const bool in0 = col < n, in1 = col + 1 < n;
-    auto ex = [](double x) {
-        const int e = (int)((__double_as_longlong(x) >> 52) & 0x7ff);
-        return e == 0x7ff ? 0x7fe : e;
-    };
+    auto ex = [](double x) { return biased_exp_or_flag((unsigned long long)__double_as_longlong(x)); };
     auto load = [&](int l) {
         double2 v = make_double2(0.0, 0.0);
         if (l < k) {
@@ -605,10 +597,7 @@ __device__ __forceinline__ void split_row_half(const double *base, int k, int kp
                                                __nv_bfloat16 *a2, int t, int bar, int *red8) {
     const double2 *src = reinterpret_cast<const double2 *>(base);
     const int k2 = k >> 1;
-    auto ex = [](double x) {
-        const int e = (int)((__double_as_longlong(x) >> 52) & 0x7ff);
-        return e == 0x7ff ? 0x7fe : e;
-    };
+    auto ex = [](double x) { return biased_exp_or_flag((unsigned long long)__double_as_longlong(x)); };
     int mx = 0;
 #pragma unroll 8
     for (int l2 = t; l2 < k2; l2 += 256) {
@@ -693,8 +682,7 @@ __global__ void colmax_b_group_kernel(const GroupSplit *gs, const int2 *jobs) {
     if (col < G.n) {
 #pragma unroll 8
         for (int l = threadIdx.y; l < G.k; l += blockDim.y) {
-            const int ex = (int)((__double_as_longlong(G.B[(long long)l * G.ldb + col]) >> 52) & 0x7ff);
-            mx = max(mx, ex == 0x7ff ? 0x7fe : ex);
+            mx = max(mx, biased_exp_or_flag((unsigned long long)__double_as_longlong(G.B[(long long)l * G.ldb + col])));
         }
     }
     __shared__ int red[8][33];

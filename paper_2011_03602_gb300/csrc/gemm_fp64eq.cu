@@ -42,7 +42,8 @@
 // FP64 C.  Sharing A_p raises the MMA work per staged byte by a third,
 // which is what bounds this kernel (operand latency, not tensor rate).
 // Every mbarrier wait is bounded.
-// Inputs must be finite.
+// A row of A or column of B holding a NaN or an infinity gives NaN in every
+// entry of C it meets (tc.cuh, kNonFiniteExp); other entries are unaffected.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -51,6 +52,7 @@
 
 #include "ff.cuh"
 #include "oo_internal.h"
+#include "eq_digits.cuh"
 #include "tc.cuh"
 
 namespace oo {
@@ -58,6 +60,9 @@ namespace oo {
 namespace {
 
 using namespace tc;
+using eq::digit;
+using eq::eff_exp;
+using eq::fixed_frac;
 
 constexpr int kBM = 128, kBN = 128, kBK = 64, kStages = 4;
 constexpr int kThreads = 320;              // producer, MMA issuer, 8 epilogue warps
@@ -70,24 +75,8 @@ constexpr uint32_t kIdescPair = idesc_bf16(kBM, 2 * kBN);
 constexpr uint32_t kIdescOne = idesc_bf16(kBM, kBN);
 constexpr unsigned char kNone = 0xff;
 
-struct EqShape {
-    int beta, levels, slices, kb, nkb, nprod;
-};
-
-EqShape eq_shape(int k) {
-    EqShape e{};
-    const int kp = (k + kBK - 1) / kBK * kBK;
-    e.kb = std::min(kp, 1024);
-    e.beta = e.kb <= 256 ? 8 : 7;
-    // smallest L with 4 (L + 2) 2^(-beta (L - 1)) <= 2^-42
-    int L = 2;
-    while (std::log2(4.0 * (L + 2)) - e.beta * (L - 1) > -42.0) ++L;
-    e.levels = L;
-    e.slices = L - 1;
-    e.nkb = (kp + e.kb - 1) / e.kb;
-    e.nprod = L * (L - 1) / 2;
-    return e;
-}
+using EqShape = eq::Shape;
+EqShape eq_shape(int k) { return eq::shape(eq::kSchemePairs, k); }
 
 // A unit: slice p of A against slices q1 and q2 (q2 = kNone: alone) of B
 struct EqUnit {
@@ -305,7 +294,7 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_fp64eq_kernel(const __grid_c
                     for (int j = 0; j < 64; ++j) {
                         const int sb = __shfl_sync(0xffffffffu, j < 32 ? e0 : e1, j & 31);
                         if (row_ok && c0 + j < a.n)
-                            crow[j] = ff::scale_pow2(ff::to_double(Sh[j], Sl[j]), sa + sb);
+                            crow[j] = nan_or_scaled(ff::to_double(Sh[j], Sl[j]), sa + sb);
                     }
                 }
             }
@@ -329,42 +318,6 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_fp64eq_kernel(const __grid_c
 }
 
 // ------------------------------------------------------------ splitting
-// Exponent field used for the scale: subnormals count as exponent 1, zero
-// as 0 (no contribution).
-__device__ __forceinline__ int eff_exp(double x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const int e = (int)((b >> 52) & 0x7ff);
-    if (e != 0) return e == 0x7ff ? 0x7fe : e;
-    return (b & 0x000fffffffffffffull) ? 1 : 0;
-}
-
-// |x| * 2^(64 - E) as a 64-bit fixed-point fraction (truncated), where
-// 2^E = 2^(mx - 1022) bounds the row / column; the sign separately.
-__device__ __forceinline__ unsigned long long fixed_frac(double x, int mx, unsigned &neg) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    neg = (unsigned)(b >> 63);
-    int e = (int)((b >> 52) & 0x7ff);
-    unsigned long long m = b & 0x000fffffffffffffull;
-    if (e == 0) {
-        if (m == 0) return 0ull;
-        e = 1;
-    } else {
-        m |= 1ull << 52;
-    }
-    // x = m 2^(e - 1075), X = x 2^(64 - (mx - 1022)) = m 2^(e - mx + 11)
-    const int sh = e - mx + 11;
-    if (sh >= 0) return m << sh;  // sh <= 11: m < 2^53 keeps X < 2^64
-    if (sh <= -64) return 0ull;
-    return m >> (-sh);
-}
-
-// digit p (0-based) of X as a signed BF16 integer
-__device__ __forceinline__ __nv_bfloat16 digit(unsigned long long X, unsigned neg, int beta, int p) {
-    const unsigned d = (unsigned)(X >> (64 - beta * (p + 1))) & ((1u << beta) - 1u);
-    const float f = __uint2float_rn(d);
-    return __float2bfloat16_rn(neg ? -f : f);
-}
-
 // A (m x k, lda) -> ea and slices As[p] (m x kp each, p < s); one warp per row
 __global__ void eq_split_rows_kernel(const double *A, long long lda, int m, int k, int kp, int beta, int s,
                                      int *ea, __nv_bfloat16 *As) {

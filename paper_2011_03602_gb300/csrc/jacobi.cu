@@ -36,6 +36,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
+#include <mutex>
 #include <type_traits>
 
 #include "ff.cuh"
@@ -480,9 +481,10 @@ __global__ void __launch_bounds__(512, 1) jacobi_fused_kernel(FusedArgs a) {
 
 size_t jacobi_fused_ctl_bytes() { return 256 + (size_t)sm_count() * 8; }
 
-bool jacobi_fused_eligible(const JacobiDims &d) {
-    if (const char *ev = std::getenv("OO_JACOBI_FUSED")) return ev[0] == '1';
+bool jacobi_fused_eligible(const JacobiDims &d, int option) {
+    if (option == 0) return false;
     const long long nall = (long long)d.I * d.J * d.K;
+    if (option == 1) return nall < (1ll << 31);
     // measured (all iteration nests, 100 iterations): fused 0.74 vs 1.17 ms at
     // 33 x 33 x 65, 2.73 vs 2.87 ms at 65 x 65 x 129, but 5.36 vs 4.83 ms at
     // 97 x 97 x 193, where the tiled kernels' bandwidth wins
@@ -925,7 +927,7 @@ __global__ void __launch_bounds__((NCW + 1) * 32, MINB)
 
 // variants: (TK, TJ, NCW, DC, DP, PPT, MINB)
 struct VariantInfo {
-    int TK, TJ, ctas_per_sm;
+    int TK, TJ, ctas_per_sm, ncw;
     void (*launch)(int grid, const StencilMaps &m, const StencilArgs &a, cudaStream_t s, bool inject);
 };
 
@@ -950,7 +952,7 @@ struct Variant {
         }
         OO_CUDA_TRY(cudaGetLastError());
     }
-    static VariantInfo info() { return VariantInfo{TK, TJ, MINB, &launch}; }
+    static VariantInfo info() { return VariantInfo{TK, TJ, MINB, NCW, &launch}; }
 };
 
 // 0: 128x8 tile, 8 consumer warps x 4 points, 1 CTA/SM
@@ -1013,17 +1015,15 @@ struct StencilPlan {
 
 namespace {
 // tensor maps, tile shape and the i-segment split of a plan (no scratch yet)
+// max_slots > 0 caps the partial-residual slots (units x consumer warps)
+// the i-segment split may use
 void fill_stencil_plan(StencilPlan *sp, const JacobiDims &d, const float *const coef[NCOEF], const float *p,
-                       float *wrk2, int num_sms) {
+                       float *wrk2, int num_sms, long long max_slots = 0) {
     sp->d = d;
     // default tile shape by row length (16 consumer warps x 2 points measured
     // ~0.6 % faster than 8 x 4 at 257 x 257 x 513) unless the caller chose
-    // one (a tuned choice); OO_STENCIL_VARIANT overrides both (sweeps)
-    if (sp->variant < 0 || sp->variant >= kNumVariants) sp->variant = d.K - 1 > 64 ? 1 : 4;
-    if (const char *ev = std::getenv("OO_STENCIL_VARIANT")) {
-        const int v = std::atoi(ev);
-        if (v >= 0 && v < kNumVariants) sp->variant = v;
-    }
+    // one (a tuned choice or the context's option)
+    if (sp->variant < 0 || sp->variant >= kNumVariants) sp->variant = stencil_default_variant(d);
     sp->TK = variant(sp->variant).TK;
     sp->TJ = variant(sp->variant).TJ;
     for (int c = 0; c < NCOEF; ++c) make_map(&sp->maps.coef[c], coef[c], d, sp->TK, sp->TJ);
@@ -1040,9 +1040,14 @@ void fill_stencil_plan(StencilPlan *sp, const JacobiDims &d, const float *const 
     // segments of the i range: balance units over one CTA per SM, with a
     // charge for the two halo planes and the prologue every unit pays
     const int G = std::max(1, num_sms * variant(sp->variant).ctas_per_sm);
+    const int ncw = variant(sp->variant).ncw;
+    OO_REQUIRE(max_slots <= 0 || (long long)cols * ncw <= max_slots, OO_EINVAL,
+               "grid too large for the static scratch: ceil((K-1)/tile_k) * ceil((J-2)/tile_j) * consumer warps "
+               "must be <= " + std::to_string(max_slots));
     double best = 1e300;
     int best_seg = 1;
     for (int ns = 1; ns <= span; ++ns) {
+        if (max_slots > 0 && (long long)cols * ns * ncw > max_slots) break;
         const int smax = (span + ns - 1) / ns;
         const long long units = (long long)cols * ns;
         const long long rounds = (units + G - 1) / G;
@@ -1123,6 +1128,7 @@ StencilPlan *stencil_plan_create(const JacobiDims &d, const float *const coef[NC
 
 int stencil_plan_variant(const StencilPlan *sp) { return sp->variant; }
 int stencil_variant_count() { return kNumVariants; }
+int stencil_default_variant(const JacobiDims &d) { return d.K - 1 > 64 ? 1 : 4; }
 
 void stencil_plan_destroy(StencilPlan *sp) {
     if (!sp) return;
@@ -1166,9 +1172,15 @@ constexpr int kMaxDevices = 64;
 // address is looked up with cudaGetSymbolAddress per device below.
 static __device__ __align__(256) unsigned char g_stencil_scratch[kStaticScratchBytes];
 
+// The device address of g_stencil_scratch on `device`, looked up once per
+// device (with that device current) under a lock, so host threads making
+// their first calls at the same time agree.  The cached address belongs to
+// the device's primary context: a device reset between calls invalidates it.
 void *static_scratch_ptr(int device) {
+    static std::mutex mu;
     static void *addr[kMaxDevices] = {nullptr};
     OO_REQUIRE(device >= 0 && device < kMaxDevices, OO_EINVAL, "device index beyond the static table");
+    std::lock_guard<std::mutex> lock(mu);
     if (!addr[device]) {
         void *p = nullptr;
         OO_CUDA_TRY(cudaGetSymbolAddress(&p, g_stencil_scratch));
@@ -1196,50 +1208,58 @@ extern "C" oo_status oo_stencil_noalloc_dev(oo_ctx *ctx, int I, int J, int K, in
         OO_REQUIRE(((uintptr_t)wrk2 & 15u) == 0, OO_EINVAL, "wrk2 must be 16-byte aligned");
         OO_REQUIRE(std::isfinite(omega), OO_EINVAL, "omega must be finite");
         OO_CUDA_TRY(cudaSetDevice(c.device));
-        const JacobiDims d{I, J, K, pitch};
-        const int v = d.K - 1 > 64 ? 0 : 4;
-        const VariantInfo &vi = variant(v);
-        const int ncw = 8;  // consumer warps per CTA in variants 0 and 4
-        StencilMaps maps;
-        for (int a = 0; a < NCOEF; ++a) make_map(&maps.coef[a], coef[a], d, vi.TK, vi.TJ);
-        make_map(&maps.p, p, d, vi.TK + 8, vi.TJ + 2);
-        StencilArgs sa{};
-        sa.I = I;
-        sa.J = J;
-        sa.K = K;
-        sa.pitch = pitch;
-        sa.n_kt = (K - 1 + vi.TK - 1) / vi.TK;
-        sa.n_jt = (J - 2 + vi.TJ - 1) / vi.TJ;
-        const long long cols = (long long)sa.n_kt * sa.n_jt;
-        OO_REQUIRE(cols * ncw <= kStaticPartials, OO_EINVAL,
-                   "grid too large for the static scratch: ceil((K-1)/tile_k) * ceil((J-2)/8) * 8 must be <= 65536");
-        const int span = I - 2;
-        const int G = std::max(1, c.num_sms * vi.ctas_per_sm);
-        double best = 1e300;
-        int best_seg = 1;
-        for (int ns = 1; ns <= span; ++ns) {
-            if (cols * ns * ncw > kStaticPartials) break;
-            const int smax = (span + ns - 1) / ns;
-            const long long rounds = (cols * ns + G - 1) / G;
-            const double cost = (double)rounds * (smax + 0.6);
-            if (cost < best - 1e-9) {
-                best = cost;
-                best_seg = ns;
-            }
-        }
-        sa.n_seg = best_seg;
-        sa.n_units = (int)(cols * best_seg);
-        sa.omega = omega;
-        sa.wrk2 = wrk2;
-        sa.res = res_dev;
+        // the plan lives on the host stack: tile variant and i-segment split
+        // as oo_stencil_dev chooses them (the context's option or tuned
+        // choice, else the default rule), the split capped at the static
+        // array's slots
+        StencilPlan sp;
+        sp.variant = c.stencil_variant_for(I, J, K);
+        fill_stencil_plan(&sp, JacobiDims{I, J, K, pitch}, coef, p, wrk2, c.num_sms, kStaticPartials);
         char *scratch = static_cast<char *>(static_scratch_ptr(c.device));
+        StencilArgs &sa = sp.args;
         sa.partials = reinterpret_cast<double *>(scratch);
         sa.counter = reinterpret_cast<unsigned *>(scratch + (size_t)kStaticPartials * 8);
         sa.err = sa.counter + 1;
+        sa.omega = omega;
+        sa.res = res_dev;
         // the array keeps the previous call's contents: the CTA counter and
         // the error word must start at zero
         OO_CUDA_TRY(cudaMemsetAsync(sa.counter, 0, 8, c.stream));
-        vi.launch(std::min(sa.n_units, G), maps, sa, c.stream, false);
+        const bool inject = c.inject_wait == OO_INJECT_STENCIL_LOAD;
+        if (inject) c.inject_wait = OO_INJECT_NONE;
+        variant(sp.variant).launch(sp.grid, sp.maps, sa, c.stream, inject);
+        OO_CUDA_TRY(cudaGetLastError());
+        c.last_error.clear();
+        return OO_OK;
+    } catch (const Error &e) {
+        c.last_error = e.msg;
+        return e.code;
+    } catch (...) {
+        c.last_error = "unknown failure";
+        return OO_ECUDA;
+    }
+}
+
+// Completion check of oo_stencil_noalloc_dev: the error word sits in the
+// static array, so reading it allocates nothing either.
+extern "C" oo_status oo_stencil_noalloc_check(oo_ctx *ctx) {
+    using namespace oo;
+    if (!ctx) return OO_EINVAL;
+    Ctx &c = ctx_state(ctx);
+    try {
+        OO_REQUIRE(c.device >= 0, OO_ESTATE, "host-only context (device -1) cannot run GPU work");
+        OO_CUDA_TRY(cudaSetDevice(c.device));
+        unsigned *err = reinterpret_cast<unsigned *>(static_cast<char *>(static_scratch_ptr(c.device)) +
+                                                     (size_t)kStaticPartials * 8) + 1;
+        unsigned e = 0;
+        OO_CUDA_TRY(cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, c.stream));
+        OO_CUDA_TRY(cudaStreamSynchronize(c.stream));
+        if (e) {
+            OO_CUDA_TRY(cudaMemsetAsync(err, 0, 4, c.stream));
+            OO_CUDA_TRY(cudaStreamSynchronize(c.stream));
+            throw Error{OO_ETIMEOUT, "stencil pipeline wait ran out (error bits " + std::to_string(e) +
+                                         "); wrk2 and the residual of that sweep are incomplete"};
+        }
         c.last_error.clear();
         return OO_OK;
     } catch (const Error &e) {

@@ -213,9 +213,16 @@ struct Ctx {
     Server *server = nullptr;
     // fault injection armed by oo_inject_wait_timeout (one-shot; 0 = none)
     int inject_wait = 0;
+    // options set by oo_set_option: OO_OPT_JACOBI_FUSED (-1 default rule,
+    // 0 never, 1 whenever the placement allows) and OO_OPT_STENCIL_VARIANT
+    // (-1 tuned choice or default rule, else that variant for every grid)
+    int opt_fused = -1;
+    int opt_stencil_variant = -1;
     // stencil tile variant chosen by oo_tune_stencil per grid: {I, J, K, variant}
     std::vector<std::array<int, 4>> stencil_choice;
+    // the variant a stencil plan for this grid should use (-1: default rule)
     int stencil_variant_for(int I, int J, int K) const {
+        if (opt_stencil_variant >= 0) return opt_stencil_variant;
         for (const auto &x : stencil_choice)
             if (x[0] == I && x[1] == J && x[2] == K) return x[3];
         return -1;
@@ -247,6 +254,8 @@ StencilPlan *stencil_plan_create(const JacobiDims &d, const float *const coef[NC
                                  const float *p, float *wrk2, int num_sms, int variant = -1);
 int stencil_plan_variant(const StencilPlan *sp);
 int stencil_variant_count();
+// the variant a plan takes when none is chosen (by row length)
+int stencil_default_variant(const JacobiDims &d);
 // A plan whose scratch (partial residuals, counter, error word) lives in
 // caller-provided device memory of at least stencil_scratch_bytes(d, sms).
 StencilPlan *stencil_plan_create_ext(const JacobiDims &d, const float *const coef[NCOEF], const float *p, float *wrk2,
@@ -262,7 +271,8 @@ void launch_stencil(StencilPlan *sp, float omega, double *res_dev, cudaStream_t 
 // All iterations of the all-GPU iteration nests in one cooperative launch
 // (small grids): ctl is jacobi_fused_ctl_bytes() of device scratch.
 size_t jacobi_fused_ctl_bytes();
-bool jacobi_fused_eligible(const JacobiDims &d);
+// option: -1 the size rule (at most 2^20 points), 0 never, 1 always
+bool jacobi_fused_eligible(const JacobiDims &d, int option);
 void launch_jacobi_fused(const JacobiDims &d, const float *const coef[NCOEF], float *p, float *wrk2, float omega,
                          int iters, double *res_dev, void *ctl, cudaStream_t s,
                          bool inject_timeout = false);

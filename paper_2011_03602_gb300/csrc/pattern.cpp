@@ -40,6 +40,19 @@ void free_work(JacobiWork *w) {
 
 JacobiWork *ensure_work(Ctx &c, int I, int J, int K, int iters) {
     JacobiWork *w = c.jw;
+    if (w && w->d.I == I && w->d.J == J && w->d.K == K) {
+        // the plan follows the context's current variant choice
+        int want = c.stencil_variant_for(I, J, K);
+        if (want < 0 || want >= stencil_variant_count()) want = stencil_default_variant(w->d);
+        if (stencil_plan_variant(w->splan) != want) {
+            OO_CUDA_TRY(cudaStreamSynchronize(c.stream));
+            const float *coef[NCOEF];
+            for (int a = 0; a < NCOEF; ++a) coef[a] = w->dptr(a);
+            StencilPlan *np = stencil_plan_create(w->d, coef, w->dptr(VAR_P), w->dptr(VAR_WRK2), c.num_sms, want);
+            stencil_plan_destroy(w->splan);
+            w->splan = np;
+        }
+    }
     if (w && w->d.I == I && w->d.J == J && w->d.K == K && w->iters_cap >= std::max(iters, 1)) return w;
     if (w && w->d.I == I && w->d.J == J && w->d.K == K) {
         // only the residual buffers are too small
@@ -291,7 +304,7 @@ void run_pattern(Ctx &c, uint64_t gene, int hoist, const oo_jacobi &prob, float 
     // launch instead of 4 x iters launches (per-nest timing keeps the
     // separate kernels).
     bool fused = false;
-    if (!timing && iters > 0 && gpu[2] && gpu[3] && gpu[4] && gpu[5] && jacobi_fused_eligible(d)) {
+    if (!timing && iters > 0 && gpu[2] && gpu[3] && gpu[4] && gpu[5] && jacobi_fused_eligible(d, c.opt_fused)) {
         fused = true;
         for (const auto &x : plan)
             if (x.point > 2 && x.point < n_points) fused = false;

@@ -13,6 +13,7 @@
 #include <cstdint>
 #include <string>
 
+#include "ff.cuh"
 #include "oo_internal.h"
 
 namespace oo {
@@ -112,6 +113,23 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t cols) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// Non-finite inputs of the matrix products.  The exponent passes over A's
+// rows and B's columns report a row / column holding a NaN or an infinity
+// as this biased exponent (above every finite one), so its scale exponent
+// is 2^20: the split then flushes every entry of that row / column to zero
+// (the products stay finite), and the epilogue writes NaN wherever the
+// row's and column's scales add up to more than any finite pair can
+// (|S| <= 1024 each).  A compensated FP64 dot product that meets an
+// infinite or NaN term gives NaN, and so does this product.
+constexpr int kNonFiniteExp = (1 << 20) + 1022;
+__device__ __forceinline__ int biased_exp_or_flag(unsigned long long bits) {
+    const int e = (int)((bits >> 52) & 0x7ff);
+    return e == 0x7ff ? kNonFiniteExp : e;
+}
+__device__ __forceinline__ double nan_or_scaled(double v, int S) {
+    return S > 4096 ? __longlong_as_double(0x7ff8000000000000ll) : ff::scale_pow2(v, S);
+}
 
 }  // namespace tc
 }  // namespace oo

@@ -114,6 +114,10 @@ def lib():
                                       _c.c_float, _vp, _vp]),
         "oo_stencil_noalloc_dev": (_c.c_int, [_vp, _c.c_int, _c.c_int, _c.c_int, _c.c_int, P(_vp), _vp,
                                               _c.c_float, _vp, _vp]),
+        "oo_stencil_check": (_c.c_int, [_vp]),
+        "oo_stencil_noalloc_check": (_c.c_int, [_vp]),
+        "oo_set_option": (_c.c_int, [_vp, _c.c_int, _c.c_int]),
+        "oo_get_option": (_c.c_int, [_vp, _c.c_int, P(_c.c_int)]),
         "oo_jacobi_pitch": (_c.c_int, [_c.c_int]),
         "oo_ga_search": (_c.c_int, [_vp, P(oo_jacobi), _c.c_int, _c.c_int, _c.c_int, _dbl, _dbl, _u64,
                                     _dbl, P(_u64), P(_dbl), _vp, _vp]),
@@ -232,6 +236,18 @@ def oo_tune_stencil(ctx, I, J, K):
 
 
 OO_INJECT_NONE, OO_INJECT_STENCIL_LOAD, OO_INJECT_FUSED_BARRIER = 0, 1, 2
+OO_OPT_JACOBI_FUSED, OO_OPT_STENCIL_VARIANT = 1, 2
+
+
+def oo_set_option(ctx, option, value):
+    """Set a per-context option (OO_OPT_JACOBI_FUSED, OO_OPT_STENCIL_VARIANT; -1 = default)."""
+    _check(ctx, lib().oo_set_option(ctx, option, value))
+
+
+def oo_get_option(ctx, option):
+    v = _c.c_int()
+    _check(ctx, lib().oo_get_option(ctx, option, _c.byref(v)))
+    return v.value
 
 
 def oo_inject_wait_timeout(ctx, what):
@@ -318,6 +334,16 @@ def oo_stencil_noalloc_dev(ctx, I, J, K, pitch, coef, p, omega, wrk2, res_dev):
     ptrs = (_vp * 12)(*[_dev_ptr(c).value for c in coef])
     _check(ctx, lib().oo_stencil_noalloc_dev(ctx, I, J, K, pitch, ptrs, _dev_ptr(p), _c.c_float(omega),
                                              _dev_ptr(wrk2), _dev_ptr(res_dev)))
+
+
+def oo_stencil_check(ctx):
+    """Synchronise; raise OOError(OO_ETIMEOUT) if an oo_stencil_dev sweep's bounded wait ran out."""
+    _check(ctx, lib().oo_stencil_check(ctx))
+
+
+def oo_stencil_noalloc_check(ctx):
+    """Synchronise; raise OOError(OO_ETIMEOUT) if an oo_stencil_noalloc_dev sweep's bounded wait ran out."""
+    _check(ctx, lib().oo_stencil_noalloc_check(ctx))
 
 
 # ---------------------------------------------------------------------- GA

@@ -148,3 +148,26 @@ def test_host_only_context_rejects_tuning_and_bad_injections():
         oo.oo_inject_wait_timeout(ctx, oo.OO_INJECT_NONE)
     finally:
         oo.oo_destroy(ctx)
+
+
+def test_context_options_host_only():
+    """Per-context options replace process-wide switches: set, read back,
+    bad options and values refused; the library reads no environment."""
+    ctx = oo.oo_create(-1)
+    try:
+        assert oo.oo_get_option(ctx, oo.OO_OPT_JACOBI_FUSED) == -1
+        assert oo.oo_get_option(ctx, oo.OO_OPT_STENCIL_VARIANT) == -1
+        oo.oo_set_option(ctx, oo.OO_OPT_JACOBI_FUSED, 0)
+        oo.oo_set_option(ctx, oo.OO_OPT_STENCIL_VARIANT, oo.OO_STENCIL_VARIANTS - 1)
+        assert oo.oo_get_option(ctx, oo.OO_OPT_JACOBI_FUSED) == 0
+        assert oo.oo_get_option(ctx, oo.OO_OPT_STENCIL_VARIANT) == oo.OO_STENCIL_VARIANTS - 1
+        for opt, val in ((oo.OO_OPT_JACOBI_FUSED, 2), (oo.OO_OPT_STENCIL_VARIANT, oo.OO_STENCIL_VARIANTS),
+                         (oo.OO_OPT_STENCIL_VARIANT, -2), (99, 0)):
+            with pytest.raises(oo.OOError) as e:
+                oo.oo_set_option(ctx, opt, val)
+            assert e.value.status == oo.OO_EINVAL
+    finally:
+        oo.oo_destroy(ctx)
+    csrc = os.path.join(ROOT, "paper_2011_03602_gb300", "csrc")
+    for f in os.listdir(csrc):
+        assert "getenv" not in open(os.path.join(csrc, f), errors="replace").read(), f

@@ -30,12 +30,12 @@ def run(oo, ctx, shape, iters):
 
 
 @pytest.mark.parametrize("what,fused", [("STENCIL_LOAD", "0"), ("FUSED_BARRIER", "1")])
-def test_wait_timeout_reported_and_context_usable(oo_mod, what, fused, monkeypatch):
+def test_wait_timeout_reported_and_context_usable(oo_mod, what, fused):
     oo = oo_mod
-    monkeypatch.setenv("OO_JACOBI_FUSED", fused)
     shape, iters = (20, 21, 70), 3
     ctx = oo.oo_create(0)
     try:
+        oo.oo_set_option(ctx, oo.OO_OPT_JACOBI_FUSED, int(fused))
         oo.oo_inject_wait_timeout(ctx, getattr(oo, "OO_INJECT_" + what))
         with pytest.raises(oo.OOError) as e:
             run(oo, ctx, shape, iters)
@@ -45,6 +45,41 @@ def test_wait_timeout_reported_and_context_usable(oo_mod, what, fused, monkeypat
         ref_res, ref_p = oracle.jacobi_run(*shape, iters, mode=1)
         assert np.array_equal(p, ref_p.reshape(-1).astype(np.float32))
         assert np.max(np.abs(res - ref_res) / ref_res) <= 1e-9
+    finally:
+        oo.oo_destroy(ctx)
+
+
+def test_single_sweep_timeout_reported(oo_mod):
+    """oo_stencil_dev on caller arrays: an injected wait time-out is reported
+    by oo_stencil_check (then cleared), and the next sweep is whole."""
+    from paper_2011_03602_gb300 import synth
+    import torch
+    oo = oo_mod
+    I, J, K = 12, 19, 140
+    pitch = oo.oo_jacobi_pitch(K)
+    ctx = oo.oo_create(0)
+    try:
+        coef = np.stack([synth.field(500 + a, (I, J, K), -1.0, 1.0) for a in range(12)])
+        p = synth.field(520, (I, J, K), 0.0, 1.0)
+
+        def pad(a):
+            t = torch.zeros((I, J, pitch), dtype=torch.float32, device="cuda")
+            t[:, :, :K] = torch.from_numpy(np.ascontiguousarray(a)).cuda()
+            return t
+        dcoef = [pad(coef[a]) for a in range(12)]
+        dp = pad(p)
+        w = torch.zeros((I, J, pitch), dtype=torch.float32, device="cuda")
+        r = torch.zeros(1, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        oo.oo_inject_wait_timeout(ctx, oo.OO_INJECT_STENCIL_LOAD)
+        oo.oo_stencil_dev(ctx, I, J, K, pitch, dcoef, dp, 0.8, w, r)
+        with pytest.raises(oo.OOError) as e:
+            oo.oo_stencil_check(ctx)
+        assert e.value.status == oo.OO_ETIMEOUT
+        oo.oo_stencil_dev(ctx, I, J, K, pitch, dcoef, dp, 0.8, w, r)
+        oo.oo_stencil_check(ctx)
+        _, r_or = oracle.stencil(coef, p.astype(np.float64), np.float32(0.8))
+        assert abs(r.item() - r_or) <= 1e-5 * abs(r_or)
     finally:
         oo.oo_destroy(ctx)
 

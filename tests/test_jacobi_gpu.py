@@ -124,17 +124,18 @@ N_VARIANTS = 5
 
 
 @pytest.mark.parametrize("variant", range(N_VARIANTS))
-def test_every_tile_variant(oo_mod, variant, monkeypatch):
+def test_every_tile_variant(oo_mod, variant):
     """Every stencil tile variant (tile shape, consumer warps, points per
-    thread, CTAs per SM; OO_STENCIL_VARIANT, read when a plan is made) against the oracle on ragged grids, and point for point
+    thread, CTAs per SM; the context option OO_OPT_STENCIL_VARIANT) against
+    the oracle on ragged grids, and point for point
     equal to the default variant: the per-point arithmetic does not depend
     on the tiling."""
     for shape in [(12, 19, 70), (6, 40, 517), (20, 21, 300), (9, 66, 131)]:
         out = {}
         for v in (variant, 1):
-            monkeypatch.setenv("OO_STENCIL_VARIANT", str(v))
             c = oo_mod.oo_create(0)
             try:
+                oo_mod.oo_set_option(c, oo_mod.OO_OPT_STENCIL_VARIANT, v)
                 out[v] = _stencil_random(oo_mod, c, shape)
             finally:
                 oo_mod.oo_destroy(c)
@@ -252,16 +253,16 @@ def test_bad_arguments(oo_mod, ctx):
 
 
 @pytest.mark.parametrize("shape,iters", [((33, 33, 65), 20), ((9, 10, 131), 5), ((65, 65, 129), 7)])
-def test_fused_iterations_equal_separate_kernels(oo_mod, shape, iters, monkeypatch):
+def test_fused_iterations_equal_separate_kernels(oo_mod, shape, iters):
     """The cooperative all-iterations kernel (small grids) against the separate
     nest kernels: p bit-identical (the same float-float arithmetic), residuals
     to summation order, both against the float-store oracle."""
     ref_res, ref_p = oracle.jacobi_run(*shape, iters, mode=1)
     out = {}
     for flag in ("1", "0"):
-        monkeypatch.setenv("OO_JACOBI_FUSED", flag)
         ctx = oo_mod.oo_create(0)
         try:
+            oo_mod.oo_set_option(ctx, oo_mod.OO_OPT_JACOBI_FUSED, int(flag))
             p, res, st = run(oo_mod, ctx, shape, iters, 63, 1)
         finally:
             oo_mod.oo_destroy(ctx)
@@ -275,14 +276,14 @@ def test_fused_iterations_equal_separate_kernels(oo_mod, shape, iters, monkeypat
 
 @pytest.mark.parametrize("shape,iters", [((3, 3, 3), 3), ((4, 4, 4), 2), ((5, 7, 5), 4), ((5, 7, 9), 3),
                                          ((9, 10, 131), 3), ((18, 66, 34), 2), ((6, 40, 517), 2)])
-def test_copyback_faces_pass_equals_separate_nests(oo_mod, shape, iters, monkeypatch):
+def test_copyback_faces_pass_equals_separate_nests(oo_mod, shape, iters):
     """N3 + N4 + N5 in one pass (all three on the GPU, no copy between them)
     against the three nest kernels (per-nest timing keeps them apart): p and
     the residuals bit-identical, and p equal to the float-store oracle."""
-    monkeypatch.setenv("OO_JACOBI_FUSED", "0")
     I, J, K = shape
     ctx = oo_mod.oo_create(0)
     try:
+        oo_mod.oo_set_option(ctx, oo_mod.OO_OPT_JACOBI_FUSED, 0)
         out = {}
         for timing in (False, True):
             p = np.empty(I * J * K, np.float32)
@@ -298,17 +299,17 @@ def test_copyback_faces_pass_equals_separate_nests(oo_mod, shape, iters, monkeyp
     assert np.array_equal(out[False][0], ref_p.reshape(-1).astype(np.float32))
 
 
-def test_stencil_autotuner(oo_mod, monkeypatch):
+def test_stencil_autotuner(oo_mod):
     """oo_tune_stencil times every tile variant for a grid, keeps the fastest
     for it, and the pattern runs that follow give the same p bits as an
     untuned context (every variant computes the same values; the residual's
     partial sums follow the variant's work units)."""
-    monkeypatch.setenv("OO_JACOBI_FUSED", "0")  # the per-iteration kernels use the tuned plan
-    monkeypatch.delenv("OO_STENCIL_VARIANT", raising=False)
     shape, iters = (40, 37, 140), 4
     plain = oo_mod.oo_create(0)
     tuned = oo_mod.oo_create(0)
     try:
+        for c in (plain, tuned):  # the per-iteration kernels use the tuned plan
+            oo_mod.oo_set_option(c, oo_mod.OO_OPT_JACOBI_FUSED, 0)
         ref = run(oo_mod, plain, shape, iters)
         v, ms = oo_mod.oo_tune_stencil(tuned, *shape)
         assert 0 <= v < oo_mod.OO_STENCIL_VARIANTS

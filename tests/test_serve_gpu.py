@@ -54,7 +54,7 @@ def alone(oo, ctx, kind, kw):
     return p, res
 
 
-def test_each_result_same_alone_and_in_the_mix(oo_mod, monkeypatch):
+def test_each_result_same_alone_and_in_the_mix(oo_mod):
     """Served Jacobi requests run the separate nest kernels; alone, a small
     grid would take the fused-iteration kernel, whose residual is summed in
     another order (p is the same either way).  So the bit-for-bit reference
@@ -65,9 +65,9 @@ def test_each_result_same_alone_and_in_the_mix(oo_mod, monkeypatch):
     ctx = oo.oo_create(0)
     try:
         fused = {i: alone(oo, ctx, k, kw) for i, (k, kw) in enumerate(mix) if k == "jacobi"}
-        monkeypatch.setenv("OO_JACOBI_FUSED", "0")
+        oo.oo_set_option(ctx, oo.OO_OPT_JACOBI_FUSED, 0)
         ref = [alone(oo, ctx, k, kw) for k, kw in mix]
-        monkeypatch.delenv("OO_JACOBI_FUSED")
+        oo.oo_set_option(ctx, oo.OO_OPT_JACOBI_FUSED, -1)
         for i, (pf, rf) in fused.items():
             assert np.array_equal(pf, ref[i][0])
             assert np.allclose(rf, ref[i][1], rtol=1e-12, atol=0)
