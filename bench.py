@@ -734,17 +734,41 @@ def run_vendor(args):
     return 0
 
 
+def _batch_errors(job):
+    """Errors of a slice of the batched requests against the oracle, in a
+    worker process: GEMM max |C - C*| / (|A||B|), FFT relative L2."""
+    import oracle
+    from paper_2011_03602_gb300 import synth
+    kind, idx, dims, out = job
+    errs = []
+    for i, d, y in zip(idx, dims, out):
+        if kind == "gemm":
+            m, n, k = d
+            A, B = synth.gemm_matrix(100 + i, m, k), synth.gemm_matrix(200000 + i, k, n)
+            errs.append(float(np.max(np.abs(y - oracle.gemm(A, B)) / (np.abs(A) @ np.abs(B)))))
+        else:
+            x = synth.complex_normal(400000 + i, 1 << d)
+            ref = oracle.fft(x, -1 if i % 2 == 0 else 1)
+            errs.append(float(np.linalg.norm(y.view(np.complex128) - ref) / np.linalg.norm(ref)))
+    return errs
+
+
 def run_batched(args):
-    """Batched uneven function blocks: 4096 split-BF16 GEMMs with m, n, k
-    log-uniform in [16, 512] and 2048 complex FFTs with lengths 2^8..2^16
-    (directions alternating), device-resident; grouped persistent kernels,
-    the same as one CUDA-graph replay, and one library call per request."""
+    """Batched uneven function blocks: 4096 GEMMs with m, n, k log-uniform
+    in [16, 512] (FP64-equivalent by default) and 2048 complex FFTs with
+    lengths 2^8..2^16 (directions alternating), device-resident; grouped
+    persistent kernels, the same as one CUDA-graph replay, and one library
+    call per request.  Every result is then checked against the oracle on
+    the host cores (worker processes)."""
+    import multiprocessing as mp
+    pool = mp.get_context("spawn").Pool(host_cores()) if not args.no_cpu_baseline else None
     import torch
     from paper_2011_03602_gb300 import oo, synth
     torch.cuda.set_device(0)
     stream = torch.cuda.Stream()
     ctx = oo.oo_create(0, stream)
     n_gemm, n_fft = args.batch_gemms, args.batch_ffts
+    prec = oo.OO_PREC_FP64EQ if args.batch_prec == "fp64eq" else oo.OO_PREC_SPLIT3_BF16
     dims = synth.log_uniform_int(4, 3 * n_gemm, 16, 512).reshape(n_gemm, 3)
     expo = 8 + np.floor(synth.uniform(5, n_fft) * 9).astype(int)
     reqs = []
@@ -752,7 +776,7 @@ def run_batched(args):
         for i, (m, n, k) in enumerate(dims.tolist()):
             A = torch.from_numpy(synth.gemm_matrix(100 + i, m, k)).to("cuda", non_blocking=False)
             B = torch.from_numpy(synth.gemm_matrix(200000 + i, k, n)).to("cuda", non_blocking=False)
-            reqs.append(dict(kind="gemm", m=m, n=n, k=k, A=A, B=B,
+            reqs.append(dict(kind="gemm", m=m, n=n, k=k, A=A, B=B, prec=prec,
                              C=torch.empty((m, n), dtype=torch.float64, device="cuda")))
         for i, e in enumerate(expo.tolist()):
             x = synth.complex_normal(400000 + i, 1 << e)
@@ -779,6 +803,26 @@ def run_batched(args):
         ms = e0.elapsed_time(e1) / args.steps
         res[names[mode]] = {"ms": round(ms, 3), "solves_per_s": round((n_gemm + n_fft) / (ms * 1e-3), 1),
                             "gemm_fp64_equiv_tflops": round(info["gemm_flops"] / (ms * 1e-3) / 1e12, 2)}
+    # outputs of the last run (the headline mode) against the oracle
+    errors = None
+    if pool is not None:
+        outs = [(r["C"] if r["kind"] == "gemm" else r["X"]).cpu().numpy() for r in reqs]
+        jobs = []
+        for s in range(0, n_gemm, 32):
+            idx = list(range(s, min(n_gemm, s + 32)))
+            jobs.append(("gemm", idx, [tuple(int(v) for v in dims[i]) for i in idx], [outs[i] for i in idx]))
+        for s in range(0, n_fft, 32):
+            idx = list(range(s, min(n_fft, s + 32)))
+            jobs.append(("fft", idx, [int(expo[i]) for i in idx], [outs[n_gemm + i] for i in idx]))
+        t0 = time.perf_counter()
+        res_e = pool.map(_batch_errors, jobs)
+        pool.close()
+        ge = [e for j, r in zip(jobs, res_e) if j[0] == "gemm" for e in r]
+        fe = [e for j, r in zip(jobs, res_e) if j[0] == "fft" for e in r]
+        errors = {"gemm_max_err_vs_oracle": max(ge), "gemm_err_metric": "max |C-C*| / (|A||B|) per result",
+                  "fft_max_rel_l2_vs_oracle": max(fe), "results_checked": len(ge) + len(fe),
+                  "oracle_seconds": round(time.perf_counter() - t0, 1), "oracle_processes": host_cores()}
+    widths = oo.oo_get_gemm_tiles(ctx).tolist()
     oo.oo_batch_destroy(b)
     oo.oo_destroy(ctx)
     headline = res.get("grouped_cuda_graph") or res.get("grouped_persistent") or res["one_call_per_request"]
@@ -787,7 +831,10 @@ def run_batched(args):
            "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
            "config": {"workload": "batched_%dgemm_logu16-512_%dfft_2e8-2e16" % (n_gemm, n_fft),
                       "gemm_flops_per_batch": info["gemm_flops"], "fft_points_per_batch": info["fft_points"],
-                      "precision": "split3_bf16 GEMM, float-float FFT"},
+                      "precision": ("fp64eq GEMM (Ozaki BF16 digit slices)" if prec == oo.OO_PREC_FP64EQ
+                                    else "split3_bf16 GEMM") + ", float-float FFT",
+                      "tile_widths_by_n_and_k_bucket": widths},
+           "errors": errors,
            "modes": res,
            "speedup_graph_vs_per_call": (round(res["one_call_per_request"]["ms"] / res["grouped_cuda_graph"]["ms"], 2)
                                          if "one_call_per_request" in res and "grouped_cuda_graph" in res else None)}
@@ -951,6 +998,7 @@ def main():
     ap.add_argument("--serve-queue", type=int, default=2048)
     ap.add_argument("--batch-gemms", type=int, default=4096)
     ap.add_argument("--batch-ffts", type=int, default=2048)
+    ap.add_argument("--batch-prec", choices=["fp64eq", "split3"], default="fp64eq")
     ap.add_argument("--batch-modes", default="2,0,1",
                     help="batched: 2 one call per request, 0 grouped kernels, 1 the grouped CUDA graph")
     ap.add_argument("--n", type=int, default=4096, help="profiling: GEMM size or FFT length")

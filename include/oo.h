@@ -388,7 +388,10 @@ oo_status oo_lookup_block(const char *callee, int lang, int *block_id);
  *                        scale; the products of slices with level p + q <= L
  *                        are formed on the tensor cores in K-blocks small
  *                        enough that FP32 accumulation is exact, and summed
- *                        in float-float before widening to FP64.  Error at
+ *                        in float-float before widening to FP64.  How the
+ *                        products share FP32 accumulators is fixed by k
+ *                        (oo_gemm_scheme), so a product gives the same bits
+ *                        alone and inside a batch.  Error at
  *                        most ~2.3e-13 of sum_l |a_il b_lj| when the entries
  *                        of each row of A and column of B are of comparable
  *                        magnitude (bound ~4 (L+2) 2^(-beta (L-1)) of
@@ -413,6 +416,41 @@ oo_status oo_gemm_check(oo_ctx *ctx, int m, int n, int k);
  * over which FP32 accumulation is exact (0 for SPLIT3).  No context needed;
  * any output pointer may be NULL.                                         */
 oo_status oo_gemm_plan(int prec, int k, int *products, int *beta, int *levels, int *k_block);
+/* How an FP64-equivalent product with inner dimension k accumulates its
+ * digit products: OO_EQ_PAIRS (one FP32 accumulator per product, products
+ * sharing an A slice paired into one MMA; k > 512) or OO_EQ_LEVELS (every
+ * product of one level p + q summed in the same accumulator, which stays
+ * exact because per_accumulator * k_block * (2^beta - 1)^2 < 2^24: 7-bit
+ * digits and 128-deep K-blocks for k <= 128, 6-bit digits and 512-deep
+ * K-blocks for k <= 512).  *per_accumulator (may be NULL) receives the
+ * most products one accumulator sums (1 for pairs, L - 1 for levels).
+ * The level schemes read fewer accumulators back, which is what bounds
+ * products with short inner dimensions.  No context needed.              */
+enum { OO_EQ_PAIRS = 0, OO_EQ_LEVELS = 1 };
+oo_status oo_gemm_scheme(int k, int *scheme, int *per_accumulator);
+
+/* Tile widths of the FP64-equivalent product in batches and in the single
+ * products of a level scheme: output tiles are 128 rows by 32, 64 or 128
+ * columns.  The width of a problem's full tiles is looked up by its n and k
+ * in a table of OO_TILE_NBUCKETS x OO_TILE_KBUCKETS entries, entry
+ * [nb * OO_TILE_KBUCKETS + kb] with nb for n <= 32, 64, 128, 256, 512 or
+ * more and kb for k <= 64, 128, 256, 512 or more; a problem's last column
+ * tile takes the narrowest width that covers it.  Widths change speed only,
+ * never a result bit.  A context starts with the library's built-in table
+ * (the autotuner's choices measured on GB300).
+ * oo_tune_gemm_tiles: the autotuner.  For every bucket it times each width
+ * on a synthetic group of products drawn in the bucket (one warm-up and
+ * three timed launches, CUDA events on the context's stream), keeps the
+ * fastest in the context's table and writes it to widths (may be NULL);
+ * ms (may be NULL) receives OO_TILE_NBUCKETS x OO_TILE_KBUCKETS x 3 mean
+ * launch times (widths 32, 64, 128).  Batches created afterwards use the
+ * table.  Synchronous; allocates device memory for the trial.
+ * oo_get_gemm_tiles / oo_set_gemm_tiles read / replace the context's table
+ * (entries 32, 64 or 128, else OO_EINVAL).                                */
+enum { OO_TILE_NBUCKETS = 6, OO_TILE_KBUCKETS = 5 };
+oo_status oo_tune_gemm_tiles(oo_ctx *ctx, int *widths, double *ms);
+oo_status oo_get_gemm_tiles(oo_ctx *ctx, int *widths);
+oo_status oo_set_gemm_tiles(oo_ctx *ctx, const int *widths);
 
 /* Sec. 3.2.2 Fourier-transform block: complex128 FFT of length n = 2^k,
  * 0 <= k <= 24, interleaved (re, im) doubles.  dir -1: forward,
@@ -530,9 +568,10 @@ oo_status oo_serve_stop(oo_ctx *ctx);
  *   GEMM (kind OO_BLOCK_GEMM): C (m x n) = A (m x k) B (k x n), row-major,
  *        contiguous (leading dimensions k, n, n); in0 = A, in1 = B, out = C;
  *        prec OO_PREC_SPLIT3_BF16 (all such requests share the grouped
- *        tensor-core kernel) or OO_PREC_FP64EQ (m, n, k <= 65536; one
- *        FP64-equivalent launch per request, in the same stream and graph,
- *        with its own part of a scratch arena the batch allocates).
+ *        split-BF16 tensor-core kernel) or OO_PREC_FP64EQ (m, n, k <=
+ *        65536; all such requests share one split launch and one grouped
+ *        FP64-equivalent tensor-core launch, with tile widths from the
+ *        context's table, oo_tune_gemm_tiles).
  *   FFT  (kind OO_BLOCK_FFT): length n = 2^e (e <= 24), in0 = x, out = X
  *        (interleaved complex128, 16-byte aligned), dir -1 / +1; m, k unused.
  * oo_batch_create builds the grouped plan once (tensor maps, split-operand
@@ -550,9 +589,10 @@ typedef struct {
 typedef struct oo_batch oo_batch;
 oo_status oo_batch_create(oo_ctx *ctx, const oo_req *reqs, int n_req, oo_batch **out);
 /* mode 0: grouped persistent kernels (GEMM split passes + one tensor-core
- *         kernel over every split-BF16 tile, then the FP64-equivalent
- *         launches; FFT maxima pass + three item launches), the GEMM and
- *         FFT groups on forked streams;
+ *         kernel over every split-BF16 tile, one split launch + one
+ *         tensor-core kernel over every FP64-equivalent tile; FFT maxima
+ *         pass + three item launches), the GEMM and FFT groups on forked
+ *         streams;
  * mode 1: the same, captured into a CUDA graph on first use and replayed;
  * mode 2: one library call per request (oo_gemm_f64_dev / oo_fft_c128_dev).
  * Asynchronous on the context's stream.                                  */

@@ -27,6 +27,7 @@ CU_FLAGS = {
     "jacobi.cu": ["-fmad=false"],
     "fft.cu": ["-fmad=false"],
     "gemm_fp64eq.cu": ["-fmad=false"],
+    "gemm_eq_group.cu": ["-fmad=false"],
 }
 CXX_FLAGS = ["-O3", "-std=c++17", "-fPIC", "-fopenmp", "-ffp-contract=off", "-Wall",
              "-I" + os.path.join(CUDA_HOME, "include"), "-I" + os.path.join(ROOT, "include")]
@@ -39,7 +40,7 @@ def _sources():
 
 
 def _headers():
-    hs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh", ".map"))]
+    hs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh", ".map", ".inc"))]
     inc = os.path.join(ROOT, "include")
     hs += [os.path.join(inc, f) for f in os.listdir(inc) if f.endswith(".h")]
     return hs

@@ -449,7 +449,8 @@ void gemm_launch(oo_ctx *ctx, int prec, int m, int n, int k, const double *dA, l
     void *scratch = ctx->c.gemm_scratch.get(gemm_scratch(prec, m, n, k));
     ctx->gemm_prec = prec;
     if (prec == OO_PREC_FP64EQ)
-        launch_gemm_fp64eq(m, n, k, dA, lda, dB, ldb, dC, ldc, scratch, s);
+        launch_gemm_fp64eq(m, n, k, dA, lda, dB, ldb, dC, ldc, scratch, s,
+                           eq_tile_width(ctx->c.eq_widths.data(), n, k));
     else
         launch_gemm_split3(m, n, k, dA, lda, dB, ldb, dC, ldc, scratch, s);
 }
@@ -535,6 +536,54 @@ oo_status oo_gemm_plan(int prec, int k, int *products, int *beta, int *levels, i
         if (beta) *beta = b;
         if (levels) *levels = l;
         if (k_block) *k_block = kb;
+    });
+}
+
+oo_status oo_gemm_scheme(int k, int *scheme, int *per_accumulator) {
+    return guarded(nullptr, [&] {
+        OO_REQUIRE(k >= 1 && k <= (1 << 21), OO_EINVAL, "k out of range");
+        const int s = eq_scheme_for(k);
+        int L = 0;
+        gemm_fp64eq_shape(k, nullptr, &L, nullptr);
+        if (scheme) *scheme = s == 0 ? OO_EQ_PAIRS : OO_EQ_LEVELS;
+        if (per_accumulator) *per_accumulator = s == 0 ? 1 : L - 1;
+    });
+}
+
+oo_status oo_get_gemm_tiles(oo_ctx *ctx, int *widths) {
+    if (!ctx) return OO_EINVAL;
+    return guarded(ctx, [&] {
+        OO_REQUIRE(widths, OO_EINVAL, "null pointer");
+        for (int nb = 0; nb < OO_TILE_NBUCKETS; ++nb)
+            for (int kb = 0; kb < OO_TILE_KBUCKETS; ++kb) {
+                const int i = nb * OO_TILE_KBUCKETS + kb;
+                widths[i] = ctx->c.eq_widths[i] ? ctx->c.eq_widths[i] : eq_default_width(nb, kb);
+            }
+    });
+}
+
+oo_status oo_set_gemm_tiles(oo_ctx *ctx, const int *widths) {
+    if (!ctx) return OO_EINVAL;
+    return guarded(ctx, [&] {
+        OO_REQUIRE(widths, OO_EINVAL, "null pointer");
+        for (int i = 0; i < OO_TILE_NBUCKETS * OO_TILE_KBUCKETS; ++i)
+            OO_REQUIRE(widths[i] == 32 || widths[i] == 64 || widths[i] == 128, OO_EINVAL,
+                       "tile widths must be 32, 64 or 128");
+        for (int i = 0; i < OO_TILE_NBUCKETS * OO_TILE_KBUCKETS; ++i) ctx->c.eq_widths[i] = widths[i];
+    });
+}
+
+oo_status oo_tune_gemm_tiles(oo_ctx *ctx, int *widths, double *ms) {
+    if (!ctx) return OO_EINVAL;
+    return guarded(ctx, [&] {
+        use_device(ctx->c);
+        tune_gemm_tiles(ctx->c, ms);
+        if (widths)
+            for (int nb = 0; nb < OO_TILE_NBUCKETS; ++nb)
+                for (int kb = 0; kb < OO_TILE_KBUCKETS; ++kb) {
+                    const int i = nb * OO_TILE_KBUCKETS + kb;
+                    widths[i] = ctx->c.eq_widths[i];
+                }
     });
 }
 

@@ -1,12 +1,11 @@
 // Batched function blocks (Sec. 3.2.2 replacements at scale): many GEMM and
 // FFT requests of uneven sizes executed as grouped persistent kernels -- the
 // split passes and one tensor-core kernel over the tiles of every
-// split-BF16 GEMM, three launches over the items of every FFT -- optionally
-// captured once into a CUDA graph with the GEMM and FFT groups on forked
-// streams, or, for comparison, as one library call per request.
-// FP64-equivalent GEMMs in a batch run as one FP64-equivalent launch each
-// (own slice of a batch-owned scratch arena) after the grouped kernel, on
-// the GEMM stream, inside the same graph.
+// split-BF16 GEMM, one split launch and one tensor-core kernel over the
+// tiles of every FP64-equivalent GEMM (tile widths from the context's
+// autotuned table), three launches over the items of every FFT --
+// optionally captured once into a CUDA graph with the GEMM and FFT groups on
+// forked streams, or, for comparison, as one library call per request.
 #include <cstring>
 
 #include "oo_internal.h"
@@ -17,10 +16,7 @@ struct oo_batch {
     std::vector<oo_req> reqs;
     oo::GemmGroup *gg = nullptr;
     oo::FftGroup *fg = nullptr;
-    // FP64-equivalent GEMMs: request index and scratch offset in eq_arena
-    std::vector<int> eq_idx;
-    std::vector<size_t> eq_off;
-    void *eq_arena = nullptr;
+    oo::EqGroup *eg = nullptr;  // every FP64-equivalent GEMM
     cudaStream_t side = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
     cudaGraph_t graph = nullptr;
@@ -41,26 +37,20 @@ void free_batch(oo_batch *b) {
     if (b->join) cudaEventDestroy(b->join);
     if (b->side) cudaStreamDestroy(b->side);
     gemm_group_destroy(b->gg);
+    eq_group_destroy(b->eg);
     fft_group_destroy(b->fg);
-    if (b->eq_arena) cudaFree(b->eq_arena);
     delete b;
 }
 
 void launch_gemms(oo_batch *b, cudaStream_t s) {
     if (b->gg) gemm_group_launch(b->gg, s);
-    char *arena = static_cast<char *>(b->eq_arena);
-    for (size_t q = 0; q < b->eq_idx.size(); ++q) {
-        const oo_req &r = b->reqs[b->eq_idx[q]];
-        launch_gemm_fp64eq((int)r.m, (int)r.n, (int)r.k, static_cast<const double *>(r.in0), r.k,
-                           static_cast<const double *>(r.in1), r.n, static_cast<double *>(r.out), r.n,
-                           arena + b->eq_off[q], s);
-    }
+    if (b->eg) eq_group_launch(b->eg, s);
 }
 
 // the grouped launches; GEMMs on the context stream, FFTs on a forked stream
 void launch_grouped(oo_batch *b) {
     cudaStream_t s = b->c->stream;
-    const bool gemms = b->gg || !b->eq_idx.empty();
+    const bool gemms = b->gg || b->eg;
     if (gemms && b->fg) {
         OO_CUDA_TRY(cudaEventRecord(b->fork, s));
         OO_CUDA_TRY(cudaStreamWaitEvent(b->side, b->fork, 0));
@@ -107,7 +97,7 @@ oo_status oo_batch_create(oo_ctx *ctx, const oo_req *reqs, int n_req, oo_batch *
         OO_REQUIRE(c.device >= 0, OO_ESTATE, "host-only context (device -1) cannot run GPU work");
         OO_CUDA_TRY(cudaSetDevice(c.device));
         b->reqs.assign(reqs, reqs + n_req);
-        std::vector<GemmDesc> gd;
+        std::vector<GemmDesc> gd, ed;
         std::vector<FftDesc> fd;
         std::vector<const FftPlan *> fp;
         for (int i = 0; i < n_req; ++i) {
@@ -122,7 +112,9 @@ oo_status oo_batch_create(oo_ctx *ctx, const oo_req *reqs, int n_req, oo_batch *
                 if (r.prec == OO_PREC_FP64EQ) {
                     OO_REQUIRE(r.m <= 65536 && r.n <= 65536 && r.k <= 65536, OO_EINVAL,
                                "FP64-equivalent GEMM dimensions above 65536 in request " + std::to_string(i));
-                    b->eq_idx.push_back(i);
+                    ed.push_back(GemmDesc{(int)r.m, (int)r.n, (int)r.k, static_cast<const double *>(r.in0), r.k,
+                                          static_cast<const double *>(r.in1), r.n, static_cast<double *>(r.out),
+                                          r.n});
                     continue;
                 }
                 gd.push_back(GemmDesc{(int)r.m, (int)r.n, (int)r.k, static_cast<const double *>(r.in0), r.k,
@@ -136,19 +128,7 @@ oo_status oo_batch_create(oo_ctx *ctx, const oo_req *reqs, int n_req, oo_batch *
             }
         }
         if (!gd.empty()) b->gg = gemm_group_create(gd, c.num_sms);
-        if (!b->eq_idx.empty()) {
-            size_t at = 0;
-            for (int i : b->eq_idx) {
-                const oo_req &r = reqs[i];
-                b->eq_off.push_back(at);
-                at += (gemm_fp64eq_scratch_bytes((int)r.m, (int)r.n, (int)r.k) + 255) / 256 * 256;
-            }
-            if (cudaMalloc(&b->eq_arena, at) != cudaSuccess) {
-                cudaGetLastError();
-                b->eq_arena = nullptr;
-                throw Error{OO_ENOMEM, "FP64-equivalent scratch of " + std::to_string(at) + " bytes"};
-            }
-        }
+        if (!ed.empty()) b->eg = eq_group_create(ed, c.num_sms, c.eq_widths.data());
         if (!fd.empty()) b->fg = fft_group_create(fd, fp, c.num_sms);
         OO_CUDA_TRY(cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking));
         OO_CUDA_TRY(cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming));
@@ -219,11 +199,10 @@ oo_status oo_batch_check(oo_batch *b) {
             const unsigned e = gemm_group_check(b->gg, b->c->stream);
             OO_REQUIRE(e == 0, OO_ETIMEOUT, "grouped GEMM pipeline wait ran out (error bits " + std::to_string(e) + ")");
         }
-        for (size_t q = 0; q < b->eq_idx.size(); ++q) {
-            const unsigned e = gemm_fp64eq_check_error(static_cast<char *>(b->eq_arena) + b->eq_off[q], b->c->stream);
+        if (b->eg) {
+            const unsigned e = eq_group_check(b->eg, b->c->stream);
             OO_REQUIRE(e == 0, OO_ETIMEOUT,
-                       "FP64-equivalent GEMM pipeline wait ran out in request " + std::to_string(b->eq_idx[q]) +
-                           " (error bits " + std::to_string(e) + ")");
+                       "grouped FP64-equivalent GEMM pipeline wait ran out (error bits " + std::to_string(e) + ")");
         }
         OO_CUDA_TRY(cudaGetLastError());
     });
@@ -233,9 +212,7 @@ oo_status oo_batch_info(const oo_batch *b, double *gemm_flops, double *fft_point
     if (!b) return OO_EINVAL;
     int ng = 0, nf = 0;
     for (const oo_req &r : b->reqs) (r.kind == OO_BLOCK_GEMM ? ng : nf)++;
-    double eq_flops = 0.0;
-    for (int i : b->eq_idx) eq_flops += 2.0 * (double)b->reqs[i].m * (double)b->reqs[i].n * (double)b->reqs[i].k;
-    if (gemm_flops) *gemm_flops = (b->gg ? gemm_group_flops(b->gg) : 0.0) + eq_flops;
+    if (gemm_flops) *gemm_flops = (b->gg ? gemm_group_flops(b->gg) : 0.0) + (b->eg ? eq_group_flops(b->eg) : 0.0);
     if (fft_points) *fft_points = b->fg ? fft_group_elements(b->fg) : 0.0;
     if (n_gemm) *n_gemm = ng;
     if (n_fft) *n_fft = nf;

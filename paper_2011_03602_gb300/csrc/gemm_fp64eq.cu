@@ -76,7 +76,10 @@ constexpr uint32_t kIdescOne = idesc_bf16(kBM, kBN);
 constexpr unsigned char kNone = 0xff;
 
 using EqShape = eq::Shape;
+// the pair scheme this file's kernel runs
 EqShape eq_shape(int k) { return eq::shape(eq::kSchemePairs, k); }
+// the scheme the library uses for inner dimension k
+EqShape eq_used_shape(int k) { return eq::shape(eq_scheme_for(k), k); }
 
 // A unit: slice p of A against slices q1 and q2 (q2 = kNone: alone) of B
 struct EqUnit {
@@ -437,7 +440,7 @@ struct EqLayout {
     size_t err, ea, eb, mxo, as, bs, total;
 };
 EqLayout eq_layout(int m, int n, int k) {
-    const EqShape e = eq_shape(k);
+    const EqShape e = eq_used_shape(k);
     const size_t kp = (size_t)(k + kBK - 1) / kBK * kBK;
     auto up = [](size_t x) { return (x + 255) / 256 * 256; };
     EqLayout L{};
@@ -455,20 +458,20 @@ EqLayout eq_layout(int m, int n, int k) {
 
 size_t gemm_fp64eq_scratch_bytes(int m, int n, int k) { return eq_layout(m, n, k).total; }
 
-int gemm_fp64eq_products(int k) { return eq_shape(k).nprod; }
+int gemm_fp64eq_products(int k) { return eq_used_shape(k).nprod; }
 
 void gemm_fp64eq_shape(int k, int *beta, int *levels, int *k_block) {
-    const EqShape e = eq_shape(k);
+    const EqShape e = eq_used_shape(k);
     if (beta) *beta = e.beta;
     if (levels) *levels = e.levels;
     if (k_block) *k_block = e.kb;
 }
 
 void launch_gemm_fp64eq(int m, int n, int k, const double *A, long long lda, const double *B, long long ldb,
-                        double *C, long long ldc, void *scratch, cudaStream_t s) {
+                        double *C, long long ldc, void *scratch, cudaStream_t s, int width) {
     OO_REQUIRE(m >= 1 && n >= 1 && k >= 1, OO_EINVAL, "m, n, k must be >= 1");
     OO_REQUIRE(lda >= k && ldb >= n && ldc >= n, OO_EINVAL, "leading dimensions too small");
-    const EqShape e = eq_shape(k);
+    const EqShape e = eq_used_shape(k);
     OO_REQUIRE((long long)e.slices * m < (1ll << 31) && (long long)e.slices * n < (1ll << 31), OO_EINVAL,
                "matrix too large for the FP64-equivalent mode");
     const int kp = (k + kBK - 1) / kBK * kBK;
@@ -501,6 +504,14 @@ void launch_gemm_fp64eq(int m, int n, int k, const double *A, long long lda, con
         eq_split_cols_t_kernel<<<grid, 256, 0, s>>>(B, ldb, k, n, kp, e.beta, e.slices, mxo, Bs);
         OO_CUDA_TRY(cudaGetLastError());
     }
+    int dev = 0, sms = 148;
+    OO_CUDA_TRY(cudaGetDevice(&dev));
+    OO_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (e.scheme != eq::kSchemePairs) {
+        // level schemes: the tiled kernel (gemm_eq_group.cu), as in batches
+        launch_gemm_eq_tiles(m, n, k, As, Bs, ea, eb, C, ldc, width, err, sms, s);
+        return;
+    }
     EqMaps maps;
     map_bf16(&maps.a, As, (long long)e.slices * m, kp, kBM);
     map_bf16(&maps.b, Bs, (long long)e.slices * n, kp, kBN);
@@ -531,9 +542,6 @@ void launch_gemm_fp64eq(int m, int n, int k, const double *A, long long lda, con
     set_smem_limit_once((const void *)gemm_fp64eq_kernel, smem_eq(), attr);
     const long long tiles = (long long)ga.m_tiles * ga.n_tiles;
     OO_REQUIRE(tiles < (1ll << 31), OO_EINVAL, "too many tiles");
-    int dev = 0, sms = 148;
-    OO_CUDA_TRY(cudaGetDevice(&dev));
-    OO_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int grid = (int)std::min<long long>(tiles, sms);
     OO_REQUIRE(grid >= 1, OO_EINVAL, "empty product");
     gemm_fp64eq_kernel<<<grid, kThreads, smem_eq(), s>>>(maps, ga);

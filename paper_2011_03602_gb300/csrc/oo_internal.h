@@ -113,11 +113,19 @@ unsigned *gemm_error_word(void *scratch, int m, int n, int k);
 size_t gemm_fp64eq_scratch_bytes(int m, int n, int k);
 int gemm_fp64eq_products(int k);
 void gemm_fp64eq_shape(int k, int *beta, int *levels, int *k_block);
+// width: tile width (32, 64 or 128) for the products of a level scheme
 void launch_gemm_fp64eq(int m, int n, int k, const double *A, long long lda, const double *B, long long ldb,
-                        double *C, long long ldc, void *scratch, cudaStream_t s);
+                        double *C, long long ldc, void *scratch, cudaStream_t s, int width);
 unsigned gemm_fp64eq_check_error(void *scratch, cudaStream_t s);
 unsigned *gemm_fp64eq_error_word(void *scratch);
 
+// FP64-equivalent accumulation scheme for inner dimension k (eq_digits.cuh:
+// 0 pairs, 1 levels with 7-bit digits, 2 levels with 6-bit digits)
+int eq_scheme_for(int k);
+// tile width of a problem's full tiles from a context's table (nullptr: the
+// built-in table)
+int eq_tile_width(const int *widths, int n, int k);
+int eq_default_width(int nb, int kb);
 // Grouped FFTs (batched function blocks): transforms of different lengths
 // and directions in two persistent launches.
 struct FftDesc {
@@ -149,6 +157,21 @@ void gemm_group_launch(GemmGroup *g, cudaStream_t s);
 unsigned gemm_group_check(GemmGroup *g, cudaStream_t s);
 double gemm_group_flops(const GemmGroup *g);
 void gemm_group_destroy(GemmGroup *g);
+
+// a single product of a level scheme on split operands (gemm_eq_group.cu)
+void launch_gemm_eq_tiles(int m, int n, int k, const void *As, const void *Bs, const int *ea,
+                          const int *eb, double *C, long long ldc, int width, unsigned *err, int num_sms,
+                          cudaStream_t s);
+// Grouped FP64-equivalent products: one split launch and one persistent
+// tensor-core launch over the tiles of every problem.
+struct EqGroup;
+EqGroup *eq_group_create(const std::vector<GemmDesc> &v, int num_sms, const int *widths);
+void eq_group_launch(EqGroup *g, cudaStream_t s);
+unsigned eq_group_check(EqGroup *g, cudaStream_t s);
+double eq_group_flops(const EqGroup *g);
+int eq_group_tiles(const EqGroup *g);
+void eq_group_destroy(EqGroup *g);
+
 
 // Raise a kernel's dynamic shared-memory limit on the current device once
 // (the attribute is per device and a process may drive several; `done`
@@ -218,6 +241,9 @@ struct Ctx {
     // (-1 tuned choice or default rule, else that variant for every grid)
     int opt_fused = -1;
     int opt_stencil_variant = -1;
+    // tile widths of the FP64-equivalent products by (n, k) bucket
+    // (oo_tune_gemm_tiles / oo_set_gemm_tiles; 0 = the built-in choice)
+    std::array<int, OO_TILE_NBUCKETS * OO_TILE_KBUCKETS> eq_widths{};
     // stencil tile variant chosen by oo_tune_stencil per grid: {I, J, K, variant}
     std::vector<std::array<int, 4>> stencil_choice;
     // the variant a stencil plan for this grid should use (-1: default rule)
@@ -296,6 +322,10 @@ void host_bc_k(const JacobiDims &d, float *p);
 // workspace; the fastest is kept for the grid and returned (ms_out: one entry
 // per variant, may be null)
 int tune_stencil(Ctx &c, int I, int J, int K, double *ms_out);
+// time every tile width of the grouped FP64-equivalent product for every
+// (n, k) bucket and keep the fastest in c.eq_widths (ms_out: buckets x 3,
+// may be null); gemm_eq_group.cu
+void tune_gemm_tiles(Ctx &c, double *ms_out);
 void run_pattern(Ctx &c, uint64_t gene, int hoist, const oo_jacobi &prob, float *p_out,
                  double *res_out, bool out_on_device, oo_run_stats *stats,
                  double abort_after_ms = 0.0, bool *aborted = nullptr);

@@ -202,7 +202,8 @@ void start(Server &S, SReq &q) {
         OO_CUDA_TRY(cudaMemcpyAsync(dB, hst + q.h_in1, (size_t)r.k * r.n * 8, cudaMemcpyHostToDevice, s));
         const unsigned *err_d;
         if (r.prec == OO_PREC_FP64EQ) {
-            launch_gemm_fp64eq((int)r.m, (int)r.n, (int)r.k, dA, r.k, dB, r.n, dC, r.n, scratch, s);
+            launch_gemm_fp64eq((int)r.m, (int)r.n, (int)r.k, dA, r.k, dB, r.n, dC, r.n, scratch, s,
+                               eq_tile_width(c.eq_widths.data(), (int)r.n, (int)r.k));
             err_d = gemm_fp64eq_error_word(scratch);
         } else {
             launch_gemm_split3((int)r.m, (int)r.n, (int)r.k, dA, r.k, dB, r.n, dC, r.n, scratch, s);

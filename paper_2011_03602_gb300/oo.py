@@ -141,6 +141,10 @@ def lib():
         "oo_ga_program": (_c.c_int, [_vp, _c.c_int, _c.c_int, OO_NEST_FN, OO_CHECK_FN, _vp, _vp, _vp, _c.c_int,
                                      _c.c_int, _dbl, _dbl, _u64, P(_u64), P(_dbl), _vp, _vp]),
         "oo_gemm_plan": (_c.c_int, [_c.c_int, _c.c_int, P(_c.c_int), P(_c.c_int), P(_c.c_int), P(_c.c_int)]),
+        "oo_gemm_scheme": (_c.c_int, [_c.c_int, P(_c.c_int), P(_c.c_int)]),
+        "oo_tune_gemm_tiles": (_c.c_int, [_vp, _vp, _vp]),
+        "oo_get_gemm_tiles": (_c.c_int, [_vp, _vp]),
+        "oo_set_gemm_tiles": (_c.c_int, [_vp, _vp]),
         "oo_batch_create": (_c.c_int, [_vp, P(oo_req), _c.c_int, P(_vp)]),
         "oo_batch_run": (_c.c_int, [_vp, _c.c_int]),
         "oo_batch_check": (_c.c_int, [_vp]),
@@ -529,6 +533,40 @@ def oo_gemm_plan(prec, k):
     v = [_c.c_int() for _ in range(4)]
     _check(None, lib().oo_gemm_plan(prec, k, *[_c.byref(x) for x in v]))
     return tuple(x.value for x in v)
+
+
+OO_EQ_PAIRS, OO_EQ_LEVELS = 0, 1
+OO_TILE_NBUCKETS, OO_TILE_KBUCKETS = 6, 5
+
+
+def oo_gemm_scheme(k):
+    """(scheme, most products summed in one FP32 accumulator) of an
+    FP64-equivalent product with inner dimension k."""
+    s, per = _c.c_int(), _c.c_int()
+    _check(None, lib().oo_gemm_scheme(k, _c.byref(s), _c.byref(per)))
+    return s.value, per.value
+
+
+def oo_tune_gemm_tiles(ctx):
+    """Autotune the FP64-equivalent tile widths; returns (widths table
+    OO_TILE_NBUCKETS x OO_TILE_KBUCKETS, mean ms per bucket and width 32/64/128)."""
+    w = np.zeros(OO_TILE_NBUCKETS * OO_TILE_KBUCKETS, np.int32)
+    ms = np.zeros(OO_TILE_NBUCKETS * OO_TILE_KBUCKETS * 3, np.float64)
+    _check(ctx, lib().oo_tune_gemm_tiles(ctx, w.ctypes.data_as(_vp), ms.ctypes.data_as(_vp)))
+    return w.reshape(OO_TILE_NBUCKETS, OO_TILE_KBUCKETS), ms.reshape(OO_TILE_NBUCKETS, OO_TILE_KBUCKETS, 3)
+
+
+def oo_get_gemm_tiles(ctx):
+    w = np.zeros(OO_TILE_NBUCKETS * OO_TILE_KBUCKETS, np.int32)
+    _check(ctx, lib().oo_get_gemm_tiles(ctx, w.ctypes.data_as(_vp)))
+    return w.reshape(OO_TILE_NBUCKETS, OO_TILE_KBUCKETS)
+
+
+def oo_set_gemm_tiles(ctx, widths):
+    w = np.ascontiguousarray(widths, np.int32).reshape(-1)
+    if w.size != OO_TILE_NBUCKETS * OO_TILE_KBUCKETS:
+        raise ValueError("need %d widths" % (OO_TILE_NBUCKETS * OO_TILE_KBUCKETS))
+    _check(ctx, lib().oo_set_gemm_tiles(ctx, w.ctypes.data_as(_vp)))
 
 
 def oo_fft_c128_dev(ctx, n, batch, direction, din, dout):

@@ -104,21 +104,51 @@ def test_missing_gpu_fails_loudly_or_creates():
 
 
 def test_gemm_plan_follows_the_exactness_rule():
-    """FP64-equivalent split: K-block kb and digit width beta keep every
-    FP32 K-block sum exact, kb (2^beta - 1)^2 < 2^24, and the level bound L
-    is the smallest with 4 (L + 2) 2^(-beta (L - 1)) <= 2^-42."""
+    """FP64-equivalent split: K-block kb, digit width beta and the number of
+    products one FP32 accumulator sums keep every accumulator exact,
+    per_acc * kb * (2^beta - 1)^2 < 2^24, and the level bound L is the
+    smallest with 4 (L + 2) 2^(-beta (L - 1)) <= 2^-42."""
     assert oo.oo_gemm_plan(oo.OO_PREC_SPLIT3_BF16, 4096) == (3, 0, 0, 0)
-    for k in (1, 63, 64, 200, 256, 257, 1000, 1024, 1025, 4096, 10000):
+    for k in (1, 63, 64, 65, 128, 129, 200, 256, 257, 512, 513, 1000, 1024, 1025, 4096, 10000):
         prods, beta, L, kb = oo.oo_gemm_plan(oo.OO_PREC_FP64EQ, k)
-        assert kb % 64 == 0 and kb >= min(k, 1024) and kb <= 1024
-        assert kb * (2 ** beta - 1) ** 2 < 2 ** 24 and beta <= 8
+        scheme, per_acc = oo.oo_gemm_scheme(k)
+        assert kb % 64 == 0 and kb <= 1024
+        assert per_acc == (1 if scheme == oo.OO_EQ_PAIRS else L - 1)
+        assert per_acc * kb * (2 ** beta - 1) ** 2 < 2 ** 24 and beta <= 8
         assert 4 * (L + 2) * 2.0 ** (-beta * (L - 1)) <= 2.0 ** -42
         assert 4 * (L + 1) * 2.0 ** (-beta * (L - 2)) > 2.0 ** -42
         assert prods == L * (L - 1) // 2
-    assert oo.oo_gemm_plan(oo.OO_PREC_FP64EQ, 256)[:3] == (21, 8, 7)
-    assert oo.oo_gemm_plan(oo.OO_PREC_FP64EQ, 4096)[:3] == (28, 7, 8)
+    # levels with 7-bit digits up to k = 128, 6-bit up to 512, pairs beyond
+    assert oo.oo_gemm_scheme(128) == (oo.OO_EQ_LEVELS, 7)
+    assert oo.oo_gemm_plan(oo.OO_PREC_FP64EQ, 100) == (28, 7, 8, 128)
+    assert oo.oo_gemm_scheme(512) == (oo.OO_EQ_LEVELS, 8)
+    assert oo.oo_gemm_plan(oo.OO_PREC_FP64EQ, 256) == (36, 6, 9, 256)
+    assert oo.oo_gemm_scheme(513) == (oo.OO_EQ_PAIRS, 1)
+    assert oo.oo_gemm_plan(oo.OO_PREC_FP64EQ, 4096) == (28, 7, 8, 1024)
     with pytest.raises(oo.OOError):
         oo.oo_gemm_plan(1, 64)
+
+
+def test_gemm_tile_table_host_only():
+    """The tile-width table of a context: built-in widths are 32, 64 or 128;
+    set / get round trip; other widths refused."""
+    ctx = oo.oo_create(-1)
+    try:
+        w = oo.oo_get_gemm_tiles(ctx)
+        assert w.shape == (oo.OO_TILE_NBUCKETS, oo.OO_TILE_KBUCKETS)
+        assert set(np.unique(w)) <= {32, 64, 128}
+        new = np.full_like(w, 64)
+        new[0, :] = 32
+        oo.oo_set_gemm_tiles(ctx, new)
+        assert np.array_equal(oo.oo_get_gemm_tiles(ctx), new)
+        bad = new.copy()
+        bad[2, 3] = 96
+        with pytest.raises(oo.OOError) as e:
+            oo.oo_set_gemm_tiles(ctx, bad)
+        assert e.value.status == oo.OO_EINVAL
+        assert np.array_equal(oo.oo_get_gemm_tiles(ctx), new)
+    finally:
+        oo.oo_destroy(ctx)
 
 
 def test_generic_program_needs_a_device_and_a_table():

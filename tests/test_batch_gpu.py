@@ -159,7 +159,8 @@ def test_full_size_batch_sampled(oo_mod):
         oo_mod.oo_destroy(ctx)
 
 
-def test_fp64_equivalent_requests_in_a_batch(oo_mod):
+@pytest.mark.parametrize("gemm_range", [(1, 260), (400, 1100)])
+def test_fp64_equivalent_requests_in_a_batch(oo_mod, gemm_range):
     """Both precision patterns in one batch: FP64-equivalent requests give
     exactly what oo_gemm_f64_dev gives for them alone (grouped, graph and
     per-call modes alike) and meet the 1e-12 bound; the split-BF16 requests
@@ -167,7 +168,9 @@ def test_fp64_equivalent_requests_in_a_batch(oo_mod):
     oo = oo_mod
     ctx = oo.oo_create(0)
     try:
-        reqs, host = make_requests(17, 10, 6, gemm_range=(1, 260))
+        # (1, 260): the level schemes (k <= 512); (400, 1100) reaches the
+        # pair scheme (k > 512), whose single products run their own kernel
+        reqs, host = make_requests(17, 10, 6, gemm_range=gemm_range)
         eq = [i for i in range(10) if i % 3 != 1]
         for i in eq:
             reqs[i]["prec"] = oo.OO_PREC_FP64EQ
