@@ -842,15 +842,39 @@ def run_batched(args):
     return 0
 
 
+def _serve_refs(job):
+    """Oracle references for the served mix, in a worker process: sampled
+    rows of a GEMM size, an FFT length, or a Jacobi grid's whole program."""
+    import oracle
+    from paper_2011_03602_gb300 import synth
+    kind, a = job
+    if kind == "gemm":
+        A, B = synth.gemm_matrix(7 + a, a, a), synth.gemm_matrix(8 + a, a, a)
+        rows = [0, a // 2, a - 1]
+        ref = np.stack([oracle.gemm(A[r:r + 1], B)[0] for r in rows])
+        scale = np.stack([np.abs(A[r]) @ np.abs(B) for r in rows])
+        return (kind, a), (rows, ref, scale)
+    if kind == "fft":
+        return (kind, a), oracle.fft(synth.complex_normal(9 + a, 1 << a), -1)
+    I, J, K = a
+    res, p = oracle.jacobi_run(I, J, K, 100, mode=1)
+    return (kind, a), (res, p.reshape(-1).astype(np.float32))
+
+
 def run_serve(args):
     """Serving loop: Poisson arrivals at each offered rate, split over three
     client threads (tags C / Python / Java; all submit through the C ABI),
-    mix 50% GEMM (square, n log-uniform in [64, 2048]), 30% FFT (2^10..2^20),
-    20% Jacobi solves (65x65x129 or 129x129x257, 100 iterations).  Reported:
-    solves/s, p50/p99 latency of admitted requests, back-pressure counts;
-    against the plain offload -- one synchronous call per solve, in arrival
-    order, on the same GPU and the same request stream."""
+    mix 50% GEMM (square, n log-uniform in [64, 2048], FP64-equivalent by
+    default), 30% FFT (2^10..2^20), 20% Jacobi solves (65x65x129 or
+    129x129x257, 100 iterations).  Reported: solves/s, p50/p99 latency of
+    admitted requests, back-pressure counts, and the error of every result
+    against the oracle (GEMM: sampled rows, max |C - C*| / (|A||B|); FFT:
+    relative L2; Jacobi: residuals relative, p absolute), against the plain
+    offload -- one synchronous call per solve in the same precision, in
+    arrival order, on the same GPU and the same request stream."""
+    import multiprocessing as mp
     import threading
+    refs_pool = mp.get_context("spawn").Pool(host_cores())
     import torch
     from paper_2011_03602_gb300 import oo, synth
     torch.cuda.set_device(0)
@@ -861,6 +885,15 @@ def run_serve(args):
     pool_g = {n: (synth.gemm_matrix(7 + n, n, n), synth.gemm_matrix(8 + n, n, n)) for n in gemm_sizes}
     pool_f = {e: synth.complex_normal(9 + e, 1 << e) for e in range(10, 21)}
     grids = [(65, 65, 129), (129, 129, 257)]
+    prec = oo.OO_PREC_FP64EQ if args.serve_prec == "fp64eq" else oo.OO_PREC_SPLIT3_BF16
+    # oracle references, computed on the host cores while the GPU serves
+    ref_jobs = [("gemm", n) for n in gemm_sizes] + [("fft", e) for e in range(10, 21)] + [("jacobi", g) for g in grids]
+    refs_async = refs_pool.map_async(_serve_refs, ref_jobs)
+    worst = {"gemm": 0.0, "fft": 0.0, "jacobi_res": 0.0, "jacobi_p": 0.0}
+    # the first result of every (kind, size) is kept and checked against the
+    # oracle at the end; every other result's digest must equal the first's
+    # (the blocks are deterministic), which keeps host memory bounded
+    first, digests, n_checked, n_differ = {}, {}, [0], [0]
 
     def draw(rng):
         u = rng.random()
@@ -875,7 +908,7 @@ def run_serve(args):
     def make(kind, a):
         if kind == "gemm":
             A, B = pool_g[a]
-            return dict(A=A, B=B, C=np.empty((a, a)))
+            return dict(A=A, B=B, C=np.empty((a, a)), prec=prec)
         if kind == "fft":
             x = pool_f[a]
             return dict(x=x, X=np.empty_like(x), dir=-1)
@@ -915,13 +948,30 @@ def run_serve(args):
                     continue
                 if st != 0:
                     raise oo.OOError(st, oo.oo_last_error(ctx))
-                mine.append((t, kw))
+                mine.append((t, kw, kinds[i]))
                 if len(mine) > 256:  # bound the client's host buffers in flight
-                    t_old, _ = mine.pop(0)
+                    t_old, kw_old, ka_old = mine.pop(0)
                     done.append(oo.oo_wait(ctx, t_old, 600000))
-            got = done + [oo.oo_wait(ctx, t, 600000) for t, _ in mine]
+                    keep(ka_old, kw_old)
+            got = done
+            for t, kw, ka in mine:
+                got.append(oo.oo_wait(ctx, t, 600000))
+                keep(ka, kw)
             with lock:
                 lat.extend(got)
+
+        def keep(ka, kw):
+            kind, _ = ka
+            outs = [kw["C"]] if kind == "gemm" else ([kw["X"]] if kind == "fft" else [kw["res"], kw["p"]])
+            words = [o.reshape(-1).view(np.uint64 if o.dtype.itemsize == 8 else np.uint32) for o in outs]
+            dg = tuple((int(np.bitwise_xor.reduce(w)), int(np.sum(w, dtype=np.uint64))) for w in words)
+            with lock:
+                n_checked[0] += 1
+                if ka not in first:
+                    first[ka] = [o.copy() for o in outs]
+                    digests[ka] = dg
+                elif digests[ka] != dg:
+                    n_differ[0] += 1
 
         ths = [threading.Thread(target=client, args=(tag,)) for tag in (0, 1, 2)]
         start = time.perf_counter()
@@ -943,7 +993,7 @@ def run_serve(args):
                 kind, a = kinds[i]
                 kw = make(kind, a)
                 if kind == "gemm":
-                    oo.oo_gemm_f64(ctx, kw["A"], kw["B"], out=kw["C"])
+                    oo.oo_gemm_f64(ctx, kw["A"], kw["B"], prec=prec, out=kw["C"])
                 elif kind == "fft":
                     oo.oo_fft_c128(ctx, kw["x"], -1, out=kw["X"])
                 else:
@@ -961,15 +1011,37 @@ def run_serve(args):
     stats = oo.oo_serve_stats(ctx)
     oo.oo_serve_stop(ctx)
     oo.oo_destroy(ctx)
+    refs = dict(refs_async.get())
+    refs_pool.close()
+    for (kind, a), outs in first.items():
+        if kind == "gemm":
+            rows, ref, scale = refs[("gemm", a)]
+            worst["gemm"] = max(worst["gemm"], float(np.max(np.abs(outs[0][rows] - ref) / scale)))
+        elif kind == "fft":
+            ref = refs[("fft", a)]
+            worst["fft"] = max(worst["fft"], float(np.linalg.norm(outs[0] - ref) / np.linalg.norm(ref)))
+        else:
+            res_ref, p_ref = refs[("jacobi", grids[a])]
+            res, p = outs
+            worst["jacobi_res"] = max(worst["jacobi_res"], float(np.max(np.abs(res - res_ref) / np.abs(res_ref))))
+            worst["jacobi_p"] = max(worst["jacobi_p"], float(np.max(np.abs(p.astype(np.float64) - p_ref))))
     best = max(r["solves_per_s"] for r in results)
     out = {"metric": "served solves/s and p50/p99 latency", "unit": "solves/s", "value": best,
            "higher_is_better": True, "data": "synthetic",
            "config": {"workload": "serve_mix_50gemm64-2048_30fft2e10-2e20_20jacobi65-129_it100",
+                      "gemm_precision": args.serve_prec,
                       "slots": args.serve_slots, "device_budget_gb": args.serve_budget_gb,
                       "queue_cap": args.serve_queue, "window_s": window, "clients": 3},
            "served": results, "plain_one_call_per_solve": plain,
            "served_vs_plain_solves_per_s": round(results[0]["solves_per_s"] / plain["solves_per_s"], 2),
-           "failed": stats["failed"], "stencil_variant_by_grid": tuned}
+           "failed": stats["failed"], "stencil_variant_by_grid": tuned,
+           "max_error_per_result_vs_oracle": {
+               "gemm": worst["gemm"], "gemm_metric": "max |C-C*| / (|A||B|) over rows 0, n/2, n-1",
+               "fft_rel_l2": worst["fft"], "jacobi_residual_rel": worst["jacobi_res"],
+               "jacobi_p_abs": worst["jacobi_p"], "results": n_checked[0],
+               "results_differing_from_first_of_same_size": n_differ[0],
+               "how": "first result of each kind and size against the oracle; every other result's "
+                      "digest against that first result's"}}
     print(json.dumps(out))
     return 0
 
@@ -992,6 +1064,7 @@ def main():
                     help="context: function blocks beside cuBLAS DGEMM / cuFFT Z2Z on the same GPU")
     ap.add_argument("--serve", action="store_true", help="serving-loop configuration")
     ap.add_argument("--serve-rates", default="2000,5000,10000,20000")
+    ap.add_argument("--serve-prec", choices=["fp64eq", "split3"], default="fp64eq")
     ap.add_argument("--serve-window", type=float, default=0.5, help="seconds of arrivals per rate")
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-budget-gb", type=int, default=16)

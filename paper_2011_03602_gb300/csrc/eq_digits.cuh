@@ -110,5 +110,21 @@ __device__ __forceinline__ __nv_bfloat16 digit(unsigned long long X, unsigned ne
     return __float2bfloat16_rn(neg ? -f : f);
 }
 
+// The same digits of two entries packed as a BF16 pair (first entry in the
+// low half), by exponent arithmetic: d < 2^8 is exact as 2^23 + d - 2^23 in
+// FP32 and in that float's top 16 bits, which are its BF16 bits; the sign is
+// OR-ed in (a zero digit of a negative entry is -0, as the conversion above
+// gives).  Bit for bit what digit() gives, without the integer-to-float and
+// float-to-BF16 conversion instructions.
+__device__ __forceinline__ unsigned digit_bits(unsigned long long X, unsigned neg, int beta, int p) {
+    const unsigned d = (unsigned)(X >> (64 - beta * (p + 1))) & ((1u << beta) - 1u);
+    const float f = __fsub_rn(__uint_as_float(0x4b000000u | d), 8388608.0f);
+    return (__float_as_uint(f) >> 16) | (neg << 15);
+}
+__device__ __forceinline__ unsigned digit_pair(unsigned long long X0, unsigned n0, unsigned long long X1, unsigned n1,
+                                               int beta, int p) {
+    return digit_bits(X0, n0, beta, p) | (digit_bits(X1, n1, beta, p) << 16);
+}
+
 }  // namespace eq
 }  // namespace oo

@@ -492,8 +492,7 @@ __global__ void __launch_bounds__(256) eq_group_split_kernel(const GSplit *gs, c
             const unsigned long long X0 = (mx != 0 && l < G.k) ? eq::fixed_frac(src[l], mx, n0) : 0ull;
             const unsigned long long X1 = (mx != 0 && l + 1 < G.k) ? eq::fixed_frac(src[l + 1], mx, n1) : 0ull;
             for (int p = 0; p < G.slices; ++p)
-                dst[p * plane2 + l2] =
-                    __halves2bfloat162(eq::digit(X0, n0, G.beta, p), eq::digit(X1, n1, G.beta, p));
+                reinterpret_cast<unsigned *>(dst)[p * plane2 + l2] = eq::digit_pair(X0, n0, X1, n1, G.beta, p);
         }
         return;
     }
@@ -531,7 +530,7 @@ __global__ void __launch_bounds__(256) eq_group_split_kernel(const GSplit *gs, c
             const unsigned long long X1 = cm != 0 ? eq::fixed_frac(t[2 * lane + 1][cc], cm, n1) : 0ull;
             __nv_bfloat162 *dst = reinterpret_cast<__nv_bfloat162 *>(G.Bs + (size_t)c * G.pitch + l0) + lane;
             for (int p = 0; p < G.slices; ++p)
-                dst[p * plane2] = __halves2bfloat162(eq::digit(X0, n0, G.beta, p), eq::digit(X1, n1, G.beta, p));
+                reinterpret_cast<unsigned *>(dst)[p * plane2] = eq::digit_pair(X0, n0, X1, n1, G.beta, p);
         }
         __syncthreads();
     }

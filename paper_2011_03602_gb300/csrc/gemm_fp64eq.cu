@@ -60,7 +60,6 @@ namespace oo {
 namespace {
 
 using namespace tc;
-using eq::digit;
 using eq::eff_exp;
 using eq::fixed_frac;
 
@@ -342,7 +341,7 @@ __global__ void eq_split_rows_kernel(const double *A, long long lda, int m, int 
         const unsigned long long X0 = (mx != 0 && l < k) ? fixed_frac(src[l], mx, n0) : 0ull;
         const unsigned long long X1 = (mx != 0 && l + 1 < k) ? fixed_frac(src[l + 1], mx, n1) : 0ull;
         for (int p = 0; p < s; ++p)
-            dst[p * (plane / 2) + l2] = __halves2bfloat162(digit(X0, n0, beta, p), digit(X1, n1, beta, p));
+            reinterpret_cast<unsigned *>(dst)[p * (plane / 2) + l2] = eq::digit_pair(X0, n0, X1, n1, beta, p);
     }
 }
 
@@ -385,7 +384,7 @@ __global__ void __launch_bounds__(256) eq_split_rows_v2_kernel(const double *A, 
         const unsigned long long X0 = mx != 0 ? fixed_frac(v.x, mx, n0) : 0ull;
         const unsigned long long X1 = mx != 0 ? fixed_frac(v.y, mx, n1) : 0ull;
         for (int p = 0; p < s; ++p)
-            dst[p * plane2 + l2] = __halves2bfloat162(digit(X0, n0, beta, p), digit(X1, n1, beta, p));
+            reinterpret_cast<unsigned *>(dst)[p * plane2 + l2] = eq::digit_pair(X0, n0, X1, n1, beta, p);
     }
 }
 
@@ -425,7 +424,7 @@ __global__ void eq_split_cols_t_kernel(const double *B, long long ldb, int k, in
         const unsigned long long X1 = mx != 0 ? fixed_frac(t[2 * lane + 1][cc], mx, n1) : 0ull;
         __nv_bfloat162 *dst = reinterpret_cast<__nv_bfloat162 *>(Bs + (size_t)c * kp + l0) + lane;
         for (int p = 0; p < s; ++p)
-            dst[p * (plane / 2)] = __halves2bfloat162(digit(X0, n0, beta, p), digit(X1, n1, beta, p));
+            reinterpret_cast<unsigned *>(dst)[p * (plane / 2)] = eq::digit_pair(X0, n0, X1, n1, beta, p);
     }
 }
 

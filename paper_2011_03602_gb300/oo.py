@@ -620,13 +620,13 @@ def oo_serve_start(ctx, slots=8, hbm_budget_bytes=8 << 30, queue_cap=4096):
 
 def serve_request(kind, **kw):
     """Build an oo_serve_req from numpy host arrays (kept alive by the caller
-    until oo_wait returns): gemm(A, B, C), fft(x, X, dir), jacobi(I, J, K,
-    iters, p, res, omega)."""
+    until oo_wait returns): gemm(A, B, C, prec), fft(x, X, dir), jacobi(I, J,
+    K, iters, p, res, omega).  GEMMs default to the FP64-equivalent pattern."""
     r = oo_serve_req()
     r.client = kw.get("client", OO_LANG_PYTHON)
     if kind == "gemm":
         A, B, C = kw["A"], kw["B"], kw["C"]
-        r.kind, r.prec, (r.m, r.k), r.n = OO_BLOCK_GEMM, kw.get("prec", 0), A.shape, B.shape[1]
+        r.kind, r.prec, (r.m, r.k), r.n = OO_BLOCK_GEMM, kw.get("prec", OO_PREC_FP64EQ), A.shape, B.shape[1]
         r.in0, r.in1, r.out = _host_ptr(A, np.float64), _host_ptr(B, np.float64), _host_ptr(C, np.float64)
     elif kind == "fft":
         x, X = kw["x"], kw["X"]
