@@ -917,103 +917,119 @@ def run_serve(args):
 
     ctx = oo.oo_create(0)
     tuned = {"%dx%dx%d" % g: oo.oo_tune_stencil(ctx, *g)[0] for g in grids}  # stencil tile per grid
-    oo.oo_serve_start(ctx, slots=args.serve_slots, hbm_budget_bytes=args.serve_budget_gb << 30,
-                      queue_cap=args.serve_queue)
-    # warm-up: one of each kind
-    for kind, a in (("gemm", 2048), ("fft", 20), ("jacobi", 1)):
+    modes = [m for m in args.serve_modes.split(",") if m]
+    per_mode = {}
+    for mode in modes:
+        if mode == "resident":
+            # the request loop resident on the device: persistent workers,
+            # no kernel launch per request
+            oo.oo_serve_start_resident(ctx, args.serve_budget_gb << 30, args.serve_queue)
+        else:
+            # the host scheduler over slot streams
+            oo.oo_serve_start(ctx, slots=args.serve_slots, hbm_budget_bytes=args.serve_budget_gb << 30,
+                              queue_cap=args.serve_queue)
+        first.clear()
+        digests.clear()
+        # warm-up: one of each kind
+        for kind, a in (("gemm", 2048), ("fft", 20), ("jacobi", 1)):
+            kw = make(kind, a)
+            oo.oo_wait(ctx, oo.oo_submit(ctx, oo.serve_request(kind, **kw)), 120000)
+        results = []
+        for rate in rates:
+            rng = np.random.default_rng(rate)
+            n_req = max(3, int(rate * window))
+            arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+            kinds = [draw(rng) for _ in range(n_req)]
+            lat, rejected, lock = [], [0], threading.Lock()
+            t0 = time.perf_counter() + 0.05
+
+            def client(tag):
+                mine, done = [], []
+                for i in range(tag, n_req, 3):
+                    kind, a = kinds[i]
+                    kw = make(kind, a)
+                    dt = t0 + arrivals[i] - time.perf_counter()
+                    if dt > 0:
+                        time.sleep(dt)
+                    st, t = oo.oo_submit_status(ctx, oo.serve_request(kind, client=tag, **kw))
+                    if st == oo.OO_EBUSY:
+                        with lock:
+                            rejected[0] += 1
+                        continue
+                    if st != 0:
+                        raise oo.OOError(st, oo.oo_last_error(ctx))
+                    mine.append((t, kw, kinds[i]))
+                    if len(mine) > 256:  # bound the client's host buffers in flight
+                        t_old, kw_old, ka_old = mine.pop(0)
+                        done.append(oo.oo_wait(ctx, t_old, 600000))
+                        keep(ka_old, kw_old)
+                got = done
+                for t, kw, ka in mine:
+                    got.append(oo.oo_wait(ctx, t, 600000))
+                    keep(ka, kw)
+                with lock:
+                    lat.extend(got)
+
+            def keep(ka, kw):
+                kind, _ = ka
+                outs = [kw["C"]] if kind == "gemm" else ([kw["X"]] if kind == "fft" else [kw["res"], kw["p"]])
+                words = [o.reshape(-1).view(np.uint64 if o.dtype.itemsize == 8 else np.uint32) for o in outs]
+                dg = tuple((int(np.bitwise_xor.reduce(w)), int(np.sum(w, dtype=np.uint64))) for w in words)
+                with lock:
+                    n_checked[0] += 1
+                    if ka not in first:
+                        first[ka] = [o.copy() for o in outs]
+                        digests[ka] = dg
+                    elif digests[ka] != dg:
+                        n_differ[0] += 1
+
+            ths = [threading.Thread(target=client, args=(tag,)) for tag in (0, 1, 2)]
+            start = time.perf_counter()
+            for th in ths:
+                th.start()
+            for th in ths:
+                th.join()
+            elapsed = time.perf_counter() - start
+            lat_a = np.array(lat) if lat else np.array([np.nan])
+            results.append({"offered_req_per_s": rate, "requests": n_req, "admitted": len(lat),
+                            "rejected_busy": rejected[0], "solves_per_s": round(len(lat) / elapsed, 1),
+                            "p50_ms": round(float(np.percentile(lat_a, 50)), 3),
+                            "p99_ms": round(float(np.percentile(lat_a, 99)), 3)})
+        stats = oo.oo_serve_stats(ctx)
+        oo.oo_serve_stop(ctx)
+        per_mode[mode] = (results, stats, dict(first))
+    # plain offload (no server running): the first rate's request stream, one
+    # synchronous call per solve; latency from the queue the arrival process
+    # would form in front of a one-at-a-time server
+    rate = rates[0]
+    rng = np.random.default_rng(rate)
+    n_req = max(3, int(rate * window))
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
+    kinds = [draw(rng) for _ in range(n_req)]
+    prev, sim_end, lat_p = 0.0, 0.0, []
+    tp0 = time.perf_counter()
+    for i in range(n_req):
+        kind, a = kinds[i]
         kw = make(kind, a)
-        oo.oo_wait(ctx, oo.oo_submit(ctx, oo.serve_request(kind, **kw)), 120000)
-    results = []
-    plain = None
-    for rate in rates:
-        rng = np.random.default_rng(rate)
-        n_req = max(3, int(rate * window))
-        arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
-        kinds = [draw(rng) for _ in range(n_req)]
-        lat, rejected, lock = [], [0], threading.Lock()
-        t0 = time.perf_counter() + 0.05
-
-        def client(tag):
-            mine, done = [], []
-            for i in range(tag, n_req, 3):
-                kind, a = kinds[i]
-                kw = make(kind, a)
-                dt = t0 + arrivals[i] - time.perf_counter()
-                if dt > 0:
-                    time.sleep(dt)
-                st, t = oo.oo_submit_status(ctx, oo.serve_request(kind, client=tag, **kw))
-                if st == oo.OO_EBUSY:
-                    with lock:
-                        rejected[0] += 1
-                    continue
-                if st != 0:
-                    raise oo.OOError(st, oo.oo_last_error(ctx))
-                mine.append((t, kw, kinds[i]))
-                if len(mine) > 256:  # bound the client's host buffers in flight
-                    t_old, kw_old, ka_old = mine.pop(0)
-                    done.append(oo.oo_wait(ctx, t_old, 600000))
-                    keep(ka_old, kw_old)
-            got = done
-            for t, kw, ka in mine:
-                got.append(oo.oo_wait(ctx, t, 600000))
-                keep(ka, kw)
-            with lock:
-                lat.extend(got)
-
-        def keep(ka, kw):
-            kind, _ = ka
-            outs = [kw["C"]] if kind == "gemm" else ([kw["X"]] if kind == "fft" else [kw["res"], kw["p"]])
-            words = [o.reshape(-1).view(np.uint64 if o.dtype.itemsize == 8 else np.uint32) for o in outs]
-            dg = tuple((int(np.bitwise_xor.reduce(w)), int(np.sum(w, dtype=np.uint64))) for w in words)
-            with lock:
-                n_checked[0] += 1
-                if ka not in first:
-                    first[ka] = [o.copy() for o in outs]
-                    digests[ka] = dg
-                elif digests[ka] != dg:
-                    n_differ[0] += 1
-
-        ths = [threading.Thread(target=client, args=(tag,)) for tag in (0, 1, 2)]
-        start = time.perf_counter()
-        for th in ths:
-            th.start()
-        for th in ths:
-            th.join()
-        elapsed = time.perf_counter() - start
-        lat_a = np.array(lat) if lat else np.array([np.nan])
-        results.append({"offered_req_per_s": rate, "requests": n_req, "admitted": len(lat),
-                        "rejected_busy": rejected[0], "solves_per_s": round(len(lat) / elapsed, 1),
-                        "p50_ms": round(float(np.percentile(lat_a, 50)), 3),
-                        "p99_ms": round(float(np.percentile(lat_a, 99)), 3)})
-        if plain is None:
-            # plain offload: the same request stream, one synchronous call per solve
-            prev, sim_end, lat_p = 0.0, 0.0, []
-            tp0 = time.perf_counter()
-            for i in range(n_req):
-                kind, a = kinds[i]
-                kw = make(kind, a)
-                if kind == "gemm":
-                    oo.oo_gemm_f64(ctx, kw["A"], kw["B"], prec=prec, out=kw["C"])
-                elif kind == "fft":
-                    oo.oo_fft_c128(ctx, kw["x"], -1, out=kw["X"])
-                else:
-                    oo.oo_run_pattern(ctx, 63, 1, oo.jacobi(kw["I"], kw["J"], kw["K"], 100), kw["p"], kw["res"])
-                # service time of this call, then the queue the arrival
-                # process would have formed in front of a one-at-a-time server
-                now = time.perf_counter() - tp0
-                sim_end = max(sim_end, arrivals[i]) + (now - prev)
-                prev = now
-                lat_p.append((sim_end - arrivals[i]) * 1e3)
-            elapsed_p = time.perf_counter() - tp0
-            plain = {"offered_req_per_s": rate, "requests": n_req, "solves_per_s": round(n_req / elapsed_p, 1),
-                     "p50_ms_if_arrivals_queue": round(float(np.percentile(lat_p, 50)), 3),
-                     "p99_ms_if_arrivals_queue": round(float(np.percentile(lat_p, 99)), 3)}
-    stats = oo.oo_serve_stats(ctx)
-    oo.oo_serve_stop(ctx)
+        if kind == "gemm":
+            oo.oo_gemm_f64(ctx, kw["A"], kw["B"], prec=prec, out=kw["C"])
+        elif kind == "fft":
+            oo.oo_fft_c128(ctx, kw["x"], -1, out=kw["X"])
+        else:
+            oo.oo_run_pattern(ctx, 63, 1, oo.jacobi(kw["I"], kw["J"], kw["K"], 100), kw["p"], kw["res"])
+        now = time.perf_counter() - tp0
+        sim_end = max(sim_end, arrivals[i]) + (now - prev)
+        prev = now
+        lat_p.append((sim_end - arrivals[i]) * 1e3)
+    elapsed_p = time.perf_counter() - tp0
+    plain = {"offered_req_per_s": rate, "requests": n_req, "solves_per_s": round(n_req / elapsed_p, 1),
+             "p50_ms_if_arrivals_queue": round(float(np.percentile(lat_p, 50)), 3),
+             "p99_ms_if_arrivals_queue": round(float(np.percentile(lat_p, 99)), 3)}
     oo.oo_destroy(ctx)
     refs = dict(refs_async.get())
     refs_pool.close()
-    for (kind, a), outs in first.items():
+    checked = [(ka, outs) for m in per_mode.values() for ka, outs in m[2].items()]
+    for (kind, a), outs in checked:
         if kind == "gemm":
             rows, ref, scale = refs[("gemm", a)]
             worst["gemm"] = max(worst["gemm"], float(np.max(np.abs(outs[0][rows] - ref) / scale)))
@@ -1025,6 +1041,7 @@ def run_serve(args):
             res, p = outs
             worst["jacobi_res"] = max(worst["jacobi_res"], float(np.max(np.abs(res - res_ref) / np.abs(res_ref))))
             worst["jacobi_p"] = max(worst["jacobi_p"], float(np.max(np.abs(p.astype(np.float64) - p_ref))))
+    results, stats, _ = per_mode[modes[0]]
     best = max(r["solves_per_s"] for r in results)
     out = {"metric": "served solves/s and p50/p99 latency", "unit": "solves/s", "value": best,
            "higher_is_better": True, "data": "synthetic",
@@ -1032,9 +1049,11 @@ def run_serve(args):
                       "gemm_precision": args.serve_prec,
                       "slots": args.serve_slots, "device_budget_gb": args.serve_budget_gb,
                       "queue_cap": args.serve_queue, "window_s": window, "clients": 3},
-           "served": results, "plain_one_call_per_solve": plain,
+           "served": results, "served_loop": modes[0],
+           "served_other_loops": {m: per_mode[m][0] for m in modes[1:]},
+           "plain_one_call_per_solve": plain,
            "served_vs_plain_solves_per_s": round(results[0]["solves_per_s"] / plain["solves_per_s"], 2),
-           "failed": stats["failed"], "stencil_variant_by_grid": tuned,
+           "failed": {m: per_mode[m][1]["failed"] for m in modes}, "stencil_variant_by_grid": tuned,
            "max_error_per_result_vs_oracle": {
                "gemm": worst["gemm"], "gemm_metric": "max |C-C*| / (|A||B|) over rows 0, n/2, n-1",
                "fft_rel_l2": worst["fft"], "jacobi_residual_rel": worst["jacobi_res"],
@@ -1065,6 +1084,9 @@ def main():
     ap.add_argument("--serve", action="store_true", help="serving-loop configuration")
     ap.add_argument("--serve-rates", default="2000,5000,10000,20000")
     ap.add_argument("--serve-prec", choices=["fp64eq", "split3"], default="fp64eq")
+    ap.add_argument("--serve-modes", default="resident,host",
+                    help="serving loops to run, the first is the headline: resident (persistent device workers), "
+                         "host (scheduler thread over slot streams)")
     ap.add_argument("--serve-window", type=float, default=0.5, help="seconds of arrivals per rate")
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-budget-gb", type=int, default=16)

@@ -297,11 +297,16 @@ oo_status oo_tune_stencil(oo_ctx *ctx, int I, int J, int K, int *variant, double
  *   OO_INJECT_FUSED_BARRIER the next fused-iteration launch (small grids,
  *                           all iteration nests on the GPU) waits at its first
  *                           grid barrier for one block more than it launched.
+ *   OO_INJECT_SERVE_STALL   the device-resident serving loop started next
+ *                           (oo_serve_start_resident) gives the first request
+ *                           it admits a work entry whose dependency never
+ *                           completes, so the workers' bounded waits run out:
+ *                           every request in flight fails with OO_ETIMEOUT.
  * Either kernel then sets its error word, waits (bounded) for its own copies
  * in flight and returns; the pattern call (or oo_stencil_check /
  * oo_stencil_noalloc_check after a single sweep) returns OO_ETIMEOUT and the
  * context stays usable.  OO_INJECT_NONE disarms; OO_EINVAL for other values. */
-enum { OO_INJECT_NONE = 0, OO_INJECT_STENCIL_LOAD = 1, OO_INJECT_FUSED_BARRIER = 2 };
+enum { OO_INJECT_NONE = 0, OO_INJECT_STENCIL_LOAD = 1, OO_INJECT_FUSED_BARRIER = 2, OO_INJECT_SERVE_STALL = 3 };
 oo_status oo_inject_wait_timeout(oo_ctx *ctx, int what);
 
 /* Context options (per context, never read from the process environment):
@@ -560,8 +565,33 @@ oo_status oo_submit(oo_ctx *ctx, const oo_serve_req *req, uint64_t *ticket);
 oo_status oo_wait(oo_ctx *ctx, uint64_t ticket, int timeout_ms, double *latency_ms);
 oo_status oo_serve_stats(oo_ctx *ctx, oo_serve_stats_t *out);
 /* Finish admitted and queued work, stop the scheduler, free the arena.
- * Tickets not yet waited for are discarded.                              */
+ * Tickets not yet waited for are discarded.  Stops either kind of service. */
 oo_status oo_serve_stop(oo_ctx *ctx);
+
+/* The same service (oo_submit, oo_wait, oo_serve_stats, oo_serve_stop) with
+ * the request loop resident on the device: two persistent worker kernels are
+ * launched here, once, and take their work from rings in device memory --
+ * one of `tensor_ctas` CTAs (0: 3/8 of the SMs) runs the tensor-core tiles of
+ * FP64-equivalent GEMMs, the other (the remaining SMs, 512 threads each) the
+ * digit splits, FFT passes and Jacobi sweeps.  A scheduler thread admits the
+ * oldest waiting requests whose device footprint fits the free part of the
+ * `hbm_budget_bytes` budget (a quarter of it holds GEMM digit slices),
+ * copies their inputs, descriptors and work entries to the device and
+ * publishes the entries through a control block in mapped host memory; it
+ * launches no kernel per request.  Requests' entries interleave in the rings,
+ * so requests that arrive while others run share the SMs (continuous
+ * batching).  The workers write each finished request's flag to mapped
+ * memory; the outputs are then copied back.  Served here: GEMMs in
+ * OO_PREC_FP64EQ with k <= 2048 (the same bits as oo_gemm_f64), FFTs up to
+ * 2^22 points (the same bits as oo_fft_c128), Jacobi programs (the tiled
+ * kernels' p bits; residuals summed in chunk order, within ~1e-12 relative of
+ * the tiled kernels'); other requests give OO_EINVAL.  Every device wait is
+ * bounded (about a second); an idle server publishes keep-alive entries.
+ * If a wait runs out, every request in flight fails with OO_ETIMEOUT and
+ * later submissions with OO_ESTATE until oo_serve_stop.  While serving, the
+ * workers hold every SM of the device: the context's other GPU calls wait
+ * for SMs.  OO_ESTATE if the context already serves.                     */
+oo_status oo_serve_start_resident(oo_ctx *ctx, uint64_t hbm_budget_bytes, int queue_cap, int tensor_ctas);
 
 /* --------------------------------------------------- batched function blocks */
 /* Many GEMM and FFT requests of uneven sizes, on caller-owned device buffers.

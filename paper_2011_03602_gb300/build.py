@@ -27,7 +27,10 @@ CU_FLAGS = {
     "jacobi.cu": ["-fmad=false"],
     "fft.cu": ["-fmad=false"],
     "gemm_fp64eq.cu": ["-fmad=false"],
-    "gemm_eq_group.cu": ["-fmad=false"],
+    # the device-resident workers read data that other SMs and copies write
+    # while they run: global loads are cached in L2 only (coherent), not L1
+    "gemm_eq_group.cu": ["-fmad=false", "-Xptxas", "-dlcm=cg"],
+    "serve_resident.cu": ["-fmad=false", "-Xptxas", "-dlcm=cg"],
 }
 CXX_FLAGS = ["-O3", "-std=c++17", "-fPIC", "-fopenmp", "-ffp-contract=off", "-Wall",
              "-I" + os.path.join(CUDA_HOME, "include"), "-I" + os.path.join(ROOT, "include")]

@@ -46,8 +46,14 @@ oo_status guarded(oo_ctx *ctx, F &&f) {
     }
 }
 
-void use_device(Ctx &c) {
+// GPU work of a context.  While the device-resident serving loop runs, its
+// persistent workers hold the device: a kernel that is loaded lazily at its
+// first launch could wait for them, so the context's other GPU calls are
+// refused until oo_serve_stop.
+void use_device(Ctx &c, bool compute = true) {
     OO_REQUIRE(c.device >= 0, OO_ESTATE, "host-only context (device -1) cannot run GPU work");
+    OO_REQUIRE(!compute || c.rserver == nullptr, OO_ESTATE,
+               "the device-resident serving loop runs on this context: oo_serve_stop it first");
     OO_CUDA_TRY(cudaSetDevice(c.device));
 }
 
@@ -133,6 +139,10 @@ void oo_destroy(oo_ctx *ctx) {
         server_stop(ctx->c.server);
         ctx->c.server = nullptr;
     }
+    if (ctx->c.rserver) {
+        resident_stop(ctx->c.rserver);
+        ctx->c.rserver = nullptr;
+    }
     if (ctx->c.stream) cudaStreamSynchronize(ctx->c.stream);
     stencil_plan_destroy(ctx->user_plan);
     jacobi_work_free(ctx->c.jw);
@@ -149,7 +159,7 @@ void oo_destroy(oo_ctx *ctx) {
 oo_status oo_sync(oo_ctx *ctx) {
     if (!ctx) return OO_EINVAL;
     return guarded(ctx, [&] {
-        use_device(ctx->c);
+        use_device(ctx->c, false);
         OO_CUDA_TRY(cudaStreamSynchronize(ctx->c.stream));
     });
 }
@@ -168,7 +178,8 @@ oo_status oo_tune_stencil(oo_ctx *ctx, int I, int J, int K, int *variant, double
 oo_status oo_inject_wait_timeout(oo_ctx *ctx, int what) {
     if (!ctx) return OO_EINVAL;
     return guarded(ctx, [&] {
-        OO_REQUIRE(what == OO_INJECT_NONE || what == OO_INJECT_STENCIL_LOAD || what == OO_INJECT_FUSED_BARRIER,
+        OO_REQUIRE(what == OO_INJECT_NONE || what == OO_INJECT_STENCIL_LOAD || what == OO_INJECT_FUSED_BARRIER ||
+                       what == OO_INJECT_SERVE_STALL,
                    OO_EINVAL, "unknown fault injection " + std::to_string(what));
         ctx->c.inject_wait = what;
     });
@@ -274,7 +285,7 @@ oo_status oo_stencil_dev(oo_ctx *ctx, int I, int J, int K, int pitch, const floa
 oo_status oo_stencil_check(oo_ctx *ctx) {
     if (!ctx) return OO_EINVAL;
     return guarded(ctx, [&] {
-        use_device(ctx->c);
+        use_device(ctx->c, false);
         OO_CUDA_TRY(cudaStreamSynchronize(ctx->c.stream));
         if (!ctx->user_plan) return;
         const unsigned e = stencil_plan_check(ctx->user_plan, ctx->c.stream);

@@ -126,5 +126,83 @@ __device__ __forceinline__ unsigned digit_pair(unsigned long long X0, unsigned n
     return digit_bits(X0, n0, beta, p) | (digit_bits(X1, n1, beta, p) << 16);
 }
 
+// One product's split job arguments (grouped products and the serving loop)
+struct GSplit {
+    const double *A, *B;
+    long long lda, ldb, pitch;  // pitch: row pitch (elements) of the stacked operands
+    int m, n, k, kp, beta, slices;
+    __nv_bfloat16 *As, *Bs;     // row 0 of slice 0 of this problem: slice p of row r at As[(p m + r) pitch]
+    int *ea, *eb;
+};
+
+// Rows [r0, r0 + warps) of A, one warp per row: the row's scale exponent ea
+// and its digit slices (zero digits fill [k, kp)).
+__device__ __forceinline__ void split_rows_job(const GSplit &G, int r0) {
+    const int lane = threadIdx.x & 31;
+    const int row = r0 + (threadIdx.x >> 5);
+    if (row >= G.m) return;
+    const double *src = G.A + (long long)row * G.lda;
+    int mx = 0;
+#pragma unroll 4
+    for (int l = lane; l < G.k; l += 32) mx = max(mx, eff_exp(src[l]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) G.ea[row] = mx == 0 ? 0 : mx - 1022;
+    const size_t plane2 = (size_t)G.m * G.pitch / 2;
+    unsigned *dst = reinterpret_cast<unsigned *>(G.As + (size_t)row * G.pitch);
+    for (int l2 = lane; l2 < G.kp / 2; l2 += 32) {
+        const int l = 2 * l2;
+        unsigned n0 = 0, n1 = 0;
+        const unsigned long long X0 = (mx != 0 && l < G.k) ? fixed_frac(src[l], mx, n0) : 0ull;
+        const unsigned long long X1 = (mx != 0 && l + 1 < G.k) ? fixed_frac(src[l + 1], mx, n1) : 0ull;
+        for (int p = 0; p < G.slices; ++p) dst[p * plane2 + l2] = digit_pair(X0, n0, X1, n1, G.beta, p);
+    }
+}
+
+// Columns [c0, c0 + 64) of B: each column's scale exponent eb (largest over
+// all k) and its transposed digit slices through 64 x 64 shared-memory
+// tiles.  Every thread of the block calls it (it synchronises the block);
+// blockDim.x a multiple of 64, t and red shared arrays of 64 x 65 doubles and
+// (blockDim.x / 64) x 64 ints.
+__device__ __forceinline__ void split_cols_job(const GSplit &G, int c0, double (*t)[65], int (*red)[64]) {
+    const int lane = threadIdx.x & 31;
+    const int ny = blockDim.x >> 6, nw = blockDim.x >> 5;
+    const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;  // 64 columns x ny row groups
+    const int col = c0 + tx;
+    int mx = 0;
+    if (col < G.n)
+#pragma unroll 4
+        for (int l = ty; l < G.k; l += ny) mx = max(mx, eff_exp(G.B[(long long)l * G.ldb + col]));
+    red[ty][tx] = mx;
+    __syncthreads();
+    if (ty == 0) {
+        for (int y = 1; y < ny; ++y) mx = max(mx, red[y][tx]);
+        red[0][tx] = mx;
+        if (col < G.n) G.eb[col] = mx == 0 ? 0 : mx - 1022;
+    }
+    __syncthreads();
+    const int w = threadIdx.x >> 5, cpw = 64 / nw;  // columns written per warp
+    const size_t plane2 = (size_t)G.n * G.pitch / 2;
+    for (int l0 = 0; l0 < G.kp; l0 += 64) {
+#pragma unroll 4
+        for (int yy = ty; yy < 64; yy += ny) {
+            const int l = l0 + yy;
+            t[yy][tx] = (l < G.k && col < G.n) ? G.B[(long long)l * G.ldb + col] : 0.0;
+        }
+        __syncthreads();
+        for (int cc = w * cpw; cc < w * cpw + cpw; ++cc) {
+            const int c = c0 + cc;
+            if (c >= G.n) break;
+            const int cm = red[0][cc];
+            unsigned n0 = 0, n1 = 0;
+            const unsigned long long X0 = cm != 0 ? fixed_frac(t[2 * lane][cc], cm, n0) : 0ull;
+            const unsigned long long X1 = cm != 0 ? fixed_frac(t[2 * lane + 1][cc], cm, n1) : 0ull;
+            unsigned *dst = reinterpret_cast<unsigned *>(G.Bs + (size_t)c * G.pitch + l0) + lane;
+            for (int p = 0; p < G.slices; ++p) dst[p * plane2] = digit_pair(X0, n0, X1, n1, G.beta, p);
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace eq
 }  // namespace oo

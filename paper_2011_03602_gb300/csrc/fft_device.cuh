@@ -1,0 +1,291 @@
+// Device code of the Fourier-transform block shared by its kernels
+// (fft.cu) and the device-resident serving loop (serve_resident.cu):
+// float-float complex values in shared memory, Stockham radix-4 stages
+// (a radix-2 stage first for odd log2 L) with per-stage twiddle tables, the
+// exact power-of-two input scaling, and one work item of a group of
+// transforms.  The design is described in fft.cu.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "ff.cuh"
+
+namespace oo {
+namespace {
+
+constexpr int kFftThreads = 512;
+constexpr int kFftBpt = 2;                               // radix-4 butterflies per thread
+constexpr int kFftElems = 4 * kFftThreads * kFftBpt;     // 4096 values per CTA
+constexpr int kTwSplit = 11;                             // four-step twiddle split: 2^11
+
+using ff::cplx;
+
+__device__ __forceinline__ cplx ld_cplx(const float4 *p) {
+    const float4 v = *p;
+    return cplx{v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ void st_cplx(float4 *p, const cplx &c) { *p = make_float4(c.rh, c.rl, c.ih, c.il); }
+
+// x * 2^-S split into a float pair (hi: top 24 mantissa bits; lo: the rest
+// rounded to 24 bits), integer-only; values below 2^-126 after scaling flush.
+__device__ __forceinline__ void split_scaled(double x, int S, float &h, float &l) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi32 = (unsigned)(b >> 32), lo32 = (unsigned)b;
+    const unsigned sign = hi32 & 0x80000000u;
+    const int e = (int)((hi32 >> 20) & 0x7ffu);
+    const int fe = e - 1023 - S + 127;  // biased float exponent of the scaled value
+    if (e == 0 || e == 0x7ff || fe <= 0) {
+        h = 0.0f;
+        l = 0.0f;
+        return;
+    }
+    const unsigned mtop = ((hi32 & 0xfffffu) << 3) | (lo32 >> 29);
+    h = __uint_as_float(sign | ((unsigned)fe << 23) | mtop);
+    const unsigned r = lo32 & 0x1fffffffu;
+    const int le = fe - 52;  // biased exponent of 2^(unbiased(fe) - 52)
+    float lf = 0.0f;
+    if (le > 0 && r != 0) lf = __fmul_rn(__uint2float_rn(r), __uint_as_float((unsigned)le << 23));
+    l = sign ? -lf : lf;
+}
+
+// (h + l) * 2^S as a double, integer-only conversion
+__device__ __forceinline__ double widen_scaled(float h, float l, int S) {
+    return ff::scale_pow2(ff::to_double(h, l), S);
+}
+
+// A transform holding a NaN or an infinity: its maximum exponent reads 0x7ff.
+// Every butterfly then sees zeros (split_scaled flushes non-finite values and
+// the scale flushes the rest) and every output component is written as NaN,
+// which is what the FP64 definition gives for any length above one.
+constexpr int kNonFiniteExpo = 0x7ff;
+__device__ __forceinline__ double2 nan2() {
+    const double q = __longlong_as_double(0x7ff8000000000000ll);
+    return make_double2(q, q);
+}
+
+__device__ __forceinline__ cplx twiddle(const float4 *stw, int idx, bool inv) {
+    cplx w = ld_cplx(stw + idx);
+    return inv ? ff::conj(w) : w;
+}
+
+// Stockham radix-2 stage with sub-length Ls on C columns of length L; used
+// only as the first stage (Ls = 1), which needs no twiddles.
+__device__ __forceinline__ void stage_r2(float4 *sd, const float4 *, int log2L, int Ls, bool) {
+    const int L = 1 << log2L, half = L >> 1;
+    cplx y0[2 * kFftBpt], y1[2 * kFftBpt];
+    int base_c[2 * kFftBpt], jj[2 * kFftBpt];
+#pragma unroll
+    for (int r = 0; r < 2 * kFftBpt; ++r) {
+        const int bidx = threadIdx.x + r * kFftThreads;
+        const int c = bidx >> (log2L - 1), j = bidx & (half - 1);
+        base_c[r] = c << log2L;
+        jj[r] = j;
+        y0[r] = ld_cplx(sd + base_c[r] + j);
+        cplx x1 = ld_cplx(sd + base_c[r] + j + half);
+        y1[r] = x1;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 2 * kFftBpt; ++r) {
+        const int j = jj[r], k = j & (Ls - 1);
+        const int o = base_c[r] + (j - k) * 2 + k;
+        st_cplx(sd + o, ff::cadd(y0[r], y1[r]));
+        st_cplx(sd + o + Ls, ff::csub(y0[r], y1[r]));
+    }
+    __syncthreads();
+}
+
+// Stockham radix-4 stage with sub-length Ls.  Twiddles come from this
+// stage's slice of the per-stage table: stw[(q - 1) Ls + k] = W_{4Ls}^{k q}
+// (= W_L^{k q L / (4 Ls)}), so lanes with consecutive k read consecutive
+// entries (no shared-memory bank conflicts, unlike strided reads of one
+// W_L table).
+__device__ __forceinline__ void stage_r4(float4 *sd, const float4 *stw, int log2L, int Ls, bool inv) {
+    const int L = 1 << log2L, q4 = L >> 2;
+    cplx Y[kFftBpt][4];
+    int base_c[kFftBpt], jj[kFftBpt];
+#pragma unroll
+    for (int r = 0; r < kFftBpt; ++r) {
+        const int bidx = threadIdx.x + r * kFftThreads;
+        const int c = bidx >> (log2L - 2), j = bidx & (q4 - 1);
+        base_c[r] = c << log2L;
+        jj[r] = j;
+        cplx x[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) x[q] = ld_cplx(sd + base_c[r] + j + q * q4);
+        if (Ls > 1) {
+            const int k = j & (Ls - 1);
+#pragma unroll
+            for (int q = 1; q < 4; ++q) x[q] = ff::cmul(x[q], twiddle(stw, (q - 1) * Ls + k, inv));
+        }
+        const cplx a0 = ff::cadd(x[0], x[2]), a1 = ff::csub(x[0], x[2]);
+        const cplx b0 = ff::cadd(x[1], x[3]), b1 = ff::csub(x[1], x[3]);
+        const cplx rb1 = inv ? ff::mul_pos_i(b1) : ff::mul_neg_i(b1);
+        Y[r][0] = ff::cadd(a0, b0);
+        Y[r][2] = ff::csub(a0, b0);
+        Y[r][1] = ff::cadd(a1, rb1);
+        Y[r][3] = ff::csub(a1, rb1);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kFftBpt; ++r) {
+        const int j = jj[r], k = j & (Ls - 1);
+        const int o = base_c[r] + (j - k) * 4 + k;
+#pragma unroll
+        for (int p = 0; p < 4; ++p) st_cplx(sd + o + p * Ls, Y[r][p]);
+    }
+    __syncthreads();
+}
+
+// A radix-2 stage (Ls = 1, no twiddles) first when log2 L is odd, then
+// radix-4 stages; stw holds the radix-4 stages' twiddle slices in order.
+__device__ void fft_in_smem(float4 *sd, const float4 *stw, int log2L, bool inv) {
+    int Ls = 1;
+    if (log2L & 1) {
+        stage_r2(sd, stw, log2L, 1, inv);
+        Ls = 2;
+    }
+    for (; Ls < (1 << log2L); Ls *= 4) {
+        stage_r4(sd, stw, log2L, Ls, inv);
+        if (Ls > 1) stw += 3 * Ls;
+    }
+}
+
+// the same, for odd log2 L, when the radix-2 stage has already been done
+__device__ void fft_in_smem_after_r2(float4 *sd, const float4 *stw, int log2L, bool inv) {
+    for (int Ls = 2; Ls < (1 << log2L); Ls *= 4) {
+        stage_r4(sd, stw, log2L, Ls, inv);
+        stw += 3 * Ls;
+    }
+}
+
+// entries of the per-stage twiddle table of a length-2^log2L transform
+__host__ __device__ __forceinline__ int stage_table_count(int log2L) {
+    return log2L < 3 ? 0 : (1 << log2L) - ((log2L & 1) ? 2 : 4);
+}
+
+// largest biased exponent among the 64-bit words [x0, x1) of p (stride
+// `step` between a thread's 16-byte loads, four loads in flight per thread);
+// kNonFiniteExpo (0x7ff, above every finite exponent) if any word is a NaN or
+// an infinity
+__device__ __forceinline__ int max_exponent(const ulonglong2 *p, long long x0, long long x1, long long step) {
+    int m = 0;
+    auto ex = [](unsigned long long w) { return (int)((w >> 52) & 0x7ffu); };
+    long long x = x0;
+    for (; x + 3 * step < x1; x += 4 * step) {
+        ulonglong2 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = p[x + u * step];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) m = max(m, max(ex(v[u].x), ex(v[u].y)));
+    }
+    for (; x < x1; x += step) {
+        const ulonglong2 v = p[x];
+        m = max(m, max(ex(v.x), ex(v.y)));
+    }
+    return m;
+}
+
+// ------------------------------------------------- grouped transforms
+// A CTA's worth of work in a batch of transforms of different lengths:
+// mode 0: `count` whole transforms of length 2^log2L (request ids at
+// tlist[first ..]); mode 1 / 2: the four-step column / row pass of request
+// `first` starting at column / row c0.
+struct FftItem {
+    int mode, log2L, first, count, c0, pad0, pad1, pad2;
+};
+struct FftGroupReq {
+    const double *in;
+    double *out;
+    float4 *mid;
+    const float4 *tw, *tw_n1, *tw_n2, *tw_hi, *tw_lo;
+    int log2n, log2n1, log2n2, inverse;
+};
+
+__device__ __forceinline__ int scale_from(int e) { return e == 0 ? 0 : e - 1023 + 1; }
+
+// One work item of a group of transforms (grouped launches and the device-
+// resident serving loop alike): mode 0, `count` whole transforms of length
+// 2^log2L (request ids at tlist[first ..]); mode 1 / 2, the four-step column /
+// row pass of request `first` starting at column / row c0.  512 threads; sd
+// holds kFftElems values, stw the pass's per-stage twiddle table.
+__device__ __forceinline__ void fft_group_item(const FftItem &item, const FftGroupReq *reqs, const int *tlist,
+                                               const int *expo, float4 *sd, float4 *stw) {
+    const int log2L = item.log2L, L = 1 << log2L;
+    const int C = kFftElems >> log2L;
+    const FftGroupReq &R0 = reqs[item.mode == 0 ? tlist[item.first] : item.first];
+    const float4 *tw = item.mode == 0 ? R0.tw : (item.mode == 1 ? R0.tw_n1 : R0.tw_n2);
+    const bool inv = R0.inverse != 0;
+    __syncthreads();  // previous item's shared-memory reads are done
+    for (int t = threadIdx.x; t < stage_table_count(log2L); t += kFftThreads) stw[t] = tw[t];
+    const int N1 = 1 << R0.log2n1, N2 = 1 << R0.log2n2;
+    // ---- load
+    for (int q = threadIdx.x; q < kFftElems; q += kFftThreads) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        int c, t;
+        if (item.mode == 1) {
+            c = q & (C - 1);
+            t = q >> (31 - __clz(C));
+        } else {
+            c = q >> log2L;
+            t = q & (L - 1);
+        }
+        if (item.mode == 0) {
+            if (c < item.count) {
+                const int r = tlist[item.first + c];
+                const double2 x = reinterpret_cast<const double2 *>(reqs[r].in)[t];
+                const int S = scale_from(expo[r]);
+                split_scaled(x.x, S, v.x, v.y);
+                split_scaled(x.y, S, v.z, v.w);
+            }
+        } else if (item.mode == 1) {
+            const int S = scale_from(expo[item.first]);
+            const double2 x = reinterpret_cast<const double2 *>(R0.in)[(long long)t * N2 + item.c0 + c];
+            split_scaled(x.x, S, v.x, v.y);
+            split_scaled(x.y, S, v.z, v.w);
+        } else {
+            v = R0.mid[(long long)(item.c0 + c) * N2 + t];
+        }
+        sd[(c << log2L) + t] = v;
+    }
+    __syncthreads();
+    fft_in_smem(sd, stw, log2L, inv);
+    // ---- store
+    for (int q = threadIdx.x; q < kFftElems; q += kFftThreads) {
+        int c, t;
+        if (item.mode == 0) {
+            c = q >> log2L;
+            t = q & (L - 1);
+        } else {
+            c = q & (C - 1);
+            t = q >> (31 - __clz(C));
+        }
+        cplx v = ld_cplx(sd + (c << log2L) + t);
+        if (item.mode == 1) {
+            const long long m = (long long)t * (item.c0 + c);
+            const int mh = (int)(m >> kTwSplit), ml = (int)(m & ((1 << kTwSplit) - 1));
+            cplx w = ff::cmul(ld_cplx(R0.tw_hi + mh), ld_cplx(R0.tw_lo + ml));
+            if (inv) w = ff::conj(w);
+            st_cplx(R0.mid + (long long)t * N2 + item.c0 + c, ff::cmul(v, w));
+        } else if (item.mode == 0) {
+            if (c >= item.count) continue;
+            const int r = tlist[item.first + c];
+            const int S = scale_from(expo[r]) - (inv ? log2L : 0);
+            double2 y = make_double2(widen_scaled(v.rh, v.rl, S), widen_scaled(v.ih, v.il, S));
+            if (log2L == 0)  // length 1: the transform is the identity, exactly
+                y = reinterpret_cast<const double2 *>(reqs[r].in)[0];
+            else if (expo[r] == kNonFiniteExpo)
+                y = nan2();
+            reinterpret_cast<double2 *>(reqs[r].out)[t] = y;
+        } else {
+            const int S = scale_from(expo[item.first]) - (inv ? R0.log2n : 0);
+            reinterpret_cast<double2 *>(R0.out)[(item.c0 + c) + (long long)N1 * t] =
+                expo[item.first] == kNonFiniteExpo
+                    ? nan2()
+                    : make_double2(widen_scaled(v.rh, v.rl, S), widen_scaled(v.ih, v.il, S));
+        }
+    }
+}
+
+}  // namespace
+}  // namespace oo

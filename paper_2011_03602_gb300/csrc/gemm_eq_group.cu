@@ -38,6 +38,7 @@
 #include "eq_digits.cuh"
 #include "ff.cuh"
 #include "oo_internal.h"
+#include "resident.h"
 #include "tc.cuh"
 
 namespace oo {
@@ -138,237 +139,268 @@ __device__ __forceinline__ void mma_rt(uint32_t d_tmem, uint64_t a, uint64_t b, 
           "=r"(r[15])                                                                                       \
         : "r"(taddr))
 
-template <class Src>
-__device__ __forceinline__ void eq_tiles_body(const GMaps &maps, const GArgs &a, const Src &src) {
+// Shared-memory pipeline of one tile CTA: a 4-stage operand ring, two
+// accumulator buffers in tensor memory, an abort flag.
+struct Pipe {
+    unsigned char *sm;
+    uint64_t *full, *empty, *tfull, *tempty;
+    volatile int *abort_flag;
+    uint32_t tmem;
+};
+
+// Barriers, abort flag and tensor memory of the CTA; `extra` more mbarriers
+// (initialised by the caller) follow the pipeline's.
+__device__ __forceinline__ Pipe pipe_setup(uint64_t **extra_bars) {
     extern __shared__ __align__(1024) unsigned char gsm_raw[];
-    unsigned char *sm = reinterpret_cast<unsigned char *>(
-        (reinterpret_cast<uintptr_t>(gsm_raw) + 1023) & ~static_cast<uintptr_t>(1023));
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + kStages * kStageBytes);
-    uint64_t *full = bars, *empty = bars + kStages;
-    uint64_t *tfull = bars + 2 * kStages, *tempty = bars + 2 * kStages + 2;
+    Pipe pp;
+    pp.sm = reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(gsm_raw) + 1023) &
+                                              ~static_cast<uintptr_t>(1023));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(pp.sm + kStages * kStageBytes);
+    pp.full = bars;
+    pp.empty = bars + kStages;
+    pp.tfull = bars + 2 * kStages;
+    pp.tempty = bars + 2 * kStages + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(bars + 2 * kStages + 4);
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
-
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tiles = src.count();
-
+    pp.abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    // 16-byte aligned (8 mbarriers then 16-byte entries follow there)
+    if (extra_bars) *extra_bars = reinterpret_cast<uint64_t *>(tmem_slot + 4);
+    const int warp = threadIdx.x >> 5;
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
-            bar_init(su32(&full[s]), 1);
-            bar_init(su32(&empty[s]), 1);
+            bar_init(su32(&pp.full[s]), 1);
+            bar_init(su32(&pp.empty[s]), 1);
         }
         for (int b = 0; b < 2; ++b) {
-            bar_init(su32(&tfull[b]), 1);
-            bar_init(su32(&tempty[b]), kEpiWarps);
+            bar_init(su32(&pp.tfull[b]), 1);
+            bar_init(su32(&pp.tempty[b]), kEpiWarps);
         }
-        *abort_flag = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        *pp.abort_flag = 0;
     }
     if (warp == 1) {
         tmem_alloc(su32(tmem_slot), 512);
         fence_before();
     }
-    __syncthreads();
-    fence_after();
-    const uint32_t tmem = *tmem_slot;
+    return pp;
+}
 
-    int loaded = 0;     // producer: stages issued
-    int units_mma = 0;  // MMA issuer: units whose accumulation was issued
-    if (warp == 0 && lane == 0) {
-        // ---------------------------------------------------- TMA producer
-        int it = 0;
-        bool ok = true;
-        for (int t = blockIdx.x; ok && t < tiles; t += gridDim.x) {
-            const int4 td = src.tile(t);
-            const GProb &P = src.prob(td.x);
-            const SchemeTab &S = a.sch[P.scheme];
-            const CUtensorMap *ma = &maps.a[P.cls], *mb = &maps.b[P.cls];
-            const int nbox = td.w / kBRows;
-            const uint32_t btile = (uint32_t)td.w * kBK * 2;
-            for (int kbi = 0; ok && kbi < P.nkb; ++kbi) {
-                const int ks0 = kbi * P.kb_steps, ks1 = min(P.ksteps, ks0 + P.kb_steps);
-                for (int u = 0; ok && u < S.nunits; ++u) {
-                    for (int tt = S.ut0[u]; ok && tt < S.ut0[u] + S.unt[u]; ++tt) {
-                        const int p = S.tp[tt], qL = S.tqL[tt], qR = S.tqR[tt];
-                        const int rowA = P.ra + p * P.m + td.y;
-                        const int rowL = P.rb + (qL == kNone ? 0 : qL) * P.n + td.z;
-                        const int rowR = P.rb + (qR == kNone ? 0 : qR) * P.n + td.z;
-                        const uint32_t bytes = kTileA + (uint32_t)((qL != kNone) + (qR != kNone)) * btile;
-                        for (int ks = ks0; ks < ks1; ++ks, ++it) {
-                            const int s = it % kStages;
-                            const uint32_t use = it / kStages;
-                            if (use > 0 && !bar_wait(su32(&empty[s]), (use - 1) & 1, abort_flag, a.err, 1u)) {
-                                ok = false;
-                                break;
-                            }
-                            unsigned char *st = sm + (size_t)s * kStageBytes;
-                            const uint32_t fb = su32(&full[s]);
-                            bar_expect_tx(fb, bytes);
-                            tma_2d(su32(st), ma, ks * kBK, rowA, fb);
-                            if (qL != kNone)
-                                for (int j = 0; j < nbox; ++j)
-                                    tma_2d(su32(st + kTileA + j * kBox), mb, ks * kBK, rowL + j * kBRows, fb);
-                            if (qR != kNone)
-                                for (int j = 0; j < nbox; ++j)
-                                    tma_2d(su32(st + kTileA + btile + j * kBox), mb, ks * kBK, rowR + j * kBRows, fb);
-                            ++loaded;
-                        }
-                    }
-                }
-            }
-        }
-    } else if (warp == 1 && lane == 0) {
-        // ---------------------------------------------------- MMA issuer
-        int it = 0, gu = 0;
-        bool ok = true;
-        for (int t = blockIdx.x; ok && t < tiles; t += gridDim.x) {
-            const int4 td = src.tile(t);
-            const GProb &P = src.prob(td.x);
-            const SchemeTab &S = a.sch[P.scheme];
-            const uint32_t btile = (uint32_t)td.w * kBK * 2;
-            const uint32_t id_pair = idesc_n(2 * td.w), id_one = idesc_n(td.w);
-            for (int kbi = 0; ok && kbi < P.nkb; ++kbi) {
-                const int ks0 = kbi * P.kb_steps, ks1 = min(P.ksteps, ks0 + P.kb_steps);
-                for (int u = 0; ok && u < S.nunits; ++u, ++gu) {
-                    const int b = gu & 1;
-                    const uint32_t buse = gu >> 1;
-                    if (buse > 0 && !bar_wait(su32(&tempty[b]), (buse - 1) & 1, abort_flag, a.err, 2u)) {
-                        ok = false;
-                        break;
-                    }
-                    fence_after();
-                    const uint32_t d = tmem + (uint32_t)(b * 256);
-                    bool first = true;
-                    for (int tt = S.ut0[u]; ok && tt < S.ut0[u] + S.unt[u]; ++tt) {
-                        const int qL = S.tqL[tt], qR = S.tqR[tt];
-                        for (int ks = ks0; ks < ks1; ++ks, ++it) {
-                            const int s = it % kStages;
-                            if (!bar_wait(su32(&full[s]), (it / kStages) & 1, abort_flag, a.err, 2u)) {
-                                ok = false;
-                                break;
-                            }
-                            fence_after();
-                            const uint32_t sa = su32(sm + (size_t)s * kStageBytes);
-                            const uint32_t sbL = sa + kTileA, sbR = sbL + btile;
-#pragma unroll
-                            for (int kk = 0; kk < kBK / 16; ++kk) {
-                                const uint32_t off = kk * 32;  // 16 BF16 along K inside the 128-byte row
-                                const uint32_t acc = first ? 0u : 1u;
-                                if (qL != kNone && qR != kNone)  // both halves: B_qL and B_qR stacked
-                                    mma_rt(d, sdesc_sw128(sa + off), sdesc_sw128(sbL + off), id_pair, acc);
-                                else if (qL != kNone)
-                                    mma_rt(d, sdesc_sw128(sa + off), sdesc_sw128(sbL + off), id_one, acc);
-                                else
-                                    mma_rt(d + (uint32_t)td.w, sdesc_sw128(sa + off), sdesc_sw128(sbR + off), id_one,
-                                           acc);
-                                first = false;
-                            }
-                            mma_commit(su32(&empty[s]));
-                        }
-                    }
-                    if (!ok) break;
-                    mma_commit(su32(&tfull[b]));  // this unit's accumulator pair is complete
-                    ++units_mma;
-                }
-            }
-        }
-    } else if (warp >= 2) {
-        // ---------------------------------------------------- epilogue
-        const int q = warp & 3;         // TMEM lane quarter this warp may access
-        const int h = (warp - 2) >> 2;  // which half of the tile's columns
-        const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-        float Sh[64], Sl[64];           // running float-float sum of this row's columns
-        int gu = 0;
-        bool ok = true;
-        for (int t = blockIdx.x; ok && t < tiles; t += gridDim.x) {
-            const int4 td = src.tile(t);
-            const GProb &P = src.prob(td.x);
-            const SchemeTab &S = a.sch[P.scheme];
-            const int cpw = td.w >> 1, cw0 = h * cpw;  // columns per warp, first column of this warp
-            const int row0 = td.y + q * 32;
-            const int ncols = min(cpw, P.n - td.z - cw0);
-            const bool active = row0 < P.m && ncols > 0;  // warp-uniform
-            const int units = P.nkb * S.nunits;
-            for (int uu = 0; uu < units; ++uu, ++gu) {
-                const int b = gu & 1;
-                if (!bar_wait(su32(&tfull[b]), (gu >> 1) & 1, abort_flag, a.err, 4u)) {
-                    ok = false;
-                    break;
-                }
-                fence_after();
-                const int u = uu % S.nunits;
-                const float fL = S.usL[u], fR = S.usR[u];
-                if (active) {
-                    const uint32_t acc = tmem + (uint32_t)(b * 256) + lane_off + (uint32_t)cw0;
-#pragma unroll
-                    for (int c = 0; c < 64; c += 16) {
-                        if (c < ncols) {
-                            uint32_t v[16];
-                            OO_TMEM_LD16(acc + c, v);
-                            tmem_wait_ld();
-#pragma unroll
-                            for (int j = 0; j < 16; ++j) {
-                                const float w = __fmul_rn(__uint_as_float(v[j]), fL);  // exact: power of two
-                                if (uu == 0) {
-                                    Sh[c + j] = w;
-                                    Sl[c + j] = 0.0f;
-                                } else {
-                                    ff::add(Sh[c + j], Sl[c + j], w, 0.0f, Sh[c + j], Sl[c + j]);
-                                }
-                            }
-                            if (fR != 0.0f) {
-                                OO_TMEM_LD16(acc + (uint32_t)td.w + c, v);
-                                tmem_wait_ld();
-#pragma unroll
-                                for (int j = 0; j < 16; ++j) {
-                                    const float w = __fmul_rn(__uint_as_float(v[j]), fR);
-                                    ff::add(Sh[c + j], Sl[c + j], w, 0.0f, Sh[c + j], Sl[c + j]);
-                                }
-                            }
-                        }
-                    }
-                }
-                fence_before();
-                __syncwarp();
-                if (lane == 0) bar_arrive(su32(&tempty[b]));
-            }
-            if (!ok) break;
-            if (active) {
-                // column scales: lane l holds columns l and l + 32 of this
-                // warp's range and hands them out by shuffle
-                const int row = row0 + lane;
-                const int c0 = td.z + cw0;
-                const int e0 = lane < ncols ? P.eb[c0 + lane] : 0;
-                const int e1 = 32 + lane < ncols ? P.eb[c0 + 32 + lane] : 0;
-                const bool row_ok = row < P.m;
-                const int sa = row_ok ? P.ea[row] : 0;
-                double *crow = P.C + (long long)row * P.ldc + c0;
-#pragma unroll
-                for (int j = 0; j < 64; ++j) {
-                    if (j < ncols) {
-                        const int sb = __shfl_sync(0xffffffffu, j < 32 ? e0 : e1, j & 31);
-                        if (row_ok) crow[j] = nan_or_scaled(ff::to_double(Sh[j], Sl[j]), sa + sb);
-                    }
+// TMA producer (one thread): the operand loads of one tile; false when the
+// pipeline aborted
+__device__ __forceinline__ bool produce_tile(const GMaps &maps, const GArgs &a, const Pipe &pp, const GProb &P,
+                                             const int4 td, int &it, int &loaded) {
+    const SchemeTab &S = a.sch[P.scheme];
+    const CUtensorMap *ma = &maps.a[P.cls], *mb = &maps.b[P.cls];
+    const int nbox = td.w / kBRows;
+    const uint32_t btile = (uint32_t)td.w * kBK * 2;
+    for (int kbi = 0; kbi < P.nkb; ++kbi) {
+        const int ks0 = kbi * P.kb_steps, ks1 = min(P.ksteps, ks0 + P.kb_steps);
+        for (int u = 0; u < S.nunits; ++u) {
+            for (int tt = S.ut0[u]; tt < S.ut0[u] + S.unt[u]; ++tt) {
+                const int p = S.tp[tt], qL = S.tqL[tt], qR = S.tqR[tt];
+                const int rowA = P.ra + p * P.m + td.y;
+                const int rowL = P.rb + (qL == kNone ? 0 : qL) * P.n + td.z;
+                const int rowR = P.rb + (qR == kNone ? 0 : qR) * P.n + td.z;
+                const uint32_t bytes = kTileA + (uint32_t)((qL != kNone) + (qR != kNone)) * btile;
+                for (int ks = ks0; ks < ks1; ++ks, ++it) {
+                    const int s = it % kStages;
+                    const uint32_t use = it / kStages;
+                    if (use > 0 && !bar_wait(su32(&pp.empty[s]), (use - 1) & 1, pp.abort_flag, a.err, 1u))
+                        return false;
+                    unsigned char *st = pp.sm + (size_t)s * kStageBytes;
+                    const uint32_t fb = su32(&pp.full[s]);
+                    bar_expect_tx(fb, bytes);
+                    tma_2d(su32(st), ma, ks * kBK, rowA, fb);
+                    if (qL != kNone)
+                        for (int j = 0; j < nbox; ++j)
+                            tma_2d(su32(st + kTileA + j * kBox), mb, ks * kBK, rowL + j * kBRows, fb);
+                    if (qR != kNone)
+                        for (int j = 0; j < nbox; ++j)
+                            tma_2d(su32(st + kTileA + btile + j * kBox), mb, ks * kBK, rowR + j * kBRows, fb);
+                    ++loaded;
                 }
             }
         }
     }
-    // drain on abort: wait (bounded) for issued MMAs and copies before TMEM
-    // is released and the CTA exits
-    if (*abort_flag) {
+    return true;
+}
+
+// MMA issuer (one thread): every unit of one tile into the accumulator
+// buffers; false when the pipeline aborted
+__device__ __forceinline__ bool mma_tile(const GArgs &a, const Pipe &pp, const GProb &P, const int4 td, int &it,
+                                         int &gu, int &units_mma) {
+    const SchemeTab &S = a.sch[P.scheme];
+    const uint32_t btile = (uint32_t)td.w * kBK * 2;
+    const uint32_t id_pair = idesc_n(2 * td.w), id_one = idesc_n(td.w);
+    for (int kbi = 0; kbi < P.nkb; ++kbi) {
+        const int ks0 = kbi * P.kb_steps, ks1 = min(P.ksteps, ks0 + P.kb_steps);
+        for (int u = 0; u < S.nunits; ++u, ++gu) {
+            const int b = gu & 1;
+            const uint32_t buse = gu >> 1;
+            if (buse > 0 && !bar_wait(su32(&pp.tempty[b]), (buse - 1) & 1, pp.abort_flag, a.err, 2u)) return false;
+            fence_after();
+            const uint32_t d = pp.tmem + (uint32_t)(b * 256);
+            bool first = true;
+            for (int tt = S.ut0[u]; tt < S.ut0[u] + S.unt[u]; ++tt) {
+                const int qL = S.tqL[tt], qR = S.tqR[tt];
+                for (int ks = ks0; ks < ks1; ++ks, ++it) {
+                    const int s = it % kStages;
+                    if (!bar_wait(su32(&pp.full[s]), (it / kStages) & 1, pp.abort_flag, a.err, 2u)) return false;
+                    fence_after();
+                    const uint32_t sa = su32(pp.sm + (size_t)s * kStageBytes);
+                    const uint32_t sbL = sa + kTileA, sbR = sbL + btile;
+#pragma unroll
+                    for (int kk = 0; kk < kBK / 16; ++kk) {
+                        const uint32_t off = kk * 32;  // 16 BF16 along K inside the 128-byte row
+                        const uint32_t acc = first ? 0u : 1u;
+                        if (qL != kNone && qR != kNone)  // both halves: B_qL and B_qR stacked
+                            mma_rt(d, sdesc_sw128(sa + off), sdesc_sw128(sbL + off), id_pair, acc);
+                        else if (qL != kNone)
+                            mma_rt(d, sdesc_sw128(sa + off), sdesc_sw128(sbL + off), id_one, acc);
+                        else
+                            mma_rt(d + (uint32_t)td.w, sdesc_sw128(sa + off), sdesc_sw128(sbR + off), id_one, acc);
+                        first = false;
+                    }
+                    mma_commit(su32(&pp.empty[s]));
+                }
+            }
+            mma_commit(su32(&pp.tfull[b]));  // this unit's accumulator pair is complete
+            ++units_mma;
+        }
+    }
+    return true;
+}
+
+// One epilogue warp (of eight: lane quarter q = warp & 3, column half h):
+// add every finished unit of one tile, scaled by its power of two, into a
+// float-float running sum (Sh, Sl) of this row's columns, then write FP64
+// C; false when the pipeline aborted
+__device__ __forceinline__ bool epilogue_tile(const GArgs &a, const Pipe &pp, const GProb &P, const int4 td, int &gu,
+                                              float (&Sh)[64], float (&Sl)[64]) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int q = warp & 3;         // TMEM lane quarter this warp may access
+    const int h = (warp - 2) >> 2;  // which half of the tile's columns
+    const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+    const SchemeTab &S = a.sch[P.scheme];
+    const int cpw = td.w >> 1, cw0 = h * cpw;  // columns per warp, first column of this warp
+    const int row0 = td.y + q * 32;
+    const int ncols = min(cpw, P.n - td.z - cw0);
+    const bool active = row0 < P.m && ncols > 0;  // warp-uniform
+    const int units = P.nkb * S.nunits;
+    for (int uu = 0; uu < units; ++uu, ++gu) {
+        const int b = gu & 1;
+        if (!bar_wait(su32(&pp.tfull[b]), (gu >> 1) & 1, pp.abort_flag, a.err, 4u)) return false;
+        fence_after();
+        const int u = uu % S.nunits;
+        const float fL = S.usL[u], fR = S.usR[u];
+        if (active) {
+            const uint32_t acc = pp.tmem + (uint32_t)(b * 256) + lane_off + (uint32_t)cw0;
+#pragma unroll
+            for (int c = 0; c < 64; c += 16) {
+                if (c < ncols) {
+                    uint32_t v[16];
+                    OO_TMEM_LD16(acc + c, v);
+                    tmem_wait_ld();
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const float w = __fmul_rn(__uint_as_float(v[j]), fL);  // exact: power of two
+                        if (uu == 0) {
+                            Sh[c + j] = w;
+                            Sl[c + j] = 0.0f;
+                        } else {
+                            ff::add(Sh[c + j], Sl[c + j], w, 0.0f, Sh[c + j], Sl[c + j]);
+                        }
+                    }
+                    if (fR != 0.0f) {
+                        OO_TMEM_LD16(acc + (uint32_t)td.w + c, v);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const float w = __fmul_rn(__uint_as_float(v[j]), fR);
+                            ff::add(Sh[c + j], Sl[c + j], w, 0.0f, Sh[c + j], Sl[c + j]);
+                        }
+                    }
+                }
+            }
+        }
+        fence_before();
+        __syncwarp();
+        if (lane == 0) bar_arrive(su32(&pp.tempty[b]));
+    }
+    if (active) {
+        // column scales: lane l holds columns l and l + 32 of this warp's
+        // range and hands them out by shuffle
+        const int row = row0 + lane;
+        const int c0 = td.z + cw0;
+        const int e0 = lane < ncols ? P.eb[c0 + lane] : 0;
+        const int e1 = 32 + lane < ncols ? P.eb[c0 + 32 + lane] : 0;
+        const bool row_ok = row < P.m;
+        const int sa = row_ok ? P.ea[row] : 0;
+        double *crow = P.C + (long long)row * P.ldc + c0;
+#pragma unroll
+        for (int j = 0; j < 64; ++j) {
+            if (j < ncols) {
+                const int sb = __shfl_sync(0xffffffffu, j < 32 ? e0 : e1, j & 31);
+                if (row_ok) crow[j] = nan_or_scaled(ff::to_double(Sh[j], Sl[j]), sa + sb);
+            }
+        }
+    }
+    return true;
+}
+
+// drain on abort: wait (bounded) for issued MMAs and copies before tensor
+// memory is released and the CTA exits
+__device__ __forceinline__ void pipe_teardown(const Pipe &pp, int loaded, int units_mma) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (*pp.abort_flag) {
         if (warp == 1 && lane == 0 && units_mma > 0)
-            bar_drain(su32(&tfull[(units_mma - 1) & 1]), ((units_mma - 1) >> 1) & 1);
+            bar_drain(su32(&pp.tfull[(units_mma - 1) & 1]), ((units_mma - 1) >> 1) & 1);
         if (warp == 0 && lane == 0)
             for (int it = (loaded > kStages ? loaded - kStages : 0); it < loaded; ++it)
-                bar_drain(su32(&full[it % kStages]), (it / kStages) & 1);
+                bar_drain(su32(&pp.full[it % kStages]), (it / kStages) & 1);
     }
     fence_before();
     __syncthreads();
     if (warp == 1) {
         fence_after();
-        tmem_dealloc(tmem, 512);
+        tmem_dealloc(pp.tmem, 512);
     }
+}
+
+template <class Src>
+__device__ __forceinline__ void eq_tiles_body(const GMaps &maps, const GArgs &a, const Src &src) {
+    Pipe pp = pipe_setup(nullptr);
+    if (threadIdx.x == 0) {
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    fence_after();
+    pp.tmem = *reinterpret_cast<uint32_t *>(pp.tempty + 2);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tiles = src.count();
+    int loaded = 0;     // producer: stages issued
+    int units_mma = 0;  // MMA issuer: units whose accumulation was issued
+    if (warp == 0 && lane == 0) {
+        int it = 0;
+        for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+            const int4 td = src.tile(t);
+            if (!produce_tile(maps, a, pp, src.prob(td.x), td, it, loaded)) break;
+        }
+    } else if (warp == 1 && lane == 0) {
+        int it = 0, gu = 0;
+        for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+            const int4 td = src.tile(t);
+            if (!mma_tile(a, pp, src.prob(td.x), td, it, gu, units_mma)) break;
+        }
+    } else if (warp >= 2) {
+        float Sh[64], Sl[64];
+        int gu = 0;
+        for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+            const int4 td = src.tile(t);
+            if (!epilogue_tile(a, pp, src.prob(td.x), td, gu, Sh, Sl)) break;
+        }
+    }
+    pipe_teardown(pp, loaded, units_mma);
 }
 
 __global__ void __launch_bounds__(kThreads, 1) gemm_eq_group_kernel(const __grid_constant__ GMaps maps,
@@ -384,6 +416,184 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_eq_single_kernel(const __gri
                                                                     const __grid_constant__ GProb P) {
     const SingleTiles src{&P};
     eq_tiles_body(maps, a, src);
+}
+
+// ------------------------------------------------ the device-resident loop
+// One GEMM request of the resident serving loop (resident.h): its tile
+// descriptor, the split entry its tiles wait for, and its completion count
+// (eight epilogue warps per tile).
+struct ResTileDesc {
+    GProb P;
+    uint32_t split_ctr, split_target;
+    uint32_t done_ctr, done_target;
+    uint32_t gen;
+    int32_t slot, pad0, pad1;
+};
+constexpr int kTileNop = -1, kTileStop = -2;
+struct ResTileArgs {
+    const int4 *ring;          // res::kRingCap entries (request slot, m0, n0, width); slot kTileNop / kTileStop
+    const ResTileDesc *desc;   // res::kSlots
+    unsigned *ctr;             // entry counters (res::kRingCap) then one per request slot
+    const unsigned *heartbeat; // incremented by the SIMT worker for every entry a CTA passes
+    res::Ctl *ctl;             // mapped control block (device address)
+    unsigned long long start;  // first tile entry of this launch
+};
+
+__device__ __forceinline__ unsigned long long ld_acquire_sys64(const volatile unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned ld_acquire_gpu32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_sys32(volatile unsigned *p, unsigned v) {
+    asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Persistent tensor-core worker of the resident loop: CTA c takes tile
+// entries start + c, start + c + CTAs, ...  Its producer thread waits (bounded)
+// for each entry's publication and for the request's split, then forwards the
+// entry through a four-deep shared-memory queue to the MMA issuer and the
+// epilogue warps (keep-alive entries too, so that no role's wait runs out
+// while the server idles) and loads the tile as the grouped kernel does.
+// The epilogue counts finished tiles; the warp that finishes a request
+// writes its generation into the control block.
+__global__ void __launch_bounds__(kThreads, 1) resident_tiles_kernel(const __grid_constant__ GMaps maps,
+                                                                    const __grid_constant__ GArgs a,
+                                                                    const __grid_constant__ ResTileArgs r) {
+    uint64_t *xb = nullptr;
+    Pipe pp = pipe_setup(&xb);
+    uint64_t *qfull = xb, *qempty = xb + 4;
+    int4 *tq = reinterpret_cast<int4 *>(xb + 8);
+    if (threadIdx.x == 0) {
+        for (int f = 0; f < 4; ++f) {
+            bar_init(su32(&qfull[f]), 1);
+            bar_init(su32(&qempty[f]), 1 + kEpiWarps);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    fence_after();
+    pp.tmem = *reinterpret_cast<uint32_t *>(pp.tempty + 2);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int loaded = 0, units_mma = 0;
+    if (threadIdx.x == 0) r.ctl->alive[res::kMaxCtas + blockIdx.x] = 1u;
+    if (warp == 0 && lane == 0) {
+        // ---------------------------------------------------- producer
+        int it = 0;
+        unsigned long long seen = 0, fi = 0;  // fi: entries forwarded to the queue
+        auto forward = [&](int4 td) {
+            const int f = (int)(fi & 3);
+            if (fi >= 4 && !bar_wait(su32(&qempty[f]), (uint32_t)((fi >> 2) - 1) & 1, pp.abort_flag, a.err, 512u))
+                return false;
+            tq[f] = td;
+            bar_arrive(su32(&qfull[f]));
+            ++fi;
+            return true;
+        };
+        for (unsigned long long i = 0;; ++i) {
+            const unsigned long long t = r.start + blockIdx.x + i * gridDim.x;
+            int4 td = make_int4(kTileStop, 0, 0, 0);
+            bool ok = true;
+            if (seen <= t) {
+                const long long t0 = clock64();
+                while ((seen = ld_acquire_sys64(&r.ctl->pub_tiles)) <= t) {
+                    if (*pp.abort_flag || clock64() - t0 > kWaitLimit) {
+                        *pp.abort_flag = 1;
+                        atomicOr(a.err, 8u);
+                        ok = false;
+                        break;
+                    }
+                }
+            }
+            if (ok) {
+                td = __ldcg(&r.ring[t % res::kRingCap]);
+                r.ctl->tile_progress[blockIdx.x] = t + gridDim.x;  // this CTA's next entry
+                if (td.x >= 0) {
+                    // The request's digit slices must be complete before they
+                    // are loaded (and seen by the async proxy).  Its split entry
+                    // may wait behind other requests' SIMT work, so the bound
+                    // is on the SIMT worker making no progress at all (its
+                    // heartbeat counter), not on the time waited; meanwhile
+                    // keep-alive markers keep the other roles' waits short.
+                    const ResTileDesc &D = r.desc[td.x];
+                    long long t0 = clock64(), tk = t0;
+                    unsigned hb = ld_acquire_gpu32(r.heartbeat);
+                    while ((int)(ld_acquire_gpu32(&r.ctr[D.split_ctr]) - D.split_target) < 0) {
+                        const long long now = clock64();
+                        const unsigned h = ld_acquire_gpu32(r.heartbeat);
+                        if (h != hb) {
+                            hb = h;
+                            t0 = now;
+                        }
+                        if (*pp.abort_flag || now - t0 > kWaitLimit) {
+                            *pp.abort_flag = 1;
+                            atomicOr(a.err, 16u);
+                            ok = false;
+                            break;
+                        }
+                        if (now - tk > kWaitLimit / 8) {
+                            if (!forward(make_int4(kTileNop, 0, 0, 0))) {
+                                ok = false;
+                                break;
+                            }
+                            tk = now;
+                        }
+                    }
+                    asm volatile("fence.proxy.async.global;" ::: "memory");
+                }
+            }
+            if (!ok) td.x = kTileStop;
+            // forward the entry to the MMA issuer and the epilogue
+            if (!forward(td)) break;
+            if (td.x == kTileStop) break;
+            if (td.x < 0) continue;
+            if (!produce_tile(maps, a, pp, r.desc[td.x].P, td, it, loaded)) break;
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------------------------------------------- MMA issuer
+        int it = 0, gu = 0;
+        for (unsigned long long i = 0;; ++i) {
+            const int f = (int)(i & 3);
+            if (!bar_wait(su32(&qfull[f]), (uint32_t)(i >> 2) & 1, pp.abort_flag, a.err, 128u)) break;
+            const int4 td = tq[f];
+            bar_arrive(su32(&qempty[f]));
+            if (td.x == kTileStop) break;
+            if (td.x < 0) continue;
+            if (!mma_tile(a, pp, r.desc[td.x].P, td, it, gu, units_mma)) break;
+        }
+    } else if (warp >= 2) {
+        // ---------------------------------------------------- epilogue
+        float Sh[64], Sl[64];
+        int gu = 0;
+        for (unsigned long long i = 0;; ++i) {
+            const int f = (int)(i & 3);
+            if (!bar_wait(su32(&qfull[f]), (uint32_t)(i >> 2) & 1, pp.abort_flag, a.err, 256u)) break;
+            const int4 td = tq[f];
+            __syncwarp();
+            if (lane == 0) bar_arrive(su32(&qempty[f]));
+            if (td.x == kTileStop) break;
+            if (td.x < 0) continue;
+            const ResTileDesc &D = r.desc[td.x];
+            if (!epilogue_tile(a, pp, D.P, td, gu, Sh, Sl)) break;
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence();
+                const unsigned old = atomicAdd(&r.ctr[D.done_ctr], 1u);
+                if (old + 1u == D.done_target) {
+                    __threadfence_system();
+                    st_release_sys32(&r.ctl->done[D.slot], D.gen);
+                }
+            }
+        }
+    }
+    pipe_teardown(pp, loaded, units_mma);
+    if (threadIdx.x == 0 && *pp.abort_flag) r.ctl->fault = 1u;  // a wait ran out: the host stops serving
 }
 
 size_t smem_bytes() { return 1024 + (size_t)kStages * kStageBytes + 256; }
@@ -457,83 +667,16 @@ int table_of(int scheme, int k) {
 int scheme_of_table(int t) { return t <= 1 ? eq::kSchemePairs : (t == 2 ? eq::kSchemeLevel7 : eq::kSchemeLevel6); }
 
 // ----------------------------------------------------------- the split
-struct GSplit {
-    const double *A, *B;
-    long long lda, ldb, pitch;  // pitch: row pitch (elements) of the class's stacked operands
-    int m, n, k, kp, beta, slices;
-    __nv_bfloat16 *As, *Bs;     // row 0 of slice 0 of this problem in its class's arrays
-    int *ea, *eb;
-};
-
-// job (0, problem, first row): eight rows of A, one warp each -> ea and the
-// digit slices (slice p of row r at As[(p m + r) pitch]); job (1, problem,
-// first column): 64 columns of B -> eb (largest exponent over all k) and
-// the transposed slices through 64 x 64 shared-memory tiles.  Zero digits
-// fill [k, kp).
-__global__ void __launch_bounds__(256) eq_group_split_kernel(const GSplit *gs, const int4 *jobs) {
-    const int4 jb = jobs[blockIdx.x];
-    const GSplit &G = gs[jb.y];
-    const int lane = threadIdx.x & 31;
-    if (jb.x == 0) {
-        const int row = jb.z + (threadIdx.x >> 5);
-        if (row >= G.m) return;
-        const double *src = G.A + (long long)row * G.lda;
-        int mx = 0;
-#pragma unroll 4
-        for (int l = lane; l < G.k; l += 32) mx = max(mx, eq::eff_exp(src[l]));
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (lane == 0) G.ea[row] = mx == 0 ? 0 : mx - 1022;
-        const size_t plane2 = (size_t)G.m * G.pitch / 2;
-        __nv_bfloat162 *dst = reinterpret_cast<__nv_bfloat162 *>(G.As + (size_t)row * G.pitch);
-        for (int l2 = lane; l2 < G.kp / 2; l2 += 32) {
-            const int l = 2 * l2;
-            unsigned n0 = 0, n1 = 0;
-            const unsigned long long X0 = (mx != 0 && l < G.k) ? eq::fixed_frac(src[l], mx, n0) : 0ull;
-            const unsigned long long X1 = (mx != 0 && l + 1 < G.k) ? eq::fixed_frac(src[l + 1], mx, n1) : 0ull;
-            for (int p = 0; p < G.slices; ++p)
-                reinterpret_cast<unsigned *>(dst)[p * plane2 + l2] = eq::digit_pair(X0, n0, X1, n1, G.beta, p);
-        }
-        return;
-    }
+// job (0, problem, first row): eight rows of A; job (1, problem, first
+// column): 64 columns of B (eq_digits.cuh)
+__global__ void __launch_bounds__(256) eq_group_split_kernel(const eq::GSplit *gs, const int4 *jobs) {
     __shared__ double t[64][65];
     __shared__ int red[4][64];
-    const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;  // 64 columns x 4 row groups
-    const int col = jb.z + tx;
-    int mx = 0;
-    if (col < G.n)
-#pragma unroll 4
-        for (int l = ty; l < G.k; l += 4) mx = max(mx, eq::eff_exp(G.B[(long long)l * G.ldb + col]));
-    red[ty][tx] = mx;
-    __syncthreads();
-    if (ty == 0) {
-        mx = max(max(red[0][tx], red[1][tx]), max(red[2][tx], red[3][tx]));
-        red[0][tx] = mx;
-        if (col < G.n) G.eb[col] = mx == 0 ? 0 : mx - 1022;
-    }
-    __syncthreads();
-    const int w = threadIdx.x >> 5;
-    const size_t plane2 = (size_t)G.n * G.pitch / 2;
-    for (int l0 = 0; l0 < G.kp; l0 += 64) {
-#pragma unroll 4
-        for (int yy = ty; yy < 64; yy += 4) {
-            const int l = l0 + yy;
-            t[yy][tx] = (l < G.k && col < G.n) ? G.B[(long long)l * G.ldb + col] : 0.0;
-        }
-        __syncthreads();
-        for (int cc = w * 8; cc < w * 8 + 8; ++cc) {
-            const int c = jb.z + cc;
-            if (c >= G.n) break;
-            const int cm = red[0][cc];
-            unsigned n0 = 0, n1 = 0;
-            const unsigned long long X0 = cm != 0 ? eq::fixed_frac(t[2 * lane][cc], cm, n0) : 0ull;
-            const unsigned long long X1 = cm != 0 ? eq::fixed_frac(t[2 * lane + 1][cc], cm, n1) : 0ull;
-            __nv_bfloat162 *dst = reinterpret_cast<__nv_bfloat162 *>(G.Bs + (size_t)c * G.pitch + l0) + lane;
-            for (int p = 0; p < G.slices; ++p)
-                reinterpret_cast<unsigned *>(dst)[p * plane2] = eq::digit_pair(X0, n0, X1, n1, G.beta, p);
-        }
-        __syncthreads();
-    }
+    const int4 jb = jobs[blockIdx.x];
+    if (jb.x == 0)
+        eq::split_rows_job(gs[jb.y], jb.z);
+    else
+        eq::split_cols_job(gs[jb.y], jb.z, t, red);
 }
 
 // 2D BF16 tensor map over rows x pitch (row-major, pitch a multiple of 64),
@@ -618,7 +761,7 @@ struct EqGroup {
     GArgs args{};
     GProb *d_probs = nullptr;
     int4 *d_tiles = nullptr;
-    GSplit *d_split = nullptr;
+    eq::GSplit *d_split = nullptr;
     int4 *d_jobs = nullptr;
     unsigned *d_err = nullptr;
     int ntiles = 0, njobs = 0, grid = 1;
@@ -691,7 +834,7 @@ EqGroup *eq_group_create(const std::vector<GemmDesc> &v, int num_sms, const int 
     const size_t off_probs = at;
     at += up(np * sizeof(GProb), 256);
     const size_t off_split = at;
-    at += up(np * sizeof(GSplit), 256);
+    at += up(np * sizeof(eq::GSplit), 256);
     const size_t off_tiles = at;
     at += up(sorted.size() * sizeof(int4), 256);
     const size_t off_jobs = at;
@@ -712,7 +855,7 @@ EqGroup *eq_group_create(const std::vector<GemmDesc> &v, int num_sms, const int 
             map_slices(&g->maps.b[c], base + off_b[c], rows_b[c], KP[c], kBRows);
         }
         std::vector<GProb> probs(np);
-        std::vector<GSplit> splits(np);
+        std::vector<eq::GSplit> splits(np);
         for (size_t i = 0; i < np; ++i) {
             const GemmDesc &d = v[i];
             const eq::Shape &e = sh[i];
@@ -734,16 +877,16 @@ EqGroup *eq_group_create(const std::vector<GemmDesc> &v, int num_sms, const int 
             P.scheme = tab[i];
             auto *As = reinterpret_cast<__nv_bfloat16 *>(base + off_a[cls[i]]) + (size_t)ra[i] * KP[cls[i]];
             auto *Bs = reinterpret_cast<__nv_bfloat16 *>(base + off_b[cls[i]]) + (size_t)rb[i] * KP[cls[i]];
-            splits[i] = GSplit{d.A, d.B, d.lda, d.ldb, (long long)KP[cls[i]], d.m, d.n, d.k, kp[i], e.beta,
+            splits[i] = eq::GSplit{d.A, d.B, d.lda, d.ldb, (long long)KP[cls[i]], d.m, d.n, d.k, kp[i], e.beta,
                                e.slices, As, Bs, ea, eb};
         }
         OO_CUDA_TRY(cudaMemcpy(base + off_probs, probs.data(), np * sizeof(GProb), cudaMemcpyHostToDevice));
-        OO_CUDA_TRY(cudaMemcpy(base + off_split, splits.data(), np * sizeof(GSplit), cudaMemcpyHostToDevice));
+        OO_CUDA_TRY(cudaMemcpy(base + off_split, splits.data(), np * sizeof(eq::GSplit), cudaMemcpyHostToDevice));
         OO_CUDA_TRY(cudaMemcpy(base + off_tiles, sorted.data(), sorted.size() * sizeof(int4), cudaMemcpyHostToDevice));
         OO_CUDA_TRY(cudaMemcpy(base + off_jobs, jobs.data(), jobs.size() * sizeof(int4), cudaMemcpyHostToDevice));
         OO_CUDA_TRY(cudaMemset(base + off_err, 0, 256));
         g->d_probs = reinterpret_cast<GProb *>(base + off_probs);
-        g->d_split = reinterpret_cast<GSplit *>(base + off_split);
+        g->d_split = reinterpret_cast<eq::GSplit *>(base + off_split);
         g->d_tiles = reinterpret_cast<int4 *>(base + off_tiles);
         g->d_jobs = reinterpret_cast<int4 *>(base + off_jobs);
         g->d_err = reinterpret_cast<unsigned *>(base + off_err);
@@ -915,6 +1058,91 @@ void tune_gemm_tiles(Ctx &c, double *ms_out) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+}
+
+// ------------------------------------------ resident loop: host-side parts
+size_t res_tile_desc_bytes() { return sizeof(ResTileDesc); }
+
+// The tile descriptor of one resident GEMM request: C (m x n, ldc), scale
+// exponents ea / eb, digit slices at rows ra (A) and rb (B) of the slice
+// region (row pitch res::kSlicePitch); its split entry's counter and target;
+// its own completion counter, whose target is base + 8 x tiles.
+void res_tile_desc_fill(void *dst, double *C, long long ldc, const int *ea, const int *eb, int m, int n, int k,
+                        int ra, int rb, unsigned split_ctr, unsigned split_target, unsigned done_ctr,
+                        unsigned done_target, unsigned gen, int slot) {
+    const eq::Shape e = eq::shape(eq_scheme_for(k), k);
+    const int kp = (k + kBK - 1) / kBK * kBK;
+    OO_REQUIRE(kp <= res::kSlicePitch, OO_EINVAL, "inner dimension above the resident slice pitch");
+    ResTileDesc D{};
+    D.P.C = C;
+    D.P.ea = ea;
+    D.P.eb = eb;
+    D.P.ldc = ldc;
+    D.P.m = m;
+    D.P.n = n;
+    D.P.ksteps = kp / kBK;
+    D.P.kb_steps = e.kb / kBK;
+    D.P.nkb = e.nkb;
+    D.P.ra = ra;
+    D.P.rb = rb;
+    D.P.cls = 0;
+    D.P.scheme = table_of(e.scheme, k);
+    D.split_ctr = split_ctr;
+    D.split_target = split_target;
+    D.done_ctr = done_ctr;
+    D.done_target = done_target;
+    D.gen = gen;
+    D.slot = slot;
+    std::memcpy(dst, &D, sizeof(D));
+}
+
+// The tile entries of one product (row blocks of 128, column tiles of the
+// table's width for n and k, the last one the narrowest that covers it).
+int res_tile_list(int m, int n, int k, const int *widths, int slot, std::vector<int4> &out) {
+    const int W = eq_tile_width(widths, n, k);
+    int count = 0;
+    for (int m0 = 0; m0 < m; m0 += kBM)
+        for (int n0 = 0; n0 < n; n0 += W) {
+            out.push_back(make_int4(slot, m0, n0, n - n0 >= W ? W : narrowest_width(n - n0)));
+            ++count;
+        }
+    return count;
+}
+
+void res_tile_marker(std::vector<int4> &out, bool stop) {
+    out.push_back(make_int4(stop ? kTileStop : kTileNop, 0, 0, 0));
+}
+
+// Launch the resident tensor-core worker (ctas CTAs, one per SM) over the
+// slice region (rows x res::kSlicePitch BF16, 16-byte aligned).
+// Loads the tile worker and sets its shared-memory limit.  With lazy module
+// loading a kernel is loaded at its first use, and loading can wait for the
+// kernels already running on the device: the SIMT worker, which waits (with
+// its bound) for entries that only come once the tile worker runs.  So both
+// workers are loaded before either is launched.
+void prepare_resident_tiles() {
+    static std::atomic<uint64_t> attr{0};
+    set_smem_limit_once((const void *)resident_tiles_kernel, smem_bytes(), attr);
+    cudaFuncAttributes fa{};
+    OO_CUDA_TRY(cudaFuncGetAttributes(&fa, (const void *)resident_tiles_kernel));
+}
+
+void launch_resident_tiles(const int4 *ring, const void *desc, unsigned *ctr, res::Ctl *ctl_dev,
+                           unsigned long long start, const void *slices, long long slice_rows, unsigned *err,
+                           int ctas, cudaStream_t s) {
+    GMaps maps{};
+    map_slices(&maps.a[0], slices, slice_rows, res::kSlicePitch, kBM);
+    map_slices(&maps.b[0], slices, slice_rows, res::kSlicePitch, kBRows);
+    const GArgs a = make_args(err);
+    ResTileArgs r{};
+    r.ring = ring;
+    r.desc = static_cast<const ResTileDesc *>(desc);
+    r.ctr = ctr;
+    r.heartbeat = ctr + res::kRingCap + res::kSlots;
+    r.ctl = ctl_dev;
+    r.start = start;
+    resident_tiles_kernel<<<ctas, kThreads, smem_bytes(), s>>>(maps, a, r);
+    OO_CUDA_TRY(cudaGetLastError());
 }
 
 }  // namespace oo

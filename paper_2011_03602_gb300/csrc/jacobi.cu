@@ -40,6 +40,7 @@
 #include <type_traits>
 
 #include "ff.cuh"
+#include "jacobi_point.cuh"
 #include "oo_internal.h"
 
 namespace oo {
@@ -383,72 +384,7 @@ __global__ void __launch_bounds__(512, 1) jacobi_fused_kernel(FusedArgs a) {
         float RH = 0.0f, RL = 0.0f;
         for (int x = tid0; x < nint; x += stride) {
             const int k = 1 + x % Ki, r = x / Ki, j = 1 + r % Ji, i = 1 + r / Ji;
-            const size_t c = (size_t)i * si + (size_t)j * sj + k;
-            // p is rewritten by other SMs between iterations: read it from L2
-            // (never a stale L1 line); the coefficients never change in here
-            const float *P = a.p;
-            auto ld = [&](size_t o) { return __ldcg(P + o); };
-            float cf[NCOEF];
-#pragma unroll
-            for (int q = 0; q < NCOEF; ++q) cf[q] = a.coef[q][c];
-            const float pc = ld(c), pE = ld(c + si), pW = ld(c - si), pN = ld(c + sj), pS = ld(c - sj);
-            const float pKp = ld(c + 1), pKm = ld(c - 1);
-            float H, L, th, tl, t1, xh, xl, e;
-            two_prod(cf[0], pE, H, L);                                   // a0 p[i+1]
-            two_prod(cf[1], pN, th, tl); ff_acc(H, L, th, tl);           // a1 p[j+1]
-            two_prod(cf[2], pKp, th, tl); ff_acc(H, L, th, tl);          // a2 p[k+1]
-            {   // b0 Xij: D(i+1) - D(i-1), D = p(j+1) - p(j-1) exact pairs
-                float dnh, dnl, gh, gl;
-                two_sum(ld(c + si + sj), -ld(c + si - sj), dnh, dnl);
-                two_sum(ld(c - si + sj), -ld(c - si - sj), gh, gl);
-                two_sum(dnh, -gh, xh, e);
-                xl = __fadd_rn(e, __fsub_rn(dnl, gl));
-                two_prod(cf[4], xh, th, t1);
-                tl = __fmaf_rn(cf[4], xl, t1);
-                ff_acc(H, L, th, tl);
-            }
-            {   // b1 Xjk: D(k+1) - D(k-1) on plane i
-                float dph, dpl, dmh, dml;
-                two_sum(ld(c + sj + 1), -ld(c - sj + 1), dph, dpl);
-                two_sum(ld(c + sj - 1), -ld(c - sj - 1), dmh, dml);
-                two_sum(dph, -dmh, xh, e);
-                xl = __fadd_rn(e, __fsub_rn(dpl, dml));
-                two_prod(cf[5], xh, th, t1);
-                tl = __fmaf_rn(cf[5], xl, t1);
-                ff_acc(H, L, th, tl);
-            }
-            {   // b2 Xik: F(k+1) - F(k-1), F = p(i+1) - p(i-1) on row j
-                float fph, fpl, fmh, fml;
-                two_sum(ld(c + si + 1), -ld(c - si + 1), fph, fpl);
-                two_sum(ld(c + si - 1), -ld(c - si - 1), fmh, fml);
-                two_sum(fph, -fmh, xh, e);
-                xl = __fadd_rn(e, __fsub_rn(fpl, fml));
-                two_prod(cf[6], xh, th, t1);
-                tl = __fmaf_rn(cf[6], xl, t1);
-                ff_acc(H, L, th, tl);
-            }
-            two_prod(cf[7], pW, th, tl); ff_acc(H, L, th, tl);           // c0 p[i-1]
-            two_prod(cf[8], pS, th, tl); ff_acc(H, L, th, tl);           // c1 p[j-1]
-            two_prod(cf[9], pKm, th, tl); ff_acc(H, L, th, tl);          // c2 p[k-1]
-            ff_acc(H, L, cf[11], 0.0f);                                  // wrk1
-            // ss = (s0 a3 - p) bnd; wrk2 = p + omega ss, rounded once
-            float dh, dl, e1, sh, s1;
-            two_prod(H, cf[3], th, t1);
-            tl = __fmaf_rn(L, cf[3], t1);
-            two_sum(th, -pc, dh, e1);
-            dl = __fadd_rn(e1, tl);
-            two_prod(dh, cf[10], sh, s1);
-            const float sl = __fmaf_rn(dl, cf[10], s1);
-            float wh, w1, yh, e2;
-            two_prod(omega, sh, wh, w1);
-            const float wl = __fmaf_rn(omega, sl, w1);
-            two_sum(pc, wh, yh, e2);
-            a.wrk2[c] = __fadd_rn(yh, __fadd_rn(e2, wl));
-            float nh, nl, qh, q1;
-            two_sum(sh, sl, nh, nl);
-            two_prod(nh, nh, qh, q1);
-            const float ql = __fmaf_rn(__fadd_rn(nh, nh), nl, q1);
-            ff_acc(RH, RL, qh, ql);
+            stencil_point_ff(a.coef, a.p, (size_t)i * si + (size_t)j * sj + k, si, sj, omega, a.wrk2, RH, RL);
         }
         double v = (double)RH + (double)RL;
 #pragma unroll

@@ -5,6 +5,7 @@
 
 #include <array>
 #include <atomic>
+#include <map>
 #include <cstdint>
 #include <functional>
 #include <string>
@@ -208,9 +209,65 @@ struct DevBuf {
     }
 };
 
-// Serving loop state (serve.cpp).
+// Serving loop state (serve.cpp: host-scheduled; serve_resident.cu: the
+// request loop resident on the device).
 struct Server;
 void server_stop(Server *S);
+struct Resident;
+void resident_stop(Resident *S);
+oo_status resident_submit(Resident *S, const oo_serve_req *req, uint64_t *ticket);
+struct Ctx;
+oo_status resident_wait(Ctx &c, Resident *S, uint64_t ticket, int timeout_ms, double *latency_ms);
+void resident_stats(Resident *S, oo_serve_stats_t *out);
+
+// first-fit allocator over [0, size) with 256-byte granules
+class Arena {
+  public:
+    void reset(size_t size) {
+        free_.clear();
+        free_[0] = size;
+        size_ = size;
+        free_bytes_ = size;
+    }
+    bool alloc(size_t bytes, size_t *off) {
+        bytes = (std::max<size_t>(bytes, 256) + 255) / 256 * 256;
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                *off = it->first;
+                const size_t rest = it->second - bytes, at = it->first + bytes;
+                free_.erase(it);
+                if (rest) free_[at] = rest;
+                free_bytes_ -= bytes;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t bytes) {
+        bytes = (std::max<size_t>(bytes, 256) + 255) / 256 * 256;
+        free_bytes_ += bytes;
+        auto it = free_.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    size_t size() const { return size_; }
+    size_t free_bytes() const { return free_bytes_; }
+
+  private:
+    std::map<size_t, size_t> free_;
+    size_t size_ = 0, free_bytes_ = 0;
+};
+
 
 // --------------------------------------------------------------- context
 struct Ctx {
@@ -234,6 +291,7 @@ struct Ctx {
     std::vector<std::pair<long long, FftPlan *>> fft_plans;
     DevBuf fft_scratch, stage_a, stage_b, stage_c, gemm_scratch;
     Server *server = nullptr;
+    Resident *rserver = nullptr;
     // fault injection armed by oo_inject_wait_timeout (one-shot; 0 = none)
     int inject_wait = 0;
     // options set by oo_set_option: OO_OPT_JACOBI_FUSED (-1 default rule,
@@ -264,6 +322,11 @@ struct Ctx {
 
 // The library state behind a C-ABI context handle (api.cpp).
 Ctx &ctx_state(oo_ctx *ctx);
+
+// FFT plan accessors for the device-resident loop (fft.cu)
+int fft_plan_log2(const FftPlan *p);
+void fft_plan_tables(const FftPlan *p, const void **tw, const void **tw_n1, const void **tw_n2, const void **tw_hi,
+                     const void **tw_lo, int *log2n, int *log2n1, int *log2n2);
 
 // Kernel launchers (jacobi.cu).  All asynchronous on `s`.
 void launch_coef(const JacobiDims &d, float *const coef[NCOEF], cudaStream_t s);

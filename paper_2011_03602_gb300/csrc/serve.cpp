@@ -39,54 +39,6 @@ double now_ms() {
 }
 size_t up256(size_t x) { return (x + 255) / 256 * 256; }
 
-// first-fit allocator over [0, size) with 256-byte granules
-class Arena {
-  public:
-    void reset(size_t size) {
-        free_.clear();
-        free_[0] = size;
-        size_ = size;
-        free_bytes_ = size;
-    }
-    bool alloc(size_t bytes, size_t *off) {
-        bytes = up256(std::max<size_t>(bytes, 256));
-        for (auto it = free_.begin(); it != free_.end(); ++it) {
-            if (it->second >= bytes) {
-                *off = it->first;
-                const size_t rest = it->second - bytes, at = it->first + bytes;
-                free_.erase(it);
-                if (rest) free_[at] = rest;
-                free_bytes_ -= bytes;
-                return true;
-            }
-        }
-        return false;
-    }
-    void release(size_t off, size_t bytes) {
-        bytes = up256(std::max<size_t>(bytes, 256));
-        free_bytes_ += bytes;
-        auto it = free_.emplace(off, bytes).first;
-        auto nx = std::next(it);
-        if (nx != free_.end() && it->first + it->second == nx->first) {
-            it->second += nx->second;
-            free_.erase(nx);
-        }
-        if (it != free_.begin()) {
-            auto pv = std::prev(it);
-            if (pv->first + pv->second == it->first) {
-                pv->second += it->second;
-                free_.erase(it);
-            }
-        }
-    }
-    size_t size() const { return size_; }
-    size_t free_bytes() const { return free_bytes_; }
-
-  private:
-    std::map<size_t, size_t> free_;
-    size_t size_ = 0, free_bytes_ = 0;
-};
-
 enum { ST_QUEUED = 0, ST_RUNNING = 1, ST_DONE = 2 };
 
 struct SReq {
@@ -366,7 +318,7 @@ oo_status oo_serve_start(oo_ctx *ctx, int slots, uint64_t hbm_budget_bytes, int 
     Ctx &c = ctx_state(ctx);
     try {
         OO_REQUIRE(c.device >= 0, OO_ESTATE, "host-only context (device -1) cannot serve");
-        OO_REQUIRE(c.server == nullptr, OO_ESTATE, "the context is already serving");
+        OO_REQUIRE(c.server == nullptr && c.rserver == nullptr, OO_ESTATE, "the context is already serving");
         OO_REQUIRE(slots >= 1 && slots <= 256, OO_EINVAL, "slots must be 1..256");
         OO_REQUIRE(queue_cap >= 1, OO_EINVAL, "queue_cap must be >= 1");
         OO_REQUIRE(hbm_budget_bytes >= (1u << 20), OO_EINVAL, "device budget below 1 MiB");
@@ -416,6 +368,7 @@ oo_status oo_serve_start(oo_ctx *ctx, int slots, uint64_t hbm_budget_bytes, int 
 oo_status oo_submit(oo_ctx *ctx, const oo_serve_req *req, uint64_t *ticket) {
     if (!ctx || !req || !ticket) return OO_EINVAL;
     Ctx &c = ctx_state(ctx);
+    if (c.rserver) return resident_submit(c.rserver, req, ticket);
     Server *S = c.server;
     if (!S) return OO_ESTATE;
     auto *q = new (std::nothrow) SReq();
@@ -464,6 +417,7 @@ oo_status oo_submit(oo_ctx *ctx, const oo_serve_req *req, uint64_t *ticket) {
 oo_status oo_wait(oo_ctx *ctx, uint64_t ticket, int timeout_ms, double *latency_ms) {
     if (!ctx) return OO_EINVAL;
     Ctx &c = ctx_state(ctx);
+    if (c.rserver) return resident_wait(c, c.rserver, ticket, timeout_ms, latency_ms);
     Server *S = c.server;
     if (!S) return OO_ESTATE;
     std::unique_lock<std::mutex> lk(S->mu);
@@ -505,6 +459,10 @@ oo_status oo_wait(oo_ctx *ctx, uint64_t ticket, int timeout_ms, double *latency_
 oo_status oo_serve_stats(oo_ctx *ctx, oo_serve_stats_t *out) {
     if (!ctx || !out) return OO_EINVAL;
     Ctx &c = ctx_state(ctx);
+    if (c.rserver) {
+        resident_stats(c.rserver, out);
+        return OO_OK;
+    }
     Server *S = c.server;
     if (!S) return OO_ESTATE;
     std::lock_guard<std::mutex> g(S->mu);
@@ -524,6 +482,11 @@ oo_status oo_serve_stats(oo_ctx *ctx, oo_serve_stats_t *out) {
 oo_status oo_serve_stop(oo_ctx *ctx) {
     if (!ctx) return OO_EINVAL;
     Ctx &c = ctx_state(ctx);
+    if (c.rserver) {
+        resident_stop(c.rserver);
+        c.rserver = nullptr;
+        return OO_OK;
+    }
     if (!c.server) return OO_ESTATE;
     server_stop(c.server);
     c.server = nullptr;

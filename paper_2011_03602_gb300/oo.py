@@ -151,6 +151,7 @@ def lib():
         "oo_batch_info": (_c.c_int, [_vp, P(_dbl), P(_dbl), P(_c.c_int), P(_c.c_int)]),
         "oo_batch_destroy": (None, [_vp]),
         "oo_serve_start": (_c.c_int, [_vp, _c.c_int, _u64, _c.c_int]),
+        "oo_serve_start_resident": (_c.c_int, [_vp, _u64, _c.c_int, _c.c_int]),
         "oo_submit": (_c.c_int, [_vp, P(oo_serve_req), P(_u64)]),
         "oo_wait": (_c.c_int, [_vp, _u64, _c.c_int, P(_dbl)]),
         "oo_serve_stats": (_c.c_int, [_vp, P(oo_serve_stats_t)]),
@@ -239,7 +240,7 @@ def oo_tune_stencil(ctx, I, J, K):
     return v.value, ms
 
 
-OO_INJECT_NONE, OO_INJECT_STENCIL_LOAD, OO_INJECT_FUSED_BARRIER = 0, 1, 2
+OO_INJECT_NONE, OO_INJECT_STENCIL_LOAD, OO_INJECT_FUSED_BARRIER, OO_INJECT_SERVE_STALL = 0, 1, 2, 3
 OO_OPT_JACOBI_FUSED, OO_OPT_STENCIL_VARIANT = 1, 2
 
 
@@ -641,6 +642,12 @@ def serve_request(kind, **kw):
             raise ValueError("res needs at least iters elements")
         r.res = None if res is None else _host_ptr(res, np.float64)
     return r
+
+
+def oo_serve_start_resident(ctx, hbm_budget_bytes, queue_cap=1024, tensor_ctas=0):
+    """Serve with the request loop resident on the device (persistent
+    workers fed through rings; no kernel launch per request)."""
+    _check(ctx, lib().oo_serve_start_resident(ctx, hbm_budget_bytes, queue_cap, tensor_ctas))
 
 
 def oo_submit(ctx, req):
