@@ -886,9 +886,9 @@ def run_serve(args):
     pool_f = {e: synth.complex_normal(9 + e, 1 << e) for e in range(10, 21)}
     grids = [(65, 65, 129), (129, 129, 257)]
     prec = oo.OO_PREC_FP64EQ if args.serve_prec == "fp64eq" else oo.OO_PREC_SPLIT3_BF16
-    # oracle references, computed on the host cores while the GPU serves
+    # oracle references: computed on the host cores after every timed phase
+    # (the serving loops' host threads and copies need those cores)
     ref_jobs = [("gemm", n) for n in gemm_sizes] + [("fft", e) for e in range(10, 21)] + [("jacobi", g) for g in grids]
-    refs_async = refs_pool.map_async(_serve_refs, ref_jobs)
     worst = {"gemm": 0.0, "fft": 0.0, "jacobi_res": 0.0, "jacobi_p": 0.0}
     # the first result of every (kind, size) is kept and checked against the
     # oracle at the end; every other result's digest must equal the first's
@@ -941,6 +941,7 @@ def run_serve(args):
             arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
             kinds = [draw(rng) for _ in range(n_req)]
             lat, rejected, lock = [], [0], threading.Lock()
+            st0 = oo.oo_serve_stats(ctx)
             t0 = time.perf_counter() + 0.05
 
             def client(tag):
@@ -991,10 +992,15 @@ def run_serve(args):
                 th.join()
             elapsed = time.perf_counter() - start
             lat_a = np.array(lat) if lat else np.array([np.nan])
+            st1 = oo.oo_serve_stats(ctx)
+            dn = max(1, st1["completed"] - st0["completed"])
+            stage = {k: round((st1["stage_ms"][k] * st1["completed"] - st0["stage_ms"][k] * st0["completed"]) / dn, 3)
+                     for k in st1["stage_ms"]}
             results.append({"offered_req_per_s": rate, "requests": n_req, "admitted": len(lat),
                             "rejected_busy": rejected[0], "solves_per_s": round(len(lat) / elapsed, 1),
                             "p50_ms": round(float(np.percentile(lat_a, 50)), 3),
-                            "p99_ms": round(float(np.percentile(lat_a, 99)), 3)})
+                            "p99_ms": round(float(np.percentile(lat_a, 99)), 3),
+                            "mean_stage_ms": stage})
         stats = oo.oo_serve_stats(ctx)
         oo.oo_serve_stop(ctx)
         per_mode[mode] = (results, stats, dict(first))
@@ -1026,7 +1032,7 @@ def run_serve(args):
              "p50_ms_if_arrivals_queue": round(float(np.percentile(lat_p, 50)), 3),
              "p99_ms_if_arrivals_queue": round(float(np.percentile(lat_p, 99)), 3)}
     oo.oo_destroy(ctx)
-    refs = dict(refs_async.get())
+    refs = dict(refs_pool.map(_serve_refs, ref_jobs))
     refs_pool.close()
     checked = [(ka, outs) for m in per_mode.values() for ka, outs in m[2].items()]
     for (kind, a), outs in checked:

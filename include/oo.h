@@ -551,6 +551,12 @@ typedef struct {
 typedef struct {
     uint64_t submitted, completed, rejected_busy, failed, queued, running;
     uint64_t device_free_bytes, device_budget_bytes;
+    /* mean time (ms) of completed requests in each stage: [0] queued (to
+     * admission), [1] input copies, [2] staging until the work is published
+     * (device-resident loop), [3] on the device (host-scheduled loop: from
+     * its start on a slot, copies included), [4] output copies; 0 where a
+     * loop has no such stage */
+    double stage_ms[5];
 } oo_serve_stats_t;
 /* Start the scheduler thread; allocates the device arena and pinned pool. */
 oo_status oo_serve_start(oo_ctx *ctx, int slots, uint64_t hbm_budget_bytes, int queue_cap);
@@ -581,7 +587,10 @@ oo_status oo_serve_stop(oo_ctx *ctx);
  * launches no kernel per request.  Requests' entries interleave in the rings,
  * so requests that arrive while others run share the SMs (continuous
  * batching).  The workers write each finished request's flag to mapped
- * memory; the outputs are then copied back.  Served here: GEMMs in
+ * memory.  Inputs are copied from the caller's buffers to the device when a
+ * request is admitted and outputs into them as soon as it completes, by the
+ * library's I/O threads (no staging copy on the host), so the buffers must
+ * stay valid until oo_wait returns.  Served here: GEMMs in
  * OO_PREC_FP64EQ with k <= 2048 (the same bits as oo_gemm_f64), FFTs up to
  * 2^22 points (the same bits as oo_fft_c128), Jacobi programs (the tiled
  * kernels' p bits; residuals summed in chunk order, within ~1e-12 relative of
@@ -589,8 +598,9 @@ oo_status oo_serve_stop(oo_ctx *ctx);
  * bounded (about a second); an idle server publishes keep-alive entries.
  * If a wait runs out, every request in flight fails with OO_ETIMEOUT and
  * later submissions with OO_ESTATE until oo_serve_stop.  While serving, the
- * workers hold every SM of the device: the context's other GPU calls wait
- * for SMs.  OO_ESTATE if the context already serves.                     */
+ * workers hold every SM of the device: the context's other GPU calls return
+ * OO_ESTATE until oo_serve_stop (a kernel loaded lazily at its first launch
+ * could wait for the workers).  OO_ESTATE if the context already serves.  */
 oo_status oo_serve_start_resident(oo_ctx *ctx, uint64_t hbm_budget_bytes, int queue_cap, int tensor_ctas);
 
 /* --------------------------------------------------- batched function blocks */

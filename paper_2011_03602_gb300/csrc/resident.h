@@ -7,8 +7,7 @@
 // mapped host memory.  No kernel is launched per request: the workers,
 // launched once when serving starts, walk the rings:
 //   - the SIMT ring (serve_resident.cu; 512-thread CTAs): digit splits of
-//     FP64-equivalent GEMMs, FFT passes, Jacobi setup / stencil / copy-back
-//     sweeps.  An entry has `nitems` items; CTA c takes items i with
+//     FP64-equivalent GEMMs, FFT passes, Jacobi setup and stencil sweeps.  An entry has `nitems` items; CTA c takes items i with
 //     (i + rot) % CTAs == c.  Every CTA reads every entry in order, so an
 //     entry's dependency (an earlier entry) is always held by CTAs that are
 //     running; items count into the entry's counter and the item that
@@ -44,8 +43,7 @@ enum EntryType {
     kFftCols = 5,     // four-step column pass: item i = columns [i C, (i + 1) C)
     kFftRows = 6,     // four-step row pass
     kJacSetup = 7,    // Jacobi setup nests N0, N1: chunks of the padded grid (float4 units)
-    kJacStencil = 8,  // N2 for iteration aux: chunks of the interior points
-    kJacCopy = 9      // N3 + N4 + N5: chunks of the grid points
+    kJacStencil = 8   // N2 for iteration aux (p and wrk2 alternate; see the item): chunks of column slabs
 };
 constexpr int kFftMaxChunk = 1 << 16;
 
@@ -78,10 +76,11 @@ struct Entry {
 struct JacDesc {
     float *arr[14];  // a0..a3, b0..b2, c0..c2, bnd, wrk1, p, wrk2 (I x J x pitch floats each)
     double *res;     // iters
-    double *partials;  // stencil items of one iteration
-    int32_t I, J, K, pitch, iters, chunk;  // chunk: points per stencil / copy item (float4 units for setup)
+    double *partials;  // two sets (iteration parity) of one partial per stencil item
+    int32_t I, J, K, pitch, iters;
+    int32_t chunk, chunk4;  // stencil units (column x slab) per item; float4 units per setup item
     float omega;
-    int32_t pad;
+    int32_t nseg;           // slabs of interior planes
 };
 
 }  // namespace res

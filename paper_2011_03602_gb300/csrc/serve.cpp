@@ -76,6 +76,7 @@ struct Server {
     std::vector<SReq *> slot_req;
     uint64_t n_submitted = 0, n_done = 0, n_busy = 0, n_failed = 0;
     double busy_since = 0;
+    double sum_queued_ms = 0, sum_slot_ms = 0;  // completed requests: queued, then on a slot
 };
 
 namespace {
@@ -219,6 +220,8 @@ void scheduler(Server *Sp) {
             const cudaError_t e = cudaEventQuery(S.events[s]);
             if (e == cudaErrorNotReady) continue;
             q->t_done = now_ms();
+            S.sum_queued_ms += q->t_start - q->t_submit;
+            S.sum_slot_ms += q->t_done - q->t_start;
             if (e != cudaSuccess) {
                 q->status = OO_ECUDA;
                 q->error = cudaGetErrorString(e);
@@ -476,6 +479,10 @@ oo_status oo_serve_stats(oo_ctx *ctx, oo_serve_stats_t *out) {
     out->running = running;
     out->device_free_bytes = S->dev.free_bytes();
     out->device_budget_bytes = S->dev.size();
+    const double n = S->n_done ? (double)S->n_done : 1.0;
+    for (double &v : out->stage_ms) v = 0.0;
+    out->stage_ms[0] = S->sum_queued_ms / n;
+    out->stage_ms[3] = S->sum_slot_ms / n;
     return OO_OK;
 }
 

@@ -4,9 +4,10 @@
 // launched when serving starts and walk append-only rings of work entries
 // (layout and protocol: resident.h):
 //   - resident_simt_kernel (here, 512-thread CTAs): FP64-equivalent digit
-//     splits, FFT passes (the grouped FFT's work items), Jacobi setup,
-//     stencil and copy-back sweeps (the per-point float-float arithmetic of
-//     the cooperative Jacobi kernel, in chunks);
+//     splits, FFT passes (the grouped FFT's work items), Jacobi setup and
+//     stencil sweeps (the per-point float-float arithmetic of the
+//     cooperative Jacobi kernel, one chunk per CTA; p and wrk2 alternate
+//     roles, which makes the copy-back nests' result without a copy);
 //   - resident_tiles_kernel (gemm_eq_group.cu): the tensor-core tiles of the
 //     FP64-equivalent products.
 // The host scheduler thread admits the oldest waiting requests whose device
@@ -27,6 +28,7 @@
 #include <mutex>
 #include <thread>
 #include <unordered_map>
+#include <unistd.h>
 #include <vector>
 
 #include "eq_digits.cuh"
@@ -54,7 +56,6 @@ namespace {
 using namespace res;
 
 constexpr long long kResWait = 2000000000ll;  // clock64 ticks (~1 s)
-constexpr int kJacChunk = 16384;              // points (float4 units for the setup) per Jacobi item
 
 // ----------------------------------------------------------- device side
 __device__ __forceinline__ unsigned long long res_ld_acquire_sys64(const volatile unsigned long long *p) {
@@ -102,7 +103,9 @@ __device__ __forceinline__ void run_item(const SimtArgs &a, const Entry &E, int 
                                          int *redi) {
     const int tid = threadIdx.x;
     if (E.type == kSplit) {
-        const eq::GSplit &G = a.split[E.slot];
+        // descriptors copied to registers: a reference into global memory
+        // would be re-read after every store (the stores may alias it)
+        const eq::GSplit G = a.split[E.slot];
         if (i < E.aux) {
             eq::split_rows_job(G, i * (kSimtThreads / 32));
         } else {
@@ -142,19 +145,19 @@ __device__ __forceinline__ void run_item(const SimtArgs &a, const Entry &E, int 
         }
         fft_group_item(it, a.fft, a.tlist, a.expo, sm, sm + kFftElems);
     } else {
-        const JacDesc &J = a.jac[E.slot];
+        const JacDesc J = a.jac[E.slot];
         const size_t sj = (size_t)J.pitch, si = (size_t)J.J * J.pitch;
         if (E.type == kJacSetup) {
             // N0 coefficients (constants) and N1 p = wrk2 = (k / (K - 1))^2,
             // the padding of each row zero, as the setup kernels write them
             const float val[NCOEF] = {1.0f, 1.0f, 1.0f, 1.0f / 6.0f, 0.0f, 0.0f, 0.0f, 1.0f, 1.0f, 1.0f, 1.0f, 0.0f};
-            const size_t n4 = (size_t)J.I * J.J * J.pitch / 4, chunks = (size_t)J.pitch / 4;
-            const size_t x0 = (size_t)i * J.chunk, x1 = min(n4, x0 + (size_t)J.chunk);
-            for (size_t x = x0 + tid; x < x1; x += kSimtThreads) {
+            const int n4 = J.I * J.J * (J.pitch / 4), chunks = J.pitch / 4;
+            const int x0 = i * J.chunk4, x1 = min(n4, x0 + J.chunk4);
+            for (int x = x0 + tid; x < x1; x += kSimtThreads) {
 #pragma unroll
                 for (int q = 0; q < NCOEF; ++q)
                     reinterpret_cast<float4 *>(J.arr[q])[x] = make_float4(val[q], val[q], val[q], val[q]);
-                const int k = (int)(x % chunks) * 4;
+                const int k = (x % chunks) * 4;
                 float v[4];
 #pragma unroll
                 for (int e = 0; e < 4; ++e) v[e] = (k + e < J.K) ? jacobi_face_value(k + e, J.K) : 0.0f;
@@ -162,46 +165,84 @@ __device__ __forceinline__ void run_item(const SimtArgs &a, const Entry &E, int 
                 reinterpret_cast<float4 *>(J.arr[VAR_P])[x] = g4;
                 reinterpret_cast<float4 *>(J.arr[VAR_WRK2])[x] = g4;
             }
-        } else if (E.type == kJacStencil) {
-            const int Ji = J.J - 2, Ki = J.K - 2;
-            const long long nint = (long long)(J.I - 2) * Ji * Ki;
-            const long long x0 = (long long)i * J.chunk, x1 = min(nint, x0 + J.chunk);
+        } else {  // kJacStencil
+            // N2 of iteration E.aux.  p and wrk2 alternate roles (even
+            // iterations read p and write wrk2, odd ones the reverse): both
+            // hold the Dirichlet faces from the setup and the stencil writes
+            // only the interior, so the array written is exactly p after the
+            // copy-back nests N3-N5, and no copy is made.
+            // Work unit: one (j, k) column over one of nseg slabs of planes;
+            // a thread marches its column along i with the 3 x 3 windows of
+            // planes i - 1, i, i + 1 in registers, reading one new window
+            // (9 values) per point, the next one ahead of the arithmetic.
+            const int Ji = J.J - 2, Ki = J.K - 2, ncols = Ji * Ki, np = J.I - 2;
+            const int units = ncols * J.nseg;
+            const int u0 = i * J.chunk, u1 = min(units, u0 + J.chunk);
+            const bool odd = (E.aux & 1) != 0;  // selects, not an index: J stays in registers
+            const float *pin = odd ? J.arr[VAR_WRK2] : J.arr[VAR_P];
+            float *pout = odd ? J.arr[VAR_P] : J.arr[VAR_WRK2];
             float RH = 0.0f, RL = 0.0f;
-            for (long long x = x0 + tid; x < x1; x += kSimtThreads) {
-                const int k = 1 + (int)(x % Ki);
-                const long long r = x / Ki;
-                const int j = 1 + (int)(r % Ji), ii = 1 + (int)(r / Ji);
-                stencil_point_ff(J.arr, J.arr[VAR_P], (size_t)ii * si + (size_t)j * sj + k, si, sj, J.omega,
-                                 J.arr[VAR_WRK2], RH, RL);
+            for (int u = u0 + tid; u < u1; u += kSimtThreads) {
+                const int sg = u / ncols, col = u - sg * ncols;
+                const int jr = col / Ki;
+                const int j = 1 + jr, k = 1 + col - jr * Ki;
+                const int ib = 1 + (int)((long long)np * sg / J.nseg);
+                const int ie = 1 + (int)((long long)np * (sg + 1) / J.nseg);
+                size_t c = (size_t)ib * si + (size_t)j * sj + k;
+                PWin W, C, Ep;
+                load_pwin(pin, c - si, sj, false, W);
+                load_pwin(pin, c, sj, true, C);
+                load_pwin(pin, c + si, sj, true, Ep);
+                float cf[NCOEF];
+#pragma unroll
+                for (int q = 0; q < NCOEF; ++q) cf[q] = J.arr[q][c];
+                for (int ii = ib; ii < ie; ++ii, c += si) {
+                    // the next point's coefficients and window ahead of this one's arithmetic
+                    const bool more = ii + 1 < ie;
+                    float cn[NCOEF];
+                    PWin Nx;
+                    if (more) {
+#pragma unroll
+                        for (int q = 0; q < NCOEF; ++q) cn[q] = J.arr[q][c + si];
+                        load_pwin(pin, c + 2 * si, sj, true, Nx);
+                    }
+                    pout[c] = stencil_point_core(cf, W, C, Ep, J.omega, RH, RL);
+                    if (more) {
+                        W = C;
+                        C = Ep;
+                        Ep = Nx;
+#pragma unroll
+                        for (int q = 0; q < NCOEF; ++q) cf[q] = cn[q];
+                    }
+                }
             }
             const double s = block_sum((double)RH + (double)RL, red);
-            if (tid == 0) J.partials[i] = s;
-        } else {  // kJacCopy: N3 (interior = wrk2), N4 and N5 (faces = (k / (K - 1))^2)
-            const long long nall = (long long)J.I * J.J * J.K;
-            const long long x0 = (long long)i * J.chunk, x1 = min(nall, x0 + J.chunk);
-            for (long long x = x0 + tid; x < x1; x += kSimtThreads) {
-                const int k = (int)(x % J.K);
-                const long long r = x / J.K;
-                const int j = (int)(r % J.J), ii = (int)(r / J.J);
-                const size_t c = (size_t)ii * si + (size_t)j * sj + k;
-                const bool interior =
-                    ii >= 1 && ii <= J.I - 2 && j >= 1 && j <= J.J - 2 && k >= 1 && k <= J.K - 2;
-                J.arr[VAR_P][c] = interior ? __ldcg(&J.arr[VAR_WRK2][c]) : jacobi_face_value(k, J.K);
-            }
+            // two partial sets, by iteration parity: the next iteration's
+            // items may start (its dependency is this entry's count) before
+            // the CTA that completes this entry has summed this set; the one
+            // after cannot start before that CTA has moved on
+            if (tid == 0) J.partials[(E.aux & 1) * E.nitems + i] = s;
         }
     }
 }
 
-// the item that completes an entry (thread 0)
+// Completion of an entry, by the first warp of the CTA whose item completed
+// it (the other CTAs may already be on the next entry, so this is kept
+// short): the Jacobi residual of the iteration -- the items' partials, each
+// lane summing a fixed stride of them, then a fixed butterfly -- and the
+// request's done flag.
 __device__ __forceinline__ void finish_entry(const SimtArgs &a, const Entry &E) {
-    __threadfence();
+    const int lane = threadIdx.x & 31;
     if (E.type == kJacStencil) {
         const JacDesc &J = a.jac[E.slot];
+        const double *part = J.partials + (E.aux & 1) * E.nitems;
         double s = 0.0;
-        for (int q = 0; q < E.nitems; ++q) s += __ldcg(&J.partials[q]);  // item order: deterministic
-        J.res[E.aux] = s;
+        for (int q = lane; q < E.nitems; q += 32) s += __ldcg(&part[q]);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) J.res[E.aux] = s;
     }
-    if (E.last) {
+    if (lane == 0 && E.last) {
         __threadfence_system();
         res_st_release_sys32(&a.ctl->done[E.slot], E.gen);
     }
@@ -210,7 +251,7 @@ __device__ __forceinline__ void finish_entry(const SimtArgs &a, const Entry &E) 
 __global__ void __launch_bounds__(kSimtThreads, 1) resident_simt_kernel(const SimtArgs a) {
     extern __shared__ __align__(16) float4 rsm[];
     __shared__ __align__(16) Entry E;  // copied in as 16-byte words
-    __shared__ int go;
+    __shared__ int go, fin;
     __shared__ double red[kSimtThreads / 32];
     __shared__ int redi[kSimtThreads / 32];
     const int G = gridDim.x, me = blockIdx.x, tid = threadIdx.x;
@@ -264,10 +305,13 @@ __global__ void __launch_bounds__(kSimtThreads, 1) resident_simt_kernel(const Si
             run_item(a, E, i, rsm, red, redi);
             __syncthreads();
             if (tid == 0) {
-                __threadfence();
+                __threadfence();  // this item's writes before its count
                 const unsigned old = atomicAdd(&a.ctr[E.ctr], 1u);
-                if (old + 1u == E.target) finish_entry(a, E);
+                fin = old + 1u == E.target;
+                if (fin) __threadfence();  // every item's writes before the completion's reads
             }
+            __syncthreads();
+            if (fin && tid < 32) finish_entry(a, E);
         }
         if (go < 0) break;
         if (tid == 0) {
@@ -285,17 +329,21 @@ using Clock = std::chrono::steady_clock;
 double now_ms() { return std::chrono::duration<double, std::milli>(Clock::now().time_since_epoch()).count(); }
 size_t up256(size_t x) { return (x + 255) / 256 * 256; }
 
-enum { RS_QUEUED = 0, RS_UPLOAD = 1, RS_RUNNING = 2, RS_DRAIN = 3, RS_DONE = 4 };
+// request states: queued; admitted, its inputs being copied in by an I/O
+// thread; inputs on the device; entries being uploaded; published; its
+// outputs being copied out by an I/O thread; done
+enum { RS_QUEUED = 0, RS_INPUT = 1, RS_READY = 2, RS_UPLOAD = 3, RS_RUNNING = 4, RS_OUTPUT = 5, RS_DONE = 6 };
 
 struct RReq {
     oo_serve_req r{};
     uint64_t ticket = 0;
     double t_submit = 0, t_done = 0;
+    double t_admit = 0, t_ready = 0, t_pub = 0, t_dev = 0;  // stage boundaries
     int state = RS_QUEUED;
     oo_status status = OO_OK;
     std::string error;
-    // pinned staging: inputs, outputs, then the upload area (descriptors, entries)
-    size_t h_off = 0, h_bytes = 0, h_in0 = 0, h_in1 = 0, h_out = 0, h_res = 0, h_up = 0;
+    // pinned upload area (descriptors, entries) while the entries are staged
+    size_t h_off = 0, h_bytes = 0;
     size_t d_off = 0, d_bytes = 0;     // device arena
     size_t row_off = 0, rows = 0;      // digit-slice rows (GEMM)
     int slot = -1;
@@ -306,6 +354,7 @@ struct RReq {
     int mark_slot = -1;   // its pinned upload slot
 };
 constexpr size_t kMarkBytes = sizeof(Entry) + (size_t)kMaxCtas * sizeof(int4);
+constexpr int kIoThreads = 4;
 constexpr int kMarkSlots = 64;
 
 }  // namespace
@@ -317,7 +366,16 @@ struct Resident {
     std::condition_variable cv_sched, cv_done;
     bool stop = false, failed = false;
     std::string fail_msg;
-    std::deque<RReq *> queue, uploading, running, draining;
+    std::deque<RReq *> queue, ready, uploading, running;
+    // I/O threads: inputs copied from the caller's buffers to the device when
+    // a request is admitted, outputs back into them when it is done, each
+    // thread on its own stream (pageable copies block the thread issuing them)
+    std::vector<std::thread> io;
+    std::vector<cudaStream_t> io_streams;
+    std::deque<RReq *> io_jobs;
+    std::condition_variable cv_io;
+    bool io_stop = false;
+    int n_io_in = 0, n_io_out = 0;
     size_t queue_cap = 0;
     std::unordered_map<uint64_t, RReq *> reqs;
     uint64_t next_ticket = 1;
@@ -350,6 +408,8 @@ struct Resident {
     std::array<int, OO_TILE_NBUCKETS * OO_TILE_KBUCKETS> widths{};
     int inject_stall = 0;
     uint64_t n_submitted = 0, n_done = 0, n_busy = 0, n_failed = 0;
+    double sum_ms[5] = {0, 0, 0, 0, 0};  // completed requests' stage times
+    uint64_t n_timed = 0;
 };
 
 namespace {
@@ -374,50 +434,64 @@ cudaEvent_t take_event(Resident &S) {
     return e;
 }
 
-// bytes of the pinned staging block and the device footprint of a request
+// the device footprint of a request and the size of its upload area
 struct Plan {
-    size_t h_in0, h_in1, h_out, h_res, h_up, h_bytes;
+    size_t h_bytes;
     size_t d_bytes, rows;
     int n_simt, n_tiles;
 };
 
-int jac_items(long long points, int chunk) { return (int)((points + chunk - 1) / chunk); }
+// Jacobi items: one per SIMT CTA (fewer when a CTA would get under one
+// unit per thread), equal chunks, so every entry is spread over the worker
+void jac_split(long long units, int ctas, int &items, int &chunk) {
+    items = (int)std::max<long long>(1, std::min<long long>(ctas, (units + kSimtThreads - 1) / kSimtThreads));
+    chunk = (int)((units + items - 1) / items);
+}
+
+// Stencil work units: (j, k) columns x nseg slabs of planes, nseg chosen for
+// the best share of busy threads (units / (threads x rounds)), discounted by
+// the two planes each unit reads before its first point.
+void jac_stencil_units(const JacobiDims &d, int ctas, int &nseg, int &items, int &chunk) {
+    const long long ncols = (long long)(d.J - 2) * (d.K - 2), np = d.I - 2;
+    const long long T = (long long)ctas * kSimtThreads;
+    nseg = 1;
+    double best = -1.0;
+    for (long long ns = 1; ns <= std::max<long long>(1, std::min<long long>(np / 4, 64)); ++ns) {
+        int it = 0, ch = 0;
+        jac_split(ncols * ns, ctas, it, ch);
+        const long long rounds = (ch + kSimtThreads - 1) / kSimtThreads;
+        const double seg = (double)np / (double)ns;
+        const double eff = (double)(ncols * ns) / (double)(T * rounds) * seg / (seg + 2.0);
+        if (eff > best + 1e-9) {
+            best = eff;
+            nseg = (int)ns;
+        }
+    }
+    jac_split(ncols * nseg, ctas, items, chunk);
+}
 
 Plan plan_request(Resident &S, const oo_serve_req &r) {
     Plan P{};
-    size_t h = 0;
-    auto hput = [&](size_t b) {
-        const size_t at = h;
-        h += up256(b);
-        return at;
-    };
     if (r.kind == OO_BLOCK_GEMM) {
         const eq::Shape e = eq::shape(eq_scheme_for((int)r.k), (int)r.k);
-        P.h_in0 = hput((size_t)r.m * r.k * 8);
-        P.h_in1 = hput((size_t)r.k * r.n * 8);
-        P.h_out = hput((size_t)r.m * r.n * 8);
         P.d_bytes = up256((size_t)r.m * r.k * 8) + up256((size_t)r.k * r.n * 8) + up256((size_t)r.m * r.n * 8) +
                     up256((size_t)r.m * 4) + up256((size_t)r.n * 4);
         P.rows = (size_t)e.slices * (r.m + r.n);
         P.n_simt = 1;
         P.n_tiles = (int)(((r.m + 127) / 128) * ((r.n + 31) / 32));  // upper bound (narrowest tiles)
     } else if (r.kind == OO_BLOCK_FFT) {
-        P.h_in0 = hput((size_t)r.n * 16);
-        P.h_out = P.h_in0;  // in place
         P.d_bytes = up256((size_t)r.n * 16) + (r.n > 4096 ? up256((size_t)r.n * 16) : 0);
         P.n_simt = r.n > 4096 ? 3 : 2;
     } else {
         const JacobiDims d{(int)r.m, (int)r.n, (int)r.k, jacobi_pitch((int)r.k)};
-        const int ns = jac_items((long long)(d.I - 2) * (d.J - 2) * (d.K - 2), kJacChunk);
-        P.h_out = hput(d.n_host() * 4);
-        P.h_res = hput((size_t)std::max(1, r.iters) * 8);
+        int nseg = 0, ns = 0, chunk = 0;
+        jac_stencil_units(d, S.simt_ctas, nseg, ns, chunk);
         P.d_bytes = (size_t)NARR * up256(d.n_dev() * 4) + up256((size_t)std::max(1, r.iters) * 8) +
-                    up256((size_t)std::max(1, ns) * 8);
-        P.n_simt = 1 + 2 * r.iters;
+                    up256((size_t)2 * std::max(1, ns) * 8);
+        P.n_simt = 1 + r.iters;
     }
-    // upload area: the request's descriptors and entries
-    P.h_up = hput(1024 + (size_t)P.n_simt * sizeof(Entry) + (size_t)P.n_tiles * sizeof(int4));
-    P.h_bytes = h;
+    // upload area: the request's descriptors (first 1 KB) and entries
+    P.h_bytes = up256(1024 + (size_t)P.n_simt * sizeof(Entry) + (size_t)P.n_tiles * sizeof(int4));
     return P;
 }
 
@@ -472,14 +546,14 @@ Entry make_entry(Resident &S, unsigned long long pos, int type, int slot, int ni
     return E;
 }
 
-// Stage a request: descriptors, entries and inputs go to the device on the
-// upload stream; an event marks when they have landed.  Returns false
-// (nothing changed) when a ring has no room yet.
+// Stage a request whose inputs are on the device: descriptors and entries
+// go to the device on the upload stream from the request's pinned upload
+// area; an event marks when they have landed.  Returns false (nothing
+// changed) when a ring has no room yet.
 bool stage(Resident &S, RReq &q) {
     const oo_serve_req &r = q.r;
-    char *hst = S.host_base + q.h_off;
     char *dev = S.dev_base + q.d_off;
-    char *upa = hst + q.h_up;  // upload area
+    char *upa = S.host_base + q.h_off;  // upload area
     std::vector<Entry> ents;
     std::vector<int4> tl;
     const unsigned long long s0 = S.simt_w, t0 = S.tile_w;
@@ -493,7 +567,7 @@ bool stage(Resident &S, RReq &q) {
     else if (r.kind == OO_BLOCK_FFT)
         n_simt = r.n > 4096 ? 3 : 2;
     else
-        n_simt = 1 + 2 * (size_t)r.iters;
+        n_simt = 1 + (size_t)r.iters;
     {
         const unsigned long long ms = min_progress(S.ctl->simt_progress, S.simt_ctas);
         const unsigned long long mt = min_progress(S.ctl->tile_progress, S.tile_ctas);
@@ -532,8 +606,6 @@ bool stage(Resident &S, RReq &q) {
         std::memcpy(upa, &G, sizeof(G));
         res_tile_desc_fill(upa + 256, C, n, ea, eb, m, n, k, (int)q.row_off, (int)(q.row_off + (size_t)e.slices * m),
                            ents[0].ctr, ents[0].target, dctr, S.ctr_base[dctr], q.gen, q.slot);
-        OO_CUDA_TRY(cudaMemcpyAsync(A, hst + q.h_in0, (size_t)m * k * 8, cudaMemcpyHostToDevice, s));
-        OO_CUDA_TRY(cudaMemcpyAsync(B, hst + q.h_in1, (size_t)k * n * 8, cudaMemcpyHostToDevice, s));
         OO_CUDA_TRY(cudaMemcpyAsync(S.split_desc + q.slot, upa, sizeof(G), cudaMemcpyHostToDevice, s));
         OO_CUDA_TRY(cudaMemcpyAsync(S.tile_desc + (size_t)q.slot * res_tile_desc_bytes(), upa + 256,
                                     res_tile_desc_bytes(), cudaMemcpyHostToDevice, s));
@@ -566,7 +638,6 @@ bool stage(Resident &S, RReq &q) {
             ents.push_back(make_entry(S, pos(), kFftCols, q.slot, N2 / (kFftElems / N1), R.log2n1, &ents[0]));
             ents.push_back(make_entry(S, pos(), kFftRows, q.slot, N1 / (kFftElems / N2), R.log2n2, &ents[1]));
         }
-        OO_CUDA_TRY(cudaMemcpyAsync(x, hst + q.h_in0, (size_t)r.n * 16, cudaMemcpyHostToDevice, s));
         OO_CUDA_TRY(cudaMemcpyAsync(S.fft_desc + q.slot, upa, sizeof(R), cudaMemcpyHostToDevice, s));
         OO_CUDA_TRY(cudaMemcpyAsync(S.expo + q.slot, upa + 512, 4, cudaMemcpyHostToDevice, s));
     } else {
@@ -581,18 +652,15 @@ bool stage(Resident &S, RReq &q) {
         J.K = d.K;
         J.pitch = d.pitch;
         J.iters = r.iters;
-        J.chunk = kJacChunk;
+        int n_setup = 0, n_st = 0;
+        jac_split((long long)(d.n_dev() / 4), S.simt_ctas, n_setup, J.chunk4);
+        jac_stencil_units(d, S.simt_ctas, J.nseg, n_st, J.chunk);
         J.omega = r.omega;
         std::memcpy(upa, &J, sizeof(J));
-        const int n_setup = jac_items((long long)(d.n_dev() / 4), kJacChunk);
-        const int n_st = jac_items((long long)(d.I - 2) * (d.J - 2) * (d.K - 2), kJacChunk);
-        const int n_cp = jac_items((long long)d.I * d.J * d.K, kJacChunk);
         ents.push_back(make_entry(S, pos(), kJacSetup, q.slot, n_setup, 0, nullptr));
         for (int it = 0; it < r.iters; ++it) {
             const Entry prev = ents.back();
             ents.push_back(make_entry(S, pos(), kJacStencil, q.slot, n_st, it, &prev));
-            const Entry st = ents.back();
-            ents.push_back(make_entry(S, pos(), kJacCopy, q.slot, n_cp, it, &st));
         }
         OO_CUDA_TRY(cudaMemcpyAsync(S.jac_desc + q.slot, upa, sizeof(J), cudaMemcpyHostToDevice, s));
     }
@@ -672,13 +740,16 @@ void fail_all(Resident &S, const std::string &why) {
         ++S.n_failed;
         ++S.n_done;
     };
-    for (auto *dq : {&S.queue, &S.uploading, &S.running, &S.draining}) {
+    // requests with an I/O thread finish there (inputs: failed; outputs:
+    // the device had completed them)
+    for (auto *dq : {&S.queue, &S.ready, &S.uploading, &S.running}) {
         for (RReq *q : *dq) fail(q);
         dq->clear();
     }
     S.cv_done.notify_all();
 }
 
+// device memory, digit-slice rows and descriptor slot back to the pools
 void release(Resident &S, RReq *q) {
     S.dev.release(q->d_off, q->d_bytes);
     if (q->rows) S.rows.release(q->row_off, q->rows);
@@ -687,27 +758,127 @@ void release(Resident &S, RReq *q) {
     q->ev = nullptr;
 }
 
-void download(Resident &S, RReq &q) {
+// inputs from the caller's buffers to the request's device memory
+void copy_in(Resident &S, const RReq &q, cudaStream_t s) {
     const oo_serve_req &r = q.r;
-    char *hst = S.host_base + q.h_off;
     char *dev = S.dev_base + q.d_off;
-    cudaStream_t s = S.down;
+    if (r.kind == OO_BLOCK_GEMM) {
+        OO_CUDA_TRY(cudaMemcpyAsync(dev, r.in0, (size_t)r.m * r.k * 8, cudaMemcpyHostToDevice, s));
+        OO_CUDA_TRY(cudaMemcpyAsync(dev + up256((size_t)r.m * r.k * 8), r.in1, (size_t)r.k * r.n * 8,
+                                    cudaMemcpyHostToDevice, s));
+    } else if (r.kind == OO_BLOCK_FFT) {
+        OO_CUDA_TRY(cudaMemcpyAsync(dev, r.in0, (size_t)r.n * 16, cudaMemcpyHostToDevice, s));
+    }
+    OO_CUDA_TRY(cudaStreamSynchronize(s));
+}
+
+// One write per page of a caller's output buffer, so that every page is
+// mapped before the copy engine writes it: a copy into pages the process
+// has never touched (a freshly allocated buffer) has the device fault them
+// in one by one, which was measured to stall that copy and the copies
+// queued behind it for tens of milliseconds; on the CPU the same pages are
+// mapped at the cost of zero-filling them.
+void touch_pages(void *p, size_t bytes) {
+    static const size_t page = [] {
+        const long v = sysconf(_SC_PAGESIZE);
+        return v > 0 ? (size_t)v : (size_t)4096;
+    }();
+    if (!p || bytes == 0) return;
+    volatile char *c = static_cast<volatile char *>(p);
+    const size_t head = (page - ((uintptr_t)p % page)) % page;  // first page boundary inside
+    c[0] = 0;
+    for (size_t o = head; o < bytes; o += page) c[o] = 0;
+    c[bytes - 1] = 0;
+}
+
+// outputs from the request's device memory to the caller's buffers
+void copy_out(Resident &S, const RReq &q, cudaStream_t s) {
+    const oo_serve_req &r = q.r;
+    const char *dev = S.dev_base + q.d_off;
+    if (r.kind == OO_BLOCK_GEMM)
+        touch_pages(r.out, (size_t)r.m * r.n * 8);
+    else if (r.kind == OO_BLOCK_FFT)
+        touch_pages(r.out, (size_t)r.n * 16);
+    else
+        touch_pages(r.out, (size_t)r.m * r.n * r.k * 4);
     if (r.kind == OO_BLOCK_GEMM) {
         const char *C = dev + up256((size_t)r.m * r.k * 8) + up256((size_t)r.k * r.n * 8);
-        OO_CUDA_TRY(cudaMemcpyAsync(hst + q.h_out, C, (size_t)r.m * r.n * 8, cudaMemcpyDeviceToHost, s));
+        OO_CUDA_TRY(cudaMemcpyAsync(r.out, C, (size_t)r.m * r.n * 8, cudaMemcpyDeviceToHost, s));
     } else if (r.kind == OO_BLOCK_FFT) {
-        OO_CUDA_TRY(cudaMemcpyAsync(hst + q.h_out, dev, (size_t)r.n * 16, cudaMemcpyDeviceToHost, s));
+        OO_CUDA_TRY(cudaMemcpyAsync(r.out, dev, (size_t)r.n * 16, cudaMemcpyDeviceToHost, s));
     } else {
         const JacobiDims d{(int)r.m, (int)r.n, (int)r.k, jacobi_pitch((int)r.k)};
         const size_t arr = up256(d.n_dev() * 4);
         const size_t wb = (size_t)d.K * 4;
-        OO_CUDA_TRY(cudaMemcpy2DAsync(hst + q.h_out, wb, dev + (size_t)VAR_P * arr, (size_t)d.pitch * 4, wb,
+        const int pv = r.iters % 2 ? VAR_WRK2 : VAR_P;  // the array the last sweep wrote
+        OO_CUDA_TRY(cudaMemcpy2DAsync(r.out, wb, dev + (size_t)pv * arr, (size_t)d.pitch * 4, wb,
                                       (size_t)d.I * d.J, cudaMemcpyDeviceToHost, s));
-        if (r.iters > 0)
-            OO_CUDA_TRY(cudaMemcpyAsync(hst + q.h_res, dev + (size_t)NARR * arr, (size_t)r.iters * 8,
+        if (r.res && r.iters > 0)
+            OO_CUDA_TRY(cudaMemcpyAsync(r.res, dev + (size_t)NARR * arr, (size_t)r.iters * 8,
                                         cudaMemcpyDeviceToHost, s));
     }
-    OO_CUDA_TRY(cudaEventRecord(q.ev, s));
+    OO_CUDA_TRY(cudaStreamSynchronize(s));
+}
+
+void io_worker(Resident *Sp, int idx) {
+    Resident &S = *Sp;
+    cudaSetDevice(S.c->device);
+    cudaStream_t s = S.io_streams[(size_t)idx];
+    std::unique_lock<std::mutex> lk(S.mu);
+    while (true) {
+        S.cv_io.wait(lk, [&] { return S.io_stop || !S.io_jobs.empty(); });
+        if (S.io_jobs.empty()) break;  // stopping, nothing left
+        RReq *q = S.io_jobs.front();
+        S.io_jobs.pop_front();
+        const bool in = q->state == RS_INPUT;
+        lk.unlock();
+        std::string err;
+        try {
+            if (in)
+                copy_in(S, *q, s);
+            else
+                copy_out(S, *q, s);
+        } catch (const Error &e) {
+            err = e.msg;
+        }
+        lk.lock();
+        if (in) {
+            --S.n_io_in;
+            if (err.empty() && !S.failed) {
+                q->t_ready = now_ms();
+                q->state = RS_READY;
+                S.ready.push_back(q);
+            } else {
+                release(S, q);
+                q->status = err.empty() ? OO_ETIMEOUT : OO_ECUDA;
+                q->error = err.empty() ? S.fail_msg : "input copy: " + err;
+                q->state = RS_DONE;
+                q->t_done = now_ms();
+                ++S.n_failed;
+                ++S.n_done;
+                S.cv_done.notify_all();
+            }
+        } else {
+            --S.n_io_out;
+            release(S, q);
+            if (!err.empty()) {
+                q->status = OO_ECUDA;
+                q->error = "output copy: " + err;
+                ++S.n_failed;
+            }
+            q->state = RS_DONE;
+            q->t_done = now_ms();
+            S.sum_ms[0] += q->t_admit - q->t_submit;
+            S.sum_ms[1] += q->t_ready - q->t_admit;
+            S.sum_ms[2] += q->t_pub - q->t_ready;
+            S.sum_ms[3] += q->t_dev - q->t_pub;
+            S.sum_ms[4] += q->t_done - q->t_dev;
+            ++S.n_timed;
+            ++S.n_done;
+            S.cv_done.notify_all();
+        }
+        S.cv_sched.notify_one();
+    }
 }
 
 void scheduler(Resident *Sp) {
@@ -730,38 +901,25 @@ void scheduler(Resident *Sp) {
                     unsigned bits = 0;
                     cudaMemcpyAsync(&bits, S.err, 4, cudaMemcpyDeviceToHost, S.down);
                     cudaStreamSynchronize(S.down);
-                    fail_all(S, "a bounded wait in the device-resident loop ran out (error bits " +
-                                    std::to_string(bits) + (S.ctl->fault ? "" : ", a worker exited") +
-                                    (a != cudaErrorNotReady && a != cudaSuccess ? std::string(", ") + cudaGetErrorString(a)
-                                                                                 : std::string()) +
-                                    (b != cudaErrorNotReady && b != cudaSuccess ? std::string(", ") + cudaGetErrorString(b)
-                                                                                 : std::string()) +
-                                    "; SIMT wait for entry " + std::to_string(S.ctl->stuck_at) + " saw " +
-                                    std::to_string(S.ctl->stuck_seen) + ", published " +
-                                    std::to_string(S.ctl->pub_simt) + ", written " + std::to_string(S.simt_w) +
-                                    ", uploading " + std::to_string(S.uploading.size()) + ", progress min " +
-                                    std::to_string(min_progress(S.ctl->simt_progress, S.simt_ctas)) +
-                                    "); the workers stop");
+                    std::string why = "a bounded wait in the device-resident loop ran out (error bits " +
+                                      std::to_string(bits) + (S.ctl->fault ? "" : ", a worker exited");
+                    if (a != cudaErrorNotReady && a != cudaSuccess) why += std::string(", ") + cudaGetErrorString(a);
+                    if (b != cudaErrorNotReady && b != cudaSuccess) why += std::string(", ") + cudaGetErrorString(b);
+                    if (bits & 32u)
+                        why += "; SIMT wait for entry " + std::to_string(S.ctl->stuck_at) + " saw publication " +
+                               std::to_string(S.ctl->stuck_seen) + " of " + std::to_string(S.simt_w) + " written";
+                    fail_all(S, why + "); the workers stop");
                 }
             }
-            // ---- drained requests: outputs are in staging
-            while (!S.draining.empty() && cudaEventQuery(S.draining.front()->ev) == cudaSuccess) {
-                RReq *q = S.draining.front();
-                S.draining.pop_front();
-                release(S, q);
-                q->state = RS_DONE;
-                q->t_done = now_ms();
-                ++S.n_done;
-                progress = true;
-                S.cv_done.notify_all();
-            }
-            // ---- finished on the device: copy the outputs back
+            // ---- finished on the device: an I/O thread copies the outputs back
             for (auto it = S.running.begin(); it != S.running.end();) {
                 RReq *q = *it;
                 if (S.ctl->done[q->slot] == q->gen) {
-                    download(S, *q);
-                    q->state = RS_DRAIN;
-                    S.draining.push_back(q);
+                    q->t_dev = now_ms();
+                    q->state = RS_OUTPUT;
+                    ++S.n_io_out;
+                    S.io_jobs.push_back(q);
+                    S.cv_io.notify_one();
                     it = S.running.erase(it);
                     progress = true;
                 } else {
@@ -784,12 +942,15 @@ void scheduler(Resident *Sp) {
                     S.mark_free.push_back(q->mark_slot);
                     delete q;
                 } else {
+                    S.host.release(q->h_off, q->h_bytes);  // the upload area has been read
+                    q->t_pub = t_pub;
                     q->state = RS_RUNNING;
                     S.running.push_back(q);
                 }
             }
             // ---- admissions: oldest first, by free device memory (arena and
-            // digit-slice rows), a free descriptor slot and ring room
+            // digit-slice rows) and a free descriptor slot; inputs go to an
+            // I/O thread
             while (!S.failed && !S.queue.empty() && !S.free_slots.empty()) {
                 RReq *q = S.queue.front();
                 size_t off = 0, roff = 0;
@@ -801,20 +962,39 @@ void scheduler(Resident *Sp) {
                 q->d_off = off;
                 q->row_off = roff;
                 q->slot = S.free_slots.back();
+                S.free_slots.pop_back();
                 q->gen = S.next_gen++;
+                S.queue.pop_front();
+                q->t_admit = now_ms();
+                if (q->r.kind == OO_BLOCK_JACOBI) {  // no inputs
+                    q->t_ready = q->t_admit;
+                    q->state = RS_READY;
+                    S.ready.push_back(q);
+                } else {
+                    q->state = RS_INPUT;
+                    ++S.n_io_in;
+                    S.io_jobs.push_back(q);
+                    S.cv_io.notify_one();
+                }
+                progress = true;
+            }
+            // ---- inputs on the device: stage descriptors and entries, in the
+            // order the inputs landed
+            while (!S.failed && !S.ready.empty()) {
+                RReq *q = S.ready.front();
+                if (!S.host.alloc(q->h_bytes, &q->h_off)) break;
                 if (!stage(S, *q)) {  // rings full: try again later
-                    S.dev.release(off, q->d_bytes);
-                    if (q->rows) S.rows.release(roff, q->rows);
+                    S.host.release(q->h_off, q->h_bytes);
                     break;
                 }
-                S.free_slots.pop_back();
-                S.queue.pop_front();
+                S.ready.pop_front();
                 q->state = RS_UPLOAD;
                 S.uploading.push_back(q);
                 progress = true;
             }
             // ---- keep-alive / stop entries
-            const bool idle_all = S.queue.empty() && S.uploading.empty() && S.running.empty() && S.draining.empty();
+            const bool idle_all = S.queue.empty() && S.ready.empty() && S.uploading.empty() && S.running.empty() &&
+                                  S.n_io_in == 0 && S.n_io_out == 0;
             if (!S.failed && !stop_sent && S.stop && idle_all) {
                 RReq *m = stage_markers(S, true);
                 if (m) {
@@ -840,11 +1020,24 @@ void scheduler(Resident *Sp) {
                 }
             }
             if (stop_sent && S.uploading.empty()) break;
-            if (S.failed && S.stop) break;
+            if (S.failed && S.stop && S.n_io_in == 0 && S.n_io_out == 0) break;
         } catch (const Error &e) {
             fail_all(S, e.msg);
         }
-        if (!progress) S.cv_sched.wait_for(lk, std::chrono::microseconds(20));
+        if (!progress) {
+            // work in flight: poll again at once (a timed wait sleeps tens of
+            // microseconds past its deadline, at each stage of a request);
+            // otherwise sleep until woken (a submission, an I/O thread), and
+            // at least every millisecond for the keep-alives
+            const bool busy = !S.uploading.empty() || !S.running.empty();
+            if (busy) {
+                lk.unlock();
+                std::this_thread::yield();
+                lk.lock();
+            } else {
+                S.cv_sched.wait_for(lk, std::chrono::milliseconds(1));
+            }
+        }
     }
 }
 
@@ -858,6 +1051,13 @@ void resident_stop(Resident *S) {
     }
     S->cv_sched.notify_all();
     if (S->th.joinable()) S->th.join();
+    {
+        std::lock_guard<std::mutex> g(S->mu);
+        S->io_stop = true;
+    }
+    S->cv_io.notify_all();
+    for (auto &t : S->io)
+        if (t.joinable()) t.join();
     // the workers exit at the stop entries (or have exited after a bounded
     // wait ran out)
     if (S->s_simt) cudaStreamSynchronize(S->s_simt);
@@ -867,6 +1067,8 @@ void resident_stop(Resident *S) {
     for (auto &kv : S->reqs) delete kv.second;
     for (auto e : S->event_pool) cudaEventDestroy(e);
     for (cudaStream_t s : {S->up, S->down, S->s_simt, S->s_tiles})
+        if (s) cudaStreamDestroy(s);
+    for (cudaStream_t s : S->io_streams)
         if (s) cudaStreamDestroy(s);
     if (S->dev_misc) cudaFree(S->dev_misc);
     if (S->dev_base) cudaFree(S->dev_base);
@@ -938,11 +1140,14 @@ extern "C" oo_status oo_serve_start_resident(oo_ctx *ctx, uint64_t hbm_budget_by
             S->slice_rows = (long long)(slice_bytes / ((size_t)kSlicePitch * 2));
             OO_REQUIRE(S->slice_rows > 2 * 128, OO_EINVAL, "device budget too small for the digit slices");
             S->rows.reset((size_t)S->slice_rows - 128);  // keep a box of rows past the end for TMA reads
-            if (cudaHostAlloc(&S->host_base, arena, cudaHostAllocDefault) != cudaSuccess) {
+            // pinned upload areas of the requests being staged (at most
+            // ~4 MB each: their entries fit the rings)
+            const size_t up_bytes = (size_t)64 << 20;
+            if (cudaHostAlloc(&S->host_base, up_bytes, cudaHostAllocDefault) != cudaSuccess) {
                 cudaGetLastError();
-                throw Error{OO_ENOMEM, "pinned staging of " + std::to_string(arena) + " bytes"};
+                throw Error{OO_ENOMEM, "pinned upload areas of " + std::to_string(up_bytes) + " bytes"};
             }
-            S->host.reset(arena);
+            S->host.reset(up_bytes);
             if (cudaHostAlloc(&S->mark_pool, (size_t)kMarkSlots * kMarkBytes, cudaHostAllocDefault) != cudaSuccess) {
                 cudaGetLastError();
                 S->mark_pool = nullptr;
@@ -1033,6 +1238,12 @@ extern "C" oo_status oo_serve_start_resident(oo_ctx *ctx, uint64_t hbm_budget_by
                 std::this_thread::sleep_for(std::chrono::microseconds(200));
             }
             S->last_simt_pub = S->last_tile_pub = S->last_tile_round = now_ms();
+            for (int i = 0; i < kIoThreads; ++i) {
+                cudaStream_t st = nullptr;
+                OO_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+                S->io_streams.push_back(st);
+            }
+            for (int i = 0; i < kIoThreads; ++i) S->io.emplace_back(io_worker, S, i);
             S->th = std::thread(scheduler, S);
         } catch (...) {
             {
@@ -1065,45 +1276,26 @@ oo_status resident_submit(Resident *S, const oo_serve_req *req, uint64_t *ticket
     try {
         validate_resident(*req);
         q->r = *req;
-        Plan P{};
-        {
-            std::lock_guard<std::mutex> g(S->mu);
-            P = plan_request(*S, *req);
-        }
-        q->h_in0 = P.h_in0;
-        q->h_in1 = P.h_in1;
-        q->h_out = P.h_out;
-        q->h_res = P.h_res;
-        q->h_up = P.h_up;
+        std::lock_guard<std::mutex> g(S->mu);
+        const Plan P = plan_request(*S, *req);
         q->h_bytes = P.h_bytes;
         q->d_bytes = P.d_bytes;
         q->rows = P.rows;
-        if (q->d_bytes > S->dev.size() || q->rows > S->rows.size() || P.n_simt + 16 > kRingCap ||
-            P.n_tiles + 2 * S->tile_ctas > kRingCap) {
+        if (q->d_bytes > S->dev.size() || q->rows > S->rows.size() || q->h_bytes > S->host.size() ||
+            P.n_simt + 16 > kRingCap || P.n_tiles + 2 * S->tile_ctas > kRingCap) {
             delete q;
             return OO_EINVAL;  // can never be admitted
         }
-        {
-            std::lock_guard<std::mutex> g(S->mu);
-            if (S->failed) {
-                S->c->last_error = S->fail_msg;
-                delete q;
-                return OO_ESTATE;
-            }
-            if (S->stop || S->queue.size() >= S->queue_cap || !S->host.alloc(q->h_bytes, &q->h_off)) {
-                ++S->n_busy;
-                delete q;
-                return OO_EBUSY;
-            }
+        if (S->failed) {
+            S->c->last_error = S->fail_msg;
+            delete q;
+            return OO_ESTATE;
         }
-        char *h = S->host_base + q->h_off;
-        if (req->kind == OO_BLOCK_GEMM) {
-            std::memcpy(h + q->h_in0, req->in0, (size_t)req->m * req->k * 8);
-            std::memcpy(h + q->h_in1, req->in1, (size_t)req->k * req->n * 8);
-        } else if (req->kind == OO_BLOCK_FFT) {
-            std::memcpy(h + q->h_in0, req->in0, (size_t)req->n * 16);
+        if (S->stop || S->queue.size() >= S->queue_cap) {
+            ++S->n_busy;
+            delete q;
+            return OO_EBUSY;
         }
-        std::lock_guard<std::mutex> g(S->mu);
         q->ticket = S->next_ticket++;
         q->t_submit = now_ms();
         S->reqs[q->ticket] = q;
@@ -1118,6 +1310,8 @@ oo_status resident_submit(Resident *S, const oo_serve_req *req, uint64_t *ticket
     return OO_OK;
 }
 
+// The outputs are in the caller's buffers once the request is done (an I/O
+// thread copied them there).
 oo_status resident_wait(Ctx &c, Resident *S, uint64_t ticket, int timeout_ms, double *latency_ms) {
     std::unique_lock<std::mutex> lk(S->mu);
     auto it = S->reqs.find(ticket);
@@ -1129,26 +1323,9 @@ oo_status resident_wait(Ctx &c, Resident *S, uint64_t ticket, int timeout_ms, do
             return OO_ETIMEOUT;
     }
     S->reqs.erase(ticket);
-    lk.unlock();
     const oo_status st = q->status;
-    if (st == OO_OK) {
-        const char *h = S->host_base + q->h_off;
-        const oo_serve_req &r = q->r;
-        if (r.kind == OO_BLOCK_GEMM) {
-            std::memcpy(r.out, h + q->h_out, (size_t)r.m * r.n * 8);
-        } else if (r.kind == OO_BLOCK_FFT) {
-            std::memcpy(r.out, h + q->h_out, (size_t)r.n * 16);
-        } else {
-            std::memcpy(r.out, h + q->h_out, (size_t)r.m * r.n * r.k * 4);
-            if (r.res && r.iters > 0) std::memcpy(r.res, h + q->h_res, (size_t)r.iters * 8);
-        }
-    }
     if (latency_ms) *latency_ms = q->t_done - q->t_submit;
-    {
-        std::lock_guard<std::mutex> g(S->mu);
-        S->host.release(q->h_off, q->h_bytes);
-        if (st != OO_OK) c.last_error = q->error;
-    }
+    if (st != OO_OK) c.last_error = q->error;
     delete q;
     return st;
 }
@@ -1160,9 +1337,11 @@ void resident_stats(Resident *S, oo_serve_stats_t *out) {
     out->rejected_busy = S->n_busy;
     out->failed = S->n_failed;
     out->queued = (uint64_t)S->queue.size();
-    out->running = (uint64_t)(S->uploading.size() + S->running.size() + S->draining.size());
+    out->running = (uint64_t)(S->n_io_in + S->ready.size() + S->uploading.size() + S->running.size() + S->n_io_out);
     out->device_free_bytes = S->dev.free_bytes();
     out->device_budget_bytes = S->dev.size();
+    const double n = S->n_timed ? (double)S->n_timed : 1.0;
+    for (int i = 0; i < 5; ++i) out->stage_ms[i] = S->sum_ms[i] / n;
 }
 
 }  // namespace oo

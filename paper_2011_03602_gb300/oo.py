@@ -10,6 +10,8 @@ import ctypes
 import math
 import os
 
+import threading
+
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -66,7 +68,7 @@ class oo_fb_site(_c.Structure):
 
 class oo_serve_stats_t(_c.Structure):
     _fields_ = [(n, _u64) for n in ("submitted", "completed", "rejected_busy", "failed", "queued", "running",
-                                    "device_free_bytes", "device_budget_bytes")]
+                                    "device_free_bytes", "device_budget_bytes")] + [("stage_ms", _dbl * 5)]
 
 
 class oo_run_stats(_c.Structure):
@@ -218,6 +220,10 @@ def oo_create(device=0, stream=None):
 
 def oo_destroy(ctx):
     lib().oo_destroy(ctx)
+    k = _ctx_key(ctx)
+    with _in_flight_lock:  # a service still running stopped with the context
+        for key in [key for key in _in_flight if key[0] == k]:
+            del _in_flight[key]
 
 
 def oo_last_error(ctx):
@@ -620,10 +626,13 @@ def oo_serve_start(ctx, slots=8, hbm_budget_bytes=8 << 30, queue_cap=4096):
 
 
 def serve_request(kind, **kw):
-    """Build an oo_serve_req from numpy host arrays (kept alive by the caller
-    until oo_wait returns): gemm(A, B, C, prec), fft(x, X, dir), jacobi(I, J,
-    K, iters, p, res, omega).  GEMMs default to the FP64-equivalent pattern."""
+    """Build an oo_serve_req from numpy host arrays: gemm(A, B, C, prec),
+    fft(x, X, dir), jacobi(I, J, K, iters, p, res, omega).  GEMMs default to
+    the FP64-equivalent pattern.  The request holds its arrays, and oo_submit
+    holds them from submission until oo_wait returns for the ticket (the
+    library reads and writes them in between)."""
     r = oo_serve_req()
+    r._arrays = tuple(v for v in kw.values() if isinstance(v, np.ndarray))
     r.client = kw.get("client", OO_LANG_PYTHON)
     if kind == "gemm":
         A, B, C = kw["A"], kw["B"], kw["C"]
@@ -650,10 +659,25 @@ def oo_serve_start_resident(ctx, hbm_budget_bytes, queue_cap=1024, tensor_ctas=0
     _check(ctx, lib().oo_serve_start_resident(ctx, hbm_budget_bytes, queue_cap, tensor_ctas))
 
 
+# arrays of submitted requests, by (context, ticket), until oo_wait returns
+_in_flight = {}
+_in_flight_lock = threading.Lock()
+
+
+def _ctx_key(ctx):
+    return ctx.value if hasattr(ctx, "value") else ctx
+
+
+def _hold(ctx, req, ticket):
+    with _in_flight_lock:
+        _in_flight[(_ctx_key(ctx), ticket)] = getattr(req, "_arrays", ())
+
+
 def oo_submit(ctx, req):
     """-> ticket; raises OOError (status OO_EBUSY when back-pressured)."""
     t = _u64()
     _check(ctx, lib().oo_submit(ctx, _c.byref(req), _c.byref(t)))
+    _hold(ctx, req, t.value)
     return t.value
 
 
@@ -661,24 +685,37 @@ def oo_submit_status(ctx, req):
     """-> (status, ticket) without raising (for load generators)."""
     t = _u64()
     st = lib().oo_submit(ctx, _c.byref(req), _c.byref(t))
+    if st == 0:
+        _hold(ctx, req, t.value)
     return st, t.value
 
 
 def oo_wait(ctx, ticket, timeout_ms=60000):
-    """-> latency in ms; raises OOError (OO_ETIMEOUT if not done in time)."""
+    """-> latency in ms; raises OOError (OO_ETIMEOUT if not done in time,
+    and the ticket and its arrays stay held)."""
     lat = _dbl()
-    _check(ctx, lib().oo_wait(ctx, ticket, timeout_ms, _c.byref(lat)))
+    st = lib().oo_wait(ctx, ticket, timeout_ms, _c.byref(lat))
+    if st != OO_ETIMEOUT:
+        with _in_flight_lock:
+            _in_flight.pop((_ctx_key(ctx), ticket), None)
+    _check(ctx, st)
     return lat.value
 
 
 def oo_serve_stats(ctx):
     st = oo_serve_stats_t()
     _check(ctx, lib().oo_serve_stats(ctx, _c.byref(st)))
-    return {n: getattr(st, n) for n, _ in oo_serve_stats_t._fields_}
+    out = {n: getattr(st, n) for n, _ in oo_serve_stats_t._fields_[:-1]}
+    out["stage_ms"] = dict(zip(("queued", "input", "staging", "device", "output"), list(st.stage_ms)))
+    return out
 
 
 def oo_serve_stop(ctx):
     _check(ctx, lib().oo_serve_stop(ctx))
+    k = _ctx_key(ctx)
+    with _in_flight_lock:  # tickets not waited for are discarded with the service
+        for key in [key for key in _in_flight if key[0] == k]:
+            del _in_flight[key]
 
 
 def oo_lookup_block(callee, lang):

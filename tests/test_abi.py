@@ -201,3 +201,21 @@ def test_context_options_host_only():
     csrc = os.path.join(ROOT, "paper_2011_03602_gb300", "csrc")
     for f in os.listdir(csrc):
         assert "getenv" not in open(os.path.join(csrc, f), errors="replace").read(), f
+
+
+def test_serve_requests_hold_their_arrays_until_waited():
+    """The Python binding keeps a request's arrays alive from oo_submit until
+    oo_wait returns: the library reads inputs and writes outputs in between
+    (the device-resident loop copies them when the request is admitted and
+    when it completes), so arrays the caller dropped must not be freed."""
+    from paper_2011_03602_gb300 import oo
+    A, B, C = np.ones((4, 3)), np.ones((3, 5)), np.empty((4, 5))
+    r = oo.serve_request("gemm", A=A, B=B, C=C)
+    assert all(any(x is y for y in r._arrays) for x in (A, B, C))
+    p, res = np.empty(27, np.float32), np.empty(2)
+    r = oo.serve_request("jacobi", I=3, J=3, K=3, iters=2, p=p, res=res)
+    assert all(any(x is y for y in r._arrays) for x in (p, res))
+    oo._hold(7, r, 11)
+    assert oo._in_flight[(7, 11)] == r._arrays
+    with oo._in_flight_lock:
+        del oo._in_flight[(7, 11)]
