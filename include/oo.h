@@ -603,6 +603,38 @@ oo_status oo_serve_stop(oo_ctx *ctx);
  * could wait for the workers).  OO_ESTATE if the context already serves.  */
 oo_status oo_serve_start_resident(oo_ctx *ctx, uint64_t hbm_budget_bytes, int queue_cap, int tensor_ctas);
 
+/* ------------------------------------------------------- serving replicas */
+/* Requests routed over several serving contexts (one per GPU; each already
+ * serving with oo_serve_start or oo_serve_start_resident) by free device
+ * memory (Sec. 3: the same method on whichever destination is free):
+ * requests are independent, so replicas share nothing.  A replica's free
+ * bytes are its arena's free bytes, but at most its budget less the
+ * footprints (oo_serve_footprint) of the requests this router sent there and
+ * that are not yet waited for (queued requests do not occupy the arena yet).
+ * A request goes to the replica with the most free bytes among those with
+ * room for its footprint (ties: fewer requests queued or running there, then the
+ * lower index); when none has room, to the replica with the fewest requests
+ * in flight, where it queues.  On OO_EBUSY or OO_ESTATE from that replica the
+ * next best is tried.  The contexts stay owned by the caller and must
+ * outlive the router.  Thread-safe.                                        */
+typedef struct oo_router oo_router;
+oo_status oo_router_create(oo_ctx *const *ctxs, int n, oo_router **out);
+/* *replica: the index (into ctxs) that took the request, for oo_router_wait */
+oo_status oo_router_submit(oo_router *r, const oo_serve_req *req, int *replica, uint64_t *ticket);
+oo_status oo_router_wait(oo_router *r, int replica, uint64_t ticket, int timeout_ms, double *latency_ms);
+void oo_router_destroy(oo_router *r);
+/* The routing decision alone, host-only: free_bytes[n] and queued[n] (queued
+ * or running) per replica, `need` the request's footprint -> *replica.       */
+oo_status oo_route_pick(const uint64_t *free_bytes, const uint64_t *queued, int n, uint64_t need, int *replica);
+/* m requests routed in order, each decision charging its replica with the
+ * request's bytes and one more request in flight: with one process per GPU,
+ * every process computes the same owners from the same all-gathered figures
+ * and serves the requests it owns.  Host-only.                             */
+oo_status oo_route_batch(const uint64_t *free_bytes, const uint64_t *queued, int n, const uint64_t *needs, int m,
+                         int *replicas);
+/* The routing estimate of a request's device footprint (bytes).  Host-only. */
+oo_status oo_serve_footprint(const oo_serve_req *req, uint64_t *bytes);
+
 /* --------------------------------------------------- batched function blocks */
 /* Many GEMM and FFT requests of uneven sizes, on caller-owned device buffers.
  *   GEMM (kind OO_BLOCK_GEMM): C (m x n) = A (m x k) B (k x n), row-major,

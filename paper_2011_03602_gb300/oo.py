@@ -158,6 +158,13 @@ def lib():
         "oo_wait": (_c.c_int, [_vp, _u64, _c.c_int, P(_dbl)]),
         "oo_serve_stats": (_c.c_int, [_vp, P(oo_serve_stats_t)]),
         "oo_serve_stop": (_c.c_int, [_vp]),
+        "oo_router_create": (_c.c_int, [_vp, _c.c_int, P(_vp)]),
+        "oo_router_submit": (_c.c_int, [_vp, P(oo_serve_req), P(_c.c_int), P(_u64)]),
+        "oo_router_wait": (_c.c_int, [_vp, _c.c_int, _u64, _c.c_int, P(_dbl)]),
+        "oo_router_destroy": (None, [_vp]),
+        "oo_route_pick": (_c.c_int, [_vp, _vp, _c.c_int, _u64, P(_c.c_int)]),
+        "oo_route_batch": (_c.c_int, [_vp, _vp, _c.c_int, _vp, _c.c_int, _vp]),
+        "oo_serve_footprint": (_c.c_int, [P(oo_serve_req), P(_u64)]),
         "oo_fft_c128_dev": (_c.c_int, [_vp, _c.c_int64, _c.c_int, _c.c_int, _vp, _vp]),
     }
     for name, (res, args) in sig.items():
@@ -716,6 +723,71 @@ def oo_serve_stop(ctx):
     with _in_flight_lock:  # tickets not waited for are discarded with the service
         for key in [key for key in _in_flight if key[0] == k]:
             del _in_flight[key]
+
+
+def oo_route_pick(free_bytes, queued, need):
+    """The replica a request of `need` bytes goes to (host-only)."""
+    f = np.ascontiguousarray(free_bytes, dtype=np.uint64)
+    q = np.ascontiguousarray(queued, dtype=np.uint64)
+    if f.size != q.size or f.size < 1:
+        raise ValueError("one free-bytes and one queued figure per replica")
+    r = _c.c_int()
+    _check(None, lib().oo_route_pick(f.ctypes.data_as(_vp), q.ctypes.data_as(_vp), f.size, int(need), _c.byref(r)))
+    return r.value
+
+
+def oo_route_batch(free_bytes, queued, needs):
+    """Owners of requests routed in order (host-only; see oo.h)."""
+    f = np.ascontiguousarray(free_bytes, dtype=np.uint64)
+    q = np.ascontiguousarray(queued, dtype=np.uint64)
+    nd = np.ascontiguousarray(needs, dtype=np.uint64)
+    if f.size != q.size or f.size < 1:
+        raise ValueError("one free-bytes and one queued figure per replica")
+    out = np.empty(nd.size, dtype=np.int32)
+    _check(None, lib().oo_route_batch(f.ctypes.data_as(_vp), q.ctypes.data_as(_vp), f.size,
+                                      nd.ctypes.data_as(_vp), nd.size, out.ctypes.data_as(_vp)))
+    return out
+
+
+def oo_serve_footprint(req):
+    b = _u64()
+    _check(None, lib().oo_serve_footprint(_c.byref(req), _c.byref(b)))
+    return b.value
+
+
+class Router:
+    """Serving replicas (oo_router_*): requests routed over serving contexts
+    by free device memory.  submit -> (replica, ticket); wait(replica,
+    ticket) -> latency ms.  The request's arrays are held until waited."""
+
+    def __init__(self, ctxs):
+        self.ctxs = list(ctxs)
+        arr = (_vp * len(self.ctxs))(*[_ctx_key(c) for c in self.ctxs])
+        h = _vp()
+        _check(None, lib().oo_router_create(arr, len(self.ctxs), _c.byref(h)))
+        self.h = h
+
+    def submit(self, req):
+        r, t = _c.c_int(), _u64()
+        st = lib().oo_router_submit(self.h, _c.byref(req), _c.byref(r), _c.byref(t))
+        if st != OO_OK:
+            raise OOError(st, "router: " + oo_status_str(st))
+        _hold(self.ctxs[r.value], req, t.value)
+        return r.value, t.value
+
+    def wait(self, replica, ticket, timeout_ms=60000):
+        lat = _dbl()
+        st = lib().oo_router_wait(self.h, replica, ticket, timeout_ms, _c.byref(lat))
+        if st != OO_ETIMEOUT:
+            with _in_flight_lock:
+                _in_flight.pop((_ctx_key(self.ctxs[replica]), ticket), None)
+        _check(self.ctxs[replica], st)
+        return lat.value
+
+    def close(self):
+        if self.h:
+            lib().oo_router_destroy(self.h)
+            self.h = None
 
 
 def oo_lookup_block(callee, lang):
