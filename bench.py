@@ -14,6 +14,7 @@ iteration; setup 56 B per point; faces 4 B per face point and iteration).
 cores on a bounded sample of the same workload.
 """
 import argparse
+import ctypes
 import json
 import os
 import statistics
@@ -861,9 +862,43 @@ def _serve_refs(job):
     return (kind, a), (res, p.reshape(-1).astype(np.float32))
 
 
+def _digest64(arrays):
+    """XOR and sum (mod 2^64) of the whole 64-bit words of each array, as the
+    C client (frontends/c/oo_loadgen.c) digests its outputs."""
+    x, t = 0, 0
+    for a in arrays:
+        b = np.ascontiguousarray(a).reshape(-1).view(np.uint8)
+        w = b[: (b.size // 8) * 8].view(np.uint64)
+        if w.size:
+            x ^= int(np.bitwise_xor.reduce(w))
+            t = (t + int(np.sum(w, dtype=np.uint64))) & ((1 << 64) - 1)
+    return x, t
+
+
+class _CLoadPools(ctypes.Structure):
+    _fields_ = [("gemm_a", ctypes.c_void_p * 16), ("gemm_b", ctypes.c_void_p * 16), ("gemm_n", ctypes.c_int32 * 16),
+                ("fft_x", ctypes.c_void_p * 32), ("fft_log2", ctypes.c_int32 * 32),
+                ("jac_i", ctypes.c_int32 * 8), ("jac_j", ctypes.c_int32 * 8), ("jac_k", ctypes.c_int32 * 8),
+                ("jac_iters", ctypes.c_int32), ("prec", ctypes.c_int32), ("client", ctypes.c_int32),
+                ("max_in_flight", ctypes.c_int32)]
+
+
+class _CLoadItem(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("size", ctypes.c_int32), ("arrival", ctypes.c_double)]
+
+
+class _CLoadResult(ctypes.Structure):
+    _fields_ = [("latency_ms", ctypes.c_double), ("status", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("digest_xor", ctypes.c_uint64), ("digest_sum", ctypes.c_uint64)]
+
+
 def run_serve(args):
-    """Serving loop: Poisson arrivals at each offered rate, split over three
-    client threads (tags C / Python / Java; all submit through the C ABI),
+    """Serving loop: Poisson arrivals at each offered rate, the stream split
+    in thirds over client front ends that all submit through the C ABI: the
+    C client (frontends/c/oo_loadgen.c, run in this process on its own
+    thread; it allocates its own output buffers), a Python ctypes client,
+    and the Java share -- no JDK exists on either machine, so a second
+    ctypes client submits that third and the line says so.
     mix 50% GEMM (square, n log-uniform in [64, 2048], FP64-equivalent by
     default), 30% FFT (2^10..2^20), 20% Jacobi solves (65x65x129 or
     129x129x257, 100 iterations).  Reported: solves/s, p50/p99 latency of
@@ -876,8 +911,14 @@ def run_serve(args):
     import threading
     refs_pool = mp.get_context("spawn").Pool(host_cores())
     import torch
+    from paper_2011_03602_gb300 import build as pkg_build
     from paper_2011_03602_gb300 import oo, synth
     torch.cuda.set_device(0)
+    oo.lib()
+    cgen = ctypes.CDLL(pkg_build.build_loadgen())
+    cgen.oo_load_run.restype = ctypes.c_int
+    cgen.oo_load_run.argtypes = [ctypes.c_void_p, ctypes.POINTER(_CLoadPools), ctypes.POINTER(_CLoadItem),
+                                 ctypes.c_int, ctypes.POINTER(_CLoadResult)]
     rates = [int(x) for x in args.serve_rates.split(",")]
     window = args.serve_window
     # input pools: one operand set per size (results are still computed per request)
@@ -894,6 +935,7 @@ def run_serve(args):
     # oracle at the end; every other result's digest must equal the first's
     # (the blocks are deterministic), which keeps host memory bounded
     first, digests, n_checked, n_differ = {}, {}, [0], [0]
+    first64, c_first, n_c_checked = {}, {}, [0]  # 64-bit-word digests (the C client's form)
 
     def draw(rng):
         u = rng.random()
@@ -917,6 +959,15 @@ def run_serve(args):
 
     ctx = oo.oo_create(0)
     tuned = {"%dx%dx%d" % g: oo.oo_tune_stencil(ctx, *g)[0] for g in grids}  # stencil tile per grid
+    # the C client's input pools: the same arrays as the ctypes clients'
+    c_pools = _CLoadPools()
+    for j, n in enumerate(gemm_sizes):
+        c_pools.gemm_a[j], c_pools.gemm_b[j], c_pools.gemm_n[j] = (pool_g[n][0].ctypes.data, pool_g[n][1].ctypes.data, n)
+    for e in range(10, 21):
+        c_pools.fft_x[e - 10], c_pools.fft_log2[e - 10] = pool_f[e].ctypes.data, e
+    for j, (I, J, K) in enumerate(grids):
+        c_pools.jac_i[j], c_pools.jac_j[j], c_pools.jac_k[j] = I, J, K
+    c_pools.jac_iters, c_pools.prec, c_pools.client, c_pools.max_in_flight = 100, prec, 0, 256
     modes = [m for m in args.serve_modes.split(",") if m]
     per_mode = {}
     for mode in modes:
@@ -930,6 +981,8 @@ def run_serve(args):
                               queue_cap=args.serve_queue)
         first.clear()
         digests.clear()
+        first64.clear()
+        c_first.clear()
         # warm-up: one of each kind
         for kind, a in (("gemm", 2048), ("fft", 20), ("jacobi", 1)):
             kw = make(kind, a)
@@ -941,11 +994,13 @@ def run_serve(args):
             arrivals = np.cumsum(rng.exponential(1.0 / rate, n_req))
             kinds = [draw(rng) for _ in range(n_req)]
             lat, rejected, lock = [], [0], threading.Lock()
+            lat_by = {"c": [], "python_ctypes": [], "java_share_via_ctypes": []}
             st0 = oo.oo_serve_stats(ctx)
             t0 = time.perf_counter() + 0.05
 
             def client(tag):
                 mine, done = [], []
+                fe = "python_ctypes" if tag == 1 else "java_share_via_ctypes"
                 for i in range(tag, n_req, 3):
                     kind, a = kinds[i]
                     kw = make(kind, a)
@@ -970,6 +1025,24 @@ def run_serve(args):
                     keep(ka, kw)
                 with lock:
                     lat.extend(got)
+                    lat_by[fe].extend(got)
+
+            c_idx = list(range(0, n_req, 3))
+            c_items = (_CLoadItem * max(1, len(c_idx)))()
+            for j, i in enumerate(c_idx):
+                kind, a = kinds[i]
+                c_items[j].kind = {"gemm": oo.OO_BLOCK_GEMM, "fft": oo.OO_BLOCK_FFT, "jacobi": oo.OO_BLOCK_JACOBI}[kind]
+                c_items[j].size = gemm_sizes.index(a) if kind == "gemm" else (a - 10 if kind == "fft" else a)
+                c_items[j].arrival = t0 + float(arrivals[i])
+            c_res = (_CLoadResult * max(1, len(c_idx)))()
+
+            def c_client():
+                busy = cgen.oo_load_run(ctx, ctypes.byref(c_pools), c_items, len(c_idx), c_res)
+                got = [c_res[j].latency_ms for j in range(len(c_idx)) if c_res[j].status == 0]
+                with lock:
+                    rejected[0] += max(0, busy)
+                    lat.extend(got)
+                    lat_by["c"].extend(got)
 
             def keep(ka, kw):
                 kind, _ = ka
@@ -981,16 +1054,33 @@ def run_serve(args):
                     if ka not in first:
                         first[ka] = [o.copy() for o in outs]
                         digests[ka] = dg
+                        first64[ka] = _digest64(outs)
                     elif digests[ka] != dg:
                         n_differ[0] += 1
 
-            ths = [threading.Thread(target=client, args=(tag,)) for tag in (0, 1, 2)]
+            ths = [threading.Thread(target=c_client)] + [threading.Thread(target=client, args=(tag,)) for tag in (1, 2)]
             start = time.perf_counter()
             for th in ths:
                 th.start()
             for th in ths:
                 th.join()
             elapsed = time.perf_counter() - start
+            # the C client's results: every one's digest equals that of the
+            # same request's result through ctypes (or, for a request kind
+            # only the C client drew, that of its first C result)
+            for j, i in enumerate(c_idx):
+                r = c_res[j]
+                if r.status == oo.OO_EBUSY:
+                    continue
+                if r.status != 0:
+                    raise oo.OOError(r.status, "C client: " + oo.oo_status_str(r.status))
+                ka = kinds[i]
+                d = (int(r.digest_xor), int(r.digest_sum))
+                ref = first64.get(ka) or c_first.setdefault(ka, d)
+                n_checked[0] += 1
+                n_c_checked[0] += 1
+                if d != ref:
+                    n_differ[0] += 1
             lat_a = np.array(lat) if lat else np.array([np.nan])
             st1 = oo.oo_serve_stats(ctx)
             dn = max(1, st1["completed"] - st0["completed"])
@@ -1000,7 +1090,11 @@ def run_serve(args):
                             "rejected_busy": rejected[0], "solves_per_s": round(len(lat) / elapsed, 1),
                             "p50_ms": round(float(np.percentile(lat_a, 50)), 3),
                             "p99_ms": round(float(np.percentile(lat_a, 99)), 3),
-                            "mean_stage_ms": stage})
+                            "mean_stage_ms": stage,
+                            "by_front_end": {k: {"admitted": len(v),
+                                                 "p50_ms": round(float(np.percentile(v, 50)), 3) if v else None,
+                                                 "p99_ms": round(float(np.percentile(v, 99)), 3) if v else None}
+                                             for k, v in lat_by.items()}})
         stats = oo.oo_serve_stats(ctx)
         oo.oo_serve_stop(ctx)
         per_mode[mode] = (results, stats, dict(first))
@@ -1054,7 +1148,12 @@ def run_serve(args):
            "config": {"workload": "serve_mix_50gemm64-2048_30fft2e10-2e20_20jacobi65-129_it100",
                       "gemm_precision": args.serve_prec,
                       "slots": args.serve_slots, "device_budget_gb": args.serve_budget_gb,
-                      "queue_cap": args.serve_queue, "window_s": window, "clients": 3},
+                      "queue_cap": args.serve_queue, "window_s": window,
+                      "front_ends": {"c": "frontends/c/oo_loadgen.c: C ABI calls from its own thread in this process, "
+                                          "its own output buffers",
+                                     "python_ctypes": "oo.py ctypes binding",
+                                     "java_share_via_ctypes": "no JDK on either machine: the Java third of the "
+                                                              "stream is submitted by a second ctypes client"}},
            "served": results, "served_loop": modes[0],
            "served_other_loops": {m: per_mode[m][0] for m in modes[1:]},
            "plain_one_call_per_solve": plain,
@@ -1065,6 +1164,7 @@ def run_serve(args):
                "fft_rel_l2": worst["fft"], "jacobi_residual_rel": worst["jacobi_res"],
                "jacobi_p_abs": worst["jacobi_p"], "results": n_checked[0],
                "results_differing_from_first_of_same_size": n_differ[0],
+               "results_of_the_c_client_checked_by_digest": n_c_checked[0],
                "how": "first result of each kind and size against the oracle; every other result's "
                       "digest against that first result's"}}
     print(json.dumps(out))

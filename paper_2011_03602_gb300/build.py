@@ -114,6 +114,27 @@ def build_c_client(force: bool = False) -> str:
     return CLIENT_BIN
 
 
+LOADGEN_SRC = os.path.join(PKG, "frontends", "c", "oo_loadgen.c")
+LOADGEN_LIB = os.path.join(PKG, "frontends", "c", "liboo_loadgen.so")
+
+
+def build_loadgen(force: bool = False) -> str:
+    """The C serving client as a shared object (run in-process by load
+    generators beside their own clients), linked against liboo.so."""
+    lib = build()
+    if not force and os.path.exists(LOADGEN_LIB) and \
+            os.path.getmtime(LOADGEN_LIB) >= max(os.path.getmtime(LOADGEN_SRC), os.path.getmtime(lib)):
+        return LOADGEN_LIB
+    tmp = LOADGEN_LIB + ".tmp.%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=c11", "-Wall", "-shared", "-fPIC", "-I" + os.path.join(ROOT, "include"),
+           LOADGEN_SRC, "-L" + PKG, "-loo", "-Wl,-rpath," + PKG, "-lpthread", "-o", tmp]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError("C load generator build failed: %s\n%s" % (r.stdout, r.stderr))
+    os.replace(tmp, LOADGEN_LIB)
+    return LOADGEN_LIB
+
+
 def clean():
     shutil.rmtree(BUILD, ignore_errors=True)
     if os.path.exists(LIB):
