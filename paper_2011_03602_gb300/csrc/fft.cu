@@ -164,9 +164,9 @@ __global__ void __launch_bounds__(kFftThreads, 2) fft_pass_kernel(FftArgs a) {
             // W_N^{k1 n2}, k1 = t, n2 = c0 + c; m < N so no reduction needed
             const long long m = (long long)t * (c0 + c);
             const int mh = (int)(m >> kTwSplit), ml = (int)(m & ((1 << kTwSplit) - 1));
-            cplx w = ff::cmul(ld_cplx(a.tw_hi + mh), ld_cplx(a.tw_lo + ml));
+            cplx w = ff::cmul_lazy(ld_cplx(a.tw_hi + mh), ld_cplx(a.tw_lo + ml));
             if (inv) w = ff::conj(w);
-            v = ff::cmul(v, w);
+            v = ff::cmul_lazy(v, w);  // pass 2 takes lazy pairs
             st_cplx(a.out_ff + (long long)b * n + (long long)t * N2 + c0 + c, v);
         } else {
             const int tb = MODE == 0 ? c0 + c : b;

@@ -116,15 +116,16 @@ __device__ __forceinline__ void stage_r4(float4 *sd, const float4 *stw, int log2
         if (Ls > 1) {
             const int k = j & (Ls - 1);
 #pragma unroll
-            for (int q = 1; q < 4; ++q) x[q] = ff::cmul(x[q], twiddle(stw, (q - 1) * Ls + k, inv));
+            for (int q = 1; q < 4; ++q) x[q] = ff::cmul_lazy(x[q], twiddle(stw, (q - 1) * Ls + k, inv));
         }
-        const cplx a0 = ff::cadd(x[0], x[2]), a1 = ff::csub(x[0], x[2]);
-        const cplx b0 = ff::cadd(x[1], x[3]), b1 = ff::csub(x[1], x[3]);
+        // lazy float-float through the butterfly, one renormalisation per output
+        const cplx a0 = ff::cadd_lazy(x[0], x[2]), a1 = ff::csub_lazy(x[0], x[2]);
+        const cplx b0 = ff::cadd_lazy(x[1], x[3]), b1 = ff::csub_lazy(x[1], x[3]);
         const cplx rb1 = inv ? ff::mul_pos_i(b1) : ff::mul_neg_i(b1);
-        Y[r][0] = ff::cadd(a0, b0);
-        Y[r][2] = ff::csub(a0, b0);
-        Y[r][1] = ff::cadd(a1, rb1);
-        Y[r][3] = ff::csub(a1, rb1);
+        Y[r][0] = ff::norm(ff::cadd_lazy(a0, b0));
+        Y[r][2] = ff::norm(ff::csub_lazy(a0, b0));
+        Y[r][1] = ff::norm(ff::cadd_lazy(a1, rb1));
+        Y[r][3] = ff::norm(ff::csub_lazy(a1, rb1));
     }
     __syncthreads();
 #pragma unroll
@@ -264,9 +265,9 @@ __device__ __forceinline__ void fft_group_item(const FftItem &item, const FftGro
         if (item.mode == 1) {
             const long long m = (long long)t * (item.c0 + c);
             const int mh = (int)(m >> kTwSplit), ml = (int)(m & ((1 << kTwSplit) - 1));
-            cplx w = ff::cmul(ld_cplx(R0.tw_hi + mh), ld_cplx(R0.tw_lo + ml));
+            cplx w = ff::cmul_lazy(ld_cplx(R0.tw_hi + mh), ld_cplx(R0.tw_lo + ml));
             if (inv) w = ff::conj(w);
-            st_cplx(R0.mid + (long long)t * N2 + item.c0 + c, ff::cmul(v, w));
+            st_cplx(R0.mid + (long long)t * N2 + item.c0 + c, ff::cmul_lazy(v, w));  // pass 2 takes lazy pairs
         } else if (item.mode == 0) {
             if (c >= item.count) continue;
             const int r = tlist[item.first + c];
