@@ -11,6 +11,69 @@
 #include "ff.cuh"
 
 namespace oo {
+namespace ff {
+
+// Lazy forms for chains of operations (the FFT's butterflies): the same
+// error-free hi-part transforms, without the final renormalisation.  A lazy
+// result (h, l) is an unevaluated sum whose l may exceed ulp(h) after
+// cancellation; every operation below takes such inputs (two-sum on the hi
+// parts, the lo parts added), and the chain ends with norm().  The error of
+// each step stays a few units of 2^-48 relative to the magnitudes of its
+// operands, which is what a normwise bound for the transform needs.
+__device__ __forceinline__ void add_lazy(float ah, float al, float bh, float bl, float &h, float &l) {
+    float e;
+    two_sum(ah, bh, h, e);
+    l = __fadd_rn(e, __fadd_rn(al, bl));
+}
+__device__ __forceinline__ cplx cadd_lazy(const cplx &a, const cplx &b) {
+    cplx r;
+    add_lazy(a.rh, a.rl, b.rh, b.rl, r.rh, r.rl);
+    add_lazy(a.ih, a.il, b.ih, b.il, r.ih, r.il);
+    return r;
+}
+__device__ __forceinline__ cplx csub_lazy(const cplx &a, const cplx &b) {
+    cplx r;
+    add_lazy(a.rh, a.rl, -b.rh, -b.rl, r.rh, r.rl);
+    add_lazy(a.ih, a.il, -b.ih, -b.il, r.ih, r.il);
+    return r;
+}
+// a * w as cmul, without its final renormalisation
+__device__ __forceinline__ cplx cmul_lazy(const cplx &a, const cplx &w) {
+    cplx r;
+    {
+        float p1, e1, p2, e2, e3;
+        two_prod(a.rh, w.rh, p1, e1);
+        two_prod(a.ih, w.ih, p2, e2);
+        two_sum(p1, -p2, r.rh, e3);
+        float e = __fadd_rn(__fsub_rn(e1, e2), e3);
+        e = __fmaf_rn(a.rh, w.rl, e);
+        e = __fmaf_rn(a.rl, w.rh, e);
+        e = __fmaf_rn(-a.ih, w.il, e);
+        r.rl = __fmaf_rn(-a.il, w.ih, e);
+    }
+    {
+        float p1, e1, p2, e2, e3;
+        two_prod(a.rh, w.ih, p1, e1);
+        two_prod(a.ih, w.rh, p2, e2);
+        two_sum(p1, p2, r.ih, e3);
+        float e = __fadd_rn(__fadd_rn(e1, e2), e3);
+        e = __fmaf_rn(a.rh, w.il, e);
+        e = __fmaf_rn(a.rl, w.ih, e);
+        e = __fmaf_rn(a.ih, w.rl, e);
+        r.il = __fmaf_rn(a.il, w.rh, e);
+    }
+    return r;
+}
+// renormalise both components (|l| <= ulp(h) / 2 afterwards when |h| >= |l|)
+__device__ __forceinline__ cplx norm(const cplx &a) {
+    cplx r;
+    fast_two_sum(a.rh, a.rl, r.rh, r.rl);
+    fast_two_sum(a.ih, a.il, r.ih, r.il);
+    return r;
+}
+
+}  // namespace ff
+
 namespace {
 
 constexpr int kFftThreads = 512;
