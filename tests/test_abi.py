@@ -219,3 +219,19 @@ def test_serve_requests_hold_their_arrays_until_waited():
     assert oo._in_flight[(7, 11)] == r._arrays
     with oo._in_flight_lock:
         del oo._in_flight[(7, 11)]
+
+
+def test_resident_loop_launches_its_workers_only_at_start():
+    """The device-resident serving loop launches no kernel per request: the
+    only launch sites in its source are the two workers', inside
+    oo_serve_start_resident, and the scheduler, admission, I/O and wait
+    code issue copies, events and stream queries only."""
+    src = open(os.path.join(os.path.dirname(oo.__file__), "csrc", "serve_resident.cu")).read()
+    start = src.index("oo_status oo_serve_start_resident(")
+    end = src.index("\n}\n", start)
+    launches = [m.start() for m in re.finditer(r"<<<", src)]
+    tiles = [m.start() for m in re.finditer(r"\blaunch_resident_tiles\(", src)]
+    assert len(launches) == 1 and start < launches[0] < end
+    calls = [t for t in tiles if not src[max(0, t - 5):t].startswith("void ")]
+    assert len(calls) == 1 and start < calls[0] < end
+    assert "cudaLaunch" not in src and "cudaGraphLaunch" not in src
