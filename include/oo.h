@@ -237,10 +237,9 @@ oo_status oo_stencil_dev(oo_ctx *ctx, int I, int J, int K, int pitch,
 oo_status oo_stencil_check(oo_ctx *ctx);
 
 /* The same stencil sweep as oo_stencil_dev, for callers that cannot
- * allocate device memory at the time they call: for example code being
- * captured into a CUDA graph (cudaMalloc is not a capturable stream
- * operation), serving loops that draw on a fixed, pre-reserved memory pool,
- * or language runtimes that own every device allocation.  The paper has no
+ * allocate device memory at the time they call: for example serving loops
+ * that draw on a fixed, pre-reserved memory pool, or language runtimes that
+ * own every device allocation.  The paper has no
  * counterpart; this is a deployment variant of the same nest.
  * It calls no cudaMalloc, cudaFree or allocating library routine: its
  * scratch (per-warp partial residuals, a completion counter, an error word)

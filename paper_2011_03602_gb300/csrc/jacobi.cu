@@ -1089,11 +1089,9 @@ unsigned stencil_plan_check(StencilPlan *sp, cudaStream_t s) {
 }
 
 // ======================================= allocation-free stencil entry point
-// Some callers cannot allocate device memory when they call in: a host that
-// is capturing its work into a CUDA graph (cudaMalloc is not a stream
-// operation and is not allowed inside a capture), a serving loop with a
-// fixed device-memory budget handed out by its own pool, or a language
-// runtime that owns every allocation on the device.  For them the stencil
+// Some callers cannot allocate device memory when they call in: a serving
+// loop with a fixed device-memory budget handed out by its own pool, or a
+// language runtime that owns every allocation on the device.  For them the stencil
 // sweep below keeps its scratch (per-warp partial residuals, the CTA-done
 // counter and the error word) in one static device array instead of
 // cudaMalloc'd memory.  The caller still passes every input and output.

@@ -1,6 +1,6 @@
 """The allocation-free stencil entry point (for callers that cannot
-allocate device memory when they call, e.g. inside a CUDA-graph capture or
-on a fixed memory pool) must give what the allocating entry point gives,
+allocate device memory when they call, e.g. on a fixed memory pool) must
+give what the allocating entry point gives,
 and what the oracle gives, and must report a bounded wait that ran out.
 
 Runs last (file name) so a failure here cannot hide other results; it works
