@@ -311,7 +311,7 @@ def gemm_component(oo, ctx, torch, prec, A_h, B_h, A, B, C, with_errors):
     for _ in range(3):
         oo.oo_gemm_f64_dev(ctx, n, n, n, A, n, B, n, C, n, prec=prec)
     oo.oo_sync(ctx)
-    reps = 10 if prec == oo.OO_PREC_SPLIT3_BF16 else 4
+    reps = 4 if prec == oo.OO_PREC_FP64EQ else 10
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(ctx_stream_holder[0])
     for _ in range(reps):
@@ -325,10 +325,17 @@ def gemm_component(oo, ctx, torch, prec, A_h, B_h, A, B, C, with_errors):
     tensor = products * 2 * n ** 3 / (ms * 1e-3) / 1e12
     g = {"n": n, "ms": round(ms, 4), "solves_per_s": round(1e3 / ms, 2),
          "fp64_equiv_tflops": round(2 * n ** 3 / (ms * 1e-3) / 1e12, 2),
-         "bf16_products": products, "tensor_tflops": round(tensor, 1), "peak_bf16_tflops": peak,
-         "peak_source": src, "frac_of_bf16_peak": round(tensor / peak, 4),
-         "precision": "split3_bf16" if prec == oo.OO_PREC_SPLIT3_BF16 else
-         "fp64eq_ozaki_bf16_beta%d_L%d_kblock%d" % (beta, levels, kb)}
+         "tensor_tflops": round(tensor, 1), "peak_source": src}
+    if prec == oo.OO_PREC_SPLIT3_TF32:
+        # TF32 peak: the measured BF16 peak x the nominal dense ratio 1.1 / 2.25 PFLOP/s
+        tpeak = peak * 1.1 / 2.25
+        g.update({"tf32_products": products, "peak_tf32_tflops": round(tpeak, 1),
+                  "peak_note": "measured BF16 peak x nominal TF32/BF16 ratio (1.1 / 2.25)",
+                  "frac_of_tf32_peak": round(tensor / tpeak, 4), "precision": "split3_tf32"})
+    else:
+        g.update({"bf16_products": products, "peak_bf16_tflops": peak, "frac_of_bf16_peak": round(tensor / peak, 4),
+                  "precision": "split3_bf16" if prec == oo.OO_PREC_SPLIT3_BF16 else
+                  "fp64eq_ozaki_bf16_beta%d_L%d_kblock%d" % (beta, levels, kb)})
     if with_errors:
         import oracle
         Ch = C.cpu().numpy()
@@ -355,6 +362,7 @@ def bench_blocks(oo, ctx, torch, with_errors=True):
     C = torch.empty(n, n, dtype=torch.float64, device="cuda")
     out["gemm"] = gemm_component(oo, ctx, torch, oo.OO_PREC_SPLIT3_BF16, A_h, B_h, A, B, C, with_errors)
     out["gemm_fp64eq"] = gemm_component(oo, ctx, torch, oo.OO_PREC_FP64EQ, A_h, B_h, A, B, C, with_errors)
+    out["gemm_tf32"] = gemm_component(oo, ctx, torch, oo.OO_PREC_SPLIT3_TF32, A_h, B_h, A, B, C, with_errors)
     del A, B, C
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     logn = 22

@@ -401,9 +401,18 @@ oo_status oo_lookup_block(const char *callee, int lang, int *block_id);
  *                        magnitude (bound ~4 (L+2) 2^(-beta (L-1)) of
  *                        k max_l|a_il| max_l|b_lj| in general).  oo_gemm_plan
  *                        reports beta, L and the number of BF16 products.
- * (Value 1 is reserved for a TF32 split; it is not provided.)
+ *   OO_PREC_SPLIT3_TF32  the split-BF16 pattern with TF32 hi + lo operands
+ *                        (FP32 with 10 fraction bits, rounded to nearest,
+ *                        ties away; kind::tf32 tensor-core products, half the
+ *                        BF16 rate): ~22 significant bits of every entry;
+ *                        the error is about 1e-6 of sum_l |a_il b_lj| or
+ *                        less (measured 3.1e-7 at k = 256, four times below
+ *                        the BF16 pattern's; 8.6e-7 at k = 4096, where the
+ *                        tensor cores' FP32 accumulation dominates both
+ *                        split patterns).  Single calls only (batches and
+ *                        the serving loops take the other two patterns).
  * oo_gemm_f64: host buffers, synchronous.                                 */
-enum { OO_PREC_SPLIT3_BF16 = 0, OO_PREC_FP64EQ = 2 };
+enum { OO_PREC_SPLIT3_BF16 = 0, OO_PREC_SPLIT3_TF32 = 1, OO_PREC_FP64EQ = 2 };
 oo_status oo_gemm_f64(oo_ctx *ctx, int prec, int m, int n, int k, const double *A, int lda,
                       const double *B, int ldb, double *C, int ldc);
 /* Device buffers (caller-owned), asynchronous on the context's stream; the

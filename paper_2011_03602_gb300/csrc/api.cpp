@@ -447,13 +447,15 @@ oo_status oo_fft_c128(oo_ctx *ctx, int64_t n, int dir, const double *in, double 
 
 namespace {
 void gemm_checks(int prec, int m, int n, int k, int lda, int ldb, int ldc) {
-    OO_REQUIRE(prec == OO_PREC_SPLIT3_BF16 || prec == OO_PREC_FP64EQ, OO_EINVAL, "unsupported precision pattern");
+    OO_REQUIRE(prec == OO_PREC_SPLIT3_BF16 || prec == OO_PREC_SPLIT3_TF32 || prec == OO_PREC_FP64EQ, OO_EINVAL,
+               "unsupported precision pattern");
     OO_REQUIRE(m >= 1 && n >= 1 && k >= 1, OO_EINVAL, "m, n, k must be >= 1");
     OO_REQUIRE(m <= (1 << 20) && n <= (1 << 20) && k <= (1 << 21), OO_EINVAL, "matrix too large");
     OO_REQUIRE(lda >= k && ldb >= n && ldc >= n, OO_EINVAL, "leading dimension too small");
 }
 size_t gemm_scratch(int prec, int m, int n, int k) {
-    return prec == OO_PREC_FP64EQ ? gemm_fp64eq_scratch_bytes(m, n, k) : gemm_scratch_bytes(m, n, k);
+    if (prec == OO_PREC_FP64EQ) return gemm_fp64eq_scratch_bytes(m, n, k);
+    return prec == OO_PREC_SPLIT3_TF32 ? gemm_tf32_scratch_bytes(m, n, k) : gemm_scratch_bytes(m, n, k);
 }
 void gemm_launch(oo_ctx *ctx, int prec, int m, int n, int k, const double *dA, long long lda, const double *dB,
                  long long ldb, double *dC, long long ldc, cudaStream_t s) {
@@ -462,12 +464,22 @@ void gemm_launch(oo_ctx *ctx, int prec, int m, int n, int k, const double *dA, l
     if (prec == OO_PREC_FP64EQ)
         launch_gemm_fp64eq(m, n, k, dA, lda, dB, ldb, dC, ldc, scratch, s,
                            eq_tile_width(ctx->c.eq_widths.data(), n, k));
+    else if (prec == OO_PREC_SPLIT3_TF32)
+        launch_gemm_split3_tf32(m, n, k, dA, lda, dB, ldb, dC, ldc, scratch, s);
     else
         launch_gemm_split3(m, n, k, dA, lda, dB, ldb, dC, ldc, scratch, s);
 }
 unsigned gemm_error(oo_ctx *ctx, int m, int n, int k) {
     void *scratch = ctx->c.gemm_scratch.ptr;
     if (ctx->gemm_prec == OO_PREC_FP64EQ) return gemm_fp64eq_check_error(scratch, ctx->c.stream);
+    if (ctx->gemm_prec == OO_PREC_SPLIT3_TF32) {
+        unsigned *err = gemm_tf32_error_word(scratch, m, n, k);
+        unsigned e = 0;
+        OO_CUDA_TRY(cudaMemcpyAsync(&e, err, 4, cudaMemcpyDeviceToHost, ctx->c.stream));
+        OO_CUDA_TRY(cudaStreamSynchronize(ctx->c.stream));
+        if (e) OO_CUDA_TRY(cudaMemsetAsync(err, 0, 4, ctx->c.stream));
+        return e;
+    }
     return gemm_check_error(scratch, m, n, k, ctx->c.stream);
 }
 }  // namespace
@@ -536,7 +548,8 @@ oo_status oo_gemm_check(oo_ctx *ctx, int m, int n, int k) {
 
 oo_status oo_gemm_plan(int prec, int k, int *products, int *beta, int *levels, int *k_block) {
     return guarded(nullptr, [&] {
-        OO_REQUIRE(prec == OO_PREC_SPLIT3_BF16 || prec == OO_PREC_FP64EQ, OO_EINVAL, "unsupported precision pattern");
+        OO_REQUIRE(prec == OO_PREC_SPLIT3_BF16 || prec == OO_PREC_SPLIT3_TF32 || prec == OO_PREC_FP64EQ, OO_EINVAL,
+                   "unsupported precision pattern");
         OO_REQUIRE(k >= 1 && k <= (1 << 21), OO_EINVAL, "k out of range");
         int pr = 3, b = 0, l = 0, kb = 0;
         if (prec == OO_PREC_FP64EQ) {

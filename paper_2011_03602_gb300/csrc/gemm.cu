@@ -48,13 +48,16 @@ constexpr int kGroupM = 8;                   // tile raster: groups of 8 m-tiles
 
 using namespace tc;
 constexpr uint32_t kIdesc = idesc_bf16(kBM, kBN);
+constexpr uint32_t kIdescTF32 = idesc_tf32(kBM, kBN);
+constexpr int kBKTF32 = 32;  // TF32 values per 128-byte row: K per pipeline stage of the TF32 pattern
 
 struct GemmMaps {
     CUtensorMap a1, a2, b1, b2;
 };
 
 struct GemmArgs {
-    int m, n, k, kp;        // kp: padded K of the split operands (multiple of 64)
+    int m, n, k, kp;        // kp: padded K of the split operands (a multiple of kstage)
+    int kstage;             // K values per pipeline stage: 64 (BF16) or 32 (TF32)
     int m_tiles, n_tiles;
     double *C;
     long long ldc;
@@ -90,12 +93,12 @@ struct SingleSrc {
     const GemmMaps *maps;
     const GemmArgs *a;
     __device__ __forceinline__ int count() const { return a->m_tiles * a->n_tiles; }
-    __device__ __forceinline__ int ksteps(int) const { return a->kp / kBK; }
+    __device__ __forceinline__ int ksteps(int) const { return a->kp / a->kstage; }
     __device__ __forceinline__ TileJob job(int t) const {
         int m0, n0;
         tile_coords(*a, t, m0, n0);
         return TileJob{&maps->a1, &maps->a2, &maps->b1, &maps->b2, a->C, a->ldc, a->ea, a->eb,
-                       a->m, a->n, m0, n0, a->kp / kBK, 0, 0};
+                       a->m, a->n, m0, n0, a->kp / a->kstage, 0, 0};
     }
 };
 
@@ -128,7 +131,10 @@ struct GroupSrc {
     }
 };
 
-template <class Src>
+// TF32: the operands are TF32-rounded FP32 (kind::tf32 MMAs, 32 K values
+// per 128-byte row); the stage layout, accumulators and epilogue are the
+// BF16 pattern's byte for byte.
+template <class Src, bool TF32 = false>
 __device__ __forceinline__ void gemm_body(const Src &src, unsigned *err) {
     extern __shared__ __align__(1024) unsigned char gsm_raw[];
     unsigned char *gsm = reinterpret_cast<unsigned char *>(
@@ -189,7 +195,7 @@ __device__ __forceinline__ void gemm_body(const Src &src, unsigned *err) {
                 unsigned char *st = gsm + (size_t)s * kStageBytes;
                 const uint32_t fb = su32(&full[s]);
                 bar_expect_tx(fb, kStageBytes);
-                const int k0 = ks * kBK;
+                const int k0 = ks * (TF32 ? kBKTF32 : kBK);
                 tma_2d(su32(st), jb.a1, k0, jb.ra + jb.m0, fb);
                 tma_2d(su32(st + kTileA), jb.a2, k0, jb.ra + jb.m0, fb);
                 tma_2d(su32(st + 2 * kTileA), jb.b1, k0, jb.rb + jb.n0, fb);
@@ -222,11 +228,17 @@ __device__ __forceinline__ void gemm_body(const Src &src, unsigned *err) {
                 const uint32_t a1 = base, a2 = base + kTileA, b1 = base + 2 * kTileA, b2 = b1 + kTileB;
 #pragma unroll
                 for (int kk = 0; kk < kBK / 16; ++kk) {
-                    const uint32_t off = kk * 32;  // 16 BF16 along K inside the 128-byte row
+                    const uint32_t off = kk * 32;  // 16 BF16 (8 TF32) along K inside the 128-byte row
                     const uint32_t acc = (ks == 0 && kk == 0) ? 0u : 1u;
-                    mma_bf16<kIdesc>(d_hh, sdesc_sw128(a1 + off), sdesc_sw128(b1 + off), acc);
-                    mma_bf16<kIdesc>(d_x, sdesc_sw128(a1 + off), sdesc_sw128(b2 + off), acc);
-                    mma_bf16<kIdesc>(d_x, sdesc_sw128(a2 + off), sdesc_sw128(b1 + off), 1u);
+                    if constexpr (TF32) {
+                        mma_tf32<kIdescTF32>(d_hh, sdesc_sw128(a1 + off), sdesc_sw128(b1 + off), acc);
+                        mma_tf32<kIdescTF32>(d_x, sdesc_sw128(a1 + off), sdesc_sw128(b2 + off), acc);
+                        mma_tf32<kIdescTF32>(d_x, sdesc_sw128(a2 + off), sdesc_sw128(b1 + off), 1u);
+                    } else {
+                        mma_bf16<kIdesc>(d_hh, sdesc_sw128(a1 + off), sdesc_sw128(b1 + off), acc);
+                        mma_bf16<kIdesc>(d_x, sdesc_sw128(a1 + off), sdesc_sw128(b2 + off), acc);
+                        mma_bf16<kIdesc>(d_x, sdesc_sw128(a2 + off), sdesc_sw128(b1 + off), 1u);
+                    }
                 }
                 mma_commit(su32(&empty[s]));
             }
@@ -325,6 +337,12 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_split3_kernel(const __gr
                                                                      const __grid_constant__ GemmArgs a) {
     const SingleSrc src{&maps, &a};
     gemm_body(src, a.err);
+}
+
+__global__ void __launch_bounds__(kGemmThreads, 1) gemm_split3_tf32_kernel(const __grid_constant__ GemmMaps maps,
+                                                                          const __grid_constant__ GemmArgs a) {
+    const SingleSrc src{&maps, &a};
+    gemm_body<SingleSrc, true>(src, a.err);
 }
 
 __global__ void __launch_bounds__(kGemmThreads, 1) gemm_group_kernel(const __grid_constant__ GemmMaps maps,
@@ -653,6 +671,122 @@ __global__ void __launch_bounds__(kStripThreads) split_ab_kernel(const double *A
                    threadIdx.x & 255, 1 + half, red8[half]);
 }
 
+// ----------------------------------------------------- TF32 splitting
+// The TF32 pattern: A = 2^sA (A1 + A2 + dA), B likewise, A1, A2, B1, B2 TF32
+// (FP32 with 10 fraction bits, rounded to nearest, ties away), so the pair
+// keeps ~22 significant bits of every entry; the products and accumulators
+// are the BF16 pattern's (D_hh = A1 B1, D_x = A1 B2 + A2 B1).
+
+// effective biased exponent for the scales: subnormals count as 1, zero 0,
+// NaN and infinities as the non-finite flag
+__device__ __forceinline__ int eff_exp_or_flag(unsigned long long bits) {
+    const int e = (int)((bits >> 52) & 0x7ff);
+    if (e == 0x7ff) return kNonFiniteExp;
+    return e != 0 ? e : ((bits & 0x000fffffffffffffull) ? 1 : 0);
+}
+
+// round an FP32 value to TF32 (10 fraction bits), to nearest with ties away
+// from zero, by integer operations; zero and subnormals pass unchanged
+__device__ __forceinline__ float round_tf32(float v) {
+    const unsigned b = __float_as_uint(v);
+    if ((b & 0x7f800000u) == 0) return v;
+    return __uint_as_float((b + 0x1000u) & 0xffffe000u);
+}
+
+// x * 2^-S as a TF32 pair (hi + lo), integer operations and FP32 only: the
+// scaled value's top 24 significant bits h (truncated) and the rest l
+// (rounded to 24 bits), then hi = tf32(h), lo = tf32((h - hi) + l).
+// Values below the FP32 range after scaling, NaN and infinities give zeros
+// (the scale flags a non-finite row or column; the epilogue writes NaN).
+__device__ __forceinline__ void split_tf32(double x, int S, float &hi, float &lo) {
+    hi = lo = 0.0f;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int e = (int)((b >> 52) & 0x7ff);
+    unsigned long long M = b & 0x000fffffffffffffull;
+    if (e == 0x7ff || (e == 0 && M == 0)) return;
+    int E = e;
+    if (e != 0) {
+        M |= 1ull << 52;
+    } else {  // subnormal: normalise the significand
+        const int lz = __clzll((long long)M) - 11;
+        M <<= lz;
+        E = 1 - lz;
+    }
+    const int fe = E - 1023 - S + 127;  // biased FP32 exponent of x 2^-S
+    if (fe <= 0 || fe >= 255) return;
+    const unsigned sign = (unsigned)(b >> 63) << 31;
+    const float h = __uint_as_float(sign | ((unsigned)fe << 23) | (unsigned)((M >> 29) & 0x7fffffu));
+    const unsigned rest = (unsigned)(M & 0x1fffffffu);
+    float l = 0.0f;
+    if (rest != 0 && fe > 52) l = __fmul_rn(__uint2float_rn(rest), __uint_as_float((unsigned)(fe - 52) << 23));
+    if (sign) l = -l;
+    hi = round_tf32(h);
+    lo = round_tf32(__fadd_rn(__fsub_rn(h, hi), l));
+}
+
+// rows of A, one warp each: scale exponent, then the TF32 pair (zeros in
+// the padding [k, kp))
+__global__ void __launch_bounds__(256) split_rows_tf32_kernel(const double *A, long long lda, int m, int k, int kp,
+                                                             int *ea, float *A1, float *A2) {
+    const int lane = threadIdx.x & 31, row = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (row >= m) return;
+    const double *src = A + (long long)row * lda;
+    int mx = 0;
+    for (int l = lane; l < k; l += 32) mx = max(mx, eff_exp_or_flag((unsigned long long)__double_as_longlong(src[l])));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    const int S = mx == 0 ? 0 : mx - 1023 + 1;
+    if (lane == 0) ea[row] = S;
+    float *d1 = A1 + (long long)row * kp, *d2 = A2 + (long long)row * kp;
+    for (int l = lane; l < kp; l += 32) {
+        float h = 0.0f, lo = 0.0f;
+        if (l < k) split_tf32(src[l], S, h, lo);
+        d1[l] = h;
+        d2[l] = lo;
+    }
+}
+
+// column scale exponents of B (k x n): 32 columns x 8 row groups per block
+__global__ void col_scale_tf32_kernel(const double *B, long long ldb, int k, int n, int *eb) {
+    __shared__ int red[8][33];
+    const int col = blockIdx.x * 32 + threadIdx.x;
+    int mx = 0;
+    if (col < n)
+        for (int l = threadIdx.y; l < k; l += 8)
+            mx = max(mx, eff_exp_or_flag((unsigned long long)__double_as_longlong(B[(long long)l * ldb + col])));
+    red[threadIdx.y][threadIdx.x] = mx;
+    __syncthreads();
+    if (threadIdx.y == 0 && col < n) {
+        for (int y = 1; y < 8; ++y) mx = max(mx, red[y][threadIdx.x]);
+        eb[col] = mx == 0 ? 0 : mx - 1023 + 1;
+    }
+}
+
+// B transposed and split: 32 x 32 tiles through shared memory (reads along
+// n, writes along k), zeros in the padding [k, kp)
+__global__ void split_cols_tf32_kernel(const double *B, long long ldb, int k, int n, int kp, const int *eb,
+                                       float *B1, float *B2) {
+    __shared__ float th[32][33], tl[32][33];
+    const int c0 = blockIdx.x * 32, l0 = blockIdx.y * 32;
+    const int x = threadIdx.x, c = c0 + x;
+    const int S = c < n ? eb[c] : 0;
+    for (int y = threadIdx.y; y < 32; y += 8) {
+        const int l = l0 + y;
+        float h = 0.0f, lo = 0.0f;
+        if (c < n && l < k) split_tf32(B[(long long)l * ldb + c], S, h, lo);
+        th[y][x] = h;
+        tl[y][x] = lo;
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += 8) {
+        const int cc = c0 + y, l = l0 + x;
+        if (cc < n && l < kp) {
+            B1[(long long)cc * kp + l] = th[x][y];
+            B2[(long long)cc * kp + l] = tl[x][y];
+        }
+    }
+}
+
 // ------------------------------------------------------- grouped splitting
 struct GroupSplit {
     const double *A, *B;
@@ -771,6 +905,7 @@ void launch_gemm_split3(int m, int n, int k, const double *A, long long lda, con
     ga.n = n;
     ga.k = k;
     ga.kp = kp;
+    ga.kstage = kBK;
     ga.m_tiles = (m + kBM - 1) / kBM;
     ga.n_tiles = (n + kBN - 1) / kBN;
     ga.C = C;
@@ -787,6 +922,82 @@ void launch_gemm_split3(int m, int n, int k, const double *A, long long lda, con
     cudaDeviceGetAttribute(&sms2, cudaDevAttrMultiProcessorCount, dev2);
     const int grid = (int)std::min<long long>(tiles, sms2);
     gemm_split3_kernel<<<grid, kGemmThreads, smem_gemm(), s>>>(maps, ga);
+    OO_CUDA_TRY(cudaGetLastError());
+}
+
+// ------------------------------------------------------- TF32 pattern
+namespace {
+struct Tf32Layout {
+    int kp;
+    size_t a_bytes, b_bytes, total;
+};
+Tf32Layout tf32_layout(int m, int n, int k) {
+    Tf32Layout L{};
+    L.kp = (k + kBKTF32 - 1) / kBKTF32 * kBKTF32;
+    L.a_bytes = ((size_t)m * L.kp * 4 + 255) / 256 * 256;
+    L.b_bytes = ((size_t)n * L.kp * 4 + 255) / 256 * 256;
+    L.total = 2 * L.a_bytes + 2 * L.b_bytes + ((size_t)m + n) * 4 + 1024;
+    return L;
+}
+}  // namespace
+
+size_t gemm_tf32_scratch_bytes(int m, int n, int k) { return tf32_layout(m, n, k).total; }
+
+unsigned *gemm_tf32_error_word(void *scratch, int m, int n, int k) {
+    const Tf32Layout L = tf32_layout(m, n, k);
+    return reinterpret_cast<unsigned *>(static_cast<char *>(scratch) + 2 * L.a_bytes + 2 * L.b_bytes +
+                                        ((size_t)m + n) * 4);
+}
+
+void launch_gemm_split3_tf32(int m, int n, int k, const double *A, long long lda, const double *B, long long ldb,
+                             double *C, long long ldc, void *scratch, cudaStream_t s) {
+    OO_REQUIRE(m >= 1 && n >= 1 && k >= 1, OO_EINVAL, "m, n, k must be >= 1");
+    OO_REQUIRE(lda >= k && ldb >= n && ldc >= n, OO_EINVAL, "leading dimensions too small");
+    const Tf32Layout L = tf32_layout(m, n, k);
+    const int kp = L.kp;
+    char *p = static_cast<char *>(scratch);
+    auto *A1 = reinterpret_cast<float *>(p);
+    auto *A2 = reinterpret_cast<float *>(p + L.a_bytes);
+    auto *B1 = reinterpret_cast<float *>(p + 2 * L.a_bytes);
+    auto *B2 = reinterpret_cast<float *>(p + 2 * L.a_bytes + L.b_bytes);
+    int *ea = reinterpret_cast<int *>(p + 2 * L.a_bytes + 2 * L.b_bytes);
+    int *eb = ea + m;
+    unsigned *err = reinterpret_cast<unsigned *>(eb + n);
+    OO_CUDA_TRY(cudaMemsetAsync(err, 0, 4, s));
+    split_rows_tf32_kernel<<<(m + 7) / 8, 256, 0, s>>>(A, lda, m, k, kp, ea, A1, A2);
+    OO_CUDA_TRY(cudaGetLastError());
+    col_scale_tf32_kernel<<<(n + 31) / 32, dim3(32, 8), 0, s>>>(B, ldb, k, n, eb);
+    OO_CUDA_TRY(cudaGetLastError());
+    OO_REQUIRE(kp / 32 <= 65535, OO_EINVAL, "k too large");
+    split_cols_tf32_kernel<<<dim3((n + 31) / 32, kp / 32), dim3(32, 8), 0, s>>>(B, ldb, k, n, kp, eb, B1, B2);
+    OO_CUDA_TRY(cudaGetLastError());
+    GemmMaps maps;
+    map_f32(&maps.a1, A1, m, kp, kBM);
+    map_f32(&maps.a2, A2, m, kp, kBM);
+    map_f32(&maps.b1, B1, n, kp, kBN);
+    map_f32(&maps.b2, B2, n, kp, kBN);
+    GemmArgs ga{};
+    ga.m = m;
+    ga.n = n;
+    ga.k = k;
+    ga.kp = kp;
+    ga.kstage = kBKTF32;
+    ga.m_tiles = (m + kBM - 1) / kBM;
+    ga.n_tiles = (n + kBN - 1) / kBN;
+    ga.C = C;
+    ga.ldc = ldc;
+    ga.ea = ea;
+    ga.eb = eb;
+    ga.err = err;
+    static std::atomic<uint64_t> attr{0};
+    set_smem_limit_once((const void *)gemm_split3_tf32_kernel, smem_gemm(), attr);
+    const long long tiles = (long long)ga.m_tiles * ga.n_tiles;
+    OO_REQUIRE(tiles < (1ll << 31), OO_EINVAL, "too many tiles");
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = (int)std::min<long long>(tiles, sms);
+    gemm_split3_tf32_kernel<<<grid, kGemmThreads, smem_gemm(), s>>>(maps, ga);
     OO_CUDA_TRY(cudaGetLastError());
 }
 

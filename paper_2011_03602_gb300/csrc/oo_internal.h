@@ -110,6 +110,12 @@ void launch_gemm_split3(int m, int n, int k, const double *A, long long lda, con
 unsigned gemm_check_error(void *scratch, int m, int n, int k, cudaStream_t s);
 // the kernel's device error word inside its scratch (for asynchronous reads)
 unsigned *gemm_error_word(void *scratch, int m, int n, int k);
+// the same products with TF32 hi / lo operands (kind::tf32); scratch and
+// error word laid out by gemm_tf32_scratch_bytes / gemm_tf32_error_word
+size_t gemm_tf32_scratch_bytes(int m, int n, int k);
+void launch_gemm_split3_tf32(int m, int n, int k, const double *A, long long lda, const double *B, long long ldb,
+                             double *C, long long ldc, void *scratch, cudaStream_t s);
+unsigned *gemm_tf32_error_word(void *scratch, int m, int n, int k);
 // FP64-equivalent mode (gemm_fp64eq.cu): Ozaki-type BF16 digit slices
 size_t gemm_fp64eq_scratch_bytes(int m, int n, int k);
 int gemm_fp64eq_products(int k);

@@ -89,6 +89,21 @@ constexpr uint32_t idesc_bf16(int M, int N) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// Instruction descriptor, kind::tf32: D = F32, A = B = TF32 (format code 2),
+// both K-major; an MMA covers K = 8 TF32 values (32 bytes of each row, as
+// K = 16 BF16 values do)
+constexpr uint32_t idesc_tf32(int M, int N) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+template <uint32_t IDESC>
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(IDESC), "r"(acc)
+        : "memory");
+}
+
 template <uint32_t IDESC>
 __device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t acc) {
     asm volatile(
@@ -187,6 +202,21 @@ inline void map_bf16(CUtensorMap *m, const void *base, long long rows, int kp, i
                                       strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     OO_REQUIRE(r == CUDA_SUCCESS, OO_ECUDA, "cuTensorMapEncodeTiled (GEMM) failed: " + std::to_string((int)r));
+}
+
+// FP32 (TF32-rounded) split operand: rows x kp floats, K-major, 128-byte
+// swizzle, boxes of 32 floats (one 128-byte row) x box_rows
+inline void map_f32(CUtensorMap *m, const void *base, long long rows, int kp, int box_rows) {
+    OO_REQUIRE(((uintptr_t)base & 15u) == 0, OO_EINVAL, "split operand must be 16-byte aligned");
+    OO_REQUIRE(kp % 32 == 0 && rows >= 1 && rows < (1ll << 31), OO_EINVAL, "bad split-operand shape");
+    const cuuint64_t dims[2] = {(cuuint64_t)kp, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)kp * 4};
+    const cuuint32_t box[2] = {32u, (cuuint32_t)box_rows};
+    const cuuint32_t es[2] = {1, 1};
+    const CUresult r = encode_tiled()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void *>(base), dims,
+                                      strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    OO_REQUIRE(r == CUDA_SUCCESS, OO_ECUDA, "cuTensorMapEncodeTiled (GEMM, FP32) failed: " + std::to_string((int)r));
 }
 
 }  // namespace tc

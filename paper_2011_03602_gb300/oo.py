@@ -515,6 +515,7 @@ def oo_fft_c128(ctx, x, direction=-1, out=None):
 
 
 OO_PREC_SPLIT3_BF16 = 0
+OO_PREC_SPLIT3_TF32 = 1
 OO_PREC_FP64EQ = 2
 
 

@@ -125,8 +125,9 @@ def test_gemm_plan_follows_the_exactness_rule():
     assert oo.oo_gemm_plan(oo.OO_PREC_FP64EQ, 256) == (36, 6, 9, 256)
     assert oo.oo_gemm_scheme(513) == (oo.OO_EQ_PAIRS, 1)
     assert oo.oo_gemm_plan(oo.OO_PREC_FP64EQ, 4096) == (28, 7, 8, 1024)
+    assert oo.oo_gemm_plan(oo.OO_PREC_SPLIT3_TF32, 64) == (3, 0, 0, 0)
     with pytest.raises(oo.OOError):
-        oo.oo_gemm_plan(1, 64)
+        oo.oo_gemm_plan(3, 64)
 
 
 def test_gemm_tile_table_host_only():
