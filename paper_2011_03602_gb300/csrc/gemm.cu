@@ -724,21 +724,29 @@ __device__ __forceinline__ void split_tf32(double x, int S, float &hi, float &lo
     lo = round_tf32(__fadd_rn(__fsub_rn(h, hi), l));
 }
 
-// rows of A, one warp each: scale exponent, then the TF32 pair (zeros in
-// the padding [k, kp))
+// rows of A, one 256-thread block each: the row's scale exponent, then
+// the TF32 pair (zeros in the padding [k, kp)); the second pass reads the
+// row from L2
 __global__ void __launch_bounds__(256) split_rows_tf32_kernel(const double *A, long long lda, int m, int k, int kp,
                                                              int *ea, float *A1, float *A2) {
-    const int lane = threadIdx.x & 31, row = blockIdx.x * 8 + (threadIdx.x >> 5);
-    if (row >= m) return;
+    __shared__ int red[8];
+    const int row = blockIdx.x, tid = threadIdx.x;
     const double *src = A + (long long)row * lda;
     int mx = 0;
-    for (int l = lane; l < k; l += 32) mx = max(mx, eff_exp_or_flag((unsigned long long)__double_as_longlong(src[l])));
+#pragma unroll 4
+    for (int l = tid; l < k; l += 256) mx = max(mx, eff_exp_or_flag((unsigned long long)__double_as_longlong(src[l])));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((tid & 31) == 0) red[tid >> 5] = mx;
+    __syncthreads();
+    mx = red[0];
+#pragma unroll
+    for (int w = 1; w < 8; ++w) mx = max(mx, red[w]);
     const int S = mx == 0 ? 0 : mx - 1023 + 1;
-    if (lane == 0) ea[row] = S;
+    if (tid == 0) ea[row] = S;
     float *d1 = A1 + (long long)row * kp, *d2 = A2 + (long long)row * kp;
-    for (int l = lane; l < kp; l += 32) {
+#pragma unroll 4
+    for (int l = tid; l < kp; l += 256) {
         float h = 0.0f, lo = 0.0f;
         if (l < k) split_tf32(src[l], S, h, lo);
         d1[l] = h;
@@ -746,20 +754,18 @@ __global__ void __launch_bounds__(256) split_rows_tf32_kernel(const double *A, l
     }
 }
 
-// column scale exponents of B (k x n): 32 columns x 8 row groups per block
-__global__ void col_scale_tf32_kernel(const double *B, long long ldb, int k, int n, int *eb) {
-    __shared__ int red[8][33];
+// column maxima of B (k x n) over chunks of 256 rows: 32 columns x 8 row
+// groups per block, atomicMax into eb (zeroed first); exp_to_scale_kernel
+// then turns the maxima into scale exponents
+__global__ void col_max_tf32_kernel(const double *B, long long ldb, int k, int n, int *eb) {
     const int col = blockIdx.x * 32 + threadIdx.x;
+    const int l0 = blockIdx.y * 256, l1 = min(k, l0 + 256);
+    if (col >= n) return;
     int mx = 0;
-    if (col < n)
-        for (int l = threadIdx.y; l < k; l += 8)
-            mx = max(mx, eff_exp_or_flag((unsigned long long)__double_as_longlong(B[(long long)l * ldb + col])));
-    red[threadIdx.y][threadIdx.x] = mx;
-    __syncthreads();
-    if (threadIdx.y == 0 && col < n) {
-        for (int y = 1; y < 8; ++y) mx = max(mx, red[y][threadIdx.x]);
-        eb[col] = mx == 0 ? 0 : mx - 1023 + 1;
-    }
+#pragma unroll 8
+    for (int l = l0 + threadIdx.y; l < l1; l += 8)
+        mx = max(mx, eff_exp_or_flag((unsigned long long)__double_as_longlong(B[(long long)l * ldb + col])));
+    if (mx > 0) atomicMax(eb + col, mx);
 }
 
 // B transposed and split: 32 x 32 tiles through shared memory (reads along
@@ -964,9 +970,13 @@ void launch_gemm_split3_tf32(int m, int n, int k, const double *A, long long lda
     int *eb = ea + m;
     unsigned *err = reinterpret_cast<unsigned *>(eb + n);
     OO_CUDA_TRY(cudaMemsetAsync(err, 0, 4, s));
-    split_rows_tf32_kernel<<<(m + 7) / 8, 256, 0, s>>>(A, lda, m, k, kp, ea, A1, A2);
+    split_rows_tf32_kernel<<<m, 256, 0, s>>>(A, lda, m, k, kp, ea, A1, A2);
     OO_CUDA_TRY(cudaGetLastError());
-    col_scale_tf32_kernel<<<(n + 31) / 32, dim3(32, 8), 0, s>>>(B, ldb, k, n, eb);
+    OO_CUDA_TRY(cudaMemsetAsync(eb, 0, (size_t)n * 4, s));
+    OO_REQUIRE((k + 255) / 256 <= 65535, OO_EINVAL, "k too large");
+    col_max_tf32_kernel<<<dim3((n + 31) / 32, (k + 255) / 256), dim3(32, 8), 0, s>>>(B, ldb, k, n, eb);
+    OO_CUDA_TRY(cudaGetLastError());
+    exp_to_scale_kernel<<<(n + 255) / 256, 256, 0, s>>>(eb, n);
     OO_CUDA_TRY(cudaGetLastError());
     OO_REQUIRE(kp / 32 <= 65535, OO_EINVAL, "k too large");
     split_cols_tf32_kernel<<<dim3((n + 31) / 32, kp / 32), dim3(32, 8), 0, s>>>(B, ldb, k, n, kp, eb, B1, B2);
