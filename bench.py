@@ -666,7 +666,7 @@ def run_block(args):
         A = torch.from_numpy(synth.gemm_matrix(1, n, n)).cuda()
         B = torch.from_numpy(synth.gemm_matrix(2, n, n)).cuda()
         C = torch.empty(n, n, dtype=torch.float64, device="cuda")
-        prec = oo.OO_PREC_FP64EQ if args.prec == "fp64eq" else oo.OO_PREC_SPLIT3_BF16
+        prec = {"fp64eq": oo.OO_PREC_FP64EQ, "tf32": oo.OO_PREC_SPLIT3_TF32}.get(args.prec, oo.OO_PREC_SPLIT3_BF16)
         for _ in range(args.steps):
             oo.oo_gemm_f64_dev(ctx, n, n, n, A, n, B, n, C, n, prec=prec)
         oo.oo_gemm_check(ctx, n, n, n)
@@ -1212,7 +1212,7 @@ def main():
                     help="batched: 2 one call per request, 0 grouped kernels, 1 the grouped CUDA graph")
     ap.add_argument("--n", type=int, default=4096, help="profiling: GEMM size or FFT length")
     ap.add_argument("--batch", type=int, default=1, help="profiling: FFT batch")
-    ap.add_argument("--prec", choices=["split3", "fp64eq"], default="split3", help="profiling: GEMM pattern")
+    ap.add_argument("--prec", choices=["split3", "tf32", "fp64eq"], default="split3", help="profiling: GEMM pattern")
     ap.add_argument("--ga-seed", type=int, default=2011)
     ap.add_argument("--ga-timeout-ms", type=float, default=3000.0)
     ap.add_argument("--grid", type=int, nargs=3, default=None,
