@@ -208,3 +208,42 @@ def test_stalled_wait_fails_requests_and_context_recovers(oo_mod):
         assert np.array_equal(X, oo.oo_fft_c128(ctx, x, -1))
     finally:
         oo.oo_destroy(ctx)
+
+
+def test_largest_requests_same_bits_as_single_calls(oo_mod):
+    """The largest requests the loop takes: FFTs of 2^20 and 2^22 points (the
+    four-step passes as SIMT items), a GEMM at k = 2048 (the digit-slice
+    region's row pitch) with n = 2048, and a 129 x 129 x 257 Jacobi solve,
+    in flight together; each result is bit for bit the library's single
+    call (Jacobi: p bits, residuals to summation order)."""
+    oo = oo_mod
+    ctx = oo.oo_create(0)
+    try:
+        xs = {e: synth.complex_normal(70 + e, 1 << e) for e in (20, 22)}
+        A, B = synth.gemm_matrix(71, 2048, 2048), synth.gemm_matrix(72, 2048, 2048)
+        A2, B2 = synth.gemm_matrix(73, 300, 2048), synth.gemm_matrix(74, 2048, 200)
+        I, J, K, it = 129, 129, 257, 12
+        want_fft = {(e, d): oo.oo_fft_c128(ctx, xs[e], d) for e in xs for d in (-1, 1)}
+        want_gemm = oo.oo_gemm_f64(ctx, A, B, prec=oo.OO_PREC_FP64EQ)
+        want_gemm2 = oo.oo_gemm_f64(ctx, A2, B2, prec=oo.OO_PREC_FP64EQ)
+        oo.oo_set_option(ctx, oo.OO_OPT_JACOBI_FUSED, 0)
+        p_ref, r_ref = np.empty(I * J * K, np.float32), np.empty(it)
+        oo.oo_run_pattern(ctx, 63, 1, oo.jacobi(I, J, K, it), p_ref, r_ref)
+        oo.oo_serve_start_resident(ctx, 8 << 30, 64)
+        outs = {key: np.empty_like(xs[key[0]]) for key in want_fft}
+        C, C2 = np.empty((2048, 2048)), np.empty((300, 200))
+        p, r = np.empty(I * J * K, np.float32), np.empty(it)
+        tickets = [oo.oo_submit(ctx, oo.serve_request("fft", x=xs[e], X=outs[(e, d)], dir=d)) for e, d in want_fft]
+        tickets.append(oo.oo_submit(ctx, oo.serve_request("gemm", A=A, B=B, C=C)))
+        tickets.append(oo.oo_submit(ctx, oo.serve_request("gemm", A=A2, B=B2, C=C2)))
+        tickets.append(oo.oo_submit(ctx, oo.serve_request("jacobi", I=I, J=J, K=K, iters=it, p=p, res=r)))
+        for t in tickets:
+            oo.oo_wait(ctx, t, 120000)
+        oo.oo_serve_stop(ctx)
+        for key, want in want_fft.items():
+            assert np.array_equal(outs[key], want), key
+        assert np.array_equal(C, want_gemm) and np.array_equal(C2, want_gemm2)
+        assert np.array_equal(p, p_ref)
+        assert np.max(np.abs(r - r_ref) / r_ref) <= 1e-12
+    finally:
+        oo.oo_destroy(ctx)
