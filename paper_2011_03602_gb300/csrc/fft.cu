@@ -51,6 +51,30 @@ __device__ __forceinline__ int scale_of(const FftArgs &a, int b) {
     return e == 0 ? 0 : e - 1023 + 1;
 }
 
+// The first stage (radix R, no twiddles) on the 8 values a thread has
+// loaded (v[r] at shared-memory position dst[r] = column << log2L | t),
+// stored in Stockham order: butterfly j's output p at column position
+// j R + p.  COLFAST: value r of the thread is t0 + r L/8 of one column, so
+// butterfly g takes r = g + m 8/R; otherwise value r = g R + m is
+// tid + m 512 of column g (L = 512 R).
+template <int R, bool COLFAST>
+__device__ __forceinline__ void first_stage_regs(float4 *sd, const float4 *v, const int *dst, int log2L, bool inv) {
+    static_assert(kFftElems / kFftThreads == 8, "eight values per thread");
+    constexpr int G = 8 / R;
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        cplx x[R];
+#pragma unroll
+        for (int m = 0; m < R; ++m) x[m] = ld_cplx(&v[COLFAST ? g + m * G : g * R + m]);
+        const int r0 = COLFAST ? g : g * R;
+        const int col = dst[r0] >> log2L, j = dst[r0] & ((1 << log2L) - 1);
+        dft_small<R>(x, inv);
+        float4 *o = sd + (col << log2L) + j * R;
+#pragma unroll
+        for (int p = 0; p < R; ++p) st_cplx(o + p, x[p]);
+    }
+}
+
 // MODE 0: whole transforms of length L = n, several per CTA (double in/out)
 // MODE 1: four-step pass 1: columns of length N1 (double in, ff out x twiddle)
 // MODE 2: four-step pass 2: rows of length N2 (ff in, double out at k1 + N1 k2)
@@ -80,8 +104,15 @@ __global__ void __launch_bounds__(kFftThreads, 2) fft_pass_kernel(FftArgs a) {
     }
 
     // ---- load: all of this thread's 16-byte loads are issued before any is
-    // used (eight in flight), then split and stored to shared memory
+    // used (eight in flight), then split and stored to shared memory -- after
+    // the first stage, done in registers where this thread holds whole
+    // butterflies of it: column-fastest loads (MODE 1) give it x[t0 + r L/8],
+    // r < 8, of one column; row-fastest loads (MODE 0 / 2) give it, for
+    // L = 1024, 2048, 4096, x[tid + m 512], m < L / 512 = the first radix, of
+    // each of its columns
     constexpr int kPer = kFftElems / kFftThreads;
+    const int b0 = first_radix_log2(log2L);
+    const bool first_here = MODE == 1 ? log2L >= 3 : (log2L >= 10 && log2L <= 12);
     {
         double2 raw[kPer];
         int dst[kPer];
@@ -121,22 +152,13 @@ __global__ void __launch_bounds__(kFftThreads, 2) fft_pass_kernel(FftArgs a) {
                 split_scaled(raw[r].y, S, v[r].z, v[r].w);
             }
         }
-        if (log2L == 11) {
-            // L = 2048: the first (radix-2, twiddle-free) stage pairs t with
-            // t + 1024 of the same column, and both are in this thread's
-            // registers (loads r and r + 4 column-fastest, r and r + 2
-            // row-fastest); do it here and store in Stockham order (y0 at
-            // 2t, y1 at 2t + 1 of the column).
-            static_assert(kPer == 8 && kFftThreads == 512, "pairing below assumes 8 loads of 512 threads");
-#pragma unroll
-            for (int pr = 0; pr < 4; ++pr) {
-                const int r0 = MODE == 1 ? pr : (pr & 1) + 4 * (pr >> 1), r1 = r0 + (MODE == 1 ? 4 : 2);
-                const cplx x0 = ld_cplx(&v[r0]), x1 = ld_cplx(&v[r1]);
-                const int col = dst[r0] >> 11, t = dst[r0] & 2047;  // t < 1024
-                float4 *o = sd + (col << 11) + 2 * t;
-                st_cplx(o, ff::cadd(x0, x1));
-                st_cplx(o + 1, ff::csub(x0, x1));
-            }
+        if (first_here) {
+            if (b0 == 1)
+                first_stage_regs<2, MODE == 1>(sd, v, dst, log2L, inv);
+            else if (b0 == 2)
+                first_stage_regs<4, MODE == 1>(sd, v, dst, log2L, inv);
+            else
+                first_stage_regs<8, MODE == 1>(sd, v, dst, log2L, inv);
         } else {
 #pragma unroll
             for (int r = 0; r < kPer; ++r) sd[dst[r]] = v[r];
@@ -144,8 +166,8 @@ __global__ void __launch_bounds__(kFftThreads, 2) fft_pass_kernel(FftArgs a) {
     }
     __syncthreads();
 
-    if (log2L == 11)
-        fft_in_smem_after_r2(sd, stw, log2L, inv);
+    if (first_here)
+        fft_in_smem_after_first(sd, stw, log2L, inv);
     else
         fft_in_smem(sd, stw, log2L, inv);
 
@@ -206,22 +228,22 @@ __global__ void fft_twiddle_kernel(float4 *table, int count, long long stride, i
     }
 }
 
-// per-stage twiddle table of a length-2^log2L transform: for each radix-4
-// stage with sub-length Ls > 1 (in execution order), 3 Ls entries
-// W_{4Ls}^{k q}, q = 1..3, k < Ls, computed in FP64 and split to float pairs
+// per-stage twiddle table of a length-2^log2L transform: for each radix-8
+// stage after the first (in execution order), 7 Ls entries W_{8Ls}^{k q},
+// q = 1..7, k < Ls, computed in FP64 and split to float pairs
 __global__ void fft_stage_twiddle_kernel(float4 *table, int log2L) {
     const int count = stage_table_count(log2L);
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < count; t += gridDim.x * blockDim.x) {
-        int Ls = (log2L & 1) ? 2 : 4, off = 0, lg = (log2L & 1) ? 1 : 2;  // lg = log2 Ls
-        while (t >= off + 3 * Ls) {
-            off += 3 * Ls;
-            Ls *= 4;
-            lg += 2;
+        int lg = first_radix_log2(log2L), Ls = 1 << lg, off = 0;  // lg = log2 Ls
+        while (t >= off + 7 * Ls) {
+            off += 7 * Ls;
+            Ls *= 8;
+            lg += 3;
         }
         const int r = t - off, q = r / Ls + 1, k = r % Ls;
-        const long long m = ((long long)k * q) & ((4ll << lg) - 1);  // W_{4Ls}^m, 4Ls = 2^(lg + 2)
+        const long long m = ((long long)k * q) & ((8ll << lg) - 1);  // W_{8Ls}^m, 8Ls = 2^(lg + 3)
         double sn, cs;
-        sincospi(ldexp((double)(2 * m), -(lg + 2)), &sn, &cs);    // angle 2 pi m / (4 Ls)
+        sincospi(ldexp((double)(2 * m), -(lg + 3)), &sn, &cs);    // angle 2 pi m / (8 Ls)
         const double re = cs, im = -sn;
         const float rh = (float)re, ih = (float)im;
         table[t] = make_float4(rh, (float)(re - (double)rh), ih, (float)(im - (double)ih));

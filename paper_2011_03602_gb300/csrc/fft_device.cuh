@@ -77,7 +77,7 @@ __device__ __forceinline__ cplx norm(const cplx &a) {
 namespace {
 
 constexpr int kFftThreads = 512;
-constexpr int kFftBpt = 2;                               // radix-4 butterflies per thread
+constexpr int kFftBpt = 2;                               // (8 values per thread: 8 / R radix-R butterflies)
 constexpr int kFftElems = 4 * kFftThreads * kFftBpt;     // 4096 values per CTA
 constexpr int kTwSplit = 11;                             // four-step twiddle split: 2^11
 
@@ -131,101 +131,160 @@ __device__ __forceinline__ cplx twiddle(const float4 *stw, int idx, bool inv) {
     return inv ? ff::conj(w) : w;
 }
 
-// Stockham radix-2 stage with sub-length Ls on C columns of length L; used
-// only as the first stage (Ls = 1), which needs no twiddles.
-__device__ __forceinline__ void stage_r2(float4 *sd, const float4 *, int log2L, int Ls, bool) {
-    const int L = 1 << log2L, half = L >> 1;
-    cplx y0[2 * kFftBpt], y1[2 * kFftBpt];
-    int base_c[2 * kFftBpt], jj[2 * kFftBpt];
-#pragma unroll
-    for (int r = 0; r < 2 * kFftBpt; ++r) {
-        const int bidx = threadIdx.x + r * kFftThreads;
-        const int c = bidx >> (log2L - 1), j = bidx & (half - 1);
-        base_c[r] = c << log2L;
-        jj[r] = j;
-        y0[r] = ld_cplx(sd + base_c[r] + j);
-        cplx x1 = ld_cplx(sd + base_c[r] + j + half);
-        y1[r] = x1;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < 2 * kFftBpt; ++r) {
-        const int j = jj[r], k = j & (Ls - 1);
-        const int o = base_c[r] + (j - k) * 2 + k;
-        st_cplx(sd + o, ff::cadd(y0[r], y1[r]));
-        st_cplx(sd + o + Ls, ff::csub(y0[r], y1[r]));
-    }
-    __syncthreads();
+// ---- stages.  A length-L transform runs a first stage of radix 2^b0,
+// b0 = ((log2 L - 1) mod 3) + 1 (the whole transform when L <= 8), then
+// radix-8 stages with sub-lengths Ls = 2^b0, 8 * 2^b0, ...  A Stockham stage
+// of radix R and sub-length Ls takes inputs j + q L/R (q < R) of butterfly
+// j, multiplies input q by W_{R Ls}^{k q} (k = j mod Ls; none in the first
+// stage, Ls = 1) from its slice of the per-stage table, stw[(q - 1) Ls + k]
+// (lanes with consecutive k read consecutive entries), and writes output p
+// to (j - k) R + k + p Ls.  Fewer, wider stages than radix 4 mean fewer
+// shared-memory round trips and barriers per point.
+
+__host__ __device__ __forceinline__ int first_radix_log2(int log2L) {
+    return log2L <= 3 ? log2L : ((log2L - 1) % 3) + 1;
+}
+// entries of the per-stage twiddle table of a length-2^log2L transform: 7 Ls
+// per radix-8 stage after the first
+__host__ __device__ __forceinline__ int stage_table_count(int log2L) {
+    return log2L <= 3 ? 0 : (1 << log2L) - (1 << first_radix_log2(log2L));
 }
 
-// Stockham radix-4 stage with sub-length Ls.  Twiddles come from this
-// stage's slice of the per-stage table: stw[(q - 1) Ls + k] = W_{4Ls}^{k q}
-// (= W_L^{k q L / (4 Ls)}), so lanes with consecutive k read consecutive
-// entries (no shared-memory bank conflicts, unlike strided reads of one
-// W_L table).
-__device__ __forceinline__ void stage_r4(float4 *sd, const float4 *stw, int log2L, int Ls, bool inv) {
-    const int L = 1 << log2L, q4 = L >> 2;
-    cplx Y[kFftBpt][4];
-    int base_c[kFftBpt], jj[kFftBpt];
+// 1 / sqrt(2) as a float pair (hi, lo)
+constexpr double kInvSqrt2 = 0.70710678118654752440084436210485;
+constexpr float kS2h = (float)kInvSqrt2;
+constexpr float kS2l = (float)(kInvSqrt2 - (double)kS2h);
+
+// (h + l) / sqrt(2), lazy
+__device__ __forceinline__ void mul_inv_sqrt2(float h, float l, float &rh, float &rl) {
+    float e;
+    ff::two_prod(h, kS2h, rh, e);
+    e = __fmaf_rn(h, kS2l, e);
+    rl = __fmaf_rn(l, kS2h, e);
+}
+
+// 4-point DFT of lazy inputs, lazy outputs (no renormalisation)
+__device__ __forceinline__ void dft4_lazy(const cplx &x0, const cplx &x1, const cplx &x2, const cplx &x3, cplx *y,
+                                          bool inv) {
+    const cplx a0 = ff::cadd_lazy(x0, x2), a1 = ff::csub_lazy(x0, x2);
+    const cplx b0 = ff::cadd_lazy(x1, x3), b1 = ff::csub_lazy(x1, x3);
+    const cplx rb1 = inv ? ff::mul_pos_i(b1) : ff::mul_neg_i(b1);
+    y[0] = ff::cadd_lazy(a0, b0);
+    y[2] = ff::csub_lazy(a0, b0);
+    y[1] = ff::cadd_lazy(a1, rb1);
+    y[3] = ff::csub_lazy(a1, rb1);
+}
+
+// R-point DFT (R = 2, 4, 8) of lazy inputs in place, x[p] <- Y_p = sum_q
+// x_q W_R^{+-p q}, each output renormalised once.  R = 8: two 4-point DFTs
+// (even and odd inputs) and Y_p = E_p + W_8^p O_p, Y_{p+4} = E_p - W_8^p O_p,
+// where W_8^{+-1}, W_8^{+-3} are a sum and a difference of O's parts times
+// 1 / sqrt(2) and W_8^{+-2} = -+i is exact.
+template <int R>
+__device__ __forceinline__ void dft_small(cplx *x, bool inv) {
+    if constexpr (R == 2) {
+        const cplx y0 = ff::cadd_lazy(x[0], x[1]), y1 = ff::csub_lazy(x[0], x[1]);
+        x[0] = ff::norm(y0);
+        x[1] = ff::norm(y1);
+    } else if constexpr (R == 4) {
+        cplx y[4];
+        dft4_lazy(x[0], x[1], x[2], x[3], y, inv);
 #pragma unroll
-    for (int r = 0; r < kFftBpt; ++r) {
-        const int bidx = threadIdx.x + r * kFftThreads;
-        const int c = bidx >> (log2L - 2), j = bidx & (q4 - 1);
-        base_c[r] = c << log2L;
-        jj[r] = j;
-        cplx x[4];
+        for (int p = 0; p < 4; ++p) x[p] = ff::norm(y[p]);
+    } else {
+        cplx E[4], O[4];
+        dft4_lazy(x[0], x[2], x[4], x[6], E, inv);
+        dft4_lazy(x[1], x[3], x[5], x[7], O, inv);
+        cplx t[4];
+        t[0] = O[0];
+        t[2] = inv ? ff::mul_pos_i(O[2]) : ff::mul_neg_i(O[2]);
+        {
+            float sh, sl, dh, dl;  // s = re + im, d = im - re
+            ff::add_lazy(O[1].rh, O[1].rl, O[1].ih, O[1].il, sh, sl);
+            ff::add_lazy(O[1].ih, O[1].il, -O[1].rh, -O[1].rl, dh, dl);
+            if (inv) {  // (1 + i) / sqrt 2: (-d + i s) / sqrt 2
+                mul_inv_sqrt2(-dh, -dl, t[1].rh, t[1].rl);
+                mul_inv_sqrt2(sh, sl, t[1].ih, t[1].il);
+            } else {    // (1 - i) / sqrt 2: (s + i d) / sqrt 2
+                mul_inv_sqrt2(sh, sl, t[1].rh, t[1].rl);
+                mul_inv_sqrt2(dh, dl, t[1].ih, t[1].il);
+            }
+        }
+        {
+            float sh, sl, dh, dl;
+            ff::add_lazy(O[3].rh, O[3].rl, O[3].ih, O[3].il, sh, sl);
+            ff::add_lazy(O[3].ih, O[3].il, -O[3].rh, -O[3].rl, dh, dl);
+            if (inv) {  // (-1 + i) / sqrt 2: (-s - i d) / sqrt 2
+                mul_inv_sqrt2(-sh, -sl, t[3].rh, t[3].rl);
+                mul_inv_sqrt2(-dh, -dl, t[3].ih, t[3].il);
+            } else {    // (-1 - i) / sqrt 2: (d - i s) / sqrt 2
+                mul_inv_sqrt2(dh, dl, t[3].rh, t[3].rl);
+                mul_inv_sqrt2(-sh, -sl, t[3].ih, t[3].il);
+            }
+        }
 #pragma unroll
-        for (int q = 0; q < 4; ++q) x[q] = ld_cplx(sd + base_c[r] + j + q * q4);
+        for (int p = 0; p < 4; ++p) {
+            x[p] = ff::norm(ff::cadd_lazy(E[p], t[p]));
+            x[p + 4] = ff::norm(ff::csub_lazy(E[p], t[p]));
+        }
+    }
+}
+
+__host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v >> 1); }
+
+// One Stockham stage of radix R over the CTA's kFftElems values (C columns of
+// length L): 8 / R butterflies per thread.
+template <int R>
+__device__ __forceinline__ void stage_radix(float4 *sd, const float4 *stw, int log2L, int Ls, bool inv) {
+    constexpr int B = kFftElems / (R * kFftThreads);
+    const int log2lr = log2L - ilog2c(R), lr = 1 << log2lr;
+    cplx Y[B][R];
+    int base_c[B], jj[B];
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+        const int bidx = threadIdx.x + b * kFftThreads;
+        const int c = bidx >> log2lr, j = bidx & (lr - 1);
+        base_c[b] = c << log2L;
+        jj[b] = j;
+#pragma unroll
+        for (int q = 0; q < R; ++q) Y[b][q] = ld_cplx(sd + base_c[b] + j + q * lr);
         if (Ls > 1) {
             const int k = j & (Ls - 1);
 #pragma unroll
-            for (int q = 1; q < 4; ++q) x[q] = ff::cmul_lazy(x[q], twiddle(stw, (q - 1) * Ls + k, inv));
+            for (int q = 1; q < R; ++q) Y[b][q] = ff::cmul_lazy(Y[b][q], twiddle(stw, (q - 1) * Ls + k, inv));
         }
-        // lazy float-float through the butterfly, one renormalisation per output
-        const cplx a0 = ff::cadd_lazy(x[0], x[2]), a1 = ff::csub_lazy(x[0], x[2]);
-        const cplx b0 = ff::cadd_lazy(x[1], x[3]), b1 = ff::csub_lazy(x[1], x[3]);
-        const cplx rb1 = inv ? ff::mul_pos_i(b1) : ff::mul_neg_i(b1);
-        Y[r][0] = ff::norm(ff::cadd_lazy(a0, b0));
-        Y[r][2] = ff::norm(ff::csub_lazy(a0, b0));
-        Y[r][1] = ff::norm(ff::cadd_lazy(a1, rb1));
-        Y[r][3] = ff::norm(ff::csub_lazy(a1, rb1));
+        dft_small<R>(Y[b], inv);
     }
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < kFftBpt; ++r) {
-        const int j = jj[r], k = j & (Ls - 1);
-        const int o = base_c[r] + (j - k) * 4 + k;
+    for (int b = 0; b < B; ++b) {
+        const int j = jj[b], k = j & (Ls - 1);
+        const int o = base_c[b] + (j - k) * R + k;
 #pragma unroll
-        for (int p = 0; p < 4; ++p) st_cplx(sd + o + p * Ls, Y[r][p]);
+        for (int p = 0; p < R; ++p) st_cplx(sd + o + p * Ls, Y[b][p]);
     }
     __syncthreads();
 }
 
-// A radix-2 stage (Ls = 1, no twiddles) first when log2 L is odd, then
-// radix-4 stages; stw holds the radix-4 stages' twiddle slices in order.
+// the radix-8 stages after the first stage (which the caller has done)
+__device__ void fft_in_smem_after_first(float4 *sd, const float4 *stw, int log2L, bool inv) {
+    for (int Ls = 1 << first_radix_log2(log2L); Ls < (1 << log2L); Ls *= 8) {
+        stage_radix<8>(sd, stw, log2L, Ls, inv);
+        stw += 7 * Ls;
+    }
+}
+
+// the whole transform of every column in shared memory
 __device__ void fft_in_smem(float4 *sd, const float4 *stw, int log2L, bool inv) {
-    int Ls = 1;
-    if (log2L & 1) {
-        stage_r2(sd, stw, log2L, 1, inv);
-        Ls = 2;
-    }
-    for (; Ls < (1 << log2L); Ls *= 4) {
-        stage_r4(sd, stw, log2L, Ls, inv);
-        if (Ls > 1) stw += 3 * Ls;
-    }
-}
-
-// the same, for odd log2 L, when the radix-2 stage has already been done
-__device__ void fft_in_smem_after_r2(float4 *sd, const float4 *stw, int log2L, bool inv) {
-    for (int Ls = 2; Ls < (1 << log2L); Ls *= 4) {
-        stage_r4(sd, stw, log2L, Ls, inv);
-        stw += 3 * Ls;
-    }
-}
-
-// entries of the per-stage twiddle table of a length-2^log2L transform
-__host__ __device__ __forceinline__ int stage_table_count(int log2L) {
-    return log2L < 3 ? 0 : (1 << log2L) - ((log2L & 1) ? 2 : 4);
+    if (log2L == 0) return;
+    const int b0 = first_radix_log2(log2L);
+    if (b0 == 1)
+        stage_radix<2>(sd, stw, log2L, 1, inv);
+    else if (b0 == 2)
+        stage_radix<4>(sd, stw, log2L, 1, inv);
+    else
+        stage_radix<8>(sd, stw, log2L, 1, inv);
+    fft_in_smem_after_first(sd, stw, log2L, inv);
 }
 
 // largest biased exponent among the 64-bit words [x0, x1) of p (stride
