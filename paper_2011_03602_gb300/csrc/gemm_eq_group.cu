@@ -666,19 +666,6 @@ int table_of(int scheme, int k) {
 }
 int scheme_of_table(int t) { return t <= 1 ? eq::kSchemePairs : (t == 2 ? eq::kSchemeLevel7 : eq::kSchemeLevel6); }
 
-// ----------------------------------------------------------- the split
-// job (0, problem, first row): eight rows of A; job (1, problem, first
-// column): 64 columns of B (eq_digits.cuh)
-__global__ void __launch_bounds__(256) eq_group_split_kernel(const eq::GSplit *gs, const int4 *jobs) {
-    __shared__ double t[64][65];
-    __shared__ int red[4][64];
-    const int4 jb = jobs[blockIdx.x];
-    if (jb.x == 0)
-        eq::split_rows_job(gs[jb.y], jb.z);
-    else
-        eq::split_cols_job(gs[jb.y], jb.z, t, red);
-}
-
 // 2D BF16 tensor map over rows x pitch (row-major, pitch a multiple of 64),
 // box 64 K-elements x box_rows rows, 128-byte swizzle
 void map_slices(CUtensorMap *m, const void *base, long long rows, long long pitch, int box_rows) {
@@ -904,8 +891,7 @@ EqGroup *eq_group_create(const std::vector<GemmDesc> &v, int num_sms, const int 
 }
 
 void eq_group_launch(EqGroup *g, cudaStream_t s) {
-    eq_group_split_kernel<<<g->njobs, 256, 0, s>>>(g->d_split, g->d_jobs);
-    OO_CUDA_TRY(cudaGetLastError());
+    launch_eq_group_split(g->d_split, g->d_jobs, g->njobs, s);
     static std::atomic<uint64_t> attr{0};
     set_smem_limit_once((const void *)gemm_eq_group_kernel, smem_bytes(), attr);
     gemm_eq_group_kernel<<<g->grid, kThreads, smem_bytes(), s>>>(g->maps, g->args, g->d_probs, g->d_tiles,

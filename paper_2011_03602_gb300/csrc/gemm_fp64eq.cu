@@ -455,6 +455,29 @@ EqLayout eq_layout(int m, int n, int k) {
 
 }  // namespace
 
+// The grouped products' digit split (their tensor-core kernel is in
+// gemm_eq_group.cu, which reads only through L2 for the device-resident
+// loop's sake; the split's second pass over a row wants L1): job (0,
+// problem, first row), eight rows of A; job (1, problem, first column), 64
+// columns of B (eq_digits.cuh).
+namespace {
+__global__ void __launch_bounds__(256) eq_group_split_kernel(const eq::GSplit *gs, const int4 *jobs) {
+    __shared__ double t[64][65];
+    __shared__ int red[4][64];
+    const int4 jb = jobs[blockIdx.x];
+    if (jb.x == 0)
+        eq::split_rows_job(gs[jb.y], jb.z);
+    else
+        eq::split_cols_job(gs[jb.y], jb.z, t, red);
+}
+}  // namespace
+
+void launch_eq_group_split(const eq::GSplit *gs, const int4 *jobs, int njobs, cudaStream_t s) {
+    if (njobs <= 0) return;
+    eq_group_split_kernel<<<njobs, 256, 0, s>>>(gs, jobs);
+    OO_CUDA_TRY(cudaGetLastError());
+}
+
 size_t gemm_fp64eq_scratch_bytes(int m, int n, int k) { return eq_layout(m, n, k).total; }
 
 int gemm_fp64eq_products(int k) { return eq_used_shape(k).nprod; }

@@ -174,6 +174,12 @@ void launch_gemm_eq_tiles(int m, int n, int k, const void *As, const void *Bs, c
 struct EqGroup;
 EqGroup *eq_group_create(const std::vector<GemmDesc> &v, int num_sms, const int *widths);
 void eq_group_launch(EqGroup *g, cudaStream_t s);
+namespace eq {
+struct GSplit;
+}
+// the grouped products' digit split (gemm_fp64eq.cu): njobs jobs of eight A
+// rows or 64 B columns
+void launch_eq_group_split(const eq::GSplit *gs, const int4 *jobs, int njobs, cudaStream_t s);
 unsigned eq_group_check(EqGroup *g, cudaStream_t s);
 double eq_group_flops(const EqGroup *g);
 int eq_group_tiles(const EqGroup *g);
