@@ -10,10 +10,12 @@
 // out of the way for any finite double input.
 //
 // Structure: a CTA holds 4096 complex float-float values (64 KB) in shared
-// memory and runs Stockham auto-sort radix-4 stages (one radix-2 stage first
-// for odd log2 L), 512 threads x 2 butterflies per stage, twiddles from a
-// per-stage table (W_{4Ls}^{kq} for stage sub-length Ls) staged into shared
-// memory; two CTAs per SM where the shared memory allows.  N <= 4096 runs in one pass
+// memory and runs Stockham auto-sort stages -- a first stage of radix 2, 4
+// or 8 (done in registers at load time where a thread holds whole
+// butterflies of it), then radix-8 stages -- 512 threads x 8 values per
+// stage, twiddles from a per-stage table (W_{8Ls}^{kq} for stage sub-length
+// Ls) staged into shared memory; two CTAs per SM where the shared memory
+// allows.  N <= 4096 runs in one pass
 // (several transforms per CTA when N is small).  Larger N uses the four-step
 // split N = N1 x N2: pass 1 does N2 column FFTs of length N1 and multiplies
 // by W_N^{k1 n2} (two-level twiddle table), writing float-float

@@ -1,7 +1,7 @@
 // Device code of the Fourier-transform block shared by its kernels
 // (fft.cu) and the device-resident serving loop (serve_resident.cu):
-// float-float complex values in shared memory, Stockham radix-4 stages
-// (a radix-2 stage first for odd log2 L) with per-stage twiddle tables, the
+// float-float complex values in shared memory, Stockham stages (a first
+// stage of radix 2, 4 or 8, then radix 8) with per-stage twiddle tables, the
 // exact power-of-two input scaling, and one work item of a group of
 // transforms.  The design is described in fft.cu.
 #pragma once
