@@ -598,7 +598,10 @@ oo_status oo_serve_stop(oo_ctx *ctx);
  * memory.  Inputs are copied from the caller's buffers to the device when a
  * request is admitted and outputs into them as soon as it completes, by the
  * library's I/O threads (no staging copy on the host), so the buffers must
- * stay valid until oo_wait returns.  Served here: GEMMs in
+ * stay valid until oo_wait returns.  Host threads: one scheduler, which
+ * polls without sleeping while requests are in flight (it holds a host core
+ * then; idle, it sleeps and wakes at least every millisecond), and four I/O
+ * threads.  Served here: GEMMs in
  * OO_PREC_FP64EQ with k <= 2048 (the same bits as oo_gemm_f64), FFTs up to
  * 2^22 points (the same bits as oo_fft_c128), Jacobi programs (the tiled
  * kernels' p bits; residuals summed in chunk order, within ~1e-12 relative of
