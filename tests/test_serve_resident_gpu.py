@@ -247,3 +247,30 @@ def test_largest_requests_same_bits_as_single_calls(oo_mod):
         assert np.max(np.abs(r - r_ref) / r_ref) <= 1e-12
     finally:
         oo.oo_destroy(ctx)
+
+
+def test_idle_loop_stays_alive_past_the_wait_bound(oo_mod):
+    """Workers wait (bounded, about a second) for published entries; an idle
+    loop publishes keep-alive entries, so after three idle seconds requests
+    are still served and nothing has failed."""
+    import time
+    oo = oo_mod
+    ctx = oo.oo_create(0)
+    try:
+        oo.oo_serve_start_resident(ctx, 512 << 20, 16)
+        time.sleep(3.0)
+        x = synth.complex_normal(9, 4096)
+        X = np.empty_like(x)
+        A, B, C = synth.gemm_matrix(10, 64, 96), synth.gemm_matrix(11, 96, 80), np.empty((64, 80))
+        t1 = oo.oo_submit(ctx, oo.serve_request("fft", x=x, X=X, dir=1))
+        t2 = oo.oo_submit(ctx, oo.serve_request("gemm", A=A, B=B, C=C))
+        oo.oo_wait(ctx, t1, 30000)
+        oo.oo_wait(ctx, t2, 30000)
+        time.sleep(1.5)
+        st = oo.oo_serve_stats(ctx)
+        assert st["failed"] == 0 and st["completed"] == 2
+        oo.oo_serve_stop(ctx)
+        assert np.array_equal(X, oo.oo_fft_c128(ctx, x, 1))
+        assert np.array_equal(C, oo.oo_gemm_f64(ctx, A, B, prec=oo.OO_PREC_FP64EQ))
+    finally:
+        oo.oo_destroy(ctx)
