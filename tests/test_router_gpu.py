@@ -62,3 +62,44 @@ def test_router_routes_by_free_memory(oo_mod):
     finally:
         for c in (small, big, idle):
             oo.oo_destroy(c)
+
+
+def test_router_falls_over_to_the_next_replica_on_back_pressure(oo_mod):
+    """A replica whose queue is full answers OO_EBUSY; the router then takes
+    the next best replica, and OO_EBUSY comes back only when every replica
+    refuses."""
+    oo = oo_mod
+    tiny, spare = oo.oo_create(0), oo.oo_create(0)
+    try:
+        oo.oo_serve_start(tiny, slots=1, hbm_budget_bytes=1 << 30, queue_cap=1)   # most free memory, no queue
+        oo.oo_serve_start(spare, slots=1, hbm_budget_bytes=512 << 20, queue_cap=64)
+        router = oo.Router([tiny, spare])
+        I, J, K = 65, 65, 129
+        handles, reps = [], []
+        for i in range(6):
+            p, r = np.empty(I * J * K, np.float32), np.empty(30)
+            rep, t = router.submit(oo.serve_request("jacobi", I=I, J=J, K=K, iters=30, p=p, res=r))
+            handles.append((rep, t, p))
+            reps.append(rep)
+        assert reps[0] == 0 and 1 in reps  # the full queue sent later requests to the spare replica
+        for rep, t, _ in handles:
+            router.wait(rep, t)
+        for _, _, p in handles[1:]:
+            assert np.array_equal(p, handles[0][2])
+        oo.oo_serve_stop(spare)
+        busy = 0
+        for i in range(4):  # only the tiny replica serves now: its one-deep queue refuses some
+            try:
+                p, r = np.empty(I * J * K, np.float32), np.empty(30)
+                rep, t = router.submit(oo.serve_request("jacobi", I=I, J=J, K=K, iters=30, p=p, res=r))
+                handles.append((rep, t, p))
+            except oo.OOError as e:
+                assert e.status == oo.OO_EBUSY
+                busy += 1
+        assert busy >= 1
+        for rep, t, _ in handles[6:]:
+            router.wait(rep, t)
+        router.close()
+    finally:
+        for c in (tiny, spare):
+            oo.oo_destroy(c)
