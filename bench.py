@@ -682,6 +682,80 @@ def run_block(args):
     return 0
 
 
+def run_blocks_sweep(args):
+    """Function blocks over the survey's size ranges (device-resident
+    inputs, CUDA events on the context's stream, splits included): the GEMM
+    at n = 256, 1024, 4096 in every precision pattern (tensor TFLOP/s and
+    error vs the oracle on sampled rows), and the FFT at N = 2^10..2^22 with
+    batch max(1, 2^24 / N) (GB/s of one- or two-pass traffic against the
+    measured HBM peak; error of the first transform vs the oracle)."""
+    import torch
+    import oracle
+    from paper_2011_03602_gb300 import oo, synth
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    ctx_stream_holder[0] = stream
+    ctx = oo.oo_create(0, stream.cuda_stream)
+    hbm, hsrc = load_peaks()
+    peak, _, psrc = load_bf16_peak()
+
+    def timed(fn, reps):
+        for _ in range(3):
+            fn()
+        oo.oo_sync(ctx)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    gemm = []
+    for n in (256, 1024, 4096):
+        A_h, B_h = synth.gemm_matrix(61 + n, n, n), synth.gemm_matrix(62 + n, n, n)
+        A, B = torch.from_numpy(A_h).cuda(), torch.from_numpy(B_h).cuda()
+        C = torch.empty(n, n, dtype=torch.float64, device="cuda")
+        rows = [0, n // 2, n - 1]
+        refs = [(oracle.gemm(A_h[r:r + 1], B_h)[0], np.abs(A_h[r]) @ np.abs(B_h)) for r in rows]
+        for name, prec in (("split3_bf16", oo.OO_PREC_SPLIT3_BF16), ("split3_tf32", oo.OO_PREC_SPLIT3_TF32),
+                           ("fp64eq", oo.OO_PREC_FP64EQ)):
+            ms = timed(lambda: oo.oo_gemm_f64_dev(ctx, n, n, n, A, n, B, n, C, n, prec=prec),
+                       20 if n < 4096 else (4 if prec == oo.OO_PREC_FP64EQ else 10))
+            oo.oo_gemm_check(ctx, n, n, n)
+            products = oo.oo_gemm_plan(prec, n)[0]
+            tensor = products * 2 * n ** 3 / (ms * 1e-3) / 1e12
+            tpeak = peak * (1.1 / 2.25 if prec == oo.OO_PREC_SPLIT3_TF32 else 1.0)
+            Ch = C.cpu().numpy()
+            err = max(float(np.max(np.abs(Ch[r] - ref) / sc)) for r, (ref, sc) in zip(rows, refs))
+            gemm.append({"n": n, "pattern": name, "ms": round(ms, 4), "solves_per_s": round(1e3 / ms, 1),
+                         "tensor_tflops": round(tensor, 1), "frac_of_pattern_peak": round(tensor / tpeak, 4),
+                         "max_err_vs_oracle": err})
+        del A, B, C
+    fft = []
+    for e in range(10, 23):
+        N = 1 << e
+        batch = max(1, (1 << 24) // N)
+        x_h = synth.complex_normal(63 + e, N * batch)
+        x = torch.from_numpy(x_h.view(np.float64).copy()).cuda()
+        y = torch.empty_like(x)
+        ms = timed(lambda: oo.oo_fft_c128_dev(ctx, N, batch, -1, x, y), 10)
+        passes = 1 if e <= 12 else 2
+        gbps = passes * 32 * N * batch / (ms * 1e-3) / 1e9
+        y0 = y[:2 * N].cpu().numpy().view(np.complex128)
+        ref = oracle.fft(x_h[:N], -1)
+        fft.append({"log2n": e, "batch": batch, "ms": round(ms, 4), "passes": passes,
+                    "GBps": round(gbps, 1), "frac_of_hbm": round(gbps / hbm, 4),
+                    "rel_l2_err_vs_oracle": float(np.linalg.norm(y0 - ref) / np.linalg.norm(ref))})
+        del x, y
+    oo.oo_destroy(ctx)
+    print(json.dumps({"metric": "function blocks over the survey's size ranges", "data": "synthetic",
+                      "peaks": {"hbm_gbs": hbm, "hbm_source": hsrc, "bf16_tflops": peak, "bf16_source": psrc,
+                                "tf32_tflops_note": "measured BF16 peak x 1.1 / 2.25"},
+                      "gemm": gemm, "fft": fft}))
+    return 0
+
+
 def run_vendor(args):
     """Context only, not the product path: the function blocks beside the
     FP64 library calls a function-block offload would otherwise make
@@ -1196,6 +1270,8 @@ def main():
     ap.add_argument("--vendor", action="store_true",
                     help="context: function blocks beside cuBLAS DGEMM / cuFFT Z2Z on the same GPU")
     ap.add_argument("--serve", action="store_true", help="serving-loop configuration")
+    ap.add_argument("--blocks-sweep", action="store_true",
+                    help="GEMM at n = 256, 1024, 4096 in every pattern; FFT at 2^10..2^22, batch 2^24 / N")
     ap.add_argument("--serve-rates", default="2000,5000,10000,20000")
     ap.add_argument("--serve-prec", choices=["fp64eq", "split3"], default="fp64eq")
     ap.add_argument("--serve-modes", default="resident,host",
@@ -1239,6 +1315,8 @@ def main():
         return run_ga(args)
     if args.block:
         return run_block(args)
+    if args.blocks_sweep:
+        return run_blocks_sweep(args)
     if args.vendor:
         return run_vendor(args)
     if args.batched:
