@@ -80,19 +80,24 @@ __device__ __forceinline__ void first_stage_regs(float4 *sd, const float4 *v, co
 // MODE 0: whole transforms of length L = n, several per CTA (double in/out)
 // MODE 1: four-step pass 1: columns of length N1 (double in, ff out x twiddle)
 // MODE 2: four-step pass 2: rows of length N2 (ff in, double out at k1 + N1 k2)
-// Two CTAs per SM (64 registers, no spills) where shared memory allows
-// (L <= 2048: 96 KB each), so one CTA's global loads and stores overlap the
-// other's butterflies: 2^22 in 0.229 ms instead of 0.262 ms with one.
+// Two CTAs per SM (64 registers, no spills; at most 96 KB of shared memory
+// each, the 4096-point table being read in place), so one CTA's global loads
+// and stores overlap the other's butterflies: 2^22 in 0.229 ms instead of
+// 0.262 ms with one.
 template <int MODE>
 __global__ void __launch_bounds__(kFftThreads, 2) fft_pass_kernel(FftArgs a) {
     extern __shared__ __align__(16) float4 fsmem[];
     float4 *sd = fsmem;
-    float4 *stw = fsmem + kFftElems;
     const int log2L = MODE == 0 ? a.log2n : (MODE == 1 ? a.log2n1 : a.log2n2);
     const int L = 1 << log2L;
     const int C = kFftElems >> log2L;  // columns (transforms / rows) in this CTA
     const bool inv = a.inverse != 0;
-    for (int t = threadIdx.x; t < stage_table_count(log2L); t += kFftThreads) stw[t] = a.tw[t];
+    const float4 *stw = a.tw;  // the 4096-point table is read in place
+    if (twiddles_staged(log2L)) {
+        float4 *t_s = fsmem + kFftElems;
+        for (int t = threadIdx.x; t < stage_table_count(log2L); t += kFftThreads) t_s[t] = a.tw[t];
+        stw = t_s;
+    }
 
     const long long n = a.n;
     const int N1 = 1 << a.log2n1, N2 = 1 << a.log2n2;
@@ -269,7 +274,7 @@ __global__ void __launch_bounds__(kFftThreads, 2)
     extern __shared__ __align__(16) float4 fsmem[];
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const FftItem item = items[it];
-        fft_group_item(item, reqs, tlist, expo, fsmem, fsmem + kFftElems);
+        fft_group_item(item, reqs, tlist, expo, fsmem, fsmem + kFftElems, false);
     }
 }
 
@@ -400,9 +405,9 @@ void launch_fft(const FftPlan *p, int batch, int dir, const double *in, double *
     a.inverse = dir > 0 ? 1 : 0;
     a.expo = expo;
     static std::atomic<uint64_t> attr_done[3];
-    auto smem_for = [&](int log2L) { return (size_t)(kFftElems + (1 << log2L)) * sizeof(float4); };
+    auto smem_for = [&](int log2L) { return fft_smem_bytes(log2L); };
     auto prep = [&](int mode, const void *fn, size_t smem) {
-        set_smem_limit_once(fn, smem_for(12), attr_done[mode]);
+        set_smem_limit_once(fn, kFftSmemMax, attr_done[mode]);
         (void)smem;
     };
     if (!four_step) {
@@ -532,12 +537,12 @@ FftGroup *fft_group_create(const std::vector<FftDesc> &v, const std::vector<cons
         part[2] = items_b;
         std::vector<FftItem> all;
         for (int q = 0; q < 3; ++q) {
-            int maxl = 0;
-            for (const FftItem &it : part[q]) maxl = std::max(maxl, it.log2L);
             all.insert(all.end(), part[q].begin(), part[q].end());
             g->n_items[q] = (int)part[q].size();
-            // data + this launch's largest per-stage twiddle table
-            g->smem[q] = (size_t)(kFftElems + (1 << maxl)) * sizeof(float4);
+            // data + the largest per-stage twiddle table staged in this launch
+            size_t smem = fft_smem_bytes(0);
+            for (const FftItem &it : part[q]) smem = std::max(smem, fft_smem_bytes(it.log2L));
+            g->smem[q] = smem;
             const int per_sm = g->smem[q] <= (size_t)110 * 1024 ? 2 : 1;
             g->grid[q] = std::max(1, std::min(g->n_items[q], num_sms * per_sm));
         }
@@ -565,7 +570,7 @@ void fft_group_launch(FftGroup *g, cudaStream_t s) {
     fft_maxexp_group_kernel<<<dim3(g->maxexp_x, g->nreq), 256, 0, s>>>(g->d_reqs, g->d_expo);
     OO_CUDA_TRY(cudaGetLastError());
     static std::atomic<uint64_t> attr{0};
-    set_smem_limit_once((const void *)fft_group_kernel, (size_t)(kFftElems + 4096) * sizeof(float4), attr);
+    set_smem_limit_once((const void *)fft_group_kernel, kFftSmemMax, attr);
     int first = 0;
     for (int q = 0; q < 3; ++q) {
         if (g->n_items[q] > 0) {

@@ -150,6 +150,21 @@ __host__ __device__ __forceinline__ int stage_table_count(int log2L) {
     return log2L <= 3 ? 0 : (1 << log2L) - (1 << first_radix_log2(log2L));
 }
 
+// Where a pass reads its per-stage table.  Up to L = 2048 (2040 entries,
+// 32 KB) it is staged in shared memory beside the 64 KB of data; the
+// 4096-point table (4088 entries, 64 KB) is read in place from global memory,
+// cached in L1: staged, it would double the CTA's shared memory to 128 KB and
+// leave one CTA per SM, while in place two CTAs fit and one's global loads and
+// stores overlap the other's butterflies.  Same entries, same arithmetic: the
+// results do not depend on where the table is read from.
+__host__ __device__ __forceinline__ bool twiddles_staged(int log2L) { return log2L < 12; }
+// dynamic shared memory of a CTA running a pass of length 2^log2L
+__host__ __device__ __forceinline__ size_t fft_smem_bytes(int log2L) {
+    return (size_t)(kFftElems + (twiddles_staged(log2L) ? (1 << log2L) : 0)) * 16;
+}
+// the largest of those (L = 2048: 96 KB)
+constexpr size_t kFftSmemMax = (size_t)(kFftElems + 2048) * 16;
+
 // 1 / sqrt(2) as a float pair (hi, lo)
 constexpr double kInvSqrt2 = 0.70710678118654752440084436210485;
 constexpr float kS2h = (float)kInvSqrt2;
@@ -331,16 +346,21 @@ __device__ __forceinline__ int scale_from(int e) { return e == 0 ? 0 : e - 1023 
 // resident serving loop alike): mode 0, `count` whole transforms of length
 // 2^log2L (request ids at tlist[first ..]); mode 1 / 2, the four-step column /
 // row pass of request `first` starting at column / row c0.  512 threads; sd
-// holds kFftElems values, stw the pass's per-stage twiddle table.
+// holds kFftElems values, stw room for the pass's per-stage twiddle table:
+// every table is staged there when stage_all is set (callers whose global
+// loads bypass L1), else the 4096-point one is read in place.
 __device__ __forceinline__ void fft_group_item(const FftItem &item, const FftGroupReq *reqs, const int *tlist,
-                                               const int *expo, float4 *sd, float4 *stw) {
+                                               const int *expo, float4 *sd, float4 *stw, bool stage_all) {
     const int log2L = item.log2L, L = 1 << log2L;
     const int C = kFftElems >> log2L;
     const FftGroupReq &R0 = reqs[item.mode == 0 ? tlist[item.first] : item.first];
     const float4 *tw = item.mode == 0 ? R0.tw : (item.mode == 1 ? R0.tw_n1 : R0.tw_n2);
     const bool inv = R0.inverse != 0;
     __syncthreads();  // previous item's shared-memory reads are done
-    for (int t = threadIdx.x; t < stage_table_count(log2L); t += kFftThreads) stw[t] = tw[t];
+    const bool staged = stage_all || twiddles_staged(log2L);
+    if (staged)
+        for (int t = threadIdx.x; t < stage_table_count(log2L); t += kFftThreads) stw[t] = tw[t];
+    const float4 *tws = staged ? stw : tw;
     const int N1 = 1 << R0.log2n1, N2 = 1 << R0.log2n2;
     // ---- load
     for (int q = threadIdx.x; q < kFftElems; q += kFftThreads) {
@@ -372,7 +392,7 @@ __device__ __forceinline__ void fft_group_item(const FftItem &item, const FftGro
         sd[(c << log2L) + t] = v;
     }
     __syncthreads();
-    fft_in_smem(sd, stw, log2L, inv);
+    fft_in_smem(sd, tws, log2L, inv);
     // ---- store
     for (int q = threadIdx.x; q < kFftElems; q += kFftThreads) {
         int c, t;

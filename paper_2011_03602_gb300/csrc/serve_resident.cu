@@ -143,7 +143,7 @@ __device__ __forceinline__ void run_item(const SimtArgs &a, const Entry &E, int 
             it.log2L = R.log2n2;
             it.c0 = i * (kFftElems >> R.log2n2);
         }
-        fft_group_item(it, a.fft, a.tlist, a.expo, sm, sm + kFftElems);
+        fft_group_item(it, a.fft, a.tlist, a.expo, sm, sm + kFftElems, true);  // loads here bypass L1
     } else {
         const JacDesc J = a.jac[E.slot];
         const size_t sj = (size_t)J.pitch, si = (size_t)J.J * J.pitch;
