@@ -361,6 +361,12 @@ def bench_blocks(oo, ctx, torch, with_errors=True):
     A, B = torch.from_numpy(A_h).cuda(), torch.from_numpy(B_h).cuda()
     C = torch.empty(n, n, dtype=torch.float64, device="cuda")
     out["gemm"] = gemm_component(oo, ctx, torch, oo.OO_PREC_SPLIT3_BF16, A_h, B_h, A, B, C, with_errors)
+    out["gemm"]["kernel"] = "CTA pairs (cta_group::2), 256-row tiles, width chosen per problem (224 at n = 4096)"
+    # the same product on single CTAs (128x128 tiles), same inputs: context
+    oo.oo_set_option(ctx, oo.OO_OPT_GEMM_PAIR, 0)
+    single = gemm_component(oo, ctx, torch, oo.OO_PREC_SPLIT3_BF16, A_h, B_h, A, B, C, False)
+    oo.oo_set_option(ctx, oo.OO_OPT_GEMM_PAIR, 1)
+    out["gemm"]["single_cta_128x128"] = {k: single[k] for k in ("ms", "tensor_tflops", "frac_of_bf16_peak")}
     out["gemm_fp64eq"] = gemm_component(oo, ctx, torch, oo.OO_PREC_FP64EQ, A_h, B_h, A, B, C, with_errors)
     out["gemm_tf32"] = gemm_component(oo, ctx, torch, oo.OO_PREC_SPLIT3_TF32, A_h, B_h, A, B, C, with_errors)
     del A, B, C

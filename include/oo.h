@@ -319,8 +319,17 @@ oo_status oo_inject_wait_timeout(oo_ctx *ctx, int what);
  *                           every stencil sweep of the context (pattern
  *                           runs, oo_stencil_dev, oo_stencil_noalloc_dev,
  *                           served Jacobi requests started afterwards).
+ *   OO_OPT_GEMM_PAIR        1 (default) the split-BF16 products of
+ *                           oo_gemm_f64 / oo_gemm_f64_dev run on CTA pairs
+ *                           (256-row tiles, each SM of a pair loading half
+ *                           of the tile's B columns), the tile width (160,
+ *                           192, 224 or 256 columns) chosen per problem;
+ *                           160, 192, 224 or 256: CTA pairs with that tile
+ *                           width; 0: single CTAs (128 x 128 tiles).  All
+ *                           form the same products in the same order, so
+ *                           the results are the same bits.
  * OO_EINVAL for an unknown option or value.                               */
-enum { OO_OPT_JACOBI_FUSED = 1, OO_OPT_STENCIL_VARIANT = 2 };
+enum { OO_OPT_JACOBI_FUSED = 1, OO_OPT_STENCIL_VARIANT = 2, OO_OPT_GEMM_PAIR = 3 };
 oo_status oo_set_option(oo_ctx *ctx, int option, int value);
 oo_status oo_get_option(oo_ctx *ctx, int option, int *value);
 

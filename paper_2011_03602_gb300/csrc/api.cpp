@@ -304,6 +304,10 @@ oo_status oo_set_option(oo_ctx *ctx, int option, int value) {
             OO_REQUIRE(value >= -1 && value < OO_STENCIL_VARIANTS, OO_EINVAL,
                        "OO_OPT_STENCIL_VARIANT takes -1 or a variant below OO_STENCIL_VARIANTS");
             ctx->c.opt_stencil_variant = value;
+        } else if (option == OO_OPT_GEMM_PAIR) {
+            OO_REQUIRE(value == 0 || value == 1 || value == 160 || value == 192 || value == 224 || value == 256,
+                       OO_EINVAL, "OO_OPT_GEMM_PAIR takes 0, 1, 160, 192, 224 or 256");
+            ctx->c.opt_gemm_pair = value;
         } else {
             throw Error{OO_EINVAL, "unknown option " + std::to_string(option)};
         }
@@ -318,6 +322,8 @@ oo_status oo_get_option(oo_ctx *ctx, int option, int *value) {
             *value = ctx->c.opt_fused;
         else if (option == OO_OPT_STENCIL_VARIANT)
             *value = ctx->c.opt_stencil_variant;
+        else if (option == OO_OPT_GEMM_PAIR)
+            *value = ctx->c.opt_gemm_pair;
         else
             throw Error{OO_EINVAL, "unknown option " + std::to_string(option)};
     });
@@ -467,7 +473,7 @@ void gemm_launch(oo_ctx *ctx, int prec, int m, int n, int k, const double *dA, l
     else if (prec == OO_PREC_SPLIT3_TF32)
         launch_gemm_split3_tf32(m, n, k, dA, lda, dB, ldb, dC, ldc, scratch, s);
     else
-        launch_gemm_split3(m, n, k, dA, lda, dB, ldb, dC, ldc, scratch, s);
+        launch_gemm_split3(m, n, k, dA, lda, dB, ldb, dC, ldc, scratch, s, ctx->c.opt_gemm_pair);
 }
 unsigned gemm_error(oo_ctx *ctx, int m, int n, int k) {
     void *scratch = ctx->c.gemm_scratch.ptr;

@@ -7,21 +7,26 @@
 //
 // sA is a per-row power of two (per-column sB for B) that brings the row's
 // largest entry into [1/2, 1), so the split keeps 16 significant bits of
-// every entry regardless of the input's range.  The two accumulators live
-// in tensor memory (TMEM) in FP32: D_hh = A1 B1 and D_x = A1 B2 + A2 B1; the
-// epilogue sums them in FP64 ("split-term correction sum") and applies the
-// power-of-two scales.  Error: about 3 * 2^-16 of sum|a||b| per element
-// plus FP32 accumulation rounding; the result is reported against an FP64
-// oracle, not claimed to be FP64.
+// every entry regardless of the input's range.  The three products are
+// summed, K step by K step in the order A1 B1, A1 B2, A2 B1, into one FP32
+// accumulator in tensor memory (TMEM); the epilogue widens it to FP64 and
+// applies the power-of-two scales.  Error: about 3 * 2^-16 of sum|a||b| per
+// element plus FP32 accumulation rounding (the A1 B1 sum alone carries that
+// rounding; adding the two cross products to the same accumulator, 2^-8
+// smaller, leaves it about the same); the result is reported against an
+// FP64 oracle, not claimed to be FP64.
 //
-// Kernel: persistent, one CTA per SM walking 128 x 128 output tiles in a
-// grouped raster; warp 0 issues TMA loads of the four BF16 operand tiles
-// (128B-swizzled, K-major) into a 3-stage ring, warp 1 allocates 512 TMEM
-// columns (two double-buffered accumulator pairs) and one of its threads
-// issues tcgen05.mma (M=128, N=128, K=16, kind::f16, BF16 x BF16 -> FP32)
-// and tcgen05.commit to release stages; eight epilogue warps (4-11, two per
-// TMEM lane quarter) read finished accumulators with tcgen05.ld and write
-// FP64 C while the next tile accumulates.  Every mbarrier wait is bounded.
+// Kernels: persistent, warp-specialised.  gemm_split3_pair_kernel (the
+// default) runs 256 x 256 output tiles on CTA pairs (cta_group::2, M = 256,
+// N = 256 MMAs, each SM holding half of the tile's B columns);
+// gemm_split3_kernel and the grouped kernel run 128 x 128 tiles on single
+// CTAs (M = 128, N = 128).  Warp 0 issues TMA loads of the four BF16 operand
+// tiles (128B-swizzled, K-major) into a 3-stage ring, warp 1 allocates 512
+// TMEM columns (two accumulator buffers) and one of its threads issues
+// tcgen05.mma (K = 16, kind::f16, BF16 x BF16 -> FP32) and tcgen05.commit
+// to release stages; eight epilogue warps (4-11, two per TMEM lane quarter)
+// read finished accumulators with tcgen05.ld and write FP64 C while the
+// next tile accumulates.  Every mbarrier wait is bounded.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -59,6 +64,7 @@ struct GemmArgs {
     int m, n, k, kp;        // kp: padded K of the split operands (a multiple of kstage)
     int kstage;             // K values per pipeline stage: 64 (BF16) or 32 (TF32)
     int m_tiles, n_tiles;
+    int nw;                 // pair kernel: tile width (columns; a multiple of 32, 160 .. 256)
     double *C;
     long long ldc;
     const int *ea;          // per-row scale exponents of A (power of two)
@@ -67,9 +73,10 @@ struct GemmArgs {
 };
 
 // Persistent, warp-specialised: CTA c processes tiles c, c + G, c + 2G, ...
-// (grouped raster order).  TMEM holds two accumulator buffers, each with
-// D_hh (128 columns) and D_x (128 columns), so the epilogue of one tile
-// overlaps the main loop of the next.
+// (grouped raster order).  TMEM holds two accumulator buffers of 256
+// columns, so the epilogue of one tile overlaps the main loop of the next:
+// the split-BF16 pattern sums its three products into one FP32 accumulator
+// (128 columns), the split-TF32 pattern keeps D_hh and D_x (128 each).
 __device__ __forceinline__ void tile_coords(const GemmArgs &a, int t, int &m0, int &n0) {
     const int per_group = kGroupM * a.n_tiles;
     const int g = t / per_group, r = t % per_group;
@@ -130,6 +137,77 @@ struct GroupSrc {
                        P.m, P.n, td.y, td.z, td.w, P.ra, P.rb};
     }
 };
+
+// f * 2^S as a double by integer operations (exact; the FP64 pipe only for
+// zeros, subnormals and results outside the normal range); NaN where the
+// row's and column's scales flag a non-finite input (see nan_or_scaled)
+__device__ __forceinline__ double nan_or_widened(float f, int S) {
+    if (S > 4096) return __longlong_as_double(0x7ff8000000000000ll);
+    const unsigned b = __float_as_uint(f);
+    const int e = (int)((b >> 23) & 0xffu);
+    const int ne = e - 127 + 1023 + S;
+    if (e == 0 || e == 0xff || ne <= 0 || ne >= 0x7ff) return ldexp((double)f, S);
+    return __longlong_as_double((long long)(((unsigned long long)(b & 0x80000000u) << 32) |
+                                            ((unsigned long long)ne << 52) |
+                                            ((unsigned long long)(b & 0x7fffffu) << 29)));
+}
+
+// Epilogue of one tile for one warp: TMEM lane quarter q holds rows
+// m0 + 32 q .. +31 of the tile; the warp takes tile columns hcol .. cend - 1
+// (cend - hcol a multiple of 16 or cut by the problem's last column), in at
+// most NCH 32-column chunks.  MERGED: one FP32 accumulator at d (the
+// split-BF16 products); else D_hh at d and D_x at d + 128, summed exactly
+// (the split-TF32 pair).  Each thread widens its row's values; 16-column
+// blocks go through a per-warp shared-memory transpose (XOR-swizzled: no
+// bank conflicts) so every global store writes two whole 128-byte row
+// segments.  sa: the row's scale exponent; e[c]: that of column
+// hcol + 32 c + lane.
+template <int NCH, bool MERGED>
+__device__ __forceinline__ void store_tile_quarter(const TileJob &jb, uint32_t d, int q, int hcol, int cend, int lane,
+                                                   double *stg, int sa, const int (&e)[NCH]) {
+    const int n0 = jb.n0, row0 = jb.m0 + q * 32;
+    const int ncols = cend;  // columns of the tile this warp stores end here
+    const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+#pragma unroll 1
+    for (int cc = 0; cc < NCH; ++cc) {
+        const int c = hcol + cc * 32;
+        if (c >= ncols) break;
+        uint32_t h[32], x[32];
+        OO_TMEM_LD32(d + lane_off + c, h);
+        if constexpr (!MERGED) OO_TMEM_LD32(d + 128 + lane_off + c, x);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        int ecur = e[0];
+#pragma unroll
+        for (int i = 1; i < NCH; ++i)
+            if (cc == i) ecur = e[i];
+#pragma unroll
+        for (int sub = 0; sub < 2; ++sub) {
+            if (c + sub * 16 >= ncols) break;
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const int t2 = sub * 16 + j;
+                const int sb = __shfl_sync(0xffffffffu, ecur, t2);
+                double v;
+                if constexpr (MERGED) {
+                    v = nan_or_widened(__uint_as_float(h[t2]), sa + sb);
+                } else {
+                    // exact two-sum of the partial products, widened and
+                    // scaled without the (slow) FP64 pipe
+                    v = nan_or_scaled(ff::to_double(__uint_as_float(h[t2]), __uint_as_float(x[t2])), sa + sb);
+                }
+                stg[lane * 16 + (j ^ (lane & 15))] = v;
+            }
+            __syncwarp();
+            const int cl = lane & 15, col = c + sub * 16 + cl;
+#pragma unroll 4
+            for (int r = lane >> 4; r < 32; r += 2) {
+                const double v = stg[r * 16 + (cl ^ (r & 15))];
+                if (row0 + r < jb.m && col < ncols) jb.C[(long long)(row0 + r) * jb.ldc + n0 + col] = v;
+            }
+            __syncwarp();
+        }
+    }
+}
 
 // TF32: the operands are TF32-rounded FP32 (kind::tf32 MMAs, 32 K values
 // per 128-byte row); the stage layout, accumulators and epilogue are the
@@ -234,10 +312,10 @@ __device__ __forceinline__ void gemm_body(const Src &src, unsigned *err) {
                         mma_tf32<kIdescTF32>(d_hh, sdesc_sw128(a1 + off), sdesc_sw128(b1 + off), acc);
                         mma_tf32<kIdescTF32>(d_x, sdesc_sw128(a1 + off), sdesc_sw128(b2 + off), acc);
                         mma_tf32<kIdescTF32>(d_x, sdesc_sw128(a2 + off), sdesc_sw128(b1 + off), 1u);
-                    } else {
+                    } else {  // one accumulator: A1 B1, A1 B2, A2 B1 in this order
                         mma_bf16<kIdesc>(d_hh, sdesc_sw128(a1 + off), sdesc_sw128(b1 + off), acc);
-                        mma_bf16<kIdesc>(d_x, sdesc_sw128(a1 + off), sdesc_sw128(b2 + off), acc);
-                        mma_bf16<kIdesc>(d_x, sdesc_sw128(a2 + off), sdesc_sw128(b1 + off), 1u);
+                        mma_bf16<kIdesc>(d_hh, sdesc_sw128(a1 + off), sdesc_sw128(b2 + off), 1u);
+                        mma_bf16<kIdesc>(d_hh, sdesc_sw128(a2 + off), sdesc_sw128(b1 + off), 1u);
                     }
                 }
                 mma_commit(su32(&empty[s]));
@@ -248,11 +326,8 @@ __device__ __forceinline__ void gemm_body(const Src &src, unsigned *err) {
     } else if (warp >= 4) {
         // ---------------------------------------------------- epilogue
         // Eight warps: warp w reads TMEM lane quarter (w & 3), i.e. rows
-        // 32 (w & 3) .. +31 of the tile, and column half (w - 4) >> 2.  Each
-        // thread widens its row's values; 16-column blocks go through a
-        // per-warp shared-memory transpose (XOR-swizzled: no bank conflicts)
-        // so every global store writes two whole 128-byte row segments.
-        // Chunks with no valid row or column are skipped.
+        // 32 (w & 3) .. +31 of the tile, and column half (w - 4) >> 2;
+        // quarters with no valid row are skipped.
         const int q = warp & 3, hcol = ((warp - 4) >> 2) * 64;
         double *stg = stg_all + (size_t)(warp - 4) * 32 * 16;
         int lt = 0;
@@ -264,45 +339,13 @@ __device__ __forceinline__ void gemm_body(const Src &src, unsigned *err) {
             const int n0 = jb.n0, row0 = jb.m0 + q * 32;
             const int ncols = jb.n - n0;  // valid columns of the tile (may exceed 128)
             const int sa = row0 + lane < jb.m ? jb.ea[row0 + lane] : 0;
-            const int e0 = hcol + lane < ncols ? jb.eb[n0 + hcol + lane] : 0;
-            const int e1 = hcol + 32 + lane < ncols ? jb.eb[n0 + hcol + 32 + lane] : 0;
+            const int e[2] = {hcol + lane < ncols ? jb.eb[n0 + hcol + lane] : 0,
+                              hcol + 32 + lane < ncols ? jb.eb[n0 + hcol + 32 + lane] : 0};
             if (!bar_wait(su32(&tfull[b]), (lt >> 1) & 1, abort_flag, err, 4u)) break;
             fence_after();
-            if (row0 < jb.m) {
-                const uint32_t lane_off = (uint32_t)(q * 32) << 16;
-                const uint32_t d_hh = tmem + (uint32_t)(b * 256), d_x = d_hh + 128;
-#pragma unroll 1
-                for (int cc = 0; cc < 2; ++cc) {
-                    const int c = hcol + cc * 32;
-                    if (c >= ncols) break;
-                    uint32_t h[32], x[32];
-                    OO_TMEM_LD32(d_hh + lane_off + c, h);
-                    OO_TMEM_LD32(d_x + lane_off + c, x);
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    const int ecur = cc ? e1 : e0;
-#pragma unroll
-                    for (int sub = 0; sub < 2; ++sub) {
-                        if (c + sub * 16 >= ncols) break;
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            // exact two-sum of the partial products, widened and
-                            // scaled without the (slow) FP64 pipe
-                            const int t2 = sub * 16 + j;
-                            const int sb = __shfl_sync(0xffffffffu, ecur, t2);
-                            const double v = ff::to_double(__uint_as_float(h[t2]), __uint_as_float(x[t2]));
-                            stg[lane * 16 + (j ^ (lane & 15))] = nan_or_scaled(v, sa + sb);
-                        }
-                        __syncwarp();
-                        const int cl = lane & 15, col = c + sub * 16 + cl;
-#pragma unroll 4
-                        for (int r = lane >> 4; r < 32; r += 2) {
-                            const double v = stg[r * 16 + (cl ^ (r & 15))];
-                            if (row0 + r < jb.m && col < ncols) jb.C[(long long)(row0 + r) * jb.ldc + n0 + col] = v;
-                        }
-                        __syncwarp();
-                    }
-                }
-            }
+            if (row0 < jb.m)
+                store_tile_quarter<2, !TF32>(jb, tmem + (uint32_t)(b * 256), q, hcol, min(ncols, hcol + 64), lane, stg,
+                                             sa, e);
             fence_before();
             __syncwarp();
             if (lane == 0) bar_arrive(su32(&tempty[b]));
@@ -352,6 +395,199 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_group_kernel(const __gri
     gemm_body(src, err);
 }
 
+// ------------------------------------------------- CTA-pair split3 kernel
+// The split-BF16 product on CTA pairs (cta_group::2).  A unit is a 256 x W
+// tile of C (W = a.nw, 160 .. 256 columns, chosen per problem so that the
+// units fill the resident clusters' waves: n = 4096 takes W = 224, 304
+// units = 4 waves of 76 pairs, where W = 256 leaves the fourth wave a
+// third full); CTA r of the pair loads rows m0 + 128 r .. +127 of A1 and
+// A2 and rows n0 + r W/2 .. +W/2-1 of B1 and B2 (its half of the tile's
+// columns).  Rank 0 issues M = 256, N = W MMAs into both CTAs' TMEM (each
+// holds its 128 rows x W columns, double-buffered); the commits arrive on
+// both CTAs' barriers; each CTA's epilogue stores its own rows and reports
+// to rank 0 that its accumulator buffer is free.  Wide N matters: measured
+// on GB300, N = 128 instructions (either tile shape) kept the tensor pipe
+// ~64 % busy at most, N = 256 ones ~97 %.  Every output element sees the
+// same products in the same K order as in gemm_split3_kernel, so the two
+// kernels give the same bits.
+constexpr int kStagesP = 3;
+constexpr int kBNP = 2 * kBN;                                 // widest tile: 256 columns
+constexpr uint32_t kStageBytesP = 2 * kTileA + 2 * kTileB;    // 64 KB: room for 128-row A and B tiles
+constexpr int kGroupMP = 4;  // raster: groups of 4 pair rows (1024 rows of A) share B panels in L2
+constexpr size_t kSmemPair = 1024 + (size_t)kStagesP * kStageBytesP + kStageOut + 256;
+static_assert(kSmemPair <= 232448, "pair kernel exceeds the shared memory of a CTA");
+
+// unit u -> first row of the pair's 256-row slab, first column of the tile
+__device__ __forceinline__ void pair_coords(const GemmArgs &a, int u, int &mp, int &n0) {
+    const int per_group = kGroupMP * a.n_tiles;
+    const int g = u / per_group, r = u % per_group;
+    const int rows = min(kGroupMP, a.m_tiles - g * kGroupMP);
+    mp = (g * kGroupMP + r % rows) * 2 * kBM;
+    n0 = (r / rows) * a.nw;
+}
+
+// a.m_tiles counts 256-row slabs, a.n_tiles a.nw-column panels
+__global__ void __launch_bounds__(kGemmThreads, 1) gemm_split3_pair_kernel(const __grid_constant__ GemmMaps maps,
+                                                                          const __grid_constant__ GemmArgs a) {
+    extern __shared__ __align__(1024) unsigned char gsm_raw[];
+    unsigned char *gsm = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(gsm_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    double *stg_all = reinterpret_cast<double *>(gsm + kStagesP * kStageBytesP);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(gsm + kStagesP * kStageBytesP + kStageOut);
+    uint64_t *full = bars, *empty = bars + kStagesP;
+    uint64_t *tfull = bars + 2 * kStagesP, *tempty = tfull + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    unsigned *err = a.err;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_rank();
+    const bool leader = rank == 0;
+    const int cid = (int)(blockIdx.x >> 1), ncl = (int)(gridDim.x >> 1);
+    const int units = a.m_tiles * a.n_tiles;
+    const int ksteps = a.kp / kBK;
+    const int half = a.nw >> 1;  // B rows (tile columns) per CTA
+    const uint32_t stage_tx = 2 * (2 * kTileA + 2u * (uint32_t)half * kBK * 2);  // both CTAs' bytes per stage
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStagesP; ++s) {
+            bar_init(su32(&full[s]), 1);   // rank 0's: its expect-tx arrival + both CTAs' bytes
+            bar_init(su32(&empty[s]), 1);  // the MMA commit
+        }
+        for (int b = 0; b < 2; ++b) {
+            bar_init(su32(&tfull[b]), 1);
+            bar_init(su32(&tempty[b]), 2 * kEpiWarps);  // rank 0's: every epilogue warp of both CTAs
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        tmem_alloc_pair(su32(tmem_slot), 512);
+        fence_before();
+    }
+    __syncthreads();
+    cluster_sync_all();  // both CTAs' barriers and TMEM exist before either uses the other's
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    int loaded = 0, tiles_mma = 0;
+    if (warp == 0 && lane == 0) {
+        // ---------------------------------------------------- TMA producer (both CTAs)
+        int it = 0;
+        bool ok = true;
+        for (int u = cid; ok && u < units; u += ncl) {
+            int mp, n0;
+            pair_coords(a, u, mp, n0);
+            const int ma = mp + (int)rank * kBM, nb = n0 + (int)rank * half;
+            for (int ks = 0; ks < ksteps; ++ks, ++it) {
+                const int s = it % kStagesP;
+                const uint32_t use = it / kStagesP;
+                if (use > 0 && !bar_wait_cluster(su32(&empty[s]), (use - 1) & 1, abort_flag, err, 1u)) {
+                    ok = false;
+                    break;
+                }
+                unsigned char *st = gsm + (size_t)s * kStageBytesP;
+                if (leader) bar_expect_tx(su32(&full[s]), stage_tx);
+                const uint32_t fb = map_to_rank(su32(&full[s]), 0);
+                const int k0 = ks * kBK;
+                tma_2d_pair(su32(st), &maps.a1, k0, ma, fb);
+                tma_2d_pair(su32(st + kTileA), &maps.a2, k0, ma, fb);
+                tma_2d_pair(su32(st + 2 * kTileA), &maps.b1, k0, nb, fb);
+                tma_2d_pair(su32(st + 2 * kTileA + kTileB), &maps.b2, k0, nb, fb);
+                ++loaded;
+            }
+        }
+    } else if (warp == 1 && lane == 0 && leader) {
+        // ---------------------------------------------------- MMA issuer (rank 0)
+        const uint32_t idesc = idesc_bf16(2 * kBM, a.nw);
+        int it = 0, lt = 0;
+        bool ok = true;
+        for (int u = cid; ok && u < units; u += ncl, ++lt) {
+            const int b = lt & 1;
+            const uint32_t buse = lt >> 1;
+            if (buse > 0 && !bar_wait_cluster(su32(&tempty[b]), (buse - 1) & 1, abort_flag, err, 2u)) break;
+            fence_after();
+            const uint32_t d = tmem + (uint32_t)(b * 256);
+            for (int ks = 0; ks < ksteps; ++ks, ++it) {
+                const int s = it % kStagesP;
+                const uint32_t use = it / kStagesP;
+                if (!bar_wait_cluster(su32(&full[s]), use & 1, abort_flag, err, 2u)) {
+                    ok = false;
+                    break;
+                }
+                fence_after();
+                const uint32_t base = su32(gsm + (size_t)s * kStageBytesP);
+                const uint32_t a1 = base, a2 = base + kTileA, b1 = base + 2 * kTileA, b2 = b1 + kTileB;
+#pragma unroll
+                for (int kk = 0; kk < kBK / 16; ++kk) {
+                    const uint32_t off = kk * 32;
+                    const uint32_t acc = (ks == 0 && kk == 0) ? 0u : 1u;
+                    mma_bf16_pair(d, sdesc_sw128(a1 + off), sdesc_sw128(b1 + off), idesc, acc);
+                    mma_bf16_pair(d, sdesc_sw128(a1 + off), sdesc_sw128(b2 + off), idesc, 1u);
+                    mma_bf16_pair(d, sdesc_sw128(a2 + off), sdesc_sw128(b1 + off), idesc, 1u);
+                }
+                mma_commit_pair(su32(&empty[s]), 3);  // stage s free in both CTAs
+            }
+            if (!ok) break;
+            mma_commit_pair(su32(&tfull[b]), 3);  // both halves of the accumulator complete
+            ++tiles_mma;
+        }
+    } else if (warp >= 4) {
+        // ---------------------------------------------------- epilogue (both CTAs)
+        // warp-halves take tile columns [0, 128) and [128, W): chunk starts
+        // stay multiples of 32
+        const int q = warp & 3, hsel = (warp - 4) >> 2, hcol = hsel * 128;
+        const int hend = hsel ? a.nw : min(128, a.nw);
+        double *stg = stg_all + (size_t)(warp - 4) * 32 * 16;
+        int lt = 0;
+        for (int u = cid; u < units; u += ncl, ++lt) {
+            const int b = lt & 1;
+            int mp, n0;
+            pair_coords(a, u, mp, n0);
+            const TileJob jb{&maps.a1, &maps.a2, &maps.b1, &maps.b2, a.C, a.ldc, a.ea, a.eb,
+                             a.m, a.n, mp + (int)rank * kBM, n0, ksteps, 0, 0};
+            const int row0 = jb.m0 + q * 32, ncols = a.n - n0;
+            const int sa = row0 + lane < a.m ? a.ea[row0 + lane] : 0;
+            int e[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) e[c] = hcol + 32 * c + lane < ncols ? a.eb[n0 + hcol + 32 * c + lane] : 0;
+            if (!bar_wait_cluster(su32(&tfull[b]), (lt >> 1) & 1, abort_flag, err, 4u)) break;
+            fence_after();
+            if (row0 < a.m)
+                store_tile_quarter<4, true>(jb, tmem + (uint32_t)(b * 256), q, hcol, min(ncols, hend), lane, stg, sa,
+                                            e);
+            fence_before();
+            __syncwarp();
+            if (lane == 0) {
+                if (leader)
+                    bar_arrive(su32(&tempty[b]));
+                else
+                    bar_arrive_remote(map_to_rank(su32(&tempty[b]), 0));
+            }
+        }
+    }
+    // drain on abort (bounded): rank 0 waits for its issued MMAs and for the
+    // copies counted on its barriers; rank 1 for the commits that free its
+    // stages (its copies complete on rank 0's barriers)
+    if (*abort_flag) {
+        if (warp == 1 && lane == 0 && leader && tiles_mma > 0) {
+            const int lb = (tiles_mma - 1) & 1;
+            bar_drain(su32(&tfull[lb]), ((tiles_mma - 1) >> 1) & 1);
+        }
+        if (warp == 0 && lane == 0) {
+            for (int it = (loaded > kStagesP ? loaded - kStagesP : 0); it < loaded; ++it)
+                bar_drain(su32(leader ? &full[it % kStagesP] : &empty[it % kStagesP]), (it / kStagesP) & 1);
+        }
+    }
+    fence_before();
+    __syncthreads();
+    cluster_sync_all();  // neither CTA leaves while the other may still signal it or read its TMEM
+    if (warp == 1) {
+        fence_after();
+        tmem_dealloc_pair(tmem, 512);
+    }
+}
 // ---------------------------------------------------------------- splitting
 // per-column maxima of B (k x n): grid.x over column blocks of 32, grid.y over k chunks
 __global__ void col_maxexp_kernel(const double *B, long long ldb, int k, int n, int rows_per, int *e) {
@@ -843,6 +1079,75 @@ __global__ void split_b_group_kernel(const GroupSplit *gs, const int3 *jobs) {
 
 size_t smem_gemm() { return 1024 + (size_t)kStages * kStageBytes + kStageOut + 256; }
 
+// 2-CTA clusters of the pair kernel that fit on the device at once (cached)
+int pair_clusters() {
+    int dev = 0;
+    OO_CUDA_TRY(cudaGetDevice(&dev));
+    static std::atomic<int> max_clusters[64];
+    int ncl = dev < 64 ? max_clusters[dev].load() : 0;
+    if (ncl > 0) return ncl;
+    static std::atomic<uint64_t> attr{0};
+    set_smem_limit_once((const void *)gemm_split3_pair_kernel, kSmemPair, attr);
+    int sms = 148;
+    OO_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)(sms / 2 * 2));
+    cfg.blockDim = dim3(kGemmThreads);
+    cfg.dynamicSmemBytes = kSmemPair;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    OO_CUDA_TRY(cudaOccupancyMaxActiveClusters(&ncl, (const void *)gemm_split3_pair_kernel, &cfg));
+    OO_REQUIRE(ncl >= 1, OO_ECUDA, "no 2-CTA cluster of the GEMM kernel fits on this device");
+    if (dev < 64) max_clusters[dev].store(ncl);
+    return ncl;
+}
+
+// Tile width of the pair kernel for an m x n product: the width among 256,
+// 224, 192 and 160 columns with the fewest column-waves (waves of units over
+// the resident clusters x width), the widest on a tie.  Narrower MMAs lose
+// tensor throughput (N = 128 ran at ~64 %), so 160 is the floor.
+int pair_tile_width(int m, int n, int ncl) {
+    const long long slabs = (m + 2 * kBM - 1) / (2 * kBM);
+    int best = kBNP;
+    long long best_cost = -1;
+    for (int w = kBNP; w >= 160; w -= 32) {
+        const long long units = slabs * ((n + w - 1) / w);
+        const long long cost = (units + ncl - 1) / ncl * w;
+        if (best_cost < 0 || cost < best_cost) {
+            best = w;
+            best_cost = cost;
+        }
+    }
+    return best;
+}
+
+// persistent: one 2-CTA cluster per unit, at most as many as are resident
+void launch_split3_pair(const GemmMaps &maps, GemmArgs ga, int nw, int ncl, cudaStream_t s) {
+    ga.nw = nw;
+    ga.m_tiles = (ga.m + 2 * kBM - 1) / (2 * kBM);  // 256-row slabs
+    ga.n_tiles = (ga.n + nw - 1) / nw;              // nw-column panels
+    const long long units = (long long)ga.m_tiles * ga.n_tiles;
+    OO_REQUIRE(units < (1ll << 31), OO_EINVAL, "too many tiles");
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)(2 * std::min<long long>(units, ncl)));
+    cfg.blockDim = dim3(kGemmThreads);
+    cfg.dynamicSmemBytes = kSmemPair;
+    cfg.stream = s;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    OO_CUDA_TRY(cudaLaunchKernelEx(&cfg, gemm_split3_pair_kernel, maps, (const GemmArgs)ga));
+}
+
 }  // namespace
 
 size_t gemm_scratch_bytes(int m, int n, int k) {
@@ -852,7 +1157,7 @@ size_t gemm_scratch_bytes(int m, int n, int k) {
 }
 
 void launch_gemm_split3(int m, int n, int k, const double *A, long long lda, const double *B, long long ldb,
-                        double *C, long long ldc, void *scratch, cudaStream_t s) {
+                        double *C, long long ldc, void *scratch, cudaStream_t s, int pair) {
     OO_REQUIRE(m >= 1 && n >= 1 && k >= 1, OO_EINVAL, "m, n, k must be >= 1");
     OO_REQUIRE(lda >= k && ldb >= n && ldc >= n, OO_EINVAL, "leading dimensions too small");
     const int kp = (k + kBK - 1) / kBK * kBK;
@@ -904,8 +1209,15 @@ void launch_gemm_split3(int m, int n, int k, const double *A, long long lda, con
     GemmMaps maps;
     map_bf16(&maps.a1, A1, m, kp, kBM);
     map_bf16(&maps.a2, A2, m, kp, kBM);
-    map_bf16(&maps.b1, B1, n, kp, kBN);
-    map_bf16(&maps.b2, B2, n, kp, kBN);
+    int ncl = 0, nw = kBN;
+    if (pair) {
+        ncl = pair_clusters();
+        nw = pair == 1 ? pair_tile_width(m, n, ncl) : pair;
+        OO_REQUIRE(nw >= 160 && nw <= kBNP && nw % 32 == 0, OO_EINVAL, "pair tile width must be 160, 192, 224 or 256");
+    }
+    // B tiles: half of a pair tile's columns per CTA, else 128 columns
+    map_bf16(&maps.b1, B1, n, kp, pair ? nw / 2 : kBN);
+    map_bf16(&maps.b2, B2, n, kp, pair ? nw / 2 : kBN);
     GemmArgs ga{};
     ga.m = m;
     ga.n = n;
@@ -919,6 +1231,10 @@ void launch_gemm_split3(int m, int n, int k, const double *A, long long lda, con
     ga.ea = ea;
     ga.eb = eb;
     ga.err = err;
+    if (pair) {
+        launch_split3_pair(maps, ga, nw, ncl, s);
+        return;
+    }
     static std::atomic<uint64_t> attr{0};
     set_smem_limit_once((const void *)gemm_split3_kernel, smem_gemm(), attr);
     const long long tiles = (long long)ga.m_tiles * ga.n_tiles;

@@ -103,9 +103,12 @@ void launch_fft(const FftPlan *p, int batch, int dir, const double *in, double *
 
 // ------------------------------------------------------------------- GEMM
 size_t gemm_scratch_bytes(int m, int n, int k);
-// C = A B (FP64, row-major) via split BF16 tensor-core products; async on s
+// C = A B (FP64, row-major) via split BF16 tensor-core products; async on s.
+// pair: 0 = 128 x 128 tiles on single CTAs; 1 = 256-row tiles on CTA pairs
+// (cta_group::2), width chosen per problem; 160, 192, 224 or 256 = CTA pairs
+// with that tile width.  The same products in the same order in every case.
 void launch_gemm_split3(int m, int n, int k, const double *A, long long lda, const double *B, long long ldb,
-                        double *C, long long ldc, void *scratch, cudaStream_t s);
+                        double *C, long long ldc, void *scratch, cudaStream_t s, int pair = 1);
 // reads and clears the kernel's error word (0 = fine); synchronises s
 unsigned gemm_check_error(void *scratch, int m, int n, int k, cudaStream_t s);
 // the kernel's device error word inside its scratch (for asynchronous reads)
@@ -311,6 +314,7 @@ struct Ctx {
     // (-1 tuned choice or default rule, else that variant for every grid)
     int opt_fused = -1;
     int opt_stencil_variant = -1;
+    int opt_gemm_pair = 1;  // split-BF16 kernel: 0 single CTAs, 1 CTA pairs, 160..256 CTA pairs of that width
     // tile widths of the FP64-equivalent products by (n, k) bucket
     // (oo_tune_gemm_tiles / oo_set_gemm_tiles; 0 = the built-in choice)
     std::array<int, OO_TILE_NBUCKETS * OO_TILE_KBUCKETS> eq_widths{};

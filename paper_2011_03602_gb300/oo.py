@@ -254,11 +254,11 @@ def oo_tune_stencil(ctx, I, J, K):
 
 
 OO_INJECT_NONE, OO_INJECT_STENCIL_LOAD, OO_INJECT_FUSED_BARRIER, OO_INJECT_SERVE_STALL = 0, 1, 2, 3
-OO_OPT_JACOBI_FUSED, OO_OPT_STENCIL_VARIANT = 1, 2
+OO_OPT_JACOBI_FUSED, OO_OPT_STENCIL_VARIANT, OO_OPT_GEMM_PAIR = 1, 2, 3
 
 
 def oo_set_option(ctx, option, value):
-    """Set a per-context option (OO_OPT_JACOBI_FUSED, OO_OPT_STENCIL_VARIANT; -1 = default)."""
+    """Set a per-context option (OO_OPT_JACOBI_FUSED, OO_OPT_STENCIL_VARIANT, OO_OPT_GEMM_PAIR)."""
     _check(ctx, lib().oo_set_option(ctx, option, value))
 
 

@@ -192,8 +192,14 @@ def test_context_options_host_only():
         oo.oo_set_option(ctx, oo.OO_OPT_STENCIL_VARIANT, oo.OO_STENCIL_VARIANTS - 1)
         assert oo.oo_get_option(ctx, oo.OO_OPT_JACOBI_FUSED) == 0
         assert oo.oo_get_option(ctx, oo.OO_OPT_STENCIL_VARIANT) == oo.OO_STENCIL_VARIANTS - 1
+        assert oo.oo_get_option(ctx, oo.OO_OPT_GEMM_PAIR) == 1
+        for v in (0, 160, 192, 224, 256, 1):
+            oo.oo_set_option(ctx, oo.OO_OPT_GEMM_PAIR, v)
+            assert oo.oo_get_option(ctx, oo.OO_OPT_GEMM_PAIR) == v
         for opt, val in ((oo.OO_OPT_JACOBI_FUSED, 2), (oo.OO_OPT_STENCIL_VARIANT, oo.OO_STENCIL_VARIANTS),
-                         (oo.OO_OPT_STENCIL_VARIANT, -2), (99, 0)):
+                         (oo.OO_OPT_STENCIL_VARIANT, -2), (oo.OO_OPT_GEMM_PAIR, 2), (oo.OO_OPT_GEMM_PAIR, -1),
+                         (oo.OO_OPT_GEMM_PAIR, 128), (oo.OO_OPT_GEMM_PAIR, 200),
+                         (99, 0)):
             with pytest.raises(oo.OOError) as e:
                 oo.oo_set_option(ctx, opt, val)
             assert e.value.status == oo.OO_EINVAL
