@@ -368,6 +368,11 @@ def bench_blocks(oo, ctx, torch, with_errors=True):
     oo.oo_set_option(ctx, oo.OO_OPT_GEMM_PAIR, 1)
     out["gemm"]["single_cta_128x128"] = {k: single[k] for k in ("ms", "tensor_tflops", "frac_of_bf16_peak")}
     out["gemm_fp64eq"] = gemm_component(oo, ctx, torch, oo.OO_PREC_FP64EQ, A_h, B_h, A, B, C, with_errors)
+    out["gemm_fp64eq"]["kernel"] = "CTA pairs (cta_group::2), 256x128 tiles"
+    oo.oo_set_option(ctx, oo.OO_OPT_GEMM_PAIR, 0)
+    single = gemm_component(oo, ctx, torch, oo.OO_PREC_FP64EQ, A_h, B_h, A, B, C, False)
+    oo.oo_set_option(ctx, oo.OO_OPT_GEMM_PAIR, 1)
+    out["gemm_fp64eq"]["single_cta_128x128"] = {k: single[k] for k in ("ms", "tensor_tflops", "frac_of_bf16_peak")}
     out["gemm_tf32"] = gemm_component(oo, ctx, torch, oo.OO_PREC_SPLIT3_TF32, A_h, B_h, A, B, C, with_errors)
     del A, B, C
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

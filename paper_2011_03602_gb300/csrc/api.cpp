@@ -469,7 +469,7 @@ void gemm_launch(oo_ctx *ctx, int prec, int m, int n, int k, const double *dA, l
     ctx->gemm_prec = prec;
     if (prec == OO_PREC_FP64EQ)
         launch_gemm_fp64eq(m, n, k, dA, lda, dB, ldb, dC, ldc, scratch, s,
-                           eq_tile_width(ctx->c.eq_widths.data(), n, k));
+                           eq_tile_width(ctx->c.eq_widths.data(), n, k), ctx->c.opt_gemm_pair != 0);
     else if (prec == OO_PREC_SPLIT3_TF32)
         launch_gemm_split3_tf32(m, n, k, dA, lda, dB, ldb, dC, ldc, scratch, s);
     else

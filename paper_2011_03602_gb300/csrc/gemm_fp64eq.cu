@@ -319,6 +319,237 @@ __global__ void __launch_bounds__(kThreads, 1) gemm_fp64eq_kernel(const __grid_c
     }
 }
 
+// ------------------------------------------------------------ CTA pairs
+// The same products on CTA pairs (cta_group::2, M = 256): a tile is 256 rows
+// x 128 columns, CTA r of the pair holding rows m0 + 128 r .. +127 of the
+// tile and its own accumulators and running sums.  A two-product unit
+// (p, q1) + (p, q2) is one M = 256, N = 256 MMA whose B operand is B_q1's
+// tile in rank 0's shared memory and B_q2's in rank 1's, so an SM stages
+// 32 KB (A_p and one B slice tile) per K step where a single CTA stages
+// 48 KB for the same MMA work; a one-product unit is an N = 128 MMA, each
+// CTA holding 64 of the tile's columns of B_q.  Rank 0 issues the MMAs;
+// the commits arrive on both CTAs' barriers; both epilogues report to rank
+// 0 that their accumulator buffer is free.  The D_pq of a K-block are exact
+// whatever the instruction shape, and the epilogue adds the units in the
+// same order, so the result is the single-CTA kernel's bit for bit.
+constexpr int kStagesPair = 6;
+constexpr uint32_t kStageBytesPair = 2 * kTile;  // A_p and this CTA's B tile
+constexpr uint32_t kIdescPair2 = idesc_bf16(2 * kBM, 2 * kBN);
+constexpr uint32_t kIdescOne2 = idesc_bf16(2 * kBM, kBN);
+
+struct EqPairMaps {
+    CUtensorMap a, b, bh;  // bh: B slices in 64-row boxes (one-product units)
+};
+
+__device__ __forceinline__ void eq_tile_pair(const EqArgs &a, int t, int &m0, int &n0) {
+    const int per_group = (kGroupM / 2) * a.n_tiles;
+    const int g = t / per_group, r = t % per_group;
+    const int rows = min(kGroupM / 2, a.m_tiles - g * (kGroupM / 2));
+    m0 = (g * (kGroupM / 2) + r % rows) * 2 * kBM;
+    n0 = (r / rows) * kBN;
+}
+
+// a.m_tiles counts 256-row slabs here
+__global__ void __launch_bounds__(kThreads, 1) gemm_fp64eq_pair_kernel(const __grid_constant__ EqPairMaps maps,
+                                                                      const __grid_constant__ EqArgs a) {
+    extern __shared__ __align__(1024) unsigned char esm_raw[];
+    unsigned char *sm = reinterpret_cast<unsigned char *>(
+        (reinterpret_cast<uintptr_t>(esm_raw) + 1023) & ~static_cast<uintptr_t>(1023));
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sm + kStagesPair * kStageBytesPair);
+    uint64_t *full = bars, *empty = bars + kStagesPair;
+    uint64_t *tfull = bars + 2 * kStagesPair, *tempty = tfull + 2;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_rank();
+    const bool leader = rank == 0;
+    const int cid = (int)(blockIdx.x >> 1), ncl = (int)(gridDim.x >> 1);
+    const int tiles = a.m_tiles * a.n_tiles;
+    const int units = a.nunits * a.nkb;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStagesPair; ++s) {
+            bar_init(su32(&full[s]), 1);   // rank 0's: its expect-tx arrival + both CTAs' bytes
+            bar_init(su32(&empty[s]), 1);  // the MMA commit
+        }
+        for (int b = 0; b < 2; ++b) {
+            bar_init(su32(&tfull[b]), 1);
+            bar_init(su32(&tempty[b]), 2 * kEpiWarps);  // rank 0's: every epilogue warp of both CTAs
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) {
+        tmem_alloc_pair(su32(tmem_slot), 512);
+        fence_before();
+    }
+    __syncthreads();
+    cluster_sync_all();  // both CTAs' barriers and TMEM exist before either uses the other's
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    int loaded = 0, units_mma = 0;
+    if (warp == 0 && lane == 0) {
+        // ---------------------------------------------------- TMA producer (both CTAs)
+        int it = 0;
+        bool ok = true;
+        for (int t = cid; ok && t < tiles; t += ncl) {
+            int m0, n0;
+            eq_tile_pair(a, t, m0, n0);
+            for (int u = 0; ok && u < units; ++u) {
+                const int kbi = u / a.nunits, pr = u % a.nunits;  // K-block outer: its slices stay in L2
+                const bool pair = a.uq2[pr] != kNone;
+                const int rowA = a.up[pr] * a.m + m0 + (int)rank * kBM;
+                const int rowB = pair ? (rank ? a.uq2[pr] : a.uq1[pr]) * a.n + n0
+                                      : a.uq1[pr] * a.n + n0 + (int)rank * (kBN / 2);
+                const uint32_t tx = pair ? 2 * 2 * kTile : 2 * (kTile + kTile / 2);
+                const int ks1 = min(a.ksteps, (kbi + 1) * a.kb_steps);
+                for (int ks = kbi * a.kb_steps; ks < ks1; ++ks, ++it) {
+                    const int s = it % kStagesPair;
+                    const uint32_t use = it / kStagesPair;
+                    if (use > 0 && !bar_wait_cluster(su32(&empty[s]), (use - 1) & 1, abort_flag, a.err, 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    unsigned char *st = sm + (size_t)s * kStageBytesPair;
+                    if (leader) bar_expect_tx(su32(&full[s]), tx);
+                    const uint32_t fb = map_to_rank(su32(&full[s]), 0);
+                    tma_2d_pair(su32(st), &maps.a, ks * kBK, rowA, fb);
+                    tma_2d_pair(su32(st + kTile), pair ? &maps.b : &maps.bh, ks * kBK, rowB, fb);
+                    ++loaded;
+                }
+            }
+        }
+    } else if (warp == 1 && lane == 0 && leader) {
+        // ---------------------------------------------------- MMA issuer (rank 0)
+        int it = 0, gu = 0;
+        bool ok = true;
+        for (int t = cid; ok && t < tiles; t += ncl) {
+            for (int u = 0; ok && u < units; ++u, ++gu) {
+                const int b = gu & 1;
+                const uint32_t buse = gu >> 1;
+                if (buse > 0 && !bar_wait_cluster(su32(&tempty[b]), (buse - 1) & 1, abort_flag, a.err, 2u)) {
+                    ok = false;
+                    break;
+                }
+                fence_after();
+                const uint32_t d = tmem + (uint32_t)(b * 2 * kBN);
+                const int kbi = u / a.nunits, pr = u % a.nunits;
+                const uint32_t idesc = a.uq2[pr] != kNone ? kIdescPair2 : kIdescOne2;
+                const int ks0 = kbi * a.kb_steps, ks1 = min(a.ksteps, (kbi + 1) * a.kb_steps);
+                for (int ks = ks0; ks < ks1; ++ks, ++it) {
+                    const int s = it % kStagesPair;
+                    if (!bar_wait_cluster(su32(&full[s]), (it / kStagesPair) & 1, abort_flag, a.err, 2u)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    const uint32_t sa = su32(sm + (size_t)s * kStageBytesPair), sb = sa + kTile;
+#pragma unroll
+                    for (int kk = 0; kk < kBK / 16; ++kk) {
+                        const uint32_t off = kk * 32;
+                        const uint32_t acc = (ks == ks0 && kk == 0) ? 0u : 1u;
+                        mma_bf16_pair(d, sdesc_sw128(sa + off), sdesc_sw128(sb + off), idesc, acc);
+                    }
+                    mma_commit_pair(su32(&empty[s]), 3);  // stage s free in both CTAs
+                }
+                if (!ok) break;
+                mma_commit_pair(su32(&tfull[b]), 3);  // this unit's accumulators complete in both CTAs
+                ++units_mma;
+            }
+        }
+    } else if (warp >= 2) {
+        // ---------------------------------------------------- epilogue (both CTAs)
+        const int q = warp & 3;
+        const int h = (warp - 2) >> 2;
+        const uint32_t lane_off = (uint32_t)(q * 32) << 16;
+        float Sh[64], Sl[64];
+        int gu = 0;
+        bool ok = true;
+        for (int t = cid; ok && t < tiles; t += ncl) {
+            int m0, n0;
+            eq_tile_pair(a, t, m0, n0);
+            m0 += (int)rank * kBM;
+            for (int u = 0; u < units; ++u, ++gu) {
+                const int b = gu & 1;
+                if (!bar_wait_cluster(su32(&tfull[b]), (gu >> 1) & 1, abort_flag, a.err, 4u)) {
+                    ok = false;
+                    break;
+                }
+                fence_after();
+                const int pr = u % a.nunits;
+                const bool pair = a.uq2[pr] != kNone, first = u == 0;
+                const float f1 = a.us1[pr], f2 = a.us2[pr];
+                const uint32_t acc = tmem + (uint32_t)(b * 2 * kBN) + lane_off + (uint32_t)(h * 64);
+#pragma unroll
+                for (int c = 0; c < 64; c += 16) {
+                    uint32_t v[16];
+#pragma unroll
+                    for (int half = 0; half < 2; ++half) {
+                        if (half == 1 && !pair) break;
+                        OO_TMEM_LD16(acc + half * kBN + c, v);
+                        tmem_wait_ld();
+                        const float f = half ? f2 : f1;
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const float w = __fmul_rn(__uint_as_float(v[j]), f);  // exact: power-of-two scale
+                            if (first && half == 0) {
+                                Sh[c + j] = w;
+                                Sl[c + j] = 0.0f;
+                            } else {
+                                ff::add(Sh[c + j], Sl[c + j], w, 0.0f, Sh[c + j], Sl[c + j]);
+                            }
+                        }
+                    }
+                }
+                fence_before();
+                __syncwarp();
+                if (lane == 0) {
+                    if (leader)
+                        bar_arrive(su32(&tempty[b]));
+                    else
+                        bar_arrive_remote(map_to_rank(su32(&tempty[b]), 0));
+                }
+                if (u == units - 1) {
+                    const int row = m0 + q * 32 + lane;
+                    const int c0 = n0 + h * 64;
+                    const int e0 = c0 + lane < a.n ? a.eb[c0 + lane] : 0;
+                    const int e1 = c0 + 32 + lane < a.n ? a.eb[c0 + 32 + lane] : 0;
+                    const bool row_ok = row < a.m;
+                    const int sa = row_ok ? a.ea[row] : 0;
+                    double *crow = a.C + (long long)row * a.ldc + c0;
+#pragma unroll
+                    for (int j = 0; j < 64; ++j) {
+                        const int sb = __shfl_sync(0xffffffffu, j < 32 ? e0 : e1, j & 31);
+                        if (row_ok && c0 + j < a.n)
+                            crow[j] = nan_or_scaled(ff::to_double(Sh[j], Sl[j]), sa + sb);
+                    }
+                }
+            }
+        }
+    }
+    // drain on abort (bounded): rank 0 waits for its issued MMAs and for the
+    // copies counted on its barriers; rank 1 for the commits that free its
+    // stages (its copies complete on rank 0's barriers)
+    if (*abort_flag) {
+        if (warp == 1 && lane == 0 && leader && units_mma > 0)
+            bar_drain(su32(&tfull[(units_mma - 1) & 1]), ((units_mma - 1) >> 1) & 1);
+        if (warp == 0 && lane == 0)
+            for (int it = (loaded > kStagesPair ? loaded - kStagesPair : 0); it < loaded; ++it)
+                bar_drain(su32(leader ? &full[it % kStagesPair] : &empty[it % kStagesPair]),
+                          (it / kStagesPair) & 1);
+    }
+    fence_before();
+    __syncthreads();
+    cluster_sync_all();  // neither CTA leaves while the other may still signal it or read its TMEM
+    if (warp == 1) {
+        fence_after();
+        tmem_dealloc_pair(tmem, 512);
+    }
+}
+
 // ------------------------------------------------------------ splitting
 // A (m x k, lda) -> ea and slices As[p] (m x kp each, p < s); one warp per row
 __global__ void eq_split_rows_kernel(const double *A, long long lda, int m, int k, int kp, int beta, int s,
@@ -434,6 +665,36 @@ __global__ void eq_col_scale_kernel(const int *mxo, int *eb, int n) {
 }
 
 size_t smem_eq() { return 1024 + (size_t)kStages * kStageBytes + 256; }
+constexpr size_t kSmemEqPair = 1024 + (size_t)kStagesPair * kStageBytesPair + 256;
+static_assert(kSmemEqPair <= 232448, "pair kernel exceeds the shared memory of a CTA");
+
+// 2-CTA clusters of the pair kernel that fit on the device at once (cached)
+int eq_pair_clusters() {
+    int dev = 0;
+    OO_CUDA_TRY(cudaGetDevice(&dev));
+    static std::atomic<int> max_clusters[64];
+    int ncl = dev < 64 ? max_clusters[dev].load() : 0;
+    if (ncl > 0) return ncl;
+    static std::atomic<uint64_t> attr{0};
+    set_smem_limit_once((const void *)gemm_fp64eq_pair_kernel, kSmemEqPair, attr);
+    int sms = 148;
+    OO_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)(sms / 2 * 2));
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = kSmemEqPair;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    OO_CUDA_TRY(cudaOccupancyMaxActiveClusters(&ncl, (const void *)gemm_fp64eq_pair_kernel, &cfg));
+    OO_REQUIRE(ncl >= 1, OO_ECUDA, "no 2-CTA cluster of the FP64-equivalent kernel fits on this device");
+    if (dev < 64) max_clusters[dev].store(ncl);
+    return ncl;
+}
 
 struct EqLayout {
     size_t err, ea, eb, mxo, as, bs, total;
@@ -490,7 +751,7 @@ void gemm_fp64eq_shape(int k, int *beta, int *levels, int *k_block) {
 }
 
 void launch_gemm_fp64eq(int m, int n, int k, const double *A, long long lda, const double *B, long long ldb,
-                        double *C, long long ldc, void *scratch, cudaStream_t s, int width) {
+                        double *C, long long ldc, void *scratch, cudaStream_t s, int width, bool pair) {
     OO_REQUIRE(m >= 1 && n >= 1 && k >= 1, OO_EINVAL, "m, n, k must be >= 1");
     OO_REQUIRE(lda >= k && ldb >= n && ldc >= n, OO_EINVAL, "leading dimensions too small");
     const EqShape e = eq_used_shape(k);
@@ -559,6 +820,30 @@ void launch_gemm_fp64eq(int m, int n, int k, const double *A, long long lda, con
         ga.uq2[i] = (unsigned char)U[i].q2;
         ga.us1[i] = std::ldexp(1.0f, -e.beta * (U[i].p + U[i].q1 + 2));
         ga.us2[i] = U[i].q2 == kNone ? 0.0f : std::ldexp(1.0f, -e.beta * (U[i].p + U[i].q2 + 2));
+    }
+    if (pair) {
+        EqPairMaps pm;
+        map_bf16(&pm.a, As, (long long)e.slices * m, kp, kBM);
+        map_bf16(&pm.b, Bs, (long long)e.slices * n, kp, kBN);
+        map_bf16(&pm.bh, Bs, (long long)e.slices * n, kp, kBN / 2);
+        ga.m_tiles = (m + 2 * kBM - 1) / (2 * kBM);  // 256-row slabs
+        const long long ptiles = (long long)ga.m_tiles * ga.n_tiles;
+        OO_REQUIRE(ptiles < (1ll << 31), OO_EINVAL, "too many tiles");
+        const int ncl = eq_pair_clusters();
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3((unsigned)(2 * std::min<long long>(ptiles, ncl)));
+        cfg.blockDim = dim3(kThreads);
+        cfg.dynamicSmemBytes = kSmemEqPair;
+        cfg.stream = s;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        OO_CUDA_TRY(cudaLaunchKernelEx(&cfg, gemm_fp64eq_pair_kernel, (const EqPairMaps)pm, (const EqArgs)ga));
+        return;
     }
     static std::atomic<uint64_t> attr{0};
     set_smem_limit_once((const void *)gemm_fp64eq_kernel, smem_eq(), attr);

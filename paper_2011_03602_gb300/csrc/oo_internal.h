@@ -123,9 +123,11 @@ unsigned *gemm_tf32_error_word(void *scratch, int m, int n, int k);
 size_t gemm_fp64eq_scratch_bytes(int m, int n, int k);
 int gemm_fp64eq_products(int k);
 void gemm_fp64eq_shape(int k, int *beta, int *levels, int *k_block);
-// width: tile width (32, 64 or 128) for the products of a level scheme
+// width: tile width (32, 64 or 128) for the products of a level scheme;
+// pair: the pair scheme's products on CTA pairs (256 x 128 tiles,
+// cta_group::2), else on single CTAs (128 x 128); the same bits either way
 void launch_gemm_fp64eq(int m, int n, int k, const double *A, long long lda, const double *B, long long ldb,
-                        double *C, long long ldc, void *scratch, cudaStream_t s, int width);
+                        double *C, long long ldc, void *scratch, cudaStream_t s, int width, bool pair = true);
 unsigned gemm_fp64eq_check_error(void *scratch, cudaStream_t s);
 unsigned *gemm_fp64eq_error_word(void *scratch);
 

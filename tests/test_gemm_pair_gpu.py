@@ -114,3 +114,34 @@ def test_nonfinite_rows_and_columns(oo_mod, ctxs):
     mask[:, 131] = False
     assert np.isfinite(Cp[mask]).all()
     np.testing.assert_array_equal(Cp[mask], Cs[mask])
+
+
+# ----------------------------------------------- FP64-equivalent pattern
+FP64EQ_TOL = 1e-12
+
+
+@pytest.mark.parametrize("m,n,k", [(256, 128, 600), (300, 200, 1000), (513, 257, 1500), (77, 640, 2048),
+                                   (1024, 1024, 4096)])
+def test_fp64eq_pair_equals_single_and_oracle(oo_mod, ctxs, m, n, k):
+    """Inner dimensions above 512 take the pair scheme (two-product units on
+    N = 256 MMAs, one-product units on N = 128): CTA pairs and single CTAs
+    give the same bits, within the FP64-equivalent tolerance of the oracle."""
+    pair, single = ctxs
+    A = synth.gemm_matrix(500 + m, m, k)
+    B = synth.gemm_matrix(600 + n, k, n)
+    Cp = oo_mod.oo_gemm_f64(pair, A, B, prec=oo_mod.OO_PREC_FP64EQ)
+    Cs = oo_mod.oo_gemm_f64(single, A, B, prec=oo_mod.OO_PREC_FP64EQ)
+    np.testing.assert_array_equal(Cp, Cs)
+    rows = sorted({0, m // 2, m - 1})
+    ref = oracle.gemm(A[rows], B)
+    assert err_metric(Cp[rows], ref, A[rows], B) <= FP64EQ_TOL
+
+
+def test_fp64eq_full_size_pair_equals_single(oo_mod, ctxs):
+    pair, single = ctxs
+    n = 4096
+    A = synth.gemm_matrix(9, n, n)
+    B = synth.gemm_matrix(10, n, n)
+    Cp = oo_mod.oo_gemm_f64(pair, A, B, prec=oo_mod.OO_PREC_FP64EQ)
+    Cs = oo_mod.oo_gemm_f64(single, A, B, prec=oo_mod.OO_PREC_FP64EQ)
+    np.testing.assert_array_equal(Cp, Cs)
