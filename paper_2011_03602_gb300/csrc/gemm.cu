@@ -5,9 +5,11 @@
 //   A = 2^sA (A1 + A2 + dA),  B = (B1 + B2 + dB) 2^sB,  A1, A2, B1, B2 in BF16
 //   C ~= 2^(sA + sB) ( A1 B1 + [A1 B2 + A2 B1] )
 //
-// sA is a per-row power of two (per-column sB for B) that brings the row's
-// largest entry into [1/2, 1), so the split keeps 16 significant bits of
-// every entry regardless of the input's range.  The three products are
+// sA is a per-row power of two that brings the row's largest entry into
+// [1/2, 1); sB is per column, 1 when the column's largest entry already lies
+// in [2^-20, 2^40) and otherwise chosen like sA (bf16_col_scale), so the
+// split keeps 16 significant bits of every entry regardless of the input's
+// range, and B is split in one pass.  The three products are
 // summed, K step by K step in the order A1 B1, A1 B2, A2 B1, into one FP32
 // accumulator in tensor memory (TMEM); the epilogue widens it to FP64 and
 // applies the power-of-two scales.  Error: about 3 * 2^-16 of sum|a||b| per
@@ -589,6 +591,22 @@ __global__ void __launch_bounds__(kGemmThreads, 1) gemm_split3_pair_kernel(const
     }
 }
 // ---------------------------------------------------------------- splitting
+// Scale exponent of a column of B in the split-BF16 pattern, from its
+// largest biased exponent mx (0: every entry zero; kNonFiniteExp: a NaN or
+// an infinity).  0 when the column's largest magnitude lies in
+// [2^-20, 2^40): BF16 and FP32 hold such a column's splits, products and
+// sums unscaled, and a power-of-two scale would change no rounding in them,
+// only flush a few entries more than 2^106 below the largest; otherwise the
+// power of two that brings the largest entry into [1/2, 1), and 2^20 (the
+// non-finite flag) for a column holding a NaN or an infinity.  Rows of A
+// always take the [1/2, 1) scale.  Unscaled columns let the split read B
+// once (split_cols_strip).
+__device__ __forceinline__ int bf16_col_scale(int mx) {
+    if (mx == 0) return 0;
+    const int u = mx - 1023;  // unbiased exponent of the largest entry
+    if (u >= -20 && u < 40) return 0;
+    return mx - 1023 + 1;
+}
 // per-column maxima of B (k x n): grid.x over column blocks of 32, grid.y over k chunks
 __global__ void col_maxexp_kernel(const double *B, long long ldb, int k, int n, int rows_per, int *e) {
     const int col = blockIdx.x * 32 + threadIdx.x;
@@ -604,6 +622,11 @@ __global__ void col_maxexp_kernel(const double *B, long long ldb, int k, int n, 
 __global__ void exp_to_scale_kernel(int *e, int count) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < count) e[i] = e[i] == 0 ? 0 : e[i] - 1023 + 1;
+}
+// the same for the columns of B in the split-BF16 pattern (bf16_col_scale)
+__global__ void exp_to_bf16_col_scale_kernel(int *e, int count) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) e[i] = bf16_col_scale(e[i]);
 }
 
 // x * 2^-S -> (hi, lo) BF16 pair with hi + lo = x * 2^-S to ~16 bits
@@ -751,16 +774,18 @@ __global__ void split_cols_t_kernel(const double *B, long long ldb, int k, int n
 
 // B (k x n, ldb even, 16-byte aligned) -> column scales eb and B1t, B2t
 // (n x kp, transposed), zero padding in [k, kp).  One CTA per strip of 16
-// columns: pass 1 reads the strip for the columns' largest exponents, pass 2
-// reads it again -- mostly from L2, since the strips of the CTAs in flight
-// (k x 128 bytes each) fit in it -- and writes the splits through a
-// shared-memory transpose.  Same scales and splits as col_maxexp +
-// split_cols_t, with B read from DRAM about once instead of twice.
+// columns, one pass over B: every entry is split unscaled (S = 0) while the
+// columns' largest exponents are gathered; a column whose scale turns out
+// not to be 0 (bf16_col_scale: its largest entry outside [2^-20, 2^40), or
+// a non-finite entry) is split again with its scale, re-reading the strip
+// -- normally no column.  Same scales and splits as col_maxexp +
+// exp_to_bf16_col_scale + split_cols_t, with B read once.
 constexpr int kStripThreads = 512;
 __device__ __forceinline__ void split_cols_strip(const double *B, long long ldb, int k, int n, int kp, int *eb,
                                                  __nv_bfloat16 *B1t, __nv_bfloat16 *B2t, int strip) {
     __shared__ int red[64][17];
     __shared__ int Ssh[16];
+    __shared__ int redo;
     __shared__ __nv_bfloat16 th[16][258], tl[16][258];
     const int c0 = strip * 16;
     const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;  // 8 column pairs x 64 rows
@@ -778,63 +803,69 @@ __device__ __forceinline__ void split_cols_strip(const double *B, long long ldb,
         }
         return v;
     };
-    // pass 1: largest biased exponent of each column
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;  // warp w writes column c0 + w
+    // one pass over the strip with scales S0, S1 for this thread's columns:
+    // 256 k values per step, the next step's four loads issued before this
+    // step's stores; with `track`, the columns' largest exponents gathered
+    auto pass = [&](int S0, int S1, bool track, int &m0, int &m1) {
+        double2 nv[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) nv[q] = load(64 * q + ty);
+        for (int l0 = 0; l0 < kp; l0 += 256) {
+            double2 v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] = nv[q];
+            if (l0 + 256 < kp) {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) nv[q] = load(l0 + 256 + 64 * q + ty);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (track) {
+                    m0 = max(m0, ex(v[q].x));
+                    m1 = max(m1, ex(v[q].y));
+                }
+                split_bf16(v[q].x, S0, th[2 * tx][64 * q + ty], tl[2 * tx][64 * q + ty]);
+                split_bf16(v[q].y, S1, th[2 * tx + 1][64 * q + ty], tl[2 * tx + 1][64 * q + ty]);
+            }
+            __syncthreads();
+            const int c = c0 + w;
+            if (c < n) {
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    const int l = l0 + 64 * h + 2 * lane;
+                    if (l < kp) {
+                        const int q = 64 * h + 2 * lane;
+                        *reinterpret_cast<__nv_bfloat162 *>(B1t + (long long)c * kp + l) =
+                            __halves2bfloat162(th[w][q], th[w][q + 1]);
+                        *reinterpret_cast<__nv_bfloat162 *>(B2t + (long long)c * kp + l) =
+                            __halves2bfloat162(tl[w][q], tl[w][q + 1]);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    };
     int m0 = 0, m1 = 0;
-#pragma unroll 8
-    for (int l = ty; l < k; l += 64) {
-        const double2 v = load(l);
-        m0 = max(m0, ex(v.x));
-        m1 = max(m1, ex(v.y));
-    }
+    pass(0, 0, true, m0, m1);
     red[ty][2 * tx] = m0;
     red[ty][2 * tx + 1] = m1;
+    if (threadIdx.x == 0) redo = 0;
     __syncthreads();
     if (threadIdx.x < 16) {
         int mx = 0;
         for (int y = 0; y < 64; ++y) mx = max(mx, red[y][threadIdx.x]);
-        const int S = mx == 0 ? 0 : mx - 1023 + 1;
+        const int S = bf16_col_scale(mx);
         Ssh[threadIdx.x] = S;
-        if (c0 + (int)threadIdx.x < n) eb[c0 + threadIdx.x] = S;
+        if (c0 + (int)threadIdx.x < n) {
+            eb[c0 + threadIdx.x] = S;
+            if (S != 0) redo = 1;
+        }
     }
     __syncthreads();
-    const int S0 = Ssh[2 * tx], S1 = Ssh[2 * tx + 1];
-    // pass 2: 256 k values per step, last rows first (the most recently
-    // read into L2); the next step's four loads are issued before this
-    // step's stores
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;  // warp w writes column c0 + w
-    const int last = (kp - 1) / 256 * 256;
-    double2 nv[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) nv[q] = load(last + 64 * q + ty);
-    for (int l0 = last; l0 >= 0; l0 -= 256) {
-        double2 v[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) v[q] = nv[q];
-        if (l0 >= 256) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) nv[q] = load(l0 - 256 + 64 * q + ty);
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            split_bf16(v[q].x, S0, th[2 * tx][64 * q + ty], tl[2 * tx][64 * q + ty]);
-            split_bf16(v[q].y, S1, th[2 * tx + 1][64 * q + ty], tl[2 * tx + 1][64 * q + ty]);
-        }
-        __syncthreads();
-        const int c = c0 + w;
-        if (c < n) {
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const int l = l0 + 64 * h + 2 * lane;
-                if (l < kp) {
-                    const int q = 64 * h + 2 * lane;
-                    *reinterpret_cast<__nv_bfloat162 *>(B1t + (long long)c * kp + l) =
-                        __halves2bfloat162(th[w][q], th[w][q + 1]);
-                    *reinterpret_cast<__nv_bfloat162 *>(B2t + (long long)c * kp + l) =
-                        __halves2bfloat162(tl[w][q], tl[w][q + 1]);
-                }
-            }
-        }
-        __syncthreads();
+    if (redo) {  // the strip again, every column with its own scale
+        int u0 = 0, u1 = 0;
+        pass(Ssh[2 * tx], Ssh[2 * tx + 1], false, u0, u1);
     }
 }
 
@@ -1066,7 +1097,7 @@ __global__ void colmax_b_group_kernel(const GroupSplit *gs, const int2 *jobs) {
     __syncthreads();
     if (threadIdx.y == 0 && col < G.n) {
         for (int y = 1; y < (int)blockDim.y; ++y) mx = max(mx, red[y][threadIdx.x]);
-        G.eb[col] = mx == 0 ? 0 : mx - 1023 + 1;
+        G.eb[col] = bf16_col_scale(mx);
     }
 }
 
@@ -1188,7 +1219,7 @@ void launch_gemm_split3(int m, int n, int k, const double *A, long long lda, con
         OO_REQUIRE(grid.y <= 65535, OO_EINVAL, "k too large");
         col_maxexp_kernel<<<grid, block, 0, s>>>(B, ldb, k, n, rows_per, eb);
         OO_CUDA_TRY(cudaGetLastError());
-        exp_to_scale_kernel<<<(n + 255) / 256, 256, 0, s>>>(eb, n);
+        exp_to_bf16_col_scale_kernel<<<(n + 255) / 256, 256, 0, s>>>(eb, n);
         OO_CUDA_TRY(cudaGetLastError());
     }
     if (!(strip_b && rows_v2)) {
