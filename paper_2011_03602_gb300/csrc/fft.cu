@@ -4,10 +4,14 @@
 // GB300 design.  FP64 units run at 1/59 of FP32 on this part, so butterflies
 // use float-float arithmetic (ff.cuh; ~47 significant bits, error ~ log2(N)
 // * 2^-47 relative) and FP64 is used only to generate twiddle tables
-// (sincospi) and to widen results back to double.  Each input transform is
-// scaled by a power of two (exact) so its largest component lies in [1/2, 1)
-// before the split into float pairs, which keeps float-float's exponent range
-// out of the way for any finite double input.
+// (sincospi) and to widen results back to double.  Inputs are scaled by
+// powers of two (exact) before the split into float pairs, which keeps
+// float-float's exponent range out of the way for any finite double input:
+// each column of a CTA (a whole transform, or a four-step first-pass column)
+// by the power that brings its own largest component into [1/2, 1), found
+// from the values the CTA loads anyway; the second pass brings the columns
+// to their transform's scale (fft_device.cuh).  No pass over the input
+// precedes the transform.
 //
 // Structure: a CTA holds 4096 complex float-float values (64 KB) in shared
 // memory and runs Stockham auto-sort stages -- a first stage of radix 2, 4
@@ -45,13 +49,9 @@ struct FftArgs {
     const float4 *tw;     // W_L^t for the pass length L (table of L entries)
     const float4 *tw_hi;  // W_N^{m_hi * 2^kTwSplit}
     const float4 *tw_lo;  // W_N^{m_lo}
-    const int *expo;      // per transform: biased double exponent of its largest component
+    int *expo;            // four-step, per transform: biased exponent of its largest component (zero first)
+    int *colmax;          // four-step, per transform: the N2 first-pass columns' largest exponents
 };
-
-__device__ __forceinline__ int scale_of(const FftArgs &a, int b) {
-    const int e = a.expo[b];
-    return e == 0 ? 0 : e - 1023 + 1;
-}
 
 // The first stage (radix R, no twiddles) on the 8 values a thread has
 // loaded (v[r] at shared-memory position dst[r] = column << log2L | t),
@@ -59,8 +59,8 @@ __device__ __forceinline__ int scale_of(const FftArgs &a, int b) {
 // j R + p.  COLFAST: value r of the thread is t0 + r L/8 of one column, so
 // butterfly g takes r = g + m 8/R; otherwise value r = g R + m is
 // tid + m 512 of column g (L = 512 R).
-template <int R, bool COLFAST>
-__device__ __forceinline__ void first_stage_regs(float4 *sd, const float4 *v, const int *dst, int log2L, bool inv) {
+template <int R, bool COLFAST, class Pos>
+__device__ __forceinline__ void first_stage_regs(float4 *sd, const float4 *v, const Pos &dst, int log2L, bool inv) {
     static_assert(kFftElems / kFftThreads == 8, "eight values per thread");
     constexpr int G = 8 / R;
 #pragma unroll
@@ -69,7 +69,7 @@ __device__ __forceinline__ void first_stage_regs(float4 *sd, const float4 *v, co
 #pragma unroll
         for (int m = 0; m < R; ++m) x[m] = ld_cplx(&v[COLFAST ? g + m * G : g * R + m]);
         const int r0 = COLFAST ? g : g * R;
-        const int col = dst[r0] >> log2L, j = dst[r0] & ((1 << log2L) - 1);
+        const int col = dst(r0) >> log2L, j = dst(r0) & ((1 << log2L) - 1);
         dft_small<R>(x, inv);
         float4 *o = sd + (col << log2L) + j * R;
 #pragma unroll
@@ -98,6 +98,10 @@ __global__ void __launch_bounds__(kFftThreads, 2) fft_pass_kernel(FftArgs a) {
         for (int t = threadIdx.x; t < stage_table_count(log2L); t += kFftThreads) t_s[t] = a.tw[t];
         stw = t_s;
     }
+    // the columns' largest exponents (modes 0, 1), after the staged table
+    int *smax = reinterpret_cast<int *>(fsmem + kFftElems + (twiddles_staged(log2L) ? L : 0));
+    if (MODE != 2)
+        for (int t = threadIdx.x; t < C; t += kFftThreads) smax[t] = 0;
 
     const long long n = a.n;
     const int N1 = 1 << a.log2n1, N2 = 1 << a.log2n2;
@@ -121,8 +125,14 @@ __global__ void __launch_bounds__(kFftThreads, 2) fft_pass_kernel(FftArgs a) {
     const int b0 = first_radix_log2(log2L);
     const bool first_here = MODE == 1 ? log2L >= 3 : (log2L >= 10 && log2L <= 12);
     {
+        // shared-memory position of value r of this thread: column c, element
+        // t at (c << log2L) + t, which row-fastest is q itself
+        auto dst = [&](int r) {
+            const int q = threadIdx.x + r * kFftThreads;
+            if (MODE == 1) return ((q & (C - 1)) << log2L) + (q >> (31 - __clz(C)));
+            return q;
+        };
         double2 raw[kPer];
-        int dst[kPer];
 #pragma unroll
         for (int r = 0; r < kPer; ++r) {
             const int q = threadIdx.x + r * kFftThreads;
@@ -134,7 +144,6 @@ __global__ void __launch_bounds__(kFftThreads, 2) fft_pass_kernel(FftArgs a) {
                 c = q >> log2L;
                 t = q & (L - 1);
             }
-            dst[r] = (c << log2L) + t;
             raw[r] = make_double2(0.0, 0.0);
             if (MODE == 0) {
                 if (c0 + c < a.batch) raw[r] = reinterpret_cast<const double2 *>(a.in_d)[(long long)(c0 + c) * n + t];
@@ -147,14 +156,39 @@ __global__ void __launch_bounds__(kFftThreads, 2) fft_pass_kernel(FftArgs a) {
             }
         }
         float4 v[kPer];
+        if (MODE == 2) {
+            // float-float intermediates: the 16 bytes as they were, brought
+            // from their column's scale to the transform's
+            const int em = a.expo[b];
 #pragma unroll
-        for (int r = 0; r < kPer; ++r) {
-            if (MODE == 2) {  // float-float intermediates: the 16 bytes as they were
-                v[r] = make_float4(__int_as_float(__double2loint(raw[r].x)), __int_as_float(__double2hiint(raw[r].x)),
-                                   __int_as_float(__double2loint(raw[r].y)), __int_as_float(__double2hiint(raw[r].y)));
+            for (int r = 0; r < kPer; ++r) {
+                const float4 f = make_float4(__int_as_float(__double2loint(raw[r].x)),
+                                             __int_as_float(__double2hiint(raw[r].x)),
+                                             __int_as_float(__double2loint(raw[r].y)),
+                                             __int_as_float(__double2hiint(raw[r].y)));
+                const int t = dst(r) & (L - 1);
+                v[r] = scale_down(f, col_shift(a.colmax[(long long)b * N2 + t], em));
+            }
+        } else {
+            __syncthreads();  // smax cleared
+            if (MODE == 1) {  // a thread's values are all of column tid mod C
+                int m = 0;
+#pragma unroll
+                for (int r = 0; r < kPer; ++r) m = max(m, expo_of(raw[r]));
+                colmax_warp(m, min(C, 32), false, smax, (int)threadIdx.x & (C - 1));
             } else {
-                const int tb = MODE == 0 ? c0 + (dst[r] >> log2L) : b;
-                const int S = (MODE == 0 && tb >= a.batch) ? 0 : scale_of(a, tb);
+#pragma unroll
+                for (int r = 0; r < kPer; ++r) colmax_warp(expo_of(raw[r]), min(L, 32), true, smax, dst(r) >> log2L);
+            }
+            __syncthreads();
+            if (MODE == 1 && (int)threadIdx.x < C) {
+                const int m = smax[threadIdx.x];
+                a.colmax[(long long)b * N2 + c0 + threadIdx.x] = m;
+                if (m > 0) atomicMax(a.expo + b, m);
+            }
+#pragma unroll
+            for (int r = 0; r < kPer; ++r) {
+                const int S = scale_from(smax[dst(r) >> log2L]);
                 split_scaled(raw[r].x, S, v[r].x, v[r].y);
                 split_scaled(raw[r].y, S, v[r].z, v[r].w);
             }
@@ -168,7 +202,7 @@ __global__ void __launch_bounds__(kFftThreads, 2) fft_pass_kernel(FftArgs a) {
                 first_stage_regs<8, MODE == 1>(sd, v, dst, log2L, inv);
         } else {
 #pragma unroll
-            for (int r = 0; r < kPer; ++r) sd[dst[r]] = v[r];
+            for (int r = 0; r < kPer; ++r) sd[dst(r)] = v[r];
         }
     }
     __syncthreads();
@@ -200,26 +234,14 @@ __global__ void __launch_bounds__(kFftThreads, 2) fft_pass_kernel(FftArgs a) {
         } else {
             const int tb = MODE == 0 ? c0 + c : b;
             if (MODE == 0 && tb >= a.batch) continue;
-            const int S = scale_of(a, tb) - (inv ? a.log2n : 0);
+            const int e = MODE == 0 ? smax[c] : a.expo[b];  // the transform's (mode 0: the column's) exponent
+            const int S = scale_from(e) - (inv ? a.log2n : 0);
             const double re = widen_scaled(v.rh, v.rl, S), im = widen_scaled(v.ih, v.il, S);
             const long long idx = MODE == 0 ? (long long)tb * n + t
                                             : (long long)b * n + (c0 + c) + (long long)N1 * t;
-            reinterpret_cast<double2 *>(a.out_d)[idx] =
-                a.expo[tb] == kNonFiniteExpo ? nan2() : make_double2(re, im);
+            reinterpret_cast<double2 *>(a.out_d)[idx] = e == kNonFiniteExpo ? nan2() : make_double2(re, im);
         }
     }
-}
-
-// biased exponent of the largest |re|, |im| of every transform (one complex
-// value = one 16-byte load)
-__global__ void fft_maxexp_kernel(const double *in, long long n, int *expo) {
-    const int b = blockIdx.y;
-    const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(in) + (long long)b * n;
-    const long long step = (long long)gridDim.x * blockDim.x;
-    int m = max_exponent(p, (long long)blockIdx.x * blockDim.x + threadIdx.x, n, step);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(expo + b, m);
 }
 
 // table[t] = W_M^{t * stride} = exp(-2 pi i t stride / M), t < count, in FP64, split to float pairs
@@ -257,20 +279,8 @@ __global__ void fft_stage_twiddle_kernel(float4 *table, int log2L) {
     }
 }
 
-__global__ void fft_maxexp_group_kernel(const FftGroupReq *reqs, int *expo) {
-    const int r = blockIdx.y;
-    const long long cnt = 1ll << reqs[r].log2n;
-    const ulonglong2 *p = reinterpret_cast<const ulonglong2 *>(reqs[r].in);
-    const long long step = (long long)gridDim.x * blockDim.x;
-    int m = max_exponent(p, (long long)blockIdx.x * blockDim.x + threadIdx.x, cnt, step);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(expo + r, m);
-}
-
-
 __global__ void __launch_bounds__(kFftThreads, 2)
-    fft_group_kernel(const FftItem *items, int nitems, const FftGroupReq *reqs, const int *tlist, const int *expo) {
+    fft_group_kernel(const FftItem *items, int nitems, const FftGroupReq *reqs, const int *tlist, int *expo) {
     extern __shared__ __align__(16) float4 fsmem[];
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const FftItem item = items[it];
@@ -369,7 +379,10 @@ void fft_plan_destroy(FftPlan *p) {
 
 size_t fft_scratch_bytes(const FftPlan *p, int batch) {
     const size_t n = (size_t)1 << p->log2n;
-    return (p->log2n > 12 ? n * (size_t)batch * sizeof(float4) : 0) + (size_t)batch * sizeof(int) + 256;
+    if (p->log2n <= 12) return 256;  // one pass: nothing beyond the CTAs' shared memory
+    // four-step: the intermediates, each transform's exponent and its
+    // first-pass columns' exponents
+    return n * (size_t)batch * sizeof(float4) + (size_t)batch * sizeof(int) * (1 + ((size_t)1 << p->log2n2)) + 256;
 }
 
 void launch_fft(const FftPlan *p, int batch, int dir, const double *in, double *out, void *scratch,
@@ -383,27 +396,21 @@ void launch_fft(const FftPlan *p, int batch, int dir, const double *in, double *
             OO_CUDA_TRY(cudaMemcpyAsync(out, in, (size_t)batch * 16, cudaMemcpyDeviceToDevice, s));
         return;
     }
-    float4 *mid = reinterpret_cast<float4 *>(scratch);
-    int *expo = reinterpret_cast<int *>(reinterpret_cast<char *>(scratch) +
-                                        (four_step ? (size_t)n * batch * sizeof(float4) : 0));
-    OO_CUDA_TRY(cudaMemsetAsync(expo, 0, (size_t)batch * sizeof(int), s));
-    {
-        // enough blocks to stream the input at full bandwidth: ~16 complex
-        // values (four 4-deep rounds of 16-byte loads) per thread
-        const int bx = (int)std::max<long long>(1, std::min<long long>(2048 / std::max(1, batch) + 1,
-                                                                         (n + 4095) / 4096));
-        OO_REQUIRE(batch <= 65535, OO_EINVAL, "batch above 65535");
-        fft_maxexp_kernel<<<dim3(bx, batch), 256, 0, s>>>(in, n, expo);
-        OO_CUDA_TRY(cudaGetLastError());
-    }
     FftArgs a{};
+    if (four_step) {
+        float4 *mid = reinterpret_cast<float4 *>(scratch);
+        a.expo = reinterpret_cast<int *>(reinterpret_cast<char *>(scratch) + (size_t)n * batch * sizeof(float4));
+        a.colmax = a.expo + batch;
+        a.out_ff = mid;
+        a.in_ff = mid;
+        OO_CUDA_TRY(cudaMemsetAsync(a.expo, 0, (size_t)batch * sizeof(int), s));
+    }
     a.log2n = p->log2n;
     a.log2n1 = p->log2n1;
     a.log2n2 = p->log2n2;
     a.n = n;
     a.batch = batch;
     a.inverse = dir > 0 ? 1 : 0;
-    a.expo = expo;
     static std::atomic<uint64_t> attr_done[3];
     auto smem_for = [&](int log2L) { return fft_smem_bytes(log2L); };
     auto prep = [&](int mode, const void *fn, size_t smem) {
@@ -427,7 +434,6 @@ void launch_fft(const FftPlan *p, int batch, int dir, const double *in, double *
     a.tw_lo = p->tw_lo;
     {
         a.in_d = in;
-        a.out_ff = mid;
         a.tw = p->tw_n1;
         const int C = kFftElems / N1;
         const long long grid = (long long)batch * (N2 / C);
@@ -437,7 +443,6 @@ void launch_fft(const FftPlan *p, int batch, int dir, const double *in, double *
         OO_CUDA_TRY(cudaGetLastError());
     }
     {
-        a.in_ff = mid;
         a.out_d = out;
         a.tw = p->tw_n2;
         const int R = kFftElems / N2;
@@ -460,7 +465,7 @@ struct FftGroup {
     // SM), [2] row passes (after every column pass); items stored in that order
     int n_items[3] = {0, 0, 0}, grid[3] = {1, 1, 1};
     size_t smem[3] = {0, 0, 0};
-    int nreq = 0, maxexp_x = 1;
+    int nreq = 0;
     double elems = 0;
 };
 
@@ -469,16 +474,16 @@ FftGroup *fft_group_create(const std::vector<FftDesc> &v, const std::vector<cons
     OO_REQUIRE(v.size() <= 65535, OO_EINVAL, "at most 65535 transforms in a group");
     auto up = [](size_t x, size_t a) { return (x + a - 1) / a * a; };
     size_t at = 0;
-    std::vector<size_t> off_mid(v.size(), 0);
-    long long maxn = 1;
+    std::vector<size_t> off_mid(v.size(), 0), off_colmax(v.size(), 0);
     for (size_t i = 0; i < v.size(); ++i) {
         OO_REQUIRE(v[i].dir == -1 || v[i].dir == 1, OO_EINVAL, "dir must be -1 or +1");
         OO_REQUIRE((((uintptr_t)v[i].in) & 15u) == 0 && (((uintptr_t)v[i].out) & 15u) == 0, OO_EINVAL,
                    "FFT buffers must be 16-byte aligned");
-        maxn = std::max(maxn, 1ll << plans[i]->log2n);
         if (plans[i]->log2n > 12) {
             off_mid[i] = at;
             at += up(((size_t)1 << plans[i]->log2n) * sizeof(float4), 256);
+            off_colmax[i] = at;  // the first pass's column exponents
+            at += up(((size_t)1 << plans[i]->log2n2) * sizeof(int), 256);
         }
     }
     // items: whole transforms grouped by (length, direction); then the passes
@@ -529,6 +534,7 @@ FftGroup *fft_group_create(const std::vector<FftDesc> &v, const std::vector<cons
             reqs[i] = FftGroupReq{v[i].in, v[i].out,
                                   p->log2n > 12 ? reinterpret_cast<float4 *>(base + off_mid[i]) : nullptr,
                                   p->tw_single, p->tw_n1, p->tw_n2, p->tw_hi, p->tw_lo,
+                                  p->log2n > 12 ? reinterpret_cast<int *>(base + off_colmax[i]) : nullptr,
                                   p->log2n, p->log2n1, p->log2n2, v[i].dir > 0 ? 1 : 0};
             elems += (double)(1ll << p->log2n);
         }
@@ -555,7 +561,6 @@ FftGroup *fft_group_create(const std::vector<FftDesc> &v, const std::vector<cons
         g->d_tlist = reinterpret_cast<int *>(base + off_tlist);
         g->d_expo = reinterpret_cast<int *>(base + off_expo);
         g->nreq = (int)v.size();
-        g->maxexp_x = (int)std::max<long long>(1, std::min<long long>(16, (maxn + 4095) / 4096));
         g->elems = elems;
     } catch (...) {
         if (g->arena) cudaFree(g->arena);
@@ -566,9 +571,7 @@ FftGroup *fft_group_create(const std::vector<FftDesc> &v, const std::vector<cons
 }
 
 void fft_group_launch(FftGroup *g, cudaStream_t s) {
-    OO_CUDA_TRY(cudaMemsetAsync(g->d_expo, 0, (size_t)g->nreq * 4, s));
-    fft_maxexp_group_kernel<<<dim3(g->maxexp_x, g->nreq), 256, 0, s>>>(g->d_reqs, g->d_expo);
-    OO_CUDA_TRY(cudaGetLastError());
+    OO_CUDA_TRY(cudaMemsetAsync(g->d_expo, 0, (size_t)g->nreq * 4, s));  // raised by the column passes
     static std::atomic<uint64_t> attr{0};
     set_smem_limit_once((const void *)fft_group_kernel, kFftSmemMax, attr);
     int first = 0;

@@ -158,12 +158,17 @@ __host__ __device__ __forceinline__ int stage_table_count(int log2L) {
 // stores overlap the other's butterflies.  Same entries, same arithmetic: the
 // results do not depend on where the table is read from.
 __host__ __device__ __forceinline__ bool twiddles_staged(int log2L) { return log2L < 12; }
-// dynamic shared memory of a CTA running a pass of length 2^log2L
-__host__ __device__ __forceinline__ size_t fft_smem_bytes(int log2L) {
-    return (size_t)(kFftElems + (twiddles_staged(log2L) ? (1 << log2L) : 0)) * 16;
+// Shared memory of a CTA running a pass of length 2^log2L: the data, the
+// staged table (if any), then one int per column of the CTA (its largest
+// input exponent), 16-byte aligned.
+__host__ __device__ __forceinline__ size_t fft_colmax_bytes(int log2L) {
+    return ((size_t)(kFftElems >> log2L) * 4 + 15) / 16 * 16;
 }
-// the largest of those (L = 2048: 96 KB)
-constexpr size_t kFftSmemMax = (size_t)(kFftElems + 2048) * 16;
+__host__ __device__ __forceinline__ size_t fft_smem_bytes(int log2L) {
+    return (size_t)(kFftElems + (twiddles_staged(log2L) ? (1 << log2L) : 0)) * 16 + fft_colmax_bytes(log2L);
+}
+// the largest of those (L = 2048: 96 KB + 16 bytes)
+constexpr size_t kFftSmemMax = (size_t)(kFftElems + 2048) * 16 + 16;
 
 // 1 / sqrt(2) as a float pair (hi, lo)
 constexpr double kInvSqrt2 = 0.70710678118654752440084436210485;
@@ -324,6 +329,51 @@ __device__ __forceinline__ int max_exponent(const ulonglong2 *p, long long x0, l
     return m;
 }
 
+// Per-column scales.  Every column of a CTA -- a whole transform, or one
+// column of a four-step transform's first pass -- is scaled by the power of
+// two that brings its own largest component into [1/2, 1); the exponents are
+// found in shared memory from the values the CTA has loaded anyway, so no
+// pass over the input precedes the transform.  A first pass records each
+// column's largest exponent and raises the transform's (atomicMax); the
+// second pass brings every column's float-float values to the transform's
+// scale, an exact multiplication by a power of two (values more than 2^126
+// below the transform's largest component become zero).  Where nothing
+// over- or underflows, the per-column scale changes no rounding: the bits
+// are those of one scale for the whole transform.
+
+// largest biased exponent of a complex value's parts (0x7ff: NaN or infinity)
+__device__ __forceinline__ int expo_of(double2 v) {
+    const int a = (int)(((unsigned long long)__double_as_longlong(v.x) >> 52) & 0x7ffu);
+    const int b = (int)(((unsigned long long)__double_as_longlong(v.y) >> 52) & 0x7ffu);
+    return max(a, b);
+}
+// Combine a warp's exponents m over lanes that hold the same column (lanes
+// equal modulo `period`, a power of two <= 32, when `low` is false; lanes in
+// the same aligned group of `period` when `low` is true) and raise smax[col]
+// once per column from the lowest such lane.
+__device__ __forceinline__ void colmax_warp(int m, int period, bool low, int *smax, int col) {
+    const int lane = threadIdx.x & 31;
+    if (low) {
+        if (period == 32)
+            m = __reduce_max_sync(0xffffffffu, m);
+        else
+            for (int o = period >> 1; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if ((lane & (period - 1)) == 0 && m > 0) atomicMax(smax + col, m);
+    } else {
+        for (int o = 16; o >= period; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane < period && m > 0) atomicMax(smax + col, m);
+    }
+}
+// (h, l) pairs of a lazy float-float complex times 2^d, d <= 0
+__device__ __forceinline__ float4 scale_down(float4 v, int d) {
+    if (d == 0) return v;
+    const float f = d >= -126 ? __uint_as_float((unsigned)(127 + d) << 23) : 0.0f;
+    return make_float4(__fmul_rn(v.x, f), __fmul_rn(v.y, f), __fmul_rn(v.z, f), __fmul_rn(v.w, f));
+}
+// the shift from a first-pass column's scale to its transform's: column
+// largest exponent cm, transform's em (0: all zero)
+__device__ __forceinline__ int col_shift(int cm, int em) { return cm == 0 ? 0 : cm - em; }
+
 // ------------------------------------------------- grouped transforms
 // A CTA's worth of work in a batch of transforms of different lengths:
 // mode 0: `count` whole transforms of length 2^log2L (request ids at
@@ -337,6 +387,7 @@ struct FftGroupReq {
     double *out;
     float4 *mid;
     const float4 *tw, *tw_n1, *tw_n2, *tw_hi, *tw_lo;
+    int *colmax;  // four-step transforms: N2 first-pass column exponents
     int log2n, log2n1, log2n2, inverse;
 };
 
@@ -346,11 +397,14 @@ __device__ __forceinline__ int scale_from(int e) { return e == 0 ? 0 : e - 1023 
 // resident serving loop alike): mode 0, `count` whole transforms of length
 // 2^log2L (request ids at tlist[first ..]); mode 1 / 2, the four-step column /
 // row pass of request `first` starting at column / row c0.  512 threads; sd
-// holds kFftElems values, stw room for the pass's per-stage twiddle table:
-// every table is staged there when stage_all is set (callers whose global
-// loads bypass L1), else the 4096-point one is read in place.
+// holds kFftElems values, stw room for the pass's per-stage twiddle table
+// followed by the columns' exponents: every table is staged there when
+// stage_all is set (callers whose global loads bypass L1), else the
+// 4096-point one is read in place.  Mode 1 raises expo[first] (zero before
+// the request's first pass) and writes the request's column exponents;
+// mode 2 reads both.
 __device__ __forceinline__ void fft_group_item(const FftItem &item, const FftGroupReq *reqs, const int *tlist,
-                                               const int *expo, float4 *sd, float4 *stw, bool stage_all) {
+                                               int *expo, float4 *sd, float4 *stw, bool stage_all) {
     const int log2L = item.log2L, L = 1 << log2L;
     const int C = kFftElems >> log2L;
     const FftGroupReq &R0 = reqs[item.mode == 0 ? tlist[item.first] : item.first];
@@ -360,12 +414,14 @@ __device__ __forceinline__ void fft_group_item(const FftItem &item, const FftGro
     const bool staged = stage_all || twiddles_staged(log2L);
     if (staged)
         for (int t = threadIdx.x; t < stage_table_count(log2L); t += kFftThreads) stw[t] = tw[t];
+    int *smax = reinterpret_cast<int *>(stw + (staged ? L : 0));
+    for (int t = threadIdx.x; t < C; t += kFftThreads) smax[t] = 0;
     const float4 *tws = staged ? stw : tw;
     const int N1 = 1 << R0.log2n1, N2 = 1 << R0.log2n2;
-    // ---- load
-    for (int q = threadIdx.x; q < kFftElems; q += kFftThreads) {
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        int c, t;
+    constexpr int kPer = kFftElems / kFftThreads;
+    // value r of this thread: column c, position t
+    auto coords = [&](int r, int &c, int &t) {
+        const int q = threadIdx.x + r * kFftThreads;
         if (item.mode == 1) {
             c = q & (C - 1);
             t = q >> (31 - __clz(C));
@@ -373,23 +429,62 @@ __device__ __forceinline__ void fft_group_item(const FftItem &item, const FftGro
             c = q >> log2L;
             t = q & (L - 1);
         }
-        if (item.mode == 0) {
-            if (c < item.count) {
-                const int r = tlist[item.first + c];
-                const double2 x = reinterpret_cast<const double2 *>(reqs[r].in)[t];
-                const int S = scale_from(expo[r]);
-                split_scaled(x.x, S, v.x, v.y);
-                split_scaled(x.y, S, v.z, v.w);
-            }
-        } else if (item.mode == 1) {
-            const int S = scale_from(expo[item.first]);
-            const double2 x = reinterpret_cast<const double2 *>(R0.in)[(long long)t * N2 + item.c0 + c];
-            split_scaled(x.x, S, v.x, v.y);
-            split_scaled(x.y, S, v.z, v.w);
-        } else {
-            v = R0.mid[(long long)(item.c0 + c) * N2 + t];
+    };
+    auto bits = [](double2 x) {
+        return make_float4(__int_as_float(__double2loint(x.x)), __int_as_float(__double2hiint(x.x)),
+                           __int_as_float(__double2loint(x.y)), __int_as_float(__double2hiint(x.y)));
+    };
+    __syncthreads();  // smax cleared
+    // ---- load.  Mode 2: the first pass's float-float values, brought from
+    // their column's scale to the transform's.  Modes 0, 1: the doubles'
+    // bits into shared memory while the columns' largest exponents are
+    // gathered, then each split in place at its column's scale.
+    if (item.mode == 2) {
+        const int em = expo[item.first];
+#pragma unroll
+        for (int r = 0; r < kPer; ++r) {
+            int c, t;
+            coords(r, c, t);
+            const float4 v = R0.mid[(long long)(item.c0 + c) * N2 + t];
+            sd[(c << log2L) + t] = scale_down(v, col_shift(R0.colmax[t], em));
         }
-        sd[(c << log2L) + t] = v;
+    } else {
+        int m = 0;
+#pragma unroll
+        for (int r = 0; r < kPer; ++r) {
+            int c, t;
+            coords(r, c, t);
+            double2 x = make_double2(0.0, 0.0);
+            if (item.mode == 0) {
+                if (c < item.count) x = reinterpret_cast<const double2 *>(reqs[tlist[item.first + c]].in)[t];
+                colmax_warp(expo_of(x), min(L, 32), true, smax, c);
+            } else {
+                x = reinterpret_cast<const double2 *>(R0.in)[(long long)t * N2 + item.c0 + c];
+                m = max(m, expo_of(x));  // a thread's values are all of column tid mod C
+            }
+            sd[(c << log2L) + t] = bits(x);
+        }
+        if (item.mode == 1) colmax_warp(m, min(C, 32), false, smax, (int)threadIdx.x & (C - 1));
+        __syncthreads();
+        if (item.mode == 1 && (int)threadIdx.x < C) {
+            const int e = smax[threadIdx.x];
+            R0.colmax[item.c0 + threadIdx.x] = e;
+            if (e > 0) atomicMax(expo + item.first, e);
+        }
+#pragma unroll
+        for (int r = 0; r < kPer; ++r) {
+            int c, t;
+            coords(r, c, t);
+            float4 *p = sd + (c << log2L) + t;
+            const float4 f = *p;
+            const double xr = __hiloint2double(__float_as_int(f.y), __float_as_int(f.x));
+            const double xi = __hiloint2double(__float_as_int(f.w), __float_as_int(f.z));
+            const int S = scale_from(smax[c]);
+            float4 v;
+            split_scaled(xr, S, v.x, v.y);
+            split_scaled(xi, S, v.z, v.w);
+            *p = v;
+        }
     }
     __syncthreads();
     fft_in_smem(sd, tws, log2L, inv);
@@ -413,19 +508,19 @@ __device__ __forceinline__ void fft_group_item(const FftItem &item, const FftGro
         } else if (item.mode == 0) {
             if (c >= item.count) continue;
             const int r = tlist[item.first + c];
-            const int S = scale_from(expo[r]) - (inv ? log2L : 0);
+            const int S = scale_from(smax[c]) - (inv ? log2L : 0);
             double2 y = make_double2(widen_scaled(v.rh, v.rl, S), widen_scaled(v.ih, v.il, S));
             if (log2L == 0)  // length 1: the transform is the identity, exactly
                 y = reinterpret_cast<const double2 *>(reqs[r].in)[0];
-            else if (expo[r] == kNonFiniteExpo)
+            else if (smax[c] == kNonFiniteExpo)
                 y = nan2();
             reinterpret_cast<double2 *>(reqs[r].out)[t] = y;
         } else {
-            const int S = scale_from(expo[item.first]) - (inv ? R0.log2n : 0);
+            const int em = expo[item.first];
+            const int S = scale_from(em) - (inv ? R0.log2n : 0);
             reinterpret_cast<double2 *>(R0.out)[(item.c0 + c) + (long long)N1 * t] =
-                expo[item.first] == kNonFiniteExpo
-                    ? nan2()
-                    : make_double2(widen_scaled(v.rh, v.rl, S), widen_scaled(v.ih, v.il, S));
+                em == kNonFiniteExpo ? nan2()
+                                     : make_double2(widen_scaled(v.rh, v.rl, S), widen_scaled(v.ih, v.il, S));
         }
     }
 }

@@ -38,14 +38,13 @@ enum EntryType {
     kNop = 0,
     kStop = 1,
     kSplit = 2,       // FP64-equivalent GEMM digit split: aux A-row items (16 rows), then B column items (64)
-    kFftMax = 3,      // FFT input maximum exponent: chunks of kFftMaxChunk values
+    // 3: unused (FFT scales come from the passes themselves)
     kFftWhole = 4,    // FFT of length <= 4096: one item
     kFftCols = 5,     // four-step column pass: item i = columns [i C, (i + 1) C)
     kFftRows = 6,     // four-step row pass
     kJacSetup = 7,    // Jacobi setup nests N0, N1: chunks of the padded grid (float4 units)
     kJacStencil = 8   // N2 for iteration aux (p and wrk2 alternate; see the item): chunks of column slabs
 };
-constexpr int kFftMaxChunk = 1 << 16;
 
 // control block in mapped pinned host memory
 struct Ctl {

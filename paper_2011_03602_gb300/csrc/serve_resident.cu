@@ -113,19 +113,6 @@ __device__ __forceinline__ void run_item(const SimtArgs &a, const Entry &E, int 
             int(*ri)[64] = reinterpret_cast<int(*)[64]>(reinterpret_cast<double *>(sm) + 64 * 65);
             eq::split_cols_job(G, (i - E.aux) * 64, t, ri);
         }
-    } else if (E.type == kFftMax) {
-        const FftGroupReq &R = a.fft[E.slot];
-        const long long n = 1ll << R.log2n;
-        const long long x0 = (long long)i * kFftMaxChunk, x1 = min(n, x0 + kFftMaxChunk);
-        int m = max_exponent(reinterpret_cast<const ulonglong2 *>(R.in), x0 + tid, x1, kSimtThreads);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if ((tid & 31) == 0) redi[tid >> 5] = m;
-        __syncthreads();
-        if (tid == 0) {
-            for (int w = 1; w < kSimtThreads / 32; ++w) m = max(m, redi[w]);
-            if (m > 0) atomicMax(a.expo + E.slot, m);
-        }
     } else if (E.type == kFftWhole || E.type == kFftCols || E.type == kFftRows) {
         const FftGroupReq &R = a.fft[E.slot];
         FftItem it{};
@@ -322,7 +309,8 @@ __global__ void __launch_bounds__(kSimtThreads, 1) resident_simt_kernel(const Si
     }
 }
 
-size_t simt_smem_bytes() { return (size_t)2 * kFftElems * sizeof(float4); }  // FFT data + twiddles: 128 KB
+// FFT data + twiddles (128 KB) + the columns' exponents
+size_t simt_smem_bytes() { return (size_t)2 * kFftElems * sizeof(float4) + 16; }
 
 // ------------------------------------------------------------- host side
 using Clock = std::chrono::steady_clock;
@@ -480,7 +468,9 @@ Plan plan_request(Resident &S, const oo_serve_req &r) {
         P.n_simt = 1;
         P.n_tiles = (int)(((r.m + 127) / 128) * ((r.n + 31) / 32));  // upper bound (narrowest tiles)
     } else if (r.kind == OO_BLOCK_FFT) {
-        P.d_bytes = up256((size_t)r.n * 16) + (r.n > 4096 ? up256((size_t)r.n * 16) : 0);
+        // data, and for four-step lengths the intermediates and the first
+        // pass's column exponents (at most 4096 of them)
+        P.d_bytes = up256((size_t)r.n * 16) + (r.n > 4096 ? up256((size_t)r.n * 16) + up256(4096 * 4) : 0);
         P.n_simt = r.n > 4096 ? 3 : 2;
     } else {
         const JacobiDims d{(int)r.m, (int)r.n, (int)r.k, jacobi_pitch((int)r.k)};
@@ -615,6 +605,7 @@ bool stage(Resident &S, RReq &q) {
         const int log2n = fft_plan_log2(p);
         double *x = reinterpret_cast<double *>(dev);
         float4 *mid = r.n > 4096 ? reinterpret_cast<float4 *>(dev + up256((size_t)r.n * 16)) : nullptr;
+        int *colmax = r.n > 4096 ? reinterpret_cast<int *>(dev + 2 * up256((size_t)r.n * 16)) : nullptr;
         FftGroupReq R{};
         const void *tw[5];
         fft_plan_tables(p, &tw[0], &tw[1], &tw[2], &tw[3], &tw[4], &R.log2n, &R.log2n1, &R.log2n2);
@@ -626,17 +617,16 @@ bool stage(Resident &S, RReq &q) {
         R.in = x;
         R.out = x;
         R.mid = mid;
+        R.colmax = colmax;
         R.inverse = r.dir > 0 ? 1 : 0;
         std::memcpy(upa, &R, sizeof(R));
-        std::memset(upa + 512, 0, 4);  // the max-exponent word starts at zero
-        const Entry mx = make_entry(S, pos(), kFftMax, q.slot, (int)((r.n + kFftMaxChunk - 1) / kFftMaxChunk), 0, nullptr);
-        ents.push_back(mx);
+        std::memset(upa + 512, 0, 4);  // the transform's exponent starts at zero (raised by the column pass)
         if (log2n <= 12) {
-            ents.push_back(make_entry(S, pos(), kFftWhole, q.slot, 1, log2n, &ents[0]));
+            ents.push_back(make_entry(S, pos(), kFftWhole, q.slot, 1, log2n, nullptr));
         } else {
             const int N1 = 1 << R.log2n1, N2 = 1 << R.log2n2;
-            ents.push_back(make_entry(S, pos(), kFftCols, q.slot, N2 / (kFftElems / N1), R.log2n1, &ents[0]));
-            ents.push_back(make_entry(S, pos(), kFftRows, q.slot, N1 / (kFftElems / N2), R.log2n2, &ents[1]));
+            ents.push_back(make_entry(S, pos(), kFftCols, q.slot, N2 / (kFftElems / N1), R.log2n1, nullptr));
+            ents.push_back(make_entry(S, pos(), kFftRows, q.slot, N1 / (kFftElems / N2), R.log2n2, &ents[0]));
         }
         OO_CUDA_TRY(cudaMemcpyAsync(S.fft_desc + q.slot, upa, sizeof(R), cudaMemcpyHostToDevice, s));
         OO_CUDA_TRY(cudaMemcpyAsync(S.expo + q.slot, upa + 512, 4, cudaMemcpyHostToDevice, s));
