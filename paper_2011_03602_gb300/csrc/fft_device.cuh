@@ -430,15 +430,11 @@ __device__ __forceinline__ void fft_group_item(const FftItem &item, const FftGro
             t = q & (L - 1);
         }
     };
-    auto bits = [](double2 x) {
-        return make_float4(__int_as_float(__double2loint(x.x)), __int_as_float(__double2hiint(x.x)),
-                           __int_as_float(__double2loint(x.y)), __int_as_float(__double2hiint(x.y)));
-    };
     __syncthreads();  // smax cleared
     // ---- load.  Mode 2: the first pass's float-float values, brought from
-    // their column's scale to the transform's.  Modes 0, 1: the doubles'
-    // bits into shared memory while the columns' largest exponents are
-    // gathered, then each split in place at its column's scale.
+    // their column's scale to the transform's.  Modes 0, 1: every load
+    // issued first, the columns' largest exponents gathered, then each value
+    // split at its column's scale straight into shared memory.
     if (item.mode == 2) {
         const int em = expo[item.first];
 #pragma unroll
@@ -449,22 +445,28 @@ __device__ __forceinline__ void fft_group_item(const FftItem &item, const FftGro
             sd[(c << log2L) + t] = scale_down(v, col_shift(R0.colmax[t], em));
         }
     } else {
-        int m = 0;
+        double2 raw[kPer];
 #pragma unroll
         for (int r = 0; r < kPer; ++r) {
             int c, t;
             coords(r, c, t);
-            double2 x = make_double2(0.0, 0.0);
+            raw[r] = make_double2(0.0, 0.0);
             if (item.mode == 0) {
-                if (c < item.count) x = reinterpret_cast<const double2 *>(reqs[tlist[item.first + c]].in)[t];
-                colmax_warp(expo_of(x), min(L, 32), true, smax, c);
+                if (c < item.count) raw[r] = reinterpret_cast<const double2 *>(reqs[tlist[item.first + c]].in)[t];
             } else {
-                x = reinterpret_cast<const double2 *>(R0.in)[(long long)t * N2 + item.c0 + c];
-                m = max(m, expo_of(x));  // a thread's values are all of column tid mod C
+                raw[r] = reinterpret_cast<const double2 *>(R0.in)[(long long)t * N2 + item.c0 + c];
             }
-            sd[(c << log2L) + t] = bits(x);
         }
-        if (item.mode == 1) colmax_warp(m, min(C, 32), false, smax, (int)threadIdx.x & (C - 1));
+        if (item.mode == 1) {  // a thread's values are all of column tid mod C
+            int m = 0;
+#pragma unroll
+            for (int r = 0; r < kPer; ++r) m = max(m, expo_of(raw[r]));
+            colmax_warp(m, min(C, 32), false, smax, (int)threadIdx.x & (C - 1));
+        } else {
+#pragma unroll
+            for (int r = 0; r < kPer; ++r)
+                colmax_warp(expo_of(raw[r]), min(L, 32), true, smax, ((int)threadIdx.x + r * kFftThreads) >> log2L);
+        }
         __syncthreads();
         if (item.mode == 1 && (int)threadIdx.x < C) {
             const int e = smax[threadIdx.x];
@@ -475,15 +477,11 @@ __device__ __forceinline__ void fft_group_item(const FftItem &item, const FftGro
         for (int r = 0; r < kPer; ++r) {
             int c, t;
             coords(r, c, t);
-            float4 *p = sd + (c << log2L) + t;
-            const float4 f = *p;
-            const double xr = __hiloint2double(__float_as_int(f.y), __float_as_int(f.x));
-            const double xi = __hiloint2double(__float_as_int(f.w), __float_as_int(f.z));
             const int S = scale_from(smax[c]);
             float4 v;
-            split_scaled(xr, S, v.x, v.y);
-            split_scaled(xi, S, v.z, v.w);
-            *p = v;
+            split_scaled(raw[r].x, S, v.x, v.y);
+            split_scaled(raw[r].y, S, v.z, v.w);
+            sd[(c << log2L) + t] = v;
         }
     }
     __syncthreads();
