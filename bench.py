@@ -294,6 +294,42 @@ def stencil_traffic():
     return nbytes if have == want else None
 
 
+def fft_sources_hash():
+    """Hash of what the FFT pass kernels are built from: ff.cuh,
+    fft_device.cuh and fft.cu."""
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2011_03602_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in ("ff.cuh", "fft_device.cuh", "fft.cu"):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def fft_issue_roofline(ms, sms):
+    """The 2^22 FFT against its bound, instruction issue: the warp
+    instructions of one transform (both passes, from the committed ncu
+    summary, or None when the FFT sources have changed since that capture)
+    per second of the live time, against SMs x 4 schedulers x one warp
+    instruction per clock at the 2070 MHz maximum SM clock."""
+    import re
+    path = os.path.join(ROOT, "profiles", "fft_c128_n2e22.md")
+    try:
+        text = open(path).read()
+        inst = int(re.search(r"warp_instructions_per_transform: (\d+)", text).group(1))
+        want = re.search(r"sources_sha256_16: ([0-9a-f]+)", text).group(1)
+    except (OSError, AttributeError, ValueError):
+        return None
+    if want != fft_sources_hash():
+        return None
+    achieved = inst / (ms * 1e-3)
+    peak = sms * 4 * 2.07e9
+    return {"bound": "issue", "unit": "warp instructions/s", "achieved": round(achieved / 1e9, 1) * 1e9,
+            "peak": peak, "frac": round(achieved / peak, 4), "warp_instructions_per_transform": inst,
+            "instructions_from": "profiles/fft_c128_n2e22.md (ncu, same sources)",
+            "peak_note": "SMs x 4 schedulers x 1 warp instruction per clock x 2070 MHz"}
+
+
 def load_bf16_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -392,7 +428,12 @@ def bench_blocks(oo, ctx, torch, with_errors=True):
     e1.synchronize()
     ms = e0.elapsed_time(e1) / reps
     f = {"n": N, "ms": round(ms, 4), "solves_per_s": round(1e3 / ms, 1),
-         "GBps_two_pass_traffic": round(4 * 16 * N / (ms * 1e-3) / 1e9, 1), "precision": "float-float"}
+         "GBps_two_pass_traffic": round(4 * 16 * N / (ms * 1e-3) / 1e9, 1), "precision": "float-float",
+         # 5 N log2 N, the usual FFT operation count, against the FP64 rate
+         # the float-float arithmetic stands in for (1.25 TFLOP/s nominal)
+         "fp64_equiv_tflops": round(5.0 * N * logn / (ms * 1e-3) / 1e12, 3),
+         "fp64_nominal_tflops": 1.25,
+         "roofline": fft_issue_roofline(ms, torch.cuda.get_device_properties(0).multi_processor_count)}
     if with_errors:
         import oracle
         yh = y.cpu().numpy().view(np.complex128)
@@ -1123,7 +1164,7 @@ def measure_serve(args):
         if mode == "resident":
             # the request loop resident on the device: persistent workers,
             # no kernel launch per request
-            oo.oo_serve_start_resident(ctx, args.serve_budget_gb << 30, args.serve_queue)
+            oo.oo_serve_start_resident(ctx, args.serve_budget_gb << 30, args.serve_queue, args.serve_tensor_ctas)
         else:
             # the host scheduler over slot streams
             oo.oo_serve_start(ctx, slots=args.serve_slots, hbm_budget_bytes=args.serve_budget_gb << 30,
@@ -1297,6 +1338,7 @@ def measure_serve(args):
            "config": {"workload": "serve_mix_50gemm64-2048_30fft2e10-2e20_20jacobi65-129_it100",
                       "gemm_precision": args.serve_prec,
                       "slots": args.serve_slots, "device_budget_gb": args.serve_budget_gb,
+                      "resident_tensor_ctas": args.serve_tensor_ctas or "library default (a quarter of the SMs)",
                       "queue_cap": args.serve_queue, "window_s": window,
                       "front_ends": {"c": "frontends/c/oo_loadgen.c: C ABI calls from its own thread in this process, "
                                           "its own output buffers",
@@ -1347,6 +1389,8 @@ def main():
                          "host (scheduler thread over slot streams)")
     ap.add_argument("--serve-window", type=float, default=0.5, help="seconds of arrivals per rate")
     ap.add_argument("--serve-slots", type=int, default=8)
+    ap.add_argument("--serve-tensor-ctas", type=int, default=0,
+                    help="resident loop: SMs for the tensor-core worker (0: the library's default, a quarter)")
     ap.add_argument("--serve-budget-gb", type=int, default=16)
     ap.add_argument("--serve-queue", type=int, default=2048)
     ap.add_argument("--batch-gemms", type=int, default=4096)
