@@ -771,7 +771,7 @@ def run_block(args):
 
 
 def run_blocks_sweep(args):
-    """Function blocks over the survey's size ranges (device-resident
+    """Function blocks over the workload's size ranges (device-resident
     inputs, CUDA events on the context's stream, splits included): the GEMM
     at n = 256, 1024, 4096 in every precision pattern (tensor TFLOP/s and
     error vs the oracle on sampled rows), and the FFT at N = 2^10..2^22 with
@@ -837,7 +837,7 @@ def run_blocks_sweep(args):
                     "rel_l2_err_vs_oracle": float(np.linalg.norm(y0 - ref) / np.linalg.norm(ref))})
         del x, y
     oo.oo_destroy(ctx)
-    print(json.dumps({"metric": "function blocks over the survey's size ranges", "data": "synthetic",
+    print(json.dumps({"metric": "function blocks over the workload's size ranges", "data": "synthetic",
                       "peaks": {"hbm_gbs": hbm, "hbm_source": hsrc, "bf16_tflops": peak, "bf16_source": psrc,
                                 "tf32_tflops_note": "measured BF16 peak x 1.1 / 2.25"},
                       "gemm": gemm, "fft": fft}))
@@ -1338,7 +1338,7 @@ def measure_serve(args):
            "config": {"workload": "serve_mix_50gemm64-2048_30fft2e10-2e20_20jacobi65-129_it100",
                       "gemm_precision": args.serve_prec,
                       "slots": args.serve_slots, "device_budget_gb": args.serve_budget_gb,
-                      "resident_tensor_ctas": args.serve_tensor_ctas or "library default (a quarter of the SMs)",
+                      "resident_tensor_ctas": args.serve_tensor_ctas or "library default (an eighth of the SMs)",
                       "queue_cap": args.serve_queue, "window_s": window,
                       "front_ends": {"c": "frontends/c/oo_loadgen.c: C ABI calls from its own thread in this process, "
                                           "its own output buffers",
@@ -1390,7 +1390,7 @@ def main():
     ap.add_argument("--serve-window", type=float, default=0.5, help="seconds of arrivals per rate")
     ap.add_argument("--serve-slots", type=int, default=8)
     ap.add_argument("--serve-tensor-ctas", type=int, default=0,
-                    help="resident loop: SMs for the tensor-core worker (0: the library's default, a quarter)")
+                    help="resident loop: SMs for the tensor-core worker (0: the library's default, an eighth)")
     ap.add_argument("--serve-budget-gb", type=int, default=16)
     ap.add_argument("--serve-queue", type=int, default=2048)
     ap.add_argument("--batch-gemms", type=int, default=4096)

@@ -594,7 +594,7 @@ oo_status oo_serve_stop(oo_ctx *ctx);
 /* The same service (oo_submit, oo_wait, oo_serve_stats, oo_serve_stop) with
  * the request loop resident on the device: two persistent worker kernels are
  * launched here, once, and take their work from rings in device memory --
- * one of `tensor_ctas` CTAs (0: a quarter of the SMs) runs the tensor-core tiles of
+ * one of `tensor_ctas` CTAs (0: an eighth of the SMs) runs the tensor-core tiles of
  * FP64-equivalent GEMMs, the other (the remaining SMs, 512 threads each) the
  * digit splits, FFT passes and Jacobi sweeps.  A scheduler thread admits the
  * oldest waiting requests whose device footprint fits the free part of the

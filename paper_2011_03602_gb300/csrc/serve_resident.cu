@@ -1103,10 +1103,12 @@ extern "C" oo_status oo_serve_start_resident(oo_ctx *ctx, uint64_t hbm_budget_by
         OO_REQUIRE(hbm_budget_bytes >= (64u << 20), OO_EINVAL, "device budget below 64 MiB");
         OO_CUDA_TRY(cudaSetDevice(c.device));
         const int sms = c.num_sms;
-        // default split: a quarter of the SMs for the tensor tiles (served
-        // mix of 50 % GEMM, 30 % FFT, 20 % Jacobi at saturation: 914 solves/s
-        // at 38 of 152 SMs, 857 at 57, 723 at 76)
-        const int tc = tensor_ctas > 0 ? tensor_ctas : sms / 4;
+        // default split: an eighth of the SMs for the tensor tiles (served
+        // mix of 50 % GEMM, 30 % FFT, 20 % Jacobi at saturation, 10 000 and
+        // 20 000 req/s offered: 1026-1081 solves/s at 19 of 152 SMs,
+        // 1012-1072 at 14, 1010-1062 at 10, 919-972 at 28, 925-973 at 38,
+        // 857 at 57, 723 at 76; the Jacobi sweeps on the SIMT worker bound it)
+        const int tc = tensor_ctas > 0 ? tensor_ctas : std::max(1, sms / 8);
         OO_REQUIRE(tc >= 1 && tc < sms && tc <= kMaxCtas && sms - tc <= kMaxCtas, OO_EINVAL,
                    "tensor_ctas must leave SMs for the SIMT worker");
         for (int e = 0; e <= 22; ++e) c.fft_plan(1ll << e);  // twiddle tables up front, before the workers
