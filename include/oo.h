@@ -389,7 +389,8 @@ oo_status oo_lookup_block(const char *callee, int lang, int *block_id);
  * is NaN (as a compensated FP64 dot product gives it); the other entries
  * are unaffected.  prec selects the precision pattern:
  *   OO_PREC_SPLIT3_BF16  A and B are scaled per row / column by powers of
- *                        two and split into BF16 hi + lo; C = A1 B1 +
+ *                        two (a column of B whose largest entry lies in
+ *                        [2^-20, 2^40) by 1) and split into BF16 hi + lo; C = A1 B1 +
  *                        (A1 B2 + A2 B1) on the tensor cores (FP32
  *                        accumulators in tensor memory), the two partial
  *                        products summed in FP64.  Error about 5e-5 of
@@ -478,9 +479,10 @@ oo_status oo_set_gemm_tiles(oo_ctx *ctx, const int *widths);
  * 0 <= k <= 24, interleaved (re, im) doubles.  dir -1: forward,
  * X_k = sum_j x_j exp(-2 pi i jk/n); dir +1: inverse with exp(+...) and 1/n.
  * Butterflies run in float-float arithmetic (relative L2 error ~1e-14 for
- * normal inputs); each transform is scaled by a power of two internally, so
- * any finite input is accepted (components more than ~2^126 below the
- * transform's largest one are flushed).  A transform of length n >= 2 with
+ * normal inputs); inputs are scaled internally by powers of two (one per
+ * transform, or per column of a long transform's first pass), so any finite
+ * input is accepted (components more than ~2^126 below the transform's
+ * largest one are flushed).  A transform of length n >= 2 with
  * a NaN or an infinity among its inputs gives NaN in every output component
  * (as the FP64 definition does); n = 1 returns its input unchanged.
  * oo_fft_c128: host buffers, synchronous; in may equal out.               */
