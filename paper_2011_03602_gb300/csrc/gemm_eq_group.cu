@@ -751,7 +751,7 @@ struct EqGroup {
     eq::GSplit *d_split = nullptr;
     int4 *d_jobs = nullptr;
     unsigned *d_err = nullptr;
-    int ntiles = 0, njobs = 0, grid = 1;
+    int ntiles = 0, njobs = 0, nrow_jobs = 0, grid = 1;
     double flops = 0;
 };
 
@@ -796,7 +796,7 @@ EqGroup *eq_group_create(const std::vector<GemmDesc> &v, int num_sms, const int 
         at += up((size_t)v[i].n * 4, 16);
     }
     at = up(at, 256);
-    std::vector<int4> tiles, jobs;
+    std::vector<int4> tiles, jobs, col_jobs;  // row jobs first, then column jobs
     std::vector<double> cost;
     double flops = 0;
     for (size_t i = 0; i < np; ++i) {
@@ -810,8 +810,10 @@ EqGroup *eq_group_create(const std::vector<GemmDesc> &v, int num_sms, const int 
                 cost.push_back(tile_cost(sh[i], kp[i] / kBK, w));
             }
         for (int r0 = 0; r0 < d.m; r0 += 8) jobs.push_back(make_int4(0, (int)i, r0, 0));
-        for (int c0 = 0; c0 < d.n; c0 += 64) jobs.push_back(make_int4(1, (int)i, c0, 0));
+        for (int c0 = 0; c0 < d.n; c0 += 64) col_jobs.push_back(make_int4(1, (int)i, c0, 0));
     }
+    const int nrow_jobs = (int)jobs.size();
+    jobs.insert(jobs.end(), col_jobs.begin(), col_jobs.end());
     OO_REQUIRE(tiles.size() < (1u << 31) && jobs.size() < (1u << 31), OO_EINVAL, "too many tiles");
     std::vector<size_t> order(tiles.size());
     for (size_t t = 0; t < order.size(); ++t) order[t] = t;
@@ -880,6 +882,7 @@ EqGroup *eq_group_create(const std::vector<GemmDesc> &v, int num_sms, const int 
         g->args = make_args(g->d_err);
         g->ntiles = (int)sorted.size();
         g->njobs = (int)jobs.size();
+        g->nrow_jobs = nrow_jobs;
         g->grid = std::max(1, std::min(g->ntiles, num_sms));
         g->flops = flops;
     } catch (...) {
@@ -891,7 +894,7 @@ EqGroup *eq_group_create(const std::vector<GemmDesc> &v, int num_sms, const int 
 }
 
 void eq_group_launch(EqGroup *g, cudaStream_t s) {
-    launch_eq_group_split(g->d_split, g->d_jobs, g->njobs, s);
+    launch_eq_group_split(g->d_split, g->d_jobs, g->nrow_jobs, g->njobs - g->nrow_jobs, s);
     static std::atomic<uint64_t> attr{0};
     set_smem_limit_once((const void *)gemm_eq_group_kernel, smem_bytes(), attr);
     gemm_eq_group_kernel<<<g->grid, kThreads, smem_bytes(), s>>>(g->maps, g->args, g->d_probs, g->d_tiles,

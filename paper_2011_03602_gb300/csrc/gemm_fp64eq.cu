@@ -718,25 +718,33 @@ EqLayout eq_layout(int m, int n, int k) {
 
 // The grouped products' digit split (their tensor-core kernel is in
 // gemm_eq_group.cu, which reads only through L2 for the device-resident
-// loop's sake; the split's second pass over a row wants L1): job (0,
-// problem, first row), eight rows of A; job (1, problem, first column), 64
-// columns of B (eq_digits.cuh).
+// loop's sake; the split's second pass over a row wants L1): jobs (0,
+// problem, first row), eight rows of A each, in one kernel that uses no
+// shared memory -- so more of its blocks fit on an SM and L1 keeps the rows
+// for their second pass -- then jobs (1, problem, first column), 64 columns
+// of B each, through shared-memory tiles (eq_digits.cuh).
 namespace {
-__global__ void __launch_bounds__(256) eq_group_split_kernel(const eq::GSplit *gs, const int4 *jobs) {
+__global__ void __launch_bounds__(256) eq_group_split_rows_kernel(const eq::GSplit *gs, const int4 *jobs) {
+    const int4 jb = jobs[blockIdx.x];
+    eq::split_rows_job(gs[jb.y], jb.z);
+}
+__global__ void __launch_bounds__(256) eq_group_split_cols_kernel(const eq::GSplit *gs, const int4 *jobs) {
     __shared__ double t[64][65];
     __shared__ int red[4][64];
     const int4 jb = jobs[blockIdx.x];
-    if (jb.x == 0)
-        eq::split_rows_job(gs[jb.y], jb.z);
-    else
-        eq::split_cols_job(gs[jb.y], jb.z, t, red);
+    eq::split_cols_job(gs[jb.y], jb.z, t, red);
 }
 }  // namespace
 
-void launch_eq_group_split(const eq::GSplit *gs, const int4 *jobs, int njobs, cudaStream_t s) {
-    if (njobs <= 0) return;
-    eq_group_split_kernel<<<njobs, 256, 0, s>>>(gs, jobs);
-    OO_CUDA_TRY(cudaGetLastError());
+void launch_eq_group_split(const eq::GSplit *gs, const int4 *jobs, int nrow_jobs, int ncol_jobs, cudaStream_t s) {
+    if (nrow_jobs > 0) {
+        eq_group_split_rows_kernel<<<nrow_jobs, 256, 0, s>>>(gs, jobs);
+        OO_CUDA_TRY(cudaGetLastError());
+    }
+    if (ncol_jobs > 0) {
+        eq_group_split_cols_kernel<<<ncol_jobs, 256, 0, s>>>(gs, jobs + nrow_jobs);
+        OO_CUDA_TRY(cudaGetLastError());
+    }
 }
 
 size_t gemm_fp64eq_scratch_bytes(int m, int n, int k) { return eq_layout(m, n, k).total; }

@@ -184,7 +184,7 @@ struct GSplit;
 }
 // the grouped products' digit split (gemm_fp64eq.cu): njobs jobs of eight A
 // rows or 64 B columns
-void launch_eq_group_split(const eq::GSplit *gs, const int4 *jobs, int njobs, cudaStream_t s);
+void launch_eq_group_split(const eq::GSplit *gs, const int4 *jobs, int nrow_jobs, int ncol_jobs, cudaStream_t s);
 unsigned eq_group_check(EqGroup *g, cudaStream_t s);
 double eq_group_flops(const EqGroup *g);
 int eq_group_tiles(const EqGroup *g);
