@@ -60,7 +60,8 @@ struct FftArgs {
 // butterfly g takes r = g + m 8/R; otherwise value r = g R + m is
 // tid + m 512 of column g (L = 512 R).
 template <int R, bool COLFAST, class Pos>
-__device__ __forceinline__ void first_stage_regs(float4 *sd, const float4 *v, const Pos &dst, int log2L, bool inv) {
+__device__ __forceinline__ void first_stage_regs(float4 *sd, const float4 *v, const Pos &dst, int log2L, bool inv,
+                                                 int ps) {
     static_assert(kFftElems / kFftThreads == 8, "eight values per thread");
     constexpr int G = 8 / R;
 #pragma unroll
@@ -71,9 +72,9 @@ __device__ __forceinline__ void first_stage_regs(float4 *sd, const float4 *v, co
         const int r0 = COLFAST ? g : g * R;
         const int col = dst(r0) >> log2L, j = dst(r0) & ((1 << log2L) - 1);
         dft_small<R>(x, inv);
-        float4 *o = sd + (col << log2L) + j * R;
+        const int o = (col << log2L) + j * R;
 #pragma unroll
-        for (int p = 0; p < R; ++p) st_cplx(o + p, x[p]);
+        for (int p = 0; p < R; ++p) st_cplx(sd + sp(o + p, ps), x[p]);
     }
 }
 
@@ -83,8 +84,10 @@ __device__ __forceinline__ void first_stage_regs(float4 *sd, const float4 *v, co
 // Two CTAs per SM (64 registers, no spills; at most 96 KB of shared memory
 // each, the 4096-point table being read in place), so one CTA's global loads
 // and stores overlap the other's butterflies: 2^22 in 0.229 ms instead of
-// 0.262 ms with one.
-template <int MODE>
+// 0.262 ms with one.  PAD: the padded shared-memory layout (every pass
+// length but 2048, fft_padded), a template parameter so that the layout
+// shift is a constant.
+template <int MODE, bool PAD>
 __global__ void __launch_bounds__(kFftThreads, 2) fft_pass_kernel(FftArgs a) {
     extern __shared__ __align__(16) float4 fsmem[];
     float4 *sd = fsmem;
@@ -94,12 +97,13 @@ __global__ void __launch_bounds__(kFftThreads, 2) fft_pass_kernel(FftArgs a) {
     const bool inv = a.inverse != 0;
     const float4 *stw = a.tw;  // the 4096-point table is read in place
     if (twiddles_staged(log2L)) {
-        float4 *t_s = fsmem + kFftElems;
+        float4 *t_s = fsmem + (PAD ? kFftElemsPad : kFftElems);
         for (int t = threadIdx.x; t < stage_table_count(log2L); t += kFftThreads) t_s[t] = a.tw[t];
         stw = t_s;
     }
     // the columns' largest exponents (modes 0, 1), after the staged table
-    int *smax = reinterpret_cast<int *>(fsmem + kFftElems + (twiddles_staged(log2L) ? L : 0));
+    int *smax = reinterpret_cast<int *>(fsmem + (PAD ? kFftElemsPad : kFftElems) + (twiddles_staged(log2L) ? L : 0));
+    constexpr int ps = PAD ? 3 : 30;  // data layout: fft_pad_shift(log2L)
     if (MODE != 2)
         for (int t = threadIdx.x; t < C; t += kFftThreads) smax[t] = 0;
 
@@ -195,22 +199,22 @@ __global__ void __launch_bounds__(kFftThreads, 2) fft_pass_kernel(FftArgs a) {
         }
         if (first_here) {
             if (b0 == 1)
-                first_stage_regs<2, MODE == 1>(sd, v, dst, log2L, inv);
+                first_stage_regs<2, MODE == 1>(sd, v, dst, log2L, inv, ps);
             else if (b0 == 2)
-                first_stage_regs<4, MODE == 1>(sd, v, dst, log2L, inv);
+                first_stage_regs<4, MODE == 1>(sd, v, dst, log2L, inv, ps);
             else
-                first_stage_regs<8, MODE == 1>(sd, v, dst, log2L, inv);
+                first_stage_regs<8, MODE == 1>(sd, v, dst, log2L, inv, ps);
         } else {
 #pragma unroll
-            for (int r = 0; r < kPer; ++r) sd[dst(r)] = v[r];
+            for (int r = 0; r < kPer; ++r) sd[sp(dst(r), ps)] = v[r];
         }
     }
     __syncthreads();
 
     if (first_here)
-        fft_in_smem_after_first(sd, stw, log2L, inv);
+        fft_in_smem_after_first(sd, stw, log2L, inv, ps);
     else
-        fft_in_smem(sd, stw, log2L, inv);
+        fft_in_smem(sd, stw, log2L, inv, ps);
 
     // ---- store
     for (int q = threadIdx.x; q < kFftElems; q += kFftThreads) {
@@ -222,7 +226,7 @@ __global__ void __launch_bounds__(kFftThreads, 2) fft_pass_kernel(FftArgs a) {
             c = q & (C - 1);
             t = q >> (31 - __clz(C));
         }
-        cplx v = ld_cplx(sd + (c << log2L) + t);
+        cplx v = ld_cplx(sd + sp((c << log2L) + t, ps));
         if (MODE == 1) {
             // W_N^{k1 n2}, k1 = t, n2 = c0 + c; m < N so no reduction needed
             const long long m = (long long)t * (c0 + c);
@@ -284,7 +288,7 @@ __global__ void __launch_bounds__(kFftThreads, 2)
     extern __shared__ __align__(16) float4 fsmem[];
     for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
         const FftItem item = items[it];
-        fft_group_item(item, reqs, tlist, expo, fsmem, fsmem + kFftElems, false);
+        fft_group_item(item, reqs, tlist, expo, fsmem, false);
     }
 }
 
@@ -411,11 +415,21 @@ void launch_fft(const FftPlan *p, int batch, int dir, const double *in, double *
     a.n = n;
     a.batch = batch;
     a.inverse = dir > 0 ? 1 : 0;
-    static std::atomic<uint64_t> attr_done[3];
+    static std::atomic<uint64_t> attr_done[6];
     auto smem_for = [&](int log2L) { return fft_smem_bytes(log2L); };
-    auto prep = [&](int mode, const void *fn, size_t smem) {
-        set_smem_limit_once(fn, kFftSmemMax, attr_done[mode]);
-        (void)smem;
+    // the pass kernel of a mode in the layout of a pass length, its shared-
+    // memory limit raised once per device
+    auto pick = [&](int mode, int log2L) {
+        const bool pad = fft_padded(log2L);
+        const void *fn = mode == 0 ? (pad ? (const void *)fft_pass_kernel<0, true> : (const void *)fft_pass_kernel<0, false>)
+                       : mode == 1 ? (pad ? (const void *)fft_pass_kernel<1, true> : (const void *)fft_pass_kernel<1, false>)
+                                   : (pad ? (const void *)fft_pass_kernel<2, true> : (const void *)fft_pass_kernel<2, false>);
+        set_smem_limit_once(fn, kFftSmemMax, attr_done[2 * mode + (pad ? 1 : 0)]);
+        return fn;
+    };
+    auto launch = [&](const void *fn, long long grid, size_t smem) {
+        void *args[] = {&a};
+        OO_CUDA_TRY(cudaLaunchKernel(fn, dim3((unsigned)grid), dim3(kFftThreads), args, smem, s));
     };
     if (!four_step) {
         const int C = kFftElems >> p->log2n;
@@ -423,10 +437,7 @@ void launch_fft(const FftPlan *p, int batch, int dir, const double *in, double *
         a.in_d = in;
         a.out_d = out;
         a.tw = p->tw_single;
-        const size_t smem = smem_for(p->log2n);
-        prep(0, (const void *)fft_pass_kernel<0>, smem);
-        fft_pass_kernel<0><<<grid, kFftThreads, smem, s>>>(a);
-        OO_CUDA_TRY(cudaGetLastError());
+        launch(pick(0, p->log2n), grid, smem_for(p->log2n));
         return;
     }
     const int N1 = 1 << p->log2n1, N2 = 1 << p->log2n2;
@@ -437,20 +448,14 @@ void launch_fft(const FftPlan *p, int batch, int dir, const double *in, double *
         a.tw = p->tw_n1;
         const int C = kFftElems / N1;
         const long long grid = (long long)batch * (N2 / C);
-        const size_t smem = smem_for(p->log2n1);
-        prep(1, (const void *)fft_pass_kernel<1>, smem);
-        fft_pass_kernel<1><<<(unsigned)grid, kFftThreads, smem, s>>>(a);
-        OO_CUDA_TRY(cudaGetLastError());
+        launch(pick(1, p->log2n1), grid, smem_for(p->log2n1));
     }
     {
         a.out_d = out;
         a.tw = p->tw_n2;
         const int R = kFftElems / N2;
         const long long grid = (long long)batch * (N1 / R);
-        const size_t smem = smem_for(p->log2n2);
-        prep(2, (const void *)fft_pass_kernel<2>, smem);
-        fft_pass_kernel<2><<<(unsigned)grid, kFftThreads, smem, s>>>(a);
-        OO_CUDA_TRY(cudaGetLastError());
+        launch(pick(2, p->log2n2), grid, smem_for(p->log2n2));
     }
 }
 

@@ -79,6 +79,19 @@ namespace {
 constexpr int kFftThreads = 512;
 constexpr int kFftBpt = 2;                               // (8 values per thread: 8 / R radix-R butterflies)
 constexpr int kFftElems = 4 * kFftThreads * kFftBpt;     // 4096 values per CTA
+// The values sit in shared memory with one float4 of padding after every
+// eight (value i at sp(i, 3)), so the strided stores of the Stockham stages
+// (R or R Ls float4 apart) and the loads across short columns fall in eight
+// different 16-byte bank groups of a quarter warp instead of one.  Passes of
+// 2048 points keep the unpadded layout (sp(i, 30) = i): with their 32 KB
+// twiddle table the padding would take two CTAs past 196 KB of shared
+// memory per SM, and the smaller L1 that leaves costs more (measured: 2^22
+// 0.205 -> 0.227 ms) than the conflicts.
+constexpr int kFftElemsPad = kFftElems + kFftElems / 8;
+__host__ __device__ __forceinline__ bool fft_padded(int log2L) { return log2L != 11; }
+__host__ __device__ __forceinline__ int fft_pad_shift(int log2L) { return fft_padded(log2L) ? 3 : 30; }
+__host__ __device__ __forceinline__ int fft_data_slots(int log2L) { return fft_padded(log2L) ? kFftElemsPad : kFftElems; }
+__host__ __device__ __forceinline__ int sp(int i, int ps) { return ps >= 30 ? i : i + (i >> ps); }
 constexpr int kTwSplit = 11;                             // four-step twiddle split: 2^11
 
 using ff::cplx;
@@ -165,9 +178,10 @@ __host__ __device__ __forceinline__ size_t fft_colmax_bytes(int log2L) {
     return ((size_t)(kFftElems >> log2L) * 4 + 15) / 16 * 16;
 }
 __host__ __device__ __forceinline__ size_t fft_smem_bytes(int log2L) {
-    return (size_t)(kFftElems + (twiddles_staged(log2L) ? (1 << log2L) : 0)) * 16 + fft_colmax_bytes(log2L);
+    return (size_t)(fft_data_slots(log2L) + (twiddles_staged(log2L) ? (1 << log2L) : 0)) * 16 +
+           fft_colmax_bytes(log2L);
 }
-// the largest of those (L = 2048: 96 KB + 16 bytes)
+// the largest of those (L = 2048, unpadded: 96 KB + 16 bytes)
 constexpr size_t kFftSmemMax = (size_t)(kFftElems + 2048) * 16 + 16;
 
 // 1 / sqrt(2) as a float pair (hi, lo)
@@ -253,9 +267,9 @@ __device__ __forceinline__ void dft_small(cplx *x, bool inv) {
 __host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v >> 1); }
 
 // One Stockham stage of radix R over the CTA's kFftElems values (C columns of
-// length L): 8 / R butterflies per thread.
+// length L): 8 / R butterflies per thread; value i at sd[sp(i, ps)].
 template <int R>
-__device__ __forceinline__ void stage_radix(float4 *sd, const float4 *stw, int log2L, int Ls, bool inv) {
+__device__ __forceinline__ void stage_radix(float4 *sd, const float4 *stw, int log2L, int Ls, bool inv, int ps) {
     constexpr int B = kFftElems / (R * kFftThreads);
     const int log2lr = log2L - ilog2c(R), lr = 1 << log2lr;
     cplx Y[B][R];
@@ -267,7 +281,7 @@ __device__ __forceinline__ void stage_radix(float4 *sd, const float4 *stw, int l
         base_c[b] = c << log2L;
         jj[b] = j;
 #pragma unroll
-        for (int q = 0; q < R; ++q) Y[b][q] = ld_cplx(sd + base_c[b] + j + q * lr);
+        for (int q = 0; q < R; ++q) Y[b][q] = ld_cplx(sd + sp(base_c[b] + j + q * lr, ps));
         if (Ls > 1) {
             const int k = j & (Ls - 1);
 #pragma unroll
@@ -281,30 +295,31 @@ __device__ __forceinline__ void stage_radix(float4 *sd, const float4 *stw, int l
         const int j = jj[b], k = j & (Ls - 1);
         const int o = base_c[b] + (j - k) * R + k;
 #pragma unroll
-        for (int p = 0; p < R; ++p) st_cplx(sd + o + p * Ls, Y[b][p]);
+        for (int p = 0; p < R; ++p) st_cplx(sd + sp(o + p * Ls, ps), Y[b][p]);
     }
     __syncthreads();
 }
 
-// the radix-8 stages after the first stage (which the caller has done)
-__device__ void fft_in_smem_after_first(float4 *sd, const float4 *stw, int log2L, bool inv) {
+// the radix-8 stages after the first stage (which the caller has done);
+// inlined, so a caller's constant layout shift ps stays a constant
+__device__ __forceinline__ void fft_in_smem_after_first(float4 *sd, const float4 *stw, int log2L, bool inv, int ps) {
     for (int Ls = 1 << first_radix_log2(log2L); Ls < (1 << log2L); Ls *= 8) {
-        stage_radix<8>(sd, stw, log2L, Ls, inv);
+        stage_radix<8>(sd, stw, log2L, Ls, inv, ps);
         stw += 7 * Ls;
     }
 }
 
 // the whole transform of every column in shared memory
-__device__ void fft_in_smem(float4 *sd, const float4 *stw, int log2L, bool inv) {
+__device__ __forceinline__ void fft_in_smem(float4 *sd, const float4 *stw, int log2L, bool inv, int ps) {
     if (log2L == 0) return;
     const int b0 = first_radix_log2(log2L);
     if (b0 == 1)
-        stage_radix<2>(sd, stw, log2L, 1, inv);
+        stage_radix<2>(sd, stw, log2L, 1, inv, ps);
     else if (b0 == 2)
-        stage_radix<4>(sd, stw, log2L, 1, inv);
+        stage_radix<4>(sd, stw, log2L, 1, inv, ps);
     else
-        stage_radix<8>(sd, stw, log2L, 1, inv);
-    fft_in_smem_after_first(sd, stw, log2L, inv);
+        stage_radix<8>(sd, stw, log2L, 1, inv, ps);
+    fft_in_smem_after_first(sd, stw, log2L, inv, ps);
 }
 
 // largest biased exponent among the 64-bit words [x0, x1) of p (stride
@@ -397,16 +412,19 @@ __device__ __forceinline__ int scale_from(int e) { return e == 0 ? 0 : e - 1023 
 // resident serving loop alike): mode 0, `count` whole transforms of length
 // 2^log2L (request ids at tlist[first ..]); mode 1 / 2, the four-step column /
 // row pass of request `first` starting at column / row c0.  512 threads; sd
-// holds kFftElems values, stw room for the pass's per-stage twiddle table
-// followed by the columns' exponents: every table is staged there when
-// stage_all is set (callers whose global loads bypass L1), else the
-// 4096-point one is read in place.  Mode 1 raises expo[first] (zero before
+// is the dynamic shared memory: the item's kFftElems values in its layout
+// (fft_data_slots float4), then room for the pass's per-stage twiddle table,
+// then the columns' exponents: every table is staged there when stage_all is
+// set (callers whose global loads bypass L1), else the 4096-point one is
+// read in place.  Mode 1 raises expo[first] (zero before
 // the request's first pass) and writes the request's column exponents;
 // mode 2 reads both.
 __device__ __forceinline__ void fft_group_item(const FftItem &item, const FftGroupReq *reqs, const int *tlist,
-                                               int *expo, float4 *sd, float4 *stw, bool stage_all) {
+                                               int *expo, float4 *sd, bool stage_all) {
     const int log2L = item.log2L, L = 1 << log2L;
     const int C = kFftElems >> log2L;
+    const int ps = fft_pad_shift(log2L);
+    float4 *stw = sd + fft_data_slots(log2L);  // the table after this item's data layout
     const FftGroupReq &R0 = reqs[item.mode == 0 ? tlist[item.first] : item.first];
     const float4 *tw = item.mode == 0 ? R0.tw : (item.mode == 1 ? R0.tw_n1 : R0.tw_n2);
     const bool inv = R0.inverse != 0;
@@ -442,7 +460,7 @@ __device__ __forceinline__ void fft_group_item(const FftItem &item, const FftGro
             int c, t;
             coords(r, c, t);
             const float4 v = R0.mid[(long long)(item.c0 + c) * N2 + t];
-            sd[(c << log2L) + t] = scale_down(v, col_shift(R0.colmax[t], em));
+            sd[sp((c << log2L) + t, ps)] = scale_down(v, col_shift(R0.colmax[t], em));
         }
     } else {
         double2 raw[kPer];
@@ -481,11 +499,11 @@ __device__ __forceinline__ void fft_group_item(const FftItem &item, const FftGro
             float4 v;
             split_scaled(raw[r].x, S, v.x, v.y);
             split_scaled(raw[r].y, S, v.z, v.w);
-            sd[(c << log2L) + t] = v;
+            sd[sp((c << log2L) + t, ps)] = v;
         }
     }
     __syncthreads();
-    fft_in_smem(sd, tws, log2L, inv);
+    fft_in_smem(sd, tws, log2L, inv, ps);
     // ---- store
     for (int q = threadIdx.x; q < kFftElems; q += kFftThreads) {
         int c, t;
@@ -496,7 +514,7 @@ __device__ __forceinline__ void fft_group_item(const FftItem &item, const FftGro
             c = q & (C - 1);
             t = q >> (31 - __clz(C));
         }
-        cplx v = ld_cplx(sd + (c << log2L) + t);
+        cplx v = ld_cplx(sd + sp((c << log2L) + t, ps));
         if (item.mode == 1) {
             const long long m = (long long)t * (item.c0 + c);
             const int mh = (int)(m >> kTwSplit), ml = (int)(m & ((1 << kTwSplit) - 1));

@@ -130,7 +130,7 @@ __device__ __forceinline__ void run_item(const SimtArgs &a, const Entry &E, int 
             it.log2L = R.log2n2;
             it.c0 = i * (kFftElems >> R.log2n2);
         }
-        fft_group_item(it, a.fft, a.tlist, a.expo, sm, sm + kFftElems, true);  // loads here bypass L1
+        fft_group_item(it, a.fft, a.tlist, a.expo, sm, true);  // loads here bypass L1
     } else {
         const JacDesc J = a.jac[E.slot];
         const size_t sj = (size_t)J.pitch, si = (size_t)J.J * J.pitch;
@@ -309,8 +309,8 @@ __global__ void __launch_bounds__(kSimtThreads, 1) resident_simt_kernel(const Si
     }
 }
 
-// FFT data + twiddles (128 KB) + the columns' exponents
-size_t simt_smem_bytes() { return (size_t)2 * kFftElems * sizeof(float4) + 16; }
+// FFT data (padded) + twiddles (up to 64 KB) + the columns' exponents
+size_t simt_smem_bytes() { return (size_t)(kFftElemsPad + kFftElems) * sizeof(float4) + 16; }
 
 // ------------------------------------------------------------- host side
 using Clock = std::chrono::steady_clock;
